@@ -1,0 +1,249 @@
+"""MGFWA CPU oracle (FP64 fitness, exact-FP32 state) -- TEST INFRASTRUCTURE.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the bench's CPU-baseline
+leg load this package.  It wraps the plain C oracle in this directory
+(``philox.c``, ``objective.c``, ``mgfwa.c``) through ctypes; nothing here is
+shared with the CUDA library.  ``build()`` compiles the C sources with gcc
+(``-ffp-contract=off`` so that FP32 state arithmetic is never fused).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SOURCES = ("philox.c", "objective.c", "mgfwa.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+INIT, EXPLODE, MAP, GMAP = 0, 1, 2, 3
+MLP_CE, SPHERE = 0, 1
+TANH, RELU = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liboracle.so``; returns the path."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES]
+    hdr = os.path.join(_HERE, "oracle.h")
+    if not force and os.path.exists(_LIB_PATH):
+        newest = max(os.path.getmtime(p) for p in srcs + [hdr, __file__])
+        if os.path.getmtime(_LIB_PATH) >= newest:
+            return _LIB_PATH
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-pthread", "-o", tmp] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int64), ("lb", ctypes.c_float), ("ub", ctypes.c_float),
+                ("mu", ctypes.c_int32), ("lam", ctypes.c_int32), ("m", ctypes.c_int32),
+                ("k", ctypes.c_int32), ("beta", ctypes.c_float), ("amp0", ctypes.c_float),
+                ("c_a", ctypes.c_float), ("c_r", ctypes.c_float)]
+
+
+class Objective(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("dim", ctypes.c_int64), ("n_layers", ctypes.c_int32),
+                ("widths", ctypes.POINTER(ctypes.c_int32)), ("acts", ctypes.POINTER(ctypes.c_int32)),
+                ("n_samples", ctypes.c_int64), ("X", ctypes.POINTER(ctypes.c_float)),
+                ("y", ctypes.POINTER(ctypes.c_int32))]
+
+
+def _p(a: np.ndarray, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            f32p, i32p, u32p = (ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int32),
+                                ctypes.POINTER(ctypes.c_uint32))
+            f64p, i64p = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)
+            pp, op = ctypes.POINTER(Params), ctypes.POINTER(Objective)
+            L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+            L.orc_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                      ctypes.c_uint32, ctypes.c_int64]
+            L.orc_uniform.restype = ctypes.c_float
+            L.orc_subset_size.argtypes = [ctypes.c_float, ctypes.c_int32]
+            L.orc_subset_size.restype = ctypes.c_int32
+            L.orc_fitness.argtypes = [op, f32p]
+            L.orc_fitness.restype = ctypes.c_double
+            L.orc_fitness_many.argtypes = [op, f32p, ctypes.c_int64, ctypes.c_int64, f64p, ctypes.c_int32]
+            L.orc_init.argtypes = [pp, ctypes.c_uint64, f32p, f32p]
+            L.orc_explode.argtypes = [pp, ctypes.c_uint64, ctypes.c_uint32, f32p, f32p, f32p]
+            L.orc_rank.argtypes = [pp, f32p, i32p, i32p]
+            L.orc_guide.argtypes = [pp, ctypes.c_uint64, ctypes.c_uint32, f32p, f32p, f32p, i32p, i32p, f32p]
+            L.orc_select.argtypes = [pp, f32p, f32p, f32p, f32p, f32p, f32p, f32p, i32p]
+            L.orc_run.argtypes = [pp, op, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                  f32p, f64p, i64p, i32p, f32p]
+            L.orc_run.restype = ctypes.c_int32
+            _lib = L
+    return _lib
+
+
+# ---------------------------------------------------------------------------
+# Thin numpy-facing helpers.
+
+def philox(ctr: Sequence[int], key: Sequence[int]) -> np.ndarray:
+    c = np.asarray(ctr, dtype=np.uint32)
+    k = np.asarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_p(c, ctypes.c_uint32), _p(k, ctypes.c_uint32), _p(out, ctypes.c_uint32))
+    return out
+
+
+def uniform(seed: int, purpose: int, gen: int, unit: int, coord: int) -> float:
+    return float(lib().orc_uniform(seed, purpose, gen, unit, coord))
+
+
+def subset_size(sigma: float, g: int) -> int:
+    return int(lib().orc_subset_size(sigma, g))
+
+
+def make_params(dim, lb, ub, mu, lam, m, sigma=0.2, k=None, beta=1.0, amp0=None, c_a=1.2, c_r=0.9) -> Params:
+    if k is None:
+        k = subset_size(sigma, lam // m)
+    if amp0 is None:
+        amp0 = float(np.float32(ub) - np.float32(lb))
+    return Params(dim, lb, ub, mu, lam, m, k, beta, amp0, c_a, c_r)
+
+
+def params_for(w, **over) -> Params:
+    """Oracle parameters of a workloads.Workload (defaults: beta 1, A0 = ub - lb, 1.2 / 0.9)."""
+    kw = dict(dim=w.dim, lb=w.lb, ub=w.ub, mu=w.n_fireworks, lam=w.sparks_per_firework,
+              m=w.guiding_per_firework, sigma=w.sigma)
+    kw.update(over)
+    return make_params(**kw)
+
+
+class Problem:
+    """An objective plus the buffers it points into (kept alive here)."""
+
+    def __init__(self, kind: int, dim: int, widths=(), acts=(), X=None, y=None):
+        self.widths = np.ascontiguousarray(widths, dtype=np.int32) if len(widths) else np.zeros(1, np.int32)
+        self.acts = np.ascontiguousarray(acts, dtype=np.int32) if len(acts) else np.zeros(1, np.int32)
+        self.X = np.ascontiguousarray(X if X is not None else np.zeros((1, 1)), dtype=np.float32)
+        self.y = np.ascontiguousarray(y if y is not None else np.zeros(1), dtype=np.int32)
+        n = 0 if X is None else self.X.shape[0]
+        self.obj = Objective(kind, dim, max(len(widths) - 1, 0), _p(self.widths, ctypes.c_int32),
+                             _p(self.acts, ctypes.c_int32), n, _p(self.X, ctypes.c_float),
+                             _p(self.y, ctypes.c_int32))
+
+    @classmethod
+    def for_workload(cls, w, X=None, y=None):
+        if w.kind == SPHERE:
+            return cls(SPHERE, w.dim)
+        if X is None:
+            import workloads
+            X, y = workloads.make_data(w)
+        return cls(MLP_CE, w.dim, w.widths, w.acts, X, y)
+
+    def fitness(self, x: np.ndarray) -> float:
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        return float(lib().orc_fitness(ctypes.byref(self.obj), _p(x, ctypes.c_float)))
+
+    def fitness_many(self, xs: np.ndarray, n_threads: int = 1) -> np.ndarray:
+        xs = np.ascontiguousarray(xs, dtype=np.float32)
+        out = np.zeros(xs.shape[0], dtype=np.float64)
+        lib().orc_fitness_many(ctypes.byref(self.obj), _p(xs, ctypes.c_float), xs.shape[0], xs.shape[1],
+                               _p(out, ctypes.c_double), n_threads)
+        return out
+
+
+def init(p: Params, seed: int):
+    x = np.zeros((p.mu, p.dim), np.float32)
+    a = np.zeros(p.mu, np.float32)
+    lib().orc_init(ctypes.byref(p), seed, _p(x, ctypes.c_float), _p(a, ctypes.c_float))
+    return x, a
+
+
+def explode(p: Params, seed: int, gen: int, fw_x: np.ndarray, fw_amp: np.ndarray) -> np.ndarray:
+    fw_x = np.ascontiguousarray(fw_x, np.float32)
+    fw_amp = np.ascontiguousarray(fw_amp, np.float32)
+    s = np.zeros((p.mu * p.lam, p.dim), np.float32)
+    lib().orc_explode(ctypes.byref(p), seed, gen, _p(fw_x, ctypes.c_float), _p(fw_amp, ctypes.c_float),
+                      _p(s, ctypes.c_float))
+    return s
+
+
+def rank(p: Params, fit_e: np.ndarray):
+    f = np.ascontiguousarray(fit_e, np.float32)
+    top = np.zeros((p.mu, p.m, p.k), np.int32)
+    bot = np.zeros((p.mu, p.m, p.k), np.int32)
+    lib().orc_rank(ctypes.byref(p), _p(f, ctypes.c_float), _p(top, ctypes.c_int32), _p(bot, ctypes.c_int32))
+    return top, bot
+
+
+def guide(p: Params, seed: int, gen: int, fw_x, fw_amp, sparks, top, bottom) -> np.ndarray:
+    fw_x = np.ascontiguousarray(fw_x, np.float32)
+    fw_amp = np.ascontiguousarray(fw_amp, np.float32)
+    sparks = np.ascontiguousarray(sparks, np.float32)
+    top = np.ascontiguousarray(top, np.int32)
+    bottom = np.ascontiguousarray(bottom, np.int32)
+    g = np.zeros((p.mu * p.m, p.dim), np.float32)
+    lib().orc_guide(ctypes.byref(p), seed, gen, _p(fw_x, ctypes.c_float), _p(fw_amp, ctypes.c_float),
+                    _p(sparks, ctypes.c_float), _p(top, ctypes.c_int32), _p(bottom, ctypes.c_int32),
+                    _p(g, ctypes.c_float))
+    return g
+
+
+def select(p: Params, fit_e, fit_g, sparks, guides, fw_x, fw_amp, fw_f):
+    """Returns updated copies (fw_x, fw_amp, fw_f, winner)."""
+    fit_e = np.ascontiguousarray(fit_e, np.float32)
+    fit_g = np.ascontiguousarray(fit_g, np.float32)
+    sparks = np.ascontiguousarray(sparks, np.float32)
+    guides = np.ascontiguousarray(guides, np.float32)
+    fw_x = np.array(fw_x, np.float32, copy=True)
+    fw_amp = np.array(fw_amp, np.float32, copy=True)
+    fw_f = np.array(fw_f, np.float32, copy=True)
+    win = np.zeros(p.mu, np.int32)
+    lib().orc_select(ctypes.byref(p), _p(fit_e, ctypes.c_float), _p(fit_g, ctypes.c_float),
+                     _p(sparks, ctypes.c_float), _p(guides, ctypes.c_float), _p(fw_x, ctypes.c_float),
+                     _p(fw_amp, ctypes.c_float), _p(fw_f, ctypes.c_float), _p(win, ctypes.c_int32))
+    return fw_x, fw_amp, fw_f, win
+
+
+def run(p: Params, prob: Problem, seed: int, budget: int, max_gens: int = 1 << 30,
+        n_threads: int = 1, want_trace: bool = False):
+    """A whole oracle run.  Returns dict(best_x, best_f, evals, gens, trace)."""
+    best_x = np.zeros(p.dim, np.float32)
+    best_f = ctypes.c_double(0.0)
+    evals = ctypes.c_int64(0)
+    gens = ctypes.c_int32(0)
+    per = p.mu * (p.lam + p.m)
+    cap = min(max_gens, max(0, (budget - p.mu) // per))
+    trace = np.zeros(max(cap, 1), np.float32) if want_trace else None
+    rc = lib().orc_run(ctypes.byref(p), ctypes.byref(prob.obj), seed, budget, min(max_gens, 1 << 30),
+                       n_threads, _p(best_x, ctypes.c_float), ctypes.byref(best_f), ctypes.byref(evals),
+                       ctypes.byref(gens), _p(trace, ctypes.c_float) if trace is not None else None)
+    if rc != 0:
+        raise ValueError("oracle run rejected its parameters")
+    out = dict(best_x=best_x, best_f=best_f.value, evals=evals.value, gens=gens.value)
+    if trace is not None:
+        out["trace"] = trace[:gens.value]
+    return out
+
+
+def generation(p: Params, prob: Problem, seed: int, gen: int, fw_x, fw_amp, fw_f, n_threads: int = 1):
+    """One oracle generation, returning every intermediate (for step-by-step parity)."""
+    sparks = explode(p, seed, gen, fw_x, fw_amp)
+    fit_e64 = prob.fitness_many(sparks, n_threads)
+    fit_e = fit_e64.astype(np.float32)
+    top, bot = rank(p, fit_e)
+    guides = guide(p, seed, gen, fw_x, fw_amp, sparks, top, bot)
+    fit_g64 = prob.fitness_many(guides, n_threads)
+    fit_g = fit_g64.astype(np.float32)
+    nx, na, nf, win = select(p, fit_e, fit_g, sparks, guides, fw_x, fw_amp, fw_f)
+    return dict(sparks=sparks, fit_e64=fit_e64, fit_e=fit_e, top=top, bottom=bot, guides=guides,
+                fit_g64=fit_g64, fit_g=fit_g, fw_x=nx, fw_amp=na, fw_f=nf, winner=win)

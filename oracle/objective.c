@@ -1,0 +1,110 @@
+/*
+ * Oracle objectives in FP64 -- TEST INFRASTRUCTURE ONLY (see oracle.h).
+ *
+ * The black box f of Algorithm 1 (the paper's Sec. 4.1, Eq. 1 minimises the
+ * output of a fixed network; here the search vector is the network's own
+ * flattened parameters and f is its mean cross-entropy on a fixed batch):
+ *
+ *   a_0 = x_n;  a_l = act(W_l a_{l-1} + b_l) for hidden layers;
+ *   z = W_L a_{L-1} + b_L;
+ *   f = (1/N) sum_n [ log sum_c exp(z_c) - z_{y_n} ],
+ *
+ * with parameters laid out in torch nn.Linear order (W_1[h1][d_in]
+ * row-major, b_1, W_2[h2][h1], b_2, ...).  log-sum-exp subtracts max_c z_c
+ * first.  Every multiply and add is plain double arithmetic in index order.
+ *
+ * The sphere objective f(x) = sum_k x_k^2 is kept for convergence checks.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "oracle.h"
+
+static double act(int32_t kind, double v) {
+  if (kind == ORC_TANH) return tanh(v);
+  return v > 0.0 ? v : 0.0;
+}
+
+static double mlp_ce(const orc_objective* obj, const float* x) {
+  const int32_t L = obj->n_layers;
+  int32_t wmax = 0;
+  for (int32_t l = 0; l <= L; ++l)
+    if (obj->widths[l] > wmax) wmax = obj->widths[l];
+  double* a = (double*)malloc(sizeof(double) * (size_t)wmax);
+  double* b = (double*)malloc(sizeof(double) * (size_t)wmax);
+  double total = 0.0;
+  for (int64_t n = 0; n < obj->n_samples; ++n) {
+    const int32_t d0 = obj->widths[0];
+    for (int32_t i = 0; i < d0; ++i) a[i] = (double)obj->X[n * d0 + i];
+    const float* p = x;
+    for (int32_t l = 0; l < L; ++l) {
+      const int32_t fan_in = obj->widths[l], fan_out = obj->widths[l + 1];
+      const float* W = p;
+      const float* bias = p + (int64_t)fan_in * fan_out;
+      for (int32_t j = 0; j < fan_out; ++j) {
+        double s = (double)bias[j];
+        for (int32_t i = 0; i < fan_in; ++i) s += (double)W[(int64_t)j * fan_in + i] * a[i];
+        b[j] = (l + 1 < L) ? act(obj->acts[l], s) : s;
+      }
+      p = bias + fan_out;
+      double* t = a; a = b; b = t;
+    }
+    const int32_t C = obj->widths[L];
+    double zmax = a[0];
+    for (int32_t c = 1; c < C; ++c)
+      if (a[c] > zmax) zmax = a[c];
+    double se = 0.0;
+    for (int32_t c = 0; c < C; ++c) se += exp(a[c] - zmax);
+    total += (zmax + log(se)) - a[obj->y[n]];
+  }
+  free(a);
+  free(b);
+  return total / (double)obj->n_samples;
+}
+
+double orc_fitness(const orc_objective* obj, const float* x) {
+  if (obj->kind == ORC_SPHERE) {
+    double s = 0.0;
+    for (int64_t k = 0; k < obj->dim; ++k) s += (double)x[k] * (double)x[k];
+    return s;
+  }
+  return mlp_ce(obj, x);
+}
+
+typedef struct {
+  const orc_objective* obj;
+  const float* xs;
+  int64_t begin, end, stride;
+  double* out;
+} fit_job;
+
+static void* fit_worker(void* arg) {
+  fit_job* j = (fit_job*)arg;
+  for (int64_t i = j->begin; i < j->end; ++i) j->out[i] = orc_fitness(j->obj, j->xs + i * j->stride);
+  return NULL;
+}
+
+void orc_fitness_many(const orc_objective* obj, const float* xs, int64_t count, int64_t stride,
+                      double* out, int32_t n_threads) {
+  if (n_threads <= 1 || count < 2) {
+    for (int64_t i = 0; i < count; ++i) out[i] = orc_fitness(obj, xs + i * stride);
+    return;
+  }
+  if (n_threads > count) n_threads = (int32_t)count;
+  pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)n_threads);
+  fit_job* jobs = (fit_job*)malloc(sizeof(fit_job) * (size_t)n_threads);
+  for (int32_t t = 0; t < n_threads; ++t) {
+    jobs[t].obj = obj;
+    jobs[t].xs = xs;
+    jobs[t].stride = stride;
+    jobs[t].out = out;
+    jobs[t].begin = count * t / n_threads;
+    jobs[t].end = count * (t + 1) / n_threads;
+    pthread_create(&th[t], NULL, fit_worker, &jobs[t]);
+  }
+  for (int32_t t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+  free(th);
+  free(jobs);
+}

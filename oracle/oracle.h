@@ -1,0 +1,99 @@
+/*
+ * MGFWA CPU oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-purpose restatement of one generation of the
+ * Multi-Guiding Spark Fireworks Algorithm (GPU-MGFWA, Algorithm 1) used to
+ * check the CUDA library.  Only the test suite, the smoke check and the
+ * bench's CPU-baseline leg may load it.  It shares no code with the CUDA
+ * path: its own Philox4x32-10 (Salmon et al., SC'11), its own MLP forward in
+ * FP64, its own ranking, guiding and selection loops.
+ *
+ * Precision contract:
+ *  - fitness (MLP cross-entropy, sphere) is computed in FP64;
+ *  - spark positions, amplitudes and guiding vectors use exact FP32
+ *    arithmetic in a fixed order (every product-add is an explicit fmaf);
+ *  - every decision (rank, argmin, strict improvement) is taken on FP32
+ *    fitness, the precision the kernels decide in: callers round the FP64
+ *    fitness to FP32 before ranking or selection.
+ *
+ * Readings of passages the paper leaves open are stated at each function.
+ * The build must use -ffp-contract=off so that no a*b+c is fused behind the
+ * code's back (gcc contracts by default on aarch64).
+ */
+#ifndef MGFWA_ORACLE_H
+#define MGFWA_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Philox stream purposes (the fourth counter word). */
+enum { ORC_INIT = 0, ORC_EXPLODE = 1, ORC_MAP = 2, ORC_GMAP = 3 };
+
+/* Objective kinds and hidden activations. */
+enum { ORC_MLP_CE = 0, ORC_SPHERE = 1 };
+enum { ORC_TANH = 0, ORC_RELU = 1 };
+
+typedef struct {
+  int64_t dim;      /* D */
+  float lb, ub;     /* scalar box bounds */
+  int32_t mu;       /* fireworks */
+  int32_t lam;      /* explosion sparks per firework */
+  int32_t m;        /* guiding sparks per firework; lam % m == 0 */
+  int32_t k;        /* top/bottom subset size per guiding group */
+  float beta;       /* guiding-vector boost */
+  float amp0;       /* initial amplitude */
+  float c_a, c_r;   /* amplitude amplification / reduction factors */
+} orc_params;
+
+typedef struct {
+  int32_t kind;            /* ORC_MLP_CE or ORC_SPHERE */
+  int64_t dim;             /* D (the sphere's length; the MLP's parameter count) */
+  int32_t n_layers;        /* linear layers (MLP) */
+  const int32_t* widths;   /* n_layers + 1 widths: d_in, h1, ..., C */
+  const int32_t* acts;     /* n_layers - 1 hidden activations */
+  int64_t n_samples;       /* N */
+  const float* X;          /* [N][d_in] row-major */
+  const int32_t* y;        /* [N] labels in [0, C) */
+} orc_objective;
+
+/* Philox4x32 with 10 rounds: out = bijection(ctr) keyed by key. */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Uniform in [0,1) on a 2^-24 grid for coordinate `coord` of unit `unit`. */
+float orc_uniform(uint64_t seed, uint32_t purpose, uint32_t gen, uint32_t unit, int64_t coord);
+
+/* Subset size k from sigma and the group size g. */
+int32_t orc_subset_size(float sigma, int32_t g);
+
+/* FP64 objective value of one FP32 search vector. */
+double orc_fitness(const orc_objective* obj, const float* x);
+
+/* FP64 objective of `count` vectors spaced `stride` floats apart. */
+void orc_fitness_many(const orc_objective* obj, const float* xs, int64_t count, int64_t stride,
+                      double* out, int32_t n_threads);
+
+void orc_init(const orc_params* p, uint64_t seed, float* fw_x, float* fw_amp);
+void orc_explode(const orc_params* p, uint64_t seed, uint32_t gen, const float* fw_x,
+                 const float* fw_amp, float* sparks);
+void orc_rank(const orc_params* p, const float* fit_e, int32_t* top, int32_t* bottom);
+void orc_guide(const orc_params* p, uint64_t seed, uint32_t gen, const float* fw_x,
+               const float* fw_amp, const float* sparks, const int32_t* top,
+               const int32_t* bottom, float* guides);
+void orc_select(const orc_params* p, const float* fit_e, const float* fit_g, const float* sparks,
+                const float* guides, float* fw_x, float* fw_amp, float* fw_f, int32_t* winner);
+
+/* A whole run: init, then generations while the budget allows (and at most
+ * max_gens).  Writes the best vector, its FP64 fitness, the evaluations
+ * used and the generations run; trace (optional, max_gens entries) gets the
+ * run's FP32 best-so-far after each generation.  Returns 0 on success. */
+int32_t orc_run(const orc_params* p, const orc_objective* obj, uint64_t seed, int64_t budget,
+                int32_t max_gens, int32_t n_threads, float* best_x, double* best_f,
+                int64_t* evals_out, int32_t* gens_out, float* trace);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
