@@ -1,0 +1,301 @@
+"""Throughput of one MGFWA generation on GB300: sparks evaluated per second.
+
+A step is one generation (explosion sampling + mapping, fitness of every
+spark, per-firework ranking, multi-guiding sparks + mapping, their fitness,
+selection and amplitude update) of the 784-64(ReLU)-10 weight-space workload
+(D = 50,890, N = 2048, 5 fireworks x 200 explosion sparks + 8 guiding sparks,
+1040 sparks per generation) on synthetic clipped-prototype data.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32]
+        python bench.py --impl reference ...   (the CPU oracle on host cores)
+Under torchrun each rank runs its own independent run (seed + rank): runs do
+not communicate, so scaling is weak and there is no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+import workloads as W
+
+WORKLOAD = W.MLP_784_64_10
+METRIC = "sparks evaluated/sec"
+UNIT = "sparks/s"
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("bf16_tflops_sustained", 1700.0), "measured"
+    return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.dev = device_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        if not getattr(self, "lines", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unparsed"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# The CPU oracle: a bounded sample of the same workload (one firework of the
+# five, i.e. 200 explosion + 8 guiding sparks of one generation).
+
+def _oracle_sample_step(orc, prob, p1, seed, gen, fw_x, fw_a, fw_f, threads):
+    out = orc.generation(p1, prob, seed, gen, fw_x, fw_a, fw_f, n_threads=threads)
+    return out["fw_x"], out["fw_amp"], out["fw_f"], p1.mu * (p1.lam + p1.m)
+
+
+def cpu_baseline(steps: int = 1, warmup: int = 0):
+    import oracle as orc
+    threads = os.cpu_count() or 1
+    X, y = W.make_data(WORKLOAD)
+    prob = orc.Problem.for_workload(WORKLOAD, X, y)
+    p1 = orc.params_for(WORKLOAD, mu=1)
+    fw_x, fw_a = orc.init(p1, 0)
+    fw_f = prob.fitness_many(fw_x, threads).astype(np.float32)
+    gen = 0
+    for _ in range(warmup):
+        gen += 1
+        fw_x, fw_a, fw_f, _ = _oracle_sample_step(orc, prob, p1, 0, gen, fw_x, fw_a, fw_f, threads)
+    sparks = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        gen += 1
+        fw_x, fw_a, fw_f, n = _oracle_sample_step(orc, prob, p1, 0, gen, fw_x, fw_a, fw_f, threads)
+        sparks += n
+    dt = time.perf_counter() - t0
+    return {"value": sparks / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{steps} oracle generation(s) of 1 of the 5 fireworks ({p1.lam}+{p1.m} sparks each) of "
+                      f"{WORKLOAD.name}, FP64 fitness, {threads} threads", "seconds": dt}
+
+
+def reference_arm(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    cb = cpu_baseline(steps=args.steps, warmup=args.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * cb["seconds"] / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(args, world),
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(args, world):
+    return {"workload": WORKLOAD.name, "widths": list(WORKLOAD.widths), "dim": WORKLOAD.dim,
+            "n_samples": WORKLOAD.n_samples, "fireworks": WORKLOAD.n_fireworks,
+            "sparks_per_firework": WORKLOAD.sparks_per_firework,
+            "guiding_per_firework": WORKLOAD.guiding_per_firework,
+            "sparks_per_generation": WORKLOAD.sparks_per_generation, "runs": world,
+            "parallelism": f"independent runs x{world}",
+            "l2": "working set > L2: 203.6 MB FP32 sparks + 101.8 MB BF16 operand rewritten every generation"}
+
+
+# ---------------------------------------------------------------------------
+
+def gpu_arm(args):
+    import torch
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2501_03944_gb300 as pkg
+    pkg.load_library()
+    prec = {"bf16": pkg.MGFWA_BF16, "fp32": pkg.MGFWA_FP32}[args.precision]
+    X, y = W.make_data(WORKLOAD)
+    seed = 1000 + rank
+    stream = torch.cuda.Stream()
+    hbm_peak, bf16_peak, bf16_sus, peak_src = _peaks()
+    P = WORKLOAD.sparks_per_generation
+
+    budget_gens = args.warmup + args.steps + 2
+    w = W.scaled(WORKLOAD, eval_budget=W.budget_for_generations(WORKLOAD.n_fireworks, WORKLOAD.sparks_per_firework,
+                                                                 WORKLOAD.guiding_per_firework, budget_gens))
+    run = pkg.Mgfwa.for_workload(w, seed, precision=prec, X=X, y=y, stream=stream.cuda_stream)
+    run.step(args.warmup)
+    torch.cuda.synchronize()
+    run.profile(True)
+    launches0 = run.info().kernel_launches
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        run.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    launches = run.info().kernel_launches - launches0
+    ms = ev0.elapsed_time(ev1)
+    ktimes = run.kernel_times()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    _, best_f, evals = run.best()
+    run.close()
+
+    # end to end through the C ABI with host buffers: create (copies X, y from pinned host memory),
+    # K generations, best position + FP64 loss back to the host, destroy.
+    Xp = torch.from_numpy(X).pin_memory().numpy()
+    yp = torch.from_numpy(y).pin_memory().numpy()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    run2 = pkg.Mgfwa.for_workload(w, seed + 7919, precision=prec, X=Xp, y=yp, stream=stream.cuda_stream)
+    run2.step(args.steps)
+    bx2, bf2, ev2 = run2.best()
+    run2.close()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank == 0:
+        sparks_total = world * P * args.steps
+        value = sparks_total / (ms / 1e3)
+        e2e_sparks = world * (WORKLOAD.n_fireworks + P * args.steps)
+        # dominant kernel: the explosion-spark fitness launch (mu*lambda sparks per launch)
+        fit_ms, fit_n = ktimes["fitness_explosion"]
+        n_e = WORKLOAD.n_fireworks * WORKLOAD.sparks_per_firework
+        flops = WORKLOAD.flops_per_spark() * n_e
+        avg_s = fit_ms / max(fit_n, 1) / 1e3
+        kernels = {g: {"ms_total": round(t, 4), "launches": n, "share": round(t / max(ms, 1e-9), 4)}
+                   for g, (t, n) in ktimes.items()}
+        if prec == pkg.MGFWA_BF16:
+            roof = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": bf16_sus, "unit": "TFLOP/s",
+                    "peak_source": f"{peak_src} bf16 sustained (kernel timed inside a long step)"}
+        else:
+            # FP32 CUDA-core path: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+            fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+            roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x 2070 MHz"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["traffic"] = None
+        roof["kernel"] = "fitness of the explosion sparks (1000 sparks x 2048 samples per launch)"
+        # HBM-bound kernels: algorithmic bytes / time
+        D = WORKLOAD.dim
+        w1 = WORKLOAD.widths[0] * WORKLOAD.widths[1]
+        op_b = 2 * w1 if prec == pkg.MGFWA_BF16 else 0
+        exp_bytes = n_e * (4 * D + op_b)
+        k = 5
+        n_g = WORKLOAD.n_fireworks * WORKLOAD.guiding_per_firework
+        guide_bytes = n_g * (2 * k * 4 * D + 4 * D + op_b)
+        hbm = {}
+        for g, b in (("explode", exp_bytes), ("guide", guide_bytes)):
+            t, n = ktimes[g]
+            if n:
+                gbs = b / (t / n / 1e3) / 1e9
+                hbm[g] = {"GB/s": round(gbs, 1), "frac": round(gbs / hbm_peak, 4), "bytes_per_launch": b}
+        cb = None
+        if world == 1 and not args.no_cpu_baseline:
+            c = cpu_baseline(steps=3)
+            cb = {k2: c[k2] for k2 in ("value", "unit", "cores", "kind", "sample")}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": {"bf16": "bf16", "fp32": "f32"}[args.precision],
+                "data": "synthetic", "config": _config(args, world),
+                "clocks": clk.summary(), "gpu_launches": launches,
+                "e2e": {"value": e2e_sparks / e2e_s, "unit": UNIT,
+                        "h2d_bytes_per_step": (X.nbytes + y.nbytes) / args.steps,
+                        "d2h_bytes_per_step": (4 * D + 8) / args.steps,
+                        "note": "create (X, y from pinned host) + K generations + best (x, FP64 loss) + destroy"},
+                "roofline": roof, "hbm_kernels": hbm, "kernels": kernels,
+                "best_f_fp64": best_f, "evals": evals, "cpu_baseline": cb}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=("gb300", "reference"))
+    ap.add_argument("--precision", default="bf16", choices=("bf16", "fp32"))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,146 @@
+/*
+ * mgfwa.h -- C ABI of a GB300 (sm_103a) library that runs the Multi-Guiding
+ * Spark Fireworks Algorithm (GPU-MGFWA, arXiv 2501.03944) on one GPU.
+ *
+ * Problem statement (Algorithm 1, Sec. 3; Eq. 1, Sec. 4.1): given a black box
+ * f over a D-dimensional box [lb, ub]^D, return the best position found and
+ * its fitness.  One generation of Algorithm 1 is: explosion sparks around
+ * each firework with random mapping of out-of-bound coordinates, multi-
+ * guiding sparks built from the ranked explosion sparks, random mapping,
+ * fitness of every spark, and selection of the best individual of each
+ * firework's population with the dynamic amplitude update.
+ *
+ * The black box here is the mean cross-entropy of a small MLP whose
+ * flattened parameters (torch nn.Linear order: W1[h1][d_in] row-major, b1,
+ * W2[h2][h1], b2, ...) are the search vector, on a fixed labelled batch; a
+ * sphere objective (sum of squares) is kept for convergence checks.
+ *
+ * Conventions for every call:
+ *  - Pointers in this header are HOST pointers unless a name says _dev.
+ *    The library copies what it needs at create time; the caller keeps
+ *    ownership of its buffers.
+ *  - The handle owns all device memory it uses (one allocation made at
+ *    create time and freed by mgfwa_destroy) and one CUDA stream (the
+ *    caller's, if given, else its own).
+ *  - Every call returns a status.  After MGFWA_ECUDA the handle can only be
+ *    destroyed.  mgfwa_last_error() gives a one-line reason.
+ *  - One handle per host thread at a time; several handles may share a GPU.
+ */
+#ifndef MGFWA_H
+#define MGFWA_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MGFWA_API __attribute__((visibility("default")))
+#else
+#define MGFWA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MGFWA_OK = 0,
+  MGFWA_EINVAL = 1,   /* an argument or configuration is invalid */
+  MGFWA_ENOMEM = 2,   /* device or host allocation failed */
+  MGFWA_ECUDA = 3,    /* a CUDA call failed; the handle is unusable */
+  MGFWA_ETIMEOUT = 4, /* a bounded device-side wait gave up */
+  MGFWA_EBUDGET = 5   /* the evaluation budget does not allow another generation */
+} mgfwa_status;
+
+typedef enum {
+  MGFWA_FP32 = 0, /* FP32 CUDA-core fitness */
+  MGFWA_BF16 = 1, /* BF16 tensor-core first layer (tcgen05), FP32 accumulate */
+  MGFWA_FP8 = 2   /* reserved: FP8 E4M3 first layer with per-spark scales */
+} mgfwa_precision;
+
+enum { MGFWA_OBJ_MLP_CE = 0, MGFWA_OBJ_SPHERE = 1 };
+enum { MGFWA_ACT_TANH = 0, MGFWA_ACT_RELU = 1 };
+
+typedef struct {
+  int64_t dim;                  /* D; equals the MLP parameter count for MLP objectives */
+  float lb, ub;                 /* scalar bounds, lb < ub */
+  int32_t n_fireworks;          /* mu >= 1 */
+  int32_t sparks_per_firework;  /* lambda, a multiple of m */
+  int32_t guiding_per_firework; /* m >= 1; group size g = lambda / m <= 1024 */
+  float sigma;                  /* top/bottom fraction: k = round-half-up(sigma g) clamped to [1, g/2] */
+  float boost;                  /* beta: guiding spark = x + beta * GV (default 1) */
+  float amp_init;               /* A0 (default ub - lb) */
+  float c_amplify, c_reduce;    /* amplitude factors on improvement / no improvement (1.2, 0.9) */
+  int64_t eval_budget;          /* total evaluations, including the mu initial ones */
+  uint64_t seed;                /* Philox key */
+  int32_t precision;            /* mgfwa_precision */
+  int32_t elite_rescore;        /* reserved: re-score elite candidates in FP32 (low precision only) */
+} mgfwa_config;
+
+typedef struct {
+  int32_t kind;          /* MGFWA_OBJ_MLP_CE or MGFWA_OBJ_SPHERE */
+  int32_t n_layers;      /* linear layers, 2 or 3 (MLP) */
+  const int32_t* widths; /* n_layers + 1 widths d_in, h1, [h2,] C; d_in % 8 == 0, h1 <= 256, C <= 32 */
+  const int32_t* acts;   /* n_layers - 1 hidden activations (MGFWA_ACT_*) */
+  int64_t n_samples;     /* N >= 1 */
+  const float* X;        /* [N][d_in] row-major FP32 */
+  const int32_t* y;      /* [N] labels in [0, C) */
+} mgfwa_objective;
+
+typedef struct mgfwa_handle mgfwa_t;
+
+/* Fill *cfg with the defaults (beta 1, A0 = ub - lb once bounds are set,
+ * C_a 1.2, C_r 0.9, sigma 0.2, FP32).  Fields the caller must still set:
+ * dim, lb, ub, n_fireworks, sparks_per_firework, guiding_per_firework,
+ * eval_budget, seed.  amp_init <= 0 means ub - lb. */
+MGFWA_API mgfwa_status mgfwa_config_init(mgfwa_config* cfg);
+
+/* Validate, allocate device state, copy the objective's batch, initialise
+ * the mu fireworks (Algorithm 1, init) and evaluate them.  `cuda_stream`
+ * is a cudaStream_t or NULL (the handle then creates its own).  On success
+ * *out is a new handle; on failure *out is NULL and nothing is leaked.
+ * Errors: EINVAL (configuration), ENOMEM, ECUDA. */
+MGFWA_API mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, void* cuda_stream,
+                          mgfwa_t** out);
+
+/* Enqueue up to n_generations generations on the handle's stream; stops
+ * early (without error) when the budget allows no further generation.
+ * Returns EBUDGET if not even one generation fits.  Asynchronous. */
+MGFWA_API mgfwa_status mgfwa_step(mgfwa_t* h, int32_t n_generations);
+
+/* Run generations until the budget is spent, then synchronise. */
+MGFWA_API mgfwa_status mgfwa_run(mgfwa_t* h);
+
+/* Synchronise; write the best position so far (x_out: D floats, may be
+ * NULL), its fitness recomputed in FP64 on the GPU (f_out, may be NULL) and
+ * the evaluations used (evals_out, may be NULL). */
+MGFWA_API mgfwa_status mgfwa_best(mgfwa_t* h, float* x_out, double* f_out, int64_t* evals_out);
+
+/* Evaluate `count` host vectors (each D floats, row-major) with the
+ * handle's objective in the given precision; f_out gets count FP32 values.
+ * Uses the handle's device workspace (count <= the sparks of one
+ * generation) and synchronises. */
+MGFWA_API mgfwa_status mgfwa_evaluate(mgfwa_t* h, const float* xs, int64_t count, int32_t precision,
+                            float* f_out);
+
+typedef struct {
+  int64_t evals;           /* evaluations so far, including init */
+  int32_t generations;     /* generations run */
+  int32_t k;               /* the subset size in use */
+  int64_t dim_padded;      /* row stride of sparks and fireworks on the device (floats) */
+  int64_t sparks_per_gen;  /* mu (lambda + m) */
+  int64_t device_bytes;    /* bytes of the handle's device allocation */
+  int64_t kernel_launches; /* kernels enqueued so far by this handle */
+} mgfwa_info;
+
+MGFWA_API mgfwa_status mgfwa_get_info(const mgfwa_t* h, mgfwa_info* info);
+
+/* Release the handle's device memory and stream.  NULL-safe. */
+MGFWA_API void mgfwa_destroy(mgfwa_t* h);
+
+/* A one-line description of the handle's last error ("" if none).  With a
+ * NULL handle: the last error of a failed mgfwa_create in this thread. */
+MGFWA_API const char* mgfwa_last_error(const mgfwa_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

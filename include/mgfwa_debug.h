@@ -1,0 +1,67 @@
+/*
+ * mgfwa_debug.h -- step-by-step access to one MGFWA generation, for parity
+ * tests and checkpointing.  Same conventions as mgfwa.h (host pointers,
+ * status codes, the handle owns its device memory).
+ *
+ * A generation of Algorithm 1 (Sec. 3) split into the phases below runs
+ * exactly what mgfwa_step() runs, one kernel group at a time, so that a
+ * test can read every intermediate and inject the oracle's fitness before
+ * ranking and selection.
+ */
+#ifndef MGFWA_DEBUG_H
+#define MGFWA_DEBUG_H
+
+#include "mgfwa.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MGFWA_PHASE_EXPLODE = 0, /* generation += 1; explosion sparks + random mapping (Alg. 1, explosion) */
+  MGFWA_PHASE_EVAL_E = 1,  /* fitness of the mu*lambda explosion sparks */
+  MGFWA_PHASE_RANK = 2,    /* per firework and guiding group: top-k / bottom-k indices */
+  MGFWA_PHASE_GUIDE = 3,   /* mu*m guiding sparks + random mapping (Alg. 1, multi-guiding) */
+  MGFWA_PHASE_EVAL_G = 4,  /* fitness of the guiding sparks */
+  MGFWA_PHASE_SELECT = 5   /* per-firework selection, amplitude update, run best, counters */
+} mgfwa_phase;
+
+/* Enqueue one phase.  Phases must come in the order above, starting with
+ * EXPLODE; EINVAL otherwise, and EBUDGET if EXPLODE would exceed the
+ * budget.  Asynchronous. */
+MGFWA_API mgfwa_status mgfwa_debug_phase(mgfwa_t* h, int32_t phase);
+
+typedef enum {
+  MGFWA_BUF_FW_X = 0,    /* [mu][D] FP32 fireworks */
+  MGFWA_BUF_FW_AMP = 1,  /* [mu] FP32 amplitudes */
+  MGFWA_BUF_FW_F = 2,    /* [mu] FP32 firework fitness */
+  MGFWA_BUF_SPARKS = 3,  /* [mu*lambda][D] FP32 explosion sparks, row i*lambda + j */
+  MGFWA_BUF_GUIDES = 4,  /* [mu*m][D] FP32 guiding sparks, row i*m + q */
+  MGFWA_BUF_FIT_E = 5,   /* [mu*lambda] FP32 explosion fitness */
+  MGFWA_BUF_FIT_G = 6,   /* [mu*m] FP32 guiding fitness */
+  MGFWA_BUF_TOP = 7,     /* [mu][m][k] int32: index within the firework of rank r, best first */
+  MGFWA_BUF_BOTTOM = 8,  /* [mu][m][k] int32: index of rank g-1-r, worst first */
+  MGFWA_BUF_WINNER = 9,  /* [mu] int32: -1 kept, j explosion j, lambda+q guiding q */
+  MGFWA_BUF_BEST_X = 10, /* [D] FP32 run best-so-far position */
+  MGFWA_BUF_BEST_F = 11  /* [1] FP32 run best-so-far fitness (the precision decisions use) */
+} mgfwa_buffer;
+
+/* Copy a buffer to / from host memory (rows packed D floats apart);
+ * nbytes must equal the buffer's size.  Synchronises. */
+MGFWA_API mgfwa_status mgfwa_debug_read(mgfwa_t* h, int32_t buf, void* host, int64_t nbytes);
+MGFWA_API mgfwa_status mgfwa_debug_write(mgfwa_t* h, int32_t buf, const void* host, int64_t nbytes);
+
+/* Kernel timing on the handle's stream.  While enabled, every kernel group
+ * the handle enqueues is bracketed by CUDA events (taken from a pool made
+ * here); mgfwa_debug_kernel_times() synchronises and returns, per group, the
+ * summed milliseconds and the number of launches since the last enable.
+ * Groups: 0 explode, 1 explosion fitness (main kernel), 2 fitness finish,
+ * 3 rank, 4 guide, 5 guiding fitness (main kernel), 6 select + run best. */
+#define MGFWA_N_KERNEL_GROUPS 7
+MGFWA_API mgfwa_status mgfwa_debug_profile(mgfwa_t* h, int32_t enable);
+MGFWA_API mgfwa_status mgfwa_debug_kernel_times(mgfwa_t* h, double* ms_out, int64_t* launches_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,295 @@
+"""Python binding of the GPU-MGFWA C ABI (``include/mgfwa.h``).
+
+Argument marshalling only: every step of a generation runs in the CUDA
+kernels of ``libmgfwa.so`` (built in-tree by ``build.py``).  There is no CPU
+or PyTorch fallback; importing the binding without the built library raises.
+
+The C calls are exposed under their own names (``mgfwa_create``,
+``mgfwa_step``, ...) with ctypes structures mirroring the header, plus a small
+``Mgfwa`` class that owns a handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmgfwa.so")
+
+MGFWA_OK, MGFWA_EINVAL, MGFWA_ENOMEM, MGFWA_ECUDA, MGFWA_ETIMEOUT, MGFWA_EBUDGET = range(6)
+MGFWA_FP32, MGFWA_BF16, MGFWA_FP8 = 0, 1, 2
+MGFWA_OBJ_MLP_CE, MGFWA_OBJ_SPHERE = 0, 1
+MGFWA_ACT_TANH, MGFWA_ACT_RELU = 0, 1
+(MGFWA_PHASE_EXPLODE, MGFWA_PHASE_EVAL_E, MGFWA_PHASE_RANK, MGFWA_PHASE_GUIDE, MGFWA_PHASE_EVAL_G,
+ MGFWA_PHASE_SELECT) = range(6)
+(MGFWA_BUF_FW_X, MGFWA_BUF_FW_AMP, MGFWA_BUF_FW_F, MGFWA_BUF_SPARKS, MGFWA_BUF_GUIDES, MGFWA_BUF_FIT_E,
+ MGFWA_BUF_FIT_G, MGFWA_BUF_TOP, MGFWA_BUF_BOTTOM, MGFWA_BUF_WINNER, MGFWA_BUF_BEST_X, MGFWA_BUF_BEST_F) = range(12)
+
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EBUDGET"}
+
+# Every symbol the headers declare (checked by the CPU test suite).
+EXPORTS = ("mgfwa_config_init", "mgfwa_create", "mgfwa_step", "mgfwa_run", "mgfwa_best", "mgfwa_evaluate",
+           "mgfwa_get_info", "mgfwa_destroy", "mgfwa_last_error", "mgfwa_debug_phase", "mgfwa_debug_read",
+           "mgfwa_debug_write", "mgfwa_debug_profile", "mgfwa_debug_kernel_times")
+N_KERNEL_GROUPS = 7
+KERNEL_GROUPS = ("explode", "fitness_explosion", "fitness_finish", "rank", "guide", "fitness_guiding", "select")
+
+
+class mgfwa_config(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int64), ("lb", ctypes.c_float), ("ub", ctypes.c_float),
+                ("n_fireworks", ctypes.c_int32), ("sparks_per_firework", ctypes.c_int32),
+                ("guiding_per_firework", ctypes.c_int32), ("sigma", ctypes.c_float), ("boost", ctypes.c_float),
+                ("amp_init", ctypes.c_float), ("c_amplify", ctypes.c_float), ("c_reduce", ctypes.c_float),
+                ("eval_budget", ctypes.c_int64), ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32),
+                ("elite_rescore", ctypes.c_int32)]
+
+
+class mgfwa_objective(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n_layers", ctypes.c_int32),
+                ("widths", ctypes.POINTER(ctypes.c_int32)), ("acts", ctypes.POINTER(ctypes.c_int32)),
+                ("n_samples", ctypes.c_int64), ("X", ctypes.POINTER(ctypes.c_float)),
+                ("y", ctypes.POINTER(ctypes.c_int32))]
+
+
+class mgfwa_info(ctypes.Structure):
+    _fields_ = [("evals", ctypes.c_int64), ("generations", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("dim_padded", ctypes.c_int64), ("sparks_per_gen", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
+
+
+class MgfwaError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: Optional[str] = None):
+    """Load ``libmgfwa.so``; raises if it has not been built."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, f32p = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_float)
+    L.mgfwa_config_init.argtypes = [ctypes.POINTER(mgfwa_config)]
+    L.mgfwa_create.argtypes = [ctypes.POINTER(mgfwa_config), ctypes.POINTER(mgfwa_objective), vp,
+                               ctypes.POINTER(vp)]
+    L.mgfwa_step.argtypes = [vp, i32]
+    L.mgfwa_run.argtypes = [vp]
+    L.mgfwa_best.argtypes = [vp, f32p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+    L.mgfwa_evaluate.argtypes = [vp, f32p, i64, i32, f32p]
+    L.mgfwa_get_info.argtypes = [vp, ctypes.POINTER(mgfwa_info)]
+    L.mgfwa_destroy.argtypes = [vp]
+    L.mgfwa_destroy.restype = None
+    L.mgfwa_last_error.argtypes = [vp]
+    L.mgfwa_last_error.restype = ctypes.c_char_p
+    L.mgfwa_debug_phase.argtypes = [vp, i32]
+    L.mgfwa_debug_read.argtypes = [vp, i32, vp, i64]
+    L.mgfwa_debug_write.argtypes = [vp, i32, vp, i64]
+    L.mgfwa_debug_profile.argtypes = [vp, i32]
+    L.mgfwa_debug_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+    for name in EXPORTS:
+        if name not in ("mgfwa_destroy", "mgfwa_last_error"):
+            getattr(L, name).restype = ctypes.c_int
+    if path == LIB_PATH:
+        _lib = L
+    return L
+
+
+def _f32p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if a is not None else None
+
+
+# ---------------------------------------------------------------------------
+# The C calls under their own names.
+
+def mgfwa_config_init() -> mgfwa_config:
+    cfg = mgfwa_config()
+    load_library().mgfwa_config_init(ctypes.byref(cfg))
+    return cfg
+
+
+def mgfwa_last_error(handle=None) -> str:
+    return load_library().mgfwa_last_error(handle).decode()
+
+
+def _check(st: int, handle=None):
+    if st != MGFWA_OK:
+        raise MgfwaError(st, mgfwa_last_error(handle))
+
+
+class _ObjectiveBuffers:
+    def __init__(self, kind, widths=(), acts=(), X=None, y=None):
+        self.widths = np.ascontiguousarray(widths if len(widths) else [0], dtype=np.int32)
+        self.acts = np.ascontiguousarray(acts if len(acts) else [0], dtype=np.int32)
+        self.X = np.ascontiguousarray(X if X is not None else np.zeros((1, 1)), dtype=np.float32)
+        self.y = np.ascontiguousarray(y if y is not None else np.zeros(1), dtype=np.int32)
+        self.obj = mgfwa_objective(kind, max(len(widths) - 1, 0),
+                                   self.widths.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   self.acts.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   0 if X is None else self.X.shape[0], _f32p(self.X),
+                                   self.y.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+
+
+def mgfwa_create(cfg: mgfwa_config, objective: mgfwa_objective, stream: int = 0) -> int:
+    h = ctypes.c_void_p()
+    st = load_library().mgfwa_create(ctypes.byref(cfg), ctypes.byref(objective),
+                                     ctypes.c_void_p(stream or None), ctypes.byref(h))
+    _check(st)
+    return h.value
+
+
+def mgfwa_step(handle: int, n_generations: int) -> int:
+    return load_library().mgfwa_step(handle, n_generations)
+
+
+def mgfwa_run(handle: int) -> int:
+    return load_library().mgfwa_run(handle)
+
+
+def mgfwa_best(handle: int, dim: int):
+    x = np.zeros(dim, np.float32)
+    f = ctypes.c_double()
+    ev = ctypes.c_int64()
+    _check(load_library().mgfwa_best(handle, _f32p(x), ctypes.byref(f), ctypes.byref(ev)), handle)
+    return x, f.value, ev.value
+
+
+def mgfwa_evaluate(handle: int, xs: np.ndarray, precision: int) -> np.ndarray:
+    xs = np.ascontiguousarray(xs, np.float32)
+    out = np.zeros(xs.shape[0], np.float32)
+    _check(load_library().mgfwa_evaluate(handle, _f32p(xs), xs.shape[0], precision, _f32p(out)), handle)
+    return out
+
+
+def mgfwa_get_info(handle: int) -> mgfwa_info:
+    info = mgfwa_info()
+    _check(load_library().mgfwa_get_info(handle, ctypes.byref(info)), handle)
+    return info
+
+
+def mgfwa_destroy(handle: int) -> None:
+    load_library().mgfwa_destroy(handle)
+
+
+def mgfwa_debug_phase(handle: int, phase: int) -> int:
+    return load_library().mgfwa_debug_phase(handle, phase)
+
+
+def mgfwa_debug_read(handle: int, buf: int, out: np.ndarray) -> np.ndarray:
+    out = np.ascontiguousarray(out)
+    _check(load_library().mgfwa_debug_read(handle, buf, out.ctypes.data, out.nbytes), handle)
+    return out
+
+
+def mgfwa_debug_write(handle: int, buf: int, src: np.ndarray) -> None:
+    src = np.ascontiguousarray(src)
+    _check(load_library().mgfwa_debug_write(handle, buf, src.ctypes.data, src.nbytes), handle)
+
+
+# ---------------------------------------------------------------------------
+# Convenience owner of one handle.
+
+class Mgfwa:
+    """One MGFWA run on the GPU, configured from plain values or a workloads.Workload."""
+
+    def __init__(self, *, dim, lb, ub, n_fireworks, sparks_per_firework, guiding_per_firework, eval_budget,
+                 seed, sigma=0.2, boost=1.0, amp_init=0.0, c_amplify=1.2, c_reduce=0.9, precision=MGFWA_FP32,
+                 kind=MGFWA_OBJ_MLP_CE, widths=(), acts=(), X=None, y=None, stream: int = 0):
+        cfg = mgfwa_config_init()
+        cfg.dim, cfg.lb, cfg.ub = dim, lb, ub
+        cfg.n_fireworks, cfg.sparks_per_firework, cfg.guiding_per_firework = (
+            n_fireworks, sparks_per_firework, guiding_per_firework)
+        cfg.sigma, cfg.boost, cfg.amp_init, cfg.c_amplify, cfg.c_reduce = sigma, boost, amp_init, c_amplify, c_reduce
+        cfg.eval_budget, cfg.seed, cfg.precision = eval_budget, seed, precision
+        self.cfg = cfg
+        self._obj = _ObjectiveBuffers(kind, widths, acts, X, y)
+        self.dim = dim
+        self.handle = mgfwa_create(cfg, self._obj.obj, stream)
+        info = mgfwa_get_info(self.handle)
+        self.k = info.k
+        self.sparks_per_gen = info.sparks_per_gen
+
+    @classmethod
+    def for_workload(cls, w, seed: int, precision: int = MGFWA_FP32, X=None, y=None, **over):
+        kw = dict(dim=w.dim, lb=w.lb, ub=w.ub, n_fireworks=w.n_fireworks, sparks_per_firework=w.sparks_per_firework,
+                  guiding_per_firework=w.guiding_per_firework, eval_budget=w.eval_budget, seed=seed,
+                  sigma=w.sigma, precision=precision, kind=w.kind)
+        if w.kind == MGFWA_OBJ_MLP_CE:
+            if X is None:
+                import workloads
+                X, y = workloads.make_data(w)
+            kw.update(widths=w.widths, acts=w.acts, X=X, y=y)
+        kw.update(over)
+        return cls(**kw)
+
+    def step(self, n: int = 1) -> int:
+        st = mgfwa_step(self.handle, n)
+        if st not in (MGFWA_OK, MGFWA_EBUDGET):
+            _check(st, self.handle)
+        return st
+
+    def run(self) -> None:
+        _check(mgfwa_run(self.handle), self.handle)
+
+    def best(self):
+        return mgfwa_best(self.handle, self.dim)
+
+    def evaluate(self, xs, precision: Optional[int] = None) -> np.ndarray:
+        return mgfwa_evaluate(self.handle, xs, self.cfg.precision if precision is None else precision)
+
+    def info(self) -> mgfwa_info:
+        return mgfwa_get_info(self.handle)
+
+    def phase(self, ph: int) -> None:
+        _check(mgfwa_debug_phase(self.handle, ph), self.handle)
+
+    def read(self, buf: int) -> np.ndarray:
+        mu, lam, m, D, k = (self.cfg.n_fireworks, self.cfg.sparks_per_firework, self.cfg.guiding_per_firework,
+                            self.dim, self.k)
+        shapes = {MGFWA_BUF_FW_X: ((mu, D), np.float32), MGFWA_BUF_FW_AMP: ((mu,), np.float32),
+                  MGFWA_BUF_FW_F: ((mu,), np.float32), MGFWA_BUF_SPARKS: ((mu * lam, D), np.float32),
+                  MGFWA_BUF_GUIDES: ((mu * m, D), np.float32), MGFWA_BUF_FIT_E: ((mu * lam,), np.float32),
+                  MGFWA_BUF_FIT_G: ((mu * m,), np.float32), MGFWA_BUF_TOP: ((mu, m, k), np.int32),
+                  MGFWA_BUF_BOTTOM: ((mu, m, k), np.int32), MGFWA_BUF_WINNER: ((mu,), np.int32),
+                  MGFWA_BUF_BEST_X: ((D,), np.float32), MGFWA_BUF_BEST_F: ((1,), np.float32)}
+        shape, dt = shapes[buf]
+        return mgfwa_debug_read(self.handle, buf, np.zeros(shape, dt))
+
+    def write(self, buf: int, arr: np.ndarray) -> None:
+        mgfwa_debug_write(self.handle, buf, arr)
+
+    def profile(self, enable: bool = True) -> None:
+        _check(load_library().mgfwa_debug_profile(self.handle, int(enable)), self.handle)
+
+    def kernel_times(self) -> dict:
+        """{group: (total ms, launches)} since the last profile(True)."""
+        ms = (ctypes.c_double * N_KERNEL_GROUPS)()
+        n = (ctypes.c_int64 * N_KERNEL_GROUPS)()
+        _check(load_library().mgfwa_debug_kernel_times(self.handle, ms, n), self.handle)
+        return {g: (ms[i], n[i]) for i, g in enumerate(KERNEL_GROUPS)}
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            mgfwa_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

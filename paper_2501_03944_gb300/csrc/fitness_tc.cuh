@@ -1,0 +1,37 @@
+// Tensor-core (tcgen05, sm_103a) fitness path: plan and launcher.
+#pragma once
+
+#include <cuda.h>
+
+#include "../../include/mgfwa.h"
+#include "mgfwa_internal.cuh"
+
+namespace mgfwa {
+
+struct TcPlan {
+  bool ready = false;
+  CUtensorMap tmap_x;   // X  [N][d_in] BF16, box 128 x 64, 128B swizzle
+  CUtensorMap tmap_w;   // op [P*h1][d_in] BF16, box h_tile x 64, 128B swizzle
+  int num_sms = 0;
+  int sparks_per_tile = 0;  // whole sparks per N-tile
+  int n_tile = 0;           // accumulator columns per tile (sparks_per_tile * h1)
+  size_t smem_bytes = 0;
+};
+
+// True if the tensor-core path handles this network (d_in % 8 == 0, first
+// hidden width a multiple of 16 in [16, 256], at most 3 linear layers).
+bool tc_supported(const int32_t* widths, int n_layers);
+
+// Encode the tensor maps over the handle's X (BF16) and operand buffers.
+mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const __nv_bfloat16* op, int64_t max_rows);
+const char* tc_last_error();
+void tc_release(TcPlan& plan);
+
+// Fitness of `count` sparks whose operand rows start at spark `first`:
+// per-(m-tile, spark) partial cross-entropy sums into partial[mtiles][count].
+// `rows` are the sparks' FP32 rows (stride ld) for the layers after the
+// first.  A device-side wait that gives up sets *status and returns.
+int launch_fitness_tc(const TcPlan& plan, const Mlp& mlp, int64_t first, const float* rows, int64_t ld,
+                      int32_t count, float* partial, uint32_t* status, cudaStream_t s);
+
+}  // namespace mgfwa

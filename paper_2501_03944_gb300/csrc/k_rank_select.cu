@@ -1,0 +1,159 @@
+// Ranking and selection kernels (GPU-MGFWA, Algorithm 1: the ranking that
+// feeds the multi-guiding sparks, and "select the best individual of each
+// population").
+//
+// Both are decided on FP32 fitness in the total order (fitness, index)
+// with NaN ranked as +infinity, so that the outcome is unique and does not
+// depend on thread scheduling.
+#include "mgfwa_internal.cuh"
+
+namespace mgfwa {
+
+namespace {
+
+// One block per (firework, guiding group).  Each thread ranks its sparks by
+// counting the sparks of the group that come strictly before them; the
+// counts are a permutation because the order is total.
+__global__ void k_rank(Problem p, const float* __restrict__ fit_e, int32_t* __restrict__ top,
+                       int32_t* __restrict__ bottom) {
+  extern __shared__ float sh[];
+  const int g = p.g, k = p.k;
+  float* f = sh;
+  int* order = reinterpret_cast<int*>(sh + g);
+  const int grp = blockIdx.x;  // i * m + q
+  const int i = grp / p.m, q = grp % p.m;
+  const int base = q * g;
+  const float* fe = fit_e + (int64_t)i * p.lam + base;
+  for (int a = threadIdx.x; a < g; a += blockDim.x) f[a] = fe[a];
+  __syncthreads();
+  for (int a = threadIdx.x; a < g; a += blockDim.x) {
+    const float fa = f[a];
+    int r = 0;
+    for (int b = 0; b < g; ++b) r += before(f[b], b, fa, a) ? 1 : 0;
+    order[r] = a;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < k; r += blockDim.x) {
+    top[(int64_t)grp * k + r] = base + order[r];
+    bottom[(int64_t)grp * k + r] = base + order[g - 1 - r];
+  }
+}
+
+constexpr int kSelThreads = 256;
+
+__device__ __forceinline__ void take_if_before(float& bf, int& bc, float of, int oc) {
+  if (oc >= 0 && (bc < 0 || before(of, oc, bf, bc))) {
+    bf = of;
+    bc = oc;
+  }
+}
+
+// One block per firework: argmin over its lam explosion and m guiding
+// sparks (candidate order: explosion 0..lam-1, guiding 0..m-1), the strict
+// improvement test, the dynamic amplitude update (x C_a on improvement,
+// x C_r otherwise), and the copy of the winning row into the firework.
+__global__ void __launch_bounds__(kSelThreads) k_select(Problem p, const float* __restrict__ fit_e,
+                                                        const float* __restrict__ fit_g,
+                                                        const float* __restrict__ sparks,
+                                                        const float* __restrict__ guides,
+                                                        float* __restrict__ fw_x, float* __restrict__ fw_amp,
+                                                        float* __restrict__ fw_f, int32_t* __restrict__ winner) {
+  __shared__ float wf[kSelThreads / 32];
+  __shared__ int wc[kSelThreads / 32];
+  __shared__ int s_win;
+  const int i = blockIdx.x;
+  const int n_cand = p.lam + p.m;
+  float bf = 0.0f;
+  int bc = -1;
+  for (int c = threadIdx.x; c < n_cand; c += blockDim.x) {
+    const float f = c < p.lam ? fit_e[(int64_t)i * p.lam + c] : fit_g[(int64_t)i * p.m + (c - p.lam)];
+    take_if_before(bf, bc, f, c);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float of = __shfl_xor_sync(0xffffffffu, bf, off);
+    const int oc = __shfl_xor_sync(0xffffffffu, bc, off);
+    take_if_before(bf, bc, of, oc);
+  }
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (lane == 0) {
+    wf[warp] = bf;
+    wc[warp] = bc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float f = wf[0];
+    int c = wc[0];
+    for (int w = 1; w < kSelThreads / 32; ++w) take_if_before(f, c, wf[w], wc[w]);
+    const float amp = fw_amp[i];
+    if (rank_key(f) < rank_key(fw_f[i])) {
+      fw_f[i] = f;
+      fw_amp[i] = __fmul_rn(amp, p.c_a);
+      s_win = c;
+    } else {
+      fw_amp[i] = __fmul_rn(amp, p.c_r);
+      s_win = -1;
+    }
+    winner[i] = s_win;
+  }
+  __syncthreads();
+  const int c = s_win;
+  if (c < 0) return;
+  const float* src = c < p.lam ? sparks + ((int64_t)i * p.lam + c) * p.Dp
+                               : guides + ((int64_t)i * p.m + (c - p.lam)) * p.Dp;
+  float4* dst = reinterpret_cast<float4*>(fw_x + (int64_t)i * p.Dp);
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+  for (int64_t e = threadIdx.x; e < p.Dp / 4; e += blockDim.x) dst[e] = s4[e];
+}
+
+// The run's best-so-far: strict improvement over the fireworks in index
+// order (init: the first minimum of the initial fireworks).
+__global__ void __launch_bounds__(kSelThreads) k_run_best(Problem p, int init, const float* __restrict__ fw_x,
+                                                          const float* __restrict__ fw_f,
+                                                          float* __restrict__ best_x, float* __restrict__ best_f) {
+  __shared__ int s_bi;
+  if (threadIdx.x == 0) {
+    int bi = init ? 0 : -1;
+    float bf = init ? fw_f[0] : *best_f;
+    for (int i = init ? 1 : 0; i < p.mu; ++i) {
+      if (rank_key(fw_f[i]) < rank_key(bf)) {
+        bf = fw_f[i];
+        bi = i;
+      }
+    }
+    if (bi >= 0) *best_f = bf;
+    s_bi = bi;
+  }
+  __syncthreads();
+  const int bi = s_bi;
+  if (bi < 0) return;
+  const float4* src = reinterpret_cast<const float4*>(fw_x + (int64_t)bi * p.Dp);
+  float4* dst = reinterpret_cast<float4*>(best_x);
+  for (int64_t e = threadIdx.x; e < p.Dp / 4; e += blockDim.x) dst[e] = src[e];
+}
+
+}  // namespace
+
+int launch_rank(const Problem& p, const float* fit_e, int32_t* top, int32_t* bottom, cudaStream_t s) {
+  const int threads = p.g >= 256 ? 256 : ((p.g + 31) / 32) * 32;
+  const size_t smem = (size_t)p.g * (sizeof(float) + sizeof(int));
+  k_rank<<<p.mu * p.m, threads, smem, s>>>(p, fit_e, top, bottom);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_select(const Problem& p, const float* fit_e, const float* fit_g, const float* sparks,
+                  const float* guides, float* fw_x, float* fw_amp, float* fw_f, int32_t* winner, float* best_x,
+                  float* best_f, cudaStream_t s) {
+  k_select<<<p.mu, kSelThreads, 0, s>>>(p, fit_e, fit_g, sparks, guides, fw_x, fw_amp, fw_f, winner);
+  if (cudaPeekAtLastError() != cudaSuccess) return -1;
+  k_run_best<<<1, kSelThreads, 0, s>>>(p, 0, fw_x, fw_f, best_x, best_f);
+  return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;
+}
+
+int launch_run_best_init(const Problem& p, const float* fw_x, const float* fw_f, float* best_x, float* best_f,
+                         cudaStream_t s) {
+  k_run_best<<<1, kSelThreads, 0, s>>>(p, 1, fw_x, fw_f, best_x, best_f);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+}  // namespace mgfwa

@@ -1,0 +1,202 @@
+// Philox-driven sampling kernels: firework initialisation, explosion sparks
+// and multi-guiding sparks, each with the random mapping of out-of-bound
+// coordinates (GPU-MGFWA, Algorithm 1: init, explosion + mapping, multi-
+// guiding + mapping).
+//
+// Every state value is produced with explicitly rounded FP32 intrinsics
+// (__fmaf_rn, __fadd_rn, ...), which the compiler never contracts or
+// reorders, so the positions are a pure function of (seed, generation,
+// unit, coordinate) and the firework state.
+//
+// Layout: rows of Dp floats (Dp a multiple of 64, so each row starts on a
+// 256-byte boundary); one thread owns four consecutive coordinates, i.e.
+// one Philox4x32 block, and moves them with 16-byte loads and stores.  The
+// BF16 first-layer operand of a spark is the first w1_elems coordinates of
+// its row, stored contiguously (row-major [h1][d_in]), written with one
+// 8-byte store per thread.
+#include "mgfwa_internal.cuh"
+
+namespace mgfwa {
+
+namespace {
+
+constexpr int kThreads = 128;
+
+// Reading of the population-based random mapping: a coordinate outside
+// [lb, ub] is redrawn uniformly in the firework's amplitude box clipped to
+// the bounds, lo + u (hi - lo).
+__device__ __forceinline__ float map_coord(float x, float amp, float lb, float ub, float u) {
+  float lo = __fsub_rn(x, amp);
+  float hi = __fadd_rn(x, amp);
+  if (lo < lb) lo = lb;
+  if (hi > ub) hi = ub;
+  return __fmaf_rn(u, __fsub_rn(hi, lo), lo);
+}
+
+__device__ __forceinline__ void store_bf16x4(__nv_bfloat16* dst, float a, float b, float c, float d) {
+  __nv_bfloat162 lo = __floats2bfloat162_rn(a, b);
+  __nv_bfloat162 hi = __floats2bfloat162_rn(c, d);
+  uint2 v;
+  v.x = *reinterpret_cast<uint32_t*>(&lo);
+  v.y = *reinterpret_cast<uint32_t*>(&hi);
+  *reinterpret_cast<uint2*>(dst) = v;
+}
+
+__global__ void __launch_bounds__(kThreads) k_init(Problem p, float* __restrict__ fw_x,
+                                                   float* __restrict__ fw_amp) {
+  const int i = blockIdx.y;
+  const int64_t c4 = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  const int64_t d0 = c4 * 4;
+  if (blockIdx.x == 0 && threadIdx.x == 0) fw_amp[i] = p.amp0;
+  if (d0 >= p.Dp) return;
+  const uint4 r = philox4x32_10(make_uint4((uint32_t)c4, (uint32_t)i, 0u, kInit), p.key0, p.key1);
+  const float width = __fsub_rn(p.ub, p.lb);
+  float v[4];
+#pragma unroll
+  for (int l = 0; l < 4; ++l)
+    v[l] = (d0 + l < p.D) ? __fmaf_rn(u24(lane_of(r, l)), width, p.lb) : 0.0f;
+  *reinterpret_cast<float4*>(fw_x + (int64_t)i * p.Dp + d0) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_explode(Problem p, uint32_t gen, const float* __restrict__ fw_x,
+                                                      const float* __restrict__ fw_amp,
+                                                      float* __restrict__ sparks,
+                                                      __nv_bfloat16* __restrict__ op, int64_t w1_elems) {
+  const int row = blockIdx.y;  // i * lam + j
+  const int i = row / p.lam;
+  const int64_t c4 = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  const int64_t d0 = c4 * 4;
+  if (d0 >= p.Dp) return;
+  const float amp = fw_amp[i];
+  const float4 x4 = *reinterpret_cast<const float4*>(fw_x + (int64_t)i * p.Dp + d0);
+  const uint4 r = philox4x32_10(make_uint4((uint32_t)c4, (uint32_t)row, gen, kExplode), p.key0, p.key1);
+  float v[4];
+  bool out_of_bounds = false;
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    const float t = __fsub_rn(__fmul_rn(2.0f, u24(lane_of(r, l))), 1.0f);
+    v[l] = __fmaf_rn(amp, t, lane_of(x4, l));
+    out_of_bounds |= (d0 + l < p.D) && (v[l] < p.lb || v[l] > p.ub);
+  }
+  if (out_of_bounds) {
+    const uint4 r2 = philox4x32_10(make_uint4((uint32_t)c4, (uint32_t)row, gen, kMap), p.key0, p.key1);
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+      if (v[l] < p.lb || v[l] > p.ub) v[l] = map_coord(lane_of(x4, l), amp, p.lb, p.ub, u24(lane_of(r2, l)));
+  }
+#pragma unroll
+  for (int l = 0; l < 4; ++l)
+    if (d0 + l >= p.D) v[l] = 0.0f;
+  *reinterpret_cast<float4*>(sparks + (int64_t)row * p.Dp + d0) = make_float4(v[0], v[1], v[2], v[3]);
+  if (op != nullptr && d0 < w1_elems) store_bf16x4(op + (int64_t)row * w1_elems + d0, v[0], v[1], v[2], v[3]);
+}
+
+// Multi-guiding sparks, reading: group q of firework i has ranked index
+// lists top (best first) and bottom (worst first);
+//   GV = (sum top rows - sum bottom rows) / k,  G = x + beta GV,
+// each sum in list order, then the random mapping with its own stream.
+__global__ void __launch_bounds__(kThreads) k_guide(Problem p, uint32_t gen, const float* __restrict__ fw_x,
+                                                    const float* __restrict__ fw_amp,
+                                                    const float* __restrict__ sparks,
+                                                    const int32_t* __restrict__ top,
+                                                    const int32_t* __restrict__ bottom,
+                                                    float* __restrict__ guides,
+                                                    __nv_bfloat16* __restrict__ op, int64_t w1_elems) {
+  const int gq = blockIdx.y;  // i * m + q
+  const int i = gq / p.m;
+  const int64_t c4 = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  const int64_t d0 = c4 * 4;
+  if (d0 >= p.Dp) return;
+  const int k = p.k;
+  const int32_t* t = top + (int64_t)gq * k;
+  const int32_t* b = bottom + (int64_t)gq * k;
+  const float* fs = sparks + (int64_t)i * p.lam * p.Dp + d0;
+  float4 st = *reinterpret_cast<const float4*>(fs + (int64_t)t[0] * p.Dp);
+  float4 sb = *reinterpret_cast<const float4*>(fs + (int64_t)b[0] * p.Dp);
+  for (int r = 1; r < k; ++r) {
+    const float4 a = *reinterpret_cast<const float4*>(fs + (int64_t)t[r] * p.Dp);
+    const float4 c = *reinterpret_cast<const float4*>(fs + (int64_t)b[r] * p.Dp);
+    st.x = __fadd_rn(st.x, a.x); st.y = __fadd_rn(st.y, a.y);
+    st.z = __fadd_rn(st.z, a.z); st.w = __fadd_rn(st.w, a.w);
+    sb.x = __fadd_rn(sb.x, c.x); sb.y = __fadd_rn(sb.y, c.y);
+    sb.z = __fadd_rn(sb.z, c.z); sb.w = __fadd_rn(sb.w, c.w);
+  }
+  const float amp = fw_amp[i];
+  const float4 x4 = *reinterpret_cast<const float4*>(fw_x + (int64_t)i * p.Dp + d0);
+  const float fk = (float)k;
+  float v[4];
+  bool out_of_bounds = false;
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    const float gv = __fdiv_rn(__fsub_rn(lane_of(st, l), lane_of(sb, l)), fk);
+    v[l] = __fmaf_rn(p.beta, gv, lane_of(x4, l));
+    out_of_bounds |= (d0 + l < p.D) && (v[l] < p.lb || v[l] > p.ub);
+  }
+  if (out_of_bounds) {
+    const uint4 r2 = philox4x32_10(make_uint4((uint32_t)c4, (uint32_t)gq, gen, kGmap), p.key0, p.key1);
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+      if (v[l] < p.lb || v[l] > p.ub) v[l] = map_coord(lane_of(x4, l), amp, p.lb, p.ub, u24(lane_of(r2, l)));
+  }
+#pragma unroll
+  for (int l = 0; l < 4; ++l)
+    if (d0 + l >= p.D) v[l] = 0.0f;
+  *reinterpret_cast<float4*>(guides + (int64_t)gq * p.Dp + d0) = make_float4(v[0], v[1], v[2], v[3]);
+  if (op != nullptr && d0 < w1_elems) store_bf16x4(op + (int64_t)gq * w1_elems + d0, v[0], v[1], v[2], v[3]);
+}
+
+__global__ void k_to_operand(const float* __restrict__ rows, int64_t ld, int64_t w1_elems,
+                             __nv_bfloat16* __restrict__ op) {
+  const int row = blockIdx.y;
+  const int64_t d0 = ((int64_t)blockIdx.x * kThreads + threadIdx.x) * 4;
+  if (d0 >= w1_elems) return;
+  const float4 v = *reinterpret_cast<const float4*>(rows + (int64_t)row * ld + d0);
+  store_bf16x4(op + (int64_t)row * w1_elems + d0, v.x, v.y, v.z, v.w);
+}
+
+__global__ void k_f32_to_bf16(const float* __restrict__ src, int64_t n, __nv_bfloat16* __restrict__ dst) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = __float2bfloat16_rn(src[e]);
+}
+
+inline unsigned blocks_for(int64_t n4) { return (unsigned)((n4 + kThreads - 1) / kThreads); }
+
+}  // namespace
+
+int launch_init(const Problem& p, float* fw_x, float* fw_amp, cudaStream_t s) {
+  dim3 grid(blocks_for(p.Dp / 4), p.mu);
+  k_init<<<grid, kThreads, 0, s>>>(p, fw_x, fw_amp);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_explode(const Problem& p, uint32_t gen, const float* fw_x, const float* fw_amp, float* sparks,
+                   __nv_bfloat16* op, int64_t w1_elems, cudaStream_t s) {
+  dim3 grid(blocks_for(p.Dp / 4), p.mu * p.lam);
+  k_explode<<<grid, kThreads, 0, s>>>(p, gen, fw_x, fw_amp, sparks, op, w1_elems);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_guide(const Problem& p, uint32_t gen, const float* fw_x, const float* fw_amp, const float* sparks,
+                 const int32_t* top, const int32_t* bottom, float* guides, __nv_bfloat16* op_guides,
+                 int64_t w1_elems, cudaStream_t s) {
+  dim3 grid(blocks_for(p.Dp / 4), p.mu * p.m);
+  k_guide<<<grid, kThreads, 0, s>>>(p, gen, fw_x, fw_amp, sparks, top, bottom, guides, op_guides, w1_elems);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_to_operand(const float* rows, int64_t ld, int32_t count, int64_t w1_elems, __nv_bfloat16* op,
+                      cudaStream_t s) {
+  if (count <= 0) return 0;
+  dim3 grid(blocks_for(w1_elems / 4), count);
+  k_to_operand<<<grid, kThreads, 0, s>>>(rows, ld, w1_elems, op);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_f32_to_bf16(const float* src, int64_t n, __nv_bfloat16* dst, cudaStream_t s) {
+  if (n <= 0) return 0;
+  const unsigned blocks = (unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  k_f32_to_bf16<<<blocks, 256, 0, s>>>(src, n, dst);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+}  // namespace mgfwa

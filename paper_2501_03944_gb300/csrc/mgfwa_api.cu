@@ -1,0 +1,657 @@
+// C ABI of the library (include/mgfwa.h, include/mgfwa_debug.h): handle
+// life cycle, device arena, the generation driver of Algorithm 1 and the
+// reporting calls.  All device work is enqueued on the handle's stream.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mgfwa.h"
+#include "../../include/mgfwa_debug.h"
+#include "fitness_tc.cuh"
+#include "mgfwa_internal.cuh"
+
+using namespace mgfwa;
+
+struct mgfwa_handle {
+  mgfwa_config cfg;
+  Problem p;
+  Mlp mlp;
+  int32_t kind = MGFWA_OBJ_MLP_CE;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  // device buffers (carved from the arena)
+  float* X = nullptr;
+  __nv_bfloat16* Xbf = nullptr;
+  int32_t* y = nullptr;
+  float* fw_x = nullptr;
+  float* fw_amp = nullptr;
+  float* fw_f = nullptr;
+  float* sparks = nullptr;  // [P][Dp]: explosion rows, then guiding rows
+  __nv_bfloat16* op = nullptr;  // [P][w1_elems] BF16 first-layer operand
+  float* fit = nullptr;         // [P]
+  float* partial = nullptr;     // [mtiles][P]
+  int32_t* top = nullptr;
+  int32_t* bottom = nullptr;
+  int32_t* winner = nullptr;
+  float* best_x = nullptr;
+  float* best_f = nullptr;
+  double* ce64 = nullptr;
+  double* f64 = nullptr;
+  uint32_t* status = nullptr;
+  int64_t P = 0;       // sparks per generation
+  int32_t mtiles = 0;  // sample tiles of 128
+  int64_t evals = 0;
+  int32_t gen = 0;
+  int32_t next_phase = MGFWA_PHASE_EXPLODE;
+  int64_t launches = 0;
+  bool broken = false;
+  TcPlan tc;
+  std::string err;
+  // kernel-group timing (mgfwa_debug_profile)
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_next = 0;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_marks;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+mgfwa_status fail(mgfwa_t* h, mgfwa_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (h) {
+    h->err = buf;
+    if (st == MGFWA_ECUDA) h->broken = true;
+  } else {
+    g_create_error = buf;
+  }
+  return st;
+}
+
+mgfwa_status cuda_fail(mgfwa_t* h, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  return fail(h, MGFWA_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CREATE_LAUNCH(expr, what)                         \
+  do {                                                    \
+    const int n_ = (expr);                                \
+    if (n_ < 0) return bail(cuda_fail(h, (what)));        \
+    h->launches += n_;                                    \
+  } while (0)
+
+#define MG_LAUNCH(h, expr, what)                          \
+  do {                                                    \
+    const int n_ = (expr);                                \
+    if (n_ < 0) return cuda_fail((h), (what));            \
+    (h)->launches += n_;                                  \
+  } while (0)
+
+int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+enum { G_EXPLODE = 0, G_FIT_E = 1, G_FINISH = 2, G_RANK = 3, G_GUIDE = 4, G_FIT_G = 5, G_SELECT = 6 };
+
+// Brackets one kernel group with events when profiling is on.
+struct Mark {
+  mgfwa_t* h;
+  int group;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Mark(mgfwa_t* h_, int g) : h(h_), group(g) {
+    if (!h->profiling || h->ev_next + 2 > h->ev_pool.size()) return;
+    a = h->ev_pool[h->ev_next++];
+    b = h->ev_pool[h->ev_next++];
+    cudaEventRecord(a, h->stream);
+  }
+  ~Mark() {
+    if (!a) return;
+    cudaEventRecord(b, h->stream);
+    h->ev_marks.push_back({group, {a, b}});
+  }
+};
+
+int32_t subset_size(float sigma, int32_t g) {
+  int32_t k = (int32_t)std::floor((double)sigma * (double)g + 0.5);
+  if (k > g / 2) k = g / 2;
+  if (k < 1) k = 1;
+  return k;
+}
+
+bool use_tc(const mgfwa_t* h, int32_t precision) {
+  return h->kind == MGFWA_OBJ_MLP_CE && precision == MGFWA_BF16;
+}
+
+// Fitness of `count` consecutive spark rows starting at row `first` into
+// fit[first..first+count).
+mgfwa_status eval_rows(mgfwa_t* h, int64_t first, int32_t count, int32_t precision) {
+  if (count <= 0) return MGFWA_OK;
+  const float* rows = h->sparks + first * h->p.Dp;
+  float* fit = h->fit + first;
+  const int group = first == 0 ? G_FIT_E : G_FIT_G;
+  if (h->kind == MGFWA_OBJ_SPHERE) {
+    Mark mk(h, group);
+    MG_LAUNCH(h, launch_fitness_sphere(rows, h->p.Dp, h->p.D, count, fit, h->stream), "sphere fitness");
+    return MGFWA_OK;
+  }
+  {
+    Mark mk(h, group);
+    if (use_tc(h, precision))
+      MG_LAUNCH(h, launch_fitness_tc(h->tc, h->mlp, first, rows, h->p.Dp, count, h->partial, h->status, h->stream),
+                "tensor-core fitness");
+    else
+      MG_LAUNCH(h, launch_fitness_simt_main(h->mlp, rows, h->p.Dp, count, h->partial, h->stream), "FP32 fitness");
+  }
+  Mark mk(h, G_FINISH);
+  MG_LAUNCH(h, launch_fitness_finish(h->partial, h->mtiles, count, h->mlp.N, fit, h->stream), "fitness finish");
+  return MGFWA_OK;
+}
+
+__nv_bfloat16* op_rows(mgfwa_t* h, int64_t first) {
+  return h->op ? h->op + first * h->mlp.w1_elems : nullptr;
+}
+
+mgfwa_status run_phase(mgfwa_t* h, int32_t phase) {
+  const Problem& p = h->p;
+  const int64_t n_e = (int64_t)p.mu * p.lam;
+  const int32_t prec = h->cfg.precision;
+  switch (phase) {
+    case MGFWA_PHASE_EXPLODE: {
+      h->gen += 1;
+      Mark mk(h, G_EXPLODE);
+      MG_LAUNCH(h, launch_explode(p, (uint32_t)h->gen, h->fw_x, h->fw_amp, h->sparks, op_rows(h, 0),
+                                  h->mlp.w1_elems, h->stream), "explode");
+      return MGFWA_OK;
+    }
+    case MGFWA_PHASE_EVAL_E:
+      return eval_rows(h, 0, (int32_t)n_e, prec);
+    case MGFWA_PHASE_RANK: {
+      Mark mk(h, G_RANK);
+      MG_LAUNCH(h, launch_rank(p, h->fit, h->top, h->bottom, h->stream), "rank");
+      return MGFWA_OK;
+    }
+    case MGFWA_PHASE_GUIDE: {
+      Mark mk(h, G_GUIDE);
+      MG_LAUNCH(h, launch_guide(p, (uint32_t)h->gen, h->fw_x, h->fw_amp, h->sparks, h->top, h->bottom,
+                                h->sparks + n_e * p.Dp, op_rows(h, n_e), h->mlp.w1_elems, h->stream), "guide");
+      return MGFWA_OK;
+    }
+    case MGFWA_PHASE_EVAL_G:
+      return eval_rows(h, n_e, p.mu * p.m, prec);
+    case MGFWA_PHASE_SELECT: {
+      Mark mk(h, G_SELECT);
+      MG_LAUNCH(h, launch_select(p, h->fit, h->fit + n_e, h->sparks, h->sparks + n_e * p.Dp, h->fw_x, h->fw_amp,
+                                 h->fw_f, h->winner, h->best_x, h->best_f, h->stream), "select");
+      h->evals += h->P;
+      return MGFWA_OK;
+    }
+  }
+  return fail(h, MGFWA_EINVAL, "unknown phase %d", phase);
+}
+
+mgfwa_status one_generation(mgfwa_t* h) {
+  for (int32_t ph = MGFWA_PHASE_EXPLODE; ph <= MGFWA_PHASE_SELECT; ++ph) {
+    mgfwa_status st = run_phase(h, ph);
+    if (st != MGFWA_OK) return st;
+  }
+  return MGFWA_OK;
+}
+
+bool budget_allows(const mgfwa_t* h) { return h->evals + h->P <= h->cfg.eval_budget; }
+
+mgfwa_status check_usable(mgfwa_t* h) {
+  if (!h) return MGFWA_EINVAL;
+  if (h->broken) return fail(h, MGFWA_ECUDA, "handle unusable after an earlier CUDA error: %s", h->err.c_str());
+  return MGFWA_OK;
+}
+
+mgfwa_status check_status_word(mgfwa_t* h) {
+  uint32_t st = 0;
+  if (cudaMemcpyAsync(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return cuda_fail(h, "synchronise");
+  if (st != 0) {
+    cudaMemsetAsync(h->status, 0, sizeof(uint32_t), h->stream);
+    return fail(h, MGFWA_ETIMEOUT, "a bounded device wait gave up (code 0x%x)", st);
+  }
+  return MGFWA_OK;
+}
+
+mgfwa_status validate(const mgfwa_config* c, const mgfwa_objective* o) {
+  if (!c || !o) return fail(nullptr, MGFWA_EINVAL, "null config or objective");
+  if (c->dim < 1 || c->dim > (int64_t)1 << 31) return fail(nullptr, MGFWA_EINVAL, "dim %lld out of range", (long long)c->dim);
+  if (!(c->lb < c->ub) || !std::isfinite(c->lb) || !std::isfinite(c->ub))
+    return fail(nullptr, MGFWA_EINVAL, "bounds must be finite with lb < ub");
+  if (c->n_fireworks < 1 || c->guiding_per_firework < 1 || c->sparks_per_firework < 2)
+    return fail(nullptr, MGFWA_EINVAL, "need mu >= 1, m >= 1, lambda >= 2");
+  if (c->sparks_per_firework % c->guiding_per_firework != 0)
+    return fail(nullptr, MGFWA_EINVAL, "lambda (%d) must be a multiple of m (%d)", c->sparks_per_firework,
+                c->guiding_per_firework);
+  const int32_t g = c->sparks_per_firework / c->guiding_per_firework;
+  if (g < 2 || g > 1024) return fail(nullptr, MGFWA_EINVAL, "group size lambda/m = %d must be in [2, 1024]", g);
+  const int64_t P = (int64_t)c->n_fireworks * (c->sparks_per_firework + c->guiding_per_firework);
+  if (P > 65535) return fail(nullptr, MGFWA_EINVAL, "mu (lambda + m) = %lld exceeds 65535", (long long)P);
+  if (!(c->sigma > 0.0f) || !(c->sigma <= 0.5f)) return fail(nullptr, MGFWA_EINVAL, "sigma must be in (0, 0.5]");
+  if (c->eval_budget < c->n_fireworks) return fail(nullptr, MGFWA_EINVAL, "eval_budget below the mu initial evaluations");
+  if (c->precision != MGFWA_FP32 && c->precision != MGFWA_BF16)
+    return fail(nullptr, MGFWA_EINVAL, "precision %d not supported (FP32 = 0, BF16 = 1)", c->precision);
+  if (o->kind == MGFWA_OBJ_SPHERE) return MGFWA_OK;
+  if (o->kind != MGFWA_OBJ_MLP_CE) return fail(nullptr, MGFWA_EINVAL, "unknown objective kind %d", o->kind);
+  if (o->n_layers < 2 || o->n_layers > 3 || !o->widths || !o->acts || !o->X || !o->y)
+    return fail(nullptr, MGFWA_EINVAL, "MLP objective needs 2 or 3 layers, widths, acts, X and y");
+  if (o->n_samples < 1 || o->n_samples > (1 << 24)) return fail(nullptr, MGFWA_EINVAL, "n_samples out of range");
+  int64_t params = 0;
+  for (int l = 0; l < o->n_layers; ++l) {
+    if (o->widths[l] < 1 || o->widths[l + 1] < 1) return fail(nullptr, MGFWA_EINVAL, "layer widths must be >= 1");
+    params += (int64_t)o->widths[l] * o->widths[l + 1] + o->widths[l + 1];
+  }
+  if (params != c->dim)
+    return fail(nullptr, MGFWA_EINVAL, "dim %lld != MLP parameter count %lld", (long long)c->dim, (long long)params);
+  if (o->widths[0] % 8 != 0) return fail(nullptr, MGFWA_EINVAL, "d_in (%d) must be a multiple of 8", o->widths[0]);
+  for (int l = 1; l < o->n_layers; ++l) {
+    if (o->widths[l] > 192) return fail(nullptr, MGFWA_EINVAL, "hidden width %d above 192", o->widths[l]);
+    if (o->acts[l - 1] != MGFWA_ACT_TANH && o->acts[l - 1] != MGFWA_ACT_RELU)
+      return fail(nullptr, MGFWA_EINVAL, "unknown activation %d", o->acts[l - 1]);
+  }
+  if (o->widths[o->n_layers] > 32 || o->widths[o->n_layers] < 2)
+    return fail(nullptr, MGFWA_EINVAL, "class count must be in [2, 32]");
+  const int C = o->widths[o->n_layers];
+  for (int64_t n = 0; n < o->n_samples; ++n)
+    if (o->y[n] < 0 || o->y[n] >= C) return fail(nullptr, MGFWA_EINVAL, "label y[%lld] out of range", (long long)n);
+  if (c->precision == MGFWA_BF16 && !tc_supported(o->widths, o->n_layers))
+    return fail(nullptr, MGFWA_EINVAL, "BF16 path needs d_in %% 8 == 0 and a first hidden width in {16..256} %% 16");
+  return MGFWA_OK;
+}
+
+template <typename T>
+T* carve(char*& cur, size_t count) {
+  T* p = reinterpret_cast<T*>(cur);
+  cur += round_up((int64_t)(count * sizeof(T)), 256);
+  return p;
+}
+
+}  // namespace
+
+extern "C" {
+
+mgfwa_status mgfwa_config_init(mgfwa_config* cfg) {
+  if (!cfg) return MGFWA_EINVAL;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->sigma = 0.2f;
+  cfg->boost = 1.0f;
+  cfg->amp_init = 0.0f;
+  cfg->c_amplify = 1.2f;
+  cfg->c_reduce = 0.9f;
+  cfg->precision = MGFWA_FP32;
+  cfg->elite_rescore = 0;
+  return MGFWA_OK;
+}
+
+mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, void* cuda_stream, mgfwa_t** out) {
+  if (!out) return fail(nullptr, MGFWA_EINVAL, "null output handle pointer");
+  *out = nullptr;
+  g_create_error.clear();
+  mgfwa_status st = validate(cfg, obj);
+  if (st != MGFWA_OK) return st;
+  mgfwa_t* h = new (std::nothrow) mgfwa_t();
+  if (!h) return fail(nullptr, MGFWA_ENOMEM, "host allocation failed");
+  h->cfg = *cfg;
+  h->kind = obj->kind;
+  cudaGetDevice(&h->device);
+
+  Problem& p = h->p;
+  p.D = cfg->dim;
+  p.Dp = round_up(cfg->dim, 64);
+  p.lb = cfg->lb;
+  p.ub = cfg->ub;
+  p.mu = cfg->n_fireworks;
+  p.lam = cfg->sparks_per_firework;
+  p.m = cfg->guiding_per_firework;
+  p.g = p.lam / p.m;
+  p.k = subset_size(cfg->sigma, p.g);
+  p.beta = cfg->boost;
+  p.amp0 = cfg->amp_init > 0.0f ? cfg->amp_init : cfg->ub - cfg->lb;
+  p.c_a = cfg->c_amplify;
+  p.c_r = cfg->c_reduce;
+  p.key0 = (uint32_t)(cfg->seed & 0xffffffffu);
+  p.key1 = (uint32_t)(cfg->seed >> 32);
+  h->P = (int64_t)p.mu * (p.lam + p.m);
+
+  Mlp& mlp = h->mlp;
+  std::memset(&mlp, 0, sizeof(mlp));
+  int64_t d_in = 0, N = 0;
+  if (obj->kind == MGFWA_OBJ_MLP_CE) {
+    mlp.n_layers = obj->n_layers;
+    for (int l = 0; l <= obj->n_layers; ++l) mlp.widths[l] = obj->widths[l];
+    for (int l = 0; l + 1 < obj->n_layers; ++l) mlp.acts[l] = obj->acts[l];
+    int64_t off = 0;
+    for (int l = 0; l < obj->n_layers; ++l) {
+      mlp.w_off[l] = off;
+      off += (int64_t)obj->widths[l] * obj->widths[l + 1];
+      mlp.b_off[l] = off;
+      off += obj->widths[l + 1];
+    }
+    mlp.N = obj->n_samples;
+    mlp.w1_elems = (int64_t)obj->widths[0] * obj->widths[1];
+    d_in = obj->widths[0];
+    N = obj->n_samples;
+    h->mtiles = (int32_t)((N + 127) / 128);
+  } else {
+    h->mtiles = 1;
+  }
+  const bool want_op = obj->kind == MGFWA_OBJ_MLP_CE && cfg->precision == MGFWA_BF16;
+
+  // One arena for all device state.
+  size_t bytes = 0;
+  auto add = [&](size_t b) { bytes += (size_t)round_up((int64_t)b, 256); };
+  add(sizeof(float) * N * d_in);                               // X
+  add(want_op ? sizeof(__nv_bfloat16) * N * d_in : 0);         // Xbf
+  add(sizeof(int32_t) * N);                                    // y
+  add(sizeof(float) * p.mu * p.Dp);                            // fw_x
+  add(sizeof(float) * p.mu);                                   // fw_amp
+  add(sizeof(float) * p.mu);                                   // fw_f
+  add(sizeof(float) * h->P * p.Dp);                            // sparks
+  add(want_op ? sizeof(__nv_bfloat16) * h->P * mlp.w1_elems : 0);  // op
+  add(sizeof(float) * h->P);                                   // fit
+  add(sizeof(float) * (size_t)h->mtiles * h->P);               // partial
+  add(sizeof(int32_t) * p.mu * p.m * p.k * 2);                 // top, bottom
+  add(sizeof(int32_t) * p.mu);                                 // winner
+  add(sizeof(float) * p.Dp);                                   // best_x
+  add(sizeof(float));                                          // best_f
+  add(sizeof(double) * (N > 0 ? N : 1));                       // ce64
+  add(sizeof(double));                                         // f64
+  add(sizeof(uint32_t));                                       // status
+  h->arena_bytes = bytes;
+
+  if (cuda_stream) {
+    h->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      return fail(nullptr, MGFWA_ECUDA, "cudaStreamCreate failed");
+    }
+    h->own_stream = true;
+  }
+  if (cudaMalloc(&h->arena, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return fail(nullptr, MGFWA_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
+  }
+  char* cur = h->arena;
+  h->X = carve<float>(cur, N * d_in);
+  h->Xbf = want_op ? carve<__nv_bfloat16>(cur, N * d_in) : nullptr;
+  h->y = carve<int32_t>(cur, N);
+  h->fw_x = carve<float>(cur, p.mu * p.Dp);
+  h->fw_amp = carve<float>(cur, p.mu);
+  h->fw_f = carve<float>(cur, p.mu);
+  h->sparks = carve<float>(cur, h->P * p.Dp);
+  h->op = want_op ? carve<__nv_bfloat16>(cur, h->P * mlp.w1_elems) : nullptr;
+  h->fit = carve<float>(cur, h->P);
+  h->partial = carve<float>(cur, (size_t)h->mtiles * h->P);
+  h->top = carve<int32_t>(cur, p.mu * p.m * p.k);
+  h->bottom = carve<int32_t>(cur, p.mu * p.m * p.k);
+  h->winner = carve<int32_t>(cur, p.mu);
+  h->best_x = carve<float>(cur, p.Dp);
+  h->best_f = carve<float>(cur, 1);
+  h->ce64 = carve<double>(cur, N > 0 ? N : 1);
+  h->f64 = carve<double>(cur, 1);
+  h->status = carve<uint32_t>(cur, 1);
+
+  mlp.X = h->X;
+  mlp.Xbf = h->Xbf;
+  mlp.y = h->y;
+
+  auto bail = [&](mgfwa_status s) {
+    std::string e = h->err;
+    mgfwa_destroy(h);
+    g_create_error = e;
+    return s;
+  };
+  if (cudaMemsetAsync(h->arena, 0, bytes, h->stream) != cudaSuccess) return bail(cuda_fail(h, "memset arena"));
+  if (N > 0) {
+    if (cudaMemcpyAsync(h->X, obj->X, sizeof(float) * N * d_in, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(h->y, obj->y, sizeof(int32_t) * N, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+      return bail(cuda_fail(h, "copy batch"));
+    if (want_op) CREATE_LAUNCH(launch_f32_to_bf16(h->X, N * d_in, h->Xbf, h->stream), "X to BF16");
+  }
+  if (want_op) {
+    st = tc_plan(h->tc, h->mlp, h->op, h->P);
+    if (st != MGFWA_OK) {
+      h->err = tc_last_error();
+      return bail(st);
+    }
+  }
+  // Algorithm 1, init: mu fireworks uniform in the box, evaluated.
+  CREATE_LAUNCH(launch_init(p, h->fw_x, h->fw_amp, h->stream), "init");
+  if (cudaMemcpy2DAsync(h->sparks, sizeof(float) * p.Dp, h->fw_x, sizeof(float) * p.Dp, sizeof(float) * p.Dp, p.mu,
+                        cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+    return bail(cuda_fail(h, "stage init rows"));
+  if (want_op) CREATE_LAUNCH(launch_to_operand(h->sparks, p.Dp, p.mu, mlp.w1_elems, h->op, h->stream), "init operand");
+  st = eval_rows(h, 0, p.mu, cfg->precision);
+  if (st != MGFWA_OK) return bail(st);
+  if (cudaMemcpyAsync(h->fw_f, h->fit, sizeof(float) * p.mu, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+    return bail(cuda_fail(h, "init fitness"));
+  CREATE_LAUNCH(launch_run_best_init(p, h->fw_x, h->fw_f, h->best_x, h->best_f, h->stream), "init best");
+  h->evals = p.mu;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(cuda_fail(h, "create synchronise"));
+  st = check_status_word(h);
+  if (st != MGFWA_OK) return bail(st);
+  *out = h;
+  return MGFWA_OK;
+}
+
+mgfwa_status mgfwa_step(mgfwa_t* h, int32_t n_generations) {
+  mgfwa_status st = check_usable(h);
+  if (st != MGFWA_OK) return st;
+  if (n_generations < 0) return fail(h, MGFWA_EINVAL, "negative generation count");
+  if (h->next_phase != MGFWA_PHASE_EXPLODE) return fail(h, MGFWA_EINVAL, "a debug generation is in progress");
+  if (n_generations > 0 && !budget_allows(h)) return fail(h, MGFWA_EBUDGET, "budget spent");
+  for (int32_t i = 0; i < n_generations && budget_allows(h); ++i) {
+    st = one_generation(h);
+    if (st != MGFWA_OK) return st;
+  }
+  return MGFWA_OK;
+}
+
+mgfwa_status mgfwa_run(mgfwa_t* h) {
+  mgfwa_status st = check_usable(h);
+  if (st != MGFWA_OK) return st;
+  if (h->next_phase != MGFWA_PHASE_EXPLODE) return fail(h, MGFWA_EINVAL, "a debug generation is in progress");
+  while (budget_allows(h)) {
+    st = one_generation(h);
+    if (st != MGFWA_OK) return st;
+  }
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h, "run synchronise");
+  return check_status_word(h);
+}
+
+mgfwa_status mgfwa_best(mgfwa_t* h, float* x_out, double* f_out, int64_t* evals_out) {
+  mgfwa_status st = check_usable(h);
+  if (st != MGFWA_OK) return st;
+  if (f_out) {
+    if (h->kind == MGFWA_OBJ_SPHERE)
+      MG_LAUNCH(h, launch_sphere_f64(h->best_x, h->p.D, h->f64, h->stream), "FP64 sphere");
+    else
+      MG_LAUNCH(h, launch_fitness_f64(h->mlp, h->best_x, h->ce64, h->f64, h->stream), "FP64 fitness");
+    if (cudaMemcpyAsync(f_out, h->f64, sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+      return cuda_fail(h, "read best fitness");
+  }
+  if (x_out && cudaMemcpyAsync(x_out, h->best_x, sizeof(float) * h->p.D, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    return cuda_fail(h, "read best position");
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h, "best synchronise");
+  if (evals_out) *evals_out = h->evals;
+  return check_status_word(h);
+}
+
+mgfwa_status mgfwa_evaluate(mgfwa_t* h, const float* xs, int64_t count, int32_t precision, float* f_out) {
+  mgfwa_status st = check_usable(h);
+  if (st != MGFWA_OK) return st;
+  if (!xs || !f_out || count < 0 || count > h->P) return fail(h, MGFWA_EINVAL, "evaluate: bad arguments (count <= %lld)", (long long)h->P);
+  if (precision != MGFWA_FP32 && precision != MGFWA_BF16) return fail(h, MGFWA_EINVAL, "evaluate: bad precision");
+  if (use_tc(h, precision) && !h->op) return fail(h, MGFWA_EINVAL, "evaluate: handle was created without the BF16 path");
+  if (h->next_phase != MGFWA_PHASE_EXPLODE) return fail(h, MGFWA_EINVAL, "a debug generation is in progress");
+  if (count == 0) return MGFWA_OK;
+  if (cudaMemcpy2DAsync(h->sparks, sizeof(float) * h->p.Dp, xs, sizeof(float) * h->p.D, sizeof(float) * h->p.D, count,
+                        cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return cuda_fail(h, "evaluate: copy rows");
+  if (use_tc(h, precision))
+    MG_LAUNCH(h, launch_to_operand(h->sparks, h->p.Dp, (int32_t)count, h->mlp.w1_elems, h->op, h->stream), "evaluate operand");
+  st = eval_rows(h, 0, (int32_t)count, precision);
+  if (st != MGFWA_OK) return st;
+  if (cudaMemcpyAsync(f_out, h->fit, sizeof(float) * count, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    return cuda_fail(h, "evaluate: read fitness");
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h, "evaluate synchronise");
+  return check_status_word(h);
+}
+
+mgfwa_status mgfwa_get_info(const mgfwa_t* h, mgfwa_info* info) {
+  if (!h || !info) return MGFWA_EINVAL;
+  info->evals = h->evals;
+  info->generations = h->gen;
+  info->k = h->p.k;
+  info->dim_padded = h->p.Dp;
+  info->sparks_per_gen = h->P;
+  info->device_bytes = (int64_t)h->arena_bytes;
+  info->kernel_launches = h->launches;
+  return MGFWA_OK;
+}
+
+void mgfwa_destroy(mgfwa_t* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  tc_release(h->tc);
+  if (h->arena) cudaFree(h->arena);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  cudaGetLastError();
+  delete h;
+}
+
+const char* mgfwa_last_error(const mgfwa_t* h) {
+  if (!h) return g_create_error.c_str();
+  return h->err.c_str();
+}
+
+// ---------------------------------------------------------------------------
+// mgfwa_debug.h
+
+mgfwa_status mgfwa_debug_phase(mgfwa_t* h, int32_t phase) {
+  mgfwa_status st = check_usable(h);
+  if (st != MGFWA_OK) return st;
+  if (phase != h->next_phase)
+    return fail(h, MGFWA_EINVAL, "phase %d out of order (expected %d)", phase, h->next_phase);
+  if (phase == MGFWA_PHASE_EXPLODE && !budget_allows(h)) return fail(h, MGFWA_EBUDGET, "budget spent");
+  st = run_phase(h, phase);
+  if (st != MGFWA_OK) return st;
+  h->next_phase = phase == MGFWA_PHASE_SELECT ? MGFWA_PHASE_EXPLODE : phase + 1;
+  return MGFWA_OK;
+}
+
+namespace {
+struct BufView {
+  void* dev;
+  int64_t rows;      // 0 for flat buffers
+  int64_t row_bytes; // packed host bytes per row
+  int64_t pitch;     // device bytes per row
+  int64_t flat_bytes;
+};
+
+bool buffer_view(mgfwa_t* h, int32_t buf, BufView* v) {
+  const Problem& p = h->p;
+  const int64_t n_e = (int64_t)p.mu * p.lam;
+  const int64_t rb = sizeof(float) * p.D, pitch = sizeof(float) * p.Dp;
+  *v = BufView{nullptr, 0, 0, 0, 0};
+  switch (buf) {
+    case MGFWA_BUF_FW_X: *v = {h->fw_x, p.mu, rb, pitch, 0}; return true;
+    case MGFWA_BUF_FW_AMP: *v = {h->fw_amp, 0, 0, 0, (int64_t)sizeof(float) * p.mu}; return true;
+    case MGFWA_BUF_FW_F: *v = {h->fw_f, 0, 0, 0, (int64_t)sizeof(float) * p.mu}; return true;
+    case MGFWA_BUF_SPARKS: *v = {h->sparks, n_e, rb, pitch, 0}; return true;
+    case MGFWA_BUF_GUIDES: *v = {h->sparks + n_e * p.Dp, (int64_t)p.mu * p.m, rb, pitch, 0}; return true;
+    case MGFWA_BUF_FIT_E: *v = {h->fit, 0, 0, 0, (int64_t)sizeof(float) * n_e}; return true;
+    case MGFWA_BUF_FIT_G: *v = {h->fit + n_e, 0, 0, 0, (int64_t)sizeof(float) * p.mu * p.m}; return true;
+    case MGFWA_BUF_TOP: *v = {h->top, 0, 0, 0, (int64_t)sizeof(int32_t) * p.mu * p.m * p.k}; return true;
+    case MGFWA_BUF_BOTTOM: *v = {h->bottom, 0, 0, 0, (int64_t)sizeof(int32_t) * p.mu * p.m * p.k}; return true;
+    case MGFWA_BUF_WINNER: *v = {h->winner, 0, 0, 0, (int64_t)sizeof(int32_t) * p.mu}; return true;
+    case MGFWA_BUF_BEST_X: *v = {h->best_x, 1, rb, pitch, 0}; return true;
+    case MGFWA_BUF_BEST_F: *v = {h->best_f, 0, 0, 0, (int64_t)sizeof(float)}; return true;
+  }
+  return false;
+}
+}  // namespace
+
+mgfwa_status mgfwa_debug_read(mgfwa_t* h, int32_t buf, void* host, int64_t nbytes) {
+  mgfwa_status st = check_usable(h);
+  if (st != MGFWA_OK) return st;
+  BufView v;
+  if (!host || !buffer_view(h, buf, &v)) return fail(h, MGFWA_EINVAL, "debug_read: unknown buffer %d", buf);
+  const int64_t want = v.rows ? v.rows * v.row_bytes : v.flat_bytes;
+  if (nbytes != want) return fail(h, MGFWA_EINVAL, "debug_read: buffer %d holds %lld bytes", buf, (long long)want);
+  cudaError_t e = v.rows ? cudaMemcpy2DAsync(host, v.row_bytes, v.dev, v.pitch, v.row_bytes, v.rows,
+                                             cudaMemcpyDeviceToHost, h->stream)
+                         : cudaMemcpyAsync(host, v.dev, v.flat_bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h, "debug_read");
+  return MGFWA_OK;
+}
+
+mgfwa_status mgfwa_debug_write(mgfwa_t* h, int32_t buf, const void* host, int64_t nbytes) {
+  mgfwa_status st = check_usable(h);
+  if (st != MGFWA_OK) return st;
+  BufView v;
+  if (!host || !buffer_view(h, buf, &v)) return fail(h, MGFWA_EINVAL, "debug_write: unknown buffer %d", buf);
+  const int64_t want = v.rows ? v.rows * v.row_bytes : v.flat_bytes;
+  if (nbytes != want) return fail(h, MGFWA_EINVAL, "debug_write: buffer %d holds %lld bytes", buf, (long long)want);
+  cudaError_t e = v.rows ? cudaMemcpy2DAsync(v.dev, v.pitch, host, v.row_bytes, v.row_bytes, v.rows,
+                                             cudaMemcpyHostToDevice, h->stream)
+                         : cudaMemcpyAsync(v.dev, host, v.flat_bytes, cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h, "debug_write");
+  return MGFWA_OK;
+}
+
+mgfwa_status mgfwa_debug_profile(mgfwa_t* h, int32_t enable) {
+  mgfwa_status st = check_usable(h);
+  if (st != MGFWA_OK) return st;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h, "profile synchronise");
+  h->ev_marks.clear();
+  h->ev_next = 0;
+  h->profiling = enable != 0;
+  if (h->profiling && h->ev_pool.empty()) {
+    h->ev_pool.resize(1 << 14);
+    for (auto& e : h->ev_pool)
+      if (cudaEventCreate(&e) != cudaSuccess) return cuda_fail(h, "event pool");
+  }
+  return MGFWA_OK;
+}
+
+mgfwa_status mgfwa_debug_kernel_times(mgfwa_t* h, double* ms_out, int64_t* launches_out) {
+  mgfwa_status st = check_usable(h);
+  if (st != MGFWA_OK) return st;
+  if (!ms_out || !launches_out) return fail(h, MGFWA_EINVAL, "kernel_times: null output");
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h, "kernel_times synchronise");
+  for (int g = 0; g < MGFWA_N_KERNEL_GROUPS; ++g) {
+    ms_out[g] = 0.0;
+    launches_out[g] = 0;
+  }
+  for (auto& m : h->ev_marks) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, m.second.first, m.second.second) != cudaSuccess) return cuda_fail(h, "elapsed");
+    ms_out[m.first] += ms;
+    launches_out[m.first] += 1;
+  }
+  return MGFWA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,123 @@
+// Internal declarations shared by the library's translation units: the
+// device-side problem description, the Philox4x32-10 generator and the
+// kernel launchers.  Nothing here is part of the C ABI (include/mgfwa.h).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mgfwa {
+
+// Philox stream purposes: the fourth counter word.
+constexpr uint32_t kInit = 0, kExplode = 1, kMap = 2, kGmap = 3;
+
+// Scalar parameters of one run, passed by value to the kernels.
+struct Problem {
+  int64_t D;       // search dimension
+  int64_t Dp;      // padded row stride (floats), a multiple of 64
+  float lb, ub;
+  int32_t mu, lam, m, g, k;
+  float beta, amp0, c_a, c_r;
+  uint32_t key0, key1;  // Philox key: low and high words of the seed
+};
+
+// The MLP objective as the kernels see it.
+struct Mlp {
+  int32_t n_layers;    // linear layers (2 or 3)
+  int32_t widths[4];   // d_in, h1, [h2,] C
+  int32_t acts[3];     // hidden activations
+  int64_t N;
+  const float* X;             // [N][d_in] FP32
+  const __nv_bfloat16* Xbf;   // [N][d_in] BF16 (tensor-core path) or null
+  const int32_t* y;           // [N]
+  int64_t w_off[3], b_off[3]; // offsets of W_l and b_l in the search vector
+  int64_t w1_elems;           // h1 * d_in
+};
+
+enum { kActTanh = 0, kActRelu = 1 };
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products
+// on words 0 and 2, xor/permute with words 1, 3 and the round key, key bumped
+// by the Weyl constants between rounds.
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Uniform on the 2^-24 grid of [0, 1).
+__device__ __forceinline__ float u24(uint32_t r) { return __uint2float_rn(r >> 8) * 0x1p-24f; }
+
+__device__ __forceinline__ float lane_of(const float4& v, int l) {
+  return l == 0 ? v.x : l == 1 ? v.y : l == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ uint32_t lane_of(const uint4& v, int l) {
+  return l == 0 ? v.x : l == 1 ? v.y : l == 2 ? v.z : v.w;
+}
+
+// NaN fitness ranks as +infinity; order is (fitness, index) ascending.
+__device__ __forceinline__ float rank_key(float f) { return isnan(f) ? __int_as_float(0x7f800000) : f; }
+__device__ __forceinline__ bool before(float fa, int ia, float fb, int ib) {
+  const float a = rank_key(fa), b = rank_key(fb);
+  return a < b || (a == b && ia < ib);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers (each returns the number of kernels it enqueued, or -1 after a
+// launch error; the caller reads cudaGetLastError()).
+
+int launch_init(const Problem& p, float* fw_x, float* fw_amp, cudaStream_t s);
+
+// Explosion sparks rows [0, mu*lam) of `sparks` (row stride Dp); if `op` is
+// non-null also the BF16 first-layer operand (w1_elems per spark row).
+int launch_explode(const Problem& p, uint32_t gen, const float* fw_x, const float* fw_amp,
+                   float* sparks, __nv_bfloat16* op, int64_t w1_elems, cudaStream_t s);
+
+int launch_rank(const Problem& p, const float* fit_e, int32_t* top, int32_t* bottom, cudaStream_t s);
+
+// Guiding sparks written to `guides` (mu*m rows of stride Dp) and, if non-
+// null, their operand rows `op_guides`.
+int launch_guide(const Problem& p, uint32_t gen, const float* fw_x, const float* fw_amp,
+                 const float* sparks, const int32_t* top, const int32_t* bottom, float* guides,
+                 __nv_bfloat16* op_guides, int64_t w1_elems, cudaStream_t s);
+
+int launch_run_best_init(const Problem& p, const float* fw_x, const float* fw_f, float* best_x, float* best_f,
+                         cudaStream_t s);
+
+int launch_select(const Problem& p, const float* fit_e, const float* fit_g, const float* sparks,
+                  const float* guides, float* fw_x, float* fw_amp, float* fw_f, int32_t* winner,
+                  float* best_x, float* best_f, cudaStream_t s);
+
+// FP32 CUDA-core fitness of `count` rows (stride `ld` floats): per-(m-tile,
+// row) partial cross-entropy sums into `partial` [mtiles][count] (the mean
+// is taken by launch_fitness_finish).
+int launch_fitness_simt_main(const Mlp& mlp, const float* rows, int64_t ld, int32_t count, float* partial,
+                             cudaStream_t s);
+size_t fitness_simt_smem_bytes(const Mlp& mlp);
+
+// fit[r] = mean over m-tiles of partial: fixed-order FP32 sum / N.
+int launch_fitness_finish(const float* partial, int32_t mtiles, int32_t count, int64_t N, float* fit,
+                          cudaStream_t s);
+
+int launch_fitness_sphere(const float* rows, int64_t ld, int64_t D, int32_t count, float* fit, cudaStream_t s);
+
+// FP64 objective of one FP32 vector: per-sample CE into ce64[N], then the
+// fixed-order mean into *out.
+int launch_fitness_f64(const Mlp& mlp, const float* x, double* ce64, double* out, cudaStream_t s);
+int launch_sphere_f64(const float* x, int64_t D, double* out, cudaStream_t s);
+
+// BF16 copy of the first-layer weights of `count` rows (stride ld) into op.
+int launch_to_operand(const float* rows, int64_t ld, int32_t count, int64_t w1_elems,
+                      __nv_bfloat16* op, cudaStream_t s);
+int launch_f32_to_bf16(const float* src, int64_t n, __nv_bfloat16* dst, cudaStream_t s);
+
+}  // namespace mgfwa
