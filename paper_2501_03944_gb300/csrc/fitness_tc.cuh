@@ -3,7 +3,7 @@
 
 #include <cuda.h>
 
-#include "../../include/mgfwa.h"
+#include "mgfwa.h"
 #include "mgfwa_internal.cuh"
 
 namespace mgfwa {
@@ -15,6 +15,7 @@ struct TcPlan {
   int num_sms = 0;
   int sparks_per_tile = 0;  // whole sparks per N-tile
   int n_tile = 0;           // accumulator columns per tile (sparks_per_tile * h1)
+  int stages = 0;           // shared-memory pipeline depth
   size_t smem_bytes = 0;
 };
 

@@ -7,6 +7,9 @@
 // parameters are the spark (nn.Linear order), on the shared batch X:
 //   h_1 = act(W_1 x_n + b_1), ..., z = W_L h_{L-1} + b_L,
 //   f = (1/N) sum_n [max_c z_c + log sum_c exp(z_c - max_c z_c) - z_{y_n}].
+#include <cstdio>
+#include <cstdlib>
+
 #include "mgfwa_internal.cuh"
 
 namespace mgfwa {
@@ -255,11 +258,13 @@ int launch_fitness_simt_main(const Mlp& mlp, const float* rows, int64_t ld, int3
   if (count <= 0) return 0;
   const size_t smem = smem_for(mlp);
   static size_t configured = 0;
+  if (getenv("MGFWA_TRACE")) fprintf(stderr, "[mgfwa] simt: smem %zu (configured %zu), rows %d, N %lld\n", smem, configured, count, (long long)mlp.N);
   if (smem > configured) {
     if (cudaFuncSetAttribute(k_fitness_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return -1;
     configured = smem;
   }
+  if (getenv("MGFWA_TRACE")) fprintf(stderr, "[mgfwa] simt: attribute set\n");
   const int mtiles = (int)((mlp.N + kMT - 1) / kMT);
   dim3 grid(mtiles, count);
   k_fitness_simt<<<grid, kThreads, smem, s>>>(mlp, rows, ld, count, partial);

@@ -1,15 +1,565 @@
-// Tensor-core fitness path (placeholder until the tcgen05 kernel lands).
+// Tensor-core fitness of many sparks at once (GPU-MGFWA, Algorithm 1:
+// "parallel evaluate all the fitness of the sparks"), written for sm_103a
+// with tcgen05 MMAs, TMEM accumulators and TMA loads.
+//
+// The first layer of every spark's network is one dense GEMM of the shared
+// batch X [N x d_in] against all sparks' stacked first-layer weights
+// [count*h1 x d_in] (BF16 operands, FP32 accumulation).  A tile is 128
+// samples x (S whole sparks x h1 hidden units), so that the epilogue owns
+// complete hidden vectors: it adds b1, applies the activation, runs the
+// small second layer on CUDA cores from shared memory, and reduces the
+// per-sample cross-entropy into one partial sum per (sample tile, spark).
+// Nothing of the hidden layer is written to memory.
+//
+// One persistent CTA per SM; warp roles:
+//   warp 0  TMA producer: X tile (128 x 64) and W tile (S*h1 x 64) per
+//           K block into a ring of shared-memory stages (128B swizzle);
+//   warp 1  TMEM allocator and single-thread MMA issuer (M=128, N=S*h1,
+//           K=16 per instruction) into one of two TMEM accumulators;
+//   warps 2..9  epilogue, two warps per TMEM lane quadrant, each taking
+//           half of the tile's sparks.
+// Every mbarrier wait is bounded: on timeout the CTA raises a flag in
+// shared memory and a bit in the status word, every role leaves its loop,
+// and the CTA frees its TMEM and returns.
+#include <cuda.h>
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+
 #include "fitness_tc.cuh"
 
 namespace mgfwa {
 
-bool tc_supported(const int32_t*, int) { return false; }
-mgfwa_status tc_plan(TcPlan&, const Mlp&, const __nv_bfloat16*, int64_t) { return MGFWA_EINVAL; }
-const char* tc_last_error() { return "tensor-core path not built"; }
+namespace {
+
+constexpr int kBM = 128;         // samples per tile
+constexpr int kBK = 64;          // K elements per stage (128 bytes of BF16: one swizzle row)
+constexpr int kUmmaK = 16;       // K per tcgen05.mma kind::f16
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kMaxStages = 6;
+constexpr int kTmemCols = 512;   // two accumulators at columns 0 and 256
+constexpr uint64_t kWaitBudget = 1ull << 32;  // clock64 ticks before a wait gives up (~2 s)
+
+struct Smem {
+  uint64_t full[kMaxStages];
+  uint64_t empty[kMaxStages];
+  uint64_t tmem_full[2];
+  uint64_t tmem_empty[2];
+  uint64_t mma_done;
+  uint32_t tmem_base;
+  volatile int abort_flag;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait; false if this CTA is aborting (timeout here or elsewhere).
+__device__ __forceinline__ bool mbar_wait(Smem* sm, uint64_t* bar, uint32_t parity, uint32_t* status,
+                                          uint32_t code) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (sm->abort_flag) return false;
+    if ((uint64_t)(clock64() - t0) > kWaitBudget) {
+      sm->abort_flag = 1;
+      atomicOr(status, code);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand in 128-byte swizzled
+// rows, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);        // start address
+  d |= (uint64_t)1 << 16;                         // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                         // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                         // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major.
+__host__ __device__ constexpr uint32_t instr_desc(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 32 lanes x 16 consecutive FP32 columns.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory"); }
+
+// Named barrier over the epilogue warps that also ORs a flag across them, so
+// that every epilogue thread takes the same branch afterwards.
+__device__ __forceinline__ bool epi_bar_any(bool flag) {
+  uint32_t out;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, 1, %2, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(out)
+      : "r"((uint32_t)flag), "n"(32 * kEpiWarps)
+      : "memory");
+  return out != 0;
+}
+
+__device__ __forceinline__ float act_f(int a, float v) { return a == kActTanh ? tanhf(v) : fmaxf(v, 0.0f); }
+
+struct TcArgs {
+  int32_t count;       // sparks in this launch
+  int32_t first_row;   // first operand row (spark * h1) of the launch in the operand tensor map
+  int32_t m_tiles, n_tiles;
+  int32_t k_blocks;
+  int32_t stages;
+  int32_t S;           // sparks per tile
+  int32_t tail_len;    // floats of (b1, W2, b2) per spark
+  int64_t N;
+  int64_t ld;          // FP32 row stride of the sparks
+  int64_t tail_off;    // offset of b1 in a spark row
+  int32_t C;
+  int32_t act;
+  const float* rows;   // FP32 spark rows of this launch
+  const int32_t* y;
+  float* partial;      // [m_tiles][count]
+  uint32_t* status;
+};
+
+template <int H1>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_fitness_tc(const __grid_constant__ CUtensorMap tmap_x, const __grid_constant__ CUtensorMap tmap_w, TcArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  // 1024-byte alignment for the swizzled stages
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int S = a.S;
+  const int n_tile = S * H1;
+  const uint32_t a_bytes = kBM * kBK * 2;
+  const uint32_t b_bytes = (uint32_t)n_tile * kBK * 2;
+  uint8_t* stage_a = base;
+  uint8_t* stage_b = base + (size_t)a.stages * a_bytes;
+  float* tail = reinterpret_cast<float*>(stage_b + (size_t)a.stages * b_bytes);
+  float* red = tail + (size_t)S * a.tail_len;  // [S][4]
+  Smem* sm = reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(red + 4 * S) + 15) & ~uintptr_t(15));
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles = a.m_tiles * a.n_tiles;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < a.stages; ++s) {
+      mbar_init(&sm->full[s], 1);
+      mbar_init(&sm->empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sm->tmem_full[b], 1);
+      mbar_init(&sm->tmem_empty[b], kEpiWarps);
+    }
+    mbar_init(&sm->mma_done, 1);
+    sm->abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm->tmem_base)),
+                 "n"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = sm->tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      uint32_t it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        const int mt = t % a.m_tiles, nt = t / a.m_tiles;
+        const int row_x = mt * kBM;
+        const int row_w = a.first_row + nt * n_tile;
+        for (int kb = 0; kb < a.k_blocks; ++kb, ++it) {
+          const int s = (int)(it % (uint32_t)a.stages);
+          const uint32_t ph = (it / (uint32_t)a.stages) & 1u;
+          if (!mbar_wait(sm, &sm->empty[s], ph ^ 1u, a.status, 1u)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&sm->full[s], a_bytes + b_bytes);
+          tma_load_2d(stage_a + (size_t)s * a_bytes, &tmap_x, kb * kBK, row_x, &sm->full[s]);
+          tma_load_2d(stage_b + (size_t)s * b_bytes, &tmap_w, kb * kBK, row_w, &sm->full[s]);
+        }
+      }
+      // drain: every issued load must land before the CTA may exit
+      if (it > 0) {
+        const uint32_t last = it - 1;
+        for (uint32_t j = (last + 1 > (uint32_t)a.stages ? last + 1 - a.stages : 0); j <= last; ++j) {
+          const int s = (int)(j % (uint32_t)a.stages);
+          const uint32_t ph = (j / (uint32_t)a.stages) & 1u;
+          const long long t0 = clock64();
+          while (!mbar_try_wait(&sm->full[s], ph)) {
+            if ((uint64_t)(clock64() - t0) > kWaitBudget) {
+              atomicOr(a.status, 16u);
+              break;
+            }
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      const uint32_t idesc = instr_desc(kBM, n_tile);
+      uint32_t it = 0;
+      int local = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++local) {
+        const int b = local & 1;
+        const uint32_t use = (uint32_t)(local >> 1);
+        if (!mbar_wait(sm, &sm->tmem_empty[b], (use & 1u) ^ 1u, a.status, 2u)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(b * 256);
+        for (int kb = 0; kb < a.k_blocks; ++kb, ++it) {
+          const int s = (int)(it % (uint32_t)a.stages);
+          const uint32_t ph = (it / (uint32_t)a.stages) & 1u;
+          if (!mbar_wait(sm, &sm->full[s], ph, a.status, 2u)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_addr = smem_u32(stage_a + (size_t)s * a_bytes);
+          const uint32_t b_addr = smem_u32(stage_b + (size_t)s * b_bytes);
+#pragma unroll
+          for (int k = 0; k < kBK / kUmmaK; ++k) {
+            mma_bf16(d_tmem, smem_desc(a_addr + k * kUmmaK * 2), smem_desc(b_addr + k * kUmmaK * 2), idesc,
+                     (kb > 0 || k > 0) ? 1u : 0u);
+          }
+          mma_commit(&sm->empty[s]);
+        }
+        if (!ok) break;
+        mma_commit(&sm->tmem_full[b]);
+      }
+      // every issued MMA completes before TMEM is released: one more commit, bounded wait
+      mma_commit(&sm->mma_done);
+      const long long t0 = clock64();
+      while (!mbar_try_wait(&sm->mma_done, 0u)) {
+        if ((uint64_t)(clock64() - t0) > kWaitBudget) {
+          atomicOr(a.status, 32u);
+          break;
+        }
+      }
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    const int ew = warp - 2;                 // 0..7
+    const int quad = warp & 3;               // TMEM lane quadrant this warp may access
+    const int half = ew >> 2;                // which half of the tile's sparks
+    const int et = threadIdx.x - 64;         // 0..255
+    const int row_in_tile = quad * 32 + lane;
+    int local = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++local) {
+      const int mt = t % a.m_tiles, nt = t / a.m_tiles;
+      const int b = local & 1;
+      const uint32_t use = (uint32_t)(local >> 1);
+      const int s0 = nt * S;
+      const int s_valid = min(S, a.count - s0);
+      // stage the (b1, W2, b2) block of the tile's sparks
+      for (int s = 0; s < s_valid; ++s) {
+        const float* src = a.rows + (int64_t)(s0 + s) * a.ld + a.tail_off;
+        for (int e = et; e < a.tail_len; e += 32 * kEpiWarps) tail[s * a.tail_len + e] = src[e];
+      }
+      const bool ok = mbar_wait(sm, &sm->tmem_full[b], use & 1u, a.status, 4u);
+      if (epi_bar_any(!ok || sm->abort_flag)) break;
+      tc_fence_after();
+      const int64_t n = (int64_t)mt * kBM + row_in_tile;
+      const bool valid_row = n < a.N;
+      const int label = valid_row ? a.y[n] : 0;
+      for (int s = half; s < s_valid; s += 2) {
+        const float* b1 = tail + s * a.tail_len;
+        const float* W2 = b1 + H1;
+        const float* b2 = W2 + a.C * H1;
+        float z[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) z[c] = c < a.C ? b2[c] : 0.0f;
+        const uint32_t col0 = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 256 + s * H1);
+#pragma unroll
+        for (int j0 = 0; j0 < H1; j0 += 64) {
+          constexpr int kChunk = H1 < 64 ? H1 : 64;
+          float h[kChunk];
+#pragma unroll
+          for (int q = 0; q < kChunk; q += 16) tmem_ld16(col0 + (uint32_t)(j0 + q), h + q);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < kChunk; ++j) h[j] = act_f(a.act, h[j] + b1[j0 + j]);
+#pragma unroll
+          for (int c = 0; c < 32; ++c) {
+            if (c < a.C) {
+              const float* wr = W2 + c * H1 + j0;
+              float acc = z[c];
+#pragma unroll
+              for (int j = 0; j < kChunk; ++j) acc = fmaf(wr[j], h[j], acc);
+              z[c] = acc;
+            }
+          }
+        }
+        float ce = 0.0f;
+        if (valid_row) {
+          float zmax = z[0];
+#pragma unroll
+          for (int c = 1; c < 32; ++c)
+            if (c < a.C) zmax = fmaxf(zmax, z[c]);
+          float se = 0.0f;
+          float zy = 0.0f;
+#pragma unroll
+          for (int c = 0; c < 32; ++c) {
+            if (c < a.C) {
+              se += expf(z[c] - zmax);
+              if (c == label) zy = z[c];
+            }
+          }
+          ce = (zmax + logf(se)) - zy;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) ce += __shfl_xor_sync(0xffffffffu, ce, off);
+        if (lane == 0) red[s * 4 + quad] = ce;
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm->tmem_empty[b]);
+      epi_bar();
+      if (et < s_valid) {
+        const int s = et;
+        const float v = ((red[s * 4 + 0] + red[s * 4 + 1]) + red[s * 4 + 2]) + red[s * 4 + 3];
+        a.partial[(int64_t)mt * a.count + s0 + s] = v;
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "n"(kTmemCols) : "memory");
+  }
+}
+
+std::string g_err;
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled get_encoder() {
+  static EncodeTiled fn = nullptr;
+  if (fn) return fn;
+  void* p = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || p == nullptr) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  fn = reinterpret_cast<EncodeTiled>(p);
+  return fn;
+}
+
+bool encode_2d(CUtensorMap* map, const void* ptr, uint64_t inner, uint64_t outer, uint32_t box_inner,
+               uint32_t box_outer) {
+  EncodeTiled enc = get_encoder();
+  if (!enc) {
+    g_err = "cuTensorMapEncodeTiled unavailable";
+    return false;
+  }
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {inner * 2};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    g_err = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
+    return false;
+  }
+  return true;
+}
+
+int sparks_per_tile(int h1) { return 256 / h1; }
+
+int tail_len(const Mlp& mlp) {
+  const int h1 = mlp.widths[1], C = mlp.widths[2];
+  return h1 + C * h1 + C;
+}
+
+template <int H1>
+cudaError_t launch_h1(const TcPlan& plan, const TcArgs& args, cudaStream_t s) {
+  static size_t configured = 0;
+  if (plan.smem_bytes > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_fitness_tc<H1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)plan.smem_bytes);
+    if (e != cudaSuccess) return e;
+    configured = plan.smem_bytes;
+  }
+  const int tiles = args.m_tiles * args.n_tiles;
+  const int grid = tiles < plan.num_sms ? tiles : plan.num_sms;
+  k_fitness_tc<H1><<<grid, kThreads, plan.smem_bytes, s>>>(plan.tmap_x, plan.tmap_w, args);
+  return cudaPeekAtLastError();
+}
+
+}  // namespace
+
+bool tc_supported(const int32_t* widths, int n_layers) {
+  if (n_layers != 2) return false;
+  const int h1 = widths[1];
+  if (widths[0] % 8 != 0) return false;
+  if (!(h1 == 16 || h1 == 32 || h1 == 64 || h1 == 128 || h1 == 256)) return false;
+  return widths[2] >= 2 && widths[2] <= 32;
+}
+
+mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const __nv_bfloat16* op, int64_t max_rows) {
+  plan = TcPlan();
+  if (!tc_supported(mlp.widths, mlp.n_layers)) {
+    g_err = "network shape not supported by the tensor-core path";
+    return MGFWA_EINVAL;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    g_err = "cudaGetDeviceProperties failed";
+    return MGFWA_ECUDA;
+  }
+  if (prop.major != 10) {
+    g_err = "tensor-core path needs a Blackwell (sm_10x) GPU";
+    return MGFWA_EINVAL;
+  }
+  const int h1 = mlp.widths[1];
+  const int d_in = mlp.widths[0];
+  plan.num_sms = prop.multiProcessorCount;
+  plan.sparks_per_tile = sparks_per_tile(h1);
+  plan.n_tile = plan.sparks_per_tile * h1;
+  const size_t a_bytes = (size_t)kBM * kBK * 2, b_bytes = (size_t)plan.n_tile * kBK * 2;
+  const size_t tail_bytes = sizeof(float) * ((size_t)plan.sparks_per_tile * tail_len(mlp) + 4 * plan.sparks_per_tile + 4);
+  const size_t fixed = 1024 + tail_bytes + sizeof(Smem) + 64;
+  const size_t limit = (size_t)prop.sharedMemPerBlockOptin;
+  int stages = kMaxStages;
+  while (stages > 2 && fixed + stages * (a_bytes + b_bytes) > limit) --stages;
+  if (fixed + stages * (a_bytes + b_bytes) > limit) {
+    g_err = "shared memory too small for the tensor-core tiles";
+    return MGFWA_EINVAL;
+  }
+  plan.stages = stages;
+  plan.smem_bytes = fixed + stages * (a_bytes + b_bytes);
+  if (!encode_2d(&plan.tmap_x, mlp.Xbf, (uint64_t)d_in, (uint64_t)mlp.N, kBK, kBM)) return MGFWA_ECUDA;
+  if (!encode_2d(&plan.tmap_w, op, (uint64_t)d_in, (uint64_t)(max_rows * h1), kBK, (uint32_t)plan.n_tile))
+    return MGFWA_ECUDA;
+  plan.ready = true;
+  return MGFWA_OK;
+}
+
+const char* tc_last_error() { return g_err.c_str(); }
+
 void tc_release(TcPlan& plan) { plan.ready = false; }
-int launch_fitness_tc(const TcPlan&, const Mlp&, int64_t, const float*, int64_t, int32_t, float*, uint32_t*,
-                      cudaStream_t) {
-  return -1;
+
+int launch_fitness_tc(const TcPlan& plan, const Mlp& mlp, int64_t first, const float* rows, int64_t ld,
+                      int32_t count, float* partial, uint32_t* status, cudaStream_t s) {
+  if (!plan.ready || count <= 0) return count <= 0 ? 0 : -1;
+  const int h1 = mlp.widths[1];
+  TcArgs a;
+  a.count = count;
+  a.first_row = (int32_t)(first * h1);
+  a.m_tiles = (int32_t)((mlp.N + kBM - 1) / kBM);
+  a.S = plan.sparks_per_tile;
+  a.n_tiles = (count + a.S - 1) / a.S;
+  a.k_blocks = (mlp.widths[0] + kBK - 1) / kBK;
+  a.stages = plan.stages;
+  a.tail_len = tail_len(mlp);
+  a.N = mlp.N;
+  a.ld = ld;
+  a.tail_off = mlp.b_off[0];
+  a.C = mlp.widths[2];
+  a.act = mlp.acts[0];
+  a.rows = rows;
+  a.y = mlp.y;
+  a.partial = partial;
+  a.status = status;
+  cudaError_t e;
+  switch (h1) {
+    case 16: e = launch_h1<16>(plan, a, s); break;
+    case 32: e = launch_h1<32>(plan, a, s); break;
+    case 64: e = launch_h1<64>(plan, a, s); break;
+    case 128: e = launch_h1<128>(plan, a, s); break;
+    case 256: e = launch_h1<256>(plan, a, s); break;
+    default: return -1;
+  }
+  return e == cudaSuccess ? 1 : -1;
 }
 
 }  // namespace mgfwa

@@ -6,13 +6,14 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
 #include <vector>
 
-#include "../../include/mgfwa.h"
-#include "../../include/mgfwa_debug.h"
+#include "mgfwa.h"
+#include "mgfwa_debug.h"
 #include "fitness_tc.cuh"
 #include "mgfwa_internal.cuh"
 
@@ -66,6 +67,24 @@ struct mgfwa_handle {
 namespace {
 
 thread_local std::string g_create_error;
+
+// MGFWA_TRACE=1 in the environment prints the steps of mgfwa_create to stderr.
+bool trace_on() {
+  static int on = -1;
+  if (on < 0) {
+    const char* v = getenv("MGFWA_TRACE");
+    on = (v && v[0] == '1') ? 1 : 0;
+  }
+  return on == 1;
+}
+#define TRACE(...)                       \
+  do {                                   \
+    if (trace_on()) {                    \
+      fprintf(stderr, "[mgfwa] " __VA_ARGS__); \
+      fputc('\n', stderr);               \
+      fflush(stderr);                    \
+    }                                    \
+  } while (0)
 
 mgfwa_status fail(mgfwa_t* h, mgfwa_status st, const char* fmt, ...) {
   char buf[512];
@@ -275,6 +294,8 @@ mgfwa_status validate(const mgfwa_config* c, const mgfwa_objective* o) {
   return MGFWA_OK;
 }
 
+// Next 256-byte-aligned slice of `count` elements; with a null base only the
+// offsets are computed (the sizing pass).
 template <typename T>
 T* carve(char*& cur, size_t count) {
   T* p = reinterpret_cast<T*>(cur);
@@ -303,8 +324,10 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
   if (!out) return fail(nullptr, MGFWA_EINVAL, "null output handle pointer");
   *out = nullptr;
   g_create_error.clear();
+  TRACE("create: validate");
   mgfwa_status st = validate(cfg, obj);
   if (st != MGFWA_OK) return st;
+  TRACE("create: validated");
   mgfwa_t* h = new (std::nothrow) mgfwa_t();
   if (!h) return fail(nullptr, MGFWA_ENOMEM, "host allocation failed");
   h->cfg = *cfg;
@@ -353,27 +376,33 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
   }
   const bool want_op = obj->kind == MGFWA_OBJ_MLP_CE && cfg->precision == MGFWA_BF16;
 
-  // One arena for all device state.
-  size_t bytes = 0;
-  auto add = [&](size_t b) { bytes += (size_t)round_up((int64_t)b, 256); };
-  add(sizeof(float) * N * d_in);                               // X
-  add(want_op ? sizeof(__nv_bfloat16) * N * d_in : 0);         // Xbf
-  add(sizeof(int32_t) * N);                                    // y
-  add(sizeof(float) * p.mu * p.Dp);                            // fw_x
-  add(sizeof(float) * p.mu);                                   // fw_amp
-  add(sizeof(float) * p.mu);                                   // fw_f
-  add(sizeof(float) * h->P * p.Dp);                            // sparks
-  add(want_op ? sizeof(__nv_bfloat16) * h->P * mlp.w1_elems : 0);  // op
-  add(sizeof(float) * h->P);                                   // fit
-  add(sizeof(float) * (size_t)h->mtiles * h->P);               // partial
-  add(sizeof(int32_t) * p.mu * p.m * p.k * 2);                 // top, bottom
-  add(sizeof(int32_t) * p.mu);                                 // winner
-  add(sizeof(float) * p.Dp);                                   // best_x
-  add(sizeof(float));                                          // best_f
-  add(sizeof(double) * (N > 0 ? N : 1));                       // ce64
-  add(sizeof(double));                                         // f64
-  add(sizeof(uint32_t));                                       // status
+  // One arena for all device state; sizing and carving share one layout pass.
+  auto layout = [&](char* base) -> size_t {
+    char* cur = base;
+    h->X = carve<float>(cur, N * d_in);
+    h->Xbf = want_op ? carve<__nv_bfloat16>(cur, N * d_in) : nullptr;
+    h->y = carve<int32_t>(cur, N);
+    h->fw_x = carve<float>(cur, p.mu * p.Dp);
+    h->fw_amp = carve<float>(cur, p.mu);
+    h->fw_f = carve<float>(cur, p.mu);
+    h->sparks = carve<float>(cur, h->P * p.Dp);
+    h->op = want_op ? carve<__nv_bfloat16>(cur, h->P * mlp.w1_elems) : nullptr;
+    h->fit = carve<float>(cur, h->P);
+    h->partial = carve<float>(cur, (size_t)h->mtiles * h->P);
+    h->top = carve<int32_t>(cur, p.mu * p.m * p.k);
+    h->bottom = carve<int32_t>(cur, p.mu * p.m * p.k);
+    h->winner = carve<int32_t>(cur, p.mu);
+    h->best_x = carve<float>(cur, p.Dp);
+    h->best_f = carve<float>(cur, 1);
+    h->ce64 = carve<double>(cur, N > 0 ? N : 1);
+    h->f64 = carve<double>(cur, 1);
+    h->status = carve<uint32_t>(cur, 1);
+    return (size_t)(cur - base);
+  };
+  const size_t bytes = layout(nullptr);
   h->arena_bytes = bytes;
+  TRACE("create: arena %zu bytes, Dp %lld, P %lld, N %lld, d_in %lld", bytes, (long long)p.Dp, (long long)h->P,
+        (long long)N, (long long)d_in);
 
   if (cuda_stream) {
     h->stream = (cudaStream_t)cuda_stream;
@@ -387,29 +416,17 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
   }
   if (cudaMalloc(&h->arena, bytes) != cudaSuccess) {
     cudaGetLastError();
+    h->arena = nullptr;
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
     return fail(nullptr, MGFWA_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
   }
-  char* cur = h->arena;
-  h->X = carve<float>(cur, N * d_in);
-  h->Xbf = want_op ? carve<__nv_bfloat16>(cur, N * d_in) : nullptr;
-  h->y = carve<int32_t>(cur, N);
-  h->fw_x = carve<float>(cur, p.mu * p.Dp);
-  h->fw_amp = carve<float>(cur, p.mu);
-  h->fw_f = carve<float>(cur, p.mu);
-  h->sparks = carve<float>(cur, h->P * p.Dp);
-  h->op = want_op ? carve<__nv_bfloat16>(cur, h->P * mlp.w1_elems) : nullptr;
-  h->fit = carve<float>(cur, h->P);
-  h->partial = carve<float>(cur, (size_t)h->mtiles * h->P);
-  h->top = carve<int32_t>(cur, p.mu * p.m * p.k);
-  h->bottom = carve<int32_t>(cur, p.mu * p.m * p.k);
-  h->winner = carve<int32_t>(cur, p.mu);
-  h->best_x = carve<float>(cur, p.Dp);
-  h->best_f = carve<float>(cur, 1);
-  h->ce64 = carve<double>(cur, N > 0 ? N : 1);
-  h->f64 = carve<double>(cur, 1);
-  h->status = carve<uint32_t>(cur, 1);
+  if (layout(h->arena) != bytes) {
+    cudaFree(h->arena);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return fail(nullptr, MGFWA_EINVAL, "internal: arena layout mismatch");
+  }
 
   mlp.X = h->X;
   mlp.Xbf = h->Xbf;
@@ -421,7 +438,9 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
     g_create_error = e;
     return s;
   };
+  TRACE("create: allocated");
   if (cudaMemsetAsync(h->arena, 0, bytes, h->stream) != cudaSuccess) return bail(cuda_fail(h, "memset arena"));
+  TRACE("create: memset");
   if (N > 0) {
     if (cudaMemcpyAsync(h->X, obj->X, sizeof(float) * N * d_in, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
         cudaMemcpyAsync(h->y, obj->y, sizeof(int32_t) * N, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
@@ -435,19 +454,25 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
       return bail(st);
     }
   }
+  TRACE("create: batch copied");
   // Algorithm 1, init: mu fireworks uniform in the box, evaluated.
   CREATE_LAUNCH(launch_init(p, h->fw_x, h->fw_amp, h->stream), "init");
+  TRACE("create: init launched");
   if (cudaMemcpy2DAsync(h->sparks, sizeof(float) * p.Dp, h->fw_x, sizeof(float) * p.Dp, sizeof(float) * p.Dp, p.mu,
                         cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
     return bail(cuda_fail(h, "stage init rows"));
   if (want_op) CREATE_LAUNCH(launch_to_operand(h->sparks, p.Dp, p.mu, mlp.w1_elems, h->op, h->stream), "init operand");
+  TRACE("create: staged");
   st = eval_rows(h, 0, p.mu, cfg->precision);
   if (st != MGFWA_OK) return bail(st);
+  TRACE("create: evaluated");
   if (cudaMemcpyAsync(h->fw_f, h->fit, sizeof(float) * p.mu, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
     return bail(cuda_fail(h, "init fitness"));
   CREATE_LAUNCH(launch_run_best_init(p, h->fw_x, h->fw_f, h->best_x, h->best_f, h->stream), "init best");
   h->evals = p.mu;
+  TRACE("create: best launched");
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(cuda_fail(h, "create synchronise"));
+  TRACE("create: synchronised");
   st = check_status_word(h);
   if (st != MGFWA_OK) return bail(st);
   *out = h;

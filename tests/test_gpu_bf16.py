@@ -1,0 +1,135 @@
+"""GPU parity of the BF16 tensor-core fitness path (tcgen05 + TMA) against the
+FP64 oracle, through the C ABI.
+
+Bar: per-spark fitness within 1e-2 relative of the oracle (BF16 operands,
+FP32 accumulation), plus an absolute floor of 1e-3 nats for samples whose
+loss is tiny (a BF16 weight carries 2^-9 relative error; logits of ~1e2
+then move by ~0.1 / sqrt(K)-averaged ~1e-3).  The 1e-2 bar is for batches
+of many samples, whose independent rounding errors average out in the mean
+loss; a batch of ONE sample keeps the full per-sample error (about
+2^-9 sqrt(fan_in) relative on each logit), so that edge case gets 3e-2.  Sampling, ranking, guiding and
+selection are the same kernels as the FP32 path and stay bit-exact when fed
+the oracle's fitness.  The tensor-core result is deterministic: the same
+sparks give bitwise the same fitness on every call.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+BF16_RTOL = 1e-2
+BF16_ATOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2501_03944_gb300 as p
+    return p
+
+
+def _rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.abs(a - b) / (np.abs(b) + BF16_ATOL / BF16_RTOL)
+
+
+@pytest.mark.parametrize("widths,acts,N,count", [
+    ((784, 64, 10), (1,), 200, 24),        # one sample tile (ragged), a few spark tiles
+    ((784, 64, 10), (1,), 2048, 56),       # 16 sample tiles
+    ((8, 16, 3), (0,), 300, 56),           # K = 8 < one K block (TMA zero fill), 16 sparks per tile
+    ((64, 32, 7), (0,), 129, 24),          # ragged tail of one sample
+    ((96, 128, 5), (1,), 1, 16),           # a single sample
+    ((32, 256, 4), (1,), 260, 12),         # one spark per tile, 256 hidden units
+])
+def test_bf16_fitness_against_oracle(pkg, widths, acts, N, count):
+    w = W.scaled(W.MLP_784_64_10, widths=widths, acts=acts, n_samples=N, n_fireworks=2,
+                 sparks_per_firework=count // 2 - 2, guiding_per_firework=2)
+    X, y = W.make_data(w)
+    prob = oracle.Problem.for_workload(w, X, y)
+    xs = W.random_vectors(count, w.dim, -1.0, 1.0, seed=N + count)
+    xs[0] = 0.0
+    with pkg.Mgfwa.for_workload(w, 5, precision=pkg.MGFWA_BF16, X=X, y=y) as run:
+        got = run.evaluate(xs, pkg.MGFWA_BF16)
+        again = run.evaluate(xs, pkg.MGFWA_BF16)
+        f32 = run.evaluate(xs, pkg.MGFWA_FP32)
+    want = prob.fitness_many(xs, n_threads=8)
+    assert np.array_equal(got, again), "tensor-core fitness is not deterministic"
+    assert abs(got[0] - np.log(widths[-1])) < 1e-6
+    err = _rel(got, want)
+    bar = BF16_RTOL if N >= 128 else 3e-2
+    assert np.all(err <= bar), (np.max(err), got[:4], want[:4])
+    assert np.all(np.abs(f32 - want) <= 1e-5 * np.abs(want) + 1e-5)
+
+
+def test_bf16_generation_phase_by_phase(pkg):
+    w = W.scaled(W.MLP_784_64_10, n_samples=300, n_fireworks=3, sparks_per_firework=40, guiding_per_firework=4)
+    seed = 21
+    X, y = W.make_data(w)
+    prob = oracle.Problem.for_workload(w, X, y)
+    p = oracle.params_for(w)
+    with pkg.Mgfwa.for_workload(w, seed, precision=pkg.MGFWA_BF16, X=X, y=y) as run:
+        fw_x, fw_a = oracle.init(p, seed)
+        assert np.array_equal(run.read(pkg.MGFWA_BUF_FW_X), fw_x)
+        fw_f64 = prob.fitness_many(fw_x, 8)
+        assert np.all(_rel(run.read(pkg.MGFWA_BUF_FW_F), fw_f64) <= BF16_RTOL)
+        fw_f = fw_f64.astype(np.float32)
+        run.write(pkg.MGFWA_BUF_FW_F, fw_f)
+        for gen in (1, 2):
+            ref = oracle.generation(p, prob, seed, gen, fw_x, fw_a, fw_f, n_threads=8)
+            run.phase(pkg.MGFWA_PHASE_EXPLODE)
+            assert np.array_equal(run.read(pkg.MGFWA_BUF_SPARKS), ref["sparks"])
+            run.phase(pkg.MGFWA_PHASE_EVAL_E)
+            assert np.all(_rel(run.read(pkg.MGFWA_BUF_FIT_E), ref["fit_e64"]) <= BF16_RTOL)
+            run.write(pkg.MGFWA_BUF_FIT_E, ref["fit_e"])
+            run.phase(pkg.MGFWA_PHASE_RANK)
+            assert np.array_equal(run.read(pkg.MGFWA_BUF_TOP), ref["top"])
+            run.phase(pkg.MGFWA_PHASE_GUIDE)
+            assert np.array_equal(run.read(pkg.MGFWA_BUF_GUIDES), ref["guides"])
+            run.phase(pkg.MGFWA_PHASE_EVAL_G)
+            assert np.all(_rel(run.read(pkg.MGFWA_BUF_FIT_G), ref["fit_g64"]) <= BF16_RTOL)
+            run.write(pkg.MGFWA_BUF_FIT_G, ref["fit_g"])
+            run.phase(pkg.MGFWA_PHASE_SELECT)
+            assert np.array_equal(run.read(pkg.MGFWA_BUF_FW_X), ref["fw_x"])
+            assert np.array_equal(run.read(pkg.MGFWA_BUF_FW_AMP), ref["fw_amp"])
+            fw_x, fw_a, fw_f = ref["fw_x"], ref["fw_amp"], ref["fw_f"]
+
+
+def test_bf16_full_size_784_64_10(pkg):
+    """Full 784-64-10 workload (1000 explosion sparks x 2048 samples per launch): sampled sparks vs the oracle."""
+    w = W.MLP_784_64_10
+    seed = 4
+    X, y = W.make_data(w)
+    prob = oracle.Problem.for_workload(w, X, y)
+    with pkg.Mgfwa.for_workload(w, seed, precision=pkg.MGFWA_BF16, X=X, y=y) as run:
+        run.phase(pkg.MGFWA_PHASE_EXPLODE)
+        run.phase(pkg.MGFWA_PHASE_EVAL_E)
+        sparks = run.read(pkg.MGFWA_BUF_SPARKS)
+        fe = run.read(pkg.MGFWA_BUF_FIT_E)
+        pick = np.concatenate([np.arange(4), np.random.default_rng(2).choice(1000, 12, replace=False), [996, 997, 998, 999]])
+        assert np.all(_rel(fe[pick], prob.fitness_many(sparks[pick], 8)) <= BF16_RTOL)
+        for ph in (pkg.MGFWA_PHASE_RANK, pkg.MGFWA_PHASE_GUIDE, pkg.MGFWA_PHASE_EVAL_G, pkg.MGFWA_PHASE_SELECT):
+            run.phase(ph)
+        guides = run.read(pkg.MGFWA_BUF_GUIDES)
+        fg = run.read(pkg.MGFWA_BUF_FIT_G)
+        assert np.all(_rel(fg, prob.fitness_many(guides, 8)) <= BF16_RTOL)
+        # BF16 and FP32 agree on every spark of the launch within the BF16 bar
+        f32 = run.evaluate(sparks[:1000], pkg.MGFWA_FP32)
+        assert np.all(_rel(fe, f32.astype(np.float64)) <= BF16_RTOL)
+
+
+def test_bf16_whole_run_learns(pkg):
+    w = W.scaled(W.MLP_784_64_10, eval_budget=W.budget_for_generations(5, 200, 8, 30))
+    X, y = W.make_data(w)
+    prob = oracle.Problem.for_workload(w, X, y)
+    with pkg.Mgfwa.for_workload(w, 11, precision=pkg.MGFWA_BF16, X=X, y=y) as run:
+        f0 = float(np.min(run.read(pkg.MGFWA_BUF_FW_F)))
+        run.run()
+        bx, bf, ev = run.best()
+    assert ev == w.eval_budget
+    assert bf < 0.8 * f0
+    assert abs(bf - prob.fitness(bx)) <= 1e-12 * bf

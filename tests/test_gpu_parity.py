@@ -5,9 +5,12 @@ Bar (per the method's arithmetic):
     (both sides compute them with the same explicitly rounded FP32 steps);
   * rank and selection decisions: bit-exact once fed the oracle's fitness
     (rounded to FP32, the precision the kernels decide in);
-  * FP32 fitness: within 1e-5 relative of the FP64 oracle -- a K-term FP32
-    dot product carries about sqrt(K) 2^-24 relative error per hidden unit,
-    ~2e-6 at K = 784, and the cross-entropy inherits it;
+  * FP32 fitness: within 1e-5 relative of the FP64 oracle plus an absolute
+    floor of 1e-5 nats -- a K-term FP32 dot product carries about
+    sqrt(K) 2^-24 relative error per hidden unit (~2e-6 at K = 784), and a
+    sample's cross-entropy is a difference of logits of magnitude up to
+    ~1e2, whose FP32 rounding (~1e2 x 2^-24 ~ 6e-6) bounds the absolute
+    error once the loss itself is tiny (confidently classified samples);
   * FP64 reported best loss: within 1e-12 relative of the oracle.
 """
 import math
@@ -21,6 +24,7 @@ import workloads as W
 pytestmark = pytest.mark.gpu
 
 FP32_RTOL = 1e-5
+FP32_ATOL = 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -38,10 +42,11 @@ def _setup(w, seed):
     return X, y, prob, p
 
 
-def _rel(a, b):
+def _rel(a, b, atol=FP32_ATOL):
+    """|a - b| / (|b| + atol / rtol): <= FP32_RTOL means within rtol |b| + atol."""
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
-    return np.abs(a - b) / np.maximum(np.abs(b), 1e-30)
+    return np.abs(a - b) / (np.abs(b) + atol / FP32_RTOL)
 
 
 SMALL_CASES = {
