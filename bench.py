@@ -208,21 +208,23 @@ def gpu_arm(args):
 
     # end to end through the C ABI with host buffers: create (copies X, y from pinned host memory),
     # K generations, best position + FP64 loss back to the host, destroy.
-    Xp = torch.from_numpy(X).pin_memory().numpy()
-    yp = torch.from_numpy(y).pin_memory().numpy()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    run2 = pkg.Mgfwa.for_workload(w, seed + 7919, precision=prec, X=Xp, y=yp, stream=stream.cuda_stream)
-    run2.step(args.steps)
-    bx2, bf2, ev2 = run2.best()
-    run2.close()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = None
+    if not args.no_e2e:
+        Xp = torch.from_numpy(X).pin_memory().numpy()
+        yp = torch.from_numpy(y).pin_memory().numpy()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run2 = pkg.Mgfwa.for_workload(w, seed + 7919, precision=prec, X=Xp, y=yp, stream=stream.cuda_stream)
+        run2.step(args.steps)
+        bx2, bf2, ev2 = run2.best()
+        run2.close()
+        e2e_s = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
 
     if rank == 0:
         sparks_total = world * P * args.steps
@@ -269,10 +271,11 @@ def gpu_arm(args):
                 "vs_baseline": None, "dtype": {"bf16": "bf16", "fp32": "f32"}[args.precision],
                 "data": "synthetic", "config": _config(args, world),
                 "clocks": clk.summary(), "gpu_launches": launches,
-                "e2e": {"value": e2e_sparks / e2e_s, "unit": UNIT,
-                        "h2d_bytes_per_step": (X.nbytes + y.nbytes) / args.steps,
-                        "d2h_bytes_per_step": (4 * D + 8) / args.steps,
-                        "note": "create (X, y from pinned host) + K generations + best (x, FP64 loss) + destroy"},
+                "e2e": None if e2e_s is None else {
+                    "value": e2e_sparks / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": (X.nbytes + y.nbytes) / args.steps,
+                    "d2h_bytes_per_step": (4 * D + 8) / args.steps,
+                    "note": "create (X, y from pinned host) + K generations + best (x, FP64 loss) + destroy"},
                 "roofline": roof, "hbm_kernels": hbm, "kernels": kernels,
                 "best_f_fp64": best_f, "evals": evals, "cpu_baseline": cb}
         print(json.dumps(line), flush=True)
@@ -289,6 +292,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=("gb300", "reference"))
     ap.add_argument("--precision", default="bf16", choices=("bf16", "fp32"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end request (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -78,7 +78,8 @@ typedef struct {
 typedef struct {
   int32_t kind;          /* MGFWA_OBJ_MLP_CE or MGFWA_OBJ_SPHERE */
   int32_t n_layers;      /* linear layers, 2 or 3 (MLP) */
-  const int32_t* widths; /* n_layers + 1 widths d_in, h1, [h2,] C; d_in % 8 == 0, h1 <= 256, C <= 32 */
+  const int32_t* widths; /* n_layers + 1 widths d_in, h1, [h2,] C: d_in % 8 == 0, hidden widths <= 192,
+                            C in [2, 32]; the BF16 path needs 2 layers and h1 in {16, 32, 64, 128} */
   const int32_t* acts;   /* n_layers - 1 hidden activations (MGFWA_ACT_*) */
   int64_t n_samples;     /* N >= 1 */
   const float* X;        /* [N][d_in] row-major FP32 */

@@ -19,8 +19,8 @@ struct TcPlan {
   size_t smem_bytes = 0;
 };
 
-// True if the tensor-core path handles this network (d_in % 8 == 0, first
-// hidden width a multiple of 16 in [16, 256], at most 3 linear layers).
+// True if the tensor-core path handles this network: two linear layers,
+// d_in % 8 == 0, first hidden width 16, 32, 64 or 128, 2..32 classes.
 bool tc_supported(const int32_t* widths, int n_layers);
 
 // Encode the tensor maps over the handle's X (BF16) and operand buffers.

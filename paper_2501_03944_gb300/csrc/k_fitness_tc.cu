@@ -12,8 +12,10 @@
 // Nothing of the hidden layer is written to memory.
 //
 // One persistent CTA per SM; warp roles:
-//   warp 0  TMA producer: X tile (128 x 64) and W tile (S*h1 x 64) per
-//           K block into a ring of shared-memory stages (128B swizzle);
+//   warp 0  TMA producer: per tile, a bulk copy of the S sparks' (b1, W2,
+//           b2) blocks into one of two tail buffers, then the X tile
+//           (128 x 64) and W tile (S*h1 x 64) of every K block into a ring
+//           of shared-memory stages (128B swizzle);
 //   warp 1  TMEM allocator and single-thread MMA issuer (M=128, N=S*h1,
 //           K=16 per instruction) into one of two TMEM accumulators;
 //   warps 2..9  epilogue, two warps per TMEM lane quadrant, each taking
@@ -47,6 +49,8 @@ struct Smem {
   uint64_t empty[kMaxStages];
   uint64_t tmem_full[2];
   uint64_t tmem_empty[2];
+  uint64_t tail_full[2];
+  uint64_t tail_empty[2];
   uint64_t mma_done;
   uint32_t tmem_base;
   volatile int abort_flag;
@@ -102,6 +106,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
           smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
+}
+
+// Untiled bulk copy global -> shared (16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -180,6 +192,7 @@ struct TcArgs {
   int32_t stages;
   int32_t S;           // sparks per tile
   int32_t tail_len;    // floats of (b1, W2, b2) per spark
+  int32_t tail_stride; // tail_len rounded up to 4 floats (16 bytes)
   int64_t N;
   int64_t ld;          // FP32 row stride of the sparks
   int64_t tail_off;    // offset of b1 in a spark row
@@ -191,7 +204,7 @@ struct TcArgs {
   uint32_t* status;
 };
 
-template <int H1>
+template <int H1, int CMAX>
 __global__ void __launch_bounds__(kThreads, 1)
     k_fitness_tc(const __grid_constant__ CUtensorMap tmap_x, const __grid_constant__ CUtensorMap tmap_w, TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -203,8 +216,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t b_bytes = (uint32_t)n_tile * kBK * 2;
   uint8_t* stage_a = base;
   uint8_t* stage_b = base + (size_t)a.stages * a_bytes;
-  float* tail = reinterpret_cast<float*>(stage_b + (size_t)a.stages * b_bytes);
-  float* red = tail + (size_t)S * a.tail_len;  // [S][4]
+  float* tails = reinterpret_cast<float*>(stage_b + (size_t)a.stages * b_bytes);  // [2][S][tail_stride]
+  float* red = tails + 2 * (size_t)S * a.tail_stride;  // [S][4]
   Smem* sm = reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(red + 4 * S) + 15) & ~uintptr_t(15));
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -218,6 +231,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sm->tmem_full[b], 1);
       mbar_init(&sm->tmem_empty[b], kEpiWarps);
+      mbar_init(&sm->tail_full[b], 1);
+      mbar_init(&sm->tail_empty[b], kEpiWarps);
     }
     mbar_init(&sm->mma_done, 1);
     sm->abort_flag = 0;
@@ -240,10 +255,25 @@ __global__ void __launch_bounds__(kThreads, 1)
       // ---------------- TMA producer ----------------
       uint32_t it = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+      int local = 0;
+      const uint32_t tail_bytes = (uint32_t)a.tail_stride * 4u;
+      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++local) {
         const int mt = t % a.m_tiles, nt = t / a.m_tiles;
         const int row_x = mt * kBM;
         const int row_w = a.first_row + nt * n_tile;
+        {
+          // (b1, W2, b2) of the tile's sparks for the epilogue
+          const int tb = local & 1;
+          const uint32_t tuse = (uint32_t)(local >> 1);
+          if (!mbar_wait(sm, &sm->tail_empty[tb], (tuse & 1u) ^ 1u, a.status, 1u)) break;
+          const int s0 = nt * S;
+          const int s_valid = min(S, a.count - s0);
+          mbar_expect_tx(&sm->tail_full[tb], tail_bytes * (uint32_t)s_valid);
+          float* dst = tails + (size_t)tb * S * a.tail_stride;
+          for (int s = 0; s < s_valid; ++s)
+            bulk_load(dst + (size_t)s * a.tail_stride, a.rows + (int64_t)(s0 + s) * a.ld + a.tail_off, tail_bytes,
+                      &sm->tail_full[tb]);
+        }
         for (int kb = 0; kb < a.k_blocks; ++kb, ++it) {
           const int s = (int)(it % (uint32_t)a.stages);
           const uint32_t ph = (it / (uint32_t)a.stages) & 1u;
@@ -257,6 +287,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       // drain: every issued load must land before the CTA may exit
+      for (int l = local - 2 > 0 ? local - 2 : 0; l < local; ++l) {
+        const long long t0 = clock64();
+        while (!mbar_try_wait(&sm->tail_full[l & 1], (uint32_t)((l >> 1) & 1))) {
+          if ((uint64_t)(clock64() - t0) > kWaitBudget) {
+            atomicOr(a.status, 16u);
+            break;
+          }
+        }
+      }
       if (it > 0) {
         const uint32_t last = it - 1;
         for (uint32_t j = (last + 1 > (uint32_t)a.stages ? last + 1 - a.stages : 0); j <= last; ++j) {
@@ -329,42 +368,50 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t use = (uint32_t)(local >> 1);
       const int s0 = nt * S;
       const int s_valid = min(S, a.count - s0);
-      // stage the (b1, W2, b2) block of the tile's sparks
-      for (int s = 0; s < s_valid; ++s) {
-        const float* src = a.rows + (int64_t)(s0 + s) * a.ld + a.tail_off;
-        for (int e = et; e < a.tail_len; e += 32 * kEpiWarps) tail[s * a.tail_len + e] = src[e];
-      }
-      const bool ok = mbar_wait(sm, &sm->tmem_full[b], use & 1u, a.status, 4u);
-      if (epi_bar_any(!ok || sm->abort_flag)) break;
-      tc_fence_after();
       const int64_t n = (int64_t)mt * kBM + row_in_tile;
       const bool valid_row = n < a.N;
-      const int label = valid_row ? a.y[n] : 0;
+      const int label = valid_row ? a.y[n] : 0;   // issued before the waits
+      bool ok = mbar_wait(sm, &sm->tmem_full[b], use & 1u, a.status, 4u);
+      ok = ok && mbar_wait(sm, &sm->tail_full[b], use & 1u, a.status, 4u);
+      if (epi_bar_any(!ok || sm->abort_flag)) break;
+      tc_fence_after();
+      const float* tail = tails + (size_t)b * S * a.tail_stride;
       for (int s = half; s < s_valid; s += 2) {
-        const float* b1 = tail + s * a.tail_len;
+        const float* b1 = tail + (size_t)s * a.tail_stride;
         const float* W2 = b1 + H1;
         const float* b2 = W2 + a.C * H1;
-        float z[32];
+        float z[CMAX];
 #pragma unroll
-        for (int c = 0; c < 32; ++c) z[c] = c < a.C ? b2[c] : 0.0f;
+        for (int c = 0; c < CMAX; ++c) z[c] = c < a.C ? b2[c] : 0.0f;
         const uint32_t col0 = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 256 + s * H1);
 #pragma unroll
-        for (int j0 = 0; j0 < H1; j0 += 64) {
-          constexpr int kChunk = H1 < 64 ? H1 : 64;
+        for (int j0 = 0; j0 < H1; j0 += 16) {
+          constexpr int kChunk = 16;
           float h[kChunk];
 #pragma unroll
           for (int q = 0; q < kChunk; q += 16) tmem_ld16(col0 + (uint32_t)(j0 + q), h + q);
           tmem_wait_ld();
+          const float4* b14 = reinterpret_cast<const float4*>(b1 + j0);
 #pragma unroll
-          for (int j = 0; j < kChunk; ++j) h[j] = act_f(a.act, h[j] + b1[j0 + j]);
+          for (int q = 0; q < kChunk / 4; ++q) {
+            const float4 bb = b14[q];
+            h[4 * q + 0] = act_f(a.act, h[4 * q + 0] + bb.x);
+            h[4 * q + 1] = act_f(a.act, h[4 * q + 1] + bb.y);
+            h[4 * q + 2] = act_f(a.act, h[4 * q + 2] + bb.z);
+            h[4 * q + 3] = act_f(a.act, h[4 * q + 3] + bb.w);
+          }
+          // layer 2: classes innermost, so every step has C independent FMA chains
 #pragma unroll
-          for (int c = 0; c < 32; ++c) {
-            if (c < a.C) {
-              const float* wr = W2 + c * H1 + j0;
-              float acc = z[c];
+          for (int q = 0; q < kChunk / 4; ++q) {
 #pragma unroll
-              for (int j = 0; j < kChunk; ++j) acc = fmaf(wr[j], h[j], acc);
-              z[c] = acc;
+            for (int c = 0; c < CMAX; ++c) {
+              if (c < a.C) {
+                const float4 wv = reinterpret_cast<const float4*>(W2 + c * H1 + j0)[q];
+                z[c] = fmaf(wv.x, h[4 * q + 0], z[c]);
+                z[c] = fmaf(wv.y, h[4 * q + 1], z[c]);
+                z[c] = fmaf(wv.z, h[4 * q + 2], z[c]);
+                z[c] = fmaf(wv.w, h[4 * q + 3], z[c]);
+              }
             }
           }
         }
@@ -372,12 +419,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (valid_row) {
           float zmax = z[0];
 #pragma unroll
-          for (int c = 1; c < 32; ++c)
+          for (int c = 1; c < CMAX; ++c)
             if (c < a.C) zmax = fmaxf(zmax, z[c]);
           float se = 0.0f;
           float zy = 0.0f;
 #pragma unroll
-          for (int c = 0; c < 32; ++c) {
+          for (int c = 0; c < CMAX; ++c) {
             if (c < a.C) {
               se += expf(z[c] - zmax);
               if (c == label) zy = z[c];
@@ -391,7 +438,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&sm->tmem_empty[b]);
+      if (lane == 0) {
+        mbar_arrive(&sm->tmem_empty[b]);
+        mbar_arrive(&sm->tail_empty[b]);
+      }
       epi_bar();
       if (et < s_valid) {
         const int s = et;
@@ -458,19 +508,29 @@ int tail_len(const Mlp& mlp) {
   return h1 + C * h1 + C;
 }
 
-template <int H1>
-cudaError_t launch_h1(const TcPlan& plan, const TcArgs& args, cudaStream_t s) {
+int tail_stride(const Mlp& mlp) { return (tail_len(mlp) + 3) / 4 * 4; }
+
+template <int H1, int CMAX>
+cudaError_t launch_hc(const TcPlan& plan, const TcArgs& args, cudaStream_t s) {
   static size_t configured = 0;
   if (plan.smem_bytes > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_fitness_tc<H1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_fitness_tc<H1, CMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)plan.smem_bytes);
     if (e != cudaSuccess) return e;
     configured = plan.smem_bytes;
   }
   const int tiles = args.m_tiles * args.n_tiles;
   const int grid = tiles < plan.num_sms ? tiles : plan.num_sms;
-  k_fitness_tc<H1><<<grid, kThreads, plan.smem_bytes, s>>>(plan.tmap_x, plan.tmap_w, args);
+  k_fitness_tc<H1, CMAX><<<grid, kThreads, plan.smem_bytes, s>>>(plan.tmap_x, plan.tmap_w, args);
   return cudaPeekAtLastError();
+}
+
+// The class count picks the smallest register array that holds the logits.
+template <int H1>
+cudaError_t launch_h1(const TcPlan& plan, const TcArgs& args, cudaStream_t s) {
+  if (args.C <= 4) return launch_hc<H1, 4>(plan, args, s);
+  if (args.C <= 16) return launch_hc<H1, 16>(plan, args, s);
+  return launch_hc<H1, 32>(plan, args, s);
 }
 
 }  // namespace
@@ -479,7 +539,7 @@ bool tc_supported(const int32_t* widths, int n_layers) {
   if (n_layers != 2) return false;
   const int h1 = widths[1];
   if (widths[0] % 8 != 0) return false;
-  if (!(h1 == 16 || h1 == 32 || h1 == 64 || h1 == 128 || h1 == 256)) return false;
+  if (!(h1 == 16 || h1 == 32 || h1 == 64 || h1 == 128)) return false;
   return widths[2] >= 2 && widths[2] <= 32;
 }
 
@@ -506,7 +566,8 @@ mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const __nv_bfloat16* op, int6
   plan.sparks_per_tile = sparks_per_tile(h1);
   plan.n_tile = plan.sparks_per_tile * h1;
   const size_t a_bytes = (size_t)kBM * kBK * 2, b_bytes = (size_t)plan.n_tile * kBK * 2;
-  const size_t tail_bytes = sizeof(float) * ((size_t)plan.sparks_per_tile * tail_len(mlp) + 4 * plan.sparks_per_tile + 4);
+  const size_t tail_bytes =
+      sizeof(float) * (2 * (size_t)plan.sparks_per_tile * tail_stride(mlp) + 4 * plan.sparks_per_tile + 4);
   const size_t fixed = 1024 + tail_bytes + sizeof(Smem) + 64;
   const size_t limit = (size_t)prop.sharedMemPerBlockOptin;
   int stages = kMaxStages;
@@ -541,6 +602,7 @@ int launch_fitness_tc(const TcPlan& plan, const Mlp& mlp, int64_t first, const f
   a.k_blocks = (mlp.widths[0] + kBK - 1) / kBK;
   a.stages = plan.stages;
   a.tail_len = tail_len(mlp);
+  a.tail_stride = tail_stride(mlp);
   a.N = mlp.N;
   a.ld = ld;
   a.tail_off = mlp.b_off[0];
@@ -556,7 +618,6 @@ int launch_fitness_tc(const TcPlan& plan, const Mlp& mlp, int64_t first, const f
     case 32: e = launch_h1<32>(plan, a, s); break;
     case 64: e = launch_h1<64>(plan, a, s); break;
     case 128: e = launch_h1<128>(plan, a, s); break;
-    case 256: e = launch_h1<256>(plan, a, s); break;
     default: return -1;
   }
   return e == cudaSuccess ? 1 : -1;

@@ -21,6 +21,7 @@ namespace mgfwa {
 namespace {
 
 constexpr int kThreads = 128;
+constexpr int kGuideUnroll = 8;
 
 // Reading of the population-based random mapping: a coordinate outside
 // [lb, ub] is redrawn uniformly in the firework's amplitude box clipped to
@@ -58,18 +59,12 @@ __global__ void __launch_bounds__(kThreads) k_init(Problem p, float* __restrict_
   *reinterpret_cast<float4*>(fw_x + (int64_t)i * p.Dp + d0) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
-__global__ void __launch_bounds__(kThreads) k_explode(Problem p, uint32_t gen, const float* __restrict__ fw_x,
-                                                      const float* __restrict__ fw_amp,
-                                                      float* __restrict__ sparks,
-                                                      __nv_bfloat16* __restrict__ op, int64_t w1_elems) {
-  const int row = blockIdx.y;  // i * lam + j
-  const int i = row / p.lam;
-  const int64_t c4 = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-  const int64_t d0 = c4 * 4;
-  if (d0 >= p.Dp) return;
-  const float amp = fw_amp[i];
-  const float4 x4 = *reinterpret_cast<const float4*>(fw_x + (int64_t)i * p.Dp + d0);
-  const uint4 r = philox4x32_10(make_uint4((uint32_t)c4, (uint32_t)row, gen, kExplode), p.key0, p.key1);
+// Coordinates [d0, d0 + 4) of explosion spark `row` (one Philox block).
+__device__ __forceinline__ void explode4(const Problem& p, uint32_t gen, int row, uint32_t c4, const float4 x4,
+                                         float amp, float* __restrict__ srow, __nv_bfloat16* __restrict__ oprow,
+                                         int64_t w1_elems) {
+  const int64_t d0 = (int64_t)c4 * 4;
+  const uint4 r = philox4x32_10(make_uint4(c4, (uint32_t)row, gen, kExplode), p.key0, p.key1);
   float v[4];
   bool out_of_bounds = false;
 #pragma unroll
@@ -79,7 +74,7 @@ __global__ void __launch_bounds__(kThreads) k_explode(Problem p, uint32_t gen, c
     out_of_bounds |= (d0 + l < p.D) && (v[l] < p.lb || v[l] > p.ub);
   }
   if (out_of_bounds) {
-    const uint4 r2 = philox4x32_10(make_uint4((uint32_t)c4, (uint32_t)row, gen, kMap), p.key0, p.key1);
+    const uint4 r2 = philox4x32_10(make_uint4(c4, (uint32_t)row, gen, kMap), p.key0, p.key1);
 #pragma unroll
     for (int l = 0; l < 4; ++l)
       if (v[l] < p.lb || v[l] > p.ub) v[l] = map_coord(lane_of(x4, l), amp, p.lb, p.ub, u24(lane_of(r2, l)));
@@ -87,8 +82,31 @@ __global__ void __launch_bounds__(kThreads) k_explode(Problem p, uint32_t gen, c
 #pragma unroll
   for (int l = 0; l < 4; ++l)
     if (d0 + l >= p.D) v[l] = 0.0f;
-  *reinterpret_cast<float4*>(sparks + (int64_t)row * p.Dp + d0) = make_float4(v[0], v[1], v[2], v[3]);
-  if (op != nullptr && d0 < w1_elems) store_bf16x4(op + (int64_t)row * w1_elems + d0, v[0], v[1], v[2], v[3]);
+  *reinterpret_cast<float4*>(srow + d0) = make_float4(v[0], v[1], v[2], v[3]);
+  if (oprow != nullptr && d0 < w1_elems) store_bf16x4(oprow + d0, v[0], v[1], v[2], v[3]);
+}
+
+// One block covers 2 * kThreads Philox blocks (8 * kThreads coordinates) of
+// one spark row; each thread does two, kThreads blocks apart, so a warp's
+// stores stay contiguous.
+__global__ void __launch_bounds__(kThreads) k_explode(Problem p, uint32_t gen, const float* __restrict__ fw_x,
+                                                      const float* __restrict__ fw_amp,
+                                                      float* __restrict__ sparks,
+                                                      __nv_bfloat16* __restrict__ op, int64_t w1_elems) {
+  const int row = blockIdx.y;  // i * lam + j
+  const int i = row / p.lam;
+  const float amp = fw_amp[i];
+  const float* xrow = fw_x + (int64_t)i * p.Dp;
+  float* srow = sparks + (int64_t)row * p.Dp;
+  __nv_bfloat16* oprow = op != nullptr ? op + (int64_t)row * w1_elems : nullptr;
+  const uint32_t n4 = (uint32_t)(p.Dp / 4);
+  const uint32_t c4a = blockIdx.x * (2 * kThreads) + threadIdx.x;
+  const uint32_t c4b = c4a + kThreads;
+  float4 xa = make_float4(0.f, 0.f, 0.f, 0.f), xb = xa;
+  if (c4a < n4) xa = *reinterpret_cast<const float4*>(xrow + (int64_t)c4a * 4);
+  if (c4b < n4) xb = *reinterpret_cast<const float4*>(xrow + (int64_t)c4b * 4);
+  if (c4a < n4) explode4(p, gen, row, c4a, xa, amp, srow, oprow, w1_elems);
+  if (c4b < n4) explode4(p, gen, row, c4b, xb, amp, srow, oprow, w1_elems);
 }
 
 // Multi-guiding sparks, reading: group q of firework i has ranked index
@@ -111,15 +129,39 @@ __global__ void __launch_bounds__(kThreads) k_guide(Problem p, uint32_t gen, con
   const int32_t* t = top + (int64_t)gq * k;
   const int32_t* b = bottom + (int64_t)gq * k;
   const float* fs = sparks + (int64_t)i * p.lam * p.Dp + d0;
-  float4 st = *reinterpret_cast<const float4*>(fs + (int64_t)t[0] * p.Dp);
-  float4 sb = *reinterpret_cast<const float4*>(fs + (int64_t)b[0] * p.Dp);
-  for (int r = 1; r < k; ++r) {
-    const float4 a = *reinterpret_cast<const float4*>(fs + (int64_t)t[r] * p.Dp);
-    const float4 c = *reinterpret_cast<const float4*>(fs + (int64_t)b[r] * p.Dp);
-    st.x = __fadd_rn(st.x, a.x); st.y = __fadd_rn(st.y, a.y);
-    st.z = __fadd_rn(st.z, a.z); st.w = __fadd_rn(st.w, a.w);
-    sb.x = __fadd_rn(sb.x, c.x); sb.y = __fadd_rn(sb.y, c.y);
-    sb.z = __fadd_rn(sb.z, c.z); sb.w = __fadd_rn(sb.w, c.w);
+  float4 st, sb;
+  if (k <= kGuideUnroll) {
+    // all 2k loads in flight before the ordered sums
+    float4 a[kGuideUnroll], c[kGuideUnroll];
+#pragma unroll
+    for (int r = 0; r < kGuideUnroll; ++r) {
+      if (r < k) {
+        a[r] = *reinterpret_cast<const float4*>(fs + (int64_t)t[r] * p.Dp);
+        c[r] = *reinterpret_cast<const float4*>(fs + (int64_t)b[r] * p.Dp);
+      }
+    }
+    st = a[0];
+    sb = c[0];
+#pragma unroll
+    for (int r = 1; r < kGuideUnroll; ++r) {
+      if (r < k) {
+        st.x = __fadd_rn(st.x, a[r].x); st.y = __fadd_rn(st.y, a[r].y);
+        st.z = __fadd_rn(st.z, a[r].z); st.w = __fadd_rn(st.w, a[r].w);
+        sb.x = __fadd_rn(sb.x, c[r].x); sb.y = __fadd_rn(sb.y, c[r].y);
+        sb.z = __fadd_rn(sb.z, c[r].z); sb.w = __fadd_rn(sb.w, c[r].w);
+      }
+    }
+  } else {
+    st = *reinterpret_cast<const float4*>(fs + (int64_t)t[0] * p.Dp);
+    sb = *reinterpret_cast<const float4*>(fs + (int64_t)b[0] * p.Dp);
+    for (int r = 1; r < k; ++r) {
+      const float4 a = *reinterpret_cast<const float4*>(fs + (int64_t)t[r] * p.Dp);
+      const float4 c = *reinterpret_cast<const float4*>(fs + (int64_t)b[r] * p.Dp);
+      st.x = __fadd_rn(st.x, a.x); st.y = __fadd_rn(st.y, a.y);
+      st.z = __fadd_rn(st.z, a.z); st.w = __fadd_rn(st.w, a.w);
+      sb.x = __fadd_rn(sb.x, c.x); sb.y = __fadd_rn(sb.y, c.y);
+      sb.z = __fadd_rn(sb.z, c.z); sb.w = __fadd_rn(sb.w, c.w);
+    }
   }
   const float amp = fw_amp[i];
   const float4 x4 = *reinterpret_cast<const float4*>(fw_x + (int64_t)i * p.Dp + d0);
@@ -171,7 +213,7 @@ int launch_init(const Problem& p, float* fw_x, float* fw_amp, cudaStream_t s) {
 
 int launch_explode(const Problem& p, uint32_t gen, const float* fw_x, const float* fw_amp, float* sparks,
                    __nv_bfloat16* op, int64_t w1_elems, cudaStream_t s) {
-  dim3 grid(blocks_for(p.Dp / 4), p.mu * p.lam);
+  dim3 grid((unsigned)((p.Dp / 4 + 2 * kThreads - 1) / (2 * kThreads)), p.mu * p.lam);
   k_explode<<<grid, kThreads, 0, s>>>(p, gen, fw_x, fw_amp, sparks, op, w1_elems);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }

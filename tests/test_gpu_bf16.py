@@ -44,7 +44,7 @@ def _rel(a, b):
     ((8, 16, 3), (0,), 300, 56),           # K = 8 < one K block (TMA zero fill), 16 sparks per tile
     ((64, 32, 7), (0,), 129, 24),          # ragged tail of one sample
     ((96, 128, 5), (1,), 1, 16),           # a single sample
-    ((32, 256, 4), (1,), 260, 12),         # one spark per tile, 256 hidden units
+    ((48, 128, 4), (1,), 260, 12),         # two sparks per tile, K = 48 inside one K block
 ])
 def test_bf16_fitness_against_oracle(pkg, widths, acts, N, count):
     w = W.scaled(W.MLP_784_64_10, widths=widths, acts=acts, n_samples=N, n_fireworks=2,
