@@ -512,13 +512,8 @@ int tail_stride(const Mlp& mlp) { return (tail_len(mlp) + 3) / 4 * 4; }
 
 template <int H1, int CMAX>
 cudaError_t launch_hc(const TcPlan& plan, const TcArgs& args, cudaStream_t s) {
-  static size_t configured = 0;
-  if (plan.smem_bytes > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_fitness_tc<H1, CMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)plan.smem_bytes);
-    if (e != cudaSuccess) return e;
-    configured = plan.smem_bytes;
-  }
+  cudaError_t e = ensure_smem_limit(k_fitness_tc<H1, CMAX>, plan.smem_bytes);
+  if (e != cudaSuccess) return e;
   const int tiles = args.m_tiles * args.n_tiles;
   const int grid = tiles < plan.num_sms ? tiles : plan.num_sms;
   k_fitness_tc<H1, CMAX><<<grid, kThreads, plan.smem_bytes, s>>>(plan.tmap_x, plan.tmap_w, args);

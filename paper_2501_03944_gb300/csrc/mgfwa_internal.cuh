@@ -37,6 +37,21 @@ struct Mlp {
 
 enum { kActTanh = 0, kActRelu = 1 };
 
+// Raise a kernel's dynamic shared-memory limit on the current device once
+// (the attribute is per device, so the cache is too).
+template <typename Kernel>
+inline cudaError_t ensure_smem_limit(Kernel k, size_t bytes) {
+  constexpr int kMaxDevices = 64;
+  static size_t configured[kMaxDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < kMaxDevices && bytes <= configured[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && dev >= 0 && dev < kMaxDevices) configured[dev] = bytes;
+  return e;
+}
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products
 // on words 0 and 2, xor/permute with words 1, 3 and the round key, key bumped
