@@ -254,7 +254,7 @@ int launch_fitness_simt_main(const Mlp& mlp, const float* rows, int64_t ld, int3
                              cudaStream_t s) {
   if (count <= 0) return 0;
   const size_t smem = smem_for(mlp);
-  if (ensure_smem_limit(k_fitness_simt, smem) != cudaSuccess) return -1;
+  if (ensure_smem_limit<k_fitness_simt>(smem) != cudaSuccess) return -1;
   const int mtiles = (int)((mlp.N + kMT - 1) / kMT);
   dim3 grid(mtiles, count);
   k_fitness_simt<<<grid, kThreads, smem, s>>>(mlp, rows, ld, count, partial);
@@ -271,7 +271,7 @@ int launch_fitness_f64(const Mlp& mlp, const float* x, double* ce64, double* out
   int wmax = 0;
   for (int l = 0; l <= mlp.n_layers; ++l) wmax = wmax > mlp.widths[l] ? wmax : mlp.widths[l];
   const size_t smem = 2 * sizeof(double) * (size_t)wmax;
-  if (smem > 48 * 1024 && ensure_smem_limit(k_fitness_f64, smem) != cudaSuccess) return -1;
+  if (smem > 48 * 1024 && ensure_smem_limit<k_fitness_f64>(smem) != cudaSuccess) return -1;
   k_fitness_f64<<<(unsigned)mlp.N, 256, smem, s>>>(mlp, x, wmax, ce64);
   if (cudaPeekAtLastError() != cudaSuccess) return -1;
   k_reduce_f64<<<1, 256, 0, s>>>(ce64, nullptr, mlp.N, 1.0 / (double)mlp.N, out);

@@ -204,7 +204,7 @@ struct TcArgs {
   uint32_t* status;
 };
 
-template <int H1, int CMAX>
+template <int H1, int CMAX, bool EXACT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_fitness_tc(const __grid_constant__ CUtensorMap tmap_x, const __grid_constant__ CUtensorMap tmap_w, TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -222,6 +222,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tiles = a.m_tiles * a.n_tiles;
+  const int C = EXACT ? CMAX : a.C;  // class count (a compile-time constant when EXACT)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < a.stages; ++s) {
@@ -379,10 +380,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int s = half; s < s_valid; s += 2) {
         const float* b1 = tail + (size_t)s * a.tail_stride;
         const float* W2 = b1 + H1;
-        const float* b2 = W2 + a.C * H1;
+        const float* b2 = W2 + C * H1;
         float z[CMAX];
 #pragma unroll
-        for (int c = 0; c < CMAX; ++c) z[c] = c < a.C ? b2[c] : 0.0f;
+        for (int c = 0; c < CMAX; ++c) z[c] = c < C ? b2[c] : 0.0f;
         const uint32_t col0 = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 256 + s * H1);
 #pragma unroll
         for (int j0 = 0; j0 < H1; j0 += 16) {
@@ -405,7 +406,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int q = 0; q < kChunk / 4; ++q) {
 #pragma unroll
             for (int c = 0; c < CMAX; ++c) {
-              if (c < a.C) {
+              if (c < C) {
                 const float4 wv = reinterpret_cast<const float4*>(W2 + c * H1 + j0)[q];
                 z[c] = fmaf(wv.x, h[4 * q + 0], z[c]);
                 z[c] = fmaf(wv.y, h[4 * q + 1], z[c]);
@@ -420,12 +421,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           float zmax = z[0];
 #pragma unroll
           for (int c = 1; c < CMAX; ++c)
-            if (c < a.C) zmax = fmaxf(zmax, z[c]);
+            if (c < C) zmax = fmaxf(zmax, z[c]);
           float se = 0.0f;
           float zy = 0.0f;
 #pragma unroll
           for (int c = 0; c < CMAX; ++c) {
-            if (c < a.C) {
+            if (c < C) {
               se += expf(z[c] - zmax);
               if (c == label) zy = z[c];
             }
@@ -510,22 +511,25 @@ int tail_len(const Mlp& mlp) {
 
 int tail_stride(const Mlp& mlp) { return (tail_len(mlp) + 3) / 4 * 4; }
 
-template <int H1, int CMAX>
+template <int H1, int CMAX, bool EXACT>
 cudaError_t launch_hc(const TcPlan& plan, const TcArgs& args, cudaStream_t s) {
-  cudaError_t e = ensure_smem_limit(k_fitness_tc<H1, CMAX>, plan.smem_bytes);
+  cudaError_t e = ensure_smem_limit<k_fitness_tc<H1, CMAX, EXACT>>(plan.smem_bytes);
   if (e != cudaSuccess) return e;
   const int tiles = args.m_tiles * args.n_tiles;
   const int grid = tiles < plan.num_sms ? tiles : plan.num_sms;
-  k_fitness_tc<H1, CMAX><<<grid, kThreads, plan.smem_bytes, s>>>(plan.tmap_x, plan.tmap_w, args);
+  k_fitness_tc<H1, CMAX, EXACT><<<grid, kThreads, plan.smem_bytes, s>>>(plan.tmap_x, plan.tmap_w, args);
   return cudaPeekAtLastError();
 }
 
-// The class count picks the smallest register array that holds the logits.
+// The class count picks the register array for the logits: exact for the
+// common counts (no per-class predicates), else the smallest that holds C.
 template <int H1>
 cudaError_t launch_h1(const TcPlan& plan, const TcArgs& args, cudaStream_t s) {
-  if (args.C <= 4) return launch_hc<H1, 4>(plan, args, s);
-  if (args.C <= 16) return launch_hc<H1, 16>(plan, args, s);
-  return launch_hc<H1, 32>(plan, args, s);
+  if (args.C == 10) return launch_hc<H1, 10, true>(plan, args, s);
+  if (args.C == 3) return launch_hc<H1, 3, true>(plan, args, s);
+  if (args.C <= 4) return launch_hc<H1, 4, false>(plan, args, s);
+  if (args.C <= 16) return launch_hc<H1, 16, false>(plan, args, s);
+  return launch_hc<H1, 32, false>(plan, args, s);
 }
 
 }  // namespace

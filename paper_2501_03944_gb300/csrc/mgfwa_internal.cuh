@@ -37,17 +37,19 @@ struct Mlp {
 
 enum { kActTanh = 0, kActRelu = 1 };
 
-// Raise a kernel's dynamic shared-memory limit on the current device once
-// (the attribute is per device, so the cache is too).
-template <typename Kernel>
-inline cudaError_t ensure_smem_limit(Kernel k, size_t bytes) {
+// Raise kernel K's dynamic shared-memory limit on the current device once.
+// The attribute belongs to one kernel on one device, so the cache is per
+// kernel (one template instance per kernel, not per kernel type) and per
+// device.
+template <auto K>
+inline cudaError_t ensure_smem_limit(size_t bytes) {
   constexpr int kMaxDevices = 64;
   static size_t configured[kMaxDevices] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 0 && dev < kMaxDevices && bytes <= configured[dev]) return cudaSuccess;
-  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess && dev >= 0 && dev < kMaxDevices) configured[dev] = bytes;
   return e;
 }
@@ -91,6 +93,9 @@ __device__ __forceinline__ bool before(float fa, int ia, float fb, int ib) {
   const float a = rank_key(fa), b = rank_key(fb);
   return a < b || (a == b && ia < ib);
 }
+
+// Sets the calling thread's error text (what mgfwa_last_error(NULL) returns).
+void set_thread_error(const char* msg);
 
 // ---------------------------------------------------------------------------
 // Launchers (each returns the number of kernels it enqueued, or -1 after a
