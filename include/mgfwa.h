@@ -138,8 +138,37 @@ MGFWA_API mgfwa_status mgfwa_get_info(const mgfwa_t* h, mgfwa_info* info);
 MGFWA_API void mgfwa_destroy(mgfwa_t* h);
 
 /* A one-line description of the handle's last error ("" if none).  With a
- * NULL handle: the last error of a failed mgfwa_create in this thread. */
+ * NULL handle: the last error of a failed mgfwa_create or
+ * mgfwa_evaluate_fp32_noalloc in this thread. */
 MGFWA_API const char* mgfwa_last_error(const mgfwa_t* h);
+
+/* FP32 fitness (mean MLP cross-entropy, the objective above) of `count`
+ * caller-owned spark rows, with NO device allocation.  The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc -- a
+ * process whose device memory is owned and budgeted by another framework's
+ * allocator, or a latency-critical loop where cudaMalloc/cudaFree may
+ * synchronise the whole device.
+ *  - X_dev [n_samples][widths[0]] FP32, y_dev [n_samples] int32 labels in
+ *    [0, C), rows_dev [count][ld] FP32 (ld >= D, ld % 4 == 0; X_dev and
+ *    rows_dev 16-byte aligned) are DEVICE pointers the caller owns; widths
+ *    and acts are host arrays as in mgfwa_objective (d_in % 8 == 0, hidden
+ *    widths <= 192, C in [2, 32]).  Labels are not checked on the device.
+ *  - fitness_dev [count] FP32 receives the results (device pointer).
+ *  - The work is enqueued on cuda_stream (a cudaStream_t, NULL = legacy
+ *    default stream); the call does not synchronise.
+ *  - Scratch is a fixed array inside the library's device image (1 MiB, held
+ *    by every GPU that loads the library until the process exits):
+ *    ceil(n_samples / 128) * count must be <= 262,144, else MGFWA_EINVAL.
+ *    The first call on each device looks up that array's device address
+ *    (cudaGetSymbolAddress), so make that first call before any stream
+ *    capture.  Calls share the array: calls that overlap on the GPU (other
+ *    streams, other threads) race and give wrong results; serialise them.
+ *  - Returns EINVAL on bad arguments (reason in mgfwa_last_error(NULL)),
+ *    ECUDA if a launch fails. */
+MGFWA_API mgfwa_status mgfwa_evaluate_fp32_noalloc(int32_t n_layers, const int32_t* widths, const int32_t* acts,
+                                                   int64_t n_samples, const float* X_dev, const int32_t* y_dev,
+                                                   const float* rows_dev, int64_t ld, int32_t count,
+                                                   float* fitness_dev, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -33,7 +33,7 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5:
 # Every symbol the headers declare (checked by the CPU test suite).
 EXPORTS = ("mgfwa_config_init", "mgfwa_create", "mgfwa_step", "mgfwa_run", "mgfwa_best", "mgfwa_evaluate",
            "mgfwa_get_info", "mgfwa_destroy", "mgfwa_last_error", "mgfwa_debug_phase", "mgfwa_debug_read",
-           "mgfwa_debug_write", "mgfwa_debug_profile", "mgfwa_debug_kernel_times")
+           "mgfwa_debug_write", "mgfwa_debug_profile", "mgfwa_debug_kernel_times", "mgfwa_evaluate_fp32_noalloc")
 N_KERNEL_GROUPS = 7
 KERNEL_GROUPS = ("explode", "fitness_explosion", "fitness_finish", "rank", "guide", "fitness_guiding", "select")
 
@@ -96,6 +96,8 @@ def load_library(path: Optional[str] = None):
     L.mgfwa_debug_write.argtypes = [vp, i32, vp, i64]
     L.mgfwa_debug_profile.argtypes = [vp, i32]
     L.mgfwa_debug_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    L.mgfwa_evaluate_fp32_noalloc.argtypes = [i32, i32p, i32p, i64, vp, vp, vp, i64, i32, vp, vp]
     for name in EXPORTS:
         if name not in ("mgfwa_destroy", "mgfwa_last_error"):
             getattr(L, name).restype = ctypes.c_int
@@ -178,6 +180,18 @@ def mgfwa_get_info(handle: int) -> mgfwa_info:
 
 def mgfwa_destroy(handle: int) -> None:
     load_library().mgfwa_destroy(handle)
+
+
+def mgfwa_evaluate_fp32_noalloc(widths, acts, n_samples: int, X_dev: int, y_dev: int, rows_dev: int, ld: int,
+                                count: int, fitness_dev: int, stream: int = 0) -> None:
+    """FP32 fitness of caller-owned device buffers (integer device addresses); allocates nothing."""
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    a = np.ascontiguousarray(acts if len(acts) else [0], dtype=np.int32)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    st = load_library().mgfwa_evaluate_fp32_noalloc(len(widths) - 1, w.ctypes.data_as(i32p), a.ctypes.data_as(i32p),
+                                                    n_samples, X_dev, y_dev, rows_dev, ld, count, fitness_dev,
+                                                    ctypes.c_void_p(stream or None))
+    _check(st)
 
 
 def mgfwa_debug_phase(handle: int, phase: int) -> int:

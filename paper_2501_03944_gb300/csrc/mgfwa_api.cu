@@ -19,6 +19,12 @@
 
 using namespace mgfwa;
 
+namespace {
+thread_local std::string g_create_error;
+}  // namespace
+
+void mgfwa::set_thread_error(const char* msg) { g_create_error = msg ? msg : ""; }
+
 struct mgfwa_handle {
   mgfwa_config cfg;
   Problem p;
@@ -65,8 +71,6 @@ struct mgfwa_handle {
 };
 
 namespace {
-
-thread_local std::string g_create_error;
 
 // MGFWA_TRACE=1 in the environment prints the steps of mgfwa_create to stderr.
 bool trace_on() {
