@@ -163,6 +163,28 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 lanes x 8 consecutive FP32 columns.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// d += a * b on two FP32 lanes at once (packed FP32 FMA).
+__device__ __forceinline__ void ffma2(float2& d, float ax, float ay, float bx, float by) {
+  asm("{\n\t.reg .b64 a, b, d;\n\t"
+      "mov.b64 a, {%2, %3};\n\t"
+      "mov.b64 b, {%4, %5};\n\t"
+      "mov.b64 d, {%0, %1};\n\t"
+      "fma.rn.f32x2 d, a, b, d;\n\t"
+      "mov.b64 {%0, %1}, d;\n\t}"
+      : "+f"(d.x), "+f"(d.y)
+      : "f"(ax), "f"(ay), "f"(bx), "f"(by));
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory"); }
@@ -381,41 +403,38 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float* b1 = tail + (size_t)s * a.tail_stride;
         const float* W2 = b1 + H1;
         const float* b2 = W2 + C * H1;
-        float z[CMAX];
+        // layer 2: two partial sums per class (even / odd hidden units) in one
+        // packed register, classes innermost so each step has C independent chains
+        float2 z2[CMAX];
 #pragma unroll
-        for (int c = 0; c < CMAX; ++c) z[c] = c < C ? b2[c] : 0.0f;
+        for (int c = 0; c < CMAX; ++c) z2[c] = make_float2(0.0f, 0.0f);
         const uint32_t col0 = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 256 + s * H1);
-#pragma unroll
-        for (int j0 = 0; j0 < H1; j0 += 16) {
-          constexpr int kChunk = 16;
-          float h[kChunk];
-#pragma unroll
-          for (int q = 0; q < kChunk; q += 16) tmem_ld16(col0 + (uint32_t)(j0 + q), h + q);
+#pragma unroll 1
+        for (int j0 = 0; j0 < H1; j0 += 8) {
+          float h[8];
+          tmem_ld8(col0 + (uint32_t)j0, h);
           tmem_wait_ld();
-          const float4* b14 = reinterpret_cast<const float4*>(b1 + j0);
+          const float4 bb0 = *reinterpret_cast<const float4*>(b1 + j0);
+          const float4 bb1 = *reinterpret_cast<const float4*>(b1 + j0 + 4);
+          h[0] = act_f(a.act, h[0] + bb0.x); h[1] = act_f(a.act, h[1] + bb0.y);
+          h[2] = act_f(a.act, h[2] + bb0.z); h[3] = act_f(a.act, h[3] + bb0.w);
+          h[4] = act_f(a.act, h[4] + bb1.x); h[5] = act_f(a.act, h[5] + bb1.y);
+          h[6] = act_f(a.act, h[6] + bb1.z); h[7] = act_f(a.act, h[7] + bb1.w);
 #pragma unroll
-          for (int q = 0; q < kChunk / 4; ++q) {
-            const float4 bb = b14[q];
-            h[4 * q + 0] = act_f(a.act, h[4 * q + 0] + bb.x);
-            h[4 * q + 1] = act_f(a.act, h[4 * q + 1] + bb.y);
-            h[4 * q + 2] = act_f(a.act, h[4 * q + 2] + bb.z);
-            h[4 * q + 3] = act_f(a.act, h[4 * q + 3] + bb.w);
-          }
-          // layer 2: classes innermost, so every step has C independent FMA chains
-#pragma unroll
-          for (int q = 0; q < kChunk / 4; ++q) {
-#pragma unroll
-            for (int c = 0; c < CMAX; ++c) {
-              if (c < C) {
-                const float4 wv = reinterpret_cast<const float4*>(W2 + c * H1 + j0)[q];
-                z[c] = fmaf(wv.x, h[4 * q + 0], z[c]);
-                z[c] = fmaf(wv.y, h[4 * q + 1], z[c]);
-                z[c] = fmaf(wv.z, h[4 * q + 2], z[c]);
-                z[c] = fmaf(wv.w, h[4 * q + 3], z[c]);
-              }
+          for (int c = 0; c < CMAX; ++c) {
+            if (c < C) {
+              const float4* w4 = reinterpret_cast<const float4*>(W2 + c * H1 + j0);
+              const float4 wa = w4[0], wb = w4[1];
+              ffma2(z2[c], wa.x, wa.y, h[0], h[1]);
+              ffma2(z2[c], wa.z, wa.w, h[2], h[3]);
+              ffma2(z2[c], wb.x, wb.y, h[4], h[5]);
+              ffma2(z2[c], wb.z, wb.w, h[6], h[7]);
             }
           }
         }
+        float z[CMAX];
+#pragma unroll
+        for (int c = 0; c < CMAX; ++c) z[c] = c < C ? b2[c] + (z2[c].x + z2[c].y) : 0.0f;
         float ce = 0.0f;
         if (valid_row) {
           float zmax = z[0];
