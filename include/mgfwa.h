@@ -52,7 +52,7 @@ typedef enum {
 
 typedef enum {
   MGFWA_FP32 = 0, /* FP32 CUDA-core fitness */
-  MGFWA_BF16 = 1, /* BF16 tensor-core first layer (tcgen05), FP32 accumulate */
+  MGFWA_BF16 = 1, /* tensor cores (tcgen05): BF16 first layer, TF32 second layer, FP32 accumulate */
   MGFWA_FP8 = 2   /* reserved: FP8 E4M3 first layer with per-spark scales */
 } mgfwa_precision;
 
@@ -79,7 +79,7 @@ typedef struct {
   int32_t kind;          /* MGFWA_OBJ_MLP_CE or MGFWA_OBJ_SPHERE */
   int32_t n_layers;      /* linear layers, 2 or 3 (MLP) */
   const int32_t* widths; /* n_layers + 1 widths d_in, h1, [h2,] C: d_in % 8 == 0, hidden widths <= 192,
-                            C in [2, 32]; the BF16 path needs 2 layers and h1 in {16, 32, 64, 128} */
+                            C in [2, 32]; the BF16 path needs 2 layers and h1 in {32, 64, 128} */
   const int32_t* acts;   /* n_layers - 1 hidden activations (MGFWA_ACT_*) */
   int64_t n_samples;     /* N >= 1 */
   const float* X;        /* [N][d_in] row-major FP32 */

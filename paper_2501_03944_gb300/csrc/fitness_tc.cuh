@@ -11,7 +11,8 @@ namespace mgfwa {
 struct TcPlan {
   bool ready = false;
   CUtensorMap tmap_x;   // X  [N][d_in] BF16, box 128 x 64, 128B swizzle
-  CUtensorMap tmap_w;   // op [P*h1][d_in] BF16, box h_tile x 64, 128B swizzle
+  CUtensorMap tmap_w;   // op [P*h1][d_in] BF16, box n_tile x 64, 128B swizzle
+  CUtensorMap tmap_w2;  // W2 inside the FP32 spark rows [P][C][h1], box 32 x C x 1, 128B swizzle
   int num_sms = 0;
   int sparks_per_tile = 0;  // whole sparks per N-tile
   int n_tile = 0;           // accumulator columns per tile (sparks_per_tile * h1)
@@ -20,18 +21,20 @@ struct TcPlan {
 };
 
 // True if the tensor-core path handles this network: two linear layers,
-// d_in % 8 == 0, first hidden width 16, 32, 64 or 128, 2..32 classes.
+// d_in % 8 == 0, first hidden width 32, 64 or 128, 2..32 classes.
 bool tc_supported(const int32_t* widths, int n_layers);
 
-// Encode the tensor maps over the handle's X (BF16) and operand buffers.
-mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const __nv_bfloat16* op, int64_t max_rows);
+// Encode the tensor maps over the handle's X (BF16), first-layer operand
+// (BF16) and FP32 spark rows (`sparks`, row stride `ld`, `max_rows` rows).
+mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const __nv_bfloat16* op, const float* sparks, int64_t ld,
+                     int64_t max_rows);
 const char* tc_last_error();
 void tc_release(TcPlan& plan);
 
-// Fitness of `count` sparks whose operand rows start at spark `first`:
-// per-(m-tile, spark) partial cross-entropy sums into partial[mtiles][count].
-// `rows` are the sparks' FP32 rows (stride ld) for the layers after the
-// first.  A device-side wait that gives up sets *status and returns.
+// Fitness of `count` sparks starting at spark row `first` of the planned
+// buffers: per-(m-tile, spark) partial cross-entropy sums into
+// partial[mtiles][count].  `rows` points at spark `first`'s FP32 row (stride
+// ld).  A device-side wait that gives up sets *status and returns.
 int launch_fitness_tc(const TcPlan& plan, const Mlp& mlp, int64_t first, const float* rows, int64_t ld,
                       int32_t count, float* partial, uint32_t* status, cudaStream_t s);
 

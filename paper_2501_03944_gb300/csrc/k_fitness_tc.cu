@@ -2,27 +2,39 @@
 // "parallel evaluate all the fitness of the sparks"), written for sm_103a
 // with tcgen05 MMAs, TMEM accumulators and TMA loads.
 //
-// The first layer of every spark's network is one dense GEMM of the shared
-// batch X [N x d_in] against all sparks' stacked first-layer weights
+// Layer 1 of every spark's network is one dense GEMM of the shared batch
+// X [N x d_in] against all sparks' stacked first-layer weights
 // [count*h1 x d_in] (BF16 operands, FP32 accumulation).  A tile is 128
-// samples x (S whole sparks x h1 hidden units), so that the epilogue owns
-// complete hidden vectors: it adds b1, applies the activation, runs the
-// small second layer on CUDA cores from shared memory, and reduces the
+// samples x S whole sparks (S*h1 accumulator columns), so that the tile owns
+// complete hidden vectors.  Layer 2 also runs on the tensor cores: the
+// epilogue adds b1 and applies the activation in place in TMEM, then one
+// TF32 MMA per 8 hidden units multiplies that TMEM operand (A) by the
+// spark's W2 (B, TMA-loaded from the FP32 spark row) into S*N2 logit
+// columns.  The epilogue then reads only the logits, adds b2 and reduces the
 // per-sample cross-entropy into one partial sum per (sample tile, spark).
 // Nothing of the hidden layer is written to memory.
 //
+// The (b1, b2, W2) tail of a tile sits in one of three shared buffers, so the
+// producer can stage tile t+1 while layer 2 of tile t-1 still reads W2.
+//
+// TMEM (512 columns) holds two halves of 256 columns; half b carries the
+// layer-1 accumulator of tile b (S*h1 columns) and, beside it, that tile's
+// logits (S*N2 columns): S = floor(256 / (h1 + N2)).
+//
 // One persistent CTA per SM; warp roles:
-//   warp 0  TMA producer: per tile, a bulk copy of the S sparks' (b1, W2,
-//           b2) blocks into one of two tail buffers, then the X tile
-//           (128 x 64) and W tile (S*h1 x 64) of every K block into a ring
-//           of shared-memory stages (128B swizzle);
-//   warp 1  TMEM allocator and single-thread MMA issuer (M=128, N=S*h1,
-//           K=16 per instruction) into one of two TMEM accumulators;
+//   warp 0  TMA producer: per tile, b1 and b2 of the S sparks (bulk copies)
+//           and their W2 (3-D tiled TMA, 128B swizzle) into one of two tail
+//           buffers; then the X tile (128 x 64) and W1 tile (S*h1 x 64) of
+//           every K block into a ring of shared-memory stages;
+//   warp 1  TMEM allocator and single-thread MMA issuer: layer 1 of tile t
+//           (M=128, N=S*h1, K=16, kind::f16), then layer 2 of tile t-1
+//           (M=128, N=N2, K=8, kind::tf32, A from TMEM);
 //   warps 2..9  epilogue, two warps per TMEM lane quadrant, each taking
-//           half of the tile's sparks.
+//           every other spark of the tile.
 // Every mbarrier wait is bounded: on timeout the CTA raises a flag in
 // shared memory and a bit in the status word, every role leaves its loop,
-// and the CTA frees its TMEM and returns.
+// and the CTA waits (bounded) for its own copies and MMAs, frees its TMEM
+// and returns.
 #include <cuda.h>
 
 #include <cstdio>
@@ -38,19 +50,25 @@ namespace {
 constexpr int kBM = 128;         // samples per tile
 constexpr int kBK = 64;          // K elements per stage (128 bytes of BF16: one swizzle row)
 constexpr int kUmmaK = 16;       // K per tcgen05.mma kind::f16
+constexpr int kUmmaK2 = 8;       // K per tcgen05.mma kind::tf32
+constexpr int kAtomK2 = 32;      // FP32 elements per 128-byte swizzle row of W2
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kMaxStages = 6;
-constexpr int kTmemCols = 512;   // two accumulators at columns 0 and 256
+constexpr int kTmemCols = 512;   // two halves of 256 columns
+constexpr int kTailBufs = 3;     // (b1, b2, W2) buffers: the producer runs a tile ahead of layer 2
 constexpr uint64_t kWaitBudget = 1ull << 32;  // clock64 ticks before a wait gives up (~2 s)
 
 struct Smem {
   uint64_t full[kMaxStages];
   uint64_t empty[kMaxStages];
-  uint64_t tmem_full[2];
-  uint64_t tmem_empty[2];
-  uint64_t tail_full[2];
-  uint64_t tail_empty[2];
+  uint64_t tmem_full[2];   // layer 1 of the half's tile is complete
+  uint64_t tmem_empty[2];  // layer 2 of the half's tile consumed its TMEM operand
+  uint64_t a2_full[2];     // the epilogue wrote act(h + b1) into TMEM
+  uint64_t l2_full[2];     // the half's logits are complete
+  uint64_t l2_empty[2];    // the epilogue read the half's logits
+  uint64_t tail_full[kTailBufs];
+  uint64_t tail_empty[kTailBufs];
   uint64_t mma_done;
   uint32_t tmem_base;
   volatile int abort_flag;
@@ -100,11 +118,30 @@ __device__ __forceinline__ bool mbar_wait(Smem* sm, uint64_t* bar, uint32_t pari
   return true;
 }
 
+// Bounded wait used while draining (ignores the abort flag).
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity, uint32_t* status) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if ((uint64_t)(clock64() - t0) > kWaitBudget) {
+      atomicOr(status, 16u);
+      return;
+    }
+  }
+}
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
           smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -131,9 +168,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return d;
 }
 
-// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major.
-__host__ __device__ constexpr uint32_t instr_desc(int m, int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+// Instruction descriptors: D FP32; A and B K-major; kind::f16 with BF16
+// inputs (format 1), kind::tf32 with TF32 inputs (format 2).
+__host__ __device__ constexpr uint32_t instr_desc(int m, int n, uint32_t ab_format) {
+  return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
@@ -145,12 +184,32 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
       : "memory");
 }
 
+// D (TMEM) (+)= A (TMEM) x B (shared memory), TF32 inputs.
+__device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
 }
 
-// 32 lanes x 16 consecutive FP32 columns.
+// 32 lanes x 8 / 16 consecutive 32-bit columns.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   uint32_t r[16];
   asm volatile(
@@ -163,29 +222,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// 32 lanes x 8 consecutive FP32 columns.
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
-  uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// d += a * b on two FP32 lanes at once (packed FP32 FMA).
-__device__ __forceinline__ void ffma2(float2& d, float ax, float ay, float bx, float by) {
-  asm("{\n\t.reg .b64 a, b, d;\n\t"
-      "mov.b64 a, {%2, %3};\n\t"
-      "mov.b64 b, {%4, %5};\n\t"
-      "mov.b64 d, {%0, %1};\n\t"
-      "fma.rn.f32x2 d, a, b, d;\n\t"
-      "mov.b64 {%0, %1}, d;\n\t}"
-      : "+f"(d.x), "+f"(d.y)
-      : "f"(ax), "f"(ay), "f"(bx), "f"(by));
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+               "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+               "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+               : "memory");
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory"); }
 
@@ -207,30 +253,33 @@ __device__ __forceinline__ bool epi_bar_any(bool flag) {
 __device__ __forceinline__ float act_f(int a, float v) { return a == kActTanh ? tanhf(v) : fmaxf(v, 0.0f); }
 
 struct TcArgs {
-  int32_t count;       // sparks in this launch
-  int32_t first_row;   // first operand row (spark * h1) of the launch in the operand tensor map
+  int32_t count;        // sparks in this launch
+  int32_t first_spark;  // first spark row of the launch (operand and W2 tensor maps)
   int32_t m_tiles, n_tiles;
   int32_t k_blocks;
   int32_t stages;
-  int32_t S;           // sparks per tile
-  int32_t tail_len;    // floats of (b1, W2, b2) per spark
-  int32_t tail_stride; // tail_len rounded up to 4 floats (16 bytes)
-  int64_t N;
-  int64_t ld;          // FP32 row stride of the sparks
-  int64_t tail_off;    // offset of b1 in a spark row
-  int32_t C;
+  int32_t S;            // sparks per tile
+  int32_t C;            // classes (<= N2)
   int32_t act;
-  const float* rows;   // FP32 spark rows of this launch
+  int32_t c_pad;        // C rounded up to 4 (floats of b2 copied)
+  int64_t N;
+  int64_t ld;           // FP32 row stride of the sparks
+  int64_t b1_off, b2_off;
+  const float* rows;    // FP32 spark rows of this launch
   const int32_t* y;
-  float* partial;      // [m_tiles][count]
+  float* partial;       // [m_tiles][count]
   uint32_t* status;
 };
 
-template <int H1, int CMAX, bool EXACT>
+template <int H1, int N2>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_fitness_tc(const __grid_constant__ CUtensorMap tmap_x, const __grid_constant__ CUtensorMap tmap_w, TcArgs a) {
+    k_fitness_tc(const __grid_constant__ CUtensorMap tmap_x, const __grid_constant__ CUtensorMap tmap_w,
+                 const __grid_constant__ CUtensorMap tmap_w2, TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  // 1024-byte alignment for the swizzled stages
+  constexpr int kAtoms = H1 / kAtomK2;               // W2 K-atoms per spark
+  constexpr uint32_t kAtomBytes = N2 * 128;          // one W2 K-atom: N2 rows x 128 B
+  constexpr uint32_t kW2Bytes = kAtoms * kAtomBytes; // W2 tile of one spark
+  constexpr int kTailFloats = H1 + 32;               // b1 then b2 (C <= 32)
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int S = a.S;
   const int n_tile = S * H1;
@@ -238,13 +287,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t b_bytes = (uint32_t)n_tile * kBK * 2;
   uint8_t* stage_a = base;
   uint8_t* stage_b = base + (size_t)a.stages * a_bytes;
-  float* tails = reinterpret_cast<float*>(stage_b + (size_t)a.stages * b_bytes);  // [2][S][tail_stride]
-  float* red = tails + 2 * (size_t)S * a.tail_stride;  // [S][4]
+  uint8_t* w2s = stage_b + (size_t)a.stages * b_bytes;                           // [kTailBufs][S][kW2Bytes]
+  float* tails = reinterpret_cast<float*>(w2s + kTailBufs * (size_t)S * kW2Bytes); // [kTailBufs][S][kTailFloats]
+  float* red = tails + kTailBufs * (size_t)S * kTailFloats;                      // [S][4]
   Smem* sm = reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(red + 4 * S) + 15) & ~uintptr_t(15));
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tiles = a.m_tiles * a.n_tiles;
-  const int C = EXACT ? CMAX : a.C;  // class count (a compile-time constant when EXACT)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < a.stages; ++s) {
@@ -253,7 +302,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sm->tmem_full[b], 1);
-      mbar_init(&sm->tmem_empty[b], kEpiWarps);
+      mbar_init(&sm->tmem_empty[b], 1);
+      mbar_init(&sm->a2_full[b], kEpiWarps);
+      mbar_init(&sm->l2_full[b], 1);
+      mbar_init(&sm->l2_empty[b], kEpiWarps);
+    }
+    for (int b = 0; b < kTailBufs; ++b) {
       mbar_init(&sm->tail_full[b], 1);
       mbar_init(&sm->tail_empty[b], kEpiWarps);
     }
@@ -279,23 +333,29 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t it = 0;
       bool ok = true;
       int local = 0;
-      const uint32_t tail_bytes = (uint32_t)a.tail_stride * 4u;
+      const uint32_t tail_bytes = (uint32_t)(H1 + a.c_pad) * 4u + (uint32_t)kAtoms * (uint32_t)a.C * 128u;
       for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++local) {
         const int mt = t % a.m_tiles, nt = t / a.m_tiles;
         const int row_x = mt * kBM;
-        const int row_w = a.first_row + nt * n_tile;
+        const int row_w = (a.first_spark + nt * S) * H1;
         {
-          // (b1, W2, b2) of the tile's sparks for the epilogue
-          const int tb = local & 1;
-          const uint32_t tuse = (uint32_t)(local >> 1);
+          // b1, b2 and W2 of the tile's sparks, for the epilogue and layer 2
+          const int tb = local % kTailBufs;
+          const uint32_t tuse = (uint32_t)(local / kTailBufs);
           if (!mbar_wait(sm, &sm->tail_empty[tb], (tuse & 1u) ^ 1u, a.status, 1u)) break;
           const int s0 = nt * S;
           const int s_valid = min(S, a.count - s0);
           mbar_expect_tx(&sm->tail_full[tb], tail_bytes * (uint32_t)s_valid);
-          float* dst = tails + (size_t)tb * S * a.tail_stride;
-          for (int s = 0; s < s_valid; ++s)
-            bulk_load(dst + (size_t)s * a.tail_stride, a.rows + (int64_t)(s0 + s) * a.ld + a.tail_off, tail_bytes,
-                      &sm->tail_full[tb]);
+          for (int s = 0; s < s_valid; ++s) {
+            const float* row = a.rows + (int64_t)(s0 + s) * a.ld;
+            float* tl = tails + ((size_t)tb * S + s) * kTailFloats;
+            bulk_load(tl, row + a.b1_off, (uint32_t)H1 * 4u, &sm->tail_full[tb]);
+            bulk_load(tl + H1, row + a.b2_off, (uint32_t)a.c_pad * 4u, &sm->tail_full[tb]);
+            uint8_t* w2 = w2s + ((size_t)tb * S + s) * kW2Bytes;
+#pragma unroll
+            for (int at = 0; at < kAtoms; ++at)
+              tma_load_3d(w2 + at * kAtomBytes, &tmap_w2, at * kAtomK2, 0, a.first_spark + s0 + s, &sm->tail_full[tb]);
+          }
         }
         for (int kb = 0; kb < a.k_blocks; ++kb, ++it) {
           const int s = (int)(it % (uint32_t)a.stages);
@@ -309,38 +369,50 @@ __global__ void __launch_bounds__(kThreads, 1)
           tma_load_2d(stage_b + (size_t)s * b_bytes, &tmap_w, kb * kBK, row_w, &sm->full[s]);
         }
       }
-      // drain: every issued load must land before the CTA may exit
-      for (int l = local - 2 > 0 ? local - 2 : 0; l < local; ++l) {
-        const long long t0 = clock64();
-        while (!mbar_try_wait(&sm->tail_full[l & 1], (uint32_t)((l >> 1) & 1))) {
-          if ((uint64_t)(clock64() - t0) > kWaitBudget) {
-            atomicOr(a.status, 16u);
-            break;
-          }
-        }
-      }
+      // drain: every issued copy must land before the CTA may exit
+      for (int l = local - kTailBufs > 0 ? local - kTailBufs : 0; l < local; ++l)
+        mbar_drain(&sm->tail_full[l % kTailBufs], (uint32_t)((l / kTailBufs) & 1), a.status);
       if (it > 0) {
         const uint32_t last = it - 1;
-        for (uint32_t j = (last + 1 > (uint32_t)a.stages ? last + 1 - a.stages : 0); j <= last; ++j) {
-          const int s = (int)(j % (uint32_t)a.stages);
-          const uint32_t ph = (j / (uint32_t)a.stages) & 1u;
-          const long long t0 = clock64();
-          while (!mbar_try_wait(&sm->full[s], ph)) {
-            if ((uint64_t)(clock64() - t0) > kWaitBudget) {
-              atomicOr(a.status, 16u);
-              break;
-            }
-          }
-        }
+        for (uint32_t j = (last + 1 > (uint32_t)a.stages ? last + 1 - a.stages : 0); j <= last; ++j)
+          mbar_drain(&sm->full[j % (uint32_t)a.stages], (j / (uint32_t)a.stages) & 1u, a.status);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
-      const uint32_t idesc = instr_desc(kBM, n_tile);
+      const uint32_t idesc1 = instr_desc(kBM, n_tile, 1u);
+      const uint32_t idesc2 = instr_desc(kBM, N2, 2u);
       uint32_t it = 0;
       int local = 0;
       bool ok = true;
+      // layer 2 of the tile with local index j (global index tj): logits = act(h + b1) x W2^T
+      auto layer2 = [&](int j, int tj) -> bool {
+        const int bj = j & 1;
+        const uint32_t uj = (uint32_t)(j >> 1);
+        const int tj_buf = j % kTailBufs;
+        if (!mbar_wait(sm, &sm->a2_full[bj], uj & 1u, a.status, 2u)) return false;
+        if (!mbar_wait(sm, &sm->tail_full[tj_buf], (uint32_t)(j / kTailBufs) & 1u, a.status, 2u)) return false;
+        if (!mbar_wait(sm, &sm->l2_empty[bj], (uj & 1u) ^ 1u, a.status, 2u)) return false;
+        tc_fence_after();
+        const int ntj = tj / a.m_tiles;
+        const int s_valid = min(S, a.count - ntj * S);
+        const uint32_t half = tmem_base + (uint32_t)(bj * 256);
+        for (int s = 0; s < s_valid; ++s) {
+          const uint32_t w2 = smem_u32(w2s + ((size_t)tj_buf * S + s) * kW2Bytes);
+#pragma unroll
+          for (int kk = 0; kk < H1 / kUmmaK2; ++kk) {
+            const uint32_t b_addr = w2 + (uint32_t)((kk * kUmmaK2) / kAtomK2) * kAtomBytes +
+                                    (uint32_t)((kk * kUmmaK2) % kAtomK2) * 4u;
+            mma_tf32_ta(half + (uint32_t)(n_tile + s * N2), half + (uint32_t)(s * H1 + kk * kUmmaK2),
+                        smem_desc(b_addr), idesc2, kk > 0 ? 1u : 0u);
+          }
+        }
+        mma_commit(&sm->l2_full[bj]);
+        mma_commit(&sm->tmem_empty[bj]);
+        return true;
+      };
+      int prev_t = -1;
       for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++local) {
         const int b = local & 1;
         const uint32_t use = (uint32_t)(local >> 1);
@@ -359,31 +431,32 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t b_addr = smem_u32(stage_b + (size_t)s * b_bytes);
 #pragma unroll
           for (int k = 0; k < kBK / kUmmaK; ++k) {
-            mma_bf16(d_tmem, smem_desc(a_addr + k * kUmmaK * 2), smem_desc(b_addr + k * kUmmaK * 2), idesc,
+            mma_bf16(d_tmem, smem_desc(a_addr + k * kUmmaK * 2), smem_desc(b_addr + k * kUmmaK * 2), idesc1,
                      (kb > 0 || k > 0) ? 1u : 0u);
           }
           mma_commit(&sm->empty[s]);
         }
         if (!ok) break;
         mma_commit(&sm->tmem_full[b]);
-      }
-      // every issued MMA completes before TMEM is released: one more commit, bounded wait
-      mma_commit(&sm->mma_done);
-      const long long t0 = clock64();
-      while (!mbar_try_wait(&sm->mma_done, 0u)) {
-        if ((uint64_t)(clock64() - t0) > kWaitBudget) {
-          atomicOr(a.status, 32u);
+        if (local > 0 && !layer2(local - 1, prev_t)) {
+          ok = false;
           break;
         }
+        prev_t = t;
       }
+      if (ok && local > 0) layer2(local - 1, prev_t);
+      // every issued MMA completes before TMEM is released: one more commit, bounded wait
+      mma_commit(&sm->mma_done);
+      mbar_drain(&sm->mma_done, 0u, a.status);
     }
   } else {
     // ---------------- epilogue ----------------
     const int ew = warp - 2;                 // 0..7
     const int quad = warp & 3;               // TMEM lane quadrant this warp may access
-    const int half = ew >> 2;                // which half of the tile's sparks
+    const int half = ew >> 2;                // which of the tile's sparks (every other one)
     const int et = threadIdx.x - 64;         // 0..255
     const int row_in_tile = quad * 32 + lane;
+    const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16);
     int local = 0;
     for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++local) {
       const int mt = t % a.m_tiles, nt = t / a.m_tiles;
@@ -394,25 +467,21 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t n = (int64_t)mt * kBM + row_in_tile;
       const bool valid_row = n < a.N;
       const int label = valid_row ? a.y[n] : 0;   // issued before the waits
+      const int tb = local % kTailBufs;
       bool ok = mbar_wait(sm, &sm->tmem_full[b], use & 1u, a.status, 4u);
-      ok = ok && mbar_wait(sm, &sm->tail_full[b], use & 1u, a.status, 4u);
+      ok = ok && mbar_wait(sm, &sm->tail_full[tb], (uint32_t)(local / kTailBufs) & 1u, a.status, 4u);
       if (epi_bar_any(!ok || sm->abort_flag)) break;
       tc_fence_after();
-      const float* tail = tails + (size_t)b * S * a.tail_stride;
+      const float* tail = tails + (size_t)tb * S * kTailFloats;
+      const uint32_t hbase = lane_base + (uint32_t)(b * 256);
+      // act(h + b1) in place: the TMEM A operand of layer 2
       for (int s = half; s < s_valid; s += 2) {
-        const float* b1 = tail + (size_t)s * a.tail_stride;
-        const float* W2 = b1 + H1;
-        const float* b2 = W2 + C * H1;
-        // layer 2: two partial sums per class (even / odd hidden units) in one
-        // packed register, classes innermost so each step has C independent chains
-        float2 z2[CMAX];
-#pragma unroll
-        for (int c = 0; c < CMAX; ++c) z2[c] = make_float2(0.0f, 0.0f);
-        const uint32_t col0 = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 256 + s * H1);
+        const float* b1 = tail + (size_t)s * kTailFloats;
 #pragma unroll 1
         for (int j0 = 0; j0 < H1; j0 += 8) {
           float h[8];
-          tmem_ld8(col0 + (uint32_t)j0, h);
+          const uint32_t col = hbase + (uint32_t)(s * H1 + j0);
+          tmem_ld8(col, h);
           tmem_wait_ld();
           const float4 bb0 = *reinterpret_cast<const float4*>(b1 + j0);
           const float4 bb1 = *reinterpret_cast<const float4*>(b1 + j0 + 4);
@@ -420,36 +489,40 @@ __global__ void __launch_bounds__(kThreads, 1)
           h[2] = act_f(a.act, h[2] + bb0.z); h[3] = act_f(a.act, h[3] + bb0.w);
           h[4] = act_f(a.act, h[4] + bb1.x); h[5] = act_f(a.act, h[5] + bb1.y);
           h[6] = act_f(a.act, h[6] + bb1.z); h[7] = act_f(a.act, h[7] + bb1.w);
-#pragma unroll
-          for (int c = 0; c < CMAX; ++c) {
-            if (c < C) {
-              const float4* w4 = reinterpret_cast<const float4*>(W2 + c * H1 + j0);
-              const float4 wa = w4[0], wb = w4[1];
-              ffma2(z2[c], wa.x, wa.y, h[0], h[1]);
-              ffma2(z2[c], wa.z, wa.w, h[2], h[3]);
-              ffma2(z2[c], wb.x, wb.y, h[4], h[5]);
-              ffma2(z2[c], wb.z, wb.w, h[6], h[7]);
-            }
-          }
+          tmem_st8(col, h);
         }
-        float z[CMAX];
+      }
+      tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm->a2_full[b]);
+      ok = mbar_wait(sm, &sm->l2_full[b], use & 1u, a.status, 4u);
+      if (epi_bar_any(!ok || sm->abort_flag)) break;
+      tc_fence_after();
+      for (int s = half; s < s_valid; s += 2) {
+        const float* b2 = tail + (size_t)s * kTailFloats + H1;
+        float z[N2];
+        const uint32_t col = hbase + (uint32_t)(n_tile + s * N2);
 #pragma unroll
-        for (int c = 0; c < CMAX; ++c) z[c] = c < C ? b2[c] + (z2[c].x + z2[c].y) : 0.0f;
+        for (int q = 0; q < N2; q += 16) tmem_ld16(col + (uint32_t)q, z + q);
+        tmem_wait_ld();
         float ce = 0.0f;
         if (valid_row) {
-          float zmax = z[0];
-#pragma unroll
-          for (int c = 1; c < CMAX; ++c)
-            if (c < C) zmax = fmaxf(zmax, z[c]);
-          float se = 0.0f;
+          const int C = a.C;
+          float zmax = -INFINITY;
           float zy = 0.0f;
 #pragma unroll
-          for (int c = 0; c < CMAX; ++c) {
+          for (int c = 0; c < N2; ++c) {
             if (c < C) {
-              se += expf(z[c] - zmax);
+              z[c] += b2[c];
+              zmax = fmaxf(zmax, z[c]);
               if (c == label) zy = z[c];
             }
           }
+          float se = 0.0f;
+#pragma unroll
+          for (int c = 0; c < N2; ++c)
+            if (c < C) se += expf(z[c] - zmax);
           ce = (zmax + logf(se)) - zy;
         }
 #pragma unroll
@@ -459,8 +532,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) {
-        mbar_arrive(&sm->tmem_empty[b]);
-        mbar_arrive(&sm->tail_empty[b]);
+        mbar_arrive(&sm->l2_empty[b]);
+        mbar_arrive(&sm->tail_empty[tb]);
       }
       epi_bar();
       if (et < s_valid) {
@@ -500,20 +573,16 @@ EncodeTiled get_encoder() {
   return fn;
 }
 
-bool encode_2d(CUtensorMap* map, const void* ptr, uint64_t inner, uint64_t outer, uint32_t box_inner,
-               uint32_t box_outer) {
+bool encode(CUtensorMap* map, CUtensorMapDataType type, uint32_t rank, const void* ptr, const cuuint64_t* dims,
+            const cuuint64_t* strides, const cuuint32_t* box) {
   EncodeTiled enc = get_encoder();
   if (!enc) {
     g_err = "cuTensorMapEncodeTiled unavailable";
     return false;
   }
-  cuuint64_t dims[2] = {inner, outer};
-  cuuint64_t strides[1] = {inner * 2};
-  cuuint32_t box[2] = {box_inner, box_outer};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, type, rank, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     g_err = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
     return false;
@@ -521,34 +590,23 @@ bool encode_2d(CUtensorMap* map, const void* ptr, uint64_t inner, uint64_t outer
   return true;
 }
 
-int sparks_per_tile(int h1) { return 256 / h1; }
+int n2_of(int C) { return C <= 16 ? 16 : 32; }
+int sparks_per_tile(int h1, int C) { return 256 / (h1 + n2_of(C)); }
 
-int tail_len(const Mlp& mlp) {
-  const int h1 = mlp.widths[1], C = mlp.widths[2];
-  return h1 + C * h1 + C;
-}
-
-int tail_stride(const Mlp& mlp) { return (tail_len(mlp) + 3) / 4 * 4; }
-
-template <int H1, int CMAX, bool EXACT>
-cudaError_t launch_hc(const TcPlan& plan, const TcArgs& args, cudaStream_t s) {
-  cudaError_t e = ensure_smem_limit<k_fitness_tc<H1, CMAX, EXACT>>(plan.smem_bytes);
+template <int H1, int N2>
+cudaError_t launch_hn(const TcPlan& plan, const TcArgs& args, cudaStream_t s) {
+  cudaError_t e = ensure_smem_limit<k_fitness_tc<H1, N2>>(plan.smem_bytes);
   if (e != cudaSuccess) return e;
   const int tiles = args.m_tiles * args.n_tiles;
   const int grid = tiles < plan.num_sms ? tiles : plan.num_sms;
-  k_fitness_tc<H1, CMAX, EXACT><<<grid, kThreads, plan.smem_bytes, s>>>(plan.tmap_x, plan.tmap_w, args);
+  k_fitness_tc<H1, N2><<<grid, kThreads, plan.smem_bytes, s>>>(plan.tmap_x, plan.tmap_w, plan.tmap_w2, args);
   return cudaPeekAtLastError();
 }
 
-// The class count picks the register array for the logits: exact for the
-// common counts (no per-class predicates), else the smallest that holds C.
 template <int H1>
 cudaError_t launch_h1(const TcPlan& plan, const TcArgs& args, cudaStream_t s) {
-  if (args.C == 10) return launch_hc<H1, 10, true>(plan, args, s);
-  if (args.C == 3) return launch_hc<H1, 3, true>(plan, args, s);
-  if (args.C <= 4) return launch_hc<H1, 4, false>(plan, args, s);
-  if (args.C <= 16) return launch_hc<H1, 16, false>(plan, args, s);
-  return launch_hc<H1, 32, false>(plan, args, s);
+  if (args.C <= 16) return launch_hn<H1, 16>(plan, args, s);
+  return launch_hn<H1, 32>(plan, args, s);
 }
 
 }  // namespace
@@ -557,11 +615,12 @@ bool tc_supported(const int32_t* widths, int n_layers) {
   if (n_layers != 2) return false;
   const int h1 = widths[1];
   if (widths[0] % 8 != 0) return false;
-  if (!(h1 == 16 || h1 == 32 || h1 == 64 || h1 == 128)) return false;
+  if (!(h1 == 32 || h1 == 64 || h1 == 128)) return false;
   return widths[2] >= 2 && widths[2] <= 32;
 }
 
-mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const __nv_bfloat16* op, int64_t max_rows) {
+mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const __nv_bfloat16* op, const float* rows, int64_t ld,
+                     int64_t max_rows) {
   plan = TcPlan();
   if (!tc_supported(mlp.widths, mlp.n_layers)) {
     g_err = "network shape not supported by the tensor-core path";
@@ -578,15 +637,16 @@ mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const __nv_bfloat16* op, int6
     g_err = "tensor-core path needs a Blackwell (sm_10x) GPU";
     return MGFWA_EINVAL;
   }
-  const int h1 = mlp.widths[1];
-  const int d_in = mlp.widths[0];
+  const int h1 = mlp.widths[1], d_in = mlp.widths[0], C = mlp.widths[2];
+  const int n2 = n2_of(C);
   plan.num_sms = prop.multiProcessorCount;
-  plan.sparks_per_tile = sparks_per_tile(h1);
+  plan.sparks_per_tile = sparks_per_tile(h1, C);
   plan.n_tile = plan.sparks_per_tile * h1;
   const size_t a_bytes = (size_t)kBM * kBK * 2, b_bytes = (size_t)plan.n_tile * kBK * 2;
+  const size_t w2_bytes = kTailBufs * (size_t)plan.sparks_per_tile * (h1 / kAtomK2) * n2 * 128;
   const size_t tail_bytes =
-      sizeof(float) * (2 * (size_t)plan.sparks_per_tile * tail_stride(mlp) + 4 * plan.sparks_per_tile + 4);
-  const size_t fixed = 1024 + tail_bytes + sizeof(Smem) + 64;
+      sizeof(float) * (kTailBufs * (size_t)plan.sparks_per_tile * (h1 + 32) + 4 * plan.sparks_per_tile);
+  const size_t fixed = 1024 + w2_bytes + tail_bytes + 16 + sizeof(Smem) + 64;
   const size_t limit = (size_t)prop.sharedMemPerBlockOptin;
   int stages = kMaxStages;
   while (stages > 2 && fixed + stages * (a_bytes + b_bytes) > limit) --stages;
@@ -596,9 +656,28 @@ mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const __nv_bfloat16* op, int6
   }
   plan.stages = stages;
   plan.smem_bytes = fixed + stages * (a_bytes + b_bytes);
-  if (!encode_2d(&plan.tmap_x, mlp.Xbf, (uint64_t)d_in, (uint64_t)mlp.N, kBK, kBM)) return MGFWA_ECUDA;
-  if (!encode_2d(&plan.tmap_w, op, (uint64_t)d_in, (uint64_t)(max_rows * h1), kBK, (uint32_t)plan.n_tile))
-    return MGFWA_ECUDA;
+  {
+    // X [N][d_in] BF16, box 64 x 128
+    cuuint64_t dims[2] = {(cuuint64_t)d_in, (cuuint64_t)mlp.N};
+    cuuint64_t strides[1] = {(cuuint64_t)d_in * 2};
+    cuuint32_t box[2] = {kBK, kBM};
+    if (!encode(&plan.tmap_x, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, mlp.Xbf, dims, strides, box)) return MGFWA_ECUDA;
+  }
+  {
+    // first-layer operand [max_rows*h1][d_in] BF16, box 64 x n_tile
+    cuuint64_t dims[2] = {(cuuint64_t)d_in, (cuuint64_t)(max_rows * h1)};
+    cuuint64_t strides[1] = {(cuuint64_t)d_in * 2};
+    cuuint32_t box[2] = {kBK, (cuuint32_t)plan.n_tile};
+    if (!encode(&plan.tmap_w, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, op, dims, strides, box)) return MGFWA_ECUDA;
+  }
+  {
+    // W2 of every spark straight from the FP32 rows: [max_rows][C][h1], box 32 x C x 1
+    cuuint64_t dims[3] = {(cuuint64_t)h1, (cuuint64_t)C, (cuuint64_t)max_rows};
+    cuuint64_t strides[2] = {(cuuint64_t)h1 * 4, (cuuint64_t)ld * 4};
+    cuuint32_t box[3] = {kAtomK2, (cuuint32_t)C, 1};
+    if (!encode(&plan.tmap_w2, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, rows + mlp.w_off[1], dims, strides, box))
+      return MGFWA_ECUDA;
+  }
   plan.ready = true;
   return MGFWA_OK;
 }
@@ -613,26 +692,25 @@ int launch_fitness_tc(const TcPlan& plan, const Mlp& mlp, int64_t first, const f
   const int h1 = mlp.widths[1];
   TcArgs a;
   a.count = count;
-  a.first_row = (int32_t)(first * h1);
+  a.first_spark = (int32_t)first;
   a.m_tiles = (int32_t)((mlp.N + kBM - 1) / kBM);
   a.S = plan.sparks_per_tile;
   a.n_tiles = (count + a.S - 1) / a.S;
   a.k_blocks = (mlp.widths[0] + kBK - 1) / kBK;
   a.stages = plan.stages;
-  a.tail_len = tail_len(mlp);
-  a.tail_stride = tail_stride(mlp);
-  a.N = mlp.N;
-  a.ld = ld;
-  a.tail_off = mlp.b_off[0];
   a.C = mlp.widths[2];
   a.act = mlp.acts[0];
+  a.c_pad = (a.C + 3) / 4 * 4;
+  a.N = mlp.N;
+  a.ld = ld;
+  a.b1_off = mlp.b_off[0];
+  a.b2_off = mlp.b_off[1];
   a.rows = rows;
   a.y = mlp.y;
   a.partial = partial;
   a.status = status;
   cudaError_t e;
   switch (h1) {
-    case 16: e = launch_h1<16>(plan, a, s); break;
     case 32: e = launch_h1<32>(plan, a, s); break;
     case 64: e = launch_h1<64>(plan, a, s); break;
     case 128: e = launch_h1<128>(plan, a, s); break;

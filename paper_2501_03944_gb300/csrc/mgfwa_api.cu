@@ -452,7 +452,7 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
     if (want_op) CREATE_LAUNCH(launch_f32_to_bf16(h->X, N * d_in, h->Xbf, h->stream), "X to BF16");
   }
   if (want_op) {
-    st = tc_plan(h->tc, h->mlp, h->op, h->P);
+    st = tc_plan(h->tc, h->mlp, h->op, h->sparks, p.Dp, h->P);
     if (st != MGFWA_OK) {
       h->err = tc_last_error();
       return bail(st);

@@ -41,7 +41,7 @@ def _rel(a, b):
 @pytest.mark.parametrize("widths,acts,N,count", [
     ((784, 64, 10), (1,), 200, 24),        # one sample tile (ragged), a few spark tiles
     ((784, 64, 10), (1,), 2048, 56),       # 16 sample tiles
-    ((8, 16, 3), (0,), 300, 56),           # K = 8 < one K block (TMA zero fill), 16 sparks per tile
+    ((8, 32, 3), (0,), 300, 56),           # K = 8 < one K block (TMA zero fill), 5 sparks per tile, tanh
     ((64, 32, 7), (0,), 129, 24),          # ragged tail of one sample
     ((96, 128, 5), (1,), 1, 16),           # a single sample
     ((48, 128, 4), (1,), 260, 12),         # two sparks per tile, K = 48 inside one K block
@@ -64,6 +64,17 @@ def test_bf16_fitness_against_oracle(pkg, widths, acts, N, count):
     bar = BF16_RTOL if N >= 128 else 3e-2
     assert np.all(err <= bar), (np.max(err), got[:4], want[:4])
     assert np.all(np.abs(f32 - want) <= 1e-5 * np.abs(want) + 1e-5)
+
+
+def test_bf16_rejects_unsupported_shapes(pkg):
+    """The tensor-core path takes two-layer nets with h1 in {32, 64, 128}; others get EINVAL at create."""
+    for widths, acts in (((8, 16, 3), (0,)), ((24, 16, 8, 5), (1, 1)), ((64, 48, 7), (1,))):
+        w = W.scaled(W.MLP_784_64_10, widths=widths, acts=acts, n_samples=64, n_fireworks=2,
+                     sparks_per_firework=8, guiding_per_firework=2)
+        X, y = W.make_data(w)
+        with pytest.raises(pkg.MgfwaError) as e:
+            pkg.Mgfwa.for_workload(w, 0, precision=pkg.MGFWA_BF16, X=X, y=y)
+        assert e.value.status == pkg.MGFWA_EINVAL
 
 
 def test_bf16_generation_phase_by_phase(pkg):
