@@ -59,54 +59,67 @@ __global__ void __launch_bounds__(kThreads) k_init(Problem p, float* __restrict_
   *reinterpret_cast<float4*>(fw_x + (int64_t)i * p.Dp + d0) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
-// Coordinates [d0, d0 + 4) of explosion spark `row` (one Philox block).
-__device__ __forceinline__ void explode4(const Problem& p, uint32_t gen, int row, uint32_t c4, const float4 x4,
+// 2u - 1 for u = (r >> 8) 2^-24, as one FMA: (r >> 8) 2^-23 - 1 is exact in
+// FP32 (a multiple of 2^-23 in [-1, 1)), so the value equals the two-step
+// form 2u - 1 bit for bit.
+__device__ __forceinline__ float signed_u24(uint32_t r) {
+  return __fmaf_rn(__uint2float_rn(r >> 8), 0x1p-23f, -1.0f);
+}
+
+// Coordinates [d0, d0 + 4) of explosion spark `row` (one Philox block);
+// `full` when all four coordinates are < D.
+__device__ __forceinline__ void explode4(const Problem& p, uint32_t gen, uint32_t row, uint32_t c4, const float4 x4,
                                          float amp, float* __restrict__ srow, __nv_bfloat16* __restrict__ oprow,
-                                         int64_t w1_elems) {
-  const int64_t d0 = (int64_t)c4 * 4;
-  const uint4 r = philox4x32_10(make_uint4(c4, (uint32_t)row, gen, kExplode), p.key0, p.key1);
+                                         uint32_t w1_elems, bool full) {
+  const uint32_t d0 = c4 * 4u;
+  const uint4 r = philox4x32_10(make_uint4(c4, row, gen, kExplode), p.key0, p.key1);
   float v[4];
-  bool out_of_bounds = false;
+#pragma unroll
+  for (int l = 0; l < 4; ++l) v[l] = __fmaf_rn(amp, signed_u24(lane_of(r, l)), lane_of(x4, l));
+  bool oob[4];
+  bool any = false;
 #pragma unroll
   for (int l = 0; l < 4; ++l) {
-    const float t = __fsub_rn(__fmul_rn(2.0f, u24(lane_of(r, l))), 1.0f);
-    v[l] = __fmaf_rn(amp, t, lane_of(x4, l));
-    out_of_bounds |= (d0 + l < p.D) && (v[l] < p.lb || v[l] > p.ub);
+    oob[l] = (v[l] < p.lb || v[l] > p.ub) && (full || d0 + l < (uint32_t)p.D);
+    any |= oob[l];
   }
-  if (out_of_bounds) {
-    const uint4 r2 = philox4x32_10(make_uint4(c4, (uint32_t)row, gen, kMap), p.key0, p.key1);
+  if (any) {
+    const uint4 r2 = philox4x32_10(make_uint4(c4, row, gen, kMap), p.key0, p.key1);
 #pragma unroll
     for (int l = 0; l < 4; ++l)
-      if (v[l] < p.lb || v[l] > p.ub) v[l] = map_coord(lane_of(x4, l), amp, p.lb, p.ub, u24(lane_of(r2, l)));
+      if (oob[l]) v[l] = map_coord(lane_of(x4, l), amp, p.lb, p.ub, u24(lane_of(r2, l)));
   }
+  if (!full) {
 #pragma unroll
-  for (int l = 0; l < 4; ++l)
-    if (d0 + l >= p.D) v[l] = 0.0f;
+    for (int l = 0; l < 4; ++l)
+      if (d0 + l >= (uint32_t)p.D) v[l] = 0.0f;
+  }
   *reinterpret_cast<float4*>(srow + d0) = make_float4(v[0], v[1], v[2], v[3]);
   if (oprow != nullptr && d0 < w1_elems) store_bf16x4(oprow + d0, v[0], v[1], v[2], v[3]);
 }
 
-// One block covers 2 * kThreads Philox blocks (8 * kThreads coordinates) of
-// one spark row; each thread does two, kThreads blocks apart, so a warp's
-// stores stay contiguous.
+// grid (coordinate blocks, lambda, mu): one block covers 2 * kThreads Philox
+// blocks (8 * kThreads coordinates) of one spark row; each thread does two,
+// kThreads blocks apart, so a warp's stores stay contiguous.
 __global__ void __launch_bounds__(kThreads) k_explode(Problem p, uint32_t gen, const float* __restrict__ fw_x,
                                                       const float* __restrict__ fw_amp,
                                                       float* __restrict__ sparks,
                                                       __nv_bfloat16* __restrict__ op, int64_t w1_elems) {
-  const int row = blockIdx.y;  // i * lam + j
-  const int i = row / p.lam;
+  const uint32_t i = blockIdx.z;
+  const uint32_t row = i * (uint32_t)p.lam + blockIdx.y;  // i * lam + j
   const float amp = fw_amp[i];
   const float* xrow = fw_x + (int64_t)i * p.Dp;
   float* srow = sparks + (int64_t)row * p.Dp;
   __nv_bfloat16* oprow = op != nullptr ? op + (int64_t)row * w1_elems : nullptr;
   const uint32_t n4 = (uint32_t)(p.Dp / 4);
+  const uint32_t full4 = (uint32_t)(p.D / 4);  // blocks whose 4 coordinates are all < D
   const uint32_t c4a = blockIdx.x * (2 * kThreads) + threadIdx.x;
   const uint32_t c4b = c4a + kThreads;
   float4 xa = make_float4(0.f, 0.f, 0.f, 0.f), xb = xa;
-  if (c4a < n4) xa = *reinterpret_cast<const float4*>(xrow + (int64_t)c4a * 4);
-  if (c4b < n4) xb = *reinterpret_cast<const float4*>(xrow + (int64_t)c4b * 4);
-  if (c4a < n4) explode4(p, gen, row, c4a, xa, amp, srow, oprow, w1_elems);
-  if (c4b < n4) explode4(p, gen, row, c4b, xb, amp, srow, oprow, w1_elems);
+  if (c4a < n4) xa = *reinterpret_cast<const float4*>(xrow + (size_t)c4a * 4);
+  if (c4b < n4) xb = *reinterpret_cast<const float4*>(xrow + (size_t)c4b * 4);
+  if (c4a < n4) explode4(p, gen, row, c4a, xa, amp, srow, oprow, (uint32_t)w1_elems, c4a < full4);
+  if (c4b < n4) explode4(p, gen, row, c4b, xb, amp, srow, oprow, (uint32_t)w1_elems, c4b < full4);
 }
 
 // Multi-guiding sparks, reading: group q of firework i has ranked index
@@ -120,8 +133,8 @@ __global__ void __launch_bounds__(kThreads) k_guide(Problem p, uint32_t gen, con
                                                     const int32_t* __restrict__ bottom,
                                                     float* __restrict__ guides,
                                                     __nv_bfloat16* __restrict__ op, int64_t w1_elems) {
-  const int gq = blockIdx.y;  // i * m + q
-  const int i = gq / p.m;
+  const int i = blockIdx.z;
+  const int gq = i * p.m + blockIdx.y;  // i * m + q
   const int64_t c4 = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   const int64_t d0 = c4 * 4;
   if (d0 >= p.Dp) return;
@@ -213,7 +226,7 @@ int launch_init(const Problem& p, float* fw_x, float* fw_amp, cudaStream_t s) {
 
 int launch_explode(const Problem& p, uint32_t gen, const float* fw_x, const float* fw_amp, float* sparks,
                    __nv_bfloat16* op, int64_t w1_elems, cudaStream_t s) {
-  dim3 grid((unsigned)((p.Dp / 4 + 2 * kThreads - 1) / (2 * kThreads)), p.mu * p.lam);
+  dim3 grid((unsigned)((p.Dp / 4 + 2 * kThreads - 1) / (2 * kThreads)), p.lam, p.mu);
   k_explode<<<grid, kThreads, 0, s>>>(p, gen, fw_x, fw_amp, sparks, op, w1_elems);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
@@ -221,7 +234,7 @@ int launch_explode(const Problem& p, uint32_t gen, const float* fw_x, const floa
 int launch_guide(const Problem& p, uint32_t gen, const float* fw_x, const float* fw_amp, const float* sparks,
                  const int32_t* top, const int32_t* bottom, float* guides, __nv_bfloat16* op_guides,
                  int64_t w1_elems, cudaStream_t s) {
-  dim3 grid(blocks_for(p.Dp / 4), p.mu * p.m);
+  dim3 grid(blocks_for(p.Dp / 4), p.m, p.mu);
   k_guide<<<grid, kThreads, 0, s>>>(p, gen, fw_x, fw_amp, sparks, top, bottom, guides, op_guides, w1_elems);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
