@@ -41,6 +41,22 @@ def _dist():
     return world, rank, local
 
 
+def _traffic(kernel: str, source: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None
+    when the kernel's source changed since that capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(kernel)
+    if not rec:
+        return None
+    sha = hashlib.sha256(open(os.path.join(ROOT, source), "rb").read()).hexdigest()
+    if sha != rec.get("sha256"):
+        return None
+    return rec["dram_bytes_read"] + rec["dram_bytes_write"]
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -246,7 +262,9 @@ def gpu_arm(args):
             roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
                     "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x 2070 MHz"}
         roof["frac"] = roof["achieved"] / roof["peak"]
-        roof["traffic"] = None
+        roof["traffic"] = (_traffic("k_fitness_tc", "paper_2501_03944_gb300/csrc/k_fitness_tc.cu")
+                           if prec == pkg.MGFWA_BF16 else None)
+        roof["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
         roof["kernel"] = "fitness of the explosion sparks (1000 sparks x 2048 samples per launch)"
         # HBM-bound kernels: algorithmic bytes / time
         D = WORKLOAD.dim
