@@ -73,6 +73,8 @@ typedef struct {
   uint64_t seed;                /* Philox key */
   int32_t precision;            /* mgfwa_precision */
   int32_t elite_rescore;        /* reserved: re-score elite candidates in FP32 (low precision only) */
+  int32_t n_runs;               /* B >= 1 independent runs of the same problem, stepped together (the
+                                   batch dimension of Table 1, Sec. 3); run b uses seed + b */
 } mgfwa_config;
 
 typedef struct {
@@ -89,7 +91,7 @@ typedef struct {
 typedef struct mgfwa_handle mgfwa_t;
 
 /* Fill *cfg with the defaults (beta 1, A0 = ub - lb once bounds are set,
- * C_a 1.2, C_r 0.9, sigma 0.2, FP32).  Fields the caller must still set:
+ * C_a 1.2, C_r 0.9, sigma 0.2, FP32, one run).  Fields the caller must still set:
  * dim, lb, ub, n_fireworks, sparks_per_firework, guiding_per_firework,
  * eval_budget, seed.  amp_init <= 0 means ub - lb. */
 MGFWA_API mgfwa_status mgfwa_config_init(mgfwa_config* cfg);
@@ -112,24 +114,29 @@ MGFWA_API mgfwa_status mgfwa_run(mgfwa_t* h);
 
 /* Synchronise; write the best position so far (x_out: D floats, may be
  * NULL), its fitness recomputed in FP64 on the GPU (f_out, may be NULL) and
- * the evaluations used (evals_out, may be NULL). */
+ * the evaluations used per run (evals_out, may be NULL).  With several runs:
+ * the best of the run whose FP32 best-so-far is lowest (the first on ties). */
 MGFWA_API mgfwa_status mgfwa_best(mgfwa_t* h, float* x_out, double* f_out, int64_t* evals_out);
+
+/* As mgfwa_best for run `run` in [0, n_runs); EINVAL otherwise. */
+MGFWA_API mgfwa_status mgfwa_best_run(mgfwa_t* h, int32_t run, float* x_out, double* f_out, int64_t* evals_out);
 
 /* Evaluate `count` host vectors (each D floats, row-major) with the
  * handle's objective in the given precision; f_out gets count FP32 values.
  * Uses the handle's device workspace (count <= the sparks of one
- * generation) and synchronises. */
+ * generation of all runs) and synchronises.  Only between generations. */
 MGFWA_API mgfwa_status mgfwa_evaluate(mgfwa_t* h, const float* xs, int64_t count, int32_t precision,
                             float* f_out);
 
 typedef struct {
-  int64_t evals;           /* evaluations so far, including init */
+  int64_t evals;           /* evaluations so far per run, including init */
   int32_t generations;     /* generations run */
   int32_t k;               /* the subset size in use */
   int64_t dim_padded;      /* row stride of sparks and fireworks on the device (floats) */
-  int64_t sparks_per_gen;  /* mu (lambda + m) */
+  int64_t sparks_per_gen;  /* n_runs mu (lambda + m): sparks evaluated per generation, all runs */
   int64_t device_bytes;    /* bytes of the handle's device allocation */
   int64_t kernel_launches; /* kernels enqueued so far by this handle */
+  int32_t n_runs;          /* B */
 } mgfwa_info;
 
 MGFWA_API mgfwa_status mgfwa_get_info(const mgfwa_t* h, mgfwa_info* info);

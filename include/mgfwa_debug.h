@@ -31,19 +31,21 @@ typedef enum {
  * budget.  Asynchronous. */
 MGFWA_API mgfwa_status mgfwa_debug_phase(mgfwa_t* h, int32_t phase);
 
+/* Buffers of all B runs, run-major (B = 1 for a single run): firework
+ * z = b*mu + i, explosion row z*lambda + j, guiding row z*m + q. */
 typedef enum {
-  MGFWA_BUF_FW_X = 0,    /* [mu][D] FP32 fireworks */
-  MGFWA_BUF_FW_AMP = 1,  /* [mu] FP32 amplitudes */
-  MGFWA_BUF_FW_F = 2,    /* [mu] FP32 firework fitness */
-  MGFWA_BUF_SPARKS = 3,  /* [mu*lambda][D] FP32 explosion sparks, row i*lambda + j */
-  MGFWA_BUF_GUIDES = 4,  /* [mu*m][D] FP32 guiding sparks, row i*m + q */
-  MGFWA_BUF_FIT_E = 5,   /* [mu*lambda] FP32 explosion fitness */
-  MGFWA_BUF_FIT_G = 6,   /* [mu*m] FP32 guiding fitness */
-  MGFWA_BUF_TOP = 7,     /* [mu][m][k] int32: index within the firework of rank r, best first */
-  MGFWA_BUF_BOTTOM = 8,  /* [mu][m][k] int32: index of rank g-1-r, worst first */
-  MGFWA_BUF_WINNER = 9,  /* [mu] int32: -1 kept, j explosion j, lambda+q guiding q */
-  MGFWA_BUF_BEST_X = 10, /* [D] FP32 run best-so-far position */
-  MGFWA_BUF_BEST_F = 11  /* [1] FP32 run best-so-far fitness (the precision decisions use) */
+  MGFWA_BUF_FW_X = 0,    /* [B*mu][D] FP32 fireworks */
+  MGFWA_BUF_FW_AMP = 1,  /* [B*mu] FP32 amplitudes */
+  MGFWA_BUF_FW_F = 2,    /* [B*mu] FP32 firework fitness */
+  MGFWA_BUF_SPARKS = 3,  /* [B*mu*lambda][D] FP32 explosion sparks */
+  MGFWA_BUF_GUIDES = 4,  /* [B*mu*m][D] FP32 guiding sparks */
+  MGFWA_BUF_FIT_E = 5,   /* [B*mu*lambda] FP32 explosion fitness */
+  MGFWA_BUF_FIT_G = 6,   /* [B*mu*m] FP32 guiding fitness */
+  MGFWA_BUF_TOP = 7,     /* [B*mu][m][k] int32: index within the firework of rank r, best first */
+  MGFWA_BUF_BOTTOM = 8,  /* [B*mu][m][k] int32: index of rank g-1-r, worst first */
+  MGFWA_BUF_WINNER = 9,  /* [B*mu] int32: -1 kept, j explosion j, lambda+q guiding q */
+  MGFWA_BUF_BEST_X = 10, /* [B][D] FP32 best-so-far position per run */
+  MGFWA_BUF_BEST_F = 11  /* [B] FP32 best-so-far fitness per run (the precision decisions use) */
 } mgfwa_buffer;
 
 /* Copy a buffer to / from host memory (rows packed D floats apart);

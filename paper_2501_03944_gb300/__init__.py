@@ -31,7 +31,8 @@ MGFWA_ACT_TANH, MGFWA_ACT_RELU = 0, 1
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EBUDGET"}
 
 # Every symbol the headers declare (checked by the CPU test suite).
-EXPORTS = ("mgfwa_config_init", "mgfwa_create", "mgfwa_step", "mgfwa_run", "mgfwa_best", "mgfwa_evaluate",
+EXPORTS = ("mgfwa_config_init", "mgfwa_create", "mgfwa_step", "mgfwa_run", "mgfwa_best", "mgfwa_best_run",
+           "mgfwa_evaluate",
            "mgfwa_get_info", "mgfwa_destroy", "mgfwa_last_error", "mgfwa_debug_phase", "mgfwa_debug_read",
            "mgfwa_debug_write", "mgfwa_debug_profile", "mgfwa_debug_kernel_times", "mgfwa_evaluate_fp32_noalloc")
 N_KERNEL_GROUPS = 7
@@ -44,7 +45,7 @@ class mgfwa_config(ctypes.Structure):
                 ("guiding_per_firework", ctypes.c_int32), ("sigma", ctypes.c_float), ("boost", ctypes.c_float),
                 ("amp_init", ctypes.c_float), ("c_amplify", ctypes.c_float), ("c_reduce", ctypes.c_float),
                 ("eval_budget", ctypes.c_int64), ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32),
-                ("elite_rescore", ctypes.c_int32)]
+                ("elite_rescore", ctypes.c_int32), ("n_runs", ctypes.c_int32)]
 
 
 class mgfwa_objective(ctypes.Structure):
@@ -57,7 +58,7 @@ class mgfwa_objective(ctypes.Structure):
 class mgfwa_info(ctypes.Structure):
     _fields_ = [("evals", ctypes.c_int64), ("generations", ctypes.c_int32), ("k", ctypes.c_int32),
                 ("dim_padded", ctypes.c_int64), ("sparks_per_gen", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("n_runs", ctypes.c_int32)]
 
 
 class MgfwaError(RuntimeError):
@@ -85,6 +86,7 @@ def load_library(path: Optional[str] = None):
     L.mgfwa_step.argtypes = [vp, i32]
     L.mgfwa_run.argtypes = [vp]
     L.mgfwa_best.argtypes = [vp, f32p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+    L.mgfwa_best_run.argtypes = [vp, i32, f32p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     L.mgfwa_evaluate.argtypes = [vp, f32p, i64, i32, f32p]
     L.mgfwa_get_info.argtypes = [vp, ctypes.POINTER(mgfwa_info)]
     L.mgfwa_destroy.argtypes = [vp]
@@ -165,6 +167,14 @@ def mgfwa_best(handle: int, dim: int):
     return x, f.value, ev.value
 
 
+def mgfwa_best_run(handle: int, run: int, dim: int):
+    x = np.zeros(dim, np.float32)
+    f = ctypes.c_double()
+    ev = ctypes.c_int64()
+    _check(load_library().mgfwa_best_run(handle, run, _f32p(x), ctypes.byref(f), ctypes.byref(ev)), handle)
+    return x, f.value, ev.value
+
+
 def mgfwa_evaluate(handle: int, xs: np.ndarray, precision: int) -> np.ndarray:
     xs = np.ascontiguousarray(xs, np.float32)
     out = np.zeros(xs.shape[0], np.float32)
@@ -217,13 +227,14 @@ class Mgfwa:
 
     def __init__(self, *, dim, lb, ub, n_fireworks, sparks_per_firework, guiding_per_firework, eval_budget,
                  seed, sigma=0.2, boost=1.0, amp_init=0.0, c_amplify=1.2, c_reduce=0.9, precision=MGFWA_FP32,
-                 kind=MGFWA_OBJ_MLP_CE, widths=(), acts=(), X=None, y=None, stream: int = 0):
+                 kind=MGFWA_OBJ_MLP_CE, widths=(), acts=(), X=None, y=None, stream: int = 0, n_runs: int = 1):
         cfg = mgfwa_config_init()
         cfg.dim, cfg.lb, cfg.ub = dim, lb, ub
         cfg.n_fireworks, cfg.sparks_per_firework, cfg.guiding_per_firework = (
             n_fireworks, sparks_per_firework, guiding_per_firework)
         cfg.sigma, cfg.boost, cfg.amp_init, cfg.c_amplify, cfg.c_reduce = sigma, boost, amp_init, c_amplify, c_reduce
         cfg.eval_budget, cfg.seed, cfg.precision = eval_budget, seed, precision
+        cfg.n_runs = n_runs
         self.cfg = cfg
         self._obj = _ObjectiveBuffers(kind, widths, acts, X, y)
         self.dim = dim
@@ -254,8 +265,10 @@ class Mgfwa:
     def run(self) -> None:
         _check(mgfwa_run(self.handle), self.handle)
 
-    def best(self):
-        return mgfwa_best(self.handle, self.dim)
+    def best(self, run: Optional[int] = None):
+        if run is None:
+            return mgfwa_best(self.handle, self.dim)
+        return mgfwa_best_run(self.handle, run, self.dim)
 
     def evaluate(self, xs, precision: Optional[int] = None) -> np.ndarray:
         return mgfwa_evaluate(self.handle, xs, self.cfg.precision if precision is None else precision)
@@ -267,14 +280,15 @@ class Mgfwa:
         _check(mgfwa_debug_phase(self.handle, ph), self.handle)
 
     def read(self, buf: int) -> np.ndarray:
-        mu, lam, m, D, k = (self.cfg.n_fireworks, self.cfg.sparks_per_firework, self.cfg.guiding_per_firework,
+        B = self.cfg.n_runs
+        mu, lam, m, D, k = (B * self.cfg.n_fireworks, self.cfg.sparks_per_firework, self.cfg.guiding_per_firework,
                             self.dim, self.k)
         shapes = {MGFWA_BUF_FW_X: ((mu, D), np.float32), MGFWA_BUF_FW_AMP: ((mu,), np.float32),
                   MGFWA_BUF_FW_F: ((mu,), np.float32), MGFWA_BUF_SPARKS: ((mu * lam, D), np.float32),
                   MGFWA_BUF_GUIDES: ((mu * m, D), np.float32), MGFWA_BUF_FIT_E: ((mu * lam,), np.float32),
                   MGFWA_BUF_FIT_G: ((mu * m,), np.float32), MGFWA_BUF_TOP: ((mu, m, k), np.int32),
                   MGFWA_BUF_BOTTOM: ((mu, m, k), np.int32), MGFWA_BUF_WINNER: ((mu,), np.int32),
-                  MGFWA_BUF_BEST_X: ((D,), np.float32), MGFWA_BUF_BEST_F: ((1,), np.float32)}
+                  MGFWA_BUF_BEST_X: ((B, D) if B > 1 else (D,), np.float32), MGFWA_BUF_BEST_F: ((B,), np.float32)}
         shape, dt = shapes[buf]
         return mgfwa_debug_read(self.handle, buf, np.zeros(shape, dt))
 

@@ -29,7 +29,7 @@ __host__ __device__ __forceinline__ int odd_ld(int w) { return w + ((w & 1) == 0
 __global__ void __launch_bounds__(kThreads) k_fitness_simt(Mlp mlp, const float* __restrict__ rows, int64_t ld,
                                                            int32_t count, float* __restrict__ partial) {
   extern __shared__ __align__(16) float smem[];
-  const int row = blockIdx.y, mt = blockIdx.x;
+  const int row = blockIdx.x, mt = blockIdx.y;
   const float* w = rows + (int64_t)row * ld;
   const int L = mlp.n_layers;
   const int d_in = mlp.widths[0], h1 = mlp.widths[1];
@@ -256,7 +256,7 @@ int launch_fitness_simt_main(const Mlp& mlp, const float* rows, int64_t ld, int3
   const size_t smem = smem_for(mlp);
   if (ensure_smem_limit<k_fitness_simt>(smem) != cudaSuccess) return -1;
   const int mtiles = (int)((mlp.N + kMT - 1) / kMT);
-  dim3 grid(mtiles, count);
+  dim3 grid(count, mtiles);
   k_fitness_simt<<<grid, kThreads, smem, s>>>(mlp, rows, ld, count, partial);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }

@@ -11,7 +11,8 @@ namespace mgfwa {
 
 namespace {
 
-// One block per (firework, guiding group).  Each thread ranks its sparks by
+// One block per (firework, guiding group), fireworks of all runs numbered
+// globally.  Each thread ranks its sparks by
 // counting the sparks of the group that come strictly before them; the
 // counts are a permutation because the order is total.
 __global__ void k_rank(Problem p, const float* __restrict__ fit_e, int32_t* __restrict__ top,
@@ -48,7 +49,7 @@ __device__ __forceinline__ void take_if_before(float& bf, int& bc, float of, int
   }
 }
 
-// One block per firework: argmin over its lam explosion and m guiding
+// One block per firework (of all runs): argmin over its lam explosion and m guiding
 // sparks (candidate order: explosion 0..lam-1, guiding 0..m-1), the strict
 // improvement test, the dynamic amplitude update (x C_a on improvement,
 // x C_r otherwise), and the copy of the winning row into the firework.
@@ -106,29 +107,32 @@ __global__ void __launch_bounds__(kSelThreads) k_select(Problem p, const float* 
   for (int64_t e = threadIdx.x; e < p.Dp / 4; e += blockDim.x) dst[e] = s4[e];
 }
 
-// The run's best-so-far: strict improvement over the fireworks in index
-// order (init: the first minimum of the initial fireworks).
+// Each run's best-so-far (one block per run): strict improvement over its
+// fireworks in index order (init: the first minimum of the initial
+// fireworks).
 __global__ void __launch_bounds__(kSelThreads) k_run_best(Problem p, int init, const float* __restrict__ fw_x,
                                                           const float* __restrict__ fw_f,
                                                           float* __restrict__ best_x, float* __restrict__ best_f) {
   __shared__ int s_bi;
+  const int b = blockIdx.x;
+  const float* f = fw_f + (int64_t)b * p.mu;
   if (threadIdx.x == 0) {
     int bi = init ? 0 : -1;
-    float bf = init ? fw_f[0] : *best_f;
+    float bf = init ? f[0] : best_f[b];
     for (int i = init ? 1 : 0; i < p.mu; ++i) {
-      if (rank_key(fw_f[i]) < rank_key(bf)) {
-        bf = fw_f[i];
+      if (rank_key(f[i]) < rank_key(bf)) {
+        bf = f[i];
         bi = i;
       }
     }
-    if (bi >= 0) *best_f = bf;
+    if (bi >= 0) best_f[b] = bf;
     s_bi = bi;
   }
   __syncthreads();
   const int bi = s_bi;
   if (bi < 0) return;
-  const float4* src = reinterpret_cast<const float4*>(fw_x + (int64_t)bi * p.Dp);
-  float4* dst = reinterpret_cast<float4*>(best_x);
+  const float4* src = reinterpret_cast<const float4*>(fw_x + ((int64_t)b * p.mu + bi) * p.Dp);
+  float4* dst = reinterpret_cast<float4*>(best_x + (int64_t)b * p.Dp);
   for (int64_t e = threadIdx.x; e < p.Dp / 4; e += blockDim.x) dst[e] = src[e];
 }
 
@@ -137,22 +141,22 @@ __global__ void __launch_bounds__(kSelThreads) k_run_best(Problem p, int init, c
 int launch_rank(const Problem& p, const float* fit_e, int32_t* top, int32_t* bottom, cudaStream_t s) {
   const int threads = p.g >= 256 ? 256 : ((p.g + 31) / 32) * 32;
   const size_t smem = (size_t)p.g * (sizeof(float) + sizeof(int));
-  k_rank<<<p.mu * p.m, threads, smem, s>>>(p, fit_e, top, bottom);
+  k_rank<<<p.B * p.mu * p.m, threads, smem, s>>>(p, fit_e, top, bottom);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 int launch_select(const Problem& p, const float* fit_e, const float* fit_g, const float* sparks,
                   const float* guides, float* fw_x, float* fw_amp, float* fw_f, int32_t* winner, float* best_x,
                   float* best_f, cudaStream_t s) {
-  k_select<<<p.mu, kSelThreads, 0, s>>>(p, fit_e, fit_g, sparks, guides, fw_x, fw_amp, fw_f, winner);
+  k_select<<<p.B * p.mu, kSelThreads, 0, s>>>(p, fit_e, fit_g, sparks, guides, fw_x, fw_amp, fw_f, winner);
   if (cudaPeekAtLastError() != cudaSuccess) return -1;
-  k_run_best<<<1, kSelThreads, 0, s>>>(p, 0, fw_x, fw_f, best_x, best_f);
+  k_run_best<<<p.B, kSelThreads, 0, s>>>(p, 0, fw_x, fw_f, best_x, best_f);
   return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;
 }
 
 int launch_run_best_init(const Problem& p, const float* fw_x, const float* fw_f, float* best_x, float* best_f,
                          cudaStream_t s) {
-  k_run_best<<<1, kSelThreads, 0, s>>>(p, 1, fw_x, fw_f, best_x, best_f);
+  k_run_best<<<p.B, kSelThreads, 0, s>>>(p, 1, fw_x, fw_f, best_x, best_f);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

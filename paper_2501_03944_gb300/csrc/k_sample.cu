@@ -43,20 +43,24 @@ __device__ __forceinline__ void store_bf16x4(__nv_bfloat16* dst, float a, float 
   *reinterpret_cast<uint2*>(dst) = v;
 }
 
+// grid (coordinate blocks, B * mu): global firework z = b * mu + i.
 __global__ void __launch_bounds__(kThreads) k_init(Problem p, float* __restrict__ fw_x,
                                                    float* __restrict__ fw_amp) {
-  const int i = blockIdx.y;
+  const int z = blockIdx.y;
+  const int b = z / p.mu, i = z - b * p.mu;
   const int64_t c4 = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   const int64_t d0 = c4 * 4;
-  if (blockIdx.x == 0 && threadIdx.x == 0) fw_amp[i] = p.amp0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) fw_amp[z] = p.amp0;
   if (d0 >= p.Dp) return;
-  const uint4 r = philox4x32_10(make_uint4((uint32_t)c4, (uint32_t)i, 0u, kInit), p.key0, p.key1);
+  uint32_t k0, k1;
+  run_key(p, b, k0, k1);
+  const uint4 r = philox4x32_10(make_uint4((uint32_t)c4, (uint32_t)i, 0u, kInit), k0, k1);
   const float width = __fsub_rn(p.ub, p.lb);
   float v[4];
 #pragma unroll
   for (int l = 0; l < 4; ++l)
     v[l] = (d0 + l < p.D) ? __fmaf_rn(u24(lane_of(r, l)), width, p.lb) : 0.0f;
-  *reinterpret_cast<float4*>(fw_x + (int64_t)i * p.Dp + d0) = make_float4(v[0], v[1], v[2], v[3]);
+  *reinterpret_cast<float4*>(fw_x + (int64_t)z * p.Dp + d0) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
 // 2u - 1 for u = (r >> 8) 2^-24, as one FMA: (r >> 8) 2^-23 - 1 is exact in
@@ -68,11 +72,11 @@ __device__ __forceinline__ float signed_u24(uint32_t r) {
 
 // Coordinates [d0, d0 + 4) of explosion spark `row` (one Philox block);
 // `full` when all four coordinates are < D.
-__device__ __forceinline__ void explode4(const Problem& p, uint32_t gen, uint32_t row, uint32_t c4, const float4 x4,
-                                         float amp, float* __restrict__ srow, __nv_bfloat16* __restrict__ oprow,
-                                         uint32_t w1_elems, bool full) {
+__device__ __forceinline__ void explode4(const Problem& p, uint32_t gen, uint32_t unit, uint32_t k0, uint32_t k1,
+                                         uint32_t c4, const float4 x4, float amp, float* __restrict__ srow,
+                                         __nv_bfloat16* __restrict__ oprow, uint32_t w1_elems, bool full) {
   const uint32_t d0 = c4 * 4u;
-  const uint4 r = philox4x32_10(make_uint4(c4, row, gen, kExplode), p.key0, p.key1);
+  const uint4 r = philox4x32_10(make_uint4(c4, unit, gen, kExplode), k0, k1);
   float v[4];
 #pragma unroll
   for (int l = 0; l < 4; ++l) v[l] = __fmaf_rn(amp, signed_u24(lane_of(r, l)), lane_of(x4, l));
@@ -84,7 +88,7 @@ __device__ __forceinline__ void explode4(const Problem& p, uint32_t gen, uint32_
     any |= oob[l];
   }
   if (any) {
-    const uint4 r2 = philox4x32_10(make_uint4(c4, row, gen, kMap), p.key0, p.key1);
+    const uint4 r2 = philox4x32_10(make_uint4(c4, unit, gen, kMap), k0, k1);
 #pragma unroll
     for (int l = 0; l < 4; ++l)
       if (oob[l]) v[l] = map_coord(lane_of(x4, l), amp, p.lb, p.ub, u24(lane_of(r2, l)));
@@ -98,17 +102,23 @@ __device__ __forceinline__ void explode4(const Problem& p, uint32_t gen, uint32_
   if (oprow != nullptr && d0 < w1_elems) store_bf16x4(oprow + d0, v[0], v[1], v[2], v[3]);
 }
 
-// grid (coordinate blocks, lambda, mu): one block covers 2 * kThreads Philox
-// blocks (8 * kThreads coordinates) of one spark row; each thread does two,
-// kThreads blocks apart, so a warp's stores stay contiguous.
+// grid (coordinate blocks, lambda, B * mu): one block covers 2 * kThreads
+// Philox blocks (8 * kThreads coordinates) of one spark row; each thread does
+// two, kThreads blocks apart, so a warp's stores stay contiguous.  Global
+// firework z = b * mu + i, spark row z * lam + j, Philox unit i * lam + j of
+// run b's stream.
 __global__ void __launch_bounds__(kThreads) k_explode(Problem p, uint32_t gen, const float* __restrict__ fw_x,
                                                       const float* __restrict__ fw_amp,
                                                       float* __restrict__ sparks,
                                                       __nv_bfloat16* __restrict__ op, int64_t w1_elems) {
-  const uint32_t i = blockIdx.z;
-  const uint32_t row = i * (uint32_t)p.lam + blockIdx.y;  // i * lam + j
-  const float amp = fw_amp[i];
-  const float* xrow = fw_x + (int64_t)i * p.Dp;
+  const uint32_t z = blockIdx.z;
+  const uint32_t b = z / (uint32_t)p.mu, i = z - b * (uint32_t)p.mu;
+  const uint32_t row = z * (uint32_t)p.lam + blockIdx.y;
+  const uint32_t unit = i * (uint32_t)p.lam + blockIdx.y;
+  uint32_t k0, k1;
+  run_key(p, (int)b, k0, k1);
+  const float amp = fw_amp[z];
+  const float* xrow = fw_x + (int64_t)z * p.Dp;
   float* srow = sparks + (int64_t)row * p.Dp;
   __nv_bfloat16* oprow = op != nullptr ? op + (int64_t)row * w1_elems : nullptr;
   const uint32_t n4 = (uint32_t)(p.Dp / 4);
@@ -118,8 +128,8 @@ __global__ void __launch_bounds__(kThreads) k_explode(Problem p, uint32_t gen, c
   float4 xa = make_float4(0.f, 0.f, 0.f, 0.f), xb = xa;
   if (c4a < n4) xa = *reinterpret_cast<const float4*>(xrow + (size_t)c4a * 4);
   if (c4b < n4) xb = *reinterpret_cast<const float4*>(xrow + (size_t)c4b * 4);
-  if (c4a < n4) explode4(p, gen, row, c4a, xa, amp, srow, oprow, (uint32_t)w1_elems, c4a < full4);
-  if (c4b < n4) explode4(p, gen, row, c4b, xb, amp, srow, oprow, (uint32_t)w1_elems, c4b < full4);
+  if (c4a < n4) explode4(p, gen, unit, k0, k1, c4a, xa, amp, srow, oprow, (uint32_t)w1_elems, c4a < full4);
+  if (c4b < n4) explode4(p, gen, unit, k0, k1, c4b, xb, amp, srow, oprow, (uint32_t)w1_elems, c4b < full4);
 }
 
 // Multi-guiding sparks, reading: group q of firework i has ranked index
@@ -133,8 +143,12 @@ __global__ void __launch_bounds__(kThreads) k_guide(Problem p, uint32_t gen, con
                                                     const int32_t* __restrict__ bottom,
                                                     float* __restrict__ guides,
                                                     __nv_bfloat16* __restrict__ op, int64_t w1_elems) {
-  const int i = blockIdx.z;
-  const int gq = i * p.m + blockIdx.y;  // i * m + q
+  const int i = blockIdx.z;               // global firework z = b * mu + i_local
+  const int gq = i * p.m + blockIdx.y;    // global guiding row z * m + q
+  const int run = i / p.mu;
+  const uint32_t gunit = (uint32_t)((i - run * p.mu) * p.m + (int)blockIdx.y);  // i_local * m + q
+  uint32_t k0, k1;
+  run_key(p, run, k0, k1);
   const int64_t c4 = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   const int64_t d0 = c4 * 4;
   if (d0 >= p.Dp) return;
@@ -188,7 +202,7 @@ __global__ void __launch_bounds__(kThreads) k_guide(Problem p, uint32_t gen, con
     out_of_bounds |= (d0 + l < p.D) && (v[l] < p.lb || v[l] > p.ub);
   }
   if (out_of_bounds) {
-    const uint4 r2 = philox4x32_10(make_uint4((uint32_t)c4, (uint32_t)gq, gen, kGmap), p.key0, p.key1);
+    const uint4 r2 = philox4x32_10(make_uint4((uint32_t)c4, gunit, gen, kGmap), k0, k1);
 #pragma unroll
     for (int l = 0; l < 4; ++l)
       if (v[l] < p.lb || v[l] > p.ub) v[l] = map_coord(lane_of(x4, l), amp, p.lb, p.ub, u24(lane_of(r2, l)));
@@ -219,14 +233,14 @@ inline unsigned blocks_for(int64_t n4) { return (unsigned)((n4 + kThreads - 1) /
 }  // namespace
 
 int launch_init(const Problem& p, float* fw_x, float* fw_amp, cudaStream_t s) {
-  dim3 grid(blocks_for(p.Dp / 4), p.mu);
+  dim3 grid(blocks_for(p.Dp / 4), p.B * p.mu);
   k_init<<<grid, kThreads, 0, s>>>(p, fw_x, fw_amp);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 int launch_explode(const Problem& p, uint32_t gen, const float* fw_x, const float* fw_amp, float* sparks,
                    __nv_bfloat16* op, int64_t w1_elems, cudaStream_t s) {
-  dim3 grid((unsigned)((p.Dp / 4 + 2 * kThreads - 1) / (2 * kThreads)), p.lam, p.mu);
+  dim3 grid((unsigned)((p.Dp / 4 + 2 * kThreads - 1) / (2 * kThreads)), p.lam, p.B * p.mu);
   k_explode<<<grid, kThreads, 0, s>>>(p, gen, fw_x, fw_amp, sparks, op, w1_elems);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
@@ -234,7 +248,7 @@ int launch_explode(const Problem& p, uint32_t gen, const float* fw_x, const floa
 int launch_guide(const Problem& p, uint32_t gen, const float* fw_x, const float* fw_amp, const float* sparks,
                  const int32_t* top, const int32_t* bottom, float* guides, __nv_bfloat16* op_guides,
                  int64_t w1_elems, cudaStream_t s) {
-  dim3 grid(blocks_for(p.Dp / 4), p.m, p.mu);
+  dim3 grid(blocks_for(p.Dp / 4), p.m, p.B * p.mu);
   k_guide<<<grid, kThreads, 0, s>>>(p, gen, fw_x, fw_amp, sparks, top, bottom, guides, op_guides, w1_elems);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }

@@ -54,7 +54,8 @@ struct mgfwa_handle {
   double* ce64 = nullptr;
   double* f64 = nullptr;
   uint32_t* status = nullptr;
-  int64_t P = 0;       // sparks per generation
+  int64_t P = 0;       // sparks per generation of one run
+  int64_t PA = 0;      // sparks per generation of all runs (rows of the spark buffers)
   int32_t mtiles = 0;  // sample tiles of 128
   int64_t evals = 0;
   int32_t gen = 0;
@@ -188,7 +189,7 @@ __nv_bfloat16* op_rows(mgfwa_t* h, int64_t first) {
 
 mgfwa_status run_phase(mgfwa_t* h, int32_t phase) {
   const Problem& p = h->p;
-  const int64_t n_e = (int64_t)p.mu * p.lam;
+  const int64_t n_e = (int64_t)p.B * p.mu * p.lam;  // explosion rows of all runs
   const int32_t prec = h->cfg.precision;
   switch (phase) {
     case MGFWA_PHASE_EXPLODE: {
@@ -212,7 +213,7 @@ mgfwa_status run_phase(mgfwa_t* h, int32_t phase) {
       return MGFWA_OK;
     }
     case MGFWA_PHASE_EVAL_G:
-      return eval_rows(h, n_e, p.mu * p.m, prec);
+      return eval_rows(h, n_e, p.B * p.mu * p.m, prec);
     case MGFWA_PHASE_SELECT: {
       Mark mk(h, G_SELECT);
       MG_LAUNCH(h, launch_select(p, h->fit, h->fit + n_e, h->sparks, h->sparks + n_e * p.Dp, h->fw_x, h->fw_amp,
@@ -264,8 +265,11 @@ mgfwa_status validate(const mgfwa_config* c, const mgfwa_objective* o) {
                 c->guiding_per_firework);
   const int32_t g = c->sparks_per_firework / c->guiding_per_firework;
   if (g < 2 || g > 1024) return fail(nullptr, MGFWA_EINVAL, "group size lambda/m = %d must be in [2, 1024]", g);
-  const int64_t P = (int64_t)c->n_fireworks * (c->sparks_per_firework + c->guiding_per_firework);
-  if (P > 65535) return fail(nullptr, MGFWA_EINVAL, "mu (lambda + m) = %lld exceeds 65535", (long long)P);
+  if (c->n_runs < 1) return fail(nullptr, MGFWA_EINVAL, "n_runs must be >= 1");
+  if ((int64_t)c->n_runs * c->n_fireworks > 65535 || c->sparks_per_firework > 65535)
+    return fail(nullptr, MGFWA_EINVAL, "n_runs * mu and lambda must each be <= 65535");
+  const int64_t PA = (int64_t)c->n_runs * c->n_fireworks * (c->sparks_per_firework + c->guiding_per_firework);
+  if (PA > (1 << 24)) return fail(nullptr, MGFWA_EINVAL, "n_runs mu (lambda + m) = %lld exceeds 2^24", (long long)PA);
   if (!(c->sigma > 0.0f) || !(c->sigma <= 0.5f)) return fail(nullptr, MGFWA_EINVAL, "sigma must be in (0, 0.5]");
   if (c->eval_budget < c->n_fireworks) return fail(nullptr, MGFWA_EINVAL, "eval_budget below the mu initial evaluations");
   if (c->precision != MGFWA_FP32 && c->precision != MGFWA_BF16)
@@ -321,6 +325,7 @@ mgfwa_status mgfwa_config_init(mgfwa_config* cfg) {
   cfg->c_reduce = 0.9f;
   cfg->precision = MGFWA_FP32;
   cfg->elite_rescore = 0;
+  cfg->n_runs = 1;
   return MGFWA_OK;
 }
 
@@ -352,9 +357,10 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
   p.amp0 = cfg->amp_init > 0.0f ? cfg->amp_init : cfg->ub - cfg->lb;
   p.c_a = cfg->c_amplify;
   p.c_r = cfg->c_reduce;
-  p.key0 = (uint32_t)(cfg->seed & 0xffffffffu);
-  p.key1 = (uint32_t)(cfg->seed >> 32);
+  p.B = cfg->n_runs;
+  p.seed = cfg->seed;
   h->P = (int64_t)p.mu * (p.lam + p.m);
+  h->PA = (int64_t)p.B * h->P;
 
   Mlp& mlp = h->mlp;
   std::memset(&mlp, 0, sizeof(mlp));
@@ -386,18 +392,19 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
     h->X = carve<float>(cur, N * d_in);
     h->Xbf = want_op ? carve<__nv_bfloat16>(cur, N * d_in) : nullptr;
     h->y = carve<int32_t>(cur, N);
-    h->fw_x = carve<float>(cur, p.mu * p.Dp);
-    h->fw_amp = carve<float>(cur, p.mu);
-    h->fw_f = carve<float>(cur, p.mu);
-    h->sparks = carve<float>(cur, h->P * p.Dp);
-    h->op = want_op ? carve<__nv_bfloat16>(cur, h->P * mlp.w1_elems) : nullptr;
-    h->fit = carve<float>(cur, h->P);
-    h->partial = carve<float>(cur, (size_t)h->mtiles * h->P);
-    h->top = carve<int32_t>(cur, p.mu * p.m * p.k);
-    h->bottom = carve<int32_t>(cur, p.mu * p.m * p.k);
-    h->winner = carve<int32_t>(cur, p.mu);
-    h->best_x = carve<float>(cur, p.Dp);
-    h->best_f = carve<float>(cur, 1);
+    const int64_t F = (int64_t)p.B * p.mu;  // fireworks of all runs
+    h->fw_x = carve<float>(cur, F * p.Dp);
+    h->fw_amp = carve<float>(cur, F);
+    h->fw_f = carve<float>(cur, F);
+    h->sparks = carve<float>(cur, h->PA * p.Dp);
+    h->op = want_op ? carve<__nv_bfloat16>(cur, h->PA * mlp.w1_elems) : nullptr;
+    h->fit = carve<float>(cur, h->PA);
+    h->partial = carve<float>(cur, (size_t)h->mtiles * h->PA);
+    h->top = carve<int32_t>(cur, F * p.m * p.k);
+    h->bottom = carve<int32_t>(cur, F * p.m * p.k);
+    h->winner = carve<int32_t>(cur, F);
+    h->best_x = carve<float>(cur, (int64_t)p.B * p.Dp);
+    h->best_f = carve<float>(cur, p.B);
     h->ce64 = carve<double>(cur, N > 0 ? N : 1);
     h->f64 = carve<double>(cur, 1);
     h->status = carve<uint32_t>(cur, 1);
@@ -452,7 +459,7 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
     if (want_op) CREATE_LAUNCH(launch_f32_to_bf16(h->X, N * d_in, h->Xbf, h->stream), "X to BF16");
   }
   if (want_op) {
-    st = tc_plan(h->tc, h->mlp, h->op, h->sparks, p.Dp, h->P);
+    st = tc_plan(h->tc, h->mlp, h->op, h->sparks, p.Dp, h->PA);
     if (st != MGFWA_OK) {
       h->err = tc_last_error();
       return bail(st);
@@ -462,15 +469,16 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
   // Algorithm 1, init: mu fireworks uniform in the box, evaluated.
   CREATE_LAUNCH(launch_init(p, h->fw_x, h->fw_amp, h->stream), "init");
   TRACE("create: init launched");
-  if (cudaMemcpy2DAsync(h->sparks, sizeof(float) * p.Dp, h->fw_x, sizeof(float) * p.Dp, sizeof(float) * p.Dp, p.mu,
+  const int32_t F = p.B * p.mu;
+  if (cudaMemcpy2DAsync(h->sparks, sizeof(float) * p.Dp, h->fw_x, sizeof(float) * p.Dp, sizeof(float) * p.Dp, F,
                         cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
     return bail(cuda_fail(h, "stage init rows"));
-  if (want_op) CREATE_LAUNCH(launch_to_operand(h->sparks, p.Dp, p.mu, mlp.w1_elems, h->op, h->stream), "init operand");
+  if (want_op) CREATE_LAUNCH(launch_to_operand(h->sparks, p.Dp, F, mlp.w1_elems, h->op, h->stream), "init operand");
   TRACE("create: staged");
-  st = eval_rows(h, 0, p.mu, cfg->precision);
+  st = eval_rows(h, 0, F, cfg->precision);
   if (st != MGFWA_OK) return bail(st);
   TRACE("create: evaluated");
-  if (cudaMemcpyAsync(h->fw_f, h->fit, sizeof(float) * p.mu, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+  if (cudaMemcpyAsync(h->fw_f, h->fit, sizeof(float) * F, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
     return bail(cuda_fail(h, "init fitness"));
   CREATE_LAUNCH(launch_run_best_init(p, h->fw_x, h->fw_f, h->best_x, h->best_f, h->stream), "init best");
   h->evals = p.mu;
@@ -508,28 +516,50 @@ mgfwa_status mgfwa_run(mgfwa_t* h) {
   return check_status_word(h);
 }
 
-mgfwa_status mgfwa_best(mgfwa_t* h, float* x_out, double* f_out, int64_t* evals_out) {
+mgfwa_status mgfwa_best_run(mgfwa_t* h, int32_t run, float* x_out, double* f_out, int64_t* evals_out) {
   mgfwa_status st = check_usable(h);
   if (st != MGFWA_OK) return st;
+  if (run < 0 || run >= h->p.B) return fail(h, MGFWA_EINVAL, "run %d out of range [0, %d)", run, h->p.B);
+  const float* bx = h->best_x + (int64_t)run * h->p.Dp;
   if (f_out) {
     if (h->kind == MGFWA_OBJ_SPHERE)
-      MG_LAUNCH(h, launch_sphere_f64(h->best_x, h->p.D, h->f64, h->stream), "FP64 sphere");
+      MG_LAUNCH(h, launch_sphere_f64(bx, h->p.D, h->f64, h->stream), "FP64 sphere");
     else
-      MG_LAUNCH(h, launch_fitness_f64(h->mlp, h->best_x, h->ce64, h->f64, h->stream), "FP64 fitness");
+      MG_LAUNCH(h, launch_fitness_f64(h->mlp, bx, h->ce64, h->f64, h->stream), "FP64 fitness");
     if (cudaMemcpyAsync(f_out, h->f64, sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
       return cuda_fail(h, "read best fitness");
   }
-  if (x_out && cudaMemcpyAsync(x_out, h->best_x, sizeof(float) * h->p.D, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+  if (x_out && cudaMemcpyAsync(x_out, bx, sizeof(float) * h->p.D, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
     return cuda_fail(h, "read best position");
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h, "best synchronise");
   if (evals_out) *evals_out = h->evals;
   return check_status_word(h);
 }
 
+mgfwa_status mgfwa_best(mgfwa_t* h, float* x_out, double* f_out, int64_t* evals_out) {
+  mgfwa_status st = check_usable(h);
+  if (st != MGFWA_OK) return st;
+  int32_t run = 0;
+  if (h->p.B > 1) {
+    // the run whose FP32 best-so-far is lowest (the first on ties)
+    std::vector<float> bf((size_t)h->p.B);
+    if (cudaMemcpyAsync(bf.data(), h->best_f, sizeof(float) * h->p.B, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+      return cuda_fail(h, "read run bests");
+    for (int32_t b = 1; b < h->p.B; ++b) {
+      const float kb = std::isnan(bf[b]) ? INFINITY : bf[b];
+      const float kr = std::isnan(bf[run]) ? INFINITY : bf[run];
+      if (kb < kr) run = b;
+    }
+  }
+  return mgfwa_best_run(h, run, x_out, f_out, evals_out);
+}
+
 mgfwa_status mgfwa_evaluate(mgfwa_t* h, const float* xs, int64_t count, int32_t precision, float* f_out) {
   mgfwa_status st = check_usable(h);
   if (st != MGFWA_OK) return st;
-  if (!xs || !f_out || count < 0 || count > h->P) return fail(h, MGFWA_EINVAL, "evaluate: bad arguments (count <= %lld)", (long long)h->P);
+  if (!xs || !f_out || count < 0 || count > h->PA)
+    return fail(h, MGFWA_EINVAL, "evaluate: bad arguments (count <= %lld)", (long long)h->PA);
   if (precision != MGFWA_FP32 && precision != MGFWA_BF16) return fail(h, MGFWA_EINVAL, "evaluate: bad precision");
   if (use_tc(h, precision) && !h->op) return fail(h, MGFWA_EINVAL, "evaluate: handle was created without the BF16 path");
   if (h->next_phase != MGFWA_PHASE_EXPLODE) return fail(h, MGFWA_EINVAL, "a debug generation is in progress");
@@ -553,9 +583,10 @@ mgfwa_status mgfwa_get_info(const mgfwa_t* h, mgfwa_info* info) {
   info->generations = h->gen;
   info->k = h->p.k;
   info->dim_padded = h->p.Dp;
-  info->sparks_per_gen = h->P;
+  info->sparks_per_gen = h->PA;
   info->device_bytes = (int64_t)h->arena_bytes;
   info->kernel_launches = h->launches;
+  info->n_runs = h->p.B;
   return MGFWA_OK;
 }
 
@@ -601,22 +632,23 @@ struct BufView {
 
 bool buffer_view(mgfwa_t* h, int32_t buf, BufView* v) {
   const Problem& p = h->p;
-  const int64_t n_e = (int64_t)p.mu * p.lam;
+  const int64_t F = (int64_t)p.B * p.mu;
+  const int64_t n_e = F * p.lam;
   const int64_t rb = sizeof(float) * p.D, pitch = sizeof(float) * p.Dp;
   *v = BufView{nullptr, 0, 0, 0, 0};
   switch (buf) {
-    case MGFWA_BUF_FW_X: *v = {h->fw_x, p.mu, rb, pitch, 0}; return true;
-    case MGFWA_BUF_FW_AMP: *v = {h->fw_amp, 0, 0, 0, (int64_t)sizeof(float) * p.mu}; return true;
-    case MGFWA_BUF_FW_F: *v = {h->fw_f, 0, 0, 0, (int64_t)sizeof(float) * p.mu}; return true;
+    case MGFWA_BUF_FW_X: *v = {h->fw_x, F, rb, pitch, 0}; return true;
+    case MGFWA_BUF_FW_AMP: *v = {h->fw_amp, 0, 0, 0, (int64_t)sizeof(float) * F}; return true;
+    case MGFWA_BUF_FW_F: *v = {h->fw_f, 0, 0, 0, (int64_t)sizeof(float) * F}; return true;
     case MGFWA_BUF_SPARKS: *v = {h->sparks, n_e, rb, pitch, 0}; return true;
-    case MGFWA_BUF_GUIDES: *v = {h->sparks + n_e * p.Dp, (int64_t)p.mu * p.m, rb, pitch, 0}; return true;
+    case MGFWA_BUF_GUIDES: *v = {h->sparks + n_e * p.Dp, F * p.m, rb, pitch, 0}; return true;
     case MGFWA_BUF_FIT_E: *v = {h->fit, 0, 0, 0, (int64_t)sizeof(float) * n_e}; return true;
-    case MGFWA_BUF_FIT_G: *v = {h->fit + n_e, 0, 0, 0, (int64_t)sizeof(float) * p.mu * p.m}; return true;
-    case MGFWA_BUF_TOP: *v = {h->top, 0, 0, 0, (int64_t)sizeof(int32_t) * p.mu * p.m * p.k}; return true;
-    case MGFWA_BUF_BOTTOM: *v = {h->bottom, 0, 0, 0, (int64_t)sizeof(int32_t) * p.mu * p.m * p.k}; return true;
-    case MGFWA_BUF_WINNER: *v = {h->winner, 0, 0, 0, (int64_t)sizeof(int32_t) * p.mu}; return true;
-    case MGFWA_BUF_BEST_X: *v = {h->best_x, 1, rb, pitch, 0}; return true;
-    case MGFWA_BUF_BEST_F: *v = {h->best_f, 0, 0, 0, (int64_t)sizeof(float)}; return true;
+    case MGFWA_BUF_FIT_G: *v = {h->fit + n_e, 0, 0, 0, (int64_t)sizeof(float) * F * p.m}; return true;
+    case MGFWA_BUF_TOP: *v = {h->top, 0, 0, 0, (int64_t)sizeof(int32_t) * F * p.m * p.k}; return true;
+    case MGFWA_BUF_BOTTOM: *v = {h->bottom, 0, 0, 0, (int64_t)sizeof(int32_t) * F * p.m * p.k}; return true;
+    case MGFWA_BUF_WINNER: *v = {h->winner, 0, 0, 0, (int64_t)sizeof(int32_t) * F}; return true;
+    case MGFWA_BUF_BEST_X: *v = {h->best_x, p.B, rb, pitch, 0}; return true;
+    case MGFWA_BUF_BEST_F: *v = {h->best_f, 0, 0, 0, (int64_t)sizeof(float) * p.B}; return true;
   }
   return false;
 }

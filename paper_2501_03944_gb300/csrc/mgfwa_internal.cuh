@@ -13,14 +13,24 @@ namespace mgfwa {
 constexpr uint32_t kInit = 0, kExplode = 1, kMap = 2, kGmap = 3;
 
 // Scalar parameters of one run, passed by value to the kernels.
+// Fireworks of all runs are numbered globally, z = b * mu + i (run b,
+// firework i); explosion rows are z * lam + j, guiding rows z * m + q.
 struct Problem {
   int64_t D;       // search dimension
   int64_t Dp;      // padded row stride (floats), a multiple of 64
   float lb, ub;
   int32_t mu, lam, m, g, k;
+  int32_t B;       // independent runs
   float beta, amp0, c_a, c_r;
-  uint32_t key0, key1;  // Philox key: low and high words of the seed
+  uint64_t seed;   // run b draws from Philox keyed by seed + b
 };
+
+// Philox key of run b: low and high words of seed + b.
+__host__ __device__ __forceinline__ void run_key(const Problem& p, int b, uint32_t& k0, uint32_t& k1) {
+  const uint64_t s = p.seed + (uint64_t)b;
+  k0 = (uint32_t)(s & 0xffffffffu);
+  k1 = (uint32_t)(s >> 32);
+}
 
 // The MLP objective as the kernels see it.
 struct Mlp {
@@ -116,6 +126,7 @@ int launch_guide(const Problem& p, uint32_t gen, const float* fw_x, const float*
                  const float* sparks, const int32_t* top, const int32_t* bottom, float* guides,
                  __nv_bfloat16* op_guides, int64_t w1_elems, cudaStream_t s);
 
+// Per run: best-so-far over its fireworks (init: the first minimum).
 int launch_run_best_init(const Problem& p, const float* fw_x, const float* fw_f, float* best_x, float* best_f,
                          cudaStream_t s);
 

@@ -39,33 +39,23 @@ def test_exports_every_declared_symbol(pkg):
 
 
 def test_structure_layout_matches_header(pkg, tmp_path):
+    """Compile a C program against the header and compare every field offset with the ctypes mirror."""
+    import ctypes
+    classes = (pkg.mgfwa_config, pkg.mgfwa_objective, pkg.mgfwa_info)
+    body = []
+    for cls in classes:
+        body.append(f'  printf("{cls.__name__} %zu\\n", sizeof({cls.__name__}));')
+        for fname, _ in cls._fields_:
+            body.append(f'  printf("{cls.__name__}.{fname} %zu\\n", offsetof({cls.__name__}, {fname}));')
     src = tmp_path / "layout.c"
-    src.write_text(r"""
-#include <stddef.h>
-#include <stdio.h>
-#include "mgfwa.h"
-#define F(T, f) printf("%s.%s %zu\n", #T, #f, offsetof(T, f));
-int main(void) {
-  printf("mgfwa_config %zu\n", sizeof(mgfwa_config));
-  printf("mgfwa_objective %zu\n", sizeof(mgfwa_objective));
-  printf("mgfwa_info %zu\n", sizeof(mgfwa_info));
-  F(mgfwa_config, dim) F(mgfwa_config, lb) F(mgfwa_config, ub) F(mgfwa_config, n_fireworks)
-  F(mgfwa_config, sparks_per_firework) F(mgfwa_config, guiding_per_firework) F(mgfwa_config, sigma)
-  F(mgfwa_config, boost) F(mgfwa_config, amp_init) F(mgfwa_config, c_amplify) F(mgfwa_config, c_reduce)
-  F(mgfwa_config, eval_budget) F(mgfwa_config, seed) F(mgfwa_config, precision) F(mgfwa_config, elite_rescore)
-  F(mgfwa_objective, kind) F(mgfwa_objective, n_layers) F(mgfwa_objective, widths) F(mgfwa_objective, acts)
-  F(mgfwa_objective, n_samples) F(mgfwa_objective, X) F(mgfwa_objective, y)
-  F(mgfwa_info, evals) F(mgfwa_info, generations) F(mgfwa_info, k) F(mgfwa_info, dim_padded)
-  F(mgfwa_info, sparks_per_gen) F(mgfwa_info, device_bytes) F(mgfwa_info, kernel_launches)
-  return 0;
-}
-""")
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"mgfwa.h\"\nint main(void) {\n" +
+                   "\n".join(body) + "\n  return 0;\n}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
     want = dict(l.rsplit(" ", 1) for l in lines if l)
-    for cls in (pkg.mgfwa_config, pkg.mgfwa_objective, pkg.mgfwa_info):
-        assert int(want[cls.__name__]) == __import__("ctypes").sizeof(cls), cls.__name__
+    for cls in classes:
+        assert int(want[cls.__name__]) == ctypes.sizeof(cls), cls.__name__
         for fname, _ in cls._fields_:
             assert int(want[f"{cls.__name__}.{fname}"]) == getattr(cls, fname).offset, (cls.__name__, fname)
 
@@ -83,7 +73,7 @@ def test_create_rejects_bad_configs_without_a_gpu(pkg):
     w = W.MLP_8_16_3
     X, y = W.make_data(w)
     bad = [dict(sparks_per_firework=41), dict(lb=1.0, ub=-1.0), dict(dim=100), dict(eval_budget=2),
-           dict(sigma=0.0), dict(precision=7)]
+           dict(sigma=0.0), dict(precision=7), dict(n_runs=0)]
     for over in bad:
         with pytest.raises(pkg.MgfwaError) as e:
             pkg.Mgfwa.for_workload(w, 0, X=X, y=y, **over)
