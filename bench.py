@@ -222,6 +222,31 @@ def gpu_arm(args):
     _, best_f, evals = run.best()
     run.close()
 
+    def timed_generations(handle_kw, steps):
+        """sparks/s of `steps` generations of a fresh handle (after 3 warm-up generations)."""
+        wk = W.scaled(WORKLOAD, eval_budget=W.budget_for_generations(
+            WORKLOAD.n_fireworks, WORKLOAD.sparks_per_firework, WORKLOAD.guiding_per_firework, steps + 5))
+        h = pkg.Mgfwa.for_workload(wk, seed + 17, X=X, y=y, stream=stream.cuda_stream, **handle_kw)
+        h.step(3)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        h.step(steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b)
+        n = h.info().sparks_per_gen * steps
+        h.close()
+        return {"value": n / (t / 1e3), "ms_per_step": t / steps}
+
+    extra = {}
+    if not args.no_extras:
+        # the plain FP32 one-run path the low-precision path is compared with
+        extra["fp32_one_run"] = dict(timed_generations({"precision": pkg.MGFWA_FP32}, 5), precision="fp32")
+        # 8 independent runs of the same workload in one handle (one fitness launch per generation)
+        extra["batched_8_runs"] = dict(timed_generations({"precision": prec, "n_runs": 8}, max(5, args.steps // 2)),
+                                       runs=8, precision=args.precision)
+
     # end to end through the C ABI with host buffers: create (copies X, y from pinned host memory),
     # K generations, best position + FP64 loss back to the host, destroy.
     e2e_s = None
@@ -295,7 +320,7 @@ def gpu_arm(args):
                     "d2h_bytes_per_step": (4 * D + 8) / args.steps,
                     "note": "create (X, y from pinned host) + K generations + best (x, FP64 loss) + destroy"},
                 "roofline": roof, "hbm_kernels": hbm, "kernels": kernels,
-                "best_f_fp64": best_f, "evals": evals, "cpu_baseline": cb}
+                "best_f_fp64": best_f, "evals": evals, "cpu_baseline": cb, **extra}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -311,6 +336,7 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=("bf16", "fp32"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end request (profiling runs)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP32 and batched comparison runs")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -72,7 +72,8 @@ typedef struct {
   int64_t eval_budget;          /* total evaluations, including the mu initial ones */
   uint64_t seed;                /* Philox key */
   int32_t precision;            /* mgfwa_precision */
-  int32_t elite_rescore;        /* reserved: re-score elite candidates in FP32 (low precision only) */
+  int32_t elite_rescore;        /* E in [0, 8], <= lambda + m: with BF16, each firework's E best candidates (by
+                                   BF16 fitness) are re-scored in FP32 before selection (default 2; 0 = off) */
   int32_t n_runs;               /* B >= 1 independent runs of the same problem, stepped together (the
                                    batch dimension of Table 1, Sec. 3); run b uses seed + b */
 } mgfwa_config;
@@ -91,7 +92,7 @@ typedef struct {
 typedef struct mgfwa_handle mgfwa_t;
 
 /* Fill *cfg with the defaults (beta 1, A0 = ub - lb once bounds are set,
- * C_a 1.2, C_r 0.9, sigma 0.2, FP32, one run).  Fields the caller must still set:
+ * C_a 1.2, C_r 0.9, sigma 0.2, FP32, two elite re-scores, one run).  Fields the caller must still set:
  * dim, lb, ub, n_fireworks, sparks_per_firework, guiding_per_firework,
  * eval_budget, seed.  amp_init <= 0 means ub - lb. */
 MGFWA_API mgfwa_status mgfwa_config_init(mgfwa_config* cfg);

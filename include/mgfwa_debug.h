@@ -23,12 +23,14 @@ typedef enum {
   MGFWA_PHASE_RANK = 2,    /* per firework and guiding group: top-k / bottom-k indices */
   MGFWA_PHASE_GUIDE = 3,   /* mu*m guiding sparks + random mapping (Alg. 1, multi-guiding) */
   MGFWA_PHASE_EVAL_G = 4,  /* fitness of the guiding sparks */
-  MGFWA_PHASE_SELECT = 5   /* per-firework selection, amplitude update, run best, counters */
+  MGFWA_PHASE_RESCORE = 5, /* low precision only: FP32 re-score of each firework's elite candidates */
+  MGFWA_PHASE_SELECT = 6   /* per-firework selection, amplitude update, run best, counters */
 } mgfwa_phase;
 
 /* Enqueue one phase.  Phases must come in the order above, starting with
- * EXPLODE; EINVAL otherwise, and EBUDGET if EXPLODE would exceed the
- * budget.  Asynchronous. */
+ * EXPLODE; RESCORE may be skipped (selection then uses the fitness as
+ * evaluated or injected).  EINVAL otherwise, and EBUDGET if EXPLODE would
+ * exceed the budget.  Asynchronous. */
 MGFWA_API mgfwa_status mgfwa_debug_phase(mgfwa_t* h, int32_t phase);
 
 /* Buffers of all B runs, run-major (B = 1 for a single run): firework
@@ -58,8 +60,9 @@ MGFWA_API mgfwa_status mgfwa_debug_write(mgfwa_t* h, int32_t buf, const void* ho
  * here); mgfwa_debug_kernel_times() synchronises and returns, per group, the
  * summed milliseconds and the number of launches since the last enable.
  * Groups: 0 explode, 1 explosion fitness (main kernel), 2 fitness finish,
- * 3 rank, 4 guide, 5 guiding fitness (main kernel), 6 select + run best. */
-#define MGFWA_N_KERNEL_GROUPS 7
+ * 3 rank, 4 guide, 5 guiding fitness (main kernel), 6 select + run best,
+ * 7 elite FP32 re-score (pick + fitness + finish). */
+#define MGFWA_N_KERNEL_GROUPS 8
 MGFWA_API mgfwa_status mgfwa_debug_profile(mgfwa_t* h, int32_t enable);
 MGFWA_API mgfwa_status mgfwa_debug_kernel_times(mgfwa_t* h, double* ms_out, int64_t* launches_out);
 

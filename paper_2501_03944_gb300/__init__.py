@@ -24,7 +24,7 @@ MGFWA_FP32, MGFWA_BF16, MGFWA_FP8 = 0, 1, 2
 MGFWA_OBJ_MLP_CE, MGFWA_OBJ_SPHERE = 0, 1
 MGFWA_ACT_TANH, MGFWA_ACT_RELU = 0, 1
 (MGFWA_PHASE_EXPLODE, MGFWA_PHASE_EVAL_E, MGFWA_PHASE_RANK, MGFWA_PHASE_GUIDE, MGFWA_PHASE_EVAL_G,
- MGFWA_PHASE_SELECT) = range(6)
+ MGFWA_PHASE_RESCORE, MGFWA_PHASE_SELECT) = range(7)
 (MGFWA_BUF_FW_X, MGFWA_BUF_FW_AMP, MGFWA_BUF_FW_F, MGFWA_BUF_SPARKS, MGFWA_BUF_GUIDES, MGFWA_BUF_FIT_E,
  MGFWA_BUF_FIT_G, MGFWA_BUF_TOP, MGFWA_BUF_BOTTOM, MGFWA_BUF_WINNER, MGFWA_BUF_BEST_X, MGFWA_BUF_BEST_F) = range(12)
 
@@ -35,8 +35,9 @@ EXPORTS = ("mgfwa_config_init", "mgfwa_create", "mgfwa_step", "mgfwa_run", "mgfw
            "mgfwa_evaluate",
            "mgfwa_get_info", "mgfwa_destroy", "mgfwa_last_error", "mgfwa_debug_phase", "mgfwa_debug_read",
            "mgfwa_debug_write", "mgfwa_debug_profile", "mgfwa_debug_kernel_times", "mgfwa_evaluate_fp32_noalloc")
-N_KERNEL_GROUPS = 7
-KERNEL_GROUPS = ("explode", "fitness_explosion", "fitness_finish", "rank", "guide", "fitness_guiding", "select")
+N_KERNEL_GROUPS = 8
+KERNEL_GROUPS = ("explode", "fitness_explosion", "fitness_finish", "rank", "guide", "fitness_guiding", "select",
+                 "elite_rescore")
 
 
 class mgfwa_config(ctypes.Structure):
@@ -227,7 +228,8 @@ class Mgfwa:
 
     def __init__(self, *, dim, lb, ub, n_fireworks, sparks_per_firework, guiding_per_firework, eval_budget,
                  seed, sigma=0.2, boost=1.0, amp_init=0.0, c_amplify=1.2, c_reduce=0.9, precision=MGFWA_FP32,
-                 kind=MGFWA_OBJ_MLP_CE, widths=(), acts=(), X=None, y=None, stream: int = 0, n_runs: int = 1):
+                 kind=MGFWA_OBJ_MLP_CE, widths=(), acts=(), X=None, y=None, stream: int = 0, n_runs: int = 1,
+                 elite_rescore: int = 2):
         cfg = mgfwa_config_init()
         cfg.dim, cfg.lb, cfg.ub = dim, lb, ub
         cfg.n_fireworks, cfg.sparks_per_firework, cfg.guiding_per_firework = (
@@ -235,6 +237,7 @@ class Mgfwa:
         cfg.sigma, cfg.boost, cfg.amp_init, cfg.c_amplify, cfg.c_reduce = sigma, boost, amp_init, c_amplify, c_reduce
         cfg.eval_budget, cfg.seed, cfg.precision = eval_budget, seed, precision
         cfg.n_runs = n_runs
+        cfg.elite_rescore = elite_rescore
         self.cfg = cfg
         self._obj = _ObjectiveBuffers(kind, widths, acts, X, y)
         self.dim = dim

@@ -136,7 +136,49 @@ __global__ void __launch_bounds__(kSelThreads) k_run_best(Problem p, int init, c
   for (int64_t e = threadIdx.x; e < p.Dp / 4; e += blockDim.x) dst[e] = src[e];
 }
 
+// One warp per firework: the E best candidates in the (fitness, index)
+// order, picked one at a time (E is small), each pick excluding the
+// previous ones.
+__global__ void k_elite_pick(Problem p, const float* __restrict__ fit_e, const float* __restrict__ fit_g,
+                             int32_t E, int32_t* __restrict__ elite) {
+  const int z = blockIdx.x;
+  const int lane = threadIdx.x;
+  const int n_cand = p.lam + p.m;
+  const int64_t n_e = (int64_t)p.B * p.mu * p.lam;
+  float prev_f = 0.0f;
+  int prev_c = -1;
+  for (int e = 0; e < E; ++e) {
+    float bf = 0.0f;
+    int bc = -1;
+    for (int c = lane; c < n_cand; c += 32) {
+      const float f = c < p.lam ? fit_e[(int64_t)z * p.lam + c] : fit_g[(int64_t)z * p.m + (c - p.lam)];
+      if (prev_c >= 0 && !before(prev_f, prev_c, f, c)) continue;  // already picked
+      take_if_before(bf, bc, f, c);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float of = __shfl_xor_sync(0xffffffffu, bf, off);
+      const int oc = __shfl_xor_sync(0xffffffffu, bc, off);
+      take_if_before(bf, bc, of, oc);
+    }
+    if (lane == 0) {
+      int32_t row = -1;
+      if (bc >= 0) row = bc < p.lam ? (int32_t)((int64_t)z * p.lam + bc) : (int32_t)(n_e + (int64_t)z * p.m + (bc - p.lam));
+      elite[(int64_t)z * E + e] = row;
+    }
+    prev_f = bf;
+    prev_c = bc;
+  }
+}
+
 }  // namespace
+
+int launch_elite_pick(const Problem& p, const float* fit_e, const float* fit_g, int32_t E, int32_t* elite,
+                      cudaStream_t s) {
+  if (E <= 0) return 0;
+  k_elite_pick<<<p.B * p.mu, 32, 0, s>>>(p, fit_e, fit_g, E, elite);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
 
 int launch_rank(const Problem& p, const float* fit_e, int32_t* top, int32_t* bottom, cudaStream_t s) {
   const int threads = p.g >= 256 ? 256 : ((p.g + 31) / 32) * 32;

@@ -49,6 +49,8 @@ struct mgfwa_handle {
   int32_t* top = nullptr;
   int32_t* bottom = nullptr;
   int32_t* winner = nullptr;
+  int32_t* elite = nullptr;     // [B*mu*E] spark rows picked for the FP32 re-score
+  float* hidden = nullptr;      // [B*mu*E][N][h1] FP32 hidden layer of the re-scored sparks
   float* best_x = nullptr;
   float* best_f = nullptr;
   double* ce64 = nullptr;
@@ -127,7 +129,7 @@ mgfwa_status cuda_fail(mgfwa_t* h, const char* what) {
 
 int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
-enum { G_EXPLODE = 0, G_FIT_E = 1, G_FINISH = 2, G_RANK = 3, G_GUIDE = 4, G_FIT_G = 5, G_SELECT = 6 };
+enum { G_EXPLODE = 0, G_FIT_E = 1, G_FINISH = 2, G_RANK = 3, G_GUIDE = 4, G_FIT_G = 5, G_SELECT = 6, G_RESCORE = 7 };
 
 // Brackets one kernel group with events when profiling is on.
 struct Mark {
@@ -214,6 +216,18 @@ mgfwa_status run_phase(mgfwa_t* h, int32_t phase) {
     }
     case MGFWA_PHASE_EVAL_G:
       return eval_rows(h, n_e, p.B * p.mu * p.m, prec);
+    case MGFWA_PHASE_RESCORE: {
+      // low precision: each firework's elite candidates get their fitness in FP32
+      const int32_t E = h->cfg.elite_rescore;
+      if (prec == MGFWA_FP32 || E <= 0 || h->kind != MGFWA_OBJ_MLP_CE) return MGFWA_OK;
+      const int32_t count = p.B * p.mu * E;
+      Mark mk(h, G_RESCORE);
+      MG_LAUNCH(h, launch_elite_pick(p, h->fit, h->fit + n_e, E, h->elite, h->stream), "elite pick");
+      MG_LAUNCH(h, launch_fitness_small(h->mlp, h->sparks, p.Dp, count, h->elite, h->hidden, h->partial, h->fit,
+                                        h->stream),
+                "elite FP32 fitness");
+      return MGFWA_OK;
+    }
     case MGFWA_PHASE_SELECT: {
       Mark mk(h, G_SELECT);
       MG_LAUNCH(h, launch_select(p, h->fit, h->fit + n_e, h->sparks, h->sparks + n_e * p.Dp, h->fw_x, h->fw_amp,
@@ -266,6 +280,9 @@ mgfwa_status validate(const mgfwa_config* c, const mgfwa_objective* o) {
   const int32_t g = c->sparks_per_firework / c->guiding_per_firework;
   if (g < 2 || g > 1024) return fail(nullptr, MGFWA_EINVAL, "group size lambda/m = %d must be in [2, 1024]", g);
   if (c->n_runs < 1) return fail(nullptr, MGFWA_EINVAL, "n_runs must be >= 1");
+  if (c->elite_rescore < 0 || c->elite_rescore > 8 ||
+      c->elite_rescore > c->sparks_per_firework + c->guiding_per_firework)
+    return fail(nullptr, MGFWA_EINVAL, "elite_rescore must be in [0, min(8, lambda + m)]");
   if ((int64_t)c->n_runs * c->n_fireworks > 65535 || c->sparks_per_firework > 65535)
     return fail(nullptr, MGFWA_EINVAL, "n_runs * mu and lambda must each be <= 65535");
   const int64_t PA = (int64_t)c->n_runs * c->n_fireworks * (c->sparks_per_firework + c->guiding_per_firework);
@@ -324,7 +341,7 @@ mgfwa_status mgfwa_config_init(mgfwa_config* cfg) {
   cfg->c_amplify = 1.2f;
   cfg->c_reduce = 0.9f;
   cfg->precision = MGFWA_FP32;
-  cfg->elite_rescore = 0;
+  cfg->elite_rescore = 2;
   cfg->n_runs = 1;
   return MGFWA_OK;
 }
@@ -403,6 +420,9 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
     h->top = carve<int32_t>(cur, F * p.m * p.k);
     h->bottom = carve<int32_t>(cur, F * p.m * p.k);
     h->winner = carve<int32_t>(cur, F);
+    h->elite = carve<int32_t>(cur, F * (cfg->elite_rescore > 0 ? cfg->elite_rescore : 1));
+    const bool rescore = want_op && cfg->elite_rescore > 0;
+    h->hidden = rescore ? carve<float>(cur, F * cfg->elite_rescore * N * mlp.widths[1]) : nullptr;
     h->best_x = carve<float>(cur, (int64_t)p.B * p.Dp);
     h->best_f = carve<float>(cur, p.B);
     h->ce64 = carve<double>(cur, N > 0 ? N : 1);
@@ -475,7 +495,8 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
     return bail(cuda_fail(h, "stage init rows"));
   if (want_op) CREATE_LAUNCH(launch_to_operand(h->sparks, p.Dp, F, mlp.w1_elems, h->op, h->stream), "init operand");
   TRACE("create: staged");
-  st = eval_rows(h, 0, F, cfg->precision);
+  // with an FP32 elite re-score the initial fireworks are scored in FP32 too
+  st = eval_rows(h, 0, F, cfg->elite_rescore > 0 ? MGFWA_FP32 : cfg->precision);
   if (st != MGFWA_OK) return bail(st);
   TRACE("create: evaluated");
   if (cudaMemcpyAsync(h->fw_f, h->fit, sizeof(float) * F, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
@@ -612,7 +633,8 @@ const char* mgfwa_last_error(const mgfwa_t* h) {
 mgfwa_status mgfwa_debug_phase(mgfwa_t* h, int32_t phase) {
   mgfwa_status st = check_usable(h);
   if (st != MGFWA_OK) return st;
-  if (phase != h->next_phase)
+  const bool skip_rescore = phase == MGFWA_PHASE_SELECT && h->next_phase == MGFWA_PHASE_RESCORE;
+  if (phase != h->next_phase && !skip_rescore)
     return fail(h, MGFWA_EINVAL, "phase %d out of order (expected %d)", phase, h->next_phase);
   if (phase == MGFWA_PHASE_EXPLODE && !budget_allows(h)) return fail(h, MGFWA_EBUDGET, "budget spent");
   st = run_phase(h, phase);

@@ -134,16 +134,32 @@ int launch_select(const Problem& p, const float* fit_e, const float* fit_g, cons
                   const float* guides, float* fw_x, float* fw_amp, float* fw_f, int32_t* winner,
                   float* best_x, float* best_f, cudaStream_t s);
 
-// FP32 CUDA-core fitness of `count` rows (stride `ld` floats): per-(m-tile,
-// row) partial cross-entropy sums into `partial` [mtiles][count] (the mean
-// is taken by launch_fitness_finish).
+// FP32 CUDA-core fitness of `count` rows (stride `ld` floats; row r is
+// rows[idx[r]] when idx is given): per-(m-tile, r) partial cross-entropy
+// sums into `partial` [mtiles][count] (the mean is taken by
+// launch_fitness_finish).
 int launch_fitness_simt_main(const Mlp& mlp, const float* rows, int64_t ld, int32_t count, float* partial,
-                             cudaStream_t s);
+                             cudaStream_t s, const int32_t* idx = nullptr);
 size_t fitness_simt_smem_bytes(const Mlp& mlp);
 
-// fit[r] = mean over m-tiles of partial: fixed-order FP32 sum / N.
+// fit[r] (fit[idx[r]] when idx is given) = mean over m-tiles of partial:
+// fixed-order FP32 sum / N.
 int launch_fitness_finish(const float* partial, int32_t mtiles, int32_t count, int64_t N, float* fit,
-                          cudaStream_t s);
+                          cudaStream_t s, const int32_t* idx = nullptr);
+
+// FP32 fitness of a few rows of a two-layer net (rows[idx[r]]), written to
+// fit[idx[r]]: layer 1 on small tiles into hidden[count][h1][N], then layer
+// 2 and the loss, then the fixed-order mean.  For counts too small to fill
+// the GPU with launch_fitness_simt_main's 128-sample x 64-unit tiles.
+int launch_fitness_small(const Mlp& mlp, const float* rows, int64_t ld, int32_t count, const int32_t* idx,
+                         float* hidden, float* partial, float* fit, cudaStream_t s);
+
+// Elite candidates for the FP32 re-score: per firework (all runs) the
+// `E` best of its lam explosion and m guiding sparks by the current
+// fitness, as rows of the spark buffer (explosion z*lam + c, guiding
+// n_e + z*m + q) into elite[z*E + e].
+int launch_elite_pick(const Problem& p, const float* fit_e, const float* fit_g, int32_t E, int32_t* elite,
+                      cudaStream_t s);
 
 int launch_fitness_sphere(const float* rows, int64_t ld, int64_t D, int32_t count, float* fit, cudaStream_t s);
 

@@ -144,3 +144,36 @@ def test_bf16_whole_run_learns(pkg):
     assert ev == w.eval_budget
     assert bf < 0.8 * f0
     assert abs(bf - prob.fitness(bx)) <= 1e-12 * bf
+
+
+def test_elite_candidates_are_rescored_in_fp32(pkg):
+    """With BF16 fitness, each firework's E best candidates (by BF16 fitness, (fitness, index) order) get their
+    fitness recomputed by the FP32 path before selection; the others keep their BF16 values."""
+    E = 3
+    w = W.scaled(W.MLP_784_64_10, n_samples=300, n_fireworks=3, sparks_per_firework=20, guiding_per_firework=4)
+    X, y = W.make_data(w)
+    mu, lam, m = w.n_fireworks, w.sparks_per_firework, w.guiding_per_firework
+    with pkg.Mgfwa.for_workload(w, 8, precision=pkg.MGFWA_BF16, X=X, y=y, elite_rescore=E) as run:
+        for ph in (pkg.MGFWA_PHASE_EXPLODE, pkg.MGFWA_PHASE_EVAL_E, pkg.MGFWA_PHASE_RANK, pkg.MGFWA_PHASE_GUIDE,
+                   pkg.MGFWA_PHASE_EVAL_G):
+            run.phase(ph)
+        fe, fg = run.read(pkg.MGFWA_BUF_FIT_E), run.read(pkg.MGFWA_BUF_FIT_G)
+        sparks, guides = run.read(pkg.MGFWA_BUF_SPARKS), run.read(pkg.MGFWA_BUF_GUIDES)
+        run.phase(pkg.MGFWA_PHASE_RESCORE)
+        fe2, fg2 = run.read(pkg.MGFWA_BUF_FIT_E), run.read(pkg.MGFWA_BUF_FIT_G)
+        run.phase(pkg.MGFWA_PHASE_SELECT)
+        f32_e = run.evaluate(sparks, pkg.MGFWA_FP32)
+        f32_g = run.evaluate(guides, pkg.MGFWA_FP32)
+    for i in range(mu):
+        cand = [(float(fe[i * lam + c]), c) for c in range(lam)] + [(float(fg[i * m + q]), lam + q) for q in range(m)]
+        elite = {c for _, c in sorted(cand)[:E]}
+        for c in range(lam + m):
+            new = fe2[i * lam + c] if c < lam else fg2[i * m + c - lam]
+            old = fe[i * lam + c] if c < lam else fg[i * m + c - lam]
+            fp32 = f32_e[i * lam + c] if c < lam else f32_g[i * m + c - lam]
+            if c in elite:
+                # the re-score's FP32 sums run in another order than the FP32 kernel's: FP32 tolerance
+                assert abs(new - fp32) <= 1e-5 * abs(fp32) + 1e-5, (i, c, new, fp32)
+                assert new != old or abs(old - fp32) <= 1e-5 * abs(fp32) + 1e-5
+            else:
+                assert new == old, (i, c)
