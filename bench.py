@@ -240,6 +240,8 @@ def gpu_arm(args):
         return {"value": n / (t / 1e3), "ms_per_step": t / steps}
 
     extra = {}
+    if not args.no_extras and world == 1:
+        extra["serving"] = serving_trace(pkg, X, y)
     if not args.no_extras:
         # the plain FP32 one-run path the low-precision path is compared with
         extra["fp32_one_run"] = dict(timed_generations({"precision": pkg.MGFWA_FP32}, 5), precision="fp32")
@@ -325,6 +327,54 @@ def gpu_arm(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def serving_trace(pkg, X, y, n_requests: int = 48, rate_hz: float = 400.0, max_live: int = 8, seed: int = 5):
+    """Continuous batching on one GPU: a Poisson stream of requests, two thirds
+    784-64-10 BF16 runs on the full batch (20 generations each) and one third
+    8-16-3 FP32 runs (40 generations), served with `max_live` slots.  Latency is
+    from each request's arrival to its result; throughput counts every spark."""
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate_hz, n_requests))
+    small = W.MLP_8_16_3
+    Xs, ys = W.make_data(small)
+    big = W.scaled(WORKLOAD, eval_budget=W.budget_for_generations(
+        WORKLOAD.n_fireworks, WORKLOAD.sparks_per_firework, WORKLOAD.guiding_per_firework, 20))
+    sm = W.scaled(small, eval_budget=W.budget_for_generations(
+        small.n_fireworks, small.sparks_per_firework, small.guiding_per_firework, 40))
+    reqs = []
+    for k in range(n_requests):
+        if k % 3 == 2:
+            reqs.append(pkg.workload_request(sm, 7000 + k, pkg.MGFWA_FP32, X=Xs, y=ys))
+        else:
+            reqs.append(pkg.workload_request(big, 7000 + k, pkg.MGFWA_BF16, X=X, y=y))
+    with pkg.Server(max_live=max_live, device_bytes_limit=1 << 36) as s:
+        ids, live_samples = [], []
+        t0 = s.now()
+        nxt = 0
+        while True:
+            now = s.now() - t0
+            while nxt < n_requests and arrivals[nxt] <= now:
+                ids.append(s.submit(*reqs[nxt]))
+                nxt += 1
+            st = s.stats()
+            if st.live or st.queued:
+                live_samples.append(st.live)
+                s.tick(1)
+            elif nxt == n_requests:
+                break
+            else:
+                time.sleep(max(0.0, min(1e-3, arrivals[nxt] - now)))
+        wall = s.now() - t0
+        st = s.stats()
+        lat = np.array([s.poll(r)[0].t_done - t0 - arrivals[i] for i, r in enumerate(ids)])
+        done = sum(s.poll(r)[0].state == pkg.MGFWA_REQ_DONE for r in ids)
+    return {"requests": n_requests, "completed": int(done), "arrival_rate_hz": rate_hz, "max_live": max_live,
+            "wall_s": round(wall, 4), "sparks_per_s": st.sparks_evaluated / wall,
+            "latency_ms_p50": round(float(np.percentile(lat, 50)) * 1e3, 3),
+            "latency_ms_p99": round(float(np.percentile(lat, 99)) * 1e3, 3),
+            "mean_live": round(float(np.mean(live_samples)), 2),
+            "mix": "2/3 784-64-10 bf16 x 20 generations, 1/3 8-16-3 fp32 x 40 generations; Poisson arrivals"}
 
 
 def main():

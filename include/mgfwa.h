@@ -105,6 +105,10 @@ MGFWA_API mgfwa_status mgfwa_config_init(mgfwa_config* cfg);
 MGFWA_API mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, void* cuda_stream,
                           mgfwa_t** out);
 
+/* Bytes of device memory mgfwa_create would allocate for this problem (the
+ * handle's one arena), without allocating.  Same validation as create. */
+MGFWA_API mgfwa_status mgfwa_footprint(const mgfwa_config* cfg, const mgfwa_objective* obj, int64_t* bytes_out);
+
 /* Enqueue up to n_generations generations on the handle's stream; stops
  * early (without error) when the budget allows no further generation.
  * Returns EBUDGET if not even one generation fits.  Asynchronous. */
@@ -177,6 +181,61 @@ MGFWA_API mgfwa_status mgfwa_evaluate_fp32_noalloc(int32_t n_layers, const int32
                                                    int64_t n_samples, const float* X_dev, const int32_t* y_dev,
                                                    const float* rows_dev, int64_t ld, int32_t count,
                                                    float* fitness_dev, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Serving: many optimisation requests on one GPU with continuous batching.
+ *
+ * Requests (a configuration and an objective, copied at submit) wait in a
+ * FIFO.  mgfwa_server_tick() first admits waiting requests in order while a
+ * slot is free and the head's device footprint (mgfwa_footprint) fits in
+ * the memory limit beside the live runs; each admitted request becomes a
+ * handle with its own stream, and all its state (fireworks, sparks, Philox
+ * counters) stays on the device until it finishes.  The tick then enqueues
+ * up to `generations` generations of every live run, on their streams, so
+ * the runs' kernels overlap on the GPU.  A run whose budget allows no more
+ * generations is finished: its best position and FP64 fitness are read
+ * back, its memory is freed and its slot is given to the next request.
+ * A request's result equals that of the same configuration run alone.
+ * Single-threaded: one host thread drives a server.
+ * ------------------------------------------------------------------------ */
+typedef struct mgfwa_server mgfwa_server_t;
+
+enum { MGFWA_REQ_QUEUED = 0, MGFWA_REQ_RUNNING = 1, MGFWA_REQ_DONE = 2, MGFWA_REQ_FAILED = 3 };
+
+typedef struct {
+  int32_t state;           /* MGFWA_REQ_* */
+  int32_t status;          /* mgfwa_status of a failed request */
+  int64_t evals;           /* evaluations used per run so far */
+  double best_f;           /* FP64 best fitness (DONE) */
+  double t_submit, t_admit, t_done; /* seconds on the server's steady clock */
+  int64_t footprint;       /* device bytes of the request's handle */
+} mgfwa_request_info;
+
+typedef struct {
+  int64_t submitted, admitted, completed, failed;
+  int32_t live, queued;
+  int64_t device_bytes_in_use; /* footprints of the live runs */
+  int64_t sparks_evaluated;    /* over all generations enqueued so far */
+} mgfwa_server_stats;
+
+/* max_live: slots for concurrent runs (>= 1); device_bytes_limit: memory the
+ * live runs may hold (> 0). */
+MGFWA_API mgfwa_status mgfwa_server_create(int32_t max_live, int64_t device_bytes_limit, mgfwa_server_t** out);
+/* Queue a request; *request_id identifies it.  EINVAL if the configuration
+ * is invalid or its footprint exceeds the server's whole limit. */
+MGFWA_API mgfwa_status mgfwa_server_submit(mgfwa_server_t* s, const mgfwa_config* cfg, const mgfwa_objective* obj,
+                                           int64_t* request_id);
+/* Admit, step every live run by up to `generations`, retire finished runs. */
+MGFWA_API mgfwa_status mgfwa_server_tick(mgfwa_server_t* s, int32_t generations);
+/* State and timing of a request; x_out (D floats, may be NULL) gets the best
+ * position once DONE. */
+MGFWA_API mgfwa_status mgfwa_server_poll(mgfwa_server_t* s, int64_t request_id, mgfwa_request_info* info,
+                                         float* x_out);
+MGFWA_API mgfwa_status mgfwa_server_stats_get(const mgfwa_server_t* s, mgfwa_server_stats* stats);
+/* Seconds on the server's steady clock (the clock of the request times). */
+MGFWA_API double mgfwa_server_now(const mgfwa_server_t* s);
+/* Finish nothing further: destroy live handles and free everything. NULL-safe. */
+MGFWA_API void mgfwa_server_destroy(mgfwa_server_t* s);
 
 #ifdef __cplusplus
 }

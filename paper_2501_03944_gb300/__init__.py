@@ -34,7 +34,10 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5:
 EXPORTS = ("mgfwa_config_init", "mgfwa_create", "mgfwa_step", "mgfwa_run", "mgfwa_best", "mgfwa_best_run",
            "mgfwa_evaluate",
            "mgfwa_get_info", "mgfwa_destroy", "mgfwa_last_error", "mgfwa_debug_phase", "mgfwa_debug_read",
-           "mgfwa_debug_write", "mgfwa_debug_profile", "mgfwa_debug_kernel_times", "mgfwa_evaluate_fp32_noalloc")
+           "mgfwa_debug_write", "mgfwa_debug_profile", "mgfwa_debug_kernel_times", "mgfwa_evaluate_fp32_noalloc",
+           "mgfwa_footprint", "mgfwa_server_create", "mgfwa_server_submit", "mgfwa_server_tick", "mgfwa_server_poll",
+           "mgfwa_server_stats_get", "mgfwa_server_now", "mgfwa_server_destroy")
+MGFWA_REQ_QUEUED, MGFWA_REQ_RUNNING, MGFWA_REQ_DONE, MGFWA_REQ_FAILED = range(4)
 N_KERNEL_GROUPS = 8
 KERNEL_GROUPS = ("explode", "fitness_explosion", "fitness_finish", "rank", "guide", "fitness_guiding", "select",
                  "elite_rescore")
@@ -60,6 +63,18 @@ class mgfwa_info(ctypes.Structure):
     _fields_ = [("evals", ctypes.c_int64), ("generations", ctypes.c_int32), ("k", ctypes.c_int32),
                 ("dim_padded", ctypes.c_int64), ("sparks_per_gen", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("n_runs", ctypes.c_int32)]
+
+
+class mgfwa_request_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("evals", ctypes.c_int64),
+                ("best_f", ctypes.c_double), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("footprint", ctypes.c_int64)]
+
+
+class mgfwa_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("live", ctypes.c_int32), ("queued", ctypes.c_int32),
+                ("device_bytes_in_use", ctypes.c_int64), ("sparks_evaluated", ctypes.c_int64)]
 
 
 class MgfwaError(RuntimeError):
@@ -101,8 +116,20 @@ def load_library(path: Optional[str] = None):
     L.mgfwa_debug_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     i32p = ctypes.POINTER(ctypes.c_int32)
     L.mgfwa_evaluate_fp32_noalloc.argtypes = [i32, i32p, i32p, i64, vp, vp, vp, i64, i32, vp, vp]
+    L.mgfwa_footprint.argtypes = [ctypes.POINTER(mgfwa_config), ctypes.POINTER(mgfwa_objective),
+                                  ctypes.POINTER(ctypes.c_int64)]
+    L.mgfwa_server_create.argtypes = [i32, i64, ctypes.POINTER(vp)]
+    L.mgfwa_server_submit.argtypes = [vp, ctypes.POINTER(mgfwa_config), ctypes.POINTER(mgfwa_objective),
+                                      ctypes.POINTER(ctypes.c_int64)]
+    L.mgfwa_server_tick.argtypes = [vp, i32]
+    L.mgfwa_server_poll.argtypes = [vp, i64, ctypes.POINTER(mgfwa_request_info), f32p]
+    L.mgfwa_server_stats_get.argtypes = [vp, ctypes.POINTER(mgfwa_server_stats)]
+    L.mgfwa_server_now.argtypes = [vp]
+    L.mgfwa_server_now.restype = ctypes.c_double
+    L.mgfwa_server_destroy.argtypes = [vp]
+    L.mgfwa_server_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("mgfwa_destroy", "mgfwa_last_error"):
+        if name not in ("mgfwa_destroy", "mgfwa_last_error", "mgfwa_server_now", "mgfwa_server_destroy"):
             getattr(L, name).restype = ctypes.c_int
     if path == LIB_PATH:
         _lib = L
@@ -311,6 +338,96 @@ class Mgfwa:
     def close(self) -> None:
         if getattr(self, "handle", None):
             mgfwa_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# Serving (continuous batching of optimisation requests on one GPU).
+
+def make_config(*, dim, lb, ub, n_fireworks, sparks_per_firework, guiding_per_firework, eval_budget, seed,
+                sigma=0.2, boost=1.0, amp_init=0.0, c_amplify=1.2, c_reduce=0.9, precision=MGFWA_FP32, n_runs=1,
+                elite_rescore=2) -> mgfwa_config:
+    cfg = mgfwa_config_init()
+    cfg.dim, cfg.lb, cfg.ub = dim, lb, ub
+    cfg.n_fireworks, cfg.sparks_per_firework, cfg.guiding_per_firework = (
+        n_fireworks, sparks_per_firework, guiding_per_firework)
+    cfg.sigma, cfg.boost, cfg.amp_init, cfg.c_amplify, cfg.c_reduce = sigma, boost, amp_init, c_amplify, c_reduce
+    cfg.eval_budget, cfg.seed, cfg.precision, cfg.n_runs, cfg.elite_rescore = (
+        eval_budget, seed, precision, n_runs, elite_rescore)
+    return cfg
+
+
+def workload_request(w, seed, precision=MGFWA_FP32, X=None, y=None, **over):
+    """(config, objective buffers) for a workloads.Workload."""
+    kw = dict(dim=w.dim, lb=w.lb, ub=w.ub, n_fireworks=w.n_fireworks, sparks_per_firework=w.sparks_per_firework,
+              guiding_per_firework=w.guiding_per_firework, eval_budget=w.eval_budget, seed=seed, sigma=w.sigma,
+              precision=precision)
+    kw.update(over)
+    cfg = make_config(**kw)
+    if w.kind == MGFWA_OBJ_MLP_CE:
+        if X is None:
+            import workloads
+            X, y = workloads.make_data(w)
+        obj = _ObjectiveBuffers(MGFWA_OBJ_MLP_CE, w.widths, w.acts, X, y)
+    else:
+        obj = _ObjectiveBuffers(MGFWA_OBJ_SPHERE)
+    return cfg, obj
+
+
+def mgfwa_footprint(cfg: mgfwa_config, obj) -> int:
+    b = ctypes.c_int64()
+    _check(load_library().mgfwa_footprint(ctypes.byref(cfg), ctypes.byref(obj.obj), ctypes.byref(b)))
+    return b.value
+
+
+class Server:
+    """Owner of an mgfwa_server_t (see include/mgfwa.h, Serving)."""
+
+    def __init__(self, max_live: int, device_bytes_limit: int):
+        h = ctypes.c_void_p()
+        _check(load_library().mgfwa_server_create(max_live, device_bytes_limit, ctypes.byref(h)))
+        self.handle = h.value
+        self.dims = {}
+
+    def submit(self, cfg: mgfwa_config, obj) -> int:
+        rid = ctypes.c_int64()
+        _check(load_library().mgfwa_server_submit(self.handle, ctypes.byref(cfg), ctypes.byref(obj.obj),
+                                                  ctypes.byref(rid)))
+        self.dims[rid.value] = cfg.dim
+        return rid.value
+
+    def tick(self, generations: int = 1) -> int:
+        return load_library().mgfwa_server_tick(self.handle, generations)
+
+    def poll(self, rid: int, want_x: bool = False):
+        info = mgfwa_request_info()
+        x = np.zeros(self.dims[rid], np.float32) if want_x else None
+        _check(load_library().mgfwa_server_poll(self.handle, rid, ctypes.byref(info), _f32p(x)))
+        return info, x
+
+    def stats(self) -> mgfwa_server_stats:
+        st = mgfwa_server_stats()
+        _check(load_library().mgfwa_server_stats_get(self.handle, ctypes.byref(st)))
+        return st
+
+    def now(self) -> float:
+        return load_library().mgfwa_server_now(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().mgfwa_server_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):

@@ -56,6 +56,7 @@ struct mgfwa_handle {
   double* ce64 = nullptr;
   double* f64 = nullptr;
   uint32_t* status = nullptr;
+  bool want_op = false; // BF16 tensor-core path: BF16 copies of X and of the first-layer weights
   int64_t P = 0;       // sparks per generation of one run
   int64_t PA = 0;      // sparks per generation of all runs (rows of the spark buffers)
   int32_t mtiles = 0;  // sample tiles of 128
@@ -328,34 +329,9 @@ T* carve(char*& cur, size_t count) {
   return p;
 }
 
-}  // namespace
-
-extern "C" {
-
-mgfwa_status mgfwa_config_init(mgfwa_config* cfg) {
-  if (!cfg) return MGFWA_EINVAL;
-  std::memset(cfg, 0, sizeof(*cfg));
-  cfg->sigma = 0.2f;
-  cfg->boost = 1.0f;
-  cfg->amp_init = 0.0f;
-  cfg->c_amplify = 1.2f;
-  cfg->c_reduce = 0.9f;
-  cfg->precision = MGFWA_FP32;
-  cfg->elite_rescore = 2;
-  cfg->n_runs = 1;
-  return MGFWA_OK;
-}
-
-mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, void* cuda_stream, mgfwa_t** out) {
-  if (!out) return fail(nullptr, MGFWA_EINVAL, "null output handle pointer");
-  *out = nullptr;
-  g_create_error.clear();
-  TRACE("create: validate");
-  mgfwa_status st = validate(cfg, obj);
-  if (st != MGFWA_OK) return st;
-  TRACE("create: validated");
-  mgfwa_t* h = new (std::nothrow) mgfwa_t();
-  if (!h) return fail(nullptr, MGFWA_ENOMEM, "host allocation failed");
+// Fill the handle's problem description and sizes from a validated
+// configuration (no allocation).
+void plan_handle(mgfwa_t* h, const mgfwa_config* cfg, const mgfwa_objective* obj) {
   h->cfg = *cfg;
   h->kind = obj->kind;
   cudaGetDevice(&h->device);
@@ -401,36 +377,90 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
   } else {
     h->mtiles = 1;
   }
-  const bool want_op = obj->kind == MGFWA_OBJ_MLP_CE && cfg->precision == MGFWA_BF16;
+  h->want_op = obj->kind == MGFWA_OBJ_MLP_CE && cfg->precision == MGFWA_BF16;
+}
 
-  // One arena for all device state; sizing and carving share one layout pass.
-  auto layout = [&](char* base) -> size_t {
-    char* cur = base;
-    h->X = carve<float>(cur, N * d_in);
-    h->Xbf = want_op ? carve<__nv_bfloat16>(cur, N * d_in) : nullptr;
-    h->y = carve<int32_t>(cur, N);
-    const int64_t F = (int64_t)p.B * p.mu;  // fireworks of all runs
-    h->fw_x = carve<float>(cur, F * p.Dp);
-    h->fw_amp = carve<float>(cur, F);
-    h->fw_f = carve<float>(cur, F);
-    h->sparks = carve<float>(cur, h->PA * p.Dp);
-    h->op = want_op ? carve<__nv_bfloat16>(cur, h->PA * mlp.w1_elems) : nullptr;
-    h->fit = carve<float>(cur, h->PA);
-    h->partial = carve<float>(cur, (size_t)h->mtiles * h->PA);
-    h->top = carve<int32_t>(cur, F * p.m * p.k);
-    h->bottom = carve<int32_t>(cur, F * p.m * p.k);
-    h->winner = carve<int32_t>(cur, F);
-    h->elite = carve<int32_t>(cur, F * (cfg->elite_rescore > 0 ? cfg->elite_rescore : 1));
-    const bool rescore = want_op && cfg->elite_rescore > 0;
-    h->hidden = rescore ? carve<float>(cur, F * cfg->elite_rescore * N * mlp.widths[1]) : nullptr;
-    h->best_x = carve<float>(cur, (int64_t)p.B * p.Dp);
-    h->best_f = carve<float>(cur, p.B);
-    h->ce64 = carve<double>(cur, N > 0 ? N : 1);
-    h->f64 = carve<double>(cur, 1);
-    h->status = carve<uint32_t>(cur, 1);
-    return (size_t)(cur - base);
-  };
-  const size_t bytes = layout(nullptr);
+// One arena for all device state; sizing (null base) and carving share this
+// one layout pass.
+size_t carve_all(mgfwa_t* h, char* base) {
+  const Problem& p = h->p;
+  const Mlp& mlp = h->mlp;
+  const mgfwa_config* cfg = &h->cfg;
+  const bool want_op = h->want_op;
+  const int64_t N = mlp.N, d_in = mlp.widths[0];
+  char* cur = base;
+  h->X = carve<float>(cur, N * d_in);
+  h->Xbf = want_op ? carve<__nv_bfloat16>(cur, N * d_in) : nullptr;
+  h->y = carve<int32_t>(cur, N);
+  const int64_t F = (int64_t)p.B * p.mu;  // fireworks of all runs
+  h->fw_x = carve<float>(cur, F * p.Dp);
+  h->fw_amp = carve<float>(cur, F);
+  h->fw_f = carve<float>(cur, F);
+  h->sparks = carve<float>(cur, h->PA * p.Dp);
+  h->op = want_op ? carve<__nv_bfloat16>(cur, h->PA * mlp.w1_elems) : nullptr;
+  h->fit = carve<float>(cur, h->PA);
+  h->partial = carve<float>(cur, (size_t)h->mtiles * h->PA);
+  h->top = carve<int32_t>(cur, F * p.m * p.k);
+  h->bottom = carve<int32_t>(cur, F * p.m * p.k);
+  h->winner = carve<int32_t>(cur, F);
+  h->elite = carve<int32_t>(cur, F * (cfg->elite_rescore > 0 ? cfg->elite_rescore : 1));
+  const bool rescore = want_op && cfg->elite_rescore > 0;
+  h->hidden = rescore ? carve<float>(cur, F * cfg->elite_rescore * N * mlp.widths[1]) : nullptr;
+  h->best_x = carve<float>(cur, (int64_t)p.B * p.Dp);
+  h->best_f = carve<float>(cur, p.B);
+  h->ce64 = carve<double>(cur, N > 0 ? N : 1);
+  h->f64 = carve<double>(cur, 1);
+  h->status = carve<uint32_t>(cur, 1);
+  return (size_t)(cur - base);
+}
+
+}  // namespace
+
+extern "C" {
+
+mgfwa_status mgfwa_config_init(mgfwa_config* cfg) {
+  if (!cfg) return MGFWA_EINVAL;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->sigma = 0.2f;
+  cfg->boost = 1.0f;
+  cfg->amp_init = 0.0f;
+  cfg->c_amplify = 1.2f;
+  cfg->c_reduce = 0.9f;
+  cfg->precision = MGFWA_FP32;
+  cfg->elite_rescore = 2;
+  cfg->n_runs = 1;
+  return MGFWA_OK;
+}
+
+mgfwa_status mgfwa_footprint(const mgfwa_config* cfg, const mgfwa_objective* obj, int64_t* bytes_out) {
+  if (!bytes_out) return fail(nullptr, MGFWA_EINVAL, "null output pointer");
+  g_create_error.clear();
+  mgfwa_status st = validate(cfg, obj);
+  if (st != MGFWA_OK) return st;
+  mgfwa_t* h = new (std::nothrow) mgfwa_t();
+  if (!h) return fail(nullptr, MGFWA_ENOMEM, "host allocation failed");
+  plan_handle(h, cfg, obj);
+  *bytes_out = (int64_t)carve_all(h, nullptr);
+  delete h;
+  return MGFWA_OK;
+}
+
+mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, void* cuda_stream, mgfwa_t** out) {
+  if (!out) return fail(nullptr, MGFWA_EINVAL, "null output handle pointer");
+  *out = nullptr;
+  g_create_error.clear();
+  TRACE("create: validate");
+  mgfwa_status st = validate(cfg, obj);
+  if (st != MGFWA_OK) return st;
+  TRACE("create: validated");
+  mgfwa_t* h = new (std::nothrow) mgfwa_t();
+  if (!h) return fail(nullptr, MGFWA_ENOMEM, "host allocation failed");
+  plan_handle(h, cfg, obj);
+  const Problem& p = h->p;
+  Mlp& mlp = h->mlp;
+  const bool want_op = h->want_op;
+  const int64_t N = mlp.N, d_in = mlp.widths[0];
+  const size_t bytes = carve_all(h, nullptr);
   h->arena_bytes = bytes;
   TRACE("create: arena %zu bytes, Dp %lld, P %lld, N %lld, d_in %lld", bytes, (long long)p.Dp, (long long)h->P,
         (long long)N, (long long)d_in);
@@ -452,7 +482,7 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
     delete h;
     return fail(nullptr, MGFWA_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
   }
-  if (layout(h->arena) != bytes) {
+  if (carve_all(h, h->arena) != bytes) {
     cudaFree(h->arena);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;

@@ -41,7 +41,8 @@ def test_exports_every_declared_symbol(pkg):
 def test_structure_layout_matches_header(pkg, tmp_path):
     """Compile a C program against the header and compare every field offset with the ctypes mirror."""
     import ctypes
-    classes = (pkg.mgfwa_config, pkg.mgfwa_objective, pkg.mgfwa_info)
+    classes = (pkg.mgfwa_config, pkg.mgfwa_objective, pkg.mgfwa_info, pkg.mgfwa_request_info,
+               pkg.mgfwa_server_stats)
     body = []
     for cls in classes:
         body.append(f'  printf("{cls.__name__} %zu\\n", sizeof({cls.__name__}));')
