@@ -48,7 +48,8 @@ class Params(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int64), ("lb", ctypes.c_float), ("ub", ctypes.c_float),
                 ("mu", ctypes.c_int32), ("lam", ctypes.c_int32), ("m", ctypes.c_int32),
                 ("k", ctypes.c_int32), ("beta", ctypes.c_float), ("amp0", ctypes.c_float),
-                ("c_a", ctypes.c_float), ("c_r", ctypes.c_float)]
+                ("c_a", ctypes.c_float), ("c_r", ctypes.c_float), ("refine_every", ctypes.c_int32),
+                ("refine_steps", ctypes.c_int32), ("refine_lr", ctypes.c_float)]
 
 
 class Objective(ctypes.Structure):
@@ -88,6 +89,13 @@ def lib():
             L.orc_run.argtypes = [pp, op, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                   f32p, f64p, i64p, i32p, f32p]
             L.orc_run.restype = ctypes.c_int32
+            L.orc_gradient.argtypes = [op, f32p, f64p]
+            L.orc_gradient.restype = ctypes.c_double
+            L.orc_refine.argtypes = [op, ctypes.c_int64, f32p, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
+                                     ctypes.c_float, f32p]
+            L.orc_refine.restype = ctypes.c_double
+            L.orc_refine_cost.argtypes = [pp]
+            L.orc_refine_cost.restype = ctypes.c_int64
             _lib = L
     return _lib
 
@@ -111,12 +119,13 @@ def subset_size(sigma: float, g: int) -> int:
     return int(lib().orc_subset_size(sigma, g))
 
 
-def make_params(dim, lb, ub, mu, lam, m, sigma=0.2, k=None, beta=1.0, amp0=None, c_a=1.2, c_r=0.9) -> Params:
+def make_params(dim, lb, ub, mu, lam, m, sigma=0.2, k=None, beta=1.0, amp0=None, c_a=1.2, c_r=0.9,
+                refine_every=0, refine_steps=0, refine_lr=0.0) -> Params:
     if k is None:
         k = subset_size(sigma, lam // m)
     if amp0 is None:
         amp0 = float(np.float32(ub) - np.float32(lb))
-    return Params(dim, lb, ub, mu, lam, m, k, beta, amp0, c_a, c_r)
+    return Params(dim, lb, ub, mu, lam, m, k, beta, amp0, c_a, c_r, refine_every, refine_steps, refine_lr)
 
 
 def params_for(w, **over) -> Params:
@@ -233,6 +242,27 @@ def run(p: Params, prob: Problem, seed: int, budget: int, max_gens: int = 1 << 3
     if trace is not None:
         out["trace"] = trace[:gens.value]
     return out
+
+
+def gradient(prob: Problem, x: np.ndarray):
+    """(FP64 objective, FP64 gradient) at the FP32 vector x, by backpropagation."""
+    x = np.ascontiguousarray(x, np.float32)
+    g = np.zeros(x.shape[0], np.float64)
+    f = lib().orc_gradient(ctypes.byref(prob.obj), _p(x, ctypes.c_float), _p(g, ctypes.c_double))
+    return f, g
+
+
+def refine(prob: Problem, x: np.ndarray, steps: int, lr: float, lb: float, ub: float):
+    """(refined FP32 vector, its FP64 objective) after `steps` projected gradient steps."""
+    x = np.ascontiguousarray(x, np.float32)
+    out = np.zeros_like(x)
+    f = lib().orc_refine(ctypes.byref(prob.obj), x.shape[0], _p(x, ctypes.c_float), steps, lr, lb, ub,
+                         _p(out, ctypes.c_float))
+    return out, f
+
+
+def refine_cost(p: Params) -> int:
+    return int(lib().orc_refine_cost(ctypes.byref(p)))
 
 
 def generation(p: Params, prob: Problem, seed: int, gen: int, fw_x, fw_amp, fw_f, n_threads: int = 1):

@@ -202,6 +202,32 @@ static void eval_f32(const orc_objective* obj, const float* xs, int64_t count, i
   free(tmp);
 }
 
+/*
+ * Hybrid refinement (the paper's outlook, Sec. 5, proposes combining MGFWA
+ * with other optimisers; this is the gradient reading of it): projected
+ * gradient descent on the objective from x_in.  Each step takes the FP64
+ * gradient, rounds it to FP32 and moves every coordinate by one fused
+ * multiply-add, then clips it to the box.
+ */
+double orc_refine(const orc_objective* obj, int64_t dim, const float* x_in, int32_t steps, float lr, float lb,
+                  float ub, float* x_out) {
+  double* g = (double*)malloc(sizeof(double) * (size_t)dim);
+  memcpy(x_out, x_in, sizeof(float) * (size_t)dim);
+  for (int32_t s = 0; s < steps; ++s) {
+    orc_gradient(obj, x_out, g);
+    for (int64_t k = 0; k < dim; ++k) x_out[k] = fminf(fmaxf(fmaf(-lr, (float)g[k], x_out[k]), lb), ub);
+  }
+  free(g);
+  return orc_fitness(obj, x_out);
+}
+
+int64_t orc_refine_cost(const orc_params* p) { return 3 * (int64_t)p->refine_steps + 1; }
+
+/* Generation `gen` (1-based) ends with a refinement. */
+static int refine_due(const orc_params* p, int32_t gen) {
+  return p->refine_every > 0 && p->refine_steps > 0 && gen % p->refine_every == 0;
+}
+
 int32_t orc_run(const orc_params* p, const orc_objective* obj, uint64_t seed, int64_t budget,
                 int32_t max_gens, int32_t n_threads, float* best_x, double* best_f,
                 int64_t* evals_out, int32_t* gens_out, float* trace) {
@@ -230,7 +256,8 @@ int32_t orc_run(const orc_params* p, const orc_objective* obj, uint64_t seed, in
 
   const int64_t per_gen = (int64_t)p->mu * (p->lam + p->m);
   int32_t gen = 0;
-  while (gen < max_gens && evals + per_gen <= budget) {
+  float* refined = (float*)malloc(sizeof(float) * (size_t)D);
+  while (gen < max_gens && evals + per_gen + (refine_due(p, gen + 1) ? orc_refine_cost(p) : 0) <= budget) {
     ++gen;
     orc_explode(p, seed, (uint32_t)gen, fw_x, fw_amp, sparks);
     eval_f32(obj, sparks, (int64_t)p->mu * p->lam, D, fit_e, n_threads);
@@ -245,6 +272,24 @@ int32_t orc_run(const orc_params* p, const orc_objective* obj, uint64_t seed, in
         memcpy(best_x, fw_x + (int64_t)i * D, sizeof(float) * (size_t)D);
       }
     }
+    if (refine_due(p, gen)) {
+      /* refine the run's elite firework (first minimum); keep the result
+       * only on strict improvement; the amplitude is left as selected */
+      int32_t e = 0;
+      for (int32_t i = 1; i < p->mu; ++i)
+        if (key(fw_f[i]) < key(fw_f[e])) e = i;
+      const float fr = (float)orc_refine(obj, D, fw_x + (int64_t)e * D, p->refine_steps, p->refine_lr, p->lb,
+                                         p->ub, refined);
+      if (key(fr) < key(fw_f[e])) {
+        memcpy(fw_x + (int64_t)e * D, refined, sizeof(float) * (size_t)D);
+        fw_f[e] = fr;
+        if (key(fr) < key(run_best)) {
+          run_best = fr;
+          memcpy(best_x, refined, sizeof(float) * (size_t)D);
+        }
+      }
+      evals += orc_refine_cost(p);
+    }
     if (trace) trace[gen - 1] = run_best;
   }
   *best_f = orc_fitness(obj, best_x);
@@ -252,6 +297,6 @@ int32_t orc_run(const orc_params* p, const orc_objective* obj, uint64_t seed, in
   *gens_out = gen;
 
   free(fw_x); free(fw_amp); free(fw_f); free(sparks); free(guides);
-  free(fit_e); free(fit_g); free(top); free(bottom); free(winner);
+  free(fit_e); free(fit_g); free(top); free(bottom); free(winner); free(refined);
   return 0;
 }

@@ -108,3 +108,106 @@ void orc_fitness_many(const orc_objective* obj, const float* xs, int64_t count, 
   free(th);
   free(jobs);
 }
+
+/*
+ * Gradient of the MLP cross-entropy above with respect to the flattened
+ * parameters, by backpropagation in FP64 (the derivative of the same
+ * formula, sample by sample in index order):
+ *
+ *   delta_L = (softmax(z) - onehot(y_n)) / N,
+ *   dW_l += delta_l a_{l-1}^T,  db_l += delta_l,
+ *   delta_{l-1} = (W_l^T delta_l) * act'(pre_{l-1}),
+ *
+ * with tanh' = 1 - tanh^2 and relu'(v) = 1 if v > 0 else 0 (the value 0 is
+ * given slope 0).  The sphere's gradient is 2x.  Returns the objective.
+ */
+double orc_gradient(const orc_objective* obj, const float* x, double* grad) {
+  if (obj->kind == ORC_SPHERE) {
+    double s = 0.0;
+    for (int64_t k = 0; k < obj->dim; ++k) {
+      s += (double)x[k] * (double)x[k];
+      grad[k] = 2.0 * (double)x[k];
+    }
+    return s;
+  }
+  const int32_t L = obj->n_layers;
+  if (L < 1 || L > 7) return NAN;
+  int64_t w_off[8], b_off[8], total_units = 0, off = 0;
+  for (int32_t l = 0; l < L; ++l) {
+    w_off[l] = off;
+    off += (int64_t)obj->widths[l] * obj->widths[l + 1];
+    b_off[l] = off;
+    off += obj->widths[l + 1];
+  }
+  for (int32_t l = 0; l <= L; ++l) total_units += obj->widths[l];
+  for (int64_t k = 0; k < off; ++k) grad[k] = 0.0;
+  /* a[l] holds layer l's output for the current sample (a[0] = input),
+   * pre[l] its pre-activation, delta[l] the loss derivative wrt pre[l] */
+  double* a = (double*)malloc(sizeof(double) * (size_t)total_units);
+  double* pre = (double*)malloc(sizeof(double) * (size_t)total_units);
+  double* delta = (double*)malloc(sizeof(double) * (size_t)total_units);
+  int64_t start[9];
+  start[0] = 0;
+  for (int32_t l = 0; l < L; ++l) start[l + 1] = start[l] + obj->widths[l];
+  const double inv_n = 1.0 / (double)obj->n_samples;
+  double total = 0.0;
+  for (int64_t n = 0; n < obj->n_samples; ++n) {
+    const int32_t d0 = obj->widths[0];
+    for (int32_t i = 0; i < d0; ++i) a[i] = (double)obj->X[n * d0 + i];
+    for (int32_t l = 0; l < L; ++l) {
+      const int32_t fan_in = obj->widths[l], fan_out = obj->widths[l + 1];
+      const float* W = x + w_off[l];
+      const float* bias = x + b_off[l];
+      const double* ain = a + start[l];
+      double* zout = pre + start[l + 1];
+      double* aout = a + start[l + 1];
+      for (int32_t j = 0; j < fan_out; ++j) {
+        double s = (double)bias[j];
+        for (int32_t i = 0; i < fan_in; ++i) s += (double)W[(int64_t)j * fan_in + i] * ain[i];
+        zout[j] = s;
+        aout[j] = (l + 1 < L) ? act(obj->acts[l], s) : s;
+      }
+    }
+    const int32_t C = obj->widths[L];
+    const double* z = a + start[L];
+    double zmax = z[0];
+    for (int32_t c = 1; c < C; ++c)
+      if (z[c] > zmax) zmax = z[c];
+    double se = 0.0;
+    for (int32_t c = 0; c < C; ++c) se += exp(z[c] - zmax);
+    total += (zmax + log(se)) - z[obj->y[n]];
+    double* dL = delta + start[L];
+    for (int32_t c = 0; c < C; ++c) dL[c] = (exp(z[c] - zmax) / se - (c == obj->y[n] ? 1.0 : 0.0)) * inv_n;
+    for (int32_t l = L - 1; l >= 0; --l) {
+      const int32_t fan_in = obj->widths[l], fan_out = obj->widths[l + 1];
+      const float* W = x + w_off[l];
+      const double* dout = delta + start[l + 1];
+      const double* ain = a + start[l];
+      double* gW = grad + w_off[l];
+      double* gb = grad + b_off[l];
+      for (int32_t j = 0; j < fan_out; ++j) {
+        for (int32_t i = 0; i < fan_in; ++i) gW[(int64_t)j * fan_in + i] += dout[j] * ain[i];
+        gb[j] += dout[j];
+      }
+      if (l == 0) break;
+      double* din = delta + start[l];
+      const double* zin = pre + start[l];
+      for (int32_t i = 0; i < fan_in; ++i) {
+        double s = 0.0;
+        for (int32_t j = 0; j < fan_out; ++j) s += (double)W[(int64_t)j * fan_in + i] * dout[j];
+        double d;
+        if (obj->acts[l - 1] == ORC_TANH) {
+          const double t = tanh(zin[i]);
+          d = 1.0 - t * t;
+        } else {
+          d = zin[i] > 0.0 ? 1.0 : 0.0;
+        }
+        din[i] = s * d;
+      }
+    }
+  }
+  free(a);
+  free(pre);
+  free(delta);
+  return total * inv_n;
+}

@@ -46,6 +46,10 @@ typedef struct {
   float beta;       /* guiding-vector boost */
   float amp0;       /* initial amplitude */
   float c_a, c_r;   /* amplitude amplification / reduction factors */
+  /* hybrid refinement of each run's elite (0 = off); see orc_refine */
+  int32_t refine_every;  /* T: after the selection of every T-th generation */
+  int32_t refine_steps;  /* T_g projected gradient steps */
+  float refine_lr;       /* eta */
 } orc_params;
 
 typedef struct {
@@ -74,6 +78,21 @@ double orc_fitness(const orc_objective* obj, const float* x);
 /* FP64 objective of `count` vectors spaced `stride` floats apart. */
 void orc_fitness_many(const orc_objective* obj, const float* xs, int64_t count, int64_t stride,
                       double* out, int32_t n_threads);
+
+/* Gradient of the objective at x (grad[D], FP64) by backpropagation;
+ * returns the FP64 objective value. */
+double orc_gradient(const orc_objective* obj, const float* x, double* grad);
+
+/* Hybrid refinement of one vector: `steps` projected gradient steps
+ *   w <- min(max(fmaf(-lr, (float)grad f(w), w), lb), ub)
+ * from x_in, result in x_out; returns the FP64 objective of the result. */
+double orc_refine(const orc_objective* obj, int64_t dim, const float* x_in, int32_t steps, float lr, float lb,
+                  float ub, float* x_out);
+
+/* Evaluations charged for one refinement: 3 per gradient step (a forward
+ * and a backward pass cost about three forward passes) plus 1 for the
+ * objective of the result. */
+int64_t orc_refine_cost(const orc_params* p);
 
 void orc_init(const orc_params* p, uint64_t seed, float* fw_x, float* fw_amp);
 void orc_explode(const orc_params* p, uint64_t seed, uint32_t gen, const float* fw_x,
