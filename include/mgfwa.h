@@ -76,6 +76,20 @@ typedef struct {
                                    BF16 fitness) are re-scored in FP32 before selection (default 2; 0 = off) */
   int32_t n_runs;               /* B >= 1 independent runs of the same problem, stepped together (the
                                    batch dimension of Table 1, Sec. 3); run b uses seed + b */
+  /* Hybrid refinement (the gradient reading of the hybrid strategies of
+   * Sec. 5; MLP objectives only).  After the selection of every
+   * refine_every-th generation (0 = never), each run's elite firework (the
+   * first minimum of its fireworks' fitness) takes refine_steps projected
+   * gradient steps w <- min(max(fma(-refine_lr, grad f(w), w), lb), ub), FP32
+   * backpropagation on the whole batch; the firework (and the run's best)
+   * take the result only if its FP32 fitness is strictly lower.  Amplitudes
+   * are unchanged.  Each refinement charges 3 * refine_steps + 1
+   * evaluations to the budget (a forward and a backward pass cost about
+   * three forward passes; one more for the result), and a generation runs
+   * only if its sparks and its refinement fit. */
+  int32_t refine_every;
+  int32_t refine_steps;
+  float refine_lr;
 } mgfwa_config;
 
 typedef struct {

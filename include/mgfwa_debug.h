@@ -24,12 +24,14 @@ typedef enum {
   MGFWA_PHASE_GUIDE = 3,   /* mu*m guiding sparks + random mapping (Alg. 1, multi-guiding) */
   MGFWA_PHASE_EVAL_G = 4,  /* fitness of the guiding sparks */
   MGFWA_PHASE_RESCORE = 5, /* low precision only: FP32 re-score of each firework's elite candidates */
-  MGFWA_PHASE_SELECT = 6   /* per-firework selection, amplitude update, run best, counters */
+  MGFWA_PHASE_SELECT = 6,  /* per-firework selection, amplitude update, run best, counters */
+  MGFWA_PHASE_REFINE = 7   /* hybrid refinement of each run's elite, in the generations it is due */
 } mgfwa_phase;
 
 /* Enqueue one phase.  Phases must come in the order above, starting with
  * EXPLODE; RESCORE may be skipped (selection then uses the fitness as
- * evaluated or injected).  EINVAL otherwise, and EBUDGET if EXPLODE would
+ * evaluated or injected), and REFINE may be skipped in generations where no
+ * refinement is due (it is a no-op there).  EINVAL otherwise, and EBUDGET if EXPLODE would
  * exceed the budget.  Asynchronous. */
 MGFWA_API mgfwa_status mgfwa_debug_phase(mgfwa_t* h, int32_t phase);
 
@@ -47,7 +49,10 @@ typedef enum {
   MGFWA_BUF_BOTTOM = 8,  /* [B*mu][m][k] int32: index of rank g-1-r, worst first */
   MGFWA_BUF_WINNER = 9,  /* [B*mu] int32: -1 kept, j explosion j, lambda+q guiding q */
   MGFWA_BUF_BEST_X = 10, /* [B][D] FP32 best-so-far position per run */
-  MGFWA_BUF_BEST_F = 11  /* [B] FP32 best-so-far fitness per run (the precision decisions use) */
+  MGFWA_BUF_BEST_F = 11, /* [B] FP32 best-so-far fitness per run (the precision decisions use) */
+  MGFWA_BUF_REFINE_X = 12,     /* [B][D] FP32 each run's vector after its last refinement (refining handles) */
+  MGFWA_BUF_REFINE_F = 13,     /* [B] FP32 fitness of that vector */
+  MGFWA_BUF_REFINE_ELITE = 14  /* [B] int32 index within the run of the firework it refined */
 } mgfwa_buffer;
 
 /* Copy a buffer to / from host memory (rows packed D floats apart);
@@ -61,8 +66,14 @@ MGFWA_API mgfwa_status mgfwa_debug_write(mgfwa_t* h, int32_t buf, const void* ho
  * summed milliseconds and the number of launches since the last enable.
  * Groups: 0 explode, 1 explosion fitness (main kernel), 2 fitness finish,
  * 3 rank, 4 guide, 5 guiding fitness (main kernel), 6 select + run best,
- * 7 elite FP32 re-score (pick + fitness + finish). */
-#define MGFWA_N_KERNEL_GROUPS 8
+ * 7 elite FP32 re-score (pick + fitness + finish), 8 hybrid refinement. */
+#define MGFWA_N_KERNEL_GROUPS 9
+/* FP32 objective and gradient (by the refinement's backpropagation
+ * kernels) of `count` <= n_runs host vectors of D floats; g_out gets
+ * count * D floats, f_out count floats.  Only for handles made with
+ * refine_every > 0, between generations.  Synchronises. */
+MGFWA_API mgfwa_status mgfwa_debug_gradient(mgfwa_t* h, const float* xs, int32_t count, float* g_out,
+                                            float* f_out);
 MGFWA_API mgfwa_status mgfwa_debug_profile(mgfwa_t* h, int32_t enable);
 MGFWA_API mgfwa_status mgfwa_debug_kernel_times(mgfwa_t* h, double* ms_out, int64_t* launches_out);
 

@@ -24,9 +24,10 @@ MGFWA_FP32, MGFWA_BF16, MGFWA_FP8 = 0, 1, 2
 MGFWA_OBJ_MLP_CE, MGFWA_OBJ_SPHERE = 0, 1
 MGFWA_ACT_TANH, MGFWA_ACT_RELU = 0, 1
 (MGFWA_PHASE_EXPLODE, MGFWA_PHASE_EVAL_E, MGFWA_PHASE_RANK, MGFWA_PHASE_GUIDE, MGFWA_PHASE_EVAL_G,
- MGFWA_PHASE_RESCORE, MGFWA_PHASE_SELECT) = range(7)
+ MGFWA_PHASE_RESCORE, MGFWA_PHASE_SELECT, MGFWA_PHASE_REFINE) = range(8)
 (MGFWA_BUF_FW_X, MGFWA_BUF_FW_AMP, MGFWA_BUF_FW_F, MGFWA_BUF_SPARKS, MGFWA_BUF_GUIDES, MGFWA_BUF_FIT_E,
- MGFWA_BUF_FIT_G, MGFWA_BUF_TOP, MGFWA_BUF_BOTTOM, MGFWA_BUF_WINNER, MGFWA_BUF_BEST_X, MGFWA_BUF_BEST_F) = range(12)
+ MGFWA_BUF_FIT_G, MGFWA_BUF_TOP, MGFWA_BUF_BOTTOM, MGFWA_BUF_WINNER, MGFWA_BUF_BEST_X, MGFWA_BUF_BEST_F,
+ MGFWA_BUF_REFINE_X, MGFWA_BUF_REFINE_F, MGFWA_BUF_REFINE_ELITE) = range(15)
 
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EBUDGET"}
 
@@ -35,12 +36,13 @@ EXPORTS = ("mgfwa_config_init", "mgfwa_create", "mgfwa_step", "mgfwa_run", "mgfw
            "mgfwa_evaluate",
            "mgfwa_get_info", "mgfwa_destroy", "mgfwa_last_error", "mgfwa_debug_phase", "mgfwa_debug_read",
            "mgfwa_debug_write", "mgfwa_debug_profile", "mgfwa_debug_kernel_times", "mgfwa_evaluate_fp32_noalloc",
+           "mgfwa_debug_gradient",
            "mgfwa_footprint", "mgfwa_server_create", "mgfwa_server_submit", "mgfwa_server_tick", "mgfwa_server_poll",
            "mgfwa_server_stats_get", "mgfwa_server_now", "mgfwa_server_destroy")
 MGFWA_REQ_QUEUED, MGFWA_REQ_RUNNING, MGFWA_REQ_DONE, MGFWA_REQ_FAILED = range(4)
-N_KERNEL_GROUPS = 8
+N_KERNEL_GROUPS = 9
 KERNEL_GROUPS = ("explode", "fitness_explosion", "fitness_finish", "rank", "guide", "fitness_guiding", "select",
-                 "elite_rescore")
+                 "elite_rescore", "refine")
 
 
 class mgfwa_config(ctypes.Structure):
@@ -49,7 +51,8 @@ class mgfwa_config(ctypes.Structure):
                 ("guiding_per_firework", ctypes.c_int32), ("sigma", ctypes.c_float), ("boost", ctypes.c_float),
                 ("amp_init", ctypes.c_float), ("c_amplify", ctypes.c_float), ("c_reduce", ctypes.c_float),
                 ("eval_budget", ctypes.c_int64), ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32),
-                ("elite_rescore", ctypes.c_int32), ("n_runs", ctypes.c_int32)]
+                ("elite_rescore", ctypes.c_int32), ("n_runs", ctypes.c_int32), ("refine_every", ctypes.c_int32),
+                ("refine_steps", ctypes.c_int32), ("refine_lr", ctypes.c_float)]
 
 
 class mgfwa_objective(ctypes.Structure):
@@ -114,6 +117,7 @@ def load_library(path: Optional[str] = None):
     L.mgfwa_debug_write.argtypes = [vp, i32, vp, i64]
     L.mgfwa_debug_profile.argtypes = [vp, i32]
     L.mgfwa_debug_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+    L.mgfwa_debug_gradient.argtypes = [vp, f32p, i32, f32p, f32p]
     i32p = ctypes.POINTER(ctypes.c_int32)
     L.mgfwa_evaluate_fp32_noalloc.argtypes = [i32, i32p, i32p, i64, vp, vp, vp, i64, i32, vp, vp]
     L.mgfwa_footprint.argtypes = [ctypes.POINTER(mgfwa_config), ctypes.POINTER(mgfwa_objective),
@@ -256,7 +260,7 @@ class Mgfwa:
     def __init__(self, *, dim, lb, ub, n_fireworks, sparks_per_firework, guiding_per_firework, eval_budget,
                  seed, sigma=0.2, boost=1.0, amp_init=0.0, c_amplify=1.2, c_reduce=0.9, precision=MGFWA_FP32,
                  kind=MGFWA_OBJ_MLP_CE, widths=(), acts=(), X=None, y=None, stream: int = 0, n_runs: int = 1,
-                 elite_rescore: int = 2):
+                 elite_rescore: int = 2, refine_every: int = 0, refine_steps: int = 0, refine_lr: float = 0.0):
         cfg = mgfwa_config_init()
         cfg.dim, cfg.lb, cfg.ub = dim, lb, ub
         cfg.n_fireworks, cfg.sparks_per_firework, cfg.guiding_per_firework = (
@@ -265,6 +269,7 @@ class Mgfwa:
         cfg.eval_budget, cfg.seed, cfg.precision = eval_budget, seed, precision
         cfg.n_runs = n_runs
         cfg.elite_rescore = elite_rescore
+        cfg.refine_every, cfg.refine_steps, cfg.refine_lr = refine_every, refine_steps, refine_lr
         self.cfg = cfg
         self._obj = _ObjectiveBuffers(kind, widths, acts, X, y)
         self.dim = dim
@@ -318,12 +323,23 @@ class Mgfwa:
                   MGFWA_BUF_GUIDES: ((mu * m, D), np.float32), MGFWA_BUF_FIT_E: ((mu * lam,), np.float32),
                   MGFWA_BUF_FIT_G: ((mu * m,), np.float32), MGFWA_BUF_TOP: ((mu, m, k), np.int32),
                   MGFWA_BUF_BOTTOM: ((mu, m, k), np.int32), MGFWA_BUF_WINNER: ((mu,), np.int32),
-                  MGFWA_BUF_BEST_X: ((B, D) if B > 1 else (D,), np.float32), MGFWA_BUF_BEST_F: ((B,), np.float32)}
+                  MGFWA_BUF_BEST_X: ((B, D) if B > 1 else (D,), np.float32), MGFWA_BUF_BEST_F: ((B,), np.float32),
+                  MGFWA_BUF_REFINE_X: ((B, D), np.float32), MGFWA_BUF_REFINE_F: ((B,), np.float32),
+                  MGFWA_BUF_REFINE_ELITE: ((B,), np.int32)}
         shape, dt = shapes[buf]
         return mgfwa_debug_read(self.handle, buf, np.zeros(shape, dt))
 
     def write(self, buf: int, arr: np.ndarray) -> None:
         mgfwa_debug_write(self.handle, buf, arr)
+
+    def gradient(self, xs):
+        """(FP32 objective [count], FP32 gradient [count][D]) of host vectors, by the refinement's kernels."""
+        xs = np.ascontiguousarray(np.atleast_2d(xs), np.float32)
+        g = np.zeros_like(xs)
+        f = np.zeros(xs.shape[0], np.float32)
+        _check(load_library().mgfwa_debug_gradient(self.handle, _f32p(xs), xs.shape[0], _f32p(g), _f32p(f)),
+               self.handle)
+        return f, g
 
     def profile(self, enable: bool = True) -> None:
         _check(load_library().mgfwa_debug_profile(self.handle, int(enable)), self.handle)
@@ -358,7 +374,7 @@ class Mgfwa:
 
 def make_config(*, dim, lb, ub, n_fireworks, sparks_per_firework, guiding_per_firework, eval_budget, seed,
                 sigma=0.2, boost=1.0, amp_init=0.0, c_amplify=1.2, c_reduce=0.9, precision=MGFWA_FP32, n_runs=1,
-                elite_rescore=2) -> mgfwa_config:
+                elite_rescore=2, refine_every=0, refine_steps=0, refine_lr=0.0) -> mgfwa_config:
     cfg = mgfwa_config_init()
     cfg.dim, cfg.lb, cfg.ub = dim, lb, ub
     cfg.n_fireworks, cfg.sparks_per_firework, cfg.guiding_per_firework = (
@@ -366,6 +382,7 @@ def make_config(*, dim, lb, ub, n_fireworks, sparks_per_firework, guiding_per_fi
     cfg.sigma, cfg.boost, cfg.amp_init, cfg.c_amplify, cfg.c_reduce = sigma, boost, amp_init, c_amplify, c_reduce
     cfg.eval_budget, cfg.seed, cfg.precision, cfg.n_runs, cfg.elite_rescore = (
         eval_budget, seed, precision, n_runs, elite_rescore)
+    cfg.refine_every, cfg.refine_steps, cfg.refine_lr = refine_every, refine_steps, refine_lr
     return cfg
 
 

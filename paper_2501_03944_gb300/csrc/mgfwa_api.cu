@@ -15,6 +15,7 @@
 #include "mgfwa.h"
 #include "mgfwa_debug.h"
 #include "fitness_tc.cuh"
+#include "grad.cuh"
 #include "mgfwa_internal.cuh"
 
 using namespace mgfwa;
@@ -56,6 +57,14 @@ struct mgfwa_handle {
   double* ce64 = nullptr;
   double* f64 = nullptr;
   uint32_t* status = nullptr;
+  // hybrid refinement (refine_every > 0): one vector per run
+  bool refine = false;
+  GradPlan gp;
+  float* rw = nullptr;        // [B][Dp] the vector being refined
+  float* rg = nullptr;        // [B][Dp] its gradient
+  float* rf = nullptr;        // [B] FP32 fitness of the refined vector
+  int32_t* relite = nullptr;  // [B] firework refined, index within the run
+  float* gscratch = nullptr;  // backpropagation scratch (GradPlan)
   bool want_op = false; // BF16 tensor-core path: BF16 copies of X and of the first-layer weights
   int64_t P = 0;       // sparks per generation of one run
   int64_t PA = 0;      // sparks per generation of all runs (rows of the spark buffers)
@@ -130,7 +139,8 @@ mgfwa_status cuda_fail(mgfwa_t* h, const char* what) {
 
 int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
-enum { G_EXPLODE = 0, G_FIT_E = 1, G_FINISH = 2, G_RANK = 3, G_GUIDE = 4, G_FIT_G = 5, G_SELECT = 6, G_RESCORE = 7 };
+enum { G_EXPLODE = 0, G_FIT_E = 1, G_FINISH = 2, G_RANK = 3, G_GUIDE = 4, G_FIT_G = 5, G_SELECT = 6, G_RESCORE = 7,
+       G_REFINE = 8 };
 
 // Brackets one kernel group with events when profiling is on.
 struct Mark {
@@ -186,6 +196,14 @@ mgfwa_status eval_rows(mgfwa_t* h, int64_t first, int32_t count, int32_t precisi
   return MGFWA_OK;
 }
 
+// Generation `gen` (1-based) ends with a hybrid refinement.
+bool refine_due(const mgfwa_t* h, int32_t gen) {
+  return h->refine && h->cfg.refine_steps > 0 && gen % h->cfg.refine_every == 0;
+}
+
+// Evaluations one refinement charges: 3 per gradient step, 1 for the result.
+int64_t refine_cost(const mgfwa_t* h) { return 3 * (int64_t)h->cfg.refine_steps + 1; }
+
 __nv_bfloat16* op_rows(mgfwa_t* h, int64_t first) {
   return h->op ? h->op + first * h->mlp.w1_elems : nullptr;
 }
@@ -236,19 +254,42 @@ mgfwa_status run_phase(mgfwa_t* h, int32_t phase) {
       h->evals += h->P;
       return MGFWA_OK;
     }
+    case MGFWA_PHASE_REFINE: {
+      // hybrid refinement of each run's elite: projected gradient descent,
+      // kept on strict improvement
+      if (!refine_due(h, h->gen)) return MGFWA_OK;
+      const mgfwa_config& c = h->cfg;
+      Mark mk(h, G_REFINE);
+      MG_LAUNCH(h, launch_refine_pick(h->fw_x, h->fw_f, p.B, p.mu, p.Dp, h->rw, h->relite, h->stream), "refine pick");
+      for (int32_t s = 0; s < c.refine_steps; ++s) {
+        MG_LAUNCH(h, launch_grad(h->gp, h->mlp, h->rw, p.Dp, h->gscratch, h->rg, nullptr, h->stream),
+                  "refine gradient");
+        MG_LAUNCH(h, launch_sgd(h->rw, h->rg, p.B, p.D, p.Dp, c.refine_lr, p.lb, p.ub, h->stream), "refine step");
+      }
+      MG_LAUNCH(h, launch_grad(h->gp, h->mlp, h->rw, p.Dp, h->gscratch, nullptr, h->rf, h->stream),
+                "refine fitness");
+      MG_LAUNCH(h, launch_refine_accept(h->rw, h->rf, h->relite, h->fw_x, h->fw_f, h->best_x, h->best_f, p.B, p.mu,
+                                        p.Dp, h->stream),
+                "refine accept");
+      h->evals += refine_cost(h);
+      return MGFWA_OK;
+    }
   }
   return fail(h, MGFWA_EINVAL, "unknown phase %d", phase);
 }
 
 mgfwa_status one_generation(mgfwa_t* h) {
-  for (int32_t ph = MGFWA_PHASE_EXPLODE; ph <= MGFWA_PHASE_SELECT; ++ph) {
+  for (int32_t ph = MGFWA_PHASE_EXPLODE; ph <= MGFWA_PHASE_REFINE; ++ph) {
     mgfwa_status st = run_phase(h, ph);
     if (st != MGFWA_OK) return st;
   }
   return MGFWA_OK;
 }
 
-bool budget_allows(const mgfwa_t* h) { return h->evals + h->P <= h->cfg.eval_budget; }
+// The next generation fits: its sparks and, if due, its refinement.
+bool budget_allows(const mgfwa_t* h) {
+  return h->evals + h->P + (refine_due(h, h->gen + 1) ? refine_cost(h) : 0) <= h->cfg.eval_budget;
+}
 
 mgfwa_status check_usable(mgfwa_t* h) {
   if (!h) return MGFWA_EINVAL;
@@ -292,6 +333,14 @@ mgfwa_status validate(const mgfwa_config* c, const mgfwa_objective* o) {
   if (c->eval_budget < c->n_fireworks) return fail(nullptr, MGFWA_EINVAL, "eval_budget below the mu initial evaluations");
   if (c->precision != MGFWA_FP32 && c->precision != MGFWA_BF16)
     return fail(nullptr, MGFWA_EINVAL, "precision %d not supported (FP32 = 0, BF16 = 1)", c->precision);
+  if (c->refine_every < 0) return fail(nullptr, MGFWA_EINVAL, "refine_every must be >= 0");
+  if (c->refine_every > 0) {
+    if (o->kind != MGFWA_OBJ_MLP_CE) return fail(nullptr, MGFWA_EINVAL, "refinement needs an MLP objective");
+    if (c->refine_steps < 1 || c->refine_steps > 10000)
+      return fail(nullptr, MGFWA_EINVAL, "refine_steps must be in [1, 10000]");
+    if (!(c->refine_lr > 0.0f) || !std::isfinite(c->refine_lr))
+      return fail(nullptr, MGFWA_EINVAL, "refine_lr must be positive and finite");
+  }
   if (o->kind == MGFWA_OBJ_SPHERE) return MGFWA_OK;
   if (o->kind != MGFWA_OBJ_MLP_CE) return fail(nullptr, MGFWA_EINVAL, "unknown objective kind %d", o->kind);
   if (o->n_layers < 2 || o->n_layers > 3 || !o->widths || !o->acts || !o->X || !o->y)
@@ -357,7 +406,7 @@ void plan_handle(mgfwa_t* h, const mgfwa_config* cfg, const mgfwa_objective* obj
 
   Mlp& mlp = h->mlp;
   std::memset(&mlp, 0, sizeof(mlp));
-  int64_t d_in = 0, N = 0;
+  int64_t N = 0;
   if (obj->kind == MGFWA_OBJ_MLP_CE) {
     mlp.n_layers = obj->n_layers;
     for (int l = 0; l <= obj->n_layers; ++l) mlp.widths[l] = obj->widths[l];
@@ -371,13 +420,21 @@ void plan_handle(mgfwa_t* h, const mgfwa_config* cfg, const mgfwa_objective* obj
     }
     mlp.N = obj->n_samples;
     mlp.w1_elems = (int64_t)obj->widths[0] * obj->widths[1];
-    d_in = obj->widths[0];
     N = obj->n_samples;
     h->mtiles = (int32_t)((N + 127) / 128);
   } else {
     h->mtiles = 1;
   }
   h->want_op = obj->kind == MGFWA_OBJ_MLP_CE && cfg->precision == MGFWA_BF16;
+  h->refine = cfg->refine_every > 0 && obj->kind == MGFWA_OBJ_MLP_CE;
+  if (h->refine) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms < 1) {
+      cudaGetLastError();
+      sms = 152;  // sizing without a device: a GB300's SM count
+    }
+    h->gp = grad_plan(mlp, p.B, sms);
+  }
 }
 
 // One arena for all device state; sizing (null base) and carving share this
@@ -411,6 +468,13 @@ size_t carve_all(mgfwa_t* h, char* base) {
   h->ce64 = carve<double>(cur, N > 0 ? N : 1);
   h->f64 = carve<double>(cur, 1);
   h->status = carve<uint32_t>(cur, 1);
+  if (h->refine) {
+    h->rw = carve<float>(cur, (int64_t)p.B * p.Dp);
+    h->rg = carve<float>(cur, (int64_t)p.B * p.Dp);
+    h->rf = carve<float>(cur, p.B);
+    h->relite = carve<int32_t>(cur, p.B);
+    h->gscratch = carve<float>(cur, (size_t)h->gp.floats);
+  }
   return (size_t)(cur - base);
 }
 
@@ -669,7 +733,11 @@ mgfwa_status mgfwa_debug_phase(mgfwa_t* h, int32_t phase) {
   if (phase == MGFWA_PHASE_EXPLODE && !budget_allows(h)) return fail(h, MGFWA_EBUDGET, "budget spent");
   st = run_phase(h, phase);
   if (st != MGFWA_OK) return st;
-  h->next_phase = phase == MGFWA_PHASE_SELECT ? MGFWA_PHASE_EXPLODE : phase + 1;
+  // after selection the generation is over unless a refinement is due
+  if (phase == MGFWA_PHASE_SELECT)
+    h->next_phase = refine_due(h, h->gen) ? MGFWA_PHASE_REFINE : MGFWA_PHASE_EXPLODE;
+  else
+    h->next_phase = phase == MGFWA_PHASE_REFINE ? MGFWA_PHASE_EXPLODE : phase + 1;
   return MGFWA_OK;
 }
 
@@ -701,6 +769,18 @@ bool buffer_view(mgfwa_t* h, int32_t buf, BufView* v) {
     case MGFWA_BUF_WINNER: *v = {h->winner, 0, 0, 0, (int64_t)sizeof(int32_t) * F}; return true;
     case MGFWA_BUF_BEST_X: *v = {h->best_x, p.B, rb, pitch, 0}; return true;
     case MGFWA_BUF_BEST_F: *v = {h->best_f, 0, 0, 0, (int64_t)sizeof(float) * p.B}; return true;
+    case MGFWA_BUF_REFINE_X:
+      if (!h->refine) return false;
+      *v = {h->rw, p.B, rb, pitch, 0};
+      return true;
+    case MGFWA_BUF_REFINE_F:
+      if (!h->refine) return false;
+      *v = {h->rf, 0, 0, 0, (int64_t)sizeof(float) * p.B};
+      return true;
+    case MGFWA_BUF_REFINE_ELITE:
+      if (!h->refine) return false;
+      *v = {h->relite, 0, 0, 0, (int64_t)sizeof(int32_t) * p.B};
+      return true;
   }
   return false;
 }
@@ -731,6 +811,25 @@ mgfwa_status mgfwa_debug_write(mgfwa_t* h, int32_t buf, const void* host, int64_
                                              cudaMemcpyHostToDevice, h->stream)
                          : cudaMemcpyAsync(v.dev, host, v.flat_bytes, cudaMemcpyHostToDevice, h->stream);
   if (e != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h, "debug_write");
+  return MGFWA_OK;
+}
+
+mgfwa_status mgfwa_debug_gradient(mgfwa_t* h, const float* xs, int32_t count, float* g_out, float* f_out) {
+  mgfwa_status st = check_usable(h);
+  if (st != MGFWA_OK) return st;
+  const Problem& p = h->p;
+  if (!h->refine) return fail(h, MGFWA_EINVAL, "debug_gradient: handle made without refinement");
+  if (!xs || !g_out || !f_out || count < 1 || count > p.B)
+    return fail(h, MGFWA_EINVAL, "debug_gradient: bad arguments (1 <= count <= %d)", p.B);
+  if (h->next_phase != MGFWA_PHASE_EXPLODE) return fail(h, MGFWA_EINVAL, "a debug generation is in progress");
+  const size_t rb = sizeof(float) * p.D, pitch = sizeof(float) * p.Dp;
+  if (cudaMemcpy2DAsync(h->rw, pitch, xs, rb, rb, count, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return cuda_fail(h, "debug_gradient: copy rows");
+  MG_LAUNCH(h, launch_grad(h->gp, h->mlp, h->rw, p.Dp, h->gscratch, h->rg, h->rf, h->stream), "debug gradient");
+  if (cudaMemcpy2DAsync(g_out, rb, h->rg, pitch, rb, count, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(f_out, h->rf, sizeof(float) * count, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    return cuda_fail(h, "debug_gradient: read");
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h, "debug_gradient synchronise");
   return MGFWA_OK;
 }
 
