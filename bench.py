@@ -41,6 +41,26 @@ def _dist():
     return world, rank, local
 
 
+def run_seed(rank: int) -> int:
+    """Each rank runs its own independent optimisation (weak scaling)."""
+    return 1000 + rank
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The slowest rank's value (timings are max-reduced over ranks)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Units all ranks processed divided by the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def _traffic(kernel: str, source: str):
     """DRAM bytes per launch of `kernel` from the committed ncu capture, or None
     when the kernel's source changed since that capture."""
@@ -189,7 +209,7 @@ def gpu_arm(args):
     pkg.load_library()
     prec = {"bf16": pkg.MGFWA_BF16, "fp32": pkg.MGFWA_FP32}[args.precision]
     X, y = W.make_data(WORKLOAD)
-    seed = 1000 + rank
+    seed = run_seed(rank)
     stream = torch.cuda.Stream()
     hbm_peak, bf16_peak, bf16_sus, peak_src = _peaks()
     P = WORKLOAD.sparks_per_generation
@@ -214,10 +234,8 @@ def gpu_arm(args):
     launches = run.info().kernel_launches - launches0
     ms = ev0.elapsed_time(ev1)
     ktimes = run.kernel_times()
+    ms = max_over_ranks(ms, dist, "cuda")
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     _, best_f, evals = run.best()
     run.close()
@@ -263,16 +281,11 @@ def gpu_arm(args):
         run2.step(args.steps)
         bx2, bf2, ev2 = run2.best()
         run2.close()
-        e2e_s = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
 
     if rank == 0:
-        sparks_total = world * P * args.steps
-        value = sparks_total / (ms / 1e3)
-        e2e_sparks = world * (WORKLOAD.n_fireworks + P * args.steps)
+        value = whole_job_rate(world, P * args.steps, ms / 1e3)
+        e2e_sparks_per_rank = WORKLOAD.n_fireworks + P * args.steps
         # dominant kernel: the explosion-spark fitness launch (mu*lambda sparks per launch)
         fit_ms, fit_n = ktimes["fitness_explosion"]
         n_e = WORKLOAD.n_fireworks * WORKLOAD.sparks_per_firework
@@ -317,7 +330,7 @@ def gpu_arm(args):
                 "data": "synthetic", "config": _config(args, world),
                 "clocks": clk.summary(), "gpu_launches": launches,
                 "e2e": None if e2e_s is None else {
-                    "value": e2e_sparks / e2e_s, "unit": UNIT,
+                    "value": whole_job_rate(world, e2e_sparks_per_rank, e2e_s), "unit": UNIT,
                     "h2d_bytes_per_step": (X.nbytes + y.nbytes) / args.steps,
                     "d2h_bytes_per_step": (4 * D + 8) / args.steps,
                     "note": "create (X, y from pinned host) + K generations + best (x, FP64 loss) + destroy"},
