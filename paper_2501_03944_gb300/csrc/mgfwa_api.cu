@@ -65,6 +65,8 @@ struct mgfwa_handle {
   float* rf = nullptr;        // [B] FP32 fitness of the refined vector
   int32_t* relite = nullptr;  // [B] firework refined, index within the run
   float* gscratch = nullptr;  // backpropagation scratch (GradPlan)
+  cudaGraphExec_t refine_exec = nullptr;  // the refinement's kernels, captured once
+  int64_t refine_kernels = 0;             // kernels in that graph
   bool want_op = false; // BF16 tensor-core path: BF16 copies of X and of the first-layer weights
   int64_t P = 0;       // sparks per generation of one run
   int64_t PA = 0;      // sparks per generation of all runs (rows of the spark buffers)
@@ -208,6 +210,51 @@ __nv_bfloat16* op_rows(mgfwa_t* h, int64_t first) {
   return h->op ? h->op + first * h->mlp.w1_elems : nullptr;
 }
 
+// Enqueue one refinement (pick, steps, fitness of the result, accept) on s;
+// returns the kernels enqueued or -1.
+int enqueue_refine(mgfwa_t* h, cudaStream_t s) {
+  const Problem& p = h->p;
+  const mgfwa_config& c = h->cfg;
+  int n = 0, k;
+  if ((k = launch_refine_pick(h->fw_x, h->fw_f, p.B, p.mu, p.Dp, h->rw, h->relite, s)) < 0) return -1;
+  n += k;
+  for (int32_t i = 0; i < c.refine_steps; ++i) {
+    if ((k = launch_grad(h->gp, h->mlp, h->rw, p.Dp, h->gscratch, h->rg, nullptr, s)) < 0) return -1;
+    n += k;
+    if ((k = launch_sgd(h->rw, h->rg, p.B, p.D, p.Dp, c.refine_lr, p.lb, p.ub, s)) < 0) return -1;
+    n += k;
+  }
+  if ((k = launch_grad(h->gp, h->mlp, h->rw, p.Dp, h->gscratch, nullptr, h->rf, s)) < 0) return -1;
+  n += k;
+  if ((k = launch_refine_accept(h->rw, h->rf, h->relite, h->fw_x, h->fw_f, h->best_x, h->best_f, p.B, p.mu, p.Dp,
+                                s)) < 0)
+    return -1;
+  return n + k;
+}
+
+// Capture the refinement into h->refine_exec (on a private stream, so the
+// caller's stream is never in capture mode).
+mgfwa_status capture_refine(mgfwa_t* h) {
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return cuda_fail(h, "capture stream");
+  cudaGraph_t graph = nullptr;
+  int n = -1;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    n = enqueue_refine(h, cs);
+    if (cudaStreamEndCapture(cs, &graph) != cudaSuccess) n = -1;
+  }
+  mgfwa_status st = MGFWA_OK;
+  if (n < 0 || !graph || cudaGraphInstantiate(&h->refine_exec, graph, 0) != cudaSuccess) {
+    h->refine_exec = nullptr;
+    st = cuda_fail(h, "refine graph capture");
+  } else {
+    h->refine_kernels = n;
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  return st;
+}
+
 mgfwa_status run_phase(mgfwa_t* h, int32_t phase) {
   const Problem& p = h->p;
   const int64_t n_e = (int64_t)p.B * p.mu * p.lam;  // explosion rows of all runs
@@ -256,21 +303,16 @@ mgfwa_status run_phase(mgfwa_t* h, int32_t phase) {
     }
     case MGFWA_PHASE_REFINE: {
       // hybrid refinement of each run's elite: projected gradient descent,
-      // kept on strict improvement
+      // kept on strict improvement.  Its ~12 launches per step do not
+      // depend on the generation, so they are captured once as a CUDA graph.
       if (!refine_due(h, h->gen)) return MGFWA_OK;
-      const mgfwa_config& c = h->cfg;
-      Mark mk(h, G_REFINE);
-      MG_LAUNCH(h, launch_refine_pick(h->fw_x, h->fw_f, p.B, p.mu, p.Dp, h->rw, h->relite, h->stream), "refine pick");
-      for (int32_t s = 0; s < c.refine_steps; ++s) {
-        MG_LAUNCH(h, launch_grad(h->gp, h->mlp, h->rw, p.Dp, h->gscratch, h->rg, nullptr, h->stream),
-                  "refine gradient");
-        MG_LAUNCH(h, launch_sgd(h->rw, h->rg, p.B, p.D, p.Dp, c.refine_lr, p.lb, p.ub, h->stream), "refine step");
+      if (!h->refine_exec) {
+        mgfwa_status st = capture_refine(h);
+        if (st != MGFWA_OK) return st;
       }
-      MG_LAUNCH(h, launch_grad(h->gp, h->mlp, h->rw, p.Dp, h->gscratch, nullptr, h->rf, h->stream),
-                "refine fitness");
-      MG_LAUNCH(h, launch_refine_accept(h->rw, h->rf, h->relite, h->fw_x, h->fw_f, h->best_x, h->best_f, p.B, p.mu,
-                                        p.Dp, h->stream),
-                "refine accept");
+      Mark mk(h, G_REFINE);
+      if (cudaGraphLaunch(h->refine_exec, h->stream) != cudaSuccess) return cuda_fail(h, "refine graph launch");
+      h->launches += h->refine_kernels;
       h->evals += refine_cost(h);
       return MGFWA_OK;
     }
@@ -710,6 +752,7 @@ void mgfwa_destroy(mgfwa_t* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   tc_release(h->tc);
+  if (h->refine_exec) cudaGraphExecDestroy(h->refine_exec);
   if (h->arena) cudaFree(h->arena);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   cudaGetLastError();
