@@ -10,12 +10,13 @@
 namespace mgfwa {
 
 // Scratch layout (float offsets into one device slice of `floats` floats)
-// for R vectors of one MLP: per layer l = 1..L the activations (for l = L
-// the logits, overwritten by dZ_L), per hidden layer its dZ, the
-// per-sample losses, and the split-K partials of the largest product.
+// for R vectors of one MLP: per hidden layer l = 1..L-1 its activations
+// and (with gradients) its dZ, the per-sample losses, and the split-K
+// partials of the largest product.
 struct GradPlan {
   int32_t R = 0;
   int32_t num_sms = 0;
+  bool forward_only = false;  // objective only (no derivative buffers)
   int64_t act_off[4] = {};
   int64_t dz_off[4] = {};
   int64_t loss_off = 0;
@@ -23,13 +24,15 @@ struct GradPlan {
   int64_t floats = 0;
 };
 
-GradPlan grad_plan(const Mlp& mlp, int32_t R, int32_t num_sms);
+GradPlan grad_plan(const Mlp& mlp, int32_t R, int32_t num_sms, bool forward_only = false);
 
 // Forward pass of the R rows W (stride ld) on the batch; with G non-null
 // also the gradient into G (same stride; padding untouched); with f_out
-// non-null the FP32 objective of each row.  Returns kernels enqueued or -1.
+// non-null the FP32 objective of each row.  With idx, row r is W[idx[r]]
+// and its objective goes to f_out[idx[r]] (objective only).  Returns
+// kernels enqueued or -1.
 int launch_grad(const GradPlan& gp, const Mlp& mlp, const float* W, int64_t ld, float* scratch, float* G,
-                float* f_out, cudaStream_t s);
+                float* f_out, cudaStream_t s, const int32_t* idx = nullptr);
 
 // w <- min(max(fma(-lr, g, w), lb), ub) on the first D coordinates of R rows.
 int launch_sgd(float* w, const float* g, int32_t R, int64_t D, int64_t Dp, float lr, float lb, float ub,
@@ -40,8 +43,10 @@ int launch_refine_pick(const float* fw_x, const float* fw_f, int32_t R, int32_t 
                        int32_t* elite, cudaStream_t s);
 
 // Per run r: if fr[r] is strictly below the elite's fitness, the elite
-// firework takes w[r] and fr[r]; the run's best-so-far likewise.
-int launch_refine_accept(const float* w, const float* fr, const int32_t* elite, float* fw_x, float* fw_f,
-                         float* best_x, float* best_f, int32_t R, int32_t mu, int64_t Dp, cudaStream_t s);
+// firework takes w[r] and fr[r]; the run's best-so-far likewise.  flags
+// ([R] int32 device scratch) carries the decisions to the row copies.
+int launch_refine_accept(const float* w, const float* fr, const int32_t* elite, int32_t* flags, float* fw_x,
+                         float* fw_f, float* best_x, float* best_f, int32_t R, int32_t mu, int64_t Dp,
+                         cudaStream_t s);
 
 }  // namespace mgfwa

@@ -145,133 +145,6 @@ __global__ void __launch_bounds__(kThreads) k_fitness_simt(Mlp mlp, const float*
   }
 }
 
-// Small-count FP32 path (a few sparks, e.g. the elite re-score) of a
-// two-layer net.  Layer 1 is a register-tiled FP32 GEMM on tiles of 64
-// samples x 64 hidden units of one spark (256 threads, 4 x 4 outputs each,
-// K in steps of 16), so that a handful of sparks still gives hundreds of
-// blocks; the activated hidden layer goes to Hs[count][h1][N] (sample-minor,
-// so the tail's loads coalesce), and k_tail_f32 runs layer 2 and the loss.
-constexpr int kSmM = 64, kSmH = 64, kSmK = 16;
-
-__global__ void __launch_bounds__(256) k_hidden_f32(Mlp mlp, const float* __restrict__ rows, int64_t ld,
-                                                    const int32_t* __restrict__ idx, float* __restrict__ Hs) {
-  __shared__ __align__(16) float Xs[kSmK][kSmM];
-  __shared__ __align__(16) float Ws[kSmK][kSmH];
-  const int r = blockIdx.x;
-  const float* w = rows + (int64_t)(idx != nullptr ? idx[r] : r) * ld;
-  const int d_in = mlp.widths[0], h1 = mlp.widths[1];
-  const int64_t n0 = (int64_t)blockIdx.y * kSmM;
-  const int j0 = blockIdx.z * kSmH;
-  const int t = threadIdx.x, tn = t >> 4, tj = t & 15;   // 4 samples x 4 hidden units per thread
-  // loader coordinates: one float4 of X and one of W per thread per K step
-  const int ln = t >> 2, lk = (t & 3) * 4;
-  float acc[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc[a][c] = 0.0f;
-  const int64_t xn = n0 + ln;
-  const bool xok = xn < mlp.N;
-  const bool wok = j0 + ln < h1;
-  const float* xp = mlp.X + xn * d_in + lk;
-  const float* wp = w + (int64_t)(j0 + ln) * d_in + lk;
-  float4 xv = make_float4(0.f, 0.f, 0.f, 0.f), wv = xv;
-  if (xok && lk < d_in) xv = *reinterpret_cast<const float4*>(xp);
-  if (wok && lk < d_in) wv = *reinterpret_cast<const float4*>(wp);
-  for (int k0 = 0; k0 < d_in; k0 += kSmK) {
-    Xs[lk + 0][ln] = xv.x; Xs[lk + 1][ln] = xv.y; Xs[lk + 2][ln] = xv.z; Xs[lk + 3][ln] = xv.w;
-    Ws[lk + 0][ln] = wv.x; Ws[lk + 1][ln] = wv.y; Ws[lk + 2][ln] = wv.z; Ws[lk + 3][ln] = wv.w;
-    __syncthreads();
-    // prefetch the next K step while this one is multiplied
-    const int kn = k0 + kSmK + lk;
-    xv = make_float4(0.f, 0.f, 0.f, 0.f);
-    wv = xv;
-    if (xok && kn < d_in) xv = *reinterpret_cast<const float4*>(xp + k0 + kSmK);
-    if (wok && kn < d_in) wv = *reinterpret_cast<const float4*>(wp + k0 + kSmK);
-#pragma unroll
-    for (int kk = 0; kk < kSmK; ++kk) {
-      const float4 xa = *reinterpret_cast<const float4*>(&Xs[kk][tn * 4]);
-      const float4 wb = *reinterpret_cast<const float4*>(&Ws[kk][tj * 4]);
-      const float xr[4] = {xa.x, xa.y, xa.z, xa.w};
-      const float wr[4] = {wb.x, wb.y, wb.z, wb.w};
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(xr[a], wr[c], acc[a][c]);
-    }
-    __syncthreads();
-  }
-  const float* b1 = w + mlp.b_off[0];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const int j = j0 + tj * 4 + c;
-    if (j >= h1) continue;
-    const float bias = b1[j];
-    float* hrow = Hs + ((int64_t)r * h1 + j) * mlp.N;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int64_t n = n0 + tn * 4 + a;
-      if (n < mlp.N) hrow[n] = act_f(mlp.acts[0], acc[a][c] + bias);
-    }
-  }
-}
-
-// Layer 2 and the cross-entropy of the small-count path: one thread per
-// sample (W2 and b2 staged in shared memory), the block's sum into
-// partial[mt][r] (fixed-order reduction).
-__global__ void __launch_bounds__(128) k_tail_f32(Mlp mlp, const float* __restrict__ rows, int64_t ld,
-                                                  const int32_t* __restrict__ idx, int32_t count,
-                                                  const float* __restrict__ Hs, float* __restrict__ partial) {
-  extern __shared__ float tw[];   // W2 [C][h1] then b2 [C]
-  __shared__ float red[4];
-  const int r = blockIdx.x, mt = blockIdx.y;
-  const float* w = rows + (int64_t)(idx != nullptr ? idx[r] : r) * ld;
-  const int h1 = mlp.widths[1], C = mlp.widths[2];
-  for (int e = threadIdx.x; e < C * h1 + C; e += blockDim.x) tw[e] = w[mlp.w_off[1] + e];  // W2 then b2
-  __syncthreads();
-  const int64_t n = (int64_t)mt * 128 + threadIdx.x;
-  float ce = 0.0f;
-  if (n < mlp.N) {
-    const float* h = Hs + (int64_t)r * h1 * mlp.N + n;
-    const int label = mlp.y[n];
-    float z[32];   // registers: every index below is a compile-time constant
-#pragma unroll
-    for (int c = 0; c < 32; ++c) z[c] = c < C ? tw[C * h1 + c] : 0.0f;
-    for (int j0 = 0; j0 < h1; j0 += 8) {
-      // eight independent loads in flight, then their FMAs
-      float hv[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) hv[q] = j0 + q < h1 ? h[(int64_t)(j0 + q) * mlp.N] : 0.0f;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        if (j0 + q < h1) {
-#pragma unroll
-          for (int c = 0; c < 32; ++c)
-            if (c < C) z[c] = fmaf(tw[c * h1 + j0 + q], hv[q], z[c]);
-        }
-      }
-    }
-    float zmax = z[0], zy = 0.0f;
-#pragma unroll
-    for (int c = 0; c < 32; ++c) {
-      if (c < C) {
-        zmax = fmaxf(zmax, z[c]);
-        if (c == label) zy = z[c];
-      }
-    }
-    float se = 0.0f;
-#pragma unroll
-    for (int c = 0; c < 32; ++c)
-      if (c < C) se += expf(z[c] - zmax);
-    ce = (zmax + logf(se)) - zy;
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) ce += __shfl_xor_sync(0xffffffffu, ce, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ce;
-  __syncthreads();
-  if (threadIdx.x == 0) partial[(int64_t)mt * count + r] = ((red[0] + red[1]) + red[2]) + red[3];
-}
-
 __global__ void k_fitness_finish(const float* __restrict__ partial, int32_t mtiles, int32_t count, float n_f,
                                  const int32_t* __restrict__ idx, float* __restrict__ fit) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -370,21 +243,6 @@ size_t smem_for(const Mlp& mlp) {
 }  // namespace
 
 size_t fitness_simt_smem_bytes(const Mlp& mlp) { return smem_for(mlp); }
-
-int launch_fitness_small(const Mlp& mlp, const float* rows, int64_t ld, int32_t count, const int32_t* idx,
-                         float* hidden, float* partial, float* fit, cudaStream_t s) {
-  if (count <= 0) return 0;
-  dim3 g1(count, (unsigned)((mlp.N + kSmM - 1) / kSmM), (unsigned)((mlp.widths[1] + kSmH - 1) / kSmH));
-  k_hidden_f32<<<g1, 256, 0, s>>>(mlp, rows, ld, idx, hidden);
-  if (cudaPeekAtLastError() != cudaSuccess) return -1;
-  const int mtiles = (int)((mlp.N + 127) / 128);
-  dim3 g2(count, mtiles);
-  const size_t tail_smem = sizeof(float) * ((size_t)mlp.widths[2] * mlp.widths[1] + mlp.widths[2]);
-  k_tail_f32<<<g2, 128, tail_smem, s>>>(mlp, rows, ld, idx, count, hidden, partial);
-  if (cudaPeekAtLastError() != cudaSuccess) return -1;
-  const int f = launch_fitness_finish(partial, mtiles, count, mlp.N, fit, s, idx);
-  return f < 0 ? -1 : 2 + f;
-}
 
 int launch_fitness_finish(const float* partial, int32_t mtiles, int32_t count, int64_t N, float* fit,
                           cudaStream_t s, const int32_t* idx) {

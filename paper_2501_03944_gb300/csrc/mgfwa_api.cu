@@ -51,7 +51,8 @@ struct mgfwa_handle {
   int32_t* bottom = nullptr;
   int32_t* winner = nullptr;
   int32_t* elite = nullptr;     // [B*mu*E] spark rows picked for the FP32 re-score
-  float* hidden = nullptr;      // [B*mu*E][N][h1] FP32 hidden layer of the re-scored sparks
+  GradPlan rescore_plan;        // FP32 forward of the B*mu*E re-scored rows
+  float* rescore_scratch = nullptr;
   float* best_x = nullptr;
   float* best_f = nullptr;
   double* ce64 = nullptr;
@@ -64,6 +65,7 @@ struct mgfwa_handle {
   float* rg = nullptr;        // [B][Dp] its gradient
   float* rf = nullptr;        // [B] FP32 fitness of the refined vector
   int32_t* relite = nullptr;  // [B] firework refined, index within the run
+  int32_t* rflags = nullptr;  // [B] refinement decisions
   float* gscratch = nullptr;  // backpropagation scratch (GradPlan)
   cudaGraphExec_t refine_exec = nullptr;  // the refinement's kernels, captured once
   int64_t refine_kernels = 0;             // kernels in that graph
@@ -226,8 +228,8 @@ int enqueue_refine(mgfwa_t* h, cudaStream_t s) {
   }
   if ((k = launch_grad(h->gp, h->mlp, h->rw, p.Dp, h->gscratch, nullptr, h->rf, s)) < 0) return -1;
   n += k;
-  if ((k = launch_refine_accept(h->rw, h->rf, h->relite, h->fw_x, h->fw_f, h->best_x, h->best_f, p.B, p.mu, p.Dp,
-                                s)) < 0)
+  if ((k = launch_refine_accept(h->rw, h->rf, h->relite, h->rflags, h->fw_x, h->fw_f, h->best_x, h->best_f, p.B,
+                                p.mu, p.Dp, s)) < 0)
     return -1;
   return n + k;
 }
@@ -286,11 +288,10 @@ mgfwa_status run_phase(mgfwa_t* h, int32_t phase) {
       // low precision: each firework's elite candidates get their fitness in FP32
       const int32_t E = h->cfg.elite_rescore;
       if (prec == MGFWA_FP32 || E <= 0 || h->kind != MGFWA_OBJ_MLP_CE) return MGFWA_OK;
-      const int32_t count = p.B * p.mu * E;
       Mark mk(h, G_RESCORE);
       MG_LAUNCH(h, launch_elite_pick(p, h->fit, h->fit + n_e, E, h->elite, h->stream), "elite pick");
-      MG_LAUNCH(h, launch_fitness_small(h->mlp, h->sparks, p.Dp, count, h->elite, h->hidden, h->partial, h->fit,
-                                        h->stream),
+      MG_LAUNCH(h, launch_grad(h->rescore_plan, h->mlp, h->sparks, p.Dp, h->rescore_scratch, nullptr, h->fit,
+                               h->stream, h->elite),
                 "elite FP32 fitness");
       return MGFWA_OK;
     }
@@ -469,13 +470,15 @@ void plan_handle(mgfwa_t* h, const mgfwa_config* cfg, const mgfwa_objective* obj
   }
   h->want_op = obj->kind == MGFWA_OBJ_MLP_CE && cfg->precision == MGFWA_BF16;
   h->refine = cfg->refine_every > 0 && obj->kind == MGFWA_OBJ_MLP_CE;
-  if (h->refine) {
+  const bool rescore = h->want_op && cfg->elite_rescore > 0;
+  if (h->refine || rescore) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms < 1) {
       cudaGetLastError();
       sms = 152;  // sizing without a device: a GB300's SM count
     }
-    h->gp = grad_plan(mlp, p.B, sms);
+    if (h->refine) h->gp = grad_plan(mlp, p.B, sms);
+    if (rescore) h->rescore_plan = grad_plan(mlp, p.B * p.mu * cfg->elite_rescore, sms, true);
   }
 }
 
@@ -504,7 +507,7 @@ size_t carve_all(mgfwa_t* h, char* base) {
   h->winner = carve<int32_t>(cur, F);
   h->elite = carve<int32_t>(cur, F * (cfg->elite_rescore > 0 ? cfg->elite_rescore : 1));
   const bool rescore = want_op && cfg->elite_rescore > 0;
-  h->hidden = rescore ? carve<float>(cur, F * cfg->elite_rescore * N * mlp.widths[1]) : nullptr;
+  h->rescore_scratch = rescore ? carve<float>(cur, (size_t)h->rescore_plan.floats) : nullptr;
   h->best_x = carve<float>(cur, (int64_t)p.B * p.Dp);
   h->best_f = carve<float>(cur, p.B);
   h->ce64 = carve<double>(cur, N > 0 ? N : 1);
@@ -515,6 +518,7 @@ size_t carve_all(mgfwa_t* h, char* base) {
     h->rg = carve<float>(cur, (int64_t)p.B * p.Dp);
     h->rf = carve<float>(cur, p.B);
     h->relite = carve<int32_t>(cur, p.B);
+    h->rflags = carve<int32_t>(cur, p.B);
     h->gscratch = carve<float>(cur, (size_t)h->gp.floats);
   }
   return (size_t)(cur - base);

@@ -147,13 +147,6 @@ size_t fitness_simt_smem_bytes(const Mlp& mlp);
 int launch_fitness_finish(const float* partial, int32_t mtiles, int32_t count, int64_t N, float* fit,
                           cudaStream_t s, const int32_t* idx = nullptr);
 
-// FP32 fitness of a few rows of a two-layer net (rows[idx[r]]), written to
-// fit[idx[r]]: layer 1 on small tiles into hidden[count][h1][N], then layer
-// 2 and the loss, then the fixed-order mean.  For counts too small to fill
-// the GPU with launch_fitness_simt_main's 128-sample x 64-unit tiles.
-int launch_fitness_small(const Mlp& mlp, const float* rows, int64_t ld, int32_t count, const int32_t* idx,
-                         float* hidden, float* partial, float* fit, cudaStream_t s);
-
 // Elite candidates for the FP32 re-score: per firework (all runs) the
 // `E` best of its lam explosion and m guiding sparks by the current
 // fitness, as rows of the spark buffer (explosion z*lam + c, guiding

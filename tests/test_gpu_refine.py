@@ -167,3 +167,24 @@ def test_refinement_gains_at_equal_budget(pkg, case):
             hybrid.append(f)
     p = stats.mannwhitneyu(hybrid, plain, alternative="less").pvalue
     assert p < 0.01 and np.median(hybrid) < np.median(plain), (np.median(hybrid), np.median(plain), p)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_refining_batch_equals_runs_made_alone(pkg, precision):
+    """Run b of a refining batch is bitwise the refining run seeded seed + b:
+    the products' split-K chunks depend on their shapes only."""
+    prec = {"fp32": pkg.MGFWA_FP32, "bf16": pkg.MGFWA_BF16}[precision]
+    w = W.scaled(W.MLP_784_64_10, n_samples=300, n_fireworks=3, sparks_per_firework=20, guiding_per_firework=4,
+                 eval_budget=W.budget_for_generations(3, 20, 4, 6) + 3 * 16)
+    X, y = W.make_data(w)
+    kw = dict(refine_every=2, refine_steps=5, refine_lr=0.05)
+    B, seed = 3, 31
+    with pkg.Mgfwa.for_workload(w, seed, precision=prec, X=X, y=y, n_runs=B, **kw) as h:
+        h.run()
+        batched = [h.best(b) for b in range(B)]
+    for b in range(B):
+        with pkg.Mgfwa.for_workload(w, seed + b, precision=prec, X=X, y=y, **kw) as h1:
+            h1.run()
+            x1, f1, e1 = h1.best()
+        bx, bf, be = batched[b]
+        assert np.array_equal(bx, x1) and bf == f1 and be == e1, b
