@@ -140,6 +140,7 @@ class Problem:
     """An objective plus the buffers it points into (kept alive here)."""
 
     def __init__(self, kind: int, dim: int, widths=(), acts=(), X=None, y=None):
+        self.kind = kind
         self.widths = np.ascontiguousarray(widths, dtype=np.int32) if len(widths) else np.zeros(1, np.int32)
         self.acts = np.ascontiguousarray(acts, dtype=np.int32) if len(acts) else np.zeros(1, np.int32)
         self.X = np.ascontiguousarray(X if X is not None else np.zeros((1, 1)), dtype=np.float32)
@@ -277,3 +278,55 @@ def generation(p: Params, prob: Problem, seed: int, gen: int, fw_x, fw_amp, fw_f
     nx, na, nf, win = select(p, fit_e, fit_g, sparks, guides, fw_x, fw_amp, fw_f)
     return dict(sparks=sparks, fit_e64=fit_e64, fit_e=fit_e, top=top, bottom=bot, guides=guides,
                 fit_g64=fit_g64, fit_g=fit_g, fw_x=nx, fw_amp=na, fw_f=nf, winner=win)
+
+
+# ---------------------------------------------------------------------------
+# FP8 (E4M3) operands: what the FP8 tensor-core path computes.
+
+def quantize_e4m3(v) -> np.ndarray:
+    """Round to the nearest value of the OCP FP8 E4M3 format, ties to even,
+    saturating at +-448 (1 sign bit, 4 exponent bits with bias 7, 3 mantissa
+    bits; normal values down to 2^-6, subnormals spaced 2^-9).  Exact: every
+    step is a power-of-two scaling or np.rint of an FP64 value."""
+    v = np.asarray(v, np.float64)
+    a = np.abs(v)
+    m, e = np.frexp(a)                     # a = m 2^e, m in [0.5, 1)
+    spacing = np.where(a >= 2.0 ** -6, np.ldexp(1.0, e - 4), 2.0 ** -9)
+    q = np.rint(a / spacing) * spacing
+    q = np.minimum(q, 448.0)
+    return np.copysign(q, v)
+
+
+def fitness_fp8(prob: Problem, x: np.ndarray, inv_scale_x: float, inv_scale_w: float) -> float:
+    """FP64 objective of the network the FP8 path evaluates: X and the first
+    layer's weights each multiplied by their inverse scale in FP32 and rounded
+    to E4M3, the first layer's products summed and multiplied back by
+    1 / (inv_scale_x inv_scale_w), the rest of the MLP unchanged (the
+    cross-entropy of orc_fitness)."""
+    if prob.kind != MLP_CE:
+        raise ValueError("FP8 objective is defined for MLPs")
+    w = tuple(int(v) for v in prob.widths)
+    X = np.asarray(prob.X, np.float32)
+    y = np.asarray(prob.y)
+    x = np.asarray(x, np.float32)
+    fx, fw = np.float32(inv_scale_x), np.float32(inv_scale_w)
+    Xq = quantize_e4m3(X * fx)
+    d_in, h1 = w[0], w[1]
+    W1q = quantize_e4m3(x[:d_in * h1].reshape(h1, d_in) * fw)
+    scale = 1.0 / (float(fx) * float(fw))
+    off = d_in * h1
+    b1 = x[off:off + h1].astype(np.float64)
+    off += h1
+    a = (Xq @ W1q.T) * np.float64(np.float32(scale)) + b1
+    acts = tuple(int(v) for v in prob.acts)
+    for l in range(1, len(w) - 1):
+        a = np.tanh(a) if acts[l - 1] == TANH else np.maximum(a, 0.0)
+        fi, fo = w[l], w[l + 1]
+        Wl = x[off:off + fi * fo].reshape(fo, fi).astype(np.float64)
+        off += fi * fo
+        bl = x[off:off + fo].astype(np.float64)
+        off += fo
+        a = a @ Wl.T + bl
+    zmax = a.max(axis=1, keepdims=True)
+    lse = zmax[:, 0] + np.log(np.exp(a - zmax).sum(axis=1))
+    return float(np.mean(lse - a[np.arange(a.shape[0]), y]))
