@@ -207,7 +207,7 @@ def gpu_arm(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_2501_03944_gb300 as pkg
     pkg.load_library()
-    prec = {"bf16": pkg.MGFWA_BF16, "fp32": pkg.MGFWA_FP32}[args.precision]
+    prec = {"bf16": pkg.MGFWA_BF16, "fp32": pkg.MGFWA_FP32, "fp8": pkg.MGFWA_FP8}[args.precision]
     X, y = W.make_data(WORKLOAD)
     seed = run_seed(rank)
     stream = torch.cuda.Stream()
@@ -263,6 +263,9 @@ def gpu_arm(args):
     if not args.no_extras:
         # the plain FP32 one-run path the low-precision path is compared with
         extra["fp32_one_run"] = dict(timed_generations({"precision": pkg.MGFWA_FP32}, 5), precision="fp32")
+        # E4M3 first layer on the tensor cores (elite candidates re-scored in FP32)
+        extra["fp8_one_run"] = dict(timed_generations({"precision": pkg.MGFWA_FP8}, max(5, args.steps // 2)),
+                                    precision="fp8")
         # 8 independent runs of the same workload in one handle (one fitness launch per generation)
         extra["batched_8_runs"] = dict(timed_generations({"precision": prec, "n_runs": 8}, max(5, args.steps // 2)),
                                        runs=8, precision=args.precision)
@@ -296,6 +299,9 @@ def gpu_arm(args):
         if prec == pkg.MGFWA_BF16:
             roof = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": bf16_sus, "unit": "TFLOP/s",
                     "peak_source": f"{peak_src} bf16 sustained (kernel timed inside a long step)"}
+        elif prec == pkg.MGFWA_FP8:
+            roof = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": 2.0 * bf16_sus, "unit": "TFLOP/s",
+                    "peak_source": f"{peak_src} bf16 sustained x 2 (the nominal fp8 / bf16 dense ratio)"}
         else:
             # FP32 CUDA-core path: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
             fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -309,7 +315,7 @@ def gpu_arm(args):
         # HBM-bound kernels: algorithmic bytes / time
         D = WORKLOAD.dim
         w1 = WORKLOAD.widths[0] * WORKLOAD.widths[1]
-        op_b = 2 * w1 if prec == pkg.MGFWA_BF16 else 0
+        op_b = {pkg.MGFWA_BF16: 2 * w1, pkg.MGFWA_FP8: w1}.get(prec, 0)
         exp_bytes = n_e * (4 * D + op_b)
         k = 5
         n_g = WORKLOAD.n_fireworks * WORKLOAD.guiding_per_firework
@@ -326,7 +332,7 @@ def gpu_arm(args):
             cb = {k2: c[k2] for k2 in ("value", "unit", "cores", "kind", "sample")}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": {"bf16": "bf16", "fp32": "f32"}[args.precision],
+                "vs_baseline": None, "dtype": {"bf16": "bf16", "fp32": "f32", "fp8": "e4m3"}[args.precision],
                 "data": "synthetic", "config": _config(args, world),
                 "clocks": clk.summary(), "gpu_launches": launches,
                 "e2e": None if e2e_s is None else {
@@ -396,7 +402,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=("gb300", "reference"))
-    ap.add_argument("--precision", default="bf16", choices=("bf16", "fp32"))
+    ap.add_argument("--precision", default="bf16", choices=("bf16", "fp32", "fp8"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end request (profiling runs)")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP32 and batched comparison runs")

@@ -53,7 +53,8 @@ typedef enum {
 typedef enum {
   MGFWA_FP32 = 0, /* FP32 CUDA-core fitness */
   MGFWA_BF16 = 1, /* tensor cores (tcgen05): BF16 first layer, TF32 second layer, FP32 accumulate */
-  MGFWA_FP8 = 2   /* reserved: FP8 E4M3 first layer with per-spark scales */
+  MGFWA_FP8 = 2,  /* tensor cores: E4M3 first layer (X scaled by 448 / max|X|, weights by 448 / max(|lb|, |ub|),
+                     the product rescaled before the bias), TF32 second layer, FP32 accumulate; d_in % 16 == 0 */
 } mgfwa_precision;
 
 enum { MGFWA_OBJ_MLP_CE = 0, MGFWA_OBJ_SPHERE = 1 };
@@ -156,6 +157,8 @@ typedef struct {
   int64_t device_bytes;    /* bytes of the handle's device allocation */
   int64_t kernel_launches; /* kernels enqueued so far by this handle */
   int32_t n_runs;          /* B */
+  float fp8_inv_scale_x;   /* FP8: X is stored as E4M3(X * this); 0 otherwise */
+  float fp8_inv_scale_w;   /* FP8: first-layer weights stored as E4M3(w * this); 0 otherwise */
 } mgfwa_info;
 
 MGFWA_API mgfwa_status mgfwa_get_info(const mgfwa_t* h, mgfwa_info* info);

@@ -65,7 +65,8 @@ class mgfwa_objective(ctypes.Structure):
 class mgfwa_info(ctypes.Structure):
     _fields_ = [("evals", ctypes.c_int64), ("generations", ctypes.c_int32), ("k", ctypes.c_int32),
                 ("dim_padded", ctypes.c_int64), ("sparks_per_gen", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("n_runs", ctypes.c_int32)]
+                ("device_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("n_runs", ctypes.c_int32),
+                ("fp8_inv_scale_x", ctypes.c_float), ("fp8_inv_scale_w", ctypes.c_float)]
 
 
 class mgfwa_request_info(ctypes.Structure):

@@ -10,8 +10,9 @@ namespace mgfwa {
 
 struct TcPlan {
   bool ready = false;
-  CUtensorMap tmap_x;   // X  [N][d_in] BF16, box 128 x 64, 128B swizzle
-  CUtensorMap tmap_w;   // op [P*h1][d_in] BF16, box n_tile x 64, 128B swizzle
+  bool f8 = false;      // E4M3 operands (else BF16)
+  CUtensorMap tmap_x;   // X  [N][d_in], box 128 rows x 128 bytes of K, 128B swizzle
+  CUtensorMap tmap_w;   // op [P*h1][d_in], box n_tile rows x 128 bytes of K, 128B swizzle
   CUtensorMap tmap_w2;  // W2 inside the FP32 spark rows [P][C][h1], box 32 x C x 1, 128B swizzle
   int num_sms = 0;
   int sparks_per_tile = 0;  // whole sparks per N-tile
@@ -24,9 +25,10 @@ struct TcPlan {
 // d_in % 8 == 0, first hidden width 32, 64 or 128, 2..32 classes.
 bool tc_supported(const int32_t* widths, int n_layers);
 
-// Encode the tensor maps over the handle's X (BF16), first-layer operand
-// (BF16) and FP32 spark rows (`sparks`, row stride `ld`, `max_rows` rows).
-mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const __nv_bfloat16* op, const float* sparks, int64_t ld,
+// Encode the tensor maps over the handle's X copy (mlp.Xop), first-layer
+// operand (BF16 or E4M3, op.kind) and FP32 spark rows (`sparks`, row stride
+// `ld`, `max_rows` rows).  E4M3 needs d_in % 16 == 0 (16-byte rows).
+mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const OpDesc& op, const float* sparks, int64_t ld,
                      int64_t max_rows);
 const char* tc_last_error();
 void tc_release(TcPlan& plan);
@@ -34,8 +36,9 @@ void tc_release(TcPlan& plan);
 // Fitness of `count` sparks starting at spark row `first` of the planned
 // buffers: per-(m-tile, spark) partial cross-entropy sums into
 // partial[mtiles][count].  `rows` points at spark `first`'s FP32 row (stride
-// ld).  A device-side wait that gives up sets *status and returns.
+// ld).  The layer-1 accumulator is multiplied by `scale` before the bias
+// (1 for BF16).  A device-side wait that gives up sets *status and returns.
 int launch_fitness_tc(const TcPlan& plan, const Mlp& mlp, int64_t first, const float* rows, int64_t ld,
-                      int32_t count, float* partial, uint32_t* status, cudaStream_t s);
+                      int32_t count, float scale, float* partial, uint32_t* status, cudaStream_t s);
 
 }  // namespace mgfwa

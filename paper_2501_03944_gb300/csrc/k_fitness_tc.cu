@@ -4,7 +4,8 @@
 //
 // Layer 1 of every spark's network is one dense GEMM of the shared batch
 // X [N x d_in] against all sparks' stacked first-layer weights
-// [count*h1 x d_in] (BF16 operands, FP32 accumulation).  A tile is 128
+// [count*h1 x d_in] (BF16 operands, or E4M3 operands with the scales applied
+// in the epilogue; FP32 accumulation).  A tile is 128
 // samples x S whole sparks (S*h1 accumulator columns), so that the tile owns
 // complete hidden vectors.  Layer 2 also runs on the tensor cores: the
 // epilogue adds b1 and applies the activation in place in TMEM, then one
@@ -48,8 +49,8 @@ namespace mgfwa {
 namespace {
 
 constexpr int kBM = 128;         // samples per tile
-constexpr int kBK = 64;          // K elements per stage (128 bytes of BF16: one swizzle row)
-constexpr int kUmmaK = 16;       // K per tcgen05.mma kind::f16
+constexpr int kRowBytes = 128;   // bytes of K per stage row: one 128-byte swizzle row
+constexpr int kUmmaKBytes = 32;  // bytes of K per layer-1 MMA (16 BF16 or 32 E4M3)
 constexpr int kUmmaK2 = 8;       // K per tcgen05.mma kind::tf32
 constexpr int kAtomK2 = 32;      // FP32 elements per 128-byte swizzle row of W2
 constexpr int kEpiWarps = 8;
@@ -169,7 +170,8 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
 }
 
 // Instruction descriptors: D FP32; A and B K-major; kind::f16 with BF16
-// inputs (format 1), kind::tf32 with TF32 inputs (format 2).
+// inputs (format 1), kind::tf32 with TF32 inputs (format 2), kind::f8f6f4
+// with E4M3 inputs (format 0).
 __host__ __device__ constexpr uint32_t instr_desc(int m, int n, uint32_t ab_format) {
   return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((uint32_t)(n >> 3) << 17) |
          ((uint32_t)(m >> 4) << 24);
@@ -180,6 +182,15 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(accum)
       : "memory");
 }
@@ -262,6 +273,7 @@ struct TcArgs {
   int32_t C;            // classes (<= N2)
   int32_t act;
   int32_t c_pad;        // C rounded up to 4 (floats of b2 copied)
+  float scale;          // layer-1 accumulator multiplier (1 for BF16; 1 / (inv_x inv_w) for E4M3)
   int64_t N;
   int64_t ld;           // FP32 row stride of the sparks
   int64_t b1_off, b2_off;
@@ -271,10 +283,11 @@ struct TcArgs {
   uint32_t* status;
 };
 
-template <int H1, int N2>
+template <int H1, int N2, bool F8>
 __global__ void __launch_bounds__(kThreads, 1)
     k_fitness_tc(const __grid_constant__ CUtensorMap tmap_x, const __grid_constant__ CUtensorMap tmap_w,
                  const __grid_constant__ CUtensorMap tmap_w2, TcArgs a) {
+  constexpr int kBK = F8 ? 128 : 64;  // K elements per stage (one 128-byte row)
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   constexpr int kAtoms = H1 / kAtomK2;               // W2 K-atoms per spark
   constexpr uint32_t kAtomBytes = N2 * 128;          // one W2 K-atom: N2 rows x 128 B
@@ -283,8 +296,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int S = a.S;
   const int n_tile = S * H1;
-  const uint32_t a_bytes = kBM * kBK * 2;
-  const uint32_t b_bytes = (uint32_t)n_tile * kBK * 2;
+  const uint32_t a_bytes = kBM * kRowBytes;
+  const uint32_t b_bytes = (uint32_t)n_tile * kRowBytes;
   uint8_t* stage_a = base;
   uint8_t* stage_b = base + (size_t)a.stages * a_bytes;
   uint8_t* w2s = stage_b + (size_t)a.stages * b_bytes;                           // [kTailBufs][S][kW2Bytes]
@@ -381,7 +394,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
-      const uint32_t idesc1 = instr_desc(kBM, n_tile, 1u);
+      const uint32_t idesc1 = instr_desc(kBM, n_tile, F8 ? 0u : 1u);
       const uint32_t idesc2 = instr_desc(kBM, N2, 2u);
       uint32_t it = 0;
       int local = 0;
@@ -430,9 +443,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t a_addr = smem_u32(stage_a + (size_t)s * a_bytes);
           const uint32_t b_addr = smem_u32(stage_b + (size_t)s * b_bytes);
 #pragma unroll
-          for (int k = 0; k < kBK / kUmmaK; ++k) {
-            mma_bf16(d_tmem, smem_desc(a_addr + k * kUmmaK * 2), smem_desc(b_addr + k * kUmmaK * 2), idesc1,
-                     (kb > 0 || k > 0) ? 1u : 0u);
+          for (int k = 0; k < kRowBytes / kUmmaKBytes; ++k) {
+            if (F8)
+              mma_e4m3(d_tmem, smem_desc(a_addr + k * kUmmaKBytes), smem_desc(b_addr + k * kUmmaKBytes), idesc1,
+                       (kb > 0 || k > 0) ? 1u : 0u);
+            else
+              mma_bf16(d_tmem, smem_desc(a_addr + k * kUmmaKBytes), smem_desc(b_addr + k * kUmmaKBytes), idesc1,
+                       (kb > 0 || k > 0) ? 1u : 0u);
           }
           mma_commit(&sm->empty[s]);
         }
@@ -485,10 +502,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           tmem_wait_ld();
           const float4 bb0 = *reinterpret_cast<const float4*>(b1 + j0);
           const float4 bb1 = *reinterpret_cast<const float4*>(b1 + j0 + 4);
-          h[0] = act_f(a.act, h[0] + bb0.x); h[1] = act_f(a.act, h[1] + bb0.y);
-          h[2] = act_f(a.act, h[2] + bb0.z); h[3] = act_f(a.act, h[3] + bb0.w);
-          h[4] = act_f(a.act, h[4] + bb1.x); h[5] = act_f(a.act, h[5] + bb1.y);
-          h[6] = act_f(a.act, h[6] + bb1.z); h[7] = act_f(a.act, h[7] + bb1.w);
+          // h * scale + b1 (one rounding; exactly h + b1 when scale is 1)
+          const float sc = a.scale;
+          h[0] = act_f(a.act, fmaf(h[0], sc, bb0.x)); h[1] = act_f(a.act, fmaf(h[1], sc, bb0.y));
+          h[2] = act_f(a.act, fmaf(h[2], sc, bb0.z)); h[3] = act_f(a.act, fmaf(h[3], sc, bb0.w));
+          h[4] = act_f(a.act, fmaf(h[4], sc, bb1.x)); h[5] = act_f(a.act, fmaf(h[5], sc, bb1.y));
+          h[6] = act_f(a.act, fmaf(h[6], sc, bb1.z)); h[7] = act_f(a.act, fmaf(h[7], sc, bb1.w));
           tmem_st8(col, h);
         }
       }
@@ -593,20 +612,20 @@ bool encode(CUtensorMap* map, CUtensorMapDataType type, uint32_t rank, const voi
 int n2_of(int C) { return C <= 16 ? 16 : 32; }
 int sparks_per_tile(int h1, int C) { return 256 / (h1 + n2_of(C)); }
 
-template <int H1, int N2>
+template <int H1, int N2, bool F8>
 cudaError_t launch_hn(const TcPlan& plan, const TcArgs& args, cudaStream_t s) {
-  cudaError_t e = ensure_smem_limit<k_fitness_tc<H1, N2>>(plan.smem_bytes);
+  cudaError_t e = ensure_smem_limit<k_fitness_tc<H1, N2, F8>>(plan.smem_bytes);
   if (e != cudaSuccess) return e;
   const int tiles = args.m_tiles * args.n_tiles;
   const int grid = tiles < plan.num_sms ? tiles : plan.num_sms;
-  k_fitness_tc<H1, N2><<<grid, kThreads, plan.smem_bytes, s>>>(plan.tmap_x, plan.tmap_w, plan.tmap_w2, args);
+  k_fitness_tc<H1, N2, F8><<<grid, kThreads, plan.smem_bytes, s>>>(plan.tmap_x, plan.tmap_w, plan.tmap_w2, args);
   return cudaPeekAtLastError();
 }
 
-template <int H1>
+template <int H1, bool F8>
 cudaError_t launch_h1(const TcPlan& plan, const TcArgs& args, cudaStream_t s) {
-  if (args.C <= 16) return launch_hn<H1, 16>(plan, args, s);
-  return launch_hn<H1, 32>(plan, args, s);
+  if (args.C <= 16) return launch_hn<H1, 16, F8>(plan, args, s);
+  return launch_hn<H1, 32, F8>(plan, args, s);
 }
 
 }  // namespace
@@ -619,9 +638,16 @@ bool tc_supported(const int32_t* widths, int n_layers) {
   return widths[2] >= 2 && widths[2] <= 32;
 }
 
-mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const __nv_bfloat16* op, const float* rows, int64_t ld,
+mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const OpDesc& op, const float* rows, int64_t ld,
                      int64_t max_rows) {
   plan = TcPlan();
+  if (op.kind != kOpBf16 && op.kind != kOpFp8) {
+    g_err = "tensor-core path needs a BF16 or FP8 operand";
+    return MGFWA_EINVAL;
+  }
+  const bool f8 = op.kind == kOpFp8;
+  const int esize = f8 ? 1 : 2, bk = kRowBytes / esize;
+  plan.f8 = f8;
   if (!tc_supported(mlp.widths, mlp.n_layers)) {
     g_err = "network shape not supported by the tensor-core path";
     return MGFWA_EINVAL;
@@ -642,7 +668,7 @@ mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const __nv_bfloat16* op, cons
   plan.num_sms = prop.multiProcessorCount;
   plan.sparks_per_tile = sparks_per_tile(h1, C);
   plan.n_tile = plan.sparks_per_tile * h1;
-  const size_t a_bytes = (size_t)kBM * kBK * 2, b_bytes = (size_t)plan.n_tile * kBK * 2;
+  const size_t a_bytes = (size_t)kBM * kRowBytes, b_bytes = (size_t)plan.n_tile * kRowBytes;
   const size_t w2_bytes = kTailBufs * (size_t)plan.sparks_per_tile * (h1 / kAtomK2) * n2 * 128;
   const size_t tail_bytes =
       sizeof(float) * (kTailBufs * (size_t)plan.sparks_per_tile * (h1 + 32) + 4 * plan.sparks_per_tile);
@@ -656,19 +682,20 @@ mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const __nv_bfloat16* op, cons
   }
   plan.stages = stages;
   plan.smem_bytes = fixed + stages * (a_bytes + b_bytes);
+  const CUtensorMapDataType dt = f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   {
-    // X [N][d_in] BF16, box 64 x 128
+    // X [N][d_in], box (one 128-byte row of K) x 128
     cuuint64_t dims[2] = {(cuuint64_t)d_in, (cuuint64_t)mlp.N};
-    cuuint64_t strides[1] = {(cuuint64_t)d_in * 2};
-    cuuint32_t box[2] = {kBK, kBM};
-    if (!encode(&plan.tmap_x, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, mlp.Xbf, dims, strides, box)) return MGFWA_ECUDA;
+    cuuint64_t strides[1] = {(cuuint64_t)d_in * esize};
+    cuuint32_t box[2] = {(cuuint32_t)bk, kBM};
+    if (!encode(&plan.tmap_x, dt, 2, mlp.Xop, dims, strides, box)) return MGFWA_ECUDA;
   }
   {
-    // first-layer operand [max_rows*h1][d_in] BF16, box 64 x n_tile
+    // first-layer operand [max_rows*h1][d_in], box (one 128-byte row of K) x n_tile
     cuuint64_t dims[2] = {(cuuint64_t)d_in, (cuuint64_t)(max_rows * h1)};
-    cuuint64_t strides[1] = {(cuuint64_t)d_in * 2};
-    cuuint32_t box[2] = {kBK, (cuuint32_t)plan.n_tile};
-    if (!encode(&plan.tmap_w, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, op, dims, strides, box)) return MGFWA_ECUDA;
+    cuuint64_t strides[1] = {(cuuint64_t)d_in * esize};
+    cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)plan.n_tile};
+    if (!encode(&plan.tmap_w, dt, 2, op.base, dims, strides, box)) return MGFWA_ECUDA;
   }
   {
     // W2 of every spark straight from the FP32 rows: [max_rows][C][h1], box 32 x C x 1
@@ -687,7 +714,7 @@ const char* tc_last_error() { return g_err.c_str(); }
 void tc_release(TcPlan& plan) { plan.ready = false; }
 
 int launch_fitness_tc(const TcPlan& plan, const Mlp& mlp, int64_t first, const float* rows, int64_t ld,
-                      int32_t count, float* partial, uint32_t* status, cudaStream_t s) {
+                      int32_t count, float scale, float* partial, uint32_t* status, cudaStream_t s) {
   if (!plan.ready || count <= 0) return count <= 0 ? 0 : -1;
   const int h1 = mlp.widths[1];
   TcArgs a;
@@ -696,7 +723,9 @@ int launch_fitness_tc(const TcPlan& plan, const Mlp& mlp, int64_t first, const f
   a.m_tiles = (int32_t)((mlp.N + kBM - 1) / kBM);
   a.S = plan.sparks_per_tile;
   a.n_tiles = (count + a.S - 1) / a.S;
-  a.k_blocks = (mlp.widths[0] + kBK - 1) / kBK;
+  const int bk = plan.f8 ? 128 : 64;
+  a.k_blocks = (mlp.widths[0] + bk - 1) / bk;
+  a.scale = scale;
   a.stages = plan.stages;
   a.C = mlp.widths[2];
   a.act = mlp.acts[0];
@@ -710,10 +739,13 @@ int launch_fitness_tc(const TcPlan& plan, const Mlp& mlp, int64_t first, const f
   a.partial = partial;
   a.status = status;
   cudaError_t e;
-  switch (h1) {
-    case 32: e = launch_h1<32>(plan, a, s); break;
-    case 64: e = launch_h1<64>(plan, a, s); break;
-    case 128: e = launch_h1<128>(plan, a, s); break;
+  switch (h1 * 2 + (plan.f8 ? 1 : 0)) {
+    case 64: e = launch_h1<32, false>(plan, a, s); break;
+    case 128: e = launch_h1<64, false>(plan, a, s); break;
+    case 256: e = launch_h1<128, false>(plan, a, s); break;
+    case 65: e = launch_h1<32, true>(plan, a, s); break;
+    case 129: e = launch_h1<64, true>(plan, a, s); break;
+    case 257: e = launch_h1<128, true>(plan, a, s); break;
     default: return -1;
   }
   return e == cudaSuccess ? 1 : -1;

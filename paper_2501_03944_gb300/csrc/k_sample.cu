@@ -11,9 +11,11 @@
 // Layout: rows of Dp floats (Dp a multiple of 64, so each row starts on a
 // 256-byte boundary); one thread owns four consecutive coordinates, i.e.
 // one Philox4x32 block, and moves them with 16-byte loads and stores.  The
-// BF16 first-layer operand of a spark is the first w1_elems coordinates of
-// its row, stored contiguously (row-major [h1][d_in]), written with one
-// 8-byte store per thread.
+// tensor-core operand of a spark is the first w1_elems coordinates of its
+// row, stored contiguously (row-major [h1][d_in]) as BF16 (one 8-byte store
+// per thread) or as E4M3 of coordinate * inv_scale (one 4-byte store).
+#include <cuda_fp8.h>
+
 #include "mgfwa_internal.cuh"
 
 namespace mgfwa {
@@ -41,6 +43,24 @@ __device__ __forceinline__ void store_bf16x4(__nv_bfloat16* dst, float a, float 
   v.x = *reinterpret_cast<uint32_t*>(&lo);
   v.y = *reinterpret_cast<uint32_t*>(&hi);
   *reinterpret_cast<uint2*>(dst) = v;
+}
+
+// Four E4M3 values of (v * inv) (round to nearest even, saturating), one
+// 4-byte store.
+__device__ __forceinline__ void store_fp8x4(uint8_t* dst, float inv, float a, float b, float c, float d) {
+  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a * inv, b * inv), __NV_SATFINITE, __NV_E4M3);
+  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c * inv, d * inv), __NV_SATFINITE, __NV_E4M3);
+  *reinterpret_cast<uint32_t*>(dst) = lo | (hi << 16);
+}
+
+// Coordinates [d0, d0 + 4) of operand row `row` (d0 < w1_elems).
+__device__ __forceinline__ void store_op4(const OpDesc& op, int64_t row, int64_t d0, float a, float b, float c,
+                                          float d) {
+  uint8_t* base = static_cast<uint8_t*>(op.base);
+  if (op.kind == kOpFp8)
+    store_fp8x4(base + row * op.w1_elems + d0, op.inv_scale, a, b, c, d);
+  else
+    store_bf16x4(reinterpret_cast<__nv_bfloat16*>(base) + row * op.w1_elems + d0, a, b, c, d);
 }
 
 // grid (coordinate blocks, B * mu): global firework z = b * mu + i.
@@ -74,7 +94,7 @@ __device__ __forceinline__ float signed_u24(uint32_t r) {
 // `full` when all four coordinates are < D.
 __device__ __forceinline__ void explode4(const Problem& p, uint32_t gen, uint32_t unit, uint32_t k0, uint32_t k1,
                                          uint32_t c4, const float4 x4, float amp, float* __restrict__ srow,
-                                         __nv_bfloat16* __restrict__ oprow, uint32_t w1_elems, bool full) {
+                                         const OpDesc& op, uint32_t row, bool full) {
   const uint32_t d0 = c4 * 4u;
   const uint4 r = philox4x32_10(make_uint4(c4, unit, gen, kExplode), k0, k1);
   float v[4];
@@ -99,7 +119,7 @@ __device__ __forceinline__ void explode4(const Problem& p, uint32_t gen, uint32_
       if (d0 + l >= (uint32_t)p.D) v[l] = 0.0f;
   }
   *reinterpret_cast<float4*>(srow + d0) = make_float4(v[0], v[1], v[2], v[3]);
-  if (oprow != nullptr && d0 < w1_elems) store_bf16x4(oprow + d0, v[0], v[1], v[2], v[3]);
+  if (op.kind != kOpNone && d0 < (uint32_t)op.w1_elems) store_op4(op, row, d0, v[0], v[1], v[2], v[3]);
 }
 
 // grid (coordinate blocks, lambda, B * mu): one block covers 2 * kThreads
@@ -109,8 +129,7 @@ __device__ __forceinline__ void explode4(const Problem& p, uint32_t gen, uint32_
 // run b's stream.
 __global__ void __launch_bounds__(kThreads) k_explode(Problem p, uint32_t gen, const float* __restrict__ fw_x,
                                                       const float* __restrict__ fw_amp,
-                                                      float* __restrict__ sparks,
-                                                      __nv_bfloat16* __restrict__ op, int64_t w1_elems) {
+                                                      float* __restrict__ sparks, const OpDesc op) {
   const uint32_t z = blockIdx.z;
   const uint32_t b = z / (uint32_t)p.mu, i = z - b * (uint32_t)p.mu;
   const uint32_t row = z * (uint32_t)p.lam + blockIdx.y;
@@ -120,7 +139,6 @@ __global__ void __launch_bounds__(kThreads) k_explode(Problem p, uint32_t gen, c
   const float amp = fw_amp[z];
   const float* xrow = fw_x + (int64_t)z * p.Dp;
   float* srow = sparks + (int64_t)row * p.Dp;
-  __nv_bfloat16* oprow = op != nullptr ? op + (int64_t)row * w1_elems : nullptr;
   const uint32_t n4 = (uint32_t)(p.Dp / 4);
   const uint32_t full4 = (uint32_t)(p.D / 4);  // blocks whose 4 coordinates are all < D
   const uint32_t c4a = blockIdx.x * (2 * kThreads) + threadIdx.x;
@@ -128,8 +146,8 @@ __global__ void __launch_bounds__(kThreads) k_explode(Problem p, uint32_t gen, c
   float4 xa = make_float4(0.f, 0.f, 0.f, 0.f), xb = xa;
   if (c4a < n4) xa = *reinterpret_cast<const float4*>(xrow + (size_t)c4a * 4);
   if (c4b < n4) xb = *reinterpret_cast<const float4*>(xrow + (size_t)c4b * 4);
-  if (c4a < n4) explode4(p, gen, unit, k0, k1, c4a, xa, amp, srow, oprow, (uint32_t)w1_elems, c4a < full4);
-  if (c4b < n4) explode4(p, gen, unit, k0, k1, c4b, xb, amp, srow, oprow, (uint32_t)w1_elems, c4b < full4);
+  if (c4a < n4) explode4(p, gen, unit, k0, k1, c4a, xa, amp, srow, op, row, c4a < full4);
+  if (c4b < n4) explode4(p, gen, unit, k0, k1, c4b, xb, amp, srow, op, row, c4b < full4);
 }
 
 // Multi-guiding sparks, reading: group q of firework i has ranked index
@@ -141,8 +159,7 @@ __global__ void __launch_bounds__(kThreads) k_guide(Problem p, uint32_t gen, con
                                                     const float* __restrict__ sparks,
                                                     const int32_t* __restrict__ top,
                                                     const int32_t* __restrict__ bottom,
-                                                    float* __restrict__ guides,
-                                                    __nv_bfloat16* __restrict__ op, int64_t w1_elems) {
+                                                    float* __restrict__ guides, const OpDesc op) {
   const int i = blockIdx.z;               // global firework z = b * mu + i_local
   const int gq = i * p.m + blockIdx.y;    // global guiding row z * m + q
   const int run = i / p.mu;
@@ -211,21 +228,24 @@ __global__ void __launch_bounds__(kThreads) k_guide(Problem p, uint32_t gen, con
   for (int l = 0; l < 4; ++l)
     if (d0 + l >= p.D) v[l] = 0.0f;
   *reinterpret_cast<float4*>(guides + (int64_t)gq * p.Dp + d0) = make_float4(v[0], v[1], v[2], v[3]);
-  if (op != nullptr && d0 < w1_elems) store_bf16x4(op + (int64_t)gq * w1_elems + d0, v[0], v[1], v[2], v[3]);
+  if (op.kind != kOpNone && d0 < op.w1_elems) store_op4(op, gq, d0, v[0], v[1], v[2], v[3]);
 }
 
-__global__ void k_to_operand(const float* __restrict__ rows, int64_t ld, int64_t w1_elems,
-                             __nv_bfloat16* __restrict__ op) {
+__global__ void k_to_operand(const float* __restrict__ rows, int64_t ld, const OpDesc op) {
   const int row = blockIdx.y;
   const int64_t d0 = ((int64_t)blockIdx.x * kThreads + threadIdx.x) * 4;
-  if (d0 >= w1_elems) return;
+  if (d0 >= op.w1_elems) return;
   const float4 v = *reinterpret_cast<const float4*>(rows + (int64_t)row * ld + d0);
-  store_bf16x4(op + (int64_t)row * w1_elems + d0, v.x, v.y, v.z, v.w);
+  store_op4(op, row, d0, v.x, v.y, v.z, v.w);
 }
 
-__global__ void k_f32_to_bf16(const float* __restrict__ src, int64_t n, __nv_bfloat16* __restrict__ dst) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    dst[e] = __float2bfloat16_rn(src[e]);
+__global__ void k_f32_to_op(const float* __restrict__ src, int64_t n, int32_t kind, float inv, void* dst) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    if (kind == kOpFp8)
+      static_cast<uint8_t*>(dst)[e] = (uint8_t)__nv_cvt_float_to_fp8(src[e] * inv, __NV_SATFINITE, __NV_E4M3);
+    else
+      static_cast<__nv_bfloat16*>(dst)[e] = __float2bfloat16_rn(src[e]);
+  }
 }
 
 inline unsigned blocks_for(int64_t n4) { return (unsigned)((n4 + kThreads - 1) / kThreads); }
@@ -239,32 +259,31 @@ int launch_init(const Problem& p, float* fw_x, float* fw_amp, cudaStream_t s) {
 }
 
 int launch_explode(const Problem& p, uint32_t gen, const float* fw_x, const float* fw_amp, float* sparks,
-                   __nv_bfloat16* op, int64_t w1_elems, cudaStream_t s) {
+                   const OpDesc& op, cudaStream_t s) {
   dim3 grid((unsigned)((p.Dp / 4 + 2 * kThreads - 1) / (2 * kThreads)), p.lam, p.B * p.mu);
-  k_explode<<<grid, kThreads, 0, s>>>(p, gen, fw_x, fw_amp, sparks, op, w1_elems);
+  k_explode<<<grid, kThreads, 0, s>>>(p, gen, fw_x, fw_amp, sparks, op);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 int launch_guide(const Problem& p, uint32_t gen, const float* fw_x, const float* fw_amp, const float* sparks,
-                 const int32_t* top, const int32_t* bottom, float* guides, __nv_bfloat16* op_guides,
-                 int64_t w1_elems, cudaStream_t s) {
+                 const int32_t* top, const int32_t* bottom, float* guides, const OpDesc& op_guides,
+                 cudaStream_t s) {
   dim3 grid(blocks_for(p.Dp / 4), p.m, p.B * p.mu);
-  k_guide<<<grid, kThreads, 0, s>>>(p, gen, fw_x, fw_amp, sparks, top, bottom, guides, op_guides, w1_elems);
+  k_guide<<<grid, kThreads, 0, s>>>(p, gen, fw_x, fw_amp, sparks, top, bottom, guides, op_guides);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
-int launch_to_operand(const float* rows, int64_t ld, int32_t count, int64_t w1_elems, __nv_bfloat16* op,
-                      cudaStream_t s) {
-  if (count <= 0) return 0;
-  dim3 grid(blocks_for(w1_elems / 4), count);
-  k_to_operand<<<grid, kThreads, 0, s>>>(rows, ld, w1_elems, op);
+int launch_to_operand(const float* rows, int64_t ld, int32_t count, const OpDesc& op, cudaStream_t s) {
+  if (count <= 0 || op.kind == kOpNone) return 0;
+  dim3 grid(blocks_for(op.w1_elems / 4), count);
+  k_to_operand<<<grid, kThreads, 0, s>>>(rows, ld, op);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
-int launch_f32_to_bf16(const float* src, int64_t n, __nv_bfloat16* dst, cudaStream_t s) {
+int launch_f32_to_op(const float* src, int64_t n, int32_t kind, float inv_scale, void* dst, cudaStream_t s) {
   if (n <= 0) return 0;
   const unsigned blocks = (unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-  k_f32_to_bf16<<<blocks, 256, 0, s>>>(src, n, dst);
+  k_f32_to_op<<<blocks, 256, 0, s>>>(src, n, kind, inv_scale, dst);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

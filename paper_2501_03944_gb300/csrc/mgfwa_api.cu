@@ -38,13 +38,16 @@ struct mgfwa_handle {
   size_t arena_bytes = 0;
   // device buffers (carved from the arena)
   float* X = nullptr;
-  __nv_bfloat16* Xbf = nullptr;
+  void* Xop = nullptr;          // [N][d_in] X as the tensor-core operand (BF16 or E4M3)
   int32_t* y = nullptr;
   float* fw_x = nullptr;
   float* fw_amp = nullptr;
   float* fw_f = nullptr;
   float* sparks = nullptr;  // [P][Dp]: explosion rows, then guiding rows
-  __nv_bfloat16* op = nullptr;  // [P][w1_elems] BF16 first-layer operand
+  void* op = nullptr;            // [P][w1_elems] first-layer operand (BF16 or E4M3)
+  int32_t op_kind = kOpNone;
+  float inv_x = 1.0f, inv_w = 1.0f;  // E4M3: stored = E4M3(value * inv)
+  float op_scale = 1.0f;             // layer-1 accumulator multiplier: 1 / (inv_x inv_w)
   float* fit = nullptr;         // [P]
   float* partial = nullptr;     // [mtiles][P]
   int32_t* top = nullptr;
@@ -69,7 +72,7 @@ struct mgfwa_handle {
   float* gscratch = nullptr;  // backpropagation scratch (GradPlan)
   cudaGraphExec_t refine_exec = nullptr;  // the refinement's kernels, captured once
   int64_t refine_kernels = 0;             // kernels in that graph
-  bool want_op = false; // BF16 tensor-core path: BF16 copies of X and of the first-layer weights
+  bool want_op = false; // tensor-core path: operand copies of X and of the first-layer weights
   int64_t P = 0;       // sparks per generation of one run
   int64_t PA = 0;      // sparks per generation of all runs (rows of the spark buffers)
   int32_t mtiles = 0;  // sample tiles of 128
@@ -172,7 +175,7 @@ int32_t subset_size(float sigma, int32_t g) {
 }
 
 bool use_tc(const mgfwa_t* h, int32_t precision) {
-  return h->kind == MGFWA_OBJ_MLP_CE && precision == MGFWA_BF16;
+  return h->kind == MGFWA_OBJ_MLP_CE && (precision == MGFWA_BF16 || precision == MGFWA_FP8);
 }
 
 // Fitness of `count` consecutive spark rows starting at row `first` into
@@ -190,7 +193,8 @@ mgfwa_status eval_rows(mgfwa_t* h, int64_t first, int32_t count, int32_t precisi
   {
     Mark mk(h, group);
     if (use_tc(h, precision))
-      MG_LAUNCH(h, launch_fitness_tc(h->tc, h->mlp, first, rows, h->p.Dp, count, h->partial, h->status, h->stream),
+      MG_LAUNCH(h, launch_fitness_tc(h->tc, h->mlp, first, rows, h->p.Dp, count, h->op_scale, h->partial,
+                                     h->status, h->stream),
                 "tensor-core fitness");
     else
       MG_LAUNCH(h, launch_fitness_simt_main(h->mlp, rows, h->p.Dp, count, h->partial, h->stream), "FP32 fitness");
@@ -208,8 +212,14 @@ bool refine_due(const mgfwa_t* h, int32_t gen) {
 // Evaluations one refinement charges: 3 per gradient step, 1 for the result.
 int64_t refine_cost(const mgfwa_t* h) { return 3 * (int64_t)h->cfg.refine_steps + 1; }
 
-__nv_bfloat16* op_rows(mgfwa_t* h, int64_t first) {
-  return h->op ? h->op + first * h->mlp.w1_elems : nullptr;
+// The operand descriptor of rows [first, ...) (kind none without a tensor-core path).
+OpDesc op_rows(const mgfwa_t* h, int64_t first) {
+  OpDesc d;
+  d.base = h->op;
+  d.kind = h->op ? h->op_kind : kOpNone;
+  d.inv_scale = h->inv_w;
+  d.w1_elems = h->mlp.w1_elems;
+  return d.from(first);
 }
 
 // Enqueue one refinement (pick, steps, fitness of the result, accept) on s;
@@ -265,8 +275,8 @@ mgfwa_status run_phase(mgfwa_t* h, int32_t phase) {
     case MGFWA_PHASE_EXPLODE: {
       h->gen += 1;
       Mark mk(h, G_EXPLODE);
-      MG_LAUNCH(h, launch_explode(p, (uint32_t)h->gen, h->fw_x, h->fw_amp, h->sparks, op_rows(h, 0),
-                                  h->mlp.w1_elems, h->stream), "explode");
+      MG_LAUNCH(h, launch_explode(p, (uint32_t)h->gen, h->fw_x, h->fw_amp, h->sparks, op_rows(h, 0), h->stream),
+                "explode");
       return MGFWA_OK;
     }
     case MGFWA_PHASE_EVAL_E:
@@ -279,7 +289,7 @@ mgfwa_status run_phase(mgfwa_t* h, int32_t phase) {
     case MGFWA_PHASE_GUIDE: {
       Mark mk(h, G_GUIDE);
       MG_LAUNCH(h, launch_guide(p, (uint32_t)h->gen, h->fw_x, h->fw_amp, h->sparks, h->top, h->bottom,
-                                h->sparks + n_e * p.Dp, op_rows(h, n_e), h->mlp.w1_elems, h->stream), "guide");
+                                h->sparks + n_e * p.Dp, op_rows(h, n_e), h->stream), "guide");
       return MGFWA_OK;
     }
     case MGFWA_PHASE_EVAL_G:
@@ -374,8 +384,8 @@ mgfwa_status validate(const mgfwa_config* c, const mgfwa_objective* o) {
   if (PA > (1 << 24)) return fail(nullptr, MGFWA_EINVAL, "n_runs mu (lambda + m) = %lld exceeds 2^24", (long long)PA);
   if (!(c->sigma > 0.0f) || !(c->sigma <= 0.5f)) return fail(nullptr, MGFWA_EINVAL, "sigma must be in (0, 0.5]");
   if (c->eval_budget < c->n_fireworks) return fail(nullptr, MGFWA_EINVAL, "eval_budget below the mu initial evaluations");
-  if (c->precision != MGFWA_FP32 && c->precision != MGFWA_BF16)
-    return fail(nullptr, MGFWA_EINVAL, "precision %d not supported (FP32 = 0, BF16 = 1)", c->precision);
+  if (c->precision != MGFWA_FP32 && c->precision != MGFWA_BF16 && c->precision != MGFWA_FP8)
+    return fail(nullptr, MGFWA_EINVAL, "precision %d not supported (FP32 = 0, BF16 = 1, FP8 = 2)", c->precision);
   if (c->refine_every < 0) return fail(nullptr, MGFWA_EINVAL, "refine_every must be >= 0");
   if (c->refine_every > 0) {
     if (o->kind != MGFWA_OBJ_MLP_CE) return fail(nullptr, MGFWA_EINVAL, "refinement needs an MLP objective");
@@ -407,8 +417,10 @@ mgfwa_status validate(const mgfwa_config* c, const mgfwa_objective* o) {
   const int C = o->widths[o->n_layers];
   for (int64_t n = 0; n < o->n_samples; ++n)
     if (o->y[n] < 0 || o->y[n] >= C) return fail(nullptr, MGFWA_EINVAL, "label y[%lld] out of range", (long long)n);
-  if (c->precision == MGFWA_BF16 && !tc_supported(o->widths, o->n_layers))
-    return fail(nullptr, MGFWA_EINVAL, "BF16 path needs d_in %% 8 == 0 and a first hidden width in {16..256} %% 16");
+  if ((c->precision == MGFWA_BF16 || c->precision == MGFWA_FP8) && !tc_supported(o->widths, o->n_layers))
+    return fail(nullptr, MGFWA_EINVAL, "tensor-core paths need two layers, d_in %% 8 == 0, h1 in {32, 64, 128}");
+  if (c->precision == MGFWA_FP8 && o->widths[0] % 16 != 0)
+    return fail(nullptr, MGFWA_EINVAL, "FP8 path needs d_in %% 16 == 0");
   return MGFWA_OK;
 }
 
@@ -468,7 +480,18 @@ void plan_handle(mgfwa_t* h, const mgfwa_config* cfg, const mgfwa_objective* obj
   } else {
     h->mtiles = 1;
   }
-  h->want_op = obj->kind == MGFWA_OBJ_MLP_CE && cfg->precision == MGFWA_BF16;
+  h->want_op = obj->kind == MGFWA_OBJ_MLP_CE && (cfg->precision == MGFWA_BF16 || cfg->precision == MGFWA_FP8);
+  h->op_kind = !h->want_op ? kOpNone : (cfg->precision == MGFWA_FP8 ? kOpFp8 : kOpBf16);
+  if (h->op_kind == kOpFp8) {
+    // E4M3 scales: X by its largest magnitude, the weights by the box bound
+    // (every coordinate lies in [lb, ub], so no spark exceeds it)
+    float amax = 0.0f;
+    for (int64_t e = 0; e < obj->n_samples * (int64_t)obj->widths[0]; ++e) amax = std::fmax(amax, std::fabs(obj->X[e]));
+    const float bound = std::fmax(std::fabs(cfg->lb), std::fabs(cfg->ub));
+    h->inv_x = amax > 0.0f ? 448.0f / amax : 1.0f;
+    h->inv_w = 448.0f / bound;
+    h->op_scale = (float)(1.0 / ((double)h->inv_x * (double)h->inv_w));
+  }
   h->refine = cfg->refine_every > 0 && obj->kind == MGFWA_OBJ_MLP_CE;
   const bool rescore = h->want_op && cfg->elite_rescore > 0;
   if (h->refine || rescore) {
@@ -492,14 +515,15 @@ size_t carve_all(mgfwa_t* h, char* base) {
   const int64_t N = mlp.N, d_in = mlp.widths[0];
   char* cur = base;
   h->X = carve<float>(cur, N * d_in);
-  h->Xbf = want_op ? carve<__nv_bfloat16>(cur, N * d_in) : nullptr;
+  const int64_t esize = h->op_kind == kOpFp8 ? 1 : 2;
+  h->Xop = want_op ? carve<uint8_t>(cur, N * d_in * esize) : nullptr;
   h->y = carve<int32_t>(cur, N);
   const int64_t F = (int64_t)p.B * p.mu;  // fireworks of all runs
   h->fw_x = carve<float>(cur, F * p.Dp);
   h->fw_amp = carve<float>(cur, F);
   h->fw_f = carve<float>(cur, F);
   h->sparks = carve<float>(cur, h->PA * p.Dp);
-  h->op = want_op ? carve<__nv_bfloat16>(cur, h->PA * mlp.w1_elems) : nullptr;
+  h->op = want_op ? carve<uint8_t>(cur, h->PA * mlp.w1_elems * esize) : nullptr;
   h->fit = carve<float>(cur, h->PA);
   h->partial = carve<float>(cur, (size_t)h->mtiles * h->PA);
   h->top = carve<int32_t>(cur, F * p.m * p.k);
@@ -600,7 +624,7 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
   }
 
   mlp.X = h->X;
-  mlp.Xbf = h->Xbf;
+  mlp.Xop = h->Xop;
   mlp.y = h->y;
 
   auto bail = [&](mgfwa_status s) {
@@ -616,10 +640,10 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
     if (cudaMemcpyAsync(h->X, obj->X, sizeof(float) * N * d_in, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
         cudaMemcpyAsync(h->y, obj->y, sizeof(int32_t) * N, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
       return bail(cuda_fail(h, "copy batch"));
-    if (want_op) CREATE_LAUNCH(launch_f32_to_bf16(h->X, N * d_in, h->Xbf, h->stream), "X to BF16");
+    if (want_op) CREATE_LAUNCH(launch_f32_to_op(h->X, N * d_in, h->op_kind, h->inv_x, h->Xop, h->stream), "X operand");
   }
   if (want_op) {
-    st = tc_plan(h->tc, h->mlp, h->op, h->sparks, p.Dp, h->PA);
+    st = tc_plan(h->tc, h->mlp, op_rows(h, 0), h->sparks, p.Dp, h->PA);
     if (st != MGFWA_OK) {
       h->err = tc_last_error();
       return bail(st);
@@ -633,7 +657,7 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
   if (cudaMemcpy2DAsync(h->sparks, sizeof(float) * p.Dp, h->fw_x, sizeof(float) * p.Dp, sizeof(float) * p.Dp, F,
                         cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
     return bail(cuda_fail(h, "stage init rows"));
-  if (want_op) CREATE_LAUNCH(launch_to_operand(h->sparks, p.Dp, F, mlp.w1_elems, h->op, h->stream), "init operand");
+  if (want_op) CREATE_LAUNCH(launch_to_operand(h->sparks, p.Dp, F, op_rows(h, 0), h->stream), "init operand");
   TRACE("create: staged");
   // with an FP32 elite re-score the initial fireworks are scored in FP32 too
   st = eval_rows(h, 0, F, cfg->elite_rescore > 0 ? MGFWA_FP32 : cfg->precision);
@@ -721,15 +745,17 @@ mgfwa_status mgfwa_evaluate(mgfwa_t* h, const float* xs, int64_t count, int32_t 
   if (st != MGFWA_OK) return st;
   if (!xs || !f_out || count < 0 || count > h->PA)
     return fail(h, MGFWA_EINVAL, "evaluate: bad arguments (count <= %lld)", (long long)h->PA);
-  if (precision != MGFWA_FP32 && precision != MGFWA_BF16) return fail(h, MGFWA_EINVAL, "evaluate: bad precision");
-  if (use_tc(h, precision) && !h->op) return fail(h, MGFWA_EINVAL, "evaluate: handle was created without the BF16 path");
+  if (precision != MGFWA_FP32 && precision != MGFWA_BF16 && precision != MGFWA_FP8)
+    return fail(h, MGFWA_EINVAL, "evaluate: bad precision");
+  if (use_tc(h, precision) && (!h->op || precision != h->cfg.precision))
+    return fail(h, MGFWA_EINVAL, "evaluate: the handle's tensor-core operand is not of precision %d", precision);
   if (h->next_phase != MGFWA_PHASE_EXPLODE) return fail(h, MGFWA_EINVAL, "a debug generation is in progress");
   if (count == 0) return MGFWA_OK;
   if (cudaMemcpy2DAsync(h->sparks, sizeof(float) * h->p.Dp, xs, sizeof(float) * h->p.D, sizeof(float) * h->p.D, count,
                         cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
     return cuda_fail(h, "evaluate: copy rows");
   if (use_tc(h, precision))
-    MG_LAUNCH(h, launch_to_operand(h->sparks, h->p.Dp, (int32_t)count, h->mlp.w1_elems, h->op, h->stream), "evaluate operand");
+    MG_LAUNCH(h, launch_to_operand(h->sparks, h->p.Dp, (int32_t)count, op_rows(h, 0), h->stream), "evaluate operand");
   st = eval_rows(h, 0, (int32_t)count, precision);
   if (st != MGFWA_OK) return st;
   if (cudaMemcpyAsync(f_out, h->fit, sizeof(float) * count, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
@@ -748,6 +774,8 @@ mgfwa_status mgfwa_get_info(const mgfwa_t* h, mgfwa_info* info) {
   info->device_bytes = (int64_t)h->arena_bytes;
   info->kernel_launches = h->launches;
   info->n_runs = h->p.B;
+  info->fp8_inv_scale_x = h->op_kind == kOpFp8 ? h->inv_x : 0.0f;
+  info->fp8_inv_scale_w = h->op_kind == kOpFp8 ? h->inv_w : 0.0f;
   return MGFWA_OK;
 }
 

@@ -39,13 +39,31 @@ struct Mlp {
   int32_t acts[3];     // hidden activations
   int64_t N;
   const float* X;             // [N][d_in] FP32
-  const __nv_bfloat16* Xbf;   // [N][d_in] BF16 (tensor-core path) or null
+  const void* Xop;            // [N][d_in] tensor-core copy of X (BF16 or FP8) or null
   const int32_t* y;           // [N]
   int64_t w_off[3], b_off[3]; // offsets of W_l and b_l in the search vector
   int64_t w1_elems;           // h1 * d_in
 };
 
 enum { kActTanh = 0, kActRelu = 1 };
+
+// The first-layer GEMM operand the samplers write beside the FP32 rows:
+// row r holds the spark's first w1_elems coordinates ([h1][d_in] row-major)
+// as BF16, or as E4M3 of (coordinate * inv_scale) with saturation.
+enum { kOpNone = 0, kOpBf16 = 1, kOpFp8 = 2 };
+struct OpDesc {
+  void* base = nullptr;  // row 0
+  int32_t kind = kOpNone;
+  float inv_scale = 1.0f;
+  int64_t w1_elems = 0;
+  __host__ __device__ int64_t row_bytes() const { return w1_elems * (kind == kOpFp8 ? 1 : 2); }
+  // the descriptor of rows [first, ...)
+  OpDesc from(int64_t first) const {
+    OpDesc d = *this;
+    if (base) d.base = static_cast<uint8_t*>(base) + first * row_bytes();
+    return d;
+  }
+};
 
 // Raise kernel K's dynamic shared-memory limit on the current device once.
 // The attribute belongs to one kernel on one device, so the cache is per
@@ -116,7 +134,7 @@ int launch_init(const Problem& p, float* fw_x, float* fw_amp, cudaStream_t s);
 // Explosion sparks rows [0, mu*lam) of `sparks` (row stride Dp); if `op` is
 // non-null also the BF16 first-layer operand (w1_elems per spark row).
 int launch_explode(const Problem& p, uint32_t gen, const float* fw_x, const float* fw_amp,
-                   float* sparks, __nv_bfloat16* op, int64_t w1_elems, cudaStream_t s);
+                   float* sparks, const OpDesc& op, cudaStream_t s);
 
 int launch_rank(const Problem& p, const float* fit_e, int32_t* top, int32_t* bottom, cudaStream_t s);
 
@@ -124,7 +142,7 @@ int launch_rank(const Problem& p, const float* fit_e, int32_t* top, int32_t* bot
 // null, their operand rows `op_guides`.
 int launch_guide(const Problem& p, uint32_t gen, const float* fw_x, const float* fw_amp,
                  const float* sparks, const int32_t* top, const int32_t* bottom, float* guides,
-                 __nv_bfloat16* op_guides, int64_t w1_elems, cudaStream_t s);
+                 const OpDesc& op_guides, cudaStream_t s);
 
 // Per run: best-so-far over its fireworks (init: the first minimum).
 int launch_run_best_init(const Problem& p, const float* fw_x, const float* fw_f, float* best_x, float* best_f,
@@ -162,8 +180,8 @@ int launch_fitness_f64(const Mlp& mlp, const float* x, double* ce64, double* out
 int launch_sphere_f64(const float* x, int64_t D, double* out, cudaStream_t s);
 
 // BF16 copy of the first-layer weights of `count` rows (stride ld) into op.
-int launch_to_operand(const float* rows, int64_t ld, int32_t count, int64_t w1_elems,
-                      __nv_bfloat16* op, cudaStream_t s);
-int launch_f32_to_bf16(const float* src, int64_t n, __nv_bfloat16* dst, cudaStream_t s);
+int launch_to_operand(const float* rows, int64_t ld, int32_t count, const OpDesc& op, cudaStream_t s);
+// dst[e] = BF16(src[e]) or E4M3(src[e] * inv_scale), e < n.
+int launch_f32_to_op(const float* src, int64_t n, int32_t kind, float inv_scale, void* dst, cudaStream_t s);
 
 }  // namespace mgfwa
