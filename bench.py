@@ -263,6 +263,8 @@ def gpu_arm(args):
     if not args.no_extras:
         # the plain FP32 one-run path the low-precision path is compared with
         extra["fp32_one_run"] = dict(timed_generations({"precision": pkg.MGFWA_FP32}, 5), precision="fp32")
+        # the 3072-128(ReLU)-64(ReLU)-10 network (N = 4096, 8 fireworks x (256 + 8) sparks) in each precision
+        extra["mlp3072_128_64_10"] = precision_sweep_3072(pkg, stream)
         # E4M3 first layer on the tensor cores (elite candidates re-scored in FP32)
         extra["fp8_one_run"] = dict(timed_generations({"precision": pkg.MGFWA_FP8}, max(5, args.steps // 2)),
                                     precision="fp8")
@@ -346,6 +348,32 @@ def gpu_arm(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def precision_sweep_3072(pkg, stream, gens: int = 3):
+    """sparks/s of a few generations of the 3072-128-64-10 workload per precision (after one warm-up
+    generation; FP32 takes 2 generations, it is two orders of magnitude slower)."""
+    import torch
+    w0 = W.MLP_3072_128_64_10
+    X3, y3 = W.make_data(w0)
+    out = {}
+    for name, prec, g in (("bf16", pkg.MGFWA_BF16, gens), ("fp8", pkg.MGFWA_FP8, gens), ("fp32", pkg.MGFWA_FP32, 2)):
+        w = W.scaled(w0, eval_budget=W.budget_for_generations(w0.n_fireworks, w0.sparks_per_firework,
+                                                              w0.guiding_per_firework, g + 1))
+        h = pkg.Mgfwa.for_workload(w, 77, precision=prec, X=X3, y=y3, stream=stream.cuda_stream)
+        h.step(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        h.step(g)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b)
+        _, best_f, _ = h.best()
+        h.close()
+        out[name] = {"sparks_per_s": h.sparks_per_gen * g / (t / 1e3), "ms_per_generation": t / g,
+                     "best_f_fp64": best_f}
+    return out
 
 
 def serving_trace(pkg, X, y, n_requests: int = 48, rate_hz: float = 400.0, max_live: int = 8, seed: int = 5):

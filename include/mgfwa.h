@@ -52,9 +52,12 @@ typedef enum {
 
 typedef enum {
   MGFWA_FP32 = 0, /* FP32 CUDA-core fitness */
-  MGFWA_BF16 = 1, /* tensor cores (tcgen05): BF16 first layer, TF32 second layer, FP32 accumulate */
+  MGFWA_BF16 = 1, /* tensor cores (tcgen05): BF16 first layer, TF32 later layers, FP32 accumulate; MLPs with
+                     d_in % 8 == 0 and two layers (h1 in {32, 64, 128}, <= 32 classes) or three ((h1, h2) in
+                     {(128, 64), (64, 32)}, <= 16 classes) */
   MGFWA_FP8 = 2,  /* tensor cores: E4M3 first layer (X scaled by 448 / max|X|, weights by 448 / max(|lb|, |ub|),
-                     the product rescaled before the bias), TF32 second layer, FP32 accumulate; d_in % 16 == 0 */
+                     the product rescaled before the bias), TF32 later layers, FP32 accumulate; the BF16 shapes
+                     with d_in % 16 == 0 */
 } mgfwa_precision;
 
 enum { MGFWA_OBJ_MLP_CE = 0, MGFWA_OBJ_SPHERE = 1 };

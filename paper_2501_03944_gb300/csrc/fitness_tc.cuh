@@ -13,7 +13,8 @@ struct TcPlan {
   bool f8 = false;      // E4M3 operands (else BF16)
   CUtensorMap tmap_x;   // X  [N][d_in], box 128 rows x 128 bytes of K, 128B swizzle
   CUtensorMap tmap_w;   // op [P*h1][d_in], box n_tile rows x 128 bytes of K, 128B swizzle
-  CUtensorMap tmap_w2;  // W2 inside the FP32 spark rows [P][C][h1], box 32 x C x 1, 128B swizzle
+  CUtensorMap tmap_w2;  // W2 inside the FP32 spark rows [P][C or h2][h1], box 32 x rows x 1, 128B swizzle
+  CUtensorMap tmap_w3;  // three layers: W3 [P][C][h2], box 32 x C x 1
   int num_sms = 0;
   int sparks_per_tile = 0;  // whole sparks per N-tile
   int n_tile = 0;           // accumulator columns per tile (sparks_per_tile * h1)
@@ -21,8 +22,9 @@ struct TcPlan {
   size_t smem_bytes = 0;
 };
 
-// True if the tensor-core path handles this network: two linear layers,
-// d_in % 8 == 0, first hidden width 32, 64 or 128, 2..32 classes.
+// True if the tensor-core path handles this network: d_in % 8 == 0 and
+// either two linear layers with h1 in {32, 64, 128} and 2..32 classes, or
+// three with (h1, h2) in {(128, 64), (64, 32)} and 2..16 classes.
 bool tc_supported(const int32_t* widths, int n_layers);
 
 // Encode the tensor maps over the handle's X copy (mlp.Xop), first-layer

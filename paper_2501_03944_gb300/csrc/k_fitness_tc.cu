@@ -57,7 +57,7 @@ constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kMaxStages = 6;
 constexpr int kTmemCols = 512;   // two halves of 256 columns
-constexpr int kTailBufs = 3;     // (b1, b2, W2) buffers: the producer runs a tile ahead of layer 2
+constexpr int kTailBufs = 3;     // tail buffers (biases, W2[, W3]): the producer runs a tile ahead of layer 2
 constexpr uint64_t kWaitBudget = 1ull << 32;  // clock64 ticks before a wait gives up (~2 s)
 
 struct Smem {
@@ -66,8 +66,10 @@ struct Smem {
   uint64_t tmem_full[2];   // layer 1 of the half's tile is complete
   uint64_t tmem_empty[2];  // layer 2 of the half's tile consumed its TMEM operand
   uint64_t a2_full[2];     // the epilogue wrote act(h + b1) into TMEM
-  uint64_t l2_full[2];     // the half's logits are complete
+  uint64_t l2_full[2];     // layer 2 of the half's tile is complete (logits, or z2 for three layers)
   uint64_t l2_empty[2];    // the epilogue read the half's logits
+  uint64_t a3_full[2];     // three layers: the epilogue wrote act(z2 + b2) into TMEM
+  uint64_t l3_full[2];     // three layers: the half's logits are complete
   uint64_t tail_full[kTailBufs];
   uint64_t tail_empty[kTailBufs];
   uint64_t mma_done;
@@ -276,23 +278,32 @@ struct TcArgs {
   float scale;          // layer-1 accumulator multiplier (1 for BF16; 1 / (inv_x inv_w) for E4M3)
   int64_t N;
   int64_t ld;           // FP32 row stride of the sparks
-  int64_t b1_off, b2_off;
+  int64_t b1_off, b2_off, bl_off;  // biases: layer 1, layer 2 (three layers), last layer
+  int32_t act2;                     // three layers: the second hidden activation
   const float* rows;    // FP32 spark rows of this launch
   const int32_t* y;
   float* partial;       // [m_tiles][count]
   uint32_t* status;
 };
 
-template <int H1, int N2, bool F8>
+// H2 = 0: two layers, logits (NL columns per spark) = act(h + b1) W2^T.
+// H2 > 0: three layers, z2 (H2 columns) = act(h + b1) W2^T, then logits =
+// act(z2 + b2) W3^T, both TF32 MMAs with A from TMEM.
+template <int H1, int H2, int NL, bool F8>
 __global__ void __launch_bounds__(kThreads, 1)
     k_fitness_tc(const __grid_constant__ CUtensorMap tmap_x, const __grid_constant__ CUtensorMap tmap_w,
-                 const __grid_constant__ CUtensorMap tmap_w2, TcArgs a) {
+                 const __grid_constant__ CUtensorMap tmap_w2, const __grid_constant__ CUtensorMap tmap_w3, TcArgs a) {
   constexpr int kBK = F8 ? 128 : 64;  // K elements per stage (one 128-byte row)
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  constexpr int kAtoms = H1 / kAtomK2;               // W2 K-atoms per spark
-  constexpr uint32_t kAtomBytes = N2 * 128;          // one W2 K-atom: N2 rows x 128 B
-  constexpr uint32_t kW2Bytes = kAtoms * kAtomBytes; // W2 tile of one spark
-  constexpr int kTailFloats = H1 + 32;               // b1 then b2 (C <= 32)
+  constexpr bool kL3 = H2 > 0;
+  constexpr int kR2 = kL3 ? H2 : NL;                  // rows of layer 2's B operand
+  constexpr int kAtoms = H1 / kAtomK2;                // W2 K-atoms per spark
+  constexpr uint32_t kAtomBytes = kR2 * 128;          // one W2 K-atom: kR2 rows x 128 B
+  constexpr int kAtoms3 = kL3 ? H2 / kAtomK2 : 0;     // W3 K-atoms per spark
+  constexpr uint32_t kAtomBytes3 = NL * 128;
+  constexpr uint32_t kW2Bytes = kAtoms * kAtomBytes + kAtoms3 * kAtomBytes3;  // W2 [and W3] of one spark
+  constexpr int kTB = kL3 ? 2 : kTailBufs;            // tail buffers in use
+  constexpr int kTailFloats = H1 + H2 + 32;           // b1, [b2,] last bias (C <= 32)
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int S = a.S;
   const int n_tile = S * H1;
@@ -300,9 +311,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t b_bytes = (uint32_t)n_tile * kRowBytes;
   uint8_t* stage_a = base;
   uint8_t* stage_b = base + (size_t)a.stages * a_bytes;
-  uint8_t* w2s = stage_b + (size_t)a.stages * b_bytes;                           // [kTailBufs][S][kW2Bytes]
-  float* tails = reinterpret_cast<float*>(w2s + kTailBufs * (size_t)S * kW2Bytes); // [kTailBufs][S][kTailFloats]
-  float* red = tails + kTailBufs * (size_t)S * kTailFloats;                      // [S][4]
+  uint8_t* w2s = stage_b + (size_t)a.stages * b_bytes;                     // [kTB][S][kW2Bytes]
+  float* tails = reinterpret_cast<float*>(w2s + kTB * (size_t)S * kW2Bytes); // [kTB][S][kTailFloats]
+  float* red = tails + kTB * (size_t)S * kTailFloats;                      // [S][4]
+  // TMEM columns of spark s within a half: layer-1 accumulator, [z2,] logits
+  auto col_h = [&](int sp) { return (uint32_t)(sp * H1); };
+  auto col_z2 = [&](int sp) { return (uint32_t)(S * H1 + sp * H2); };
+  auto col_lg = [&](int sp) { return (uint32_t)(S * (H1 + H2) + sp * NL); };
   Smem* sm = reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(red + 4 * S) + 15) & ~uintptr_t(15));
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -319,8 +334,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&sm->a2_full[b], kEpiWarps);
       mbar_init(&sm->l2_full[b], 1);
       mbar_init(&sm->l2_empty[b], kEpiWarps);
+      mbar_init(&sm->a3_full[b], kEpiWarps);
+      mbar_init(&sm->l3_full[b], 1);
     }
-    for (int b = 0; b < kTailBufs; ++b) {
+    for (int b = 0; b < kTB; ++b) {
       mbar_init(&sm->tail_full[b], 1);
       mbar_init(&sm->tail_empty[b], kEpiWarps);
     }
@@ -346,15 +363,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t it = 0;
       bool ok = true;
       int local = 0;
-      const uint32_t tail_bytes = (uint32_t)(H1 + a.c_pad) * 4u + (uint32_t)kAtoms * (uint32_t)a.C * 128u;
+      const uint32_t tail_bytes = (uint32_t)(H1 + H2 + a.c_pad) * 4u +
+                                  (uint32_t)kAtoms * (uint32_t)(kL3 ? H2 : a.C) * 128u +
+                                  (uint32_t)kAtoms3 * (uint32_t)a.C * 128u;
       for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++local) {
         const int mt = t % a.m_tiles, nt = t / a.m_tiles;
         const int row_x = mt * kBM;
         const int row_w = (a.first_spark + nt * S) * H1;
         {
-          // b1, b2 and W2 of the tile's sparks, for the epilogue and layer 2
-          const int tb = local % kTailBufs;
-          const uint32_t tuse = (uint32_t)(local / kTailBufs);
+          // biases, W2 [and W3] of the tile's sparks, for the epilogue and layers 2 [and 3]
+          const int tb = local % kTB;
+          const uint32_t tuse = (uint32_t)(local / kTB);
           if (!mbar_wait(sm, &sm->tail_empty[tb], (tuse & 1u) ^ 1u, a.status, 1u)) break;
           const int s0 = nt * S;
           const int s_valid = min(S, a.count - s0);
@@ -363,11 +382,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             const float* row = a.rows + (int64_t)(s0 + s) * a.ld;
             float* tl = tails + ((size_t)tb * S + s) * kTailFloats;
             bulk_load(tl, row + a.b1_off, (uint32_t)H1 * 4u, &sm->tail_full[tb]);
-            bulk_load(tl + H1, row + a.b2_off, (uint32_t)a.c_pad * 4u, &sm->tail_full[tb]);
+            if (kL3) bulk_load(tl + H1, row + a.b2_off, (uint32_t)H2 * 4u, &sm->tail_full[tb]);
+            bulk_load(tl + H1 + H2, row + a.bl_off, (uint32_t)a.c_pad * 4u, &sm->tail_full[tb]);
             uint8_t* w2 = w2s + ((size_t)tb * S + s) * kW2Bytes;
 #pragma unroll
             for (int at = 0; at < kAtoms; ++at)
               tma_load_3d(w2 + at * kAtomBytes, &tmap_w2, at * kAtomK2, 0, a.first_spark + s0 + s, &sm->tail_full[tb]);
+#pragma unroll
+            for (int at = 0; at < kAtoms3; ++at)
+              tma_load_3d(w2 + kAtoms * kAtomBytes + at * kAtomBytes3, &tmap_w3, at * kAtomK2, 0, a.first_spark + s0 + s,
+                          &sm->tail_full[tb]);
           }
         }
         for (int kb = 0; kb < a.k_blocks; ++kb, ++it) {
@@ -383,8 +407,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       // drain: every issued copy must land before the CTA may exit
-      for (int l = local - kTailBufs > 0 ? local - kTailBufs : 0; l < local; ++l)
-        mbar_drain(&sm->tail_full[l % kTailBufs], (uint32_t)((l / kTailBufs) & 1), a.status);
+      for (int l = local - kTB > 0 ? local - kTB : 0; l < local; ++l)
+        mbar_drain(&sm->tail_full[l % kTB], (uint32_t)((l / kTB) & 1), a.status);
       if (it > 0) {
         const uint32_t last = it - 1;
         for (uint32_t j = (last + 1 > (uint32_t)a.stages ? last + 1 - a.stages : 0); j <= last; ++j)
@@ -395,17 +419,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
       const uint32_t idesc1 = instr_desc(kBM, n_tile, F8 ? 0u : 1u);
-      const uint32_t idesc2 = instr_desc(kBM, N2, 2u);
+      const uint32_t idesc2 = instr_desc(kBM, kR2, 2u);
+      const uint32_t idesc3 = instr_desc(kBM, NL, 2u);
       uint32_t it = 0;
       int local = 0;
       bool ok = true;
-      // layer 2 of the tile with local index j (global index tj): logits = act(h + b1) x W2^T
+      // layer 2 [and 3] of the tile with local index j (global index tj):
+      // logits = act(h + b1) W2^T, or z2 = act(h + b1) W2^T then logits = act(z2 + b2) W3^T
       auto layer2 = [&](int j, int tj) -> bool {
         const int bj = j & 1;
         const uint32_t uj = (uint32_t)(j >> 1);
-        const int tj_buf = j % kTailBufs;
+        const int tj_buf = j % kTB;
         if (!mbar_wait(sm, &sm->a2_full[bj], uj & 1u, a.status, 2u)) return false;
-        if (!mbar_wait(sm, &sm->tail_full[tj_buf], (uint32_t)(j / kTailBufs) & 1u, a.status, 2u)) return false;
+        if (!mbar_wait(sm, &sm->tail_full[tj_buf], (uint32_t)(j / kTB) & 1u, a.status, 2u)) return false;
         if (!mbar_wait(sm, &sm->l2_empty[bj], (uj & 1u) ^ 1u, a.status, 2u)) return false;
         tc_fence_after();
         const int ntj = tj / a.m_tiles;
@@ -417,11 +443,26 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int kk = 0; kk < H1 / kUmmaK2; ++kk) {
             const uint32_t b_addr = w2 + (uint32_t)((kk * kUmmaK2) / kAtomK2) * kAtomBytes +
                                     (uint32_t)((kk * kUmmaK2) % kAtomK2) * 4u;
-            mma_tf32_ta(half + (uint32_t)(n_tile + s * N2), half + (uint32_t)(s * H1 + kk * kUmmaK2),
+            mma_tf32_ta(half + (kL3 ? col_z2(s) : col_lg(s)), half + col_h(s) + (uint32_t)(kk * kUmmaK2),
                         smem_desc(b_addr), idesc2, kk > 0 ? 1u : 0u);
           }
         }
         mma_commit(&sm->l2_full[bj]);
+        if (kL3) {
+          if (!mbar_wait(sm, &sm->a3_full[bj], uj & 1u, a.status, 2u)) return false;
+          tc_fence_after();
+          for (int s = 0; s < s_valid; ++s) {
+            const uint32_t w3 = smem_u32(w2s + ((size_t)tj_buf * S + s) * kW2Bytes) + (uint32_t)(kAtoms * kAtomBytes);
+#pragma unroll
+            for (int kk = 0; kk < (kL3 ? H2 : 8) / kUmmaK2; ++kk) {
+              const uint32_t b_addr = w3 + (uint32_t)((kk * kUmmaK2) / kAtomK2) * kAtomBytes3 +
+                                      (uint32_t)((kk * kUmmaK2) % kAtomK2) * 4u;
+              mma_tf32_ta(half + col_lg(s), half + col_z2(s) + (uint32_t)(kk * kUmmaK2), smem_desc(b_addr), idesc3,
+                          kk > 0 ? 1u : 0u);
+            }
+          }
+          mma_commit(&sm->l3_full[bj]);
+        }
         mma_commit(&sm->tmem_empty[bj]);
         return true;
       };
@@ -484,9 +525,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t n = (int64_t)mt * kBM + row_in_tile;
       const bool valid_row = n < a.N;
       const int label = valid_row ? a.y[n] : 0;   // issued before the waits
-      const int tb = local % kTailBufs;
+      const int tb = local % kTB;
       bool ok = mbar_wait(sm, &sm->tmem_full[b], use & 1u, a.status, 4u);
-      ok = ok && mbar_wait(sm, &sm->tail_full[tb], (uint32_t)(local / kTailBufs) & 1u, a.status, 4u);
+      ok = ok && mbar_wait(sm, &sm->tail_full[tb], (uint32_t)(local / kTB) & 1u, a.status, 4u);
       if (epi_bar_any(!ok || sm->abort_flag)) break;
       tc_fence_after();
       const float* tail = tails + (size_t)tb * S * kTailFloats;
@@ -497,7 +538,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 1
         for (int j0 = 0; j0 < H1; j0 += 8) {
           float h[8];
-          const uint32_t col = hbase + (uint32_t)(s * H1 + j0);
+          const uint32_t col = hbase + col_h(s) + (uint32_t)j0;
           tmem_ld8(col, h);
           tmem_wait_ld();
           const float4 bb0 = *reinterpret_cast<const float4*>(b1 + j0);
@@ -518,12 +559,35 @@ __global__ void __launch_bounds__(kThreads, 1)
       ok = mbar_wait(sm, &sm->l2_full[b], use & 1u, a.status, 4u);
       if (epi_bar_any(!ok || sm->abort_flag)) break;
       tc_fence_after();
-      for (int s = half; s < s_valid; s += 2) {
-        const float* b2 = tail + (size_t)s * kTailFloats + H1;
-        float z[N2];
-        const uint32_t col = hbase + (uint32_t)(n_tile + s * N2);
+      if (kL3) {
+        // act(z2 + b2) in place: the TMEM A operand of layer 3
+        for (int s = half; s < s_valid; s += 2) {
+          const float* b2 = tail + (size_t)s * kTailFloats + H1;
+#pragma unroll 1
+          for (int j0 = 0; j0 < H2; j0 += 8) {
+            float h[8];
+            const uint32_t col = hbase + col_z2(s) + (uint32_t)j0;
+            tmem_ld8(col, h);
+            tmem_wait_ld();
 #pragma unroll
-        for (int q = 0; q < N2; q += 16) tmem_ld16(col + (uint32_t)q, z + q);
+            for (int q = 0; q < 8; ++q) h[q] = act_f(a.act2, h[q] + b2[j0 + q]);
+            tmem_st8(col, h);
+          }
+        }
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm->a3_full[b]);
+        ok = mbar_wait(sm, &sm->l3_full[b], use & 1u, a.status, 4u);
+        if (epi_bar_any(!ok || sm->abort_flag)) break;
+        tc_fence_after();
+      }
+      for (int s = half; s < s_valid; s += 2) {
+        const float* b2 = tail + (size_t)s * kTailFloats + H1 + H2;  // the last layer's bias
+        float z[NL];
+        const uint32_t col = hbase + col_lg(s);
+#pragma unroll
+        for (int q = 0; q < NL; q += 16) tmem_ld16(col + (uint32_t)q, z + q);
         tmem_wait_ld();
         float ce = 0.0f;
         if (valid_row) {
@@ -531,7 +595,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           float zmax = -INFINITY;
           float zy = 0.0f;
 #pragma unroll
-          for (int c = 0; c < N2; ++c) {
+          for (int c = 0; c < NL; ++c) {
             if (c < C) {
               z[c] += b2[c];
               zmax = fmaxf(zmax, z[c]);
@@ -540,7 +604,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           float se = 0.0f;
 #pragma unroll
-          for (int c = 0; c < N2; ++c)
+          for (int c = 0; c < NL; ++c)
             if (c < C) se += expf(z[c] - zmax);
           ce = (zmax + logf(se)) - zy;
         }
@@ -610,32 +674,42 @@ bool encode(CUtensorMap* map, CUtensorMapDataType type, uint32_t rank, const voi
 }
 
 int n2_of(int C) { return C <= 16 ? 16 : 32; }
-int sparks_per_tile(int h1, int C) { return 256 / (h1 + n2_of(C)); }
+// two layers: h2 = 0
+int sparks_per_tile(int h1, int h2, int C) { return 256 / (h1 + h2 + n2_of(C)); }
 
-template <int H1, int N2, bool F8>
+template <int H1, int H2, int NL, bool F8>
 cudaError_t launch_hn(const TcPlan& plan, const TcArgs& args, cudaStream_t s) {
-  cudaError_t e = ensure_smem_limit<k_fitness_tc<H1, N2, F8>>(plan.smem_bytes);
+  cudaError_t e = ensure_smem_limit<k_fitness_tc<H1, H2, NL, F8>>(plan.smem_bytes);
   if (e != cudaSuccess) return e;
   const int tiles = args.m_tiles * args.n_tiles;
   const int grid = tiles < plan.num_sms ? tiles : plan.num_sms;
-  k_fitness_tc<H1, N2, F8><<<grid, kThreads, plan.smem_bytes, s>>>(plan.tmap_x, plan.tmap_w, plan.tmap_w2, args);
+  k_fitness_tc<H1, H2, NL, F8><<<grid, kThreads, plan.smem_bytes, s>>>(plan.tmap_x, plan.tmap_w, plan.tmap_w2,
+                                                                        plan.tmap_w3, args);
   return cudaPeekAtLastError();
 }
 
 template <int H1, bool F8>
 cudaError_t launch_h1(const TcPlan& plan, const TcArgs& args, cudaStream_t s) {
-  if (args.C <= 16) return launch_hn<H1, 16, F8>(plan, args, s);
-  return launch_hn<H1, 32, F8>(plan, args, s);
+  if (args.C <= 16) return launch_hn<H1, 0, 16, F8>(plan, args, s);
+  return launch_hn<H1, 0, 32, F8>(plan, args, s);
 }
 
 }  // namespace
 
 bool tc_supported(const int32_t* widths, int n_layers) {
-  if (n_layers != 2) return false;
-  const int h1 = widths[1];
   if (widths[0] % 8 != 0) return false;
-  if (!(h1 == 32 || h1 == 64 || h1 == 128)) return false;
-  return widths[2] >= 2 && widths[2] <= 32;
+  const int h1 = widths[1];
+  if (n_layers == 2) {
+    if (!(h1 == 32 || h1 == 64 || h1 == 128)) return false;
+    return widths[2] >= 2 && widths[2] <= 32;
+  }
+  if (n_layers == 3) {
+    // (h1, h2) in {(128, 64), (64, 32)}, at most 16 classes
+    const int h2 = widths[2];
+    if (!((h1 == 128 && h2 == 64) || (h1 == 64 && h2 == 32))) return false;
+    return widths[3] >= 2 && widths[3] <= 16;
+  }
+  return false;
 }
 
 mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const OpDesc& op, const float* rows, int64_t ld,
@@ -663,15 +737,19 @@ mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const OpDesc& op, const float
     g_err = "tensor-core path needs a Blackwell (sm_10x) GPU";
     return MGFWA_EINVAL;
   }
-  const int h1 = mlp.widths[1], d_in = mlp.widths[0], C = mlp.widths[2];
+  const bool l3 = mlp.n_layers == 3;
+  const int h1 = mlp.widths[1], d_in = mlp.widths[0], h2 = l3 ? mlp.widths[2] : 0;
+  const int C = mlp.widths[mlp.n_layers];
   const int n2 = n2_of(C);
   plan.num_sms = prop.multiProcessorCount;
-  plan.sparks_per_tile = sparks_per_tile(h1, C);
+  plan.sparks_per_tile = sparks_per_tile(h1, h2, C);
   plan.n_tile = plan.sparks_per_tile * h1;
   const size_t a_bytes = (size_t)kBM * kRowBytes, b_bytes = (size_t)plan.n_tile * kRowBytes;
-  const size_t w2_bytes = kTailBufs * (size_t)plan.sparks_per_tile * (h1 / kAtomK2) * n2 * 128;
+  const int tbufs = l3 ? 2 : kTailBufs;  // the kernel's kTB
+  const size_t wt_bytes = (size_t)(h1 / kAtomK2) * (l3 ? h2 : n2) * 128 + (l3 ? (size_t)(h2 / kAtomK2) * n2 * 128 : 0);
+  const size_t w2_bytes = tbufs * (size_t)plan.sparks_per_tile * wt_bytes;
   const size_t tail_bytes =
-      sizeof(float) * (kTailBufs * (size_t)plan.sparks_per_tile * (h1 + 32) + 4 * plan.sparks_per_tile);
+      sizeof(float) * (tbufs * (size_t)plan.sparks_per_tile * (h1 + h2 + 32) + 4 * plan.sparks_per_tile);
   const size_t fixed = 1024 + w2_bytes + tail_bytes + 16 + sizeof(Smem) + 64;
   const size_t limit = (size_t)prop.sharedMemPerBlockOptin;
   int stages = kMaxStages;
@@ -698,12 +776,23 @@ mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const OpDesc& op, const float
     if (!encode(&plan.tmap_w, dt, 2, op.base, dims, strides, box)) return MGFWA_ECUDA;
   }
   {
-    // W2 of every spark straight from the FP32 rows: [max_rows][C][h1], box 32 x C x 1
-    cuuint64_t dims[3] = {(cuuint64_t)h1, (cuuint64_t)C, (cuuint64_t)max_rows};
+    // W2 of every spark straight from the FP32 rows: [max_rows][C or h2][h1], box 32 x rows x 1
+    const int r2 = l3 ? h2 : C;
+    cuuint64_t dims[3] = {(cuuint64_t)h1, (cuuint64_t)r2, (cuuint64_t)max_rows};
     cuuint64_t strides[2] = {(cuuint64_t)h1 * 4, (cuuint64_t)ld * 4};
-    cuuint32_t box[3] = {kAtomK2, (cuuint32_t)C, 1};
+    cuuint32_t box[3] = {kAtomK2, (cuuint32_t)r2, 1};
     if (!encode(&plan.tmap_w2, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, rows + mlp.w_off[1], dims, strides, box))
       return MGFWA_ECUDA;
+  }
+  if (l3) {
+    // W3 [max_rows][C][h2], box 32 x C x 1
+    cuuint64_t dims[3] = {(cuuint64_t)h2, (cuuint64_t)C, (cuuint64_t)max_rows};
+    cuuint64_t strides[2] = {(cuuint64_t)h2 * 4, (cuuint64_t)ld * 4};
+    cuuint32_t box[3] = {kAtomK2, (cuuint32_t)C, 1};
+    if (!encode(&plan.tmap_w3, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, rows + mlp.w_off[2], dims, strides, box))
+      return MGFWA_ECUDA;
+  } else {
+    plan.tmap_w3 = plan.tmap_w2;  // unused by the two-layer kernels
   }
   plan.ready = true;
   return MGFWA_OK;
@@ -727,18 +816,32 @@ int launch_fitness_tc(const TcPlan& plan, const Mlp& mlp, int64_t first, const f
   a.k_blocks = (mlp.widths[0] + bk - 1) / bk;
   a.scale = scale;
   a.stages = plan.stages;
-  a.C = mlp.widths[2];
+  const bool l3 = mlp.n_layers == 3;
+  a.C = mlp.widths[mlp.n_layers];
   a.act = mlp.acts[0];
+  a.act2 = l3 ? mlp.acts[1] : 0;
   a.c_pad = (a.C + 3) / 4 * 4;
   a.N = mlp.N;
   a.ld = ld;
   a.b1_off = mlp.b_off[0];
-  a.b2_off = mlp.b_off[1];
+  a.b2_off = l3 ? mlp.b_off[1] : 0;
+  a.bl_off = mlp.b_off[mlp.n_layers - 1];
   a.rows = rows;
   a.y = mlp.y;
   a.partial = partial;
   a.status = status;
   cudaError_t e;
+  if (l3) {
+    // three layers: (128, 64) or (64, 32), at most 16 classes
+    const int h2 = mlp.widths[2];
+    if (h1 == 128 && h2 == 64)
+      e = plan.f8 ? launch_hn<128, 64, 16, true>(plan, a, s) : launch_hn<128, 64, 16, false>(plan, a, s);
+    else if (h1 == 64 && h2 == 32)
+      e = plan.f8 ? launch_hn<64, 32, 16, true>(plan, a, s) : launch_hn<64, 32, 16, false>(plan, a, s);
+    else
+      return -1;
+    return e == cudaSuccess ? 1 : -1;
+  }
   switch (h1 * 2 + (plan.f8 ? 1 : 0)) {
     case 64: e = launch_h1<32, false>(plan, a, s); break;
     case 128: e = launch_h1<64, false>(plan, a, s); break;

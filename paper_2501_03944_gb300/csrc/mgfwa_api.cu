@@ -418,7 +418,9 @@ mgfwa_status validate(const mgfwa_config* c, const mgfwa_objective* o) {
   for (int64_t n = 0; n < o->n_samples; ++n)
     if (o->y[n] < 0 || o->y[n] >= C) return fail(nullptr, MGFWA_EINVAL, "label y[%lld] out of range", (long long)n);
   if ((c->precision == MGFWA_BF16 || c->precision == MGFWA_FP8) && !tc_supported(o->widths, o->n_layers))
-    return fail(nullptr, MGFWA_EINVAL, "tensor-core paths need two layers, d_in %% 8 == 0, h1 in {32, 64, 128}");
+    return fail(nullptr, MGFWA_EINVAL,
+                "tensor-core paths need d_in %% 8 == 0 and two layers with h1 in {32, 64, 128} (<= 32 classes) or "
+                "three with (h1, h2) in {(128, 64), (64, 32)} (<= 16 classes)");
   if (c->precision == MGFWA_FP8 && o->widths[0] % 16 != 0)
     return fail(nullptr, MGFWA_EINVAL, "FP8 path needs d_in %% 16 == 0");
   return MGFWA_OK;

@@ -45,6 +45,8 @@ def _rel(a, b):
     ((64, 32, 7), (0,), 129, 24),          # ragged tail of one sample
     ((96, 128, 5), (1,), 1, 16),           # a single sample
     ((48, 128, 4), (1,), 260, 12),         # two sparks per tile, K = 48 inside one K block
+    ((64, 64, 32, 5), (1, 0), 300, 24),    # three layers (ReLU, tanh): layers 2 and 3 on the tensor cores
+    ((3072, 128, 64, 10), (1, 1), 256, 12),  # the 3072-128-64-10 network, one spark per tile
 ])
 def test_bf16_fitness_against_oracle(pkg, widths, acts, N, count):
     w = W.scaled(W.MLP_784_64_10, widths=widths, acts=acts, n_samples=N, n_fireworks=2,
@@ -67,8 +69,10 @@ def test_bf16_fitness_against_oracle(pkg, widths, acts, N, count):
 
 
 def test_bf16_rejects_unsupported_shapes(pkg):
-    """The tensor-core path takes two-layer nets with h1 in {32, 64, 128}; others get EINVAL at create."""
-    for widths, acts in (((8, 16, 3), (0,)), ((24, 16, 8, 5), (1, 1)), ((64, 48, 7), (1,))):
+    """The tensor-core path takes two-layer nets with h1 in {32, 64, 128} and three-layer nets with (h1, h2) in
+    {(128, 64), (64, 32)} and at most 16 classes; others get EINVAL at create."""
+    for widths, acts in (((8, 16, 3), (0,)), ((24, 16, 8, 5), (1, 1)), ((64, 48, 7), (1,)),
+                         ((64, 64, 64, 5), (1, 1)), ((64, 64, 32, 20), (1, 1))):
         w = W.scaled(W.MLP_784_64_10, widths=widths, acts=acts, n_samples=64, n_fireworks=2,
                      sparks_per_firework=8, guiding_per_firework=2)
         X, y = W.make_data(w)

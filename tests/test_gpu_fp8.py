@@ -41,6 +41,8 @@ def _rel(a, b):
     ((16, 32, 3), (0,), 300, 56),          # K = 16 < one 128-element K block (TMA zero fill), tanh
     ((64, 32, 7), (0,), 129, 24),          # ragged tail of one sample
     ((48, 128, 4), (1,), 260, 12),         # two sparks per tile
+    ((64, 64, 32, 5), (1, 0), 300, 24),    # three layers (ReLU, tanh)
+    ((3072, 128, 64, 10), (1, 1), 256, 12),  # the 3072-128-64-10 network
 ])
 def test_fp8_fitness_equals_quantized_oracle(pkg, widths, acts, N, count):
     w = W.scaled(W.MLP_784_64_10, widths=widths, acts=acts, n_samples=N, n_fireworks=2,
