@@ -260,6 +260,7 @@ def gpu_arm(args):
     extra = {}
     if not args.no_extras and world == 1:
         extra["serving"] = serving_trace(pkg, X, y)
+        extra["grouped_64_mixed"] = grouped_mixed(pkg)
     if not args.no_extras:
         # the plain FP32 one-run path the low-precision path is compared with
         extra["fp32_one_run"] = dict(timed_generations({"precision": pkg.MGFWA_FP32}, 5), precision="fp32")
@@ -373,6 +374,60 @@ def precision_sweep_3072(pkg, stream, gens: int = 3):
         h.close()
         out[name] = {"sparks_per_s": h.sparks_per_gen * g / (t / 1e3), "ms_per_generation": t / g,
                      "best_f_fp64": best_f}
+    return out
+
+
+def grouped_mixed(pkg, n: int = 64, gens: int = 5, seed: int = 3):
+    """64 runs of different shapes (D log-uniform in [195, 50,890] over the MLP families, 3..8 fireworks,
+    32..256 sparks, batches of 512..2048; BF16 where the tensor-core path takes the net, else FP32), timed
+    end to end (wall clock, synchronised) three ways: one CUDA graph launch per generation for all runs
+    (a group), every run's generation launched on its own stream in turn, and one run at a time."""
+    import torch
+    ws = W.mixed_batch(n, seed, generations=gens + 1)
+    data = [W.make_data(w) for w in ws]
+    precs = [pkg.MGFWA_BF16 if w.widths[1] == 64 else pkg.MGFWA_FP32 for w in ws]
+
+    def members():
+        return [pkg.Mgfwa.for_workload(w, 500 + k, precision=p, X=d[0], y=d[1])
+                for k, (w, p, d) in enumerate(zip(ws, precs, data))]
+
+    sparks = gens * sum(w.sparks_per_generation for w in ws)
+    out = {"runs": n, "generations": gens, "sparks_per_step": sparks // gens,
+           "dims": [int(min(w.dim for w in ws)), int(max(w.dim for w in ws))]}
+    hs = members()
+    g = pkg.Group(hs)
+    g.step(1)  # captures the graph
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.step(gens)
+    torch.cuda.synchronize()
+    out["graph"] = {"sparks_per_s": sparks / (time.perf_counter() - t0)}
+    g.close()
+    for h in hs:
+        h.close()
+    hs = members()
+    for h in hs:
+        h.step(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(gens):
+        for h in hs:
+            h.step(1)
+    torch.cuda.synchronize()
+    out["streams"] = {"sparks_per_s": sparks / (time.perf_counter() - t0)}
+    for h in hs:
+        h.close()
+    hs = members()
+    for h in hs:
+        h.step(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for h in hs:
+        h.step(gens)
+        torch.cuda.synchronize()
+    out["one_at_a_time"] = {"sparks_per_s": sparks / (time.perf_counter() - t0)}
+    for h in hs:
+        h.close()
     return out
 
 

@@ -257,6 +257,28 @@ MGFWA_API double mgfwa_server_now(const mgfwa_server_t* s);
 /* Finish nothing further: destroy live handles and free everything. NULL-safe. */
 MGFWA_API void mgfwa_server_destroy(mgfwa_server_t* s);
 
+/* ------------------------------------------------------------------------
+ * Groups: many handles of any shapes (dimension, population, network,
+ * batch, precision) stepped together.  mgfwa_group_step() captures one
+ * generation of every member whose budget allows one as parallel branches
+ * of a single CUDA graph, then launches that graph once per generation; it
+ * is captured again only when a member's budget runs out.  Each member's
+ * results equal those of the same handle stepped alone (the generation
+ * number is read on the device).  Members must not refine (refine_every =
+ * 0), profile, or be inside a debug generation, and stay owned by the
+ * caller; a handle belongs to at most one group.  Work already enqueued on
+ * a member's stream runs before the group's generations, and later work on
+ * it after them.  Asynchronous.
+ * ------------------------------------------------------------------------ */
+typedef struct mgfwa_group mgfwa_group_t;
+
+MGFWA_API mgfwa_status mgfwa_group_create(mgfwa_t* const* handles, int32_t count, mgfwa_group_t** out);
+/* Up to n_generations generations of every member (each stops at its
+ * budget); EBUDGET if none could run one. */
+MGFWA_API mgfwa_status mgfwa_group_step(mgfwa_group_t* g, int32_t n_generations);
+/* The members stay valid (and usable alone again). NULL-safe. */
+MGFWA_API void mgfwa_group_destroy(mgfwa_group_t* g);
+
 #ifdef __cplusplus
 }
 #endif

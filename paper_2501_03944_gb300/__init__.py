@@ -38,7 +38,8 @@ EXPORTS = ("mgfwa_config_init", "mgfwa_create", "mgfwa_step", "mgfwa_run", "mgfw
            "mgfwa_debug_write", "mgfwa_debug_profile", "mgfwa_debug_kernel_times", "mgfwa_evaluate_fp32_noalloc",
            "mgfwa_debug_gradient",
            "mgfwa_footprint", "mgfwa_server_create", "mgfwa_server_submit", "mgfwa_server_tick", "mgfwa_server_poll",
-           "mgfwa_server_stats_get", "mgfwa_server_now", "mgfwa_server_destroy")
+           "mgfwa_server_stats_get", "mgfwa_server_now", "mgfwa_server_destroy", "mgfwa_group_create",
+           "mgfwa_group_step", "mgfwa_group_destroy")
 MGFWA_REQ_QUEUED, MGFWA_REQ_RUNNING, MGFWA_REQ_DONE, MGFWA_REQ_FAILED = range(4)
 N_KERNEL_GROUPS = 9
 KERNEL_GROUPS = ("explode", "fitness_explosion", "fitness_finish", "rank", "guide", "fitness_guiding", "select",
@@ -133,8 +134,13 @@ def load_library(path: Optional[str] = None):
     L.mgfwa_server_now.restype = ctypes.c_double
     L.mgfwa_server_destroy.argtypes = [vp]
     L.mgfwa_server_destroy.restype = None
+    L.mgfwa_group_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]
+    L.mgfwa_group_step.argtypes = [vp, i32]
+    L.mgfwa_group_destroy.argtypes = [vp]
+    L.mgfwa_group_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("mgfwa_destroy", "mgfwa_last_error", "mgfwa_server_now", "mgfwa_server_destroy"):
+        if name not in ("mgfwa_destroy", "mgfwa_last_error", "mgfwa_server_now", "mgfwa_server_destroy",
+                        "mgfwa_group_destroy"):
             getattr(L, name).restype = ctypes.c_int
     if path == LIB_PATH:
         _lib = L
@@ -446,6 +452,48 @@ class Server:
     def close(self):
         if getattr(self, "handle", None):
             load_library().mgfwa_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Group:
+    """Owner of an mgfwa_group_t over Mgfwa objects (see include/mgfwa.h, Groups); the members must outlive it."""
+
+    def __init__(self, members):
+        self.members = list(members)
+        arr = (ctypes.c_void_p * len(self.members))(*[m.handle for m in self.members])
+        h = ctypes.c_void_p()
+        _check(load_library().mgfwa_group_create(arr, len(self.members), ctypes.byref(h)))
+        self.handle = h.value
+
+    def step(self, n: int = 1) -> int:
+        st = load_library().mgfwa_group_step(self.handle, n)
+        if st not in (MGFWA_OK, MGFWA_EBUDGET):
+            _check(st)
+        return st
+
+    def run(self, max_generations: int = 1 << 30, chunk: int = 16) -> None:
+        """Step until no member's budget allows another generation."""
+        done = 0
+        while done < max_generations:
+            if self.step(min(chunk, max_generations - done)) == MGFWA_EBUDGET:
+                return
+            done += chunk
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().mgfwa_group_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):

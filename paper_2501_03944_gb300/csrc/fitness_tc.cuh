@@ -33,6 +33,9 @@ bool tc_supported(const int32_t* widths, int n_layers);
 mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const OpDesc& op, const float* sparks, int64_t ld,
                      int64_t max_rows);
 const char* tc_last_error();
+// Give the plan's kernel its shared-memory allowance now (not at its first
+// launch, which may be inside a stream capture).
+cudaError_t tc_prepare(const TcPlan& plan, const Mlp& mlp);
 void tc_release(TcPlan& plan);
 
 // Fitness of `count` sparks starting at spark row `first` of the planned

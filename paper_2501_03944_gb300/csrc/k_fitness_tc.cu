@@ -678,9 +678,9 @@ int n2_of(int C) { return C <= 16 ? 16 : 32; }
 int sparks_per_tile(int h1, int h2, int C) { return 256 / (h1 + h2 + n2_of(C)); }
 
 template <int H1, int H2, int NL, bool F8>
-cudaError_t launch_hn(const TcPlan& plan, const TcArgs& args, cudaStream_t s) {
+cudaError_t launch_hn(const TcPlan& plan, const TcArgs& args, cudaStream_t s, bool prepare_only) {
   cudaError_t e = ensure_smem_limit<k_fitness_tc<H1, H2, NL, F8>>(plan.smem_bytes);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || prepare_only) return e;
   const int tiles = args.m_tiles * args.n_tiles;
   const int grid = tiles < plan.num_sms ? tiles : plan.num_sms;
   k_fitness_tc<H1, H2, NL, F8><<<grid, kThreads, plan.smem_bytes, s>>>(plan.tmap_x, plan.tmap_w, plan.tmap_w2,
@@ -689,9 +689,33 @@ cudaError_t launch_hn(const TcPlan& plan, const TcArgs& args, cudaStream_t s) {
 }
 
 template <int H1, bool F8>
-cudaError_t launch_h1(const TcPlan& plan, const TcArgs& args, cudaStream_t s) {
-  if (args.C <= 16) return launch_hn<H1, 0, 16, F8>(plan, args, s);
-  return launch_hn<H1, 0, 32, F8>(plan, args, s);
+cudaError_t launch_h1(const TcPlan& plan, const TcArgs& args, cudaStream_t s, bool prep) {
+  if (args.C <= 16) return launch_hn<H1, 0, 16, F8>(plan, args, s, prep);
+  return launch_hn<H1, 0, 32, F8>(plan, args, s, prep);
+}
+
+// The kernel instance for the plan's network and precision: launched, or
+// (prep) only given its shared-memory allowance.
+cudaError_t dispatch(const TcPlan& plan, const Mlp& mlp, const TcArgs& a, cudaStream_t s, bool prep) {
+  const int h1 = mlp.widths[1];
+  if (mlp.n_layers == 3) {
+    // three layers: (128, 64) or (64, 32), at most 16 classes
+    const int h2 = mlp.widths[2];
+    if (h1 == 128 && h2 == 64)
+      return plan.f8 ? launch_hn<128, 64, 16, true>(plan, a, s, prep) : launch_hn<128, 64, 16, false>(plan, a, s, prep);
+    if (h1 == 64 && h2 == 32)
+      return plan.f8 ? launch_hn<64, 32, 16, true>(plan, a, s, prep) : launch_hn<64, 32, 16, false>(plan, a, s, prep);
+    return cudaErrorInvalidValue;
+  }
+  switch (h1 * 2 + (plan.f8 ? 1 : 0)) {
+    case 64: return launch_h1<32, false>(plan, a, s, prep);
+    case 128: return launch_h1<64, false>(plan, a, s, prep);
+    case 256: return launch_h1<128, false>(plan, a, s, prep);
+    case 65: return launch_h1<32, true>(plan, a, s, prep);
+    case 129: return launch_h1<64, true>(plan, a, s, prep);
+    case 257: return launch_h1<128, true>(plan, a, s, prep);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
@@ -805,7 +829,6 @@ void tc_release(TcPlan& plan) { plan.ready = false; }
 int launch_fitness_tc(const TcPlan& plan, const Mlp& mlp, int64_t first, const float* rows, int64_t ld,
                       int32_t count, float scale, float* partial, uint32_t* status, cudaStream_t s) {
   if (!plan.ready || count <= 0) return count <= 0 ? 0 : -1;
-  const int h1 = mlp.widths[1];
   TcArgs a;
   a.count = count;
   a.first_spark = (int32_t)first;
@@ -830,28 +853,14 @@ int launch_fitness_tc(const TcPlan& plan, const Mlp& mlp, int64_t first, const f
   a.y = mlp.y;
   a.partial = partial;
   a.status = status;
-  cudaError_t e;
-  if (l3) {
-    // three layers: (128, 64) or (64, 32), at most 16 classes
-    const int h2 = mlp.widths[2];
-    if (h1 == 128 && h2 == 64)
-      e = plan.f8 ? launch_hn<128, 64, 16, true>(plan, a, s) : launch_hn<128, 64, 16, false>(plan, a, s);
-    else if (h1 == 64 && h2 == 32)
-      e = plan.f8 ? launch_hn<64, 32, 16, true>(plan, a, s) : launch_hn<64, 32, 16, false>(plan, a, s);
-    else
-      return -1;
-    return e == cudaSuccess ? 1 : -1;
-  }
-  switch (h1 * 2 + (plan.f8 ? 1 : 0)) {
-    case 64: e = launch_h1<32, false>(plan, a, s); break;
-    case 128: e = launch_h1<64, false>(plan, a, s); break;
-    case 256: e = launch_h1<128, false>(plan, a, s); break;
-    case 65: e = launch_h1<32, true>(plan, a, s); break;
-    case 129: e = launch_h1<64, true>(plan, a, s); break;
-    case 257: e = launch_h1<128, true>(plan, a, s); break;
-    default: return -1;
-  }
-  return e == cudaSuccess ? 1 : -1;
+  return dispatch(plan, mlp, a, s, false) == cudaSuccess ? 1 : -1;
+}
+
+cudaError_t tc_prepare(const TcPlan& plan, const Mlp& mlp) {
+  if (!plan.ready) return cudaErrorInvalidValue;
+  TcArgs a = {};
+  a.C = mlp.widths[mlp.n_layers];
+  return dispatch(plan, mlp, a, nullptr, true);
 }
 
 }  // namespace mgfwa

@@ -112,7 +112,8 @@ __global__ void __launch_bounds__(kSelThreads) k_select(Problem p, const float* 
 // fireworks).
 __global__ void __launch_bounds__(kSelThreads) k_run_best(Problem p, int init, const float* __restrict__ fw_x,
                                                           const float* __restrict__ fw_f,
-                                                          float* __restrict__ best_x, float* __restrict__ best_f) {
+                                                          float* __restrict__ best_x, float* __restrict__ best_f,
+                                                          uint32_t* __restrict__ gens_done) {
   __shared__ int s_bi;
   const int b = blockIdx.x;
   const float* f = fw_f + (int64_t)b * p.mu;
@@ -127,6 +128,7 @@ __global__ void __launch_bounds__(kSelThreads) k_run_best(Problem p, int init, c
     }
     if (bi >= 0) best_f[b] = bf;
     s_bi = bi;
+    if (gens_done && b == 0) *gens_done += 1u;  // the generation is complete
   }
   __syncthreads();
   const int bi = s_bi;
@@ -189,16 +191,16 @@ int launch_rank(const Problem& p, const float* fit_e, int32_t* top, int32_t* bot
 
 int launch_select(const Problem& p, const float* fit_e, const float* fit_g, const float* sparks,
                   const float* guides, float* fw_x, float* fw_amp, float* fw_f, int32_t* winner, float* best_x,
-                  float* best_f, cudaStream_t s) {
+                  float* best_f, uint32_t* gens_done, cudaStream_t s) {
   k_select<<<p.B * p.mu, kSelThreads, 0, s>>>(p, fit_e, fit_g, sparks, guides, fw_x, fw_amp, fw_f, winner);
   if (cudaPeekAtLastError() != cudaSuccess) return -1;
-  k_run_best<<<p.B, kSelThreads, 0, s>>>(p, 0, fw_x, fw_f, best_x, best_f);
+  k_run_best<<<p.B, kSelThreads, 0, s>>>(p, 0, fw_x, fw_f, best_x, best_f, gens_done);
   return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;
 }
 
 int launch_run_best_init(const Problem& p, const float* fw_x, const float* fw_f, float* best_x, float* best_f,
                          cudaStream_t s) {
-  k_run_best<<<p.B, kSelThreads, 0, s>>>(p, 1, fw_x, fw_f, best_x, best_f);
+  k_run_best<<<p.B, kSelThreads, 0, s>>>(p, 1, fw_x, fw_f, best_x, best_f, nullptr);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

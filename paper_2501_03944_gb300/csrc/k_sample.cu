@@ -127,9 +127,11 @@ __device__ __forceinline__ void explode4(const Problem& p, uint32_t gen, uint32_
 // two, kThreads blocks apart, so a warp's stores stay contiguous.  Global
 // firework z = b * mu + i, spark row z * lam + j, Philox unit i * lam + j of
 // run b's stream.
-__global__ void __launch_bounds__(kThreads) k_explode(Problem p, uint32_t gen, const float* __restrict__ fw_x,
+__global__ void __launch_bounds__(kThreads) k_explode(Problem p, const uint32_t* __restrict__ gens_done,
+                                                      const float* __restrict__ fw_x,
                                                       const float* __restrict__ fw_amp,
                                                       float* __restrict__ sparks, const OpDesc op) {
+  const uint32_t gen = *gens_done + 1u;  // this generation (the counter is advanced by the selection)
   const uint32_t z = blockIdx.z;
   const uint32_t b = z / (uint32_t)p.mu, i = z - b * (uint32_t)p.mu;
   const uint32_t row = z * (uint32_t)p.lam + blockIdx.y;
@@ -154,12 +156,14 @@ __global__ void __launch_bounds__(kThreads) k_explode(Problem p, uint32_t gen, c
 // lists top (best first) and bottom (worst first);
 //   GV = (sum top rows - sum bottom rows) / k,  G = x + beta GV,
 // each sum in list order, then the random mapping with its own stream.
-__global__ void __launch_bounds__(kThreads) k_guide(Problem p, uint32_t gen, const float* __restrict__ fw_x,
+__global__ void __launch_bounds__(kThreads) k_guide(Problem p, const uint32_t* __restrict__ gens_done,
+                                                    const float* __restrict__ fw_x,
                                                     const float* __restrict__ fw_amp,
                                                     const float* __restrict__ sparks,
                                                     const int32_t* __restrict__ top,
                                                     const int32_t* __restrict__ bottom,
                                                     float* __restrict__ guides, const OpDesc op) {
+  const uint32_t gen = *gens_done + 1u;
   const int i = blockIdx.z;               // global firework z = b * mu + i_local
   const int gq = i * p.m + blockIdx.y;    // global guiding row z * m + q
   const int run = i / p.mu;
@@ -258,18 +262,18 @@ int launch_init(const Problem& p, float* fw_x, float* fw_amp, cudaStream_t s) {
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
-int launch_explode(const Problem& p, uint32_t gen, const float* fw_x, const float* fw_amp, float* sparks,
+int launch_explode(const Problem& p, const uint32_t* gens_done, const float* fw_x, const float* fw_amp, float* sparks,
                    const OpDesc& op, cudaStream_t s) {
   dim3 grid((unsigned)((p.Dp / 4 + 2 * kThreads - 1) / (2 * kThreads)), p.lam, p.B * p.mu);
-  k_explode<<<grid, kThreads, 0, s>>>(p, gen, fw_x, fw_amp, sparks, op);
+  k_explode<<<grid, kThreads, 0, s>>>(p, gens_done, fw_x, fw_amp, sparks, op);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
-int launch_guide(const Problem& p, uint32_t gen, const float* fw_x, const float* fw_amp, const float* sparks,
+int launch_guide(const Problem& p, const uint32_t* gens_done, const float* fw_x, const float* fw_amp, const float* sparks,
                  const int32_t* top, const int32_t* bottom, float* guides, const OpDesc& op_guides,
                  cudaStream_t s) {
   dim3 grid(blocks_for(p.Dp / 4), p.m, p.B * p.mu);
-  k_guide<<<grid, kThreads, 0, s>>>(p, gen, fw_x, fw_amp, sparks, top, bottom, guides, op_guides);
+  k_guide<<<grid, kThreads, 0, s>>>(p, gens_done, fw_x, fw_amp, sparks, top, bottom, guides, op_guides);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

@@ -61,6 +61,7 @@ struct mgfwa_handle {
   double* ce64 = nullptr;
   double* f64 = nullptr;
   uint32_t* status = nullptr;
+  uint32_t* gens_done = nullptr;  // device copy of the completed-generation count (Philox counter word)
   // hybrid refinement (refine_every > 0): one vector per run
   bool refine = false;
   GradPlan gp;
@@ -71,6 +72,8 @@ struct mgfwa_handle {
   int32_t* rflags = nullptr;  // [B] refinement decisions
   float* gscratch = nullptr;  // backpropagation scratch (GradPlan)
   cudaGraphExec_t refine_exec = nullptr;  // the refinement's kernels, captured once
+  bool capturing = false;                 // a group is capturing this handle's generation: no host counters
+  bool grouped = false;                   // member of a group
   int64_t refine_kernels = 0;             // kernels in that graph
   bool want_op = false; // tensor-core path: operand copies of X and of the first-layer weights
   int64_t P = 0;       // sparks per generation of one run
@@ -273,9 +276,9 @@ mgfwa_status run_phase(mgfwa_t* h, int32_t phase) {
   const int32_t prec = h->cfg.precision;
   switch (phase) {
     case MGFWA_PHASE_EXPLODE: {
-      h->gen += 1;
+      if (!h->capturing) h->gen += 1;
       Mark mk(h, G_EXPLODE);
-      MG_LAUNCH(h, launch_explode(p, (uint32_t)h->gen, h->fw_x, h->fw_amp, h->sparks, op_rows(h, 0), h->stream),
+      MG_LAUNCH(h, launch_explode(p, h->gens_done, h->fw_x, h->fw_amp, h->sparks, op_rows(h, 0), h->stream),
                 "explode");
       return MGFWA_OK;
     }
@@ -288,7 +291,7 @@ mgfwa_status run_phase(mgfwa_t* h, int32_t phase) {
     }
     case MGFWA_PHASE_GUIDE: {
       Mark mk(h, G_GUIDE);
-      MG_LAUNCH(h, launch_guide(p, (uint32_t)h->gen, h->fw_x, h->fw_amp, h->sparks, h->top, h->bottom,
+      MG_LAUNCH(h, launch_guide(p, h->gens_done, h->fw_x, h->fw_amp, h->sparks, h->top, h->bottom,
                                 h->sparks + n_e * p.Dp, op_rows(h, n_e), h->stream), "guide");
       return MGFWA_OK;
     }
@@ -308,8 +311,8 @@ mgfwa_status run_phase(mgfwa_t* h, int32_t phase) {
     case MGFWA_PHASE_SELECT: {
       Mark mk(h, G_SELECT);
       MG_LAUNCH(h, launch_select(p, h->fit, h->fit + n_e, h->sparks, h->sparks + n_e * p.Dp, h->fw_x, h->fw_amp,
-                                 h->fw_f, h->winner, h->best_x, h->best_f, h->stream), "select");
-      h->evals += h->P;
+                                 h->fw_f, h->winner, h->best_x, h->best_f, h->gens_done, h->stream), "select");
+      if (!h->capturing) h->evals += h->P;
       return MGFWA_OK;
     }
     case MGFWA_PHASE_REFINE: {
@@ -539,6 +542,7 @@ size_t carve_all(mgfwa_t* h, char* base) {
   h->ce64 = carve<double>(cur, N > 0 ? N : 1);
   h->f64 = carve<double>(cur, 1);
   h->status = carve<uint32_t>(cur, 1);
+  h->gens_done = carve<uint32_t>(cur, 1);
   if (h->refine) {
     h->rw = carve<float>(cur, (int64_t)p.B * p.Dp);
     h->rg = carve<float>(cur, (int64_t)p.B * p.Dp);
@@ -650,6 +654,7 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
       h->err = tc_last_error();
       return bail(st);
     }
+    if (tc_prepare(h->tc, h->mlp) != cudaSuccess) return bail(cuda_fail(h, "tensor-core kernel attributes"));
   }
   TRACE("create: batch copied");
   // Algorithm 1, init: mu fireworks uniform in the box, evaluated.
@@ -796,6 +801,185 @@ void mgfwa_destroy(mgfwa_t* h) {
 const char* mgfwa_last_error(const mgfwa_t* h) {
   if (!h) return g_create_error.c_str();
   return h->err.c_str();
+}
+
+// ---------------------------------------------------------------------------
+// Groups: many handles (any shapes) stepped together, one CUDA graph per step.
+
+}  // extern "C"
+
+struct mgfwa_group {
+  std::vector<mgfwa_t*> members;
+  cudaStream_t stream = nullptr;          // where the graph runs
+  std::vector<cudaStream_t> branch;       // capture branches, one per member
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr, done = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<int> live;                  // members captured in exec
+  std::vector<int64_t> kernels;           // kernels per generation of each member
+  std::string err;
+};
+
+namespace {
+
+void group_release(mgfwa_group* g) {
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  g->exec = nullptr;
+  for (cudaStream_t b : g->branch) if (b) cudaStreamDestroy(b);
+  for (cudaEvent_t e : g->join) if (e) cudaEventDestroy(e);
+  if (g->fork) cudaEventDestroy(g->fork);
+  if (g->done) cudaEventDestroy(g->done);
+  if (g->stream) cudaStreamDestroy(g->stream);
+  cudaGetLastError();
+}
+
+mgfwa_status group_fail(mgfwa_group* g, mgfwa_status st, const char* what) {
+  g->err = what;
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) g->err += std::string(": ") + cudaGetErrorString(e);
+  set_thread_error(g->err.c_str());
+  return st;
+}
+
+// Capture one generation of every live member as parallel branches of one
+// graph: fork from the group stream, each member's kernels on its branch
+// (the member's stream swapped for the branch while capturing), join.
+mgfwa_status group_capture(mgfwa_group* g, const std::vector<int>& live) {
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  g->exec = nullptr;
+  g->live.clear();
+  if (cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return group_fail(g, MGFWA_ECUDA, "group: begin capture");
+  mgfwa_status st = MGFWA_OK;
+  bool ok = cudaEventRecord(g->fork, g->stream) == cudaSuccess;
+  for (int i : live) {
+    if (!ok) break;
+    mgfwa_t* h = g->members[(size_t)i];
+    ok = cudaStreamWaitEvent(g->branch[(size_t)i], g->fork, 0) == cudaSuccess;
+    if (!ok) break;
+    cudaStream_t own = h->stream;
+    h->stream = g->branch[(size_t)i];
+    h->capturing = true;
+    const int64_t before = h->launches;
+    for (int32_t ph = MGFWA_PHASE_EXPLODE; ph <= MGFWA_PHASE_SELECT && st == MGFWA_OK; ++ph) st = run_phase(h, ph);
+    g->kernels[(size_t)i] = h->launches - before;
+    h->launches = before;
+    h->capturing = false;
+    h->stream = own;
+    if (st != MGFWA_OK) {
+      ok = false;
+      break;
+    }
+    ok = cudaEventRecord(g->join[(size_t)i], g->branch[(size_t)i]) == cudaSuccess &&
+         cudaStreamWaitEvent(g->stream, g->join[(size_t)i], 0) == cudaSuccess;
+  }
+  cudaGraph_t graph = nullptr;
+  const bool ended = cudaStreamEndCapture(g->stream, &graph) == cudaSuccess;
+  if (!ok || !ended || !graph || cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    g->exec = nullptr;
+    return st != MGFWA_OK ? st : group_fail(g, MGFWA_ECUDA, "group: capture of a generation");
+  }
+  cudaGraphDestroy(graph);
+  g->live = live;
+  return MGFWA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mgfwa_status mgfwa_group_create(mgfwa_t* const* handles, int32_t count, mgfwa_group_t** out) {
+  if (!out || !handles || count < 1) {
+    set_thread_error("group: need an output pointer and at least one handle");
+    return MGFWA_EINVAL;
+  }
+  *out = nullptr;
+  for (int32_t i = 0; i < count; ++i) {
+    mgfwa_t* h = handles[i];
+    if (!h || h->broken || h->grouped) {
+      set_thread_error("group: a handle is null, unusable or already in a group");
+      return MGFWA_EINVAL;
+    }
+    for (int32_t j = 0; j < i; ++j)
+      if (handles[j] == h) {
+        set_thread_error("group: a handle appears twice");
+        return MGFWA_EINVAL;
+      }
+    if (h->refine || h->profiling || h->next_phase != MGFWA_PHASE_EXPLODE || h->device != handles[0]->device) {
+      set_thread_error("group: members must not refine, profile or be inside a debug generation, one device");
+      return MGFWA_EINVAL;
+    }
+  }
+  mgfwa_group* g = new (std::nothrow) mgfwa_group();
+  if (!g) return MGFWA_ENOMEM;
+  g->members.assign(handles, handles + count);
+  g->branch.assign((size_t)count, nullptr);
+  g->join.assign((size_t)count, nullptr);
+  g->kernels.assign((size_t)count, 0);
+  bool ok = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming) == cudaSuccess;
+  for (int32_t i = 0; i < count && ok; ++i)
+    ok = cudaStreamCreateWithFlags(&g->branch[(size_t)i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&g->join[(size_t)i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    group_fail(g, MGFWA_ECUDA, "group: streams and events");
+    group_release(g);
+    delete g;
+    return MGFWA_ECUDA;
+  }
+  for (mgfwa_t* h : g->members) h->grouped = true;
+  *out = g;
+  return MGFWA_OK;
+}
+
+mgfwa_status mgfwa_group_step(mgfwa_group_t* g, int32_t n_generations) {
+  if (!g || n_generations < 0) return MGFWA_EINVAL;
+  const size_t M = g->members.size();
+  for (mgfwa_t* h : g->members) {
+    if (h->broken) return group_fail(g, MGFWA_ECUDA, "group: a member is unusable after a CUDA error");
+    if (h->next_phase != MGFWA_PHASE_EXPLODE) return group_fail(g, MGFWA_EINVAL, "group: a member is mid-generation");
+  }
+  // the group stream starts after everything already enqueued on the members' streams
+  for (mgfwa_t* h : g->members)
+    if (cudaEventRecord(g->done, h->stream) != cudaSuccess || cudaStreamWaitEvent(g->stream, g->done, 0) != cudaSuccess)
+      return group_fail(g, MGFWA_ECUDA, "group: order after the members' streams");
+  int32_t ran = 0;
+  std::vector<int> live;
+  for (int32_t it = 0; it < n_generations; ++it) {
+    live.clear();
+    for (size_t i = 0; i < M; ++i)
+      if (budget_allows(g->members[i])) live.push_back((int)i);
+    if (live.empty()) break;
+    if (!g->exec || live != g->live) {
+      mgfwa_status st = group_capture(g, live);
+      if (st != MGFWA_OK) return st;
+    }
+    if (cudaGraphLaunch(g->exec, g->stream) != cudaSuccess) return group_fail(g, MGFWA_ECUDA, "group: graph launch");
+    for (int i : live) {
+      mgfwa_t* h = g->members[(size_t)i];
+      h->gen += 1;
+      h->evals += h->P;
+      h->launches += g->kernels[(size_t)i];
+    }
+    ++ran;
+  }
+  // later work on a member's own stream runs after the group's
+  if (cudaEventRecord(g->done, g->stream) != cudaSuccess) return group_fail(g, MGFWA_ECUDA, "group: record");
+  for (mgfwa_t* h : g->members)
+    if (cudaStreamWaitEvent(h->stream, g->done, 0) != cudaSuccess)
+      return group_fail(g, MGFWA_ECUDA, "group: order before the members' streams");
+  if (n_generations > 0 && ran == 0) return group_fail(g, MGFWA_EBUDGET, "group: no member's budget allows a generation");
+  return MGFWA_OK;
+}
+
+void mgfwa_group_destroy(mgfwa_group_t* g) {
+  if (!g) return;
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  for (mgfwa_t* h : g->members) h->grouped = false;
+  group_release(g);
+  delete g;
 }
 
 // ---------------------------------------------------------------------------

@@ -133,14 +133,17 @@ int launch_init(const Problem& p, float* fw_x, float* fw_amp, cudaStream_t s);
 
 // Explosion sparks rows [0, mu*lam) of `sparks` (row stride Dp); if `op` is
 // non-null also the BF16 first-layer operand (w1_elems per spark row).
-int launch_explode(const Problem& p, uint32_t gen, const float* fw_x, const float* fw_amp,
+// The generation number is read on the device: gens_done[0] + 1, where
+// gens_done counts completed generations (launch_select advances it), so a
+// captured generation replays with the right Philox counters.
+int launch_explode(const Problem& p, const uint32_t* gens_done, const float* fw_x, const float* fw_amp,
                    float* sparks, const OpDesc& op, cudaStream_t s);
 
 int launch_rank(const Problem& p, const float* fit_e, int32_t* top, int32_t* bottom, cudaStream_t s);
 
 // Guiding sparks written to `guides` (mu*m rows of stride Dp) and, if non-
 // null, their operand rows `op_guides`.
-int launch_guide(const Problem& p, uint32_t gen, const float* fw_x, const float* fw_amp,
+int launch_guide(const Problem& p, const uint32_t* gens_done, const float* fw_x, const float* fw_amp,
                  const float* sparks, const int32_t* top, const int32_t* bottom, float* guides,
                  const OpDesc& op_guides, cudaStream_t s);
 
@@ -148,9 +151,10 @@ int launch_guide(const Problem& p, uint32_t gen, const float* fw_x, const float*
 int launch_run_best_init(const Problem& p, const float* fw_x, const float* fw_f, float* best_x, float* best_f,
                          cudaStream_t s);
 
+// ... and advances gens_done[0] by one (the generation is complete).
 int launch_select(const Problem& p, const float* fit_e, const float* fit_g, const float* sparks,
                   const float* guides, float* fw_x, float* fw_amp, float* fw_f, int32_t* winner,
-                  float* best_x, float* best_f, cudaStream_t s);
+                  float* best_x, float* best_f, uint32_t* gens_done, cudaStream_t s);
 
 // FP32 CUDA-core fitness of `count` rows (stride `ld` floats; row r is
 // rows[idx[r]] when idx is given): per-(m-tile, r) partial cross-entropy

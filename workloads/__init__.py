@@ -157,3 +157,31 @@ def random_vectors(n: int, dim: int, lo: float, hi: float, seed: int) -> np.ndar
     rng = np.random.default_rng(seed)
     return rng.uniform(lo, hi, size=(n, dim)).astype(np.float32)
 
+
+
+def mixed_batch(n: int, seed: int, generations: int = 10):
+    """n MLP workloads of different shapes for batching many runs at once:
+    D log-uniform in [195, 50,890] across the 8-16(tanh)-3 and d_in-64(ReLU)-10
+    families (d_in a multiple of 16, 16..784; below D = 1,226 the 8-16-3 net),
+    3..8 fireworks, 32..256 sparks per firework with 4 or 8 guiding sparks,
+    each with its own Gaussian-mixture batch of 512..2048 samples, and a
+    budget of `generations` generations."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        D = float(np.exp(rng.uniform(np.log(195.0), np.log(50890.0))))
+        if D < 1226:
+            widths, acts = (8, 16, 3), (ACT_TANH,)
+        else:
+            d_in = int(np.clip(round((D - 64 - 650) / 64 / 16) * 16, 16, 784))
+            widths, acts = (d_in, 64, 10), (ACT_RELU,)
+        m = int(rng.choice([4, 8]))
+        lam = int(rng.choice([32, 64, 128, 256]))
+        mu = int(rng.integers(3, 9))
+        N = int(rng.integers(4, 17)) * 128
+        w = Workload(name=f"mixed{k}", kind=KIND_MLP_CE, widths=widths, acts=acts, n_samples=N,
+                     dim=mlp_param_count(widths), lb=-1.0, ub=1.0, n_fireworks=mu, sparks_per_firework=lam,
+                     guiding_per_firework=m, sigma=0.2, eval_budget=budget_for_generations(mu, lam, m, generations),
+                     data_recipe="mixture", data_params=(2.0, 1.0), data_seed=1000 + k)
+        out.append(w)
+    return out
