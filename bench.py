@@ -431,25 +431,27 @@ def grouped_mixed(pkg, n: int = 64, gens: int = 5, seed: int = 3):
     return out
 
 
-def serving_trace(pkg, X, y, n_requests: int = 48, rate_hz: float = 400.0, max_live: int = 8, seed: int = 5):
-    """Continuous batching on one GPU: a Poisson stream of requests, two thirds
-    784-64-10 BF16 runs on the full batch (20 generations each) and one third
-    8-16-3 FP32 runs (40 generations), served with `max_live` slots.  Latency is
-    from each request's arrival to its result; throughput counts every spark."""
+def serving_trace(pkg, X, y, n_requests: int = 40, rate_hz: float = 200.0, max_live: int = 8, seed: int = 5):
+    """Continuous batching on one GPU: Poisson arrivals (mean rate_hz) of optimisation requests drawn
+    0.6 / 0.3 / 0.1 from the 8-16(tanh)-3 (FP32: its 16-unit layer is not a tensor-core shape),
+    784-64-10 (BF16, FP32 elite re-score) and 3072-128-64-10 (BF16, FP32 elite re-score) workloads, each
+    with a budget drawn uniformly in [10k, 100k] evaluations (whole generations).  Latency is from each
+    request's arrival to its result; throughput counts every spark."""
     rng = np.random.default_rng(seed)
     arrivals = np.cumsum(rng.exponential(1.0 / rate_hz, n_requests))
-    small = W.MLP_8_16_3
-    Xs, ys = W.make_data(small)
-    big = W.scaled(WORKLOAD, eval_budget=W.budget_for_generations(
-        WORKLOAD.n_fireworks, WORKLOAD.sparks_per_firework, WORKLOAD.guiding_per_firework, 20))
-    sm = W.scaled(small, eval_budget=W.budget_for_generations(
-        small.n_fireworks, small.sparks_per_firework, small.guiding_per_firework, 40))
-    reqs = []
+    fams = [(W.MLP_8_16_3, pkg.MGFWA_FP32), (WORKLOAD, pkg.MGFWA_BF16), (W.MLP_3072_128_64_10, pkg.MGFWA_BF16)]
+    data = [W.make_data(f[0]) for f in fams]
+    data[1] = (X, y)
+    reqs, kinds = [], []
     for k in range(n_requests):
-        if k % 3 == 2:
-            reqs.append(pkg.workload_request(sm, 7000 + k, pkg.MGFWA_FP32, X=Xs, y=ys))
-        else:
-            reqs.append(pkg.workload_request(big, 7000 + k, pkg.MGFWA_BF16, X=X, y=y))
+        j = int(rng.choice(3, p=[0.6, 0.3, 0.1]))
+        w0, prec = fams[j]
+        budget = int(rng.uniform(10_000, 100_000))
+        gens = max(1, (budget - w0.n_fireworks) // w0.sparks_per_generation)
+        w = W.scaled(w0, eval_budget=W.budget_for_generations(w0.n_fireworks, w0.sparks_per_firework,
+                                                              w0.guiding_per_firework, gens))
+        reqs.append(pkg.workload_request(w, 7000 + k, prec, X=data[j][0], y=data[j][1]))
+        kinds.append(j)
     with pkg.Server(max_live=max_live, device_bytes_limit=1 << 36) as s:
         ids, live_samples = [], []
         t0 = s.now()
@@ -469,14 +471,22 @@ def serving_trace(pkg, X, y, n_requests: int = 48, rate_hz: float = 400.0, max_l
                 time.sleep(max(0.0, min(1e-3, arrivals[nxt] - now)))
         wall = s.now() - t0
         st = s.stats()
-        lat = np.array([s.poll(r)[0].t_done - t0 - arrivals[i] for i, r in enumerate(ids)])
-        done = sum(s.poll(r)[0].state == pkg.MGFWA_REQ_DONE for r in ids)
-    return {"requests": n_requests, "completed": int(done), "arrival_rate_hz": rate_hz, "max_live": max_live,
-            "wall_s": round(wall, 4), "sparks_per_s": st.sparks_evaluated / wall,
+        infos = [s.poll(r)[0] for r in ids]
+    lat = np.array([i.t_done - t0 - arrivals[k] for k, i in enumerate(infos)])
+    by = {}
+    for j, name in enumerate(("mlp8-16-3", "mlp784-64-10", "mlp3072-128-64-10")):
+        sel = [k for k in range(n_requests) if kinds[k] == j]
+        if sel:
+            by[name] = {"requests": len(sel), "latency_ms_p50": round(float(np.percentile(lat[sel], 50)) * 1e3, 2),
+                        "latency_ms_p99": round(float(np.percentile(lat[sel], 99)) * 1e3, 2)}
+    return {"requests": n_requests, "completed": int(sum(i.state == pkg.MGFWA_REQ_DONE for i in infos)),
+            "arrival_rate_hz": rate_hz, "max_live": max_live, "wall_s": round(wall, 4),
+            "sparks_per_s": st.sparks_evaluated / wall,
             "latency_ms_p50": round(float(np.percentile(lat, 50)) * 1e3, 3),
             "latency_ms_p99": round(float(np.percentile(lat, 99)) * 1e3, 3),
-            "mean_live": round(float(np.mean(live_samples)), 2),
-            "mix": "2/3 784-64-10 bf16 x 20 generations, 1/3 8-16-3 fp32 x 40 generations; Poisson arrivals"}
+            "mean_live": round(float(np.mean(live_samples)), 2), "by_workload": by,
+            "mix": "0.6 mlp8-16-3 fp32 / 0.3 mlp784-64-10 bf16 / 0.1 mlp3072-128-64-10 bf16; budgets U(10k, 100k) "
+                   "evaluations; Poisson arrivals"}
 
 
 def main():
