@@ -166,6 +166,19 @@ typedef struct {
 
 MGFWA_API mgfwa_status mgfwa_get_info(const mgfwa_t* h, mgfwa_info* info);
 
+/* Checkpoint / resume.  A checkpoint (host memory, mgfwa_checkpoint_size
+ * bytes) holds what the rest of a run depends on: the fireworks, their
+ * amplitudes and fitness, each run's best-so-far, the evaluation and
+ * generation counts (the generation is a word of the Philox counter).  It
+ * loads only into a handle created with the same configuration (the budget
+ * may differ) and objective (a fingerprint of both is checked: EINVAL
+ * otherwise), between
+ * generations, and the run then continues exactly as the saved one would
+ * have.  Both calls synchronise. */
+MGFWA_API mgfwa_status mgfwa_checkpoint_size(const mgfwa_t* h, int64_t* bytes);
+MGFWA_API mgfwa_status mgfwa_checkpoint_save(mgfwa_t* h, void* host, int64_t bytes);
+MGFWA_API mgfwa_status mgfwa_checkpoint_load(mgfwa_t* h, const void* host, int64_t bytes);
+
 /* Release the handle's device memory and stream.  NULL-safe. */
 MGFWA_API void mgfwa_destroy(mgfwa_t* h);
 

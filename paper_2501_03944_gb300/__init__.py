@@ -39,7 +39,8 @@ EXPORTS = ("mgfwa_config_init", "mgfwa_create", "mgfwa_step", "mgfwa_run", "mgfw
            "mgfwa_debug_gradient",
            "mgfwa_footprint", "mgfwa_server_create", "mgfwa_server_submit", "mgfwa_server_tick", "mgfwa_server_poll",
            "mgfwa_server_stats_get", "mgfwa_server_now", "mgfwa_server_destroy", "mgfwa_group_create",
-           "mgfwa_group_step", "mgfwa_group_destroy")
+           "mgfwa_group_step", "mgfwa_group_destroy", "mgfwa_checkpoint_size", "mgfwa_checkpoint_save",
+           "mgfwa_checkpoint_load")
 MGFWA_REQ_QUEUED, MGFWA_REQ_RUNNING, MGFWA_REQ_DONE, MGFWA_REQ_FAILED = range(4)
 N_KERNEL_GROUPS = 9
 KERNEL_GROUPS = ("explode", "fitness_explosion", "fitness_finish", "rank", "guide", "fitness_guiding", "select",
@@ -137,6 +138,9 @@ def load_library(path: Optional[str] = None):
     L.mgfwa_group_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]
     L.mgfwa_group_step.argtypes = [vp, i32]
     L.mgfwa_group_destroy.argtypes = [vp]
+    L.mgfwa_checkpoint_size.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    L.mgfwa_checkpoint_save.argtypes = [vp, vp, i64]
+    L.mgfwa_checkpoint_load.argtypes = [vp, vp, i64]
     L.mgfwa_group_destroy.restype = None
     for name in EXPORTS:
         if name not in ("mgfwa_destroy", "mgfwa_last_error", "mgfwa_server_now", "mgfwa_server_destroy",
@@ -338,6 +342,19 @@ class Mgfwa:
 
     def write(self, buf: int, arr: np.ndarray) -> None:
         mgfwa_debug_write(self.handle, buf, arr)
+
+    def checkpoint(self) -> bytes:
+        """The run's state (see include/mgfwa.h, Checkpoint / resume)."""
+        L = load_library()
+        n = ctypes.c_int64()
+        _check(L.mgfwa_checkpoint_size(self.handle, ctypes.byref(n)), self.handle)
+        buf = ctypes.create_string_buffer(n.value)
+        _check(L.mgfwa_checkpoint_save(self.handle, buf, n.value), self.handle)
+        return buf.raw
+
+    def restore(self, data: bytes) -> None:
+        buf = ctypes.create_string_buffer(data, len(data))
+        _check(load_library().mgfwa_checkpoint_load(self.handle, buf, len(data)), self.handle)
 
     def gradient(self, xs):
         """(FP32 objective [count], FP32 gradient [count][D]) of host vectors, by the refinement's kernels."""

@@ -36,6 +36,7 @@ struct mgfwa_handle {
   bool own_stream = false;
   char* arena = nullptr;
   size_t arena_bytes = 0;
+  uint64_t fingerprint = 0;  // configuration + objective (checkpoints load only into the same problem)
   // device buffers (carved from the arena)
   float* X = nullptr;
   void* Xop = nullptr;          // [N][d_in] X as the tensor-core operand (BF16 or E4M3)
@@ -438,6 +439,48 @@ T* carve(char*& cur, size_t count) {
   return p;
 }
 
+// FNV-1a over the configuration (but its budget), the network shape and
+// (every 61st element of) the batch: a checkpoint is refused by a handle of
+// another problem.
+uint64_t problem_fingerprint(const mgfwa_config* cfg, const mgfwa_objective* obj) {
+  uint64_t f = 1469598103934665603ull;
+  auto mix = [&](const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) f = (f ^ b[i]) * 1099511628211ull;
+  };
+  // field by field (struct padding is not part of the problem); the budget is
+  // left out so that a resumed run may be given a larger one
+  mix(&cfg->dim, sizeof(cfg->dim));
+  mix(&cfg->lb, sizeof(cfg->lb));
+  mix(&cfg->ub, sizeof(cfg->ub));
+  mix(&cfg->n_fireworks, sizeof(cfg->n_fireworks));
+  mix(&cfg->sparks_per_firework, sizeof(cfg->sparks_per_firework));
+  mix(&cfg->guiding_per_firework, sizeof(cfg->guiding_per_firework));
+  mix(&cfg->sigma, sizeof(cfg->sigma));
+  mix(&cfg->boost, sizeof(cfg->boost));
+  mix(&cfg->amp_init, sizeof(cfg->amp_init));
+  mix(&cfg->c_amplify, sizeof(cfg->c_amplify));
+  mix(&cfg->c_reduce, sizeof(cfg->c_reduce));
+  mix(&cfg->seed, sizeof(cfg->seed));
+  mix(&cfg->precision, sizeof(cfg->precision));
+  mix(&cfg->elite_rescore, sizeof(cfg->elite_rescore));
+  mix(&cfg->n_runs, sizeof(cfg->n_runs));
+  mix(&cfg->refine_every, sizeof(cfg->refine_every));
+  mix(&cfg->refine_steps, sizeof(cfg->refine_steps));
+  mix(&cfg->refine_lr, sizeof(cfg->refine_lr));
+  mix(&obj->kind, sizeof(obj->kind));
+  mix(&obj->n_layers, sizeof(obj->n_layers));
+  if (obj->kind == MGFWA_OBJ_MLP_CE) {
+    mix(obj->widths, sizeof(int32_t) * (size_t)(obj->n_layers + 1));
+    mix(obj->acts, sizeof(int32_t) * (size_t)(obj->n_layers > 1 ? obj->n_layers - 1 : 0));
+    mix(&obj->n_samples, sizeof(obj->n_samples));
+    const int64_t nx = obj->n_samples * (int64_t)obj->widths[0];
+    for (int64_t e = 0; e < nx; e += 61) mix(obj->X + e, sizeof(float));
+    for (int64_t e = 0; e < obj->n_samples; e += 61) mix(obj->y + e, sizeof(int32_t));
+  }
+  return f;
+}
+
 // Fill the handle's problem description and sizes from a validated
 // configuration (no allocation).
 void plan_handle(mgfwa_t* h, const mgfwa_config* cfg, const mgfwa_objective* obj) {
@@ -485,6 +528,7 @@ void plan_handle(mgfwa_t* h, const mgfwa_config* cfg, const mgfwa_objective* obj
   } else {
     h->mtiles = 1;
   }
+  h->fingerprint = problem_fingerprint(cfg, obj);
   h->want_op = obj->kind == MGFWA_OBJ_MLP_CE && (cfg->precision == MGFWA_BF16 || cfg->precision == MGFWA_FP8);
   h->op_kind = !h->want_op ? kOpNone : (cfg->precision == MGFWA_FP8 ? kOpFp8 : kOpBf16);
   if (h->op_kind == kOpFp8) {
@@ -769,6 +813,93 @@ mgfwa_status mgfwa_evaluate(mgfwa_t* h, const float* xs, int64_t count, int32_t 
     return cuda_fail(h, "evaluate: read fitness");
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h, "evaluate synchronise");
   return check_status_word(h);
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoints: header, then fw_x [B*mu][D], fw_amp, fw_f [B*mu], best_x [B][D],
+// best_f [B] (FP32), packed.
+
+namespace {
+struct CkptHeader {
+  uint64_t magic;
+  uint64_t fingerprint;
+  int64_t evals;
+  int64_t launches;
+  int32_t gen;
+  uint32_t gens_done;
+  int64_t payload_bytes;
+};
+constexpr uint64_t kCkptMagic = 0x31544b43415746ull;  // "FWACKT1"
+
+int64_t ckpt_payload(const mgfwa_t* h) {
+  const int64_t F = (int64_t)h->p.B * h->p.mu, B = h->p.B, D = h->p.D;
+  return (int64_t)sizeof(float) * (F * D + 2 * F + B * D + B);
+}
+}  // namespace
+
+mgfwa_status mgfwa_checkpoint_size(const mgfwa_t* h, int64_t* bytes) {
+  if (!h || !bytes) return MGFWA_EINVAL;
+  *bytes = (int64_t)sizeof(CkptHeader) + ckpt_payload(h);
+  return MGFWA_OK;
+}
+
+mgfwa_status mgfwa_checkpoint_save(mgfwa_t* h, void* host, int64_t bytes) {
+  mgfwa_status st = check_usable(h);
+  if (st != MGFWA_OK) return st;
+  const int64_t need = (int64_t)sizeof(CkptHeader) + ckpt_payload(h);
+  if (!host || bytes != need) return fail(h, MGFWA_EINVAL, "checkpoint: buffer must hold %lld bytes", (long long)need);
+  if (h->next_phase != MGFWA_PHASE_EXPLODE) return fail(h, MGFWA_EINVAL, "a debug generation is in progress");
+  CkptHeader hd{kCkptMagic, h->fingerprint, h->evals, h->launches, h->gen, 0u, ckpt_payload(h)};
+  char* out = static_cast<char*>(host) + sizeof(CkptHeader);
+  const int64_t F = (int64_t)h->p.B * h->p.mu, B = h->p.B;
+  const size_t rb = sizeof(float) * h->p.D, pitch = sizeof(float) * h->p.Dp;
+  cudaError_t e = cudaMemcpyAsync(&hd.gens_done, h->gens_done, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpy2DAsync(out, rb, h->fw_x, pitch, rb, F, cudaMemcpyDeviceToHost, h->stream);
+  out += rb * F;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, h->fw_amp, sizeof(float) * F, cudaMemcpyDeviceToHost, h->stream);
+  out += sizeof(float) * F;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, h->fw_f, sizeof(float) * F, cudaMemcpyDeviceToHost, h->stream);
+  out += sizeof(float) * F;
+  if (e == cudaSuccess) e = cudaMemcpy2DAsync(out, rb, h->best_x, pitch, rb, B, cudaMemcpyDeviceToHost, h->stream);
+  out += rb * B;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, h->best_f, sizeof(float) * B, cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h, "checkpoint save");
+  std::memcpy(host, &hd, sizeof(hd));
+  return check_status_word(h);
+}
+
+mgfwa_status mgfwa_checkpoint_load(mgfwa_t* h, const void* host, int64_t bytes) {
+  mgfwa_status st = check_usable(h);
+  if (st != MGFWA_OK) return st;
+  const int64_t need = (int64_t)sizeof(CkptHeader) + ckpt_payload(h);
+  if (!host || bytes != need) return fail(h, MGFWA_EINVAL, "checkpoint: buffer must hold %lld bytes", (long long)need);
+  if (h->next_phase != MGFWA_PHASE_EXPLODE || h->grouped)
+    return fail(h, MGFWA_EINVAL, "checkpoint: not between generations, or the handle is in a group");
+  CkptHeader hd;
+  std::memcpy(&hd, host, sizeof(hd));
+  if (hd.magic != kCkptMagic || hd.payload_bytes != ckpt_payload(h))
+    return fail(h, MGFWA_EINVAL, "checkpoint: not a checkpoint of this layout");
+  if (hd.fingerprint != h->fingerprint)
+    return fail(h, MGFWA_EINVAL, "checkpoint: made for another configuration or objective");
+  const char* in = static_cast<const char*>(host) + sizeof(CkptHeader);
+  const int64_t F = (int64_t)h->p.B * h->p.mu, B = h->p.B;
+  const size_t rb = sizeof(float) * h->p.D, pitch = sizeof(float) * h->p.Dp;
+  // the staged host copy must outlive the asynchronous copies: synchronise below
+  cudaError_t e = cudaMemcpyAsync(h->gens_done, &hd.gens_done, sizeof(uint32_t), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpy2DAsync(h->fw_x, pitch, in, rb, rb, F, cudaMemcpyHostToDevice, h->stream);
+  in += rb * F;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->fw_amp, in, sizeof(float) * F, cudaMemcpyHostToDevice, h->stream);
+  in += sizeof(float) * F;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->fw_f, in, sizeof(float) * F, cudaMemcpyHostToDevice, h->stream);
+  in += sizeof(float) * F;
+  if (e == cudaSuccess) e = cudaMemcpy2DAsync(h->best_x, pitch, in, rb, rb, B, cudaMemcpyHostToDevice, h->stream);
+  in += rb * B;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->best_f, in, sizeof(float) * B, cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h, "checkpoint load");
+  h->evals = hd.evals;
+  h->gen = hd.gen;
+  h->launches = hd.launches;
+  return MGFWA_OK;
 }
 
 mgfwa_status mgfwa_get_info(const mgfwa_t* h, mgfwa_info* info) {
