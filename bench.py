@@ -261,6 +261,7 @@ def gpu_arm(args):
     if not args.no_extras and world == 1:
         extra["serving"] = serving_trace(pkg, X, y)
         extra["grouped_64_mixed"] = grouped_mixed(pkg)
+        extra["fitness_rel_err_vs_fp32"] = fitness_error_vs_fp32(pkg, X, y, stream)
     if not args.no_extras:
         # the plain FP32 one-run path the low-precision path is compared with
         extra["fp32_one_run"] = dict(timed_generations({"precision": pkg.MGFWA_FP32}, 5), precision="fp32")
@@ -374,6 +375,27 @@ def precision_sweep_3072(pkg, stream, gens: int = 3):
         h.close()
         out[name] = {"sparks_per_s": h.sparks_per_gen * g / (t / 1e3), "ms_per_generation": t / g,
                      "best_f_fp64": best_f}
+    return out
+
+
+def fitness_error_vs_fp32(pkg, X, y, stream, n_sparks: int = 128):
+    """Relative error of the BF16 and FP8 fitness against the FP32 path on the bench workload's own
+    explosion sparks (generation 4 of a run), the qualifier of the throughput metric (<= 1e-2)."""
+    out = {}
+    w = W.scaled(WORKLOAD, eval_budget=10 ** 9)
+    for name, prec in (("bf16", pkg.MGFWA_BF16), ("fp8", pkg.MGFWA_FP8)):
+        h = pkg.Mgfwa.for_workload(w, 4242, precision=prec, X=X, y=y, stream=stream.cuda_stream)
+        h.step(3)
+        h.phase(pkg.MGFWA_PHASE_EXPLODE)
+        sparks = h.read(pkg.MGFWA_BUF_SPARKS)[:n_sparks]
+        for ph in range(pkg.MGFWA_PHASE_EVAL_E, pkg.MGFWA_PHASE_SELECT + 1):
+            h.phase(ph)
+        low = h.evaluate(sparks, prec).astype(np.float64)
+        f32 = h.evaluate(sparks, pkg.MGFWA_FP32).astype(np.float64)
+        h.close()
+        rel = np.abs(low - f32) / np.abs(f32)
+        out[name] = {"max": float(rel.max()), "median": float(np.median(rel)), "sparks": int(n_sparks),
+                     "within_1e-2": bool(rel.max() <= 1e-2)}
     return out
 
 

@@ -171,16 +171,23 @@ __global__ void __launch_bounds__(256) k_sphere(const float* __restrict__ rows, 
   }
 }
 
-// FP64 forward of one sample per block; one warp per output unit, lanes
-// striding over the inputs, then a fixed xor tree.
+// FP64 forward of kF64Samples samples per block (so that every weight read
+// feeds that many FMAs); one warp per output unit, lanes striding over the
+// inputs in index order, then a fixed xor tree per sample.
+constexpr int kF64Samples = 4;
+
 __global__ void __launch_bounds__(256) k_fitness_f64(Mlp mlp, const float* __restrict__ x, int wmax,
                                                      double* __restrict__ ce64) {
   extern __shared__ double sd[];
-  double* a = sd;
-  double* b = sd + wmax;
-  const int64_t n = blockIdx.x;
+  double* a = sd;                          // [kF64Samples][wmax]
+  double* b = sd + (size_t)kF64Samples * wmax;
+  const int64_t n0 = (int64_t)blockIdx.x * kF64Samples;
+  const int ns = (int)(mlp.N - n0 < kF64Samples ? mlp.N - n0 : kF64Samples);
   const int d_in = mlp.widths[0];
-  for (int i = threadIdx.x; i < d_in; i += blockDim.x) a[i] = (double)mlp.X[n * d_in + i];
+  for (int e = threadIdx.x; e < kF64Samples * d_in; e += blockDim.x) {
+    const int q = e / d_in, i = e - q * d_in;
+    a[q * wmax + i] = q < ns ? (double)mlp.X[(n0 + q) * d_in + i] : 0.0;
+  }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   const int L = mlp.n_layers;
@@ -189,26 +196,40 @@ __global__ void __launch_bounds__(256) k_fitness_f64(Mlp mlp, const float* __res
     const float* W = x + mlp.w_off[l];
     const float* bias = x + mlp.b_off[l];
     for (int j = warp; j < fo; j += nwarps) {
-      double s = 0.0;
-      for (int i = lane; i < fi; i += 32) s += (double)W[(int64_t)j * fi + i] * a[i];
+      double s[kF64Samples];
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-      if (lane == 0) {
-        s += (double)bias[j];
-        if (l + 1 < L) s = mlp.acts[l] == kActTanh ? tanh(s) : (s > 0.0 ? s : 0.0);
-        b[j] = s;
+      for (int q = 0; q < kF64Samples; ++q) s[q] = 0.0;
+      for (int i = lane; i < fi; i += 32) {
+        const double wv = (double)W[(int64_t)j * fi + i];
+#pragma unroll
+        for (int q = 0; q < kF64Samples; ++q) s[q] += wv * a[q * wmax + i];
+      }
+#pragma unroll
+      for (int q = 0; q < kF64Samples; ++q) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
+      }
+      if (lane < kF64Samples) {
+        double v = s[0];
+#pragma unroll
+        for (int q = 1; q < kF64Samples; ++q) v = lane == q ? s[q] : v;
+        v += (double)bias[j];
+        if (l + 1 < L) v = mlp.acts[l] == kActTanh ? tanh(v) : (v > 0.0 ? v : 0.0);
+        b[lane * wmax + j] = v;
       }
     }
     __syncthreads();
     double* t = a; a = b; b = t;
   }
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < ns) {
+    const int q = threadIdx.x;
+    const double* z = a + q * wmax;
     const int C = mlp.widths[L];
-    double zmax = a[0];
-    for (int c = 1; c < C; ++c) zmax = a[c] > zmax ? a[c] : zmax;
+    double zmax = z[0];
+    for (int c = 1; c < C; ++c) zmax = z[c] > zmax ? z[c] : zmax;
     double se = 0.0;
-    for (int c = 0; c < C; ++c) se += exp(a[c] - zmax);
-    ce64[n] = (zmax + log(se)) - a[mlp.y[n]];
+    for (int c = 0; c < C; ++c) se += exp(z[c] - zmax);
+    ce64[n0 + q] = (zmax + log(se)) - z[mlp.y[n0 + q]];
   }
 }
 
@@ -271,9 +292,9 @@ int launch_fitness_sphere(const float* rows, int64_t ld, int64_t D, int32_t coun
 int launch_fitness_f64(const Mlp& mlp, const float* x, double* ce64, double* out, cudaStream_t s) {
   int wmax = 0;
   for (int l = 0; l <= mlp.n_layers; ++l) wmax = wmax > mlp.widths[l] ? wmax : mlp.widths[l];
-  const size_t smem = 2 * sizeof(double) * (size_t)wmax;
+  const size_t smem = 2 * sizeof(double) * (size_t)kF64Samples * wmax;
   if (smem > 48 * 1024 && ensure_smem_limit<k_fitness_f64>(smem) != cudaSuccess) return -1;
-  k_fitness_f64<<<(unsigned)mlp.N, 256, smem, s>>>(mlp, x, wmax, ce64);
+  k_fitness_f64<<<(unsigned)((mlp.N + kF64Samples - 1) / kF64Samples), 256, smem, s>>>(mlp, x, wmax, ce64);
   if (cudaPeekAtLastError() != cudaSuccess) return -1;
   k_reduce_f64<<<1, 256, 0, s>>>(ce64, nullptr, mlp.N, 1.0 / (double)mlp.N, out);
   return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;
