@@ -100,7 +100,7 @@ typedef struct {
   int32_t kind;          /* MGFWA_OBJ_MLP_CE or MGFWA_OBJ_SPHERE */
   int32_t n_layers;      /* linear layers, 2 or 3 (MLP) */
   const int32_t* widths; /* n_layers + 1 widths d_in, h1, [h2,] C: d_in % 8 == 0, hidden widths <= 192,
-                            C in [2, 32]; the BF16 path needs 2 layers and h1 in {32, 64, 128} */
+                            C in [2, 32]; the tensor-core shapes are listed at mgfwa_precision */
   const int32_t* acts;   /* n_layers - 1 hidden activations (MGFWA_ACT_*) */
   int64_t n_samples;     /* N >= 1 */
   const float* X;        /* [N][d_in] row-major FP32 */
@@ -117,9 +117,11 @@ MGFWA_API mgfwa_status mgfwa_config_init(mgfwa_config* cfg);
 
 /* Validate, allocate device state, copy the objective's batch, initialise
  * the mu fireworks (Algorithm 1, init) and evaluate them.  `cuda_stream`
- * is a cudaStream_t or NULL (the handle then creates its own).  On success
- * *out is a new handle; on failure *out is NULL and nothing is leaked.
- * Errors: EINVAL (configuration), ENOMEM, ECUDA. */
+ * is a cudaStream_t or NULL (the handle then creates its own).  The device
+ * state is one allocation from the library's stream-ordered pool (one per
+ * device); memory freed by mgfwa_destroy stays in that pool for later
+ * handles.  On success *out is a new handle; on failure *out is NULL and
+ * nothing is leaked.  Errors: EINVAL (configuration), ENOMEM, ECUDA. */
 MGFWA_API mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, void* cuda_stream,
                           mgfwa_t** out);
 

@@ -36,6 +36,7 @@ struct mgfwa_handle {
   bool own_stream = false;
   char* arena = nullptr;
   size_t arena_bytes = 0;
+  bool pooled = false;       // the arena came from the library's stream-ordered pool
   uint64_t fingerprint = 0;  // configuration + objective (checkpoints load only into the same problem)
   // device buffers (carved from the arena)
   float* X = nullptr;
@@ -439,6 +440,41 @@ T* carve(char*& cur, size_t count) {
   return p;
 }
 
+// The library's device memory pool (one per device, created on first use):
+// arenas are allocated and freed in stream order from it, and freed memory
+// stays in the pool for the next handle instead of returning to the driver,
+// so creating a handle of a size seen before costs no driver allocation.
+cudaMemPool_t arena_pool(int device) {
+  constexpr int kMaxDevices = 64;
+  static cudaMemPool_t pools[kMaxDevices] = {};
+  static bool tried[kMaxDevices] = {};
+  if (device < 0 || device >= kMaxDevices) return nullptr;
+  if (!tried[device]) {
+    tried[device] = true;
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      pools[device] = pool;
+    }
+    cudaGetLastError();
+  }
+  return pools[device];
+}
+
+void arena_free(mgfwa_t* h) {
+  if (!h->arena) return;
+  if (h->pooled)
+    cudaFreeAsync(h->arena, h->stream);
+  else
+    cudaFree(h->arena);
+  h->arena = nullptr;
+}
+
 // FNV-1a over the configuration (but its budget), the network shape and
 // (every 61st element of) the batch: a checkpoint is refused by a handle of
 // another problem.
@@ -659,15 +695,27 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
     }
     h->own_stream = true;
   }
-  if (cudaMalloc(&h->arena, bytes) != cudaSuccess) {
+  {
+    void* mem = nullptr;
+    cudaMemPool_t pool = arena_pool(h->device);
+    if (pool && cudaMallocFromPoolAsync(&mem, bytes, pool, h->stream) == cudaSuccess) {
+      h->pooled = true;
+    } else {
+      cudaGetLastError();
+      mem = nullptr;
+      if (cudaMalloc(&mem, bytes) != cudaSuccess) mem = nullptr;
+    }
+    h->arena = static_cast<char*>(mem);
+  }
+  if (!h->arena) {
     cudaGetLastError();
-    h->arena = nullptr;
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
-    return fail(nullptr, MGFWA_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
+    return fail(nullptr, MGFWA_ENOMEM, "device allocation of %zu bytes failed", bytes);
   }
   if (carve_all(h, h->arena) != bytes) {
-    cudaFree(h->arena);
+    arena_free(h);
+    cudaStreamSynchronize(h->stream);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
     return fail(nullptr, MGFWA_EINVAL, "internal: arena layout mismatch");
@@ -923,7 +971,8 @@ void mgfwa_destroy(mgfwa_t* h) {
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   tc_release(h->tc);
   if (h->refine_exec) cudaGraphExecDestroy(h->refine_exec);
-  if (h->arena) cudaFree(h->arena);
+  arena_free(h);
+  if (h->stream) cudaStreamSynchronize(h->stream);  // the pool's free completes in stream order
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   cudaGetLastError();
   delete h;
