@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "fp32x3.cuh"
 #include "mgfwa_internal.cuh"
 
 namespace mgfwa {
@@ -31,8 +32,11 @@ GradPlan grad_plan(const Mlp& mlp, int32_t R, int32_t num_sms, bool forward_only
 // non-null the FP32 objective of each row.  With idx, row r is W[idx[r]]
 // and its objective goes to f_out[idx[r]] (objective only).  Returns
 // kernels enqueued or -1.
+// With l1 (a ready plan over the same rows W, stride ld), the first layer
+// runs on the tensor cores at FP32 accuracy (status: its wait-timeout word).
 int launch_grad(const GradPlan& gp, const Mlp& mlp, const float* W, int64_t ld, float* scratch, float* G,
-                float* f_out, cudaStream_t s, const int32_t* idx = nullptr);
+                float* f_out, cudaStream_t s, const int32_t* idx = nullptr, const L1Plan* l1 = nullptr,
+                uint32_t* status = nullptr);
 
 // w <- min(max(fma(-lr, g, w), lb), ub) on the first D coordinates of R rows.
 int launch_sgd(float* w, const float* g, int32_t R, int64_t D, int64_t Dp, float lr, float lb, float ub,

@@ -684,7 +684,7 @@ GemmArgs make_gemm(const Gemm& sh, int R, float* P) {
 }  // namespace
 
 int launch_grad(const GradPlan& gp, const Mlp& mlp, const float* W, int64_t ld, float* scratch, float* G,
-                float* f_out, cudaStream_t s, const int32_t* idx) {
+                float* f_out, cudaStream_t s, const int32_t* idx, const L1Plan* l1, uint32_t* status) {
   const int L = mlp.n_layers;
   const int R = gp.R;
   const int64_t N = mlp.N;
@@ -701,6 +701,16 @@ int launch_grad(const GradPlan& gp, const Mlp& mlp, const float* W, int64_t ld, 
   // hidden layers: Z_l = A_{l-1} W_l^T, then bias and activation
   for (int l = 1; l < L; ++l) {
     const int64_t fi = mlp.widths[l - 1];
+    const int64_t l1_ctas = (int64_t)R * ((N + 127) / 128);  // one CTA per (128-sample tile, vector)
+    if (l == 1 && l1 && l1->ready && status && 2 * l1_ctas >= gp.num_sms) {
+      // the first layer on the tensor cores at FP32 accuracy, when its CTAs fill at least half the SMs
+      // (fewer vectors keep the CUDA-core products, whose split-K gives every SM work)
+      ++gi;
+      const int k = launch_l1_fp32x3(*l1, mlp, idx, R, act(1), status, s);
+      if (k < 0) return -1;
+      q.n += k;
+      continue;
+    }
     GemmArgs g = make_gemm(gl[gi++], R, P);
     if (l == 1) {
       g.A = mlp.X, g.sam = fi, g.sak = 1, g.sar = 0;

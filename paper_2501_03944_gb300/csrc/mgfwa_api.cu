@@ -58,6 +58,8 @@ struct mgfwa_handle {
   int32_t* elite = nullptr;     // [B*mu*E] spark rows picked for the FP32 re-score
   GradPlan rescore_plan;        // FP32 forward of the B*mu*E re-scored rows
   float* rescore_scratch = nullptr;
+  L1Plan rescore_l1;            // their first layer on the tensor cores (over the spark rows)
+  L1Plan refine_l1;             // the refinement's first layer on the tensor cores (over its rows)
   float* best_x = nullptr;
   float* best_f = nullptr;
   double* ce64 = nullptr;
@@ -236,12 +238,16 @@ int enqueue_refine(mgfwa_t* h, cudaStream_t s) {
   if ((k = launch_refine_pick(h->fw_x, h->fw_f, p.B, p.mu, p.Dp, h->rw, h->relite, s)) < 0) return -1;
   n += k;
   for (int32_t i = 0; i < c.refine_steps; ++i) {
-    if ((k = launch_grad(h->gp, h->mlp, h->rw, p.Dp, h->gscratch, h->rg, nullptr, s)) < 0) return -1;
+    if ((k = launch_grad(h->gp, h->mlp, h->rw, p.Dp, h->gscratch, h->rg, nullptr, s, nullptr, &h->refine_l1,
+                         h->status)) < 0)
+      return -1;
     n += k;
     if ((k = launch_sgd(h->rw, h->rg, p.B, p.D, p.Dp, c.refine_lr, p.lb, p.ub, s)) < 0) return -1;
     n += k;
   }
-  if ((k = launch_grad(h->gp, h->mlp, h->rw, p.Dp, h->gscratch, nullptr, h->rf, s)) < 0) return -1;
+  if ((k = launch_grad(h->gp, h->mlp, h->rw, p.Dp, h->gscratch, nullptr, h->rf, s, nullptr, &h->refine_l1,
+                       h->status)) < 0)
+    return -1;
   n += k;
   if ((k = launch_refine_accept(h->rw, h->rf, h->relite, h->rflags, h->fw_x, h->fw_f, h->best_x, h->best_f, p.B,
                                 p.mu, p.Dp, s)) < 0)
@@ -306,7 +312,7 @@ mgfwa_status run_phase(mgfwa_t* h, int32_t phase) {
       Mark mk(h, G_RESCORE);
       MG_LAUNCH(h, launch_elite_pick(p, h->fit, h->fit + n_e, E, h->elite, h->stream), "elite pick");
       MG_LAUNCH(h, launch_grad(h->rescore_plan, h->mlp, h->sparks, p.Dp, h->rescore_scratch, nullptr, h->fit,
-                               h->stream, h->elite),
+                               h->stream, h->elite, &h->rescore_l1, h->status),
                 "elite FP32 fitness");
       return MGFWA_OK;
     }
@@ -748,6 +754,10 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
     }
     if (tc_prepare(h->tc, h->mlp) != cudaSuccess) return bail(cuda_fail(h, "tensor-core kernel attributes"));
   }
+  // the FP32-accurate first layer of the elite re-score and of the refinement on the tensor cores
+  // (where the shape allows; otherwise they keep the CUDA-core products)
+  if (h->rescore_scratch) l1_fp32x3_plan(h->rescore_l1, h->mlp, h->sparks, p.Dp, h->PA);
+  if (h->refine) l1_fp32x3_plan(h->refine_l1, h->mlp, h->rw, p.Dp, p.B);
   TRACE("create: batch copied");
   // Algorithm 1, init: mu fireworks uniform in the box, evaluated.
   CREATE_LAUNCH(launch_init(p, h->fw_x, h->fw_amp, h->stream), "init");
@@ -1266,7 +1276,9 @@ mgfwa_status mgfwa_debug_gradient(mgfwa_t* h, const float* xs, int32_t count, fl
   const size_t rb = sizeof(float) * p.D, pitch = sizeof(float) * p.Dp;
   if (cudaMemcpy2DAsync(h->rw, pitch, xs, rb, rb, count, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
     return cuda_fail(h, "debug_gradient: copy rows");
-  MG_LAUNCH(h, launch_grad(h->gp, h->mlp, h->rw, p.Dp, h->gscratch, h->rg, h->rf, h->stream), "debug gradient");
+  MG_LAUNCH(h, launch_grad(h->gp, h->mlp, h->rw, p.Dp, h->gscratch, h->rg, h->rf, h->stream, nullptr,
+                           &h->refine_l1, h->status),
+            "debug gradient");
   if (cudaMemcpy2DAsync(g_out, rb, h->rg, pitch, rb, count, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
       cudaMemcpyAsync(f_out, h->rf, sizeof(float) * count, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
     return cuda_fail(h, "debug_gradient: read");
