@@ -23,7 +23,6 @@ namespace mgfwa {
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kGuideUnroll = 8;
 
 // Reading of the population-based random mapping: a coordinate outside
 // [lb, ub] is redrawn uniformly in the firework's amplitude box clipped to
@@ -156,6 +155,9 @@ __global__ void __launch_bounds__(kThreads) k_explode(Problem p, const uint32_t*
 // lists top (best first) and bottom (worst first);
 //   GV = (sum top rows - sum bottom rows) / k,  G = x + beta GV,
 // each sum in list order, then the random mapping with its own stream.
+// KU > 0: k == KU, all 2k row loads in flight before the ordered sums, with
+// registers for exactly those rows; KU == 0: any k, two rows at a time.
+template <int KU>
 __global__ void __launch_bounds__(kThreads) k_guide(Problem p, const uint32_t* __restrict__ gens_done,
                                                     const float* __restrict__ fw_x,
                                                     const float* __restrict__ fw_amp,
@@ -178,26 +180,22 @@ __global__ void __launch_bounds__(kThreads) k_guide(Problem p, const uint32_t* _
   const int32_t* b = bottom + (int64_t)gq * k;
   const float* fs = sparks + (int64_t)i * p.lam * p.Dp + d0;
   float4 st, sb;
-  if (k <= kGuideUnroll) {
+  if (KU > 0) {
     // all 2k loads in flight before the ordered sums
-    float4 a[kGuideUnroll], c[kGuideUnroll];
+    float4 a[KU > 0 ? KU : 1], c[KU > 0 ? KU : 1];
 #pragma unroll
-    for (int r = 0; r < kGuideUnroll; ++r) {
-      if (r < k) {
-        a[r] = *reinterpret_cast<const float4*>(fs + (int64_t)t[r] * p.Dp);
-        c[r] = *reinterpret_cast<const float4*>(fs + (int64_t)b[r] * p.Dp);
-      }
+    for (int r = 0; r < KU; ++r) {
+      a[r] = *reinterpret_cast<const float4*>(fs + (int64_t)t[r] * p.Dp);
+      c[r] = *reinterpret_cast<const float4*>(fs + (int64_t)b[r] * p.Dp);
     }
     st = a[0];
     sb = c[0];
 #pragma unroll
-    for (int r = 1; r < kGuideUnroll; ++r) {
-      if (r < k) {
-        st.x = __fadd_rn(st.x, a[r].x); st.y = __fadd_rn(st.y, a[r].y);
-        st.z = __fadd_rn(st.z, a[r].z); st.w = __fadd_rn(st.w, a[r].w);
-        sb.x = __fadd_rn(sb.x, c[r].x); sb.y = __fadd_rn(sb.y, c[r].y);
-        sb.z = __fadd_rn(sb.z, c[r].z); sb.w = __fadd_rn(sb.w, c[r].w);
-      }
+    for (int r = 1; r < KU; ++r) {
+      st.x = __fadd_rn(st.x, a[r].x); st.y = __fadd_rn(st.y, a[r].y);
+      st.z = __fadd_rn(st.z, a[r].z); st.w = __fadd_rn(st.w, a[r].w);
+      sb.x = __fadd_rn(sb.x, c[r].x); sb.y = __fadd_rn(sb.y, c[r].y);
+      sb.z = __fadd_rn(sb.z, c[r].z); sb.w = __fadd_rn(sb.w, c[r].w);
     }
   } else {
     st = *reinterpret_cast<const float4*>(fs + (int64_t)t[0] * p.Dp);
@@ -273,7 +271,13 @@ int launch_guide(const Problem& p, const uint32_t* gens_done, const float* fw_x,
                  const int32_t* top, const int32_t* bottom, float* guides, const OpDesc& op_guides,
                  cudaStream_t s) {
   dim3 grid(blocks_for(p.Dp / 4), p.m, p.B * p.mu);
-  k_guide<<<grid, kThreads, 0, s>>>(p, gens_done, fw_x, fw_amp, sparks, top, bottom, guides, op_guides);
+  switch (p.k) {
+#define MG_GUIDE_K(K) \
+  case K: k_guide<K><<<grid, kThreads, 0, s>>>(p, gens_done, fw_x, fw_amp, sparks, top, bottom, guides, op_guides); break;
+    MG_GUIDE_K(1) MG_GUIDE_K(2) MG_GUIDE_K(3) MG_GUIDE_K(4) MG_GUIDE_K(5) MG_GUIDE_K(6) MG_GUIDE_K(7) MG_GUIDE_K(8)
+#undef MG_GUIDE_K
+    default: k_guide<0><<<grid, kThreads, 0, s>>>(p, gens_done, fw_x, fw_amp, sparks, top, bottom, guides, op_guides);
+  }
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
