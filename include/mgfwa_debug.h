@@ -74,6 +74,14 @@ MGFWA_API mgfwa_status mgfwa_debug_write(mgfwa_t* h, int32_t buf, const void* ho
  * refine_every > 0, between generations.  Synchronises. */
 MGFWA_API mgfwa_status mgfwa_debug_gradient(mgfwa_t* h, const float* xs, int32_t count, float* g_out,
                                             float* f_out);
+/* Which products serve the handle's FP32 first layer: *rescore (the elite
+ * re-score of a BF16 or FP8 handle) and *refine (the hybrid refinement and
+ * mgfwa_debug_gradient) are 1 where the FP32-accurate tensor-core layer runs
+ * (split TF32 products on tcgen05; a Blackwell GPU, first-layer width 32,
+ * 64 or 128, d_in a multiple of 4, and its (128-sample tile, vector)
+ * pairs numbering at least half the SMs), 0 where the CUDA-core products
+ * run, -1 where the handle has no such phase.  Either pointer may be NULL. */
+MGFWA_API mgfwa_status mgfwa_debug_fp32_tc(const mgfwa_t* h, int32_t* rescore, int32_t* refine);
 MGFWA_API mgfwa_status mgfwa_debug_profile(mgfwa_t* h, int32_t enable);
 MGFWA_API mgfwa_status mgfwa_debug_kernel_times(mgfwa_t* h, double* ms_out, int64_t* launches_out);
 

@@ -36,7 +36,7 @@ EXPORTS = ("mgfwa_config_init", "mgfwa_create", "mgfwa_step", "mgfwa_run", "mgfw
            "mgfwa_evaluate",
            "mgfwa_get_info", "mgfwa_destroy", "mgfwa_last_error", "mgfwa_debug_phase", "mgfwa_debug_read",
            "mgfwa_debug_write", "mgfwa_debug_profile", "mgfwa_debug_kernel_times", "mgfwa_evaluate_fp32_noalloc",
-           "mgfwa_debug_gradient",
+           "mgfwa_debug_gradient", "mgfwa_debug_fp32_tc",
            "mgfwa_footprint", "mgfwa_server_create", "mgfwa_server_submit", "mgfwa_server_tick", "mgfwa_server_poll",
            "mgfwa_server_stats_get", "mgfwa_server_now", "mgfwa_server_destroy", "mgfwa_group_create",
            "mgfwa_group_step", "mgfwa_group_destroy", "mgfwa_checkpoint_size", "mgfwa_checkpoint_save",
@@ -121,6 +121,7 @@ def load_library(path: Optional[str] = None):
     L.mgfwa_debug_profile.argtypes = [vp, i32]
     L.mgfwa_debug_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     L.mgfwa_debug_gradient.argtypes = [vp, f32p, i32, f32p, f32p]
+    L.mgfwa_debug_fp32_tc.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
     i32p = ctypes.POINTER(ctypes.c_int32)
     L.mgfwa_evaluate_fp32_noalloc.argtypes = [i32, i32p, i32p, i64, vp, vp, vp, i64, i32, vp, vp]
     L.mgfwa_footprint.argtypes = [ctypes.POINTER(mgfwa_config), ctypes.POINTER(mgfwa_objective),
@@ -262,6 +263,12 @@ def mgfwa_debug_write(handle: int, buf: int, src: np.ndarray) -> None:
     _check(load_library().mgfwa_debug_write(handle, buf, src.ctypes.data, src.nbytes), handle)
 
 
+def mgfwa_debug_fp32_tc(handle: int) -> tuple:
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(load_library().mgfwa_debug_fp32_tc(handle, ctypes.byref(a), ctypes.byref(b)), handle)
+    return a.value, b.value
+
+
 # ---------------------------------------------------------------------------
 # Convenience owner of one handle.
 
@@ -364,6 +371,11 @@ class Mgfwa:
         _check(load_library().mgfwa_debug_gradient(self.handle, _f32p(xs), xs.shape[0], _f32p(g), _f32p(f)),
                self.handle)
         return f, g
+
+    def fp32_tensor_cores(self) -> tuple:
+        """(re-score, refinement): 1 where the FP32-accurate tensor-core first layer serves it, 0 where the
+        CUDA-core products do, -1 where the handle has no such phase."""
+        return mgfwa_debug_fp32_tc(self.handle)
 
     def profile(self, enable: bool = True) -> None:
         _check(load_library().mgfwa_debug_profile(self.handle, int(enable)), self.handle)

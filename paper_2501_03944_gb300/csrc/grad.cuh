@@ -34,6 +34,12 @@ GradPlan grad_plan(const Mlp& mlp, int32_t R, int32_t num_sms, bool forward_only
 // kernels enqueued or -1.
 // With l1 (a ready plan over the same rows W, stride ld), the first layer
 // runs on the tensor cores at FP32 accuracy (status: its wait-timeout word).
+// Whether launch_grad runs the first layer of this plan on the tensor cores:
+// the plan over the rows is ready and its (128-sample tile, vector) pairs
+// number at least half the SMs; fewer vectors keep the CUDA-core products,
+// whose split-K gives every SM work.
+bool l1_on_tensor_cores(const GradPlan& gp, const Mlp& mlp, const L1Plan* l1);
+
 int launch_grad(const GradPlan& gp, const Mlp& mlp, const float* W, int64_t ld, float* scratch, float* G,
                 float* f_out, cudaStream_t s, const int32_t* idx = nullptr, const L1Plan* l1 = nullptr,
                 uint32_t* status = nullptr);

@@ -16,15 +16,20 @@
 // in FP32.  That keeps the result within FP32 accuracy for K in the
 // thousands.
 //
-// One CTA per (128-sample tile, vector): warp 0 issues TMA (FP32 tiles of X
-// and W1, 32 K-elements = one 128-byte swizzle row), warps 2..5 split each
-// landed stage in place (v1 over the FP32 tile, v2 and v3 into two twin
-// buffers at the same offsets, so the swizzled layout carries over
-// unchanged), warp 1 issues the MMAs into H TMEM columns, and warps 2..5
-// finally read the
-// accumulator (one sample row per thread), add b1, apply the activation and
-// store the row.  Every wait is bounded; a wait that gives up sets a bit in
-// the status word and the CTA drains its copies and MMAs and returns.
+// One CTA per 128-sample tile and 128 / h1 vectors.  Warp 0 issues TMA
+// (FP32 tiles of X and of the vectors' W1, 32 K-elements = one 128-byte
+// swizzle row per stage).  Warps
+// 2..5 split each landed stage: the W1 tile in place (v1 over the FP32
+// tile, v2 and v3 into two twin buffers at the same offsets, so the
+// swizzled layout carries over unchanged), and the X tile row by row (one
+// sample per thread, its TMEM lane) into a ring of TMEM slots, each holding
+// the three parts of 16 K-elements.  Warp 1 issues the MMAs with A (the X
+// parts) from TMEM and B (the W1 parts) from shared memory, so the tensor
+// core reads only the narrow operand from shared memory.  Warps 2..5
+// finally read the accumulators (one sample row per thread), add b1, apply
+// the activation and store the row.  Every wait is bounded; a wait that
+// gives up sets a bit in the status word and the CTA drains its copies and
+// MMAs and returns.
 #include <cuda.h>
 
 #include "fp32x3.cuh"
@@ -35,15 +40,19 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kBKf = 32;           // FP32 K elements per stage (128 bytes)
-constexpr int kMaxStages = 3;
+constexpr int kSlotK = 16;         // K elements per TMEM slot of the X parts
+constexpr int kMaxStages = 6;
+constexpr int kMaxSlots = 8;
 constexpr int kParts = 3;          // TF32 parts per operand
 constexpr int kThreads = 192;      // warp 0 TMA, warp 1 MMA, warps 2..5 convert + epilogue
+constexpr uint32_t kTmemCols = 512;
 constexpr uint64_t kWaitBudget = 1ull << 32;
 
 struct Bars {
-  uint64_t full[kMaxStages];
-  uint64_t conv[kMaxStages];
-  uint64_t empty[kMaxStages];
+  uint64_t full[kMaxStages];   // stage landed (TMA)
+  uint64_t empty[kMaxStages];  // stage free (its MMAs completed)
+  uint64_t a_full[kMaxSlots];  // slot written (and, for a stage's first slot, the stage's W1 parts split)
+  uint64_t a_empty[kMaxSlots]; // slot free (its MMAs completed)
   uint64_t done;
   uint32_t tmem_base;
   volatile int abort_flag;
@@ -121,12 +130,25 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
 __host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+// D (TMEM) (+)= A (TMEM) x B (shared memory), TF32 inputs.
+__device__ __forceinline__ void mma_tf32_ta(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t accum) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+// 32 lanes x 16 consecutive 32-bit columns.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+      "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+      "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
       : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* b) {
@@ -174,37 +196,55 @@ struct Args {
   int64_t b1_off;   // offset of b1 in a row
   const float* rows;
   const int32_t* idx;  // vector r is spark row idx[r] (or r)
+  int32_t R;        // vectors
   float* out;       // [R][N][H]
   uint32_t* status;
 };
 
-// Stages that fit: 3 parts of the X and W1 tiles per stage.
-constexpr int stages_for(int h) { return h >= 128 ? 2 : kMaxStages; }
+// Each CTA takes V = 128 / H vectors, so that every MMA is M=128, N=128:
+// the tensor core's cost per instruction barely depends on N at these
+// widths, so fewer, wider products are the faster way through the six.
+// Shared memory per stage: the FP32 X tile and the three parts of the V
+// stacked W1 tiles (128 rows).  TMEM: the accumulators (main even, main odd,
+// corrections: 3 x 128 columns) and then the X slots, 3 parts x 16 columns.
+constexpr int kN = 128;
+constexpr int kStages = 3;
+constexpr int kSlots = 2;
+constexpr uint32_t kABytes = kBM * 128;
+constexpr uint32_t kBBytes = kN * 128;
+constexpr uint32_t kSlotCols = kParts * kSlotK;
+constexpr uint32_t kSlot0 = 3 * kN;  // first TMEM column of the X slots
+static_assert(kSlot0 + kSlots * kSlotCols <= kTmemCols, "accumulators and X slots fit in TMEM");
+static_assert(kStages <= kMaxStages && kSlots <= kMaxSlots, "barrier arrays");
+static_assert(kBKf == 2 * kSlotK, "two slots per stage");
 
 template <int H>
 __global__ void __launch_bounds__(kThreads, 1)
     k_l1_fp32x3(const __grid_constant__ CUtensorMap tmap_x, const __grid_constant__ CUtensorMap tmap_w, Args a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  constexpr int kStages = stages_for(H);
-  constexpr uint32_t kABytes = kBM * 128;  // one stage of the X tile (FP32)
-  constexpr uint32_t kBBytes = H * 128;    // one stage of the W1 tile (FP32)
-  constexpr uint32_t kTmemCols = H == 32 ? 128 : (H == 64 ? 256 : 512);  // >= 3 H columns: main even, main odd, corrections
+  constexpr int V = kN / H;
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  // part p of stage s: A at base + (p * kStages + s) * kABytes, B after all A parts
-  uint8_t* a_part = base;
-  uint8_t* b_part = base + (size_t)kParts * kStages * kABytes;
-  auto A = [&](int p, int s) { return a_part + ((size_t)p * kStages + s) * kABytes; };
+  // X tile of stage s at base + s * kABytes; part p of the W1 tiles of stage s after all X tiles
+  uint8_t* b_part = base + (size_t)kStages * kABytes;
+  auto A = [&](int s) { return base + (size_t)s * kABytes; };
   auto Bp = [&](int p, int s) { return b_part + ((size_t)p * kStages + s) * kBBytes; };
   Bars* sb = reinterpret_cast<Bars*>(b_part + (size_t)kParts * kStages * kBBytes);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int mt = blockIdx.x, r = blockIdx.y;
-  const int row = a.idx ? a.idx[r] : r;
+  const int mt = blockIdx.x, r0 = blockIdx.y * V;
+  // vector v of this CTA: r0 + v, or (past the last vector) the last one again, computed and not stored
+  auto row_of = [&](int v) {
+    const int r = r0 + v < a.R ? r0 + v : a.R - 1;
+    return a.idx ? a.idx[r] : r;
+  };
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&sb->full[s], 1);
-      mbar_init(&sb->conv[s], 4);
       mbar_init(&sb->empty[s], 1);
+    }
+    for (int j = 0; j < kSlots; ++j) {
+      mbar_init(&sb->a_full[j], 4);
+      mbar_init(&sb->a_empty[j], 1);
     }
     mbar_init(&sb->done, 1);
     sb->abort_flag = 0;
@@ -224,14 +264,19 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {
+      int rows[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) rows[v] = row_of(v);
       int kb = 0;
       for (; kb < a.k_blocks; ++kb) {
         const int s = kb % kStages;
         const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
         if (!mbar_wait(sb, &sb->empty[s], ph ^ 1u, a.status, 1u)) break;
         mbar_expect_tx(&sb->full[s], kABytes + kBBytes);
-        tma_2d(A(0, s), &tmap_x, kb * kBKf, mt * kBM, &sb->full[s]);
-        tma_3d(Bp(0, s), &tmap_w, kb * kBKf, 0, row, &sb->full[s]);
+        tma_2d(A(s), &tmap_x, kb * kBKf, mt * kBM, &sb->full[s]);
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+          tma_3d(Bp(0, s) + (size_t)v * H * 128, &tmap_w, kb * kBKf, 0, rows[v], &sb->full[s]);
       }
       // every issued copy lands before the CTA may exit
       for (int j = kb - kStages > 0 ? kb - kStages : 0; j < kb; ++j)
@@ -239,80 +284,117 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = idesc_tf32(kBM, H);
+      const uint32_t idesc = idesc_tf32(kBM, kN);
       int kb = 0;
-      for (; kb < a.k_blocks; ++kb) {
+      bool ok = true;
+      for (; kb < a.k_blocks && ok; ++kb) {
         const int s = kb % kStages;
-        const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
-        if (!mbar_wait(sb, &sb->conv[s], ph, a.status, 2u)) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a1 = smem_u32(A(0, s)), a2 = smem_u32(A(1, s)), a3 = smem_u32(A(2, s));
         const uint32_t b1 = smem_u32(Bp(0, s)), b2 = smem_u32(Bp(1, s)), b3 = smem_u32(Bp(2, s));
-        const uint32_t d_main = tmem + (uint32_t)((kb & 1) * H), d_corr = tmem + (uint32_t)(2 * H);
+        const uint32_t d_main = tmem + (uint32_t)((kb & 1) * kN), d_corr = tmem + (uint32_t)(2 * kN);
 #pragma unroll
-        for (int k = 0; k < kBKf / 8; ++k) {
-          const uint32_t o = (uint32_t)k * 32u;
-          const uint32_t first = (kb < 2 && k == 0) ? 0u : 1u;        // this main accumulator's first product
-          const uint32_t first_c = (kb == 0 && k == 0) ? 0u : 1u;     // the corrections' first product
-          mma_tf32(d_main, smem_desc(a1 + o), smem_desc(b1 + o), idesc, first);
-          mma_tf32(d_corr, smem_desc(a1 + o), smem_desc(b2 + o), idesc, first_c);
-          mma_tf32(d_corr, smem_desc(a2 + o), smem_desc(b1 + o), idesc, 1u);
-          mma_tf32(d_corr, smem_desc(a2 + o), smem_desc(b2 + o), idesc, 1u);
-          mma_tf32(d_corr, smem_desc(a1 + o), smem_desc(b3 + o), idesc, 1u);
-          mma_tf32(d_corr, smem_desc(a3 + o), smem_desc(b1 + o), idesc, 1u);
+        for (int j = 0; j < 2; ++j) {
+          const int hk = 2 * kb + j;  // slot use number
+          const int slot = hk % kSlots;
+          if (!mbar_wait(sb, &sb->a_full[slot], (uint32_t)(hk / kSlots) & 1u, a.status, 2u)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t xa = tmem + kSlot0 + (uint32_t)slot * kSlotCols;
+#pragma unroll
+          for (int kk = 0; kk < kSlotK / 8; ++kk) {
+            const uint32_t o = (uint32_t)(j * (kSlotK / 8) + kk) * 32u;  // byte offset of this K step in a W1 row
+            const uint32_t a1 = xa + (uint32_t)(kk * 8), a2 = a1 + kSlotK, a3 = a1 + 2 * kSlotK;
+            const uint32_t first = (kb < 2 && j == 0 && kk == 0) ? 0u : 1u;     // this main accumulator's first
+            const uint32_t first_c = (kb == 0 && j == 0 && kk == 0) ? 0u : 1u;  // the corrections' first
+            mma_tf32_ta(d_main, a1, smem_desc(b1 + o), idesc, first);
+            mma_tf32_ta(d_corr, a1, smem_desc(b2 + o), idesc, first_c);
+            mma_tf32_ta(d_corr, a2, smem_desc(b1 + o), idesc, 1u);
+            mma_tf32_ta(d_corr, a2, smem_desc(b2 + o), idesc, 1u);
+            mma_tf32_ta(d_corr, a1, smem_desc(b3 + o), idesc, 1u);
+            mma_tf32_ta(d_corr, a3, smem_desc(b1 + o), idesc, 1u);
+          }
+          mma_commit(&sb->a_empty[slot]);
         }
-        mma_commit(&sb->empty[s]);
+        if (ok) mma_commit(&sb->empty[s]);
       }
       mma_commit(&sb->done);  // after every issued MMA (also on abort)
     }
   } else {
-    // split each landed stage: hi in place, lo into the twin buffer
-    const int ct = threadIdx.x - 64;  // 0..127
+    const int ct = threadIdx.x - 64;   // 0..127
+    const int q = warp & 3;            // TMEM lane quadrant this warp may access
+    const int rrow = q * 32 + lane;    // this thread's sample row of the tile = its TMEM lane
+    const uint32_t lanes = tmem + ((uint32_t)(q * 32) << 16);
     bool ok = true;
     for (int kb = 0; kb < a.k_blocks && ok; ++kb) {
       const int s = kb % kStages;
       const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
-      // the twin buffers of this stage are free once the stage's MMAs completed
       ok = mbar_wait(sb, &sb->full[s], ph, a.status, 4u);
       if (!ok) break;
-      split3(reinterpret_cast<float4*>(A(0, s)), reinterpret_cast<float4*>(A(1, s)),
-             reinterpret_cast<float4*>(A(2, s)), (int)(kABytes / 16), ct);
+      // W1 parts: v1 in place, v2 and v3 into the twins (free: the stage's MMAs of its last use completed)
       split3(reinterpret_cast<float4*>(Bp(0, s)), reinterpret_cast<float4*>(Bp(1, s)),
              reinterpret_cast<float4*>(Bp(2, s)), (int)(kBBytes / 16), ct);
       // generic-proxy writes become visible to the tensor core's (async proxy) reads
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sb->conv[s]);
+      const uint8_t* xrow = A(s) + rrow * 128;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int hk = 2 * kb + j;
+        const int slot = hk % kSlots;
+        // 16 K-elements of this sample: 16-byte chunks 4j..4j+3 of its row, at chunk c ^ (row & 7) (128-byte swizzle)
+        float v1[kSlotK], v2[kSlotK], v3[kSlotK];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float4 v = *reinterpret_cast<const float4*>(xrow + (((4 * j + c) ^ (rrow & 7)) << 4));
+          split1(v.x, v1[4 * c + 0], v2[4 * c + 0], v3[4 * c + 0]);
+          split1(v.y, v1[4 * c + 1], v2[4 * c + 1], v3[4 * c + 1]);
+          split1(v.z, v1[4 * c + 2], v2[4 * c + 2], v3[4 * c + 2]);
+          split1(v.w, v1[4 * c + 3], v2[4 * c + 3], v3[4 * c + 3]);
+        }
+        ok = mbar_wait(sb, &sb->a_empty[slot], ((uint32_t)(hk / kSlots) & 1u) ^ 1u, a.status, 8u);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t xa = lanes + kSlot0 + (uint32_t)slot * kSlotCols;
+        tmem_st16(xa, v1);
+        tmem_st16(xa + kSlotK, v2);
+        tmem_st16(xa + 2 * kSlotK, v3);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sb->a_full[slot]);
+      }
     }
-    // epilogue: row = this thread's TMEM lane
-    const int q = warp & 3;            // lane quadrant this warp may access
-    const int rrow = q * 32 + lane;
+    // epilogue: row = this thread's TMEM lane; columns [v H, (v + 1) H) are vector r0 + v
     mbar_drain(&sb->done, 0u, a.status);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int64_t n = (int64_t)mt * kBM + rrow;
-    const float* bias = a.rows + (int64_t)row * a.ld + a.b1_off;
-    float* out = a.out + ((int64_t)r * a.N + n) * H;
     const bool valid = ok && !sb->abort_flag && n < a.N;
-    const uint32_t lanes = tmem + ((uint32_t)(q * 32) << 16);
     const bool odd = a.k_blocks > 1;  // the odd-block accumulator holds products
 #pragma unroll 1
-    for (int j0 = 0; j0 < H; j0 += 8) {
-      float v[8], v1[8], vc[8];
-      tmem_ld8(lanes + (uint32_t)j0, v);
-      tmem_ld8(lanes + (uint32_t)(H + j0), v1);
-      tmem_ld8(lanes + (uint32_t)(2 * H + j0), vc);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    for (int v = 0; v < V; ++v) {
+      const bool store = valid && r0 + v < a.R;
+      const float* bias = a.rows + (int64_t)row_of(v) * a.ld + a.b1_off;
+      float* out = a.out + ((int64_t)(r0 + v) * a.N + n) * H;
+#pragma unroll 1
+      for (int j0 = 0; j0 < H; j0 += 8) {
+        const uint32_t c = (uint32_t)(v * H + j0);
+        float x[8], x1[8], xc[8];
+        tmem_ld8(lanes + c, x);
+        tmem_ld8(lanes + (uint32_t)kN + c, x1);
+        tmem_ld8(lanes + (uint32_t)(2 * kN) + c, xc);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int i = 0; i < 8; ++i) v[i] = (odd ? v[i] + v1[i] : v[i]) + vc[i];
-      if (valid) {
-        float o[8];
+        for (int i = 0; i < 8; ++i) x[i] = (odd ? x[i] + x1[i] : x[i]) + xc[i];
+        if (store) {
+          float o[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const float z = v[i] + bias[j0 + i];
-          o[i] = a.act == kActTanh ? tanhf(z) : fmaxf(z, 0.f);
+          for (int i = 0; i < 8; ++i) {
+            const float z = x[i] + bias[j0 + i];
+            o[i] = a.act == kActTanh ? tanhf(z) : fmaxf(z, 0.f);
+          }
+          *reinterpret_cast<float4*>(out + j0) = make_float4(o[0], o[1], o[2], o[3]);
+          *reinterpret_cast<float4*>(out + j0 + 4) = make_float4(o[4], o[5], o[6], o[7]);
         }
-        *reinterpret_cast<float4*>(out + j0) = make_float4(o[0], o[1], o[2], o[3]);
-        *reinterpret_cast<float4*>(out + j0 + 4) = make_float4(o[4], o[5], o[6], o[7]);
       }
     }
   }
@@ -353,16 +435,15 @@ bool encode(CUtensorMap* map, uint32_t rank, const void* ptr, const cuuint64_t* 
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t smem_bytes(int H) {
-  return 1024 + (size_t)stages_for(H) * kParts * ((size_t)kBM * 128 + (size_t)H * 128) + sizeof(Bars) + 64;
-}
+size_t smem_bytes() { return 1024 + (size_t)kStages * (kABytes + (size_t)kParts * kBBytes) + sizeof(Bars) + 64; }
 
 template <int H>
 cudaError_t go(const L1Plan& pl, const Args& a, int R, cudaStream_t s, bool prep) {
-  cudaError_t e = ensure_smem_limit<k_l1_fp32x3<H>>(smem_bytes(H));
+  cudaError_t e = ensure_smem_limit<k_l1_fp32x3<H>>(smem_bytes());
   if (e != cudaSuccess || prep) return e;
-  const dim3 grid((unsigned)((a.N + kBM - 1) / kBM), (unsigned)R);
-  k_l1_fp32x3<H><<<grid, kThreads, smem_bytes(H), s>>>(pl.tmap_x, pl.tmap_w, a);
+  constexpr int V = kN / H;
+  const dim3 grid((unsigned)((a.N + kBM - 1) / kBM), (unsigned)((R + V - 1) / V));
+  k_l1_fp32x3<H><<<grid, kThreads, smem_bytes(), s>>>(pl.tmap_x, pl.tmap_w, a);
   return cudaPeekAtLastError();
 }
 
@@ -422,6 +503,7 @@ int launch_l1_fp32x3(const L1Plan& pl, const Mlp& mlp, const int32_t* idx, int32
   a.b1_off = mlp.b_off[0];
   a.rows = pl.rows;
   a.idx = idx;
+  a.R = R;
   a.out = out;
   a.status = status;
   cudaError_t e;

@@ -683,6 +683,11 @@ GemmArgs make_gemm(const Gemm& sh, int R, float* P) {
 
 }  // namespace
 
+bool l1_on_tensor_cores(const GradPlan& gp, const Mlp& mlp, const L1Plan* l1) {
+  const int64_t l1_ctas = (int64_t)gp.R * ((mlp.N + 127) / 128);
+  return l1 && l1->ready && 2 * l1_ctas >= gp.num_sms;
+}
+
 int launch_grad(const GradPlan& gp, const Mlp& mlp, const float* W, int64_t ld, float* scratch, float* G,
                 float* f_out, cudaStream_t s, const int32_t* idx, const L1Plan* l1, uint32_t* status) {
   const int L = mlp.n_layers;
@@ -701,10 +706,8 @@ int launch_grad(const GradPlan& gp, const Mlp& mlp, const float* W, int64_t ld, 
   // hidden layers: Z_l = A_{l-1} W_l^T, then bias and activation
   for (int l = 1; l < L; ++l) {
     const int64_t fi = mlp.widths[l - 1];
-    const int64_t l1_ctas = (int64_t)R * ((N + 127) / 128);  // one CTA per (128-sample tile, vector)
-    if (l == 1 && l1 && l1->ready && status && 2 * l1_ctas >= gp.num_sms) {
-      // the first layer on the tensor cores at FP32 accuracy, when its CTAs fill at least half the SMs
-      // (fewer vectors keep the CUDA-core products, whose split-K gives every SM work)
+    if (l == 1 && status && l1_on_tensor_cores(gp, mlp, l1)) {
+      // the first layer on the tensor cores at FP32 accuracy
       ++gi;
       const int k = launch_l1_fp32x3(*l1, mlp, idx, R, act(1), status, s);
       if (k < 0) return -1;

@@ -1286,6 +1286,13 @@ mgfwa_status mgfwa_debug_gradient(mgfwa_t* h, const float* xs, int32_t count, fl
   return MGFWA_OK;
 }
 
+mgfwa_status mgfwa_debug_fp32_tc(const mgfwa_t* h, int32_t* rescore, int32_t* refine) {
+  if (!h) return MGFWA_EINVAL;
+  if (rescore) *rescore = h->rescore_scratch ? (l1_on_tensor_cores(h->rescore_plan, h->mlp, &h->rescore_l1) ? 1 : 0) : -1;
+  if (refine) *refine = h->refine ? (l1_on_tensor_cores(h->gp, h->mlp, &h->refine_l1) ? 1 : 0) : -1;
+  return MGFWA_OK;
+}
+
 mgfwa_status mgfwa_debug_profile(mgfwa_t* h, int32_t enable) {
   mgfwa_status st = check_usable(h);
   if (st != MGFWA_OK) return st;

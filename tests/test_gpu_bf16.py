@@ -150,14 +150,19 @@ def test_bf16_whole_run_learns(pkg):
     assert abs(bf - prob.fitness(bx)) <= 1e-12 * bf
 
 
-def test_elite_candidates_are_rescored_in_fp32(pkg):
+@pytest.mark.parametrize("N,mu,E", [(300, 3, 3), (2048, 5, 2)])
+def test_elite_candidates_are_rescored_in_fp32(pkg, N, mu, E):
     """With BF16 fitness, each firework's E best candidates (by BF16 fitness, (fitness, index) order) get their
-    fitness recomputed by the FP32 path before selection; the others keep their BF16 values."""
-    E = 3
-    w = W.scaled(W.MLP_784_64_10, n_samples=300, n_fireworks=3, sparks_per_firework=20, guiding_per_firework=4)
+    fitness recomputed by the FP32 path before selection; the others keep their BF16 values.  At 2048 samples
+    the 10 re-scored rows x 16 sample tiles engage the FP32-accurate tensor-core first layer; at 300 samples
+    the CUDA-core products run."""
+    import torch
+    w = W.scaled(W.MLP_784_64_10, n_samples=N, n_fireworks=mu, sparks_per_firework=20, guiding_per_firework=4)
     X, y = W.make_data(w)
     mu, lam, m = w.n_fireworks, w.sparks_per_firework, w.guiding_per_firework
     with pkg.Mgfwa.for_workload(w, 8, precision=pkg.MGFWA_BF16, X=X, y=y, elite_rescore=E) as run:
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        assert run.fp32_tensor_cores() == (int(2 * mu * E * ((N + 127) // 128) >= sms), -1)
         for ph in (pkg.MGFWA_PHASE_EXPLODE, pkg.MGFWA_PHASE_EVAL_E, pkg.MGFWA_PHASE_RANK, pkg.MGFWA_PHASE_GUIDE,
                    pkg.MGFWA_PHASE_EVAL_G):
             run.phase(ph)

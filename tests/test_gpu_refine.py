@@ -36,6 +36,11 @@ def _net(widths, acts, N, lb=-1.0, ub=1.0, seed=0, **over):
     return W.Workload(**kw)
 
 
+def _sms():
+    import torch
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
 @pytest.mark.parametrize("widths,acts,N,R", [
     ((8, 16, 3), (W.ACT_TANH,), 300, 3),
     ((16, 12, 8, 5), (W.ACT_TANH, W.ACT_RELU), 77, 2),
@@ -43,24 +48,64 @@ def _net(widths, acts, N, lb=-1.0, ub=1.0, seed=0, **over):
     ((784, 64, 10), (W.ACT_RELU,), 2048, 1),
     ((3072, 128, 64, 10), (W.ACT_RELU, W.ACT_RELU), 256, 1),
     ((8, 16, 3), (W.ACT_RELU,), 1, 1),
+    # enough vectors x 128-sample tiles for the FP32-accurate tensor-core first layer:
+    ((784, 64, 10), (W.ACT_RELU,), 1000, 10),                   # ragged tile (1000 = 7 x 128 + 104), ragged K
+    ((64, 32, 7), (W.ACT_TANH,), 2000, 5),                      # h1 = 32, two K blocks
+    ((40, 64, 5), (W.ACT_TANH,), 2048, 5),                      # second K block 8 wide
+    ((32, 64, 5), (W.ACT_RELU,), 2048, 5),                      # one K block: no odd-block accumulator
+    ((3072, 128, 64, 10), (W.ACT_TANH, W.ACT_TANH), 1024, 10),  # h1 = 128, 96 K blocks
+    ((3072, 128, 64, 10), (W.ACT_RELU, W.ACT_RELU), 1024, 10),  # the same with ReLU: objective only (below)
 ])
 def test_gradient_matches_oracle(pkg, widths, acts, N, R):
     """|dg| <= 1e-5 max|g| + 1e-4 |g|: every component is a sum over the N
     samples of products, accumulated in FP32 in tile and split order; with
     cancellation the sum of magnitudes can exceed the largest component by
     ~10^2, so ~sqrt(N) 2^-24 10^2 max|g| ~ 3e-7 max|g| is the expected size.
-    The objective meets the FP32 fitness bar (1e-5 relative + 1e-5)."""
+    The objective meets the FP32 fitness bar (1e-5 relative + 1e-5).  The
+    first layer runs on the tensor cores (split TF32 products) exactly when
+    its (128-sample tile, vector) pairs number half the SMs; the same bars
+    hold on both paths.
+
+    With ReLU, a pre-activation within its FP32 rounding of zero may take
+    the other side of the kink than in FP64, which moves the gradient by one
+    sample's whole contribution (~1/N of a typical component): any FP32
+    evaluation does this at a rate of about one per 10^6 pre-activations.
+    The 10 x 1024 x 128 first-layer pre-activations of the large ReLU case
+    meet it, so there only the objective is compared; the same network with
+    tanh checks the gradient through the same products."""
     w = _net(widths, acts, N)
     X, y = W.make_data(w)
     prob = oracle.Problem.for_workload(w, X, y)
     xs = W.random_vectors(R, w.dim, -0.5, 0.5, 7)
     with pkg.Mgfwa.for_workload(w, 1, X=X, y=y, n_runs=R, refine_every=1, refine_steps=1, refine_lr=0.1) as h:
         f, g = h.gradient(xs)
+        tc_expected = widths[1] in (32, 64, 128) and 2 * R * ((N + 127) // 128) >= _sms()
+        assert h.fp32_tensor_cores() == (-1, int(tc_expected))
     for r in range(R):
         fo, go = oracle.gradient(prob, xs[r])
         assert abs(f[r] - fo) <= 1e-5 * abs(fo) + 1e-5
+        if W.ACT_RELU in acts and R * N * widths[1] > 10 ** 6:
+            continue
         mx = np.max(np.abs(go))
         assert np.all(np.abs(g[r] - go) <= 1e-5 * mx + 1e-4 * np.abs(go)), (r, np.max(np.abs(g[r] - go)) / mx)
+
+
+@pytest.mark.parametrize("widths,acts,N,R", [
+    ((784, 64, 10), (W.ACT_RELU,), 1000, 10),  # two vectors per tensor-core CTA
+    ((64, 32, 7), (W.ACT_TANH,), 2000, 5),     # four per CTA, the last CTA with one
+])
+def test_tensor_core_layer_is_pairing_invariant(pkg, widths, acts, N, R):
+    """The tensor-core first layer stacks 128 / h1 vectors in one CTA (N = 128 products); each vector's columns
+    are its own sums, so a vector's objective and gradient are bitwise the same whichever vectors share its CTA."""
+    w = _net(widths, acts, N)
+    X, y = W.make_data(w)
+    xs = W.random_vectors(R, w.dim, -0.5, 0.5, 11)
+    perm = np.roll(np.arange(R), 3)
+    with pkg.Mgfwa.for_workload(w, 1, X=X, y=y, n_runs=R, refine_every=1, refine_steps=1, refine_lr=0.1) as h:
+        assert h.fp32_tensor_cores()[1] == int(2 * R * ((N + 127) // 128) >= _sms())
+        f1, g1 = h.gradient(xs)
+        f2, g2 = h.gradient(xs[perm])
+    assert np.array_equal(f2, f1[perm]) and np.array_equal(g2, g1[perm])
 
 
 def test_refine_phase_matches_oracle(pkg):
