@@ -29,6 +29,8 @@ __host__ __device__ __forceinline__ int odd_ld(int w) { return w + ((w & 1) == 0
 __global__ void __launch_bounds__(kThreads) k_fitness_simt(Mlp mlp, const float* __restrict__ rows, int64_t ld,
                                                            int32_t count, const int32_t* __restrict__ idx,
                                                            float* __restrict__ partial) {
+  griddep_wait();
+  griddep_launch_dependents();
   extern __shared__ __align__(16) float smem[];
   const int row = blockIdx.x, mt = blockIdx.y;
   const float* w = rows + (int64_t)(idx != nullptr ? idx[row] : row) * ld;
@@ -147,6 +149,8 @@ __global__ void __launch_bounds__(kThreads) k_fitness_simt(Mlp mlp, const float*
 
 __global__ void k_fitness_finish(const float* __restrict__ partial, int32_t mtiles, int32_t count, float n_f,
                                  const int32_t* __restrict__ idx, float* __restrict__ fit) {
+  griddep_wait();
+  griddep_launch_dependents();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= count) return;
   float s = partial[r];
@@ -156,6 +160,8 @@ __global__ void k_fitness_finish(const float* __restrict__ partial, int32_t mtil
 
 __global__ void __launch_bounds__(256) k_sphere(const float* __restrict__ rows, int64_t ld, int64_t D,
                                                 float* __restrict__ fit) {
+  griddep_wait();
+  griddep_launch_dependents();
   __shared__ float red[8];
   const float* x = rows + (int64_t)blockIdx.x * ld;
   float s = 0.0f;
@@ -178,6 +184,8 @@ constexpr int kF64Samples = 4;
 
 __global__ void __launch_bounds__(256) k_fitness_f64(Mlp mlp, const float* __restrict__ x, int wmax,
                                                      double* __restrict__ ce64) {
+  griddep_wait();
+  griddep_launch_dependents();
   extern __shared__ double sd[];
   double* a = sd;                          // [kF64Samples][wmax]
   double* b = sd + (size_t)kF64Samples * wmax;
@@ -236,6 +244,8 @@ __global__ void __launch_bounds__(256) k_fitness_f64(Mlp mlp, const float* __res
 // Fixed-order mean (or sum of squares) in FP64 by one block.
 __global__ void __launch_bounds__(256) k_reduce_f64(const double* __restrict__ v, const float* __restrict__ xf,
                                                     int64_t n, double scale, double* __restrict__ out) {
+  griddep_wait();
+  griddep_launch_dependents();
   __shared__ double red[256];
   double s = 0.0;
   for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
@@ -268,8 +278,10 @@ size_t fitness_simt_smem_bytes(const Mlp& mlp) { return smem_for(mlp); }
 int launch_fitness_finish(const float* partial, int32_t mtiles, int32_t count, int64_t N, float* fit,
                           cudaStream_t s, const int32_t* idx) {
   if (count <= 0) return 0;
-  k_fitness_finish<<<(count + 255) / 256, 256, 0, s>>>(partial, mtiles, count, (float)N, idx, fit);
-  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+  return launch_pdl(k_fitness_finish, dim3((count + 255) / 256), dim3(256), 0, s, partial, mtiles, count, (float)N,
+                    idx, fit) == cudaSuccess
+             ? 1
+             : -1;
 }
 
 int launch_fitness_simt_main(const Mlp& mlp, const float* rows, int64_t ld, int32_t count, float* partial,
@@ -279,14 +291,14 @@ int launch_fitness_simt_main(const Mlp& mlp, const float* rows, int64_t ld, int3
   if (ensure_smem_limit<k_fitness_simt>(smem) != cudaSuccess) return -1;
   const int mtiles = (int)((mlp.N + kMT - 1) / kMT);
   dim3 grid(count, mtiles);
-  k_fitness_simt<<<grid, kThreads, smem, s>>>(mlp, rows, ld, count, idx, partial);
-  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+  return launch_pdl(k_fitness_simt, grid, dim3(kThreads), smem, s, mlp, rows, ld, count, idx, partial) == cudaSuccess
+             ? 1
+             : -1;
 }
 
 int launch_fitness_sphere(const float* rows, int64_t ld, int64_t D, int32_t count, float* fit, cudaStream_t s) {
   if (count <= 0) return 0;
-  k_sphere<<<count, 256, 0, s>>>(rows, ld, D, fit);
-  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+  return launch_pdl(k_sphere, dim3(count), dim3(256), 0, s, rows, ld, D, fit) == cudaSuccess ? 1 : -1;
 }
 
 int launch_fitness_f64(const Mlp& mlp, const float* x, double* ce64, double* out, cudaStream_t s) {

@@ -293,6 +293,8 @@ template <int H1, int H2, int NL, bool F8>
 __global__ void __launch_bounds__(kThreads, 1)
     k_fitness_tc(const __grid_constant__ CUtensorMap tmap_x, const __grid_constant__ CUtensorMap tmap_w,
                  const __grid_constant__ CUtensorMap tmap_w2, const __grid_constant__ CUtensorMap tmap_w3, TcArgs a) {
+  griddep_wait();
+  griddep_launch_dependents();
   constexpr int kBK = F8 ? 128 : 64;  // K elements per stage (one 128-byte row)
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   constexpr bool kL3 = H2 > 0;
@@ -683,9 +685,8 @@ cudaError_t launch_hn(const TcPlan& plan, const TcArgs& args, cudaStream_t s, bo
   if (e != cudaSuccess || prepare_only) return e;
   const int tiles = args.m_tiles * args.n_tiles;
   const int grid = tiles < plan.num_sms ? tiles : plan.num_sms;
-  k_fitness_tc<H1, H2, NL, F8><<<grid, kThreads, plan.smem_bytes, s>>>(plan.tmap_x, plan.tmap_w, plan.tmap_w2,
-                                                                        plan.tmap_w3, args);
-  return cudaPeekAtLastError();
+  return launch_pdl(k_fitness_tc<H1, H2, NL, F8>, dim3(grid), dim3(kThreads), plan.smem_bytes, s, plan.tmap_x,
+                    plan.tmap_w, plan.tmap_w2, plan.tmap_w3, args);
 }
 
 template <int H1, bool F8>

@@ -221,6 +221,8 @@ static_assert(kBKf == 2 * kSlotK, "two slots per stage");
 template <int H>
 __global__ void __launch_bounds__(kThreads, 1)
     k_l1_fp32x3(const __grid_constant__ CUtensorMap tmap_x, const __grid_constant__ CUtensorMap tmap_w, Args a) {
+  griddep_wait();
+  griddep_launch_dependents();
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   constexpr int V = kN / H;
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -443,8 +445,7 @@ cudaError_t go(const L1Plan& pl, const Args& a, int R, cudaStream_t s, bool prep
   if (e != cudaSuccess || prep) return e;
   constexpr int V = kN / H;
   const dim3 grid((unsigned)((a.N + kBM - 1) / kBM), (unsigned)((R + V - 1) / V));
-  k_l1_fp32x3<H><<<grid, kThreads, smem_bytes(), s>>>(pl.tmap_x, pl.tmap_w, a);
-  return cudaPeekAtLastError();
+  return launch_pdl(k_l1_fp32x3<H>, grid, dim3(kThreads), smem_bytes(), s, pl.tmap_x, pl.tmap_w, a);
 }
 
 }  // namespace

@@ -60,6 +60,8 @@ struct GemmArgs {
 // of 4).
 template <int BM, int BN, bool A_K, bool B_K, bool VEC>
 __global__ void __launch_bounds__(256, 2) k_gemm_f32(GemmArgs g) {
+  griddep_wait();
+  griddep_launch_dependents();
   constexpr int TM = BM / 16, TN = BN / 16;
   constexpr int EA = BM * kBK / 256, EB = BN * kBK / 256;  // scalar loads per thread
   constexpr int PADM = BM + 4, PADN = BN + 4;
@@ -265,6 +267,8 @@ struct RedArgs {
 
 
 __global__ void k_reduce_epi(RedArgs a) {
+  griddep_wait();
+  griddep_launch_dependents();
   const int64_t per = (int64_t)a.M * a.Nc;
   const int64_t total = per * a.R;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -315,6 +319,8 @@ __global__ void k_reduce_epi(RedArgs a) {
 // f[r] = mean of loss[r][0..N): per-thread sums in sample order, then a
 // fixed tree, so the value does not depend on scheduling.
 __global__ void __launch_bounds__(256) k_loss_mean(const float* loss, int64_t N, float* f, const int32_t* idx) {
+  griddep_wait();
+  griddep_launch_dependents();
   __shared__ float part[256];
   const float* l = loss + (int64_t)blockIdx.x * N;
   float s = 0.f;
@@ -330,6 +336,8 @@ __global__ void __launch_bounds__(256) k_loss_mean(const float* loss, int64_t N,
 
 // w <- min(max(fma(-lr, g, w), lb), ub) on the D real coordinates.
 __global__ void k_sgd(float* w, const float* g, int32_t R, int64_t D, int64_t Dp, float lr, float lb, float ub) {
+  griddep_wait();
+  griddep_launch_dependents();
   const int64_t total = (int64_t)R * D;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -344,6 +352,8 @@ __global__ void k_sgd(float* w, const float* g, int32_t R, int64_t D, int64_t Dp
 // refinement buffer by all blocks of the run, each a slice of the row.
 __global__ void __launch_bounds__(256) k_refine_pick(const float* fw_x, const float* fw_f, int32_t mu, int64_t Dp,
                                                      float* w, int32_t* elite) {
+  griddep_wait();
+  griddep_launch_dependents();
   __shared__ int e_s;
   const int r = blockIdx.y;
   if (threadIdx.x == 0) {
@@ -366,6 +376,8 @@ __global__ void __launch_bounds__(256) k_refine_pick(const float* fw_x, const fl
 // by k_refine_copy.
 __global__ void k_refine_decide(const float* fr, const int32_t* elite, float* fw_f, float* best_f, int32_t mu,
                                 int32_t R, int32_t* flags) {
+  griddep_wait();
+  griddep_launch_dependents();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= R) return;
   const int64_t z = (int64_t)r * mu + elite[r];
@@ -379,6 +391,8 @@ __global__ void k_refine_decide(const float* fr, const int32_t* elite, float* fw
 
 __global__ void __launch_bounds__(256) k_refine_copy(const float* w, const int32_t* elite, const int32_t* flags,
                                                      float* fw_x, float* best_x, int32_t mu, int64_t Dp) {
+  griddep_wait();
+  griddep_launch_dependents();
   const int r = blockIdx.y;
   const int fl = flags[r];
   if (!(fl & 1)) return;
@@ -421,6 +435,8 @@ size_t tail_smem_bytes(int h, int C) {
 }
 
 __global__ void __launch_bounds__(256) k_out_layer(TailArgs t) {
+  griddep_wait();
+  griddep_launch_dependents();
   extern __shared__ float sm[];
   const int h = t.h, C = t.C, hp = h + 1, cp = C + 1;
   float* As = sm;                       // [128][hp]
@@ -597,10 +613,9 @@ struct Enq {
   template <int BM, int BN, bool AK, bool BK>
   void go(const GemmArgs& g, bool vec) {
     const dim3 grid((unsigned)((g.Nc + BN - 1) / BN), (unsigned)((g.M + BM - 1) / BM), (unsigned)(g.R * g.S));
-    if (vec)
-      k_gemm_f32<BM, BN, AK, BK, true><<<grid, 256, 0, s>>>(g);
-    else
-      k_gemm_f32<BM, BN, AK, BK, false><<<grid, 256, 0, s>>>(g);
+    const cudaError_t e = vec ? launch_pdl(k_gemm_f32<BM, BN, AK, BK, true>, grid, dim3(256), 0, s, g)
+                              : launch_pdl(k_gemm_f32<BM, BN, AK, BK, false>, grid, dim3(256), 0, s, g);
+    if (e != cudaSuccess) ok = false;
   }
   template <int BM, int BN>
   void go_tile(const GemmArgs& g, bool vec) {
@@ -657,7 +672,8 @@ struct Enq {
     return aligned(g.A) && aligned(g.B) && g.sar % 4 == 0 && g.sbr % 4 == 0;
   }
   void reduce(const RedArgs& a) {
-    k_reduce_epi<<<grid_for((int64_t)a.R * a.M * a.Nc), 256, 0, s>>>(a);
+    if (launch_pdl(k_reduce_epi, dim3(grid_for((int64_t)a.R * a.M * a.Nc)), dim3(256), 0, s, a) != cudaSuccess)
+      ok = false;
     note();
   }
   void note() {
@@ -754,11 +770,12 @@ int launch_grad(const GradPlan& gp, const Mlp& mlp, const float* W, int64_t ld, 
     const size_t smem = tail_smem_bytes(t.h, t.C);
     if (smem > 48 * 1024 && ensure_smem_limit<k_out_layer>(smem) != cudaSuccess) return -1;
     const dim3 grid((unsigned)((N + kTailM - 1) / kTailM), (unsigned)R);
-    k_out_layer<<<grid, 256, smem, s>>>(t);
+    if (launch_pdl(k_out_layer, grid, dim3(256), smem, s, t) != cudaSuccess) return -1;
     q.note();
   }
   if (f_out) {
-    k_loss_mean<<<R, 256, 0, s>>>(loss, N, f_out, idx);
+    if (launch_pdl(k_loss_mean, dim3(R), dim3(256), 0, s, (const float*)loss, N, f_out, idx) != cudaSuccess)
+      return -1;
     q.note();
   }
   if (!want_grad) return q.ok ? q.n : -1;
@@ -809,8 +826,10 @@ int launch_grad(const GradPlan& gp, const Mlp& mlp, const float* W, int64_t ld, 
 
 int launch_sgd(float* w, const float* g, int32_t R, int64_t D, int64_t Dp, float lr, float lb, float ub,
                cudaStream_t s) {
-  k_sgd<<<grid_for((int64_t)R * D), 256, 0, s>>>(w, g, R, D, Dp, lr, lb, ub);
-  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+  return launch_pdl(k_sgd, dim3(grid_for((int64_t)R * D)), dim3(256), 0, s, w, g, R, D, Dp, lr, lb, ub) ==
+                 cudaSuccess
+             ? 1
+             : -1;
 }
 
 namespace {
@@ -823,17 +842,22 @@ unsigned copy_blocks(int64_t Dp) {
 
 int launch_refine_pick(const float* fw_x, const float* fw_f, int32_t R, int32_t mu, int64_t Dp, float* w,
                        int32_t* elite, cudaStream_t s) {
-  k_refine_pick<<<dim3(copy_blocks(Dp), (unsigned)R), 256, 0, s>>>(fw_x, fw_f, mu, Dp, w, elite);
-  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+  return launch_pdl(k_refine_pick, dim3(copy_blocks(Dp), (unsigned)R), dim3(256), 0, s, fw_x, fw_f, mu, Dp, w,
+                    elite) == cudaSuccess
+             ? 1
+             : -1;
 }
 
 int launch_refine_accept(const float* w, const float* fr, const int32_t* elite, int32_t* flags, float* fw_x,
                          float* fw_f, float* best_x, float* best_f, int32_t R, int32_t mu, int64_t Dp,
                          cudaStream_t s) {
-  k_refine_decide<<<(R + 127) / 128, 128, 0, s>>>(fr, elite, fw_f, best_f, mu, R, flags);
-  if (cudaPeekAtLastError() != cudaSuccess) return -1;
-  k_refine_copy<<<dim3(copy_blocks(Dp), (unsigned)R), 256, 0, s>>>(w, elite, flags, fw_x, best_x, mu, Dp);
-  return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;
+  if (launch_pdl(k_refine_decide, dim3((R + 127) / 128), dim3(128), 0, s, fr, elite, fw_f, best_f, mu, R, flags) !=
+      cudaSuccess)
+    return -1;
+  return launch_pdl(k_refine_copy, dim3(copy_blocks(Dp), (unsigned)R), dim3(256), 0, s, w, elite,
+                    (const int32_t*)flags, fw_x, best_x, mu, Dp) == cudaSuccess
+             ? 2
+             : -1;
 }
 
 }  // namespace mgfwa

@@ -17,6 +17,8 @@ namespace {
 // counts are a permutation because the order is total.
 __global__ void k_rank(Problem p, const float* __restrict__ fit_e, int32_t* __restrict__ top,
                        int32_t* __restrict__ bottom) {
+  griddep_wait();
+  griddep_launch_dependents();
   extern __shared__ float sh[];
   const int g = p.g, k = p.k;
   float* f = sh;
@@ -59,6 +61,8 @@ __global__ void __launch_bounds__(kSelThreads) k_select(Problem p, const float* 
                                                         const float* __restrict__ guides,
                                                         float* __restrict__ fw_x, float* __restrict__ fw_amp,
                                                         float* __restrict__ fw_f, int32_t* __restrict__ winner) {
+  griddep_wait();
+  griddep_launch_dependents();
   __shared__ float wf[kSelThreads / 32];
   __shared__ int wc[kSelThreads / 32];
   __shared__ int s_win;
@@ -114,6 +118,8 @@ __global__ void __launch_bounds__(kSelThreads) k_run_best(Problem p, int init, c
                                                           const float* __restrict__ fw_f,
                                                           float* __restrict__ best_x, float* __restrict__ best_f,
                                                           uint32_t* __restrict__ gens_done) {
+  griddep_wait();
+  griddep_launch_dependents();
   __shared__ int s_bi;
   const int b = blockIdx.x;
   const float* f = fw_f + (int64_t)b * p.mu;
@@ -143,6 +149,8 @@ __global__ void __launch_bounds__(kSelThreads) k_run_best(Problem p, int init, c
 // previous ones.
 __global__ void k_elite_pick(Problem p, const float* __restrict__ fit_e, const float* __restrict__ fit_g,
                              int32_t E, int32_t* __restrict__ elite) {
+  griddep_wait();
+  griddep_launch_dependents();
   const int z = blockIdx.x;
   const int lane = threadIdx.x;
   const int n_cand = p.lam + p.m;
@@ -178,23 +186,28 @@ __global__ void k_elite_pick(Problem p, const float* __restrict__ fit_e, const f
 int launch_elite_pick(const Problem& p, const float* fit_e, const float* fit_g, int32_t E, int32_t* elite,
                       cudaStream_t s) {
   if (E <= 0) return 0;
-  k_elite_pick<<<p.B * p.mu, 32, 0, s>>>(p, fit_e, fit_g, E, elite);
+  if (launch_pdl(k_elite_pick, dim3(p.B * p.mu), dim3(32), 0, s, p, fit_e, fit_g, E, elite) != cudaSuccess) return -1;
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 int launch_rank(const Problem& p, const float* fit_e, int32_t* top, int32_t* bottom, cudaStream_t s) {
   const int threads = p.g >= 256 ? 256 : ((p.g + 31) / 32) * 32;
   const size_t smem = (size_t)p.g * (sizeof(float) + sizeof(int));
-  k_rank<<<p.B * p.mu * p.m, threads, smem, s>>>(p, fit_e, top, bottom);
+  if (launch_pdl(k_rank, dim3(p.B * p.mu * p.m), dim3(threads), smem, s, p, fit_e, top, bottom) != cudaSuccess)
+    return -1;
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 int launch_select(const Problem& p, const float* fit_e, const float* fit_g, const float* sparks,
                   const float* guides, float* fw_x, float* fw_amp, float* fw_f, int32_t* winner, float* best_x,
                   float* best_f, uint32_t* gens_done, cudaStream_t s) {
-  k_select<<<p.B * p.mu, kSelThreads, 0, s>>>(p, fit_e, fit_g, sparks, guides, fw_x, fw_amp, fw_f, winner);
+  if (launch_pdl(k_select, dim3(p.B * p.mu), dim3(kSelThreads), 0, s, p, fit_e, fit_g, sparks, guides, fw_x, fw_amp,
+                 fw_f, winner) != cudaSuccess)
+    return -1;
   if (cudaPeekAtLastError() != cudaSuccess) return -1;
-  k_run_best<<<p.B, kSelThreads, 0, s>>>(p, 0, fw_x, fw_f, best_x, best_f, gens_done);
+  if (launch_pdl(k_run_best, dim3(p.B), dim3(kSelThreads), 0, s, p, 0, (const float*)fw_x, (const float*)fw_f,
+                 best_x, best_f, gens_done) != cudaSuccess)
+    return -1;
   return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;
 }
 

@@ -65,6 +65,8 @@ __device__ __forceinline__ void store_op4(const OpDesc& op, int64_t row, int64_t
 // grid (coordinate blocks, B * mu): global firework z = b * mu + i.
 __global__ void __launch_bounds__(kThreads) k_init(Problem p, float* __restrict__ fw_x,
                                                    float* __restrict__ fw_amp) {
+  griddep_wait();
+  griddep_launch_dependents();
   const int z = blockIdx.y;
   const int b = z / p.mu, i = z - b * p.mu;
   const int64_t c4 = (int64_t)blockIdx.x * kThreads + threadIdx.x;
@@ -130,6 +132,8 @@ __global__ void __launch_bounds__(kThreads) k_explode(Problem p, const uint32_t*
                                                       const float* __restrict__ fw_x,
                                                       const float* __restrict__ fw_amp,
                                                       float* __restrict__ sparks, const OpDesc op) {
+  griddep_wait();
+  griddep_launch_dependents();
   const uint32_t gen = *gens_done + 1u;  // this generation (the counter is advanced by the selection)
   const uint32_t z = blockIdx.z;
   const uint32_t b = z / (uint32_t)p.mu, i = z - b * (uint32_t)p.mu;
@@ -165,6 +169,8 @@ __global__ void __launch_bounds__(kThreads) k_guide(Problem p, const uint32_t* _
                                                     const int32_t* __restrict__ top,
                                                     const int32_t* __restrict__ bottom,
                                                     float* __restrict__ guides, const OpDesc op) {
+  griddep_wait();
+  griddep_launch_dependents();
   const uint32_t gen = *gens_done + 1u;
   const int i = blockIdx.z;               // global firework z = b * mu + i_local
   const int gq = i * p.m + blockIdx.y;    // global guiding row z * m + q
@@ -234,6 +240,8 @@ __global__ void __launch_bounds__(kThreads) k_guide(Problem p, const uint32_t* _
 }
 
 __global__ void k_to_operand(const float* __restrict__ rows, int64_t ld, const OpDesc op) {
+  griddep_wait();
+  griddep_launch_dependents();
   const int row = blockIdx.y;
   const int64_t d0 = ((int64_t)blockIdx.x * kThreads + threadIdx.x) * 4;
   if (d0 >= op.w1_elems) return;
@@ -242,6 +250,8 @@ __global__ void k_to_operand(const float* __restrict__ rows, int64_t ld, const O
 }
 
 __global__ void k_f32_to_op(const float* __restrict__ src, int64_t n, int32_t kind, float inv, void* dst) {
+  griddep_wait();
+  griddep_launch_dependents();
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     if (kind == kOpFp8)
       static_cast<uint8_t*>(dst)[e] = (uint8_t)__nv_cvt_float_to_fp8(src[e] * inv, __NV_SATFINITE, __NV_E4M3);
@@ -263,22 +273,26 @@ int launch_init(const Problem& p, float* fw_x, float* fw_amp, cudaStream_t s) {
 int launch_explode(const Problem& p, const uint32_t* gens_done, const float* fw_x, const float* fw_amp, float* sparks,
                    const OpDesc& op, cudaStream_t s) {
   dim3 grid((unsigned)((p.Dp / 4 + 2 * kThreads - 1) / (2 * kThreads)), p.lam, p.B * p.mu);
-  k_explode<<<grid, kThreads, 0, s>>>(p, gens_done, fw_x, fw_amp, sparks, op);
-  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+  return launch_pdl(k_explode, grid, dim3(kThreads), 0, s, p, gens_done, fw_x, fw_amp, sparks, op) == cudaSuccess
+             ? 1
+             : -1;
 }
 
 int launch_guide(const Problem& p, const uint32_t* gens_done, const float* fw_x, const float* fw_amp, const float* sparks,
                  const int32_t* top, const int32_t* bottom, float* guides, const OpDesc& op_guides,
                  cudaStream_t s) {
   dim3 grid(blocks_for(p.Dp / 4), p.m, p.B * p.mu);
+  cudaError_t e;
   switch (p.k) {
 #define MG_GUIDE_K(K) \
-  case K: k_guide<K><<<grid, kThreads, 0, s>>>(p, gens_done, fw_x, fw_amp, sparks, top, bottom, guides, op_guides); break;
+  case K: e = launch_pdl(k_guide<K>, grid, dim3(kThreads), 0, s, p, gens_done, fw_x, fw_amp, sparks, top, bottom, \
+                         guides, op_guides); break;
     MG_GUIDE_K(1) MG_GUIDE_K(2) MG_GUIDE_K(3) MG_GUIDE_K(4) MG_GUIDE_K(5) MG_GUIDE_K(6) MG_GUIDE_K(7) MG_GUIDE_K(8)
 #undef MG_GUIDE_K
-    default: k_guide<0><<<grid, kThreads, 0, s>>>(p, gens_done, fw_x, fw_amp, sparks, top, bottom, guides, op_guides);
+    default: e = launch_pdl(k_guide<0>, grid, dim3(kThreads), 0, s, p, gens_done, fw_x, fw_amp, sparks, top, bottom,
+                            guides, op_guides);
   }
-  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+  return e == cudaSuccess ? 1 : -1;
 }
 
 int launch_to_operand(const float* rows, int64_t ld, int32_t count, const OpDesc& op, cudaStream_t s) {

@@ -76,9 +76,11 @@ struct mgfwa_handle {
   int32_t* rflags = nullptr;  // [B] refinement decisions
   float* gscratch = nullptr;  // backpropagation scratch (GradPlan)
   cudaGraphExec_t refine_exec = nullptr;  // the refinement's kernels, captured once
-  bool capturing = false;                 // a group is capturing this handle's generation: no host counters
+  bool capturing = false;                 // a graph (its own or a group's) is capturing a generation: no host counters
   bool grouped = false;                   // member of a group
   int64_t refine_kernels = 0;             // kernels in that graph
+  cudaGraphExec_t gen_exec = nullptr;     // one generation (explode .. select), captured at the first step
+  int64_t gen_kernels = 0;                // kernels in that graph
   bool want_op = false; // tensor-core path: operand copies of X and of the first-layer weights
   int64_t P = 0;       // sparks per generation of one run
   int64_t PA = 0;      // sparks per generation of all runs (rows of the spark buffers)
@@ -342,12 +344,56 @@ mgfwa_status run_phase(mgfwa_t* h, int32_t phase) {
   return fail(h, MGFWA_EINVAL, "unknown phase %d", phase);
 }
 
+// Capture the phases explode .. select into h->gen_exec, on a private stream
+// swapped in for the handle's (so the caller's stream is never in capture
+// mode).  Nothing in them depends on the host's generation counter: the
+// kernels read the generation from the device.
+mgfwa_status capture_generation(mgfwa_t* h) {
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return cuda_fail(h, "capture stream");
+  cudaStream_t own = h->stream;
+  const int64_t before = h->launches;
+  cudaGraph_t graph = nullptr;
+  mgfwa_status st = MGFWA_OK;
+  bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    h->stream = cs;
+    h->capturing = true;
+    for (int32_t ph = MGFWA_PHASE_EXPLODE; ph <= MGFWA_PHASE_SELECT && st == MGFWA_OK; ++ph) st = run_phase(h, ph);
+    h->capturing = false;
+    h->stream = own;
+    ok = cudaStreamEndCapture(cs, &graph) == cudaSuccess && st == MGFWA_OK;
+  }
+  h->gen_kernels = h->launches - before;
+  h->launches = before;
+  if (!ok || !graph || cudaGraphInstantiate(&h->gen_exec, graph, 0) != cudaSuccess) {
+    h->gen_exec = nullptr;
+    if (st == MGFWA_OK) st = cuda_fail(h, "generation graph capture");
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  return st;
+}
+
+// One generation: explode .. select as one graph launch (direct launches
+// while kernel groups are being timed), then the refinement when due.
 mgfwa_status one_generation(mgfwa_t* h) {
-  for (int32_t ph = MGFWA_PHASE_EXPLODE; ph <= MGFWA_PHASE_REFINE; ++ph) {
-    mgfwa_status st = run_phase(h, ph);
+  if (h->profiling) {
+    for (int32_t ph = MGFWA_PHASE_EXPLODE; ph <= MGFWA_PHASE_REFINE; ++ph) {
+      mgfwa_status st = run_phase(h, ph);
+      if (st != MGFWA_OK) return st;
+    }
+    return MGFWA_OK;
+  }
+  if (!h->gen_exec) {
+    mgfwa_status st = capture_generation(h);
     if (st != MGFWA_OK) return st;
   }
-  return MGFWA_OK;
+  h->gen += 1;
+  if (cudaGraphLaunch(h->gen_exec, h->stream) != cudaSuccess) return cuda_fail(h, "generation graph launch");
+  h->launches += h->gen_kernels;
+  h->evals += h->P;
+  return run_phase(h, MGFWA_PHASE_REFINE);
 }
 
 // The next generation fits: its sparks and, if due, its refinement.
@@ -981,6 +1027,7 @@ void mgfwa_destroy(mgfwa_t* h) {
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   tc_release(h->tc);
   if (h->refine_exec) cudaGraphExecDestroy(h->refine_exec);
+  if (h->gen_exec) cudaGraphExecDestroy(h->gen_exec);
   arena_free(h);
   if (h->stream) cudaStreamSynchronize(h->stream);  // the pool's free completes in stream order
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);

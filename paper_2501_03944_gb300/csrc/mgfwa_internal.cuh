@@ -65,6 +65,36 @@ struct OpDesc {
   }
 };
 
+// Programmatic dependent launch.  A kernel started by launch_pdl may be
+// scheduled while its predecessor on the stream is still running, so every
+// kernel of the library begins with griddep_wait(), which returns once the
+// predecessor grid has completed and its memory writes are visible (at once
+// when the launch was an ordinary one), and then calls
+// griddep_launch_dependents(), which lets the next such launch be scheduled
+// as soon as every CTA of this grid has started.  What overlaps is the next
+// kernel's launch and CTA dispatch with this kernel's last wave, never its
+// memory accesses.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Raise kernel K's dynamic shared-memory limit on the current device once.
 // The attribute belongs to one kernel on one device, so the cache is per
 // kernel (one template instance per kernel, not per kernel type) and per
