@@ -93,11 +93,11 @@ __device__ __forceinline__ float signed_u24(uint32_t r) {
 
 // Coordinates [d0, d0 + 4) of explosion spark `row` (one Philox block);
 // `full` when all four coordinates are < D.
-__device__ __forceinline__ void explode4(const Problem& p, uint32_t gen, uint32_t unit, uint32_t k0, uint32_t k1,
+__device__ __forceinline__ void explode4(const Problem& p, uint32_t gen, uint32_t unit, const PhiloxKeys& rk,
                                          uint32_t c4, const float4 x4, float amp, float* __restrict__ srow,
                                          const OpDesc& op, uint32_t row, bool full) {
   const uint32_t d0 = c4 * 4u;
-  const uint4 r = philox4x32_10(make_uint4(c4, unit, gen, kExplode), k0, k1);
+  const uint4 r = philox4x32_10(make_uint4(c4, unit, gen, kExplode), rk);
   float v[4];
 #pragma unroll
   for (int l = 0; l < 4; ++l) v[l] = __fmaf_rn(amp, signed_u24(lane_of(r, l)), lane_of(x4, l));
@@ -109,7 +109,7 @@ __device__ __forceinline__ void explode4(const Problem& p, uint32_t gen, uint32_
     any |= oob[l];
   }
   if (any) {
-    const uint4 r2 = philox4x32_10(make_uint4(c4, unit, gen, kMap), k0, k1);
+    const uint4 r2 = philox4x32_10(make_uint4(c4, unit, gen, kMap), rk);
 #pragma unroll
     for (int l = 0; l < 4; ++l)
       if (oob[l]) v[l] = map_coord(lane_of(x4, l), amp, p.lb, p.ub, u24(lane_of(r2, l)));
@@ -141,18 +141,19 @@ __global__ void __launch_bounds__(kThreads) k_explode(Problem p, const uint32_t*
   const uint32_t unit = i * (uint32_t)p.lam + blockIdx.y;
   uint32_t k0, k1;
   run_key(p, (int)b, k0, k1);
+  const PhiloxKeys rk = philox_keys(k0, k1);  // shared by the thread's (up to four) Philox blocks
   const float amp = fw_amp[z];
   const float* xrow = fw_x + (int64_t)z * p.Dp;
   float* srow = sparks + (int64_t)row * p.Dp;
   const uint32_t n4 = (uint32_t)(p.Dp / 4);
   const uint32_t full4 = (uint32_t)(p.D / 4);  // blocks whose 4 coordinates are all < D
-  const uint32_t c4a = blockIdx.x * (2 * kThreads) + threadIdx.x;
-  const uint32_t c4b = c4a + kThreads;
-  float4 xa = make_float4(0.f, 0.f, 0.f, 0.f), xb = xa;
-  if (c4a < n4) xa = *reinterpret_cast<const float4*>(xrow + (size_t)c4a * 4);
-  if (c4b < n4) xb = *reinterpret_cast<const float4*>(xrow + (size_t)c4b * 4);
-  if (c4a < n4) explode4(p, gen, unit, k0, k1, c4a, xa, amp, srow, op, row, c4a < full4);
-  if (c4b < n4) explode4(p, gen, unit, k0, k1, c4b, xb, amp, srow, op, row, c4b < full4);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const uint32_t c4 = blockIdx.x * (2 * kThreads) + (uint32_t)h * kThreads + threadIdx.x;
+    if (c4 >= n4) continue;
+    const float4 x4 = *reinterpret_cast<const float4*>(xrow + (size_t)c4 * 4);
+    explode4(p, gen, unit, rk, c4, x4, amp, srow, op, row, c4 < full4);
+  }
 }
 
 // Multi-guiding sparks, reading: group q of firework i has ranked index

@@ -135,6 +135,31 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
+// The ten round keys of one Philox key, for a thread that draws several
+// blocks under the same key (the same values the loop above steps through).
+struct PhiloxKeys {
+  uint32_t k0[10], k1[10];
+};
+__device__ __forceinline__ PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
+  PhiloxKeys rk;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    rk.k0[r] = k0 + (uint32_t)r * 0x9E3779B9u;
+    rk.k1[r] = k1 + (uint32_t)r * 0xBB67AE85u;
+  }
+  return rk;
+}
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys& rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = mul_wide_u32(0xD2511F53u, c.x);
+    const uint64_t p1 = mul_wide_u32(0xCD9E8D57u, c.z);
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk.k0[r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ rk.k1[r],
+                   (uint32_t)p0);
+  }
+  return c;
+}
+
 // Uniform on the 2^-24 grid of [0, 1).
 __device__ __forceinline__ float u24(uint32_t r) { return __uint2float_rn(r >> 8) * 0x1p-24f; }
 
