@@ -51,64 +51,112 @@ __device__ __forceinline__ void take_if_before(float& bf, int& bc, float of, int
   }
 }
 
-// One block per firework (of all runs): argmin over its lam explosion and m guiding
-// sparks (candidate order: explosion 0..lam-1, guiding 0..m-1), the strict
-// improvement test, the dynamic amplitude update (x C_a on improvement,
-// x C_r otherwise), and the copy of the winning row into the firework.
-__global__ void __launch_bounds__(kSelThreads) k_select(Problem p, const float* __restrict__ fit_e,
-                                                        const float* __restrict__ fit_g,
-                                                        const float* __restrict__ sparks,
-                                                        const float* __restrict__ guides,
-                                                        float* __restrict__ fw_x, float* __restrict__ fw_amp,
-                                                        float* __restrict__ fw_f, int32_t* __restrict__ winner) {
+// Selection decisions, one block per run and one warp per firework of the
+// run (fireworks in turn when mu exceeds the warps): argmin over the
+// firework's lam explosion and m guiding sparks (candidate order: explosion
+// 0..lam-1, guiding 0..m-1), the strict improvement test and the dynamic
+// amplitude update (x C_a on improvement, x C_r otherwise); winner[z] is
+// the winning candidate or -1.  Then the run's best-so-far: strict
+// improvement over its new fireworks in index order; winner[B*mu + b] is
+// that firework or -1.  k_select_copy moves the rows.
+__global__ void __launch_bounds__(kSelThreads) k_select_decide(Problem p, const float* __restrict__ fit_e,
+                                                               const float* __restrict__ fit_g,
+                                                               float* __restrict__ fw_amp, float* __restrict__ fw_f,
+                                                               int32_t* __restrict__ winner,
+                                                               float* __restrict__ best_f,
+                                                               uint32_t* __restrict__ gens_done) {
   griddep_wait();
   griddep_launch_dependents();
-  __shared__ float wf[kSelThreads / 32];
-  __shared__ int wc[kSelThreads / 32];
-  __shared__ int s_win;
-  const int i = blockIdx.x;
-  const int n_cand = p.lam + p.m;
-  float bf = 0.0f;
-  int bc = -1;
-  for (int c = threadIdx.x; c < n_cand; c += blockDim.x) {
-    const float f = c < p.lam ? fit_e[(int64_t)i * p.lam + c] : fit_g[(int64_t)i * p.m + (c - p.lam)];
-    take_if_before(bf, bc, f, c);
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    const float of = __shfl_xor_sync(0xffffffffu, bf, off);
-    const int oc = __shfl_xor_sync(0xffffffffu, bc, off);
-    take_if_before(bf, bc, of, oc);
-  }
+  const int b = blockIdx.x;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  if (lane == 0) {
-    wf[warp] = bf;
-    wc[warp] = bc;
+  const int n_cand = p.lam + p.m;
+  for (int il = warp; il < p.mu; il += kSelThreads / 32) {
+    const int i = b * p.mu + il;  // global firework
+    float bf = 0.0f;
+    int bc = -1;
+    for (int c = lane; c < n_cand; c += 32) {
+      const float f = c < p.lam ? fit_e[(int64_t)i * p.lam + c] : fit_g[(int64_t)i * p.m + (c - p.lam)];
+      take_if_before(bf, bc, f, c);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float of = __shfl_xor_sync(0xffffffffu, bf, off);
+      const int oc = __shfl_xor_sync(0xffffffffu, bc, off);
+      take_if_before(bf, bc, of, oc);
+    }
+    if (lane == 0) {
+      const float amp = fw_amp[i];
+      if (rank_key(bf) < rank_key(fw_f[i])) {
+        fw_f[i] = bf;
+        fw_amp[i] = __fmul_rn(amp, p.c_a);
+        winner[i] = bc;
+      } else {
+        fw_amp[i] = __fmul_rn(amp, p.c_r);
+        winner[i] = -1;
+      }
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    float f = wf[0];
-    int c = wc[0];
-    for (int w = 1; w < kSelThreads / 32; ++w) take_if_before(f, c, wf[w], wc[w]);
-    const float amp = fw_amp[i];
-    if (rank_key(f) < rank_key(fw_f[i])) {
-      fw_f[i] = f;
-      fw_amp[i] = __fmul_rn(amp, p.c_a);
-      s_win = c;
-    } else {
-      fw_amp[i] = __fmul_rn(amp, p.c_r);
-      s_win = -1;
+    const float* f = fw_f + (int64_t)b * p.mu;
+    int bi = -1;
+    float bfv = best_f[b];
+    for (int i = 0; i < p.mu; ++i) {
+      if (rank_key(f[i]) < rank_key(bfv)) {
+        bfv = f[i];
+        bi = i;
+      }
     }
-    winner[i] = s_win;
+    if (bi >= 0) best_f[b] = bfv;
+    winner[(int64_t)p.B * p.mu + b] = bi;
+    if (gens_done && b == 0) *gens_done += 1u;  // the generation is complete
   }
-  __syncthreads();
-  const int c = s_win;
-  if (c < 0) return;
-  const float* src = c < p.lam ? sparks + ((int64_t)i * p.lam + c) * p.Dp
-                               : guides + ((int64_t)i * p.m + (c - p.lam)) * p.Dp;
-  float4* dst = reinterpret_cast<float4*>(fw_x + (int64_t)i * p.Dp);
+}
+
+// Blocks per row copy: about 1 KB of the row per thread block, at most 64.
+__host__ __device__ inline int copy_blocks(int64_t Dp) {
+  const int64_t b = (Dp / 4 + 255) / 256;
+  return (int)(b < 1 ? 1 : (b > 64 ? 64 : b));
+}
+
+// The rows of the selection, grid (row chunks, B*mu + B): row y < B*mu is
+// firework y's winning candidate copied into fw_x (when one won); row
+// B*mu + b is run b's best firework copied into best_x, read from where
+// that firework's new position comes from (its winning candidate, or its
+// own row, which no block writes then).
+__global__ void __launch_bounds__(256) k_select_copy(Problem p, const float* __restrict__ sparks,
+                                                     const float* __restrict__ guides, float* __restrict__ fw_x,
+                                                     const int32_t* __restrict__ winner,
+                                                     float* __restrict__ best_x) {
+  griddep_wait();
+  griddep_launch_dependents();
+  const int nz = p.B * p.mu;
+  const int y = blockIdx.y;
+  int z, c;
+  float* dst;
+  if (y < nz) {
+    z = y;
+    c = winner[z];
+    if (c < 0) return;
+    dst = fw_x + (int64_t)z * p.Dp;
+  } else {
+    const int b = y - nz;
+    const int bi = winner[nz + b];
+    if (bi < 0) return;
+    z = b * p.mu + bi;
+    c = winner[z];
+    dst = best_x + (int64_t)b * p.Dp;
+  }
+  const float* src = c < 0 ? fw_x + (int64_t)z * p.Dp
+                     : c < p.lam ? sparks + ((int64_t)z * p.lam + c) * p.Dp
+                                 : guides + ((int64_t)z * p.m + (c - p.lam)) * p.Dp;
+  const int64_t n4 = p.Dp / 4;
+  const int64_t chunk = (n4 + gridDim.x - 1) / gridDim.x;
+  const int64_t e0 = (int64_t)blockIdx.x * chunk;
+  const int64_t e1 = e0 + chunk < n4 ? e0 + chunk : n4;
   const float4* s4 = reinterpret_cast<const float4*>(src);
-  for (int64_t e = threadIdx.x; e < p.Dp / 4; e += blockDim.x) dst[e] = s4[e];
+  float4* d4 = reinterpret_cast<float4*>(dst);
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) d4[e] = s4[e];
 }
 
 // Each run's best-so-far (one block per run): strict improvement over its
@@ -201,12 +249,11 @@ int launch_rank(const Problem& p, const float* fit_e, int32_t* top, int32_t* bot
 int launch_select(const Problem& p, const float* fit_e, const float* fit_g, const float* sparks,
                   const float* guides, float* fw_x, float* fw_amp, float* fw_f, int32_t* winner, float* best_x,
                   float* best_f, uint32_t* gens_done, cudaStream_t s) {
-  if (launch_pdl(k_select, dim3(p.B * p.mu), dim3(kSelThreads), 0, s, p, fit_e, fit_g, sparks, guides, fw_x, fw_amp,
-                 fw_f, winner) != cudaSuccess)
+  if (launch_pdl(k_select_decide, dim3(p.B), dim3(kSelThreads), 0, s, p, fit_e, fit_g, fw_amp, fw_f, winner, best_f,
+                 gens_done) != cudaSuccess)
     return -1;
-  if (cudaPeekAtLastError() != cudaSuccess) return -1;
-  if (launch_pdl(k_run_best, dim3(p.B), dim3(kSelThreads), 0, s, p, 0, (const float*)fw_x, (const float*)fw_f,
-                 best_x, best_f, gens_done) != cudaSuccess)
+  if (launch_pdl(k_select_copy, dim3(copy_blocks(p.Dp), p.B * p.mu + p.B), dim3(256), 0, s, p, sparks, guides, fw_x,
+                 (const int32_t*)winner, best_x) != cudaSuccess)
     return -1;
   return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;
 }

@@ -435,8 +435,8 @@ mgfwa_status validate(const mgfwa_config* c, const mgfwa_objective* o) {
   if (c->elite_rescore < 0 || c->elite_rescore > 8 ||
       c->elite_rescore > c->sparks_per_firework + c->guiding_per_firework)
     return fail(nullptr, MGFWA_EINVAL, "elite_rescore must be in [0, min(8, lambda + m)]");
-  if ((int64_t)c->n_runs * c->n_fireworks > 65535 || c->sparks_per_firework > 65535)
-    return fail(nullptr, MGFWA_EINVAL, "n_runs * mu and lambda must each be <= 65535");
+  if ((int64_t)c->n_runs * (c->n_fireworks + 1) > 65535 || c->sparks_per_firework > 65535)
+    return fail(nullptr, MGFWA_EINVAL, "n_runs * (mu + 1) and lambda must each be <= 65535");
   const int64_t PA = (int64_t)c->n_runs * c->n_fireworks * (c->sparks_per_firework + c->guiding_per_firework);
   if (PA > (1 << 24)) return fail(nullptr, MGFWA_EINVAL, "n_runs mu (lambda + m) = %lld exceeds 2^24", (long long)PA);
   if (!(c->sigma > 0.0f) || !(c->sigma <= 0.5f)) return fail(nullptr, MGFWA_EINVAL, "sigma must be in (0, 0.5]");
@@ -665,7 +665,7 @@ size_t carve_all(mgfwa_t* h, char* base) {
   h->partial = carve<float>(cur, (size_t)h->mtiles * h->PA);
   h->top = carve<int32_t>(cur, F * p.m * p.k);
   h->bottom = carve<int32_t>(cur, F * p.m * p.k);
-  h->winner = carve<int32_t>(cur, F);
+  h->winner = carve<int32_t>(cur, F + p.B);  // per firework, then per run (the selection's decisions)
   h->elite = carve<int32_t>(cur, F * (cfg->elite_rescore > 0 ? cfg->elite_rescore : 1));
   const bool rescore = want_op && cfg->elite_rescore > 0;
   h->rescore_scratch = rescore ? carve<float>(cur, (size_t)h->rescore_plan.floats) : nullptr;

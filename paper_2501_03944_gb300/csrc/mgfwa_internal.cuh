@@ -206,7 +206,11 @@ int launch_guide(const Problem& p, const uint32_t* gens_done, const float* fw_x,
 int launch_run_best_init(const Problem& p, const float* fw_x, const float* fw_f, float* best_x, float* best_f,
                          cudaStream_t s);
 
-// ... and advances gens_done[0] by one (the generation is complete).
+// Selection of every firework (winner[z]: its winning candidate or -1) and
+// each run's best-so-far (winner[B*mu + b]: the run's improving firework or
+// -1; winner holds B*mu + B entries), then the copies of the winning rows
+// into fw_x and best_x; advances gens_done[0] by one (the generation is
+// complete).
 int launch_select(const Problem& p, const float* fit_e, const float* fit_g, const float* sparks,
                   const float* guides, float* fw_x, float* fw_amp, float* fw_f, int32_t* winner,
                   float* best_x, float* best_f, uint32_t* gens_done, cudaStream_t s);
