@@ -197,8 +197,14 @@ struct Args {
   const float* rows;
   const int32_t* idx;  // vector r is spark row idx[r] (or r)
   int32_t R;        // vectors
-  float* out;       // [R][N][H]
+  float* out;       // [R][N][H] (unless the output layer is fused)
   uint32_t* status;
+  // fused output layer (two-layer nets, objective only): loss[r][n] from the
+  // logits W2 a + b2 of the vector's row, instead of the activations
+  float* loss;      // [R][N], or null
+  int64_t w2_off, b2_off;
+  int32_t C;
+  const int32_t* y;
 };
 
 // Each CTA takes V = 128 / H vectors, so that every MMA is M=128, N=128:
@@ -208,6 +214,7 @@ struct Args {
 // stacked W1 tiles (128 rows).  TMEM: the accumulators (main even, main odd,
 // corrections: 3 x 128 columns) and then the X slots, 3 parts x 16 columns.
 constexpr int kN = 128;
+constexpr int kMaxC = 32;           // classes of a fused output layer
 constexpr int kStages = 3;
 constexpr int kSlots = 2;
 constexpr uint32_t kABytes = kBM * 128;
@@ -218,7 +225,8 @@ static_assert(kSlot0 + kSlots * kSlotCols <= kTmemCols, "accumulators and X slot
 static_assert(kStages <= kMaxStages && kSlots <= kMaxSlots, "barrier arrays");
 static_assert(kBKf == 2 * kSlotK, "two slots per stage");
 
-template <int H>
+// NL: register slots for the logits of a fused output layer (C <= NL).
+template <int H, int NL>
 __global__ void __launch_bounds__(kThreads, 1)
     k_l1_fp32x3(const __grid_constant__ CUtensorMap tmap_x, const __grid_constant__ CUtensorMap tmap_w, Args a) {
   griddep_wait();
@@ -231,6 +239,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto A = [&](int s) { return base + (size_t)s * kABytes; };
   auto Bp = [&](int p, int s) { return b_part + ((size_t)p * kStages + s) * kBBytes; };
   Bars* sb = reinterpret_cast<Bars*>(b_part + (size_t)kParts * kStages * kBBytes);
+  float* w2s = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(sb) + ((sizeof(Bars) + 15) & ~size_t(15)));
+  float* b2s = w2s + (size_t)V * kMaxC * H;  // fused output layer: W2 [V][C][H], b2 [V][C] of the CTA's vectors
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int mt = blockIdx.x, r0 = blockIdx.y * V;
@@ -327,6 +337,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3;            // TMEM lane quadrant this warp may access
     const int rrow = q * 32 + lane;    // this thread's sample row of the tile = its TMEM lane
     const uint32_t lanes = tmem + ((uint32_t)(q * 32) << 16);
+    const bool fused = a.loss != nullptr;
+    if (fused) {
+      // W2 and b2 of the CTA's vectors, read by the epilogue below (ordered by the named barrier there)
+      for (int e = ct; e < V * a.C * H; e += 128) {
+        const int v = e / (a.C * H), rem = e - v * (a.C * H);
+        w2s[e] = a.rows[(int64_t)row_of(v) * a.ld + a.w2_off + rem];
+      }
+      for (int e = ct; e < V * a.C; e += 128) {
+        const int v = e / a.C;
+        b2s[e] = a.rows[(int64_t)row_of(v) * a.ld + a.b2_off + (e - v * a.C)];
+      }
+    }
     bool ok = true;
     for (int kb = 0; kb < a.k_blocks && ok; ++kb) {
       const int s = kb % kStages;
@@ -372,8 +394,58 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int64_t n = (int64_t)mt * kBM + rrow;
     const bool valid = ok && !sb->abort_flag && n < a.N;
     const bool odd = a.k_blocks > 1;  // the odd-block accumulator holds products
+    if (fused) {
+      asm volatile("bar.sync 1, 128;" ::: "memory");  // W2, b2 staged by all four warps
+      const int yn = valid ? a.y[n] : 0;
 #pragma unroll 1
-    for (int v = 0; v < V; ++v) {
+      for (int v = 0; v < V; ++v) {
+        const float* bias = a.rows + (int64_t)row_of(v) * a.ld + a.b1_off;
+        const float* w2 = w2s + (size_t)v * a.C * H;
+        // logits in the order of the CUDA-core output layer: z_c = b2_c, then fma over j ascending
+        float z[NL];
+#pragma unroll
+        for (int c = 0; c < NL; ++c) z[c] = c < a.C ? b2s[v * a.C + c] : 0.f;
+#pragma unroll 1
+        for (int j0 = 0; j0 < H; j0 += 8) {
+          const uint32_t col = (uint32_t)(v * H + j0);
+          float x[8], x1[8], xc[8];
+          tmem_ld8(lanes + col, x);
+          tmem_ld8(lanes + (uint32_t)kN + col, x1);
+          tmem_ld8(lanes + (uint32_t)(2 * kN) + col, xc);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float zz = ((odd ? x[i] + x1[i] : x[i]) + xc[i]) + bias[j0 + i];
+            x[i] = a.act == kActTanh ? tanhf(zz) : fmaxf(zz, 0.f);
+          }
+#pragma unroll
+          for (int c = 0; c < NL; ++c) {
+            if (c < a.C) {
+              const float* wc = w2 + (size_t)c * H + j0;
+#pragma unroll
+              for (int i = 0; i < 8; ++i) z[c] = fmaf(x[i], wc[i], z[c]);
+            }
+          }
+        }
+        if (valid && r0 + v < a.R) {
+          float zmax = z[0];
+#pragma unroll
+          for (int c = 1; c < NL; ++c)
+            if (c < a.C) zmax = fmaxf(zmax, z[c]);
+          float se = 0.f, zy = 0.f;
+#pragma unroll
+          for (int c = 0; c < NL; ++c) {
+            if (c < a.C) {
+              se += expf(z[c] - zmax);
+              if (c == yn) zy = z[c];
+            }
+          }
+          a.loss[(int64_t)(r0 + v) * a.N + n] = (zmax + logf(se)) - zy;
+        }
+      }
+    }
+#pragma unroll 1
+    for (int v = 0; v < (fused ? 0 : V); ++v) {
       const bool store = valid && r0 + v < a.R;
       const float* bias = a.rows + (int64_t)row_of(v) * a.ld + a.b1_off;
       float* out = a.out + ((int64_t)(r0 + v) * a.N + n) * H;
@@ -437,15 +509,27 @@ bool encode(CUtensorMap* map, uint32_t rank, const void* ptr, const cuuint64_t* 
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t smem_bytes() { return 1024 + (size_t)kStages * (kABytes + (size_t)kParts * kBBytes) + sizeof(Bars) + 64; }
+size_t smem_bytes() {
+  return 1024 + (size_t)kStages * (kABytes + (size_t)kParts * kBBytes) + ((sizeof(Bars) + 15) & ~size_t(15)) +
+         sizeof(float) * ((size_t)kN * kMaxC + (size_t)kN / 32 * kMaxC) + 64;
+}
 
-template <int H>
-cudaError_t go(const L1Plan& pl, const Args& a, int R, cudaStream_t s, bool prep) {
-  cudaError_t e = ensure_smem_limit<k_l1_fp32x3<H>>(smem_bytes());
+template <int H, int NL>
+cudaError_t go_nl(const L1Plan& pl, const Args& a, int R, cudaStream_t s, bool prep) {
+  cudaError_t e = ensure_smem_limit<k_l1_fp32x3<H, NL>>(smem_bytes());
   if (e != cudaSuccess || prep) return e;
   constexpr int V = kN / H;
   const dim3 grid((unsigned)((a.N + kBM - 1) / kBM), (unsigned)((R + V - 1) / V));
-  return launch_pdl(k_l1_fp32x3<H>, grid, dim3(kThreads), smem_bytes(), s, pl.tmap_x, pl.tmap_w, a);
+  return launch_pdl(k_l1_fp32x3<H, NL>, grid, dim3(kThreads), smem_bytes(), s, pl.tmap_x, pl.tmap_w, a);
+}
+
+template <int H>
+cudaError_t go(const L1Plan& pl, const Args& a, int R, cudaStream_t s, bool prep) {
+  if (prep) {
+    const cudaError_t e = go_nl<H, 16>(pl, a, R, s, true);
+    return e != cudaSuccess ? e : go_nl<H, 32>(pl, a, R, s, true);
+  }
+  return a.loss && a.C > 16 ? go_nl<H, 32>(pl, a, R, s, false) : go_nl<H, 16>(pl, a, R, s, false);
 }
 
 }  // namespace
@@ -492,8 +576,10 @@ bool l1_fp32x3_plan(L1Plan& pl, const Mlp& mlp, const float* rows, int64_t ld, i
   return pl.ready;
 }
 
+bool l1_fp32x3_fuses_output(const Mlp& mlp) { return mlp.n_layers == 2 && mlp.widths[2] <= kMaxC; }
+
 int launch_l1_fp32x3(const L1Plan& pl, const Mlp& mlp, const int32_t* idx, int32_t R, float* out,
-                     uint32_t* status, cudaStream_t s) {
+                     uint32_t* status, cudaStream_t s, float* loss) {
   if (!pl.ready || R <= 0) return R <= 0 ? 0 : -1;
   Args a;
   a.N = (int32_t)mlp.N;
@@ -507,6 +593,15 @@ int launch_l1_fp32x3(const L1Plan& pl, const Mlp& mlp, const int32_t* idx, int32
   a.R = R;
   a.out = out;
   a.status = status;
+  a.loss = nullptr;
+  if (loss) {
+    if (!l1_fp32x3_fuses_output(mlp)) return -1;
+    a.loss = loss;
+    a.w2_off = mlp.w_off[1];
+    a.b2_off = mlp.b_off[1];
+    a.C = mlp.widths[2];
+    a.y = mlp.y;
+  }
   cudaError_t e;
   switch (mlp.widths[1]) {
     case 32: e = go<32>(pl, a, R, s, false); break;

@@ -720,12 +720,15 @@ int launch_grad(const GradPlan& gp, const Mlp& mlp, const float* W, int64_t ld, 
   Enq q{s, gp.num_sms};
   int gi = 0;
   // hidden layers: Z_l = A_{l-1} W_l^T, then bias and activation
+  // objective only on a two-layer net with the tensor-core first layer: the output layer and the
+  // per-sample losses come out of that kernel's epilogue
+  const bool fused_out = !want_grad && status && l1_on_tensor_cores(gp, mlp, l1) && l1_fp32x3_fuses_output(mlp);
   for (int l = 1; l < L; ++l) {
     const int64_t fi = mlp.widths[l - 1];
     if (l == 1 && status && l1_on_tensor_cores(gp, mlp, l1)) {
       // the first layer on the tensor cores at FP32 accuracy
       ++gi;
-      const int k = launch_l1_fp32x3(*l1, mlp, idx, R, act(1), status, s);
+      const int k = launch_l1_fp32x3(*l1, mlp, idx, R, act(1), status, s, fused_out ? loss : nullptr);
       if (k < 0) return -1;
       q.n += k;
       continue;
@@ -757,7 +760,7 @@ int launch_grad(const GradPlan& gp, const Mlp& mlp, const float* W, int64_t ld, 
     q.reduce(a);
   }
   // output layer, loss and (with a gradient) its derivatives, per sample tile
-  {
+  if (!fused_out) {
     TailArgs t{};
     t.A = act(L - 1);
     t.W = W, t.idx = idx, t.ld = ld, t.w_off = mlp.w_off[L - 1], t.b_off = mlp.b_off[L - 1];
