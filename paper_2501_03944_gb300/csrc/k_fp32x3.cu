@@ -405,14 +405,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         float z[NL];
 #pragma unroll
         for (int c = 0; c < NL; ++c) z[c] = c < a.C ? b2s[v * a.C + c] : 0.f;
-#pragma unroll 1
-        for (int j0 = 0; j0 < H; j0 += 8) {
-          const uint32_t col = (uint32_t)(v * H + j0);
-          float x[8], x1[8], xc[8];
+        // 8 hidden units at a time; the next 8 are loaded from TMEM while these are used
+        float x[8], x1[8], xc[8], nx[8], nx1[8], nxc[8];
+        {
+          const uint32_t col = (uint32_t)(v * H);
           tmem_ld8(lanes + col, x);
           tmem_ld8(lanes + (uint32_t)kN + col, x1);
           tmem_ld8(lanes + (uint32_t)(2 * kN) + col, xc);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        }
+#pragma unroll 1
+        for (int j0 = 0; j0 < H; j0 += 8) {
+          const bool more = j0 + 8 < H;
+          if (more) {
+            const uint32_t col = (uint32_t)(v * H + j0 + 8);
+            tmem_ld8(lanes + col, nx);
+            tmem_ld8(lanes + (uint32_t)kN + col, nx1);
+            tmem_ld8(lanes + (uint32_t)(2 * kN) + col, nxc);
+          }
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const float zz = ((odd ? x[i] + x1[i] : x[i]) + xc[i]) + bias[j0 + i];
@@ -421,9 +431,25 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int c = 0; c < NL; ++c) {
             if (c < a.C) {
-              const float* wc = w2 + (size_t)c * H + j0;
+              const float4 w0 = *reinterpret_cast<const float4*>(w2 + (size_t)c * H + j0);
+              const float4 w1 = *reinterpret_cast<const float4*>(w2 + (size_t)c * H + j0 + 4);
+              z[c] = fmaf(x[0], w0.x, z[c]);
+              z[c] = fmaf(x[1], w0.y, z[c]);
+              z[c] = fmaf(x[2], w0.z, z[c]);
+              z[c] = fmaf(x[3], w0.w, z[c]);
+              z[c] = fmaf(x[4], w1.x, z[c]);
+              z[c] = fmaf(x[5], w1.y, z[c]);
+              z[c] = fmaf(x[6], w1.z, z[c]);
+              z[c] = fmaf(x[7], w1.w, z[c]);
+            }
+          }
+          if (more) {
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-              for (int i = 0; i < 8; ++i) z[c] = fmaf(x[i], wc[i], z[c]);
+            for (int i = 0; i < 8; ++i) {
+              x[i] = nx[i];
+              x1[i] = nx1[i];
+              xc[i] = nxc[i];
             }
           }
         }
