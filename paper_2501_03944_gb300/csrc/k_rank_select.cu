@@ -14,9 +14,13 @@ namespace {
 // One block per (firework, guiding group), fireworks of all runs numbered
 // globally.  Each thread ranks its sparks by
 // counting the sparks of the group that come strictly before them; the
-// counts are a permutation because the order is total.
-__global__ void k_rank(Problem p, const float* __restrict__ fit_e, int32_t* __restrict__ top,
-                       int32_t* __restrict__ bottom) {
+// counts are a permutation because the order is total.  With `partial`
+// (per-sample-tile loss sums [mtiles][count] of the explosion rows), the
+// block first finishes its sparks' fitness as the fitness-finish kernel
+// does (tile sums in tile order, then / N) and stores it in fit_e.
+__global__ void k_rank(Problem p, float* __restrict__ fit_e, int32_t* __restrict__ top,
+                       int32_t* __restrict__ bottom, const float* __restrict__ partial, int32_t mtiles,
+                       int32_t count, float n_f) {
   griddep_wait();
   griddep_launch_dependents();
   extern __shared__ float sh[];
@@ -26,8 +30,18 @@ __global__ void k_rank(Problem p, const float* __restrict__ fit_e, int32_t* __re
   const int grp = blockIdx.x;  // i * m + q
   const int i = grp / p.m, q = grp % p.m;
   const int base = q * g;
-  const float* fe = fit_e + (int64_t)i * p.lam + base;
-  for (int a = threadIdx.x; a < g; a += blockDim.x) f[a] = fe[a];
+  float* fe = fit_e + (int64_t)i * p.lam + base;
+  for (int a = threadIdx.x; a < g; a += blockDim.x) {
+    if (partial) {
+      const int64_t r = (int64_t)i * p.lam + base + a;
+      float s = partial[r];
+      for (int mt = 1; mt < mtiles; ++mt) s += partial[(int64_t)mt * count + r];
+      fe[a] = __fdiv_rn(s, n_f);
+      f[a] = fe[a];
+    } else {
+      f[a] = fe[a];
+    }
+  }
   __syncthreads();
   for (int a = threadIdx.x; a < g; a += blockDim.x) {
     const float fa = f[a];
@@ -194,13 +208,25 @@ __global__ void __launch_bounds__(kSelThreads) k_run_best(Problem p, int init, c
 
 // One warp per firework: the E best candidates in the (fitness, index)
 // order, picked one at a time (E is small), each pick excluding the
-// previous ones.
-__global__ void k_elite_pick(Problem p, const float* __restrict__ fit_e, const float* __restrict__ fit_g,
-                             int32_t E, int32_t* __restrict__ elite) {
+// previous ones.  With `partial` (per-sample-tile loss sums [mtiles][count]
+// of the guiding rows), the warp first finishes its firework's guiding
+// fitness as the fitness-finish kernel does and stores it in fit_g.
+__global__ void k_elite_pick(Problem p, const float* __restrict__ fit_e, float* __restrict__ fit_g,
+                             int32_t E, int32_t* __restrict__ elite, const float* __restrict__ partial,
+                             int32_t mtiles, int32_t count, float n_f) {
   griddep_wait();
   griddep_launch_dependents();
   const int z = blockIdx.x;
   const int lane = threadIdx.x;
+  if (partial) {
+    for (int q = lane; q < p.m; q += 32) {
+      const int64_t r = (int64_t)z * p.m + q;
+      float s = partial[r];
+      for (int mt = 1; mt < mtiles; ++mt) s += partial[(int64_t)mt * count + r];
+      fit_g[r] = __fdiv_rn(s, n_f);
+    }
+    __syncwarp();
+  }
   const int n_cand = p.lam + p.m;
   const int64_t n_e = (int64_t)p.B * p.mu * p.lam;
   float prev_f = 0.0f;
@@ -231,17 +257,21 @@ __global__ void k_elite_pick(Problem p, const float* __restrict__ fit_e, const f
 
 }  // namespace
 
-int launch_elite_pick(const Problem& p, const float* fit_e, const float* fit_g, int32_t E, int32_t* elite,
-                      cudaStream_t s) {
+int launch_elite_pick(const Problem& p, const float* fit_e, float* fit_g, int32_t E, int32_t* elite,
+                      cudaStream_t s, const float* partial, int32_t mtiles, int64_t N) {
   if (E <= 0) return 0;
-  if (launch_pdl(k_elite_pick, dim3(p.B * p.mu), dim3(32), 0, s, p, fit_e, fit_g, E, elite) != cudaSuccess) return -1;
+  if (launch_pdl(k_elite_pick, dim3(p.B * p.mu), dim3(32), 0, s, p, fit_e, fit_g, E, elite, partial, mtiles,
+                 p.B * p.mu * p.m, (float)N) != cudaSuccess)
+    return -1;
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
-int launch_rank(const Problem& p, const float* fit_e, int32_t* top, int32_t* bottom, cudaStream_t s) {
+int launch_rank(const Problem& p, float* fit_e, int32_t* top, int32_t* bottom, cudaStream_t s, const float* partial,
+                int32_t mtiles, int64_t N) {
   const int threads = p.g >= 256 ? 256 : ((p.g + 31) / 32) * 32;
   const size_t smem = (size_t)p.g * (sizeof(float) + sizeof(int));
-  if (launch_pdl(k_rank, dim3(p.B * p.mu * p.m), dim3(threads), smem, s, p, fit_e, top, bottom) != cudaSuccess)
+  if (launch_pdl(k_rank, dim3(p.B * p.mu * p.m), dim3(threads), smem, s, p, fit_e, top, bottom, partial, mtiles,
+                 p.B * p.mu * p.lam, (float)N) != cudaSuccess)
     return -1;
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }

@@ -188,8 +188,9 @@ bool use_tc(const mgfwa_t* h, int32_t precision) {
 }
 
 // Fitness of `count` consecutive spark rows starting at row `first` into
-// fit[first..first+count).
-mgfwa_status eval_rows(mgfwa_t* h, int64_t first, int32_t count, int32_t precision) {
+// fit[first..first+count); with defer_finish the per-tile sums stay in
+// h->partial for the next kernel to finish (MLP objectives only).
+mgfwa_status eval_rows(mgfwa_t* h, int64_t first, int32_t count, int32_t precision, bool defer_finish = false) {
   if (count <= 0) return MGFWA_OK;
   const float* rows = h->sparks + first * h->p.Dp;
   float* fit = h->fit + first;
@@ -208,10 +209,24 @@ mgfwa_status eval_rows(mgfwa_t* h, int64_t first, int32_t count, int32_t precisi
     else
       MG_LAUNCH(h, launch_fitness_simt_main(h->mlp, rows, h->p.Dp, count, h->partial, h->stream), "FP32 fitness");
   }
+  if (defer_finish) return MGFWA_OK;
   Mark mk(h, G_FINISH);
   MG_LAUNCH(h, launch_fitness_finish(h->partial, h->mtiles, count, h->mlp.N, fit, h->stream), "fitness finish");
   return MGFWA_OK;
 }
+
+// The generation's elite re-score runs (low precision, E > 0, MLP objective).
+bool rescore_on(const mgfwa_t* h) {
+  return h->cfg.precision != MGFWA_FP32 && h->cfg.elite_rescore > 0 && h->kind == MGFWA_OBJ_MLP_CE;
+}
+
+// In a captured generation the fitness means are finished by the kernel
+// that first reads them (the explosion sparks' by the rank, the guiding
+// sparks' by the elite pick when the re-score runs), one launch fewer
+// each; phase-by-phase stepping keeps the separate finish so that every
+// phase's buffers can be read.
+bool finish_in_rank(const mgfwa_t* h) { return h->capturing && h->kind == MGFWA_OBJ_MLP_CE; }
+bool finish_in_pick(const mgfwa_t* h) { return h->capturing && rescore_on(h); }
 
 // Generation `gen` (1-based) ends with a hybrid refinement.
 bool refine_due(const mgfwa_t* h, int32_t gen) {
@@ -293,10 +308,13 @@ mgfwa_status run_phase(mgfwa_t* h, int32_t phase) {
       return MGFWA_OK;
     }
     case MGFWA_PHASE_EVAL_E:
-      return eval_rows(h, 0, (int32_t)n_e, prec);
+      return eval_rows(h, 0, (int32_t)n_e, prec, finish_in_rank(h));
     case MGFWA_PHASE_RANK: {
       Mark mk(h, G_RANK);
-      MG_LAUNCH(h, launch_rank(p, h->fit, h->top, h->bottom, h->stream), "rank");
+      if (finish_in_rank(h))
+        MG_LAUNCH(h, launch_rank(p, h->fit, h->top, h->bottom, h->stream, h->partial, h->mtiles, h->mlp.N), "rank");
+      else
+        MG_LAUNCH(h, launch_rank(p, h->fit, h->top, h->bottom, h->stream), "rank");
       return MGFWA_OK;
     }
     case MGFWA_PHASE_GUIDE: {
@@ -306,13 +324,18 @@ mgfwa_status run_phase(mgfwa_t* h, int32_t phase) {
       return MGFWA_OK;
     }
     case MGFWA_PHASE_EVAL_G:
-      return eval_rows(h, n_e, p.B * p.mu * p.m, prec);
+      return eval_rows(h, n_e, p.B * p.mu * p.m, prec, finish_in_pick(h));
     case MGFWA_PHASE_RESCORE: {
       // low precision: each firework's elite candidates get their fitness in FP32
       const int32_t E = h->cfg.elite_rescore;
-      if (prec == MGFWA_FP32 || E <= 0 || h->kind != MGFWA_OBJ_MLP_CE) return MGFWA_OK;
+      if (!rescore_on(h)) return MGFWA_OK;
       Mark mk(h, G_RESCORE);
-      MG_LAUNCH(h, launch_elite_pick(p, h->fit, h->fit + n_e, E, h->elite, h->stream), "elite pick");
+      if (finish_in_pick(h))
+        MG_LAUNCH(h, launch_elite_pick(p, h->fit, h->fit + n_e, E, h->elite, h->stream, h->partial, h->mtiles,
+                                       h->mlp.N),
+                  "elite pick");
+      else
+        MG_LAUNCH(h, launch_elite_pick(p, h->fit, h->fit + n_e, E, h->elite, h->stream), "elite pick");
       MG_LAUNCH(h, launch_grad(h->rescore_plan, h->mlp, h->sparks, p.Dp, h->rescore_scratch, nullptr, h->fit,
                                h->stream, h->elite, &h->rescore_l1, h->status),
                 "elite FP32 fitness");

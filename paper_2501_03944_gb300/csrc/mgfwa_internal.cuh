@@ -194,7 +194,11 @@ int launch_init(const Problem& p, float* fw_x, float* fw_amp, cudaStream_t s);
 int launch_explode(const Problem& p, const uint32_t* gens_done, const float* fw_x, const float* fw_amp,
                    float* sparks, const OpDesc& op, cudaStream_t s);
 
-int launch_rank(const Problem& p, const float* fit_e, int32_t* top, int32_t* bottom, cudaStream_t s);
+// With `partial` ([mtiles][mu*lam] per-sample-tile loss sums of the
+// explosion rows, N samples), the rank kernel also finishes the explosion
+// fitness into fit_e, exactly as launch_fitness_finish would.
+int launch_rank(const Problem& p, float* fit_e, int32_t* top, int32_t* bottom, cudaStream_t s,
+                const float* partial = nullptr, int32_t mtiles = 0, int64_t N = 0);
 
 // Guiding sparks written to `guides` (mu*m rows of stride Dp) and, if non-
 // null, their operand rows `op_guides`.
@@ -232,8 +236,11 @@ int launch_fitness_finish(const float* partial, int32_t mtiles, int32_t count, i
 // `E` best of its lam explosion and m guiding sparks by the current
 // fitness, as rows of the spark buffer (explosion z*lam + c, guiding
 // n_e + z*m + q) into elite[z*E + e].
-int launch_elite_pick(const Problem& p, const float* fit_e, const float* fit_g, int32_t E, int32_t* elite,
-                      cudaStream_t s);
+// With `partial` ([mtiles][mu*m] per-sample-tile loss sums of the guiding
+// rows, N samples), the pick also finishes the guiding fitness into fit_g
+// first, exactly as launch_fitness_finish would.
+int launch_elite_pick(const Problem& p, const float* fit_e, float* fit_g, int32_t E, int32_t* elite,
+                      cudaStream_t s, const float* partial = nullptr, int32_t mtiles = 0, int64_t N = 0);
 
 int launch_fitness_sphere(const float* rows, int64_t ld, int64_t D, int32_t count, float* fit, cudaStream_t s);
 

@@ -2,8 +2,9 @@
 graph per generation (explode .. select), its kernels chained by
 programmatic dependent launch; while kernel groups are timed
 (mgfwa_debug_profile) it launches the same kernels one by one between
-events.  Both paths must end bitwise in the same state and count the same
-kernels: FP32, BF16 with the elite re-score (at full size on the
+events, and with the fitness means finished by their own kernel instead
+of inside the rank and the elite pick.  Both paths must end bitwise in the
+same state: FP32, BF16 with the elite re-score (at full size on the
 tensor-core FP32 layer with its fused output layer), FP8, a three-layer
 net, the sphere, two runs in one handle, and the hybrid refinement."""
 import numpy as np
@@ -61,7 +62,7 @@ def test_graph_replay_equals_kernel_by_kernel(pkg, case):
             states.append((bests, h.read(pkg.MGFWA_BUF_FW_F), h.read(pkg.MGFWA_BUF_FW_X), info.generations,
                            info.kernel_launches))
     (ba, fa, xa, ga, la), (bb, fb, xb, gb, lb) = states
-    assert ga == gb and la == lb
+    assert ga == gb and lb <= la
     assert np.array_equal(fa, fb) and np.array_equal(xa, xb)
     for (x1, f1, e1), (x2, f2, e2) in zip(ba, bb):
         assert np.array_equal(x1, x2) and f1 == f2 and e1 == e2
