@@ -86,27 +86,69 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """SM clock and clock-event reasons sampled while running: read-only NVML queries every 2 ms from a
+    thread (through the driver's libnvidia-ml), else nvidia-smi every 200 ms."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits (nvml.h)
+    REASON_BITS = (("hw_slowdown", 0x8), ("hw_thermal_slowdown", 0x40), ("sw_thermal_slowdown", 0x20),
+                   ("sw_power_cap", 0x4))
 
     def __init__(self, device_index: int):
         self.proc = None
         self.dev = device_index
+        self.samples = []          # (sm MHz, max MHz, reason bits) from NVML
+        self.source = None
+
+    def _nvml_start(self):
+        import ctypes
+        import threading
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        handle = ctypes.c_void_p()
+        if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.dev), ctypes.byref(handle)) != 0:
+            lib.nvmlShutdown()
+            raise OSError("no NVML handle")
+        self._lib, self._handle = lib, handle
+        self._stop = threading.Event()
+
+        def loop():
+            sm, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+            while not self._stop.is_set():
+                if (lib.nvmlDeviceGetClockInfo(handle, 1, ctypes.byref(sm)) == 0 and
+                        lib.nvmlDeviceGetMaxClockInfo(handle, 1, ctypes.byref(mx)) == 0 and
+                        lib.nvmlDeviceGetCurrentClocksEventReasons(handle, ctypes.byref(rs)) == 0):
+                    self.samples.append((sm.value, mx.value, rs.value))
+                time.sleep(0.002)
+
+        self._thread = threading.Thread(target=loop, daemon=True)
+        self._thread.start()
+        self.source = "nvml"
 
     def __enter__(self):
+        try:
+            self._nvml_start()
+            return self
+        except (OSError, AttributeError):
+            pass
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.source = "nvidia-smi"
         except OSError:
             self.proc = None
         return self
 
     def __exit__(self, *exc):
         self.lines = []
+        if self.source == "nvml":
+            self._stop.set()
+            self._thread.join(timeout=5)
+            self._lib.nvmlShutdown()
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -117,24 +159,31 @@ class ClockSampler:
             self.lines = [l for l in out.splitlines() if l.strip()]
 
     def summary(self):
-        if not getattr(self, "lines", None):
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         sm, smax, reasons = [], [], set()
-        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for l in self.lines:
-            parts = [p.strip() for p in l.split(",")]
-            try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except (ValueError, IndexError):
-                continue
-            for n, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
+        if self.source == "nvml":
+            for c, m, bits in self.samples:
+                sm.append(float(c))
+                smax.append(float(m))
+                for n, bit in self.REASON_BITS:
+                    if bits & bit:
+                        reasons.add(n)
+        else:
+            names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+            for l in getattr(self, "lines", []):
+                parts = [p.strip() for p in l.split(",")]
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except (ValueError, IndexError):
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unparsed"], "samples": 0}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0,
+                    "source": self.source}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": self.source}
 
 
 # ---------------------------------------------------------------------------
@@ -529,7 +578,7 @@ def serving_trace(pkg, X, y, n_requests: int = 40, rate_hz: float = 200.0, max_l
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=("gb300", "reference"))
     ap.add_argument("--precision", default="bf16", choices=("bf16", "fp32", "fp8"))
