@@ -30,8 +30,8 @@
 //   warp 1  TMEM allocator and single-thread MMA issuer: layer 1 of tile t
 //           (M=128, N=S*h1, K=16, kind::f16), then layer 2 of tile t-1
 //           (M=128, N=N2, K=8, kind::tf32, A from TMEM);
-//   warps 2..9  epilogue, two warps per TMEM lane quadrant, each taking
-//           every other spark of the tile.
+//   warps 2..  epilogue, two (BF16) or three (E4M3) warps per TMEM lane
+//           quadrant, each taking every second or third spark of the tile.
 // Every mbarrier wait is bounded: on timeout the CTA raises a flag in
 // shared memory and a bit in the status word, every role leaves its loop,
 // and the CTA waits (bounded) for its own copies and MMAs, frees its TMEM
@@ -53,8 +53,11 @@ constexpr int kRowBytes = 128;   // bytes of K per stage row: one 128-byte swizz
 constexpr int kUmmaKBytes = 32;  // bytes of K per layer-1 MMA (16 BF16 or 32 E4M3)
 constexpr int kUmmaK2 = 8;       // K per tcgen05.mma kind::tf32
 constexpr int kAtomK2 = 32;      // FP32 elements per 128-byte swizzle row of W2
-constexpr int kEpiWarps = 8;
-constexpr int kThreads = 64 + 32 * kEpiWarps;
+// Epilogue warps: 8 (two per TMEM lane quadrant) with BF16 operands, where layer 1's
+// MMAs set the pace; 12 (three per quadrant) with E4M3, whose MMAs take half as long
+// and leave the epilogue as the limit.
+__host__ __device__ constexpr int epi_warps(bool f8) { return f8 ? 12 : 8; }
+__host__ __device__ constexpr int threads_for(bool f8) { return 64 + 32 * epi_warps(f8); }
 constexpr int kMaxStages = 6;
 constexpr int kTmemCols = 512;   // two halves of 256 columns
 constexpr int kTailBufs = 3;     // tail buffers (biases, W2[, W3]): the producer runs a tile ahead of layer 2
@@ -246,10 +249,12 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float* v) {
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory"); }
+template <int kEpi>
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpi) : "memory"); }
 
 // Named barrier over the epilogue warps that also ORs a flag across them, so
 // that every epilogue thread takes the same branch afterwards.
+template <int kEpi>
 __device__ __forceinline__ bool epi_bar_any(bool flag) {
   uint32_t out;
   asm volatile(
@@ -258,7 +263,7 @@ __device__ __forceinline__ bool epi_bar_any(bool flag) {
       "bar.red.or.pred q, 1, %2, p;\n\t"
       "selp.u32 %0, 1, 0, q;\n\t}"
       : "=r"(out)
-      : "r"((uint32_t)flag), "n"(32 * kEpiWarps)
+      : "r"((uint32_t)flag), "n"(32 * kEpi)
       : "memory");
   return out != 0;
 }
@@ -290,12 +295,14 @@ struct TcArgs {
 // H2 > 0: three layers, z2 (H2 columns) = act(h + b1) W2^T, then logits =
 // act(z2 + b2) W3^T, both TF32 MMAs with A from TMEM.
 template <int H1, int H2, int NL, bool F8>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(threads_for(F8), 1)
     k_fitness_tc(const __grid_constant__ CUtensorMap tmap_x, const __grid_constant__ CUtensorMap tmap_w,
                  const __grid_constant__ CUtensorMap tmap_w2, const __grid_constant__ CUtensorMap tmap_w3, TcArgs a) {
   griddep_wait();
   griddep_launch_dependents();
   constexpr int kBK = F8 ? 128 : 64;  // K elements per stage (one 128-byte row)
+  constexpr int kEpiWarps = epi_warps(F8);
+  constexpr int kGroups = kEpiWarps / 4;  // epilogue warps per TMEM lane quadrant
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   constexpr bool kL3 = H2 > 0;
   constexpr int kR2 = kL3 ? H2 : NL;                  // rows of layer 2's B operand
@@ -511,10 +518,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ---------------- epilogue ----------------
-    const int ew = warp - 2;                 // 0..7
+    const int ew = warp - 2;                 // 0 .. kEpiWarps-1
     const int quad = warp & 3;               // TMEM lane quadrant this warp may access
-    const int half = ew >> 2;                // which of the tile's sparks (every other one)
-    const int et = threadIdx.x - 64;         // 0..255
+    const int grp = ew >> 2;                 // which of the tile's sparks (every kGroups-th one)
+    const int et = threadIdx.x - 64;         // 0 .. 32 kEpiWarps - 1
     const int row_in_tile = quad * 32 + lane;
     const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16);
     int local = 0;
@@ -530,12 +537,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int tb = local % kTB;
       bool ok = mbar_wait(sm, &sm->tmem_full[b], use & 1u, a.status, 4u);
       ok = ok && mbar_wait(sm, &sm->tail_full[tb], (uint32_t)(local / kTB) & 1u, a.status, 4u);
-      if (epi_bar_any(!ok || sm->abort_flag)) break;
+      if (epi_bar_any<kEpiWarps>(!ok || sm->abort_flag)) break;
       tc_fence_after();
       const float* tail = tails + (size_t)tb * S * kTailFloats;
       const uint32_t hbase = lane_base + (uint32_t)(b * 256);
       // act(h + b1) in place: the TMEM A operand of layer 2
-      for (int s = half; s < s_valid; s += 2) {
+      for (int s = grp; s < s_valid; s += kGroups) {
         const float* b1 = tail + (size_t)s * kTailFloats;
 #pragma unroll 1
         for (int j0 = 0; j0 < H1; j0 += 8) {
@@ -559,11 +566,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&sm->a2_full[b]);
       ok = mbar_wait(sm, &sm->l2_full[b], use & 1u, a.status, 4u);
-      if (epi_bar_any(!ok || sm->abort_flag)) break;
+      if (epi_bar_any<kEpiWarps>(!ok || sm->abort_flag)) break;
       tc_fence_after();
       if (kL3) {
         // act(z2 + b2) in place: the TMEM A operand of layer 3
-        for (int s = half; s < s_valid; s += 2) {
+        for (int s = grp; s < s_valid; s += kGroups) {
           const float* b2 = tail + (size_t)s * kTailFloats + H1;
 #pragma unroll 1
           for (int j0 = 0; j0 < H2; j0 += 8) {
@@ -581,10 +588,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm->a3_full[b]);
         ok = mbar_wait(sm, &sm->l3_full[b], use & 1u, a.status, 4u);
-        if (epi_bar_any(!ok || sm->abort_flag)) break;
+        if (epi_bar_any<kEpiWarps>(!ok || sm->abort_flag)) break;
         tc_fence_after();
       }
-      for (int s = half; s < s_valid; s += 2) {
+      for (int s = grp; s < s_valid; s += kGroups) {
         const float* b2 = tail + (size_t)s * kTailFloats + H1 + H2;  // the last layer's bias
         float z[NL];
         const uint32_t col = hbase + col_lg(s);
@@ -620,7 +627,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_arrive(&sm->l2_empty[b]);
         mbar_arrive(&sm->tail_empty[tb]);
       }
-      epi_bar();
+      epi_bar<kEpiWarps>();
       if (et < s_valid) {
         const int s = et;
         const float v = ((red[s * 4 + 0] + red[s * 4 + 1]) + red[s * 4 + 2]) + red[s * 4 + 3];
@@ -685,7 +692,7 @@ cudaError_t launch_hn(const TcPlan& plan, const TcArgs& args, cudaStream_t s, bo
   if (e != cudaSuccess || prepare_only) return e;
   const int tiles = args.m_tiles * args.n_tiles;
   const int grid = tiles < plan.num_sms ? tiles : plan.num_sms;
-  return launch_pdl(k_fitness_tc<H1, H2, NL, F8>, dim3(grid), dim3(kThreads), plan.smem_bytes, s, plan.tmap_x,
+  return launch_pdl(k_fitness_tc<H1, H2, NL, F8>, dim3(grid), dim3(threads_for(F8)), plan.smem_bytes, s, plan.tmap_x,
                     plan.tmap_w, plan.tmap_w2, plan.tmap_w3, args);
 }
 
