@@ -28,7 +28,7 @@ bool l1_fp32x3_supported(const Mlp& mlp);
 bool l1_fp32x3_plan(L1Plan& pl, const Mlp& mlp, const float* rows, int64_t ld, int64_t max_rows);
 
 // out[r][n][j] = act(X[n] . W1_j + b1_j) of rows idx[r] (or r) of the
-// planned buffer, r < R; FP32-accurate (split TF32 products).  With loss
+// planned buffer, r < R; FP32-accurate (split BF16 products).  With loss
 // (two-layer nets with at most 32 classes, l1_fp32x3_fuses_output), the
 // output layer runs in the same kernel instead: loss[r][n] is the sample's
 // cross-entropy of the logits W2 a + b2, computed in the same order as the

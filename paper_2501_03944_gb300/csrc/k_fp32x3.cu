@@ -4,32 +4,31 @@
 // output-layer kernel.  Used where FP32 accuracy is required (the elite
 // re-score, the refinement's forward pass).
 //
-// Each FP32 operand v is split into three TF32-exact parts: v1 = v with its
-// low 13 mantissa bits cleared, v2 = the same of v - v1, v3 = v - v1 - v2
-// (all exact in FP32; |v2| <= 2^-10 |v|, |v3| <= 2^-20 |v|).  Six tcgen05
-// kind::tf32 MMAs per K step accumulate a1b1 + a1b2 + a2b1 + a2b2 + a1b3 +
-// a3b1 in FP32: the products are exact, and the dropped terms (a2b3, a3b2,
-// a3b3, and the TF32 reading of v3) are below 2^-29 of each product.  The
-// tensor core's own accumulation rounds at every step, so the main products
-// a1b1 go to two accumulators (even and odd K blocks) and the five
-// corrections (about 2^-10 of them) to a third; the epilogue adds the three
-// in FP32.  That keeps the result within FP32 accuracy for K in the
-// thousands.
+// Each FP32 operand v is split into three BF16 parts, each rounded to
+// nearest: v1 = bf16(v), v2 = bf16(v - v1), v3 = bf16(v - v1 - v2) (the
+// differences are exact in FP32; |v2| <= 2^-9 |v|, |v3| <= 2^-18 |v|, and
+// v - v1 - v2 - v3 <= 2^-27 |v|).  Six tcgen05 kind::f16 MMAs (BF16 in,
+// FP32 accumulate, K = 16) per K step accumulate a1b1 + a1b2 + a2b1 + a2b2
+// + a1b3 + a3b1: the products of 8-bit significands are exact in FP32, and
+// the dropped terms (a2b3, a3b2, a3b3 and the residuals) are below about
+// 2^-25 of each product, under FP32's own rounding.  The tensor core's own
+// accumulation rounds at every step, so the main products a1b1 go to two
+// accumulators (even and odd K blocks) and the five corrections (about 2^-8
+// of them) to a third; the epilogue adds the three in FP32.  That keeps the
+// result within FP32 accuracy for K in the thousands.
 //
 // One CTA per 128-sample tile and 128 / h1 vectors.  Warp 0 issues TMA
 // (FP32 tiles of X and of the vectors' W1, 32 K-elements = one 128-byte
-// swizzle row per stage).  Warps
-// 2..5 split each landed stage: the W1 tile in place (v1 over the FP32
-// tile, v2 and v3 into two twin buffers at the same offsets, so the
-// swizzled layout carries over unchanged), and the X tile row by row (one
-// sample per thread, its TMEM lane) into a ring of TMEM slots, each holding
-// the three parts of 16 K-elements.  Warp 1 issues the MMAs with A (the X
-// parts) from TMEM and B (the W1 parts) from shared memory, so the tensor
-// core reads only the narrow operand from shared memory.  Warps 2..5
-// finally read the accumulators (one sample row per thread), add b1, apply
-// the activation and store the row.  Every wait is bounded; a wait that
-// gives up sets a bit in the status word and the CTA drains its copies and
-// MMAs and returns.
+// swizzle row per stage).  Warps 2..5 split each landed stage: the W1 tile
+// row by row into three BF16 part tiles (64-byte rows, 64-byte swizzle), and
+// the X tile row by row (one sample per thread, its TMEM lane) into a ring
+// of TMEM slots, each holding the three parts of 16 K-elements (two BF16 per
+// 32-bit column).  Warp 1 issues the MMAs with A (the X parts) from TMEM and
+// B (the W1 parts) from shared memory, so the tensor core reads only the
+// narrow operand from shared memory.  Warps 2..5 finally read the
+// accumulators (one sample row per thread), add b1, apply the activation and
+// store the row.  Every wait is bounded; a wait that gives up sets a bit in
+// the status word and the CTA drains its copies and MMAs and returns.
 #include <cuda.h>
 
 #include "fp32x3.cuh"
@@ -43,7 +42,7 @@ constexpr int kBKf = 32;           // FP32 K elements per stage (128 bytes)
 constexpr int kSlotK = 16;         // K elements per TMEM slot of the X parts
 constexpr int kMaxStages = 6;
 constexpr int kMaxSlots = 8;
-constexpr int kParts = 3;          // TF32 parts per operand
+constexpr int kParts = 3;          // BF16 parts per operand
 constexpr int kThreads = 192;      // warp 0 TMA, warp 1 MMA, warps 2..5 convert + epilogue
 constexpr uint32_t kTmemCols = 512;
 constexpr uint64_t kWaitBudget = 1ull << 32;
@@ -118,38 +117,35 @@ __device__ __forceinline__ void tma_3d(void* dst, const CUtensorMap* m, int x, i
       "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(b))
       : "memory");
 }
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+// Shared-memory matrix descriptor of a K-major BF16 operand in 64-byte
+// swizzled rows (32 K-elements per row), 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
   uint64_t d = 0;
-  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;          // stride byte offset: 8 rows x 64 B
+  d |= (uint64_t)1 << 46;                   // descriptor version for tcgen05
+  d |= (uint64_t)4 << 61;                   // 64-byte swizzle
   return d;
 }
-__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+// kind::f16 with BF16 A and B, FP32 D.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
-// D (TMEM) (+)= A (TMEM) x B (shared memory), TF32 inputs.
-__device__ __forceinline__ void mma_tf32_ta(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t accum) {
+// D (TMEM) (+)= A (TMEM) x B (shared memory), BF16 inputs.
+__device__ __forceinline__ void mma_bf16_ta(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t accum) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
       "r"(a_tmem), "l"(b), "r"(idesc), "r"(accum)
       : "memory");
 }
-// 32 lanes x 16 consecutive 32-bit columns.
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16};" ::"r"(taddr),
-      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
-      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
-      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
-      "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
-      "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
-      : "memory");
+// 32 lanes x 8 consecutive 32-bit columns.
+__device__ __forceinline__ void tmem_st8u(uint32_t taddr, const uint32_t* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* b) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(b))
@@ -164,27 +160,17 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// v -> (v1, v2, v3): v1 the TF32 truncation of v, v2 that of v - v1, v3 the rest.
-__device__ __forceinline__ void split1(float v, float& p1, float& p2, float& p3) {
-  p1 = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-  const float r = v - p1;
-  p2 = __uint_as_float(__float_as_uint(r) & 0xFFFFE000u);
-  p3 = r - p2;
-}
-
-// Elements [t, n) step 128 of a stage buffer: v1 in place, v2 and v3 to the twins.
-__device__ __forceinline__ void split3(float4* p1, float4* p2, float4* p3, int n, int t) {
-  for (int e = t; e < n; e += 128) {
-    const float4 v = p1[e];
-    float4 x, y, z;
-    split1(v.x, x.x, y.x, z.x);
-    split1(v.y, x.y, y.y, z.y);
-    split1(v.z, x.z, y.z, z.z);
-    split1(v.w, x.w, y.w, z.w);
-    p1[e] = x;
-    p2[e] = y;
-    p3[e] = z;
-  }
+// Two consecutive K elements (a, b) -> their three BF16 parts, each packed
+// with a in the low half (the lower K index first): v1 = bf16(v), v2 =
+// bf16(v - v1), v3 = bf16(v - v1 - v2), round to nearest.
+__device__ __forceinline__ void split2(float a, float b, uint32_t& p1, uint32_t& p2, uint32_t& p3) {
+  const __nv_bfloat162 h1 = __floats2bfloat162_rn(a, b);
+  const float ra = __fsub_rn(a, __low2float(h1)), rb = __fsub_rn(b, __high2float(h1));
+  const __nv_bfloat162 h2 = __floats2bfloat162_rn(ra, rb);
+  const __nv_bfloat162 h3 = __floats2bfloat162_rn(__fsub_rn(ra, __low2float(h2)), __fsub_rn(rb, __high2float(h2)));
+  p1 = *reinterpret_cast<const uint32_t*>(&h1);
+  p2 = *reinterpret_cast<const uint32_t*>(&h2);
+  p3 = *reinterpret_cast<const uint32_t*>(&h3);
 }
 
 struct Args {
@@ -210,16 +196,20 @@ struct Args {
 // Each CTA takes V = 128 / H vectors, so that every MMA is M=128, N=128:
 // the tensor core's cost per instruction barely depends on N at these
 // widths, so fewer, wider products are the faster way through the six.
-// Shared memory per stage: the FP32 X tile and the three parts of the V
-// stacked W1 tiles (128 rows).  TMEM: the accumulators (main even, main odd,
-// corrections: 3 x 128 columns) and then the X slots, 3 parts x 16 columns.
+// Shared memory per stage: the FP32 X tile, the FP32 tile of the V stacked
+// W1 blocks (128 rows) and its three BF16 parts (128 rows x 64 bytes each).
+// TMEM: the accumulators (main even, main odd, corrections: 3 x 128 columns)
+// and then the X slots: one K step of 16, 3 parts x 8 columns (two BF16 per
+// 32-bit column).
 constexpr int kN = 128;
 constexpr int kMaxC = 32;           // classes of a fused output layer
 constexpr int kStages = 3;
-constexpr int kSlots = 2;
+constexpr int kSlots = 4;
 constexpr uint32_t kABytes = kBM * 128;
-constexpr uint32_t kBBytes = kN * 128;
-constexpr uint32_t kSlotCols = kParts * kSlotK;
+constexpr uint32_t kBBytes = kN * 128;     // FP32 W1 tile of a stage
+constexpr uint32_t kBhBytes = kN * 64;     // one BF16 part of it
+constexpr uint32_t kPartCols = kSlotK / 2;
+constexpr uint32_t kSlotCols = kParts * kPartCols;
 constexpr uint32_t kSlot0 = 3 * kN;  // first TMEM column of the X slots
 static_assert(kSlot0 + kSlots * kSlotCols <= kTmemCols, "accumulators and X slots fit in TMEM");
 static_assert(kStages <= kMaxStages && kSlots <= kMaxSlots, "barrier arrays");
@@ -235,10 +225,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int V = kN / H;
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   // X tile of stage s at base + s * kABytes; part p of the W1 tiles of stage s after all X tiles
-  uint8_t* b_part = base + (size_t)kStages * kABytes;
+  uint8_t* b_f32 = base + (size_t)kStages * kABytes;
+  uint8_t* b_half = b_f32 + (size_t)kStages * kBBytes;
   auto A = [&](int s) { return base + (size_t)s * kABytes; };
-  auto Bp = [&](int p, int s) { return b_part + ((size_t)p * kStages + s) * kBBytes; };
-  Bars* sb = reinterpret_cast<Bars*>(b_part + (size_t)kParts * kStages * kBBytes);
+  auto Bf = [&](int s) { return b_f32 + (size_t)s * kBBytes; };
+  auto Bh = [&](int p, int s) { return b_half + ((size_t)p * kStages + s) * kBhBytes; };
+  Bars* sb = reinterpret_cast<Bars*>(b_half + (size_t)kParts * kStages * kBhBytes);
   float* w2s = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(sb) + ((sizeof(Bars) + 15) & ~size_t(15)));
   float* b2s = w2s + (size_t)V * kMaxC * H;  // fused output layer: W2 [V][C][H], b2 [V][C] of the CTA's vectors
 
@@ -288,7 +280,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tma_2d(A(s), &tmap_x, kb * kBKf, mt * kBM, &sb->full[s]);
 #pragma unroll
         for (int v = 0; v < V; ++v)
-          tma_3d(Bp(0, s) + (size_t)v * H * 128, &tmap_w, kb * kBKf, 0, rows[v], &sb->full[s]);
+          tma_3d(Bf(s) + (size_t)v * H * 128, &tmap_w, kb * kBKf, 0, rows[v], &sb->full[s]);
       }
       // every issued copy lands before the CTA may exit
       for (int j = kb - kStages > 0 ? kb - kStages : 0; j < kb; ++j)
@@ -296,12 +288,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = idesc_tf32(kBM, kN);
+      const uint32_t idesc = idesc_bf16(kBM, kN);
       int kb = 0;
       bool ok = true;
       for (; kb < a.k_blocks && ok; ++kb) {
         const int s = kb % kStages;
-        const uint32_t b1 = smem_u32(Bp(0, s)), b2 = smem_u32(Bp(1, s)), b3 = smem_u32(Bp(2, s));
+        const uint32_t b1 = smem_u32(Bh(0, s)), b2 = smem_u32(Bh(1, s)), b3 = smem_u32(Bh(2, s));
         const uint32_t d_main = tmem + (uint32_t)((kb & 1) * kN), d_corr = tmem + (uint32_t)(2 * kN);
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
@@ -312,20 +304,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t xa = tmem + kSlot0 + (uint32_t)slot * kSlotCols;
-#pragma unroll
-          for (int kk = 0; kk < kSlotK / 8; ++kk) {
-            const uint32_t o = (uint32_t)(j * (kSlotK / 8) + kk) * 32u;  // byte offset of this K step in a W1 row
-            const uint32_t a1 = xa + (uint32_t)(kk * 8), a2 = a1 + kSlotK, a3 = a1 + 2 * kSlotK;
-            const uint32_t first = (kb < 2 && j == 0 && kk == 0) ? 0u : 1u;     // this main accumulator's first
-            const uint32_t first_c = (kb == 0 && j == 0 && kk == 0) ? 0u : 1u;  // the corrections' first
-            mma_tf32_ta(d_main, a1, smem_desc(b1 + o), idesc, first);
-            mma_tf32_ta(d_corr, a1, smem_desc(b2 + o), idesc, first_c);
-            mma_tf32_ta(d_corr, a2, smem_desc(b1 + o), idesc, 1u);
-            mma_tf32_ta(d_corr, a2, smem_desc(b2 + o), idesc, 1u);
-            mma_tf32_ta(d_corr, a1, smem_desc(b3 + o), idesc, 1u);
-            mma_tf32_ta(d_corr, a3, smem_desc(b1 + o), idesc, 1u);
-          }
+          const uint32_t a1 = tmem + kSlot0 + (uint32_t)slot * kSlotCols, a2 = a1 + kPartCols, a3 = a2 + kPartCols;
+          const uint32_t o = (uint32_t)j * 32u;  // byte offset of this K step (16 BF16) in a 64-byte W1 row
+          const uint32_t first = (kb < 2 && j == 0) ? 0u : 1u;     // this main accumulator's first product
+          const uint32_t first_c = (kb == 0 && j == 0) ? 0u : 1u;  // the corrections' first
+          mma_bf16_ta(d_main, a1, smem_desc_sw64(b1 + o), idesc, first);
+          mma_bf16_ta(d_corr, a1, smem_desc_sw64(b2 + o), idesc, first_c);
+          mma_bf16_ta(d_corr, a2, smem_desc_sw64(b1 + o), idesc, 1u);
+          mma_bf16_ta(d_corr, a2, smem_desc_sw64(b2 + o), idesc, 1u);
+          mma_bf16_ta(d_corr, a1, smem_desc_sw64(b3 + o), idesc, 1u);
+          mma_bf16_ta(d_corr, a3, smem_desc_sw64(b1 + o), idesc, 1u);
           mma_commit(&sb->a_empty[slot]);
         }
         if (ok) mma_commit(&sb->empty[s]);
@@ -355,9 +343,25 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
       ok = mbar_wait(sb, &sb->full[s], ph, a.status, 4u);
       if (!ok) break;
-      // W1 parts: v1 in place, v2 and v3 into the twins (free: the stage's MMAs of its last use completed)
-      split3(reinterpret_cast<float4*>(Bp(0, s)), reinterpret_cast<float4*>(Bp(1, s)),
-             reinterpret_cast<float4*>(Bp(2, s)), (int)(kBBytes / 16), ct);
+      // W1 row ct -> its three BF16 parts, each a 64-byte row with 16-byte chunk c at c ^ ((row / 2) & 3)
+      // (64-byte swizzle; the part buffers are free: the stage's MMAs of its last use completed)
+      {
+        const uint8_t* wrow = Bf(s) + ct * 128;
+        uint32_t w1[16], w2[16], w3[16];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const float4 v = *reinterpret_cast<const float4*>(wrow + ((c ^ (ct & 7)) << 4));
+          split2(v.x, v.y, w1[2 * c], w2[2 * c], w3[2 * c]);
+          split2(v.z, v.w, w1[2 * c + 1], w2[2 * c + 1], w3[2 * c + 1]);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int off = ct * 64 + ((c ^ ((ct >> 1) & 3)) << 4);
+          *reinterpret_cast<uint4*>(Bh(0, s) + off) = make_uint4(w1[4 * c], w1[4 * c + 1], w1[4 * c + 2], w1[4 * c + 3]);
+          *reinterpret_cast<uint4*>(Bh(1, s) + off) = make_uint4(w2[4 * c], w2[4 * c + 1], w2[4 * c + 2], w2[4 * c + 3]);
+          *reinterpret_cast<uint4*>(Bh(2, s) + off) = make_uint4(w3[4 * c], w3[4 * c + 1], w3[4 * c + 2], w3[4 * c + 3]);
+        }
+      }
       // generic-proxy writes become visible to the tensor core's (async proxy) reads
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       const uint8_t* xrow = A(s) + rrow * 128;
@@ -366,22 +370,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int hk = 2 * kb + j;
         const int slot = hk % kSlots;
         // 16 K-elements of this sample: 16-byte chunks 4j..4j+3 of its row, at chunk c ^ (row & 7) (128-byte swizzle)
-        float v1[kSlotK], v2[kSlotK], v3[kSlotK];
+        uint32_t x1[8], x2[8], x3[8];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const float4 v = *reinterpret_cast<const float4*>(xrow + (((4 * j + c) ^ (rrow & 7)) << 4));
-          split1(v.x, v1[4 * c + 0], v2[4 * c + 0], v3[4 * c + 0]);
-          split1(v.y, v1[4 * c + 1], v2[4 * c + 1], v3[4 * c + 1]);
-          split1(v.z, v1[4 * c + 2], v2[4 * c + 2], v3[4 * c + 2]);
-          split1(v.w, v1[4 * c + 3], v2[4 * c + 3], v3[4 * c + 3]);
+          split2(v.x, v.y, x1[2 * c], x2[2 * c], x3[2 * c]);
+          split2(v.z, v.w, x1[2 * c + 1], x2[2 * c + 1], x3[2 * c + 1]);
         }
         ok = mbar_wait(sb, &sb->a_empty[slot], ((uint32_t)(hk / kSlots) & 1u) ^ 1u, a.status, 8u);
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t xa = lanes + kSlot0 + (uint32_t)slot * kSlotCols;
-        tmem_st16(xa, v1);
-        tmem_st16(xa + kSlotK, v2);
-        tmem_st16(xa + 2 * kSlotK, v3);
+        tmem_st8u(xa, x1);
+        tmem_st8u(xa + kPartCols, x2);
+        tmem_st8u(xa + 2 * kPartCols, x3);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
@@ -536,7 +538,7 @@ bool encode(CUtensorMap* map, uint32_t rank, const void* ptr, const cuuint64_t* 
 }
 
 size_t smem_bytes() {
-  return 1024 + (size_t)kStages * (kABytes + (size_t)kParts * kBBytes) + ((sizeof(Bars) + 15) & ~size_t(15)) +
+  return 1024 + (size_t)kStages * (kABytes + kBBytes + (size_t)kParts * kBhBytes) + ((sizeof(Bars) + 15) & ~size_t(15)) +
          sizeof(float) * ((size_t)kN * kMaxC + (size_t)kN / 32 * kMaxC) + 64;
 }
 
