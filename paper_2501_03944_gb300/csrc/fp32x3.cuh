@@ -10,22 +10,36 @@
 
 namespace mgfwa {
 
-// Tensor maps over the FP32 batch X and over the first-layer weights of a
-// buffer of FP32 rows (row stride ld floats, max_rows rows).
+// The layer's operands as BF16 parts: X's three parts [3][N][d_in], made
+// once (launch_l1_split_x), and the three parts of the W1 blocks of the
+// vectors of one launch [max_rows][3][h1][d_in], made by each launch; tensor
+// maps over both.  rows/ld: the FP32 rows the vectors come from.
 struct L1Plan {
   bool ready = false;
-  CUtensorMap tmap_x;
-  CUtensorMap tmap_w;
+  CUtensorMap tmap_xs;
+  CUtensorMap tmap_ws;
   const float* rows = nullptr;
   int64_t ld = 0;
+  uint32_t* xs = nullptr;
+  uint32_t* ws = nullptr;
+  int64_t max_rows = 0;
 };
 
-// d_in % 4 == 0 and h1 in {32, 64, 128}.
+// d_in % 8 == 0 and h1 in {32, 64, 128}.
 bool l1_fp32x3_supported(const Mlp& mlp);
+
+// 32-bit words of the X parts and of the W1 parts of max_rows vectors (two
+// BF16 per word).
+int64_t l1_fp32x3_x_words(const Mlp& mlp);
+int64_t l1_fp32x3_w_words(const Mlp& mlp, int64_t max_rows);
 
 // False (plan not ready) when unsupported or not on a Blackwell GPU; the
 // callers then use the CUDA-core products.
-bool l1_fp32x3_plan(L1Plan& pl, const Mlp& mlp, const float* rows, int64_t ld, int64_t max_rows);
+bool l1_fp32x3_plan(L1Plan& pl, const Mlp& mlp, const float* rows, int64_t ld, int64_t max_rows, uint32_t* xs,
+                    uint32_t* ws);
+
+// X -> its BF16 parts in the plan's buffer (once, after X is on the device).
+int launch_l1_split_x(const L1Plan& pl, const Mlp& mlp, cudaStream_t s);
 
 // out[r][n][j] = act(X[n] . W1_j + b1_j) of rows idx[r] (or r) of the
 // planned buffer, r < R; FP32-accurate (split BF16 products).  With loss

@@ -17,18 +17,16 @@
 // of them) to a third; the epilogue adds the three in FP32.  That keeps the
 // result within FP32 accuracy for K in the thousands.
 //
-// One CTA per 128-sample tile and 128 / h1 vectors.  Warp 0 issues TMA
-// (FP32 tiles of X and of the vectors' W1, 32 K-elements = one 128-byte
-// swizzle row per stage).  Warps 2..5 split each landed stage: the W1 tile
-// row by row into three BF16 part tiles (64-byte rows, 64-byte swizzle), and
-// the X tile row by row (one sample per thread, its TMEM lane) into a ring
-// of TMEM slots, each holding the three parts of 16 K-elements (two BF16 per
-// 32-bit column).  Warp 1 issues the MMAs with A (the X parts) from TMEM and
-// B (the W1 parts) from shared memory, so the tensor core reads only the
-// narrow operand from shared memory.  Warps 2..5 finally read the
-// accumulators (one sample row per thread), add b1, apply the activation and
-// store the row.  Every wait is bounded; a wait that gives up sets a bit in
-// the status word and the CTA drains its copies and MMAs and returns.
+// The parts are made once per operand by k_split_bf16x3 (X at create, the
+// vectors' W1 blocks before each launch), so the layer itself is a plain
+// TMA -> MMA pipeline.  One CTA per 128-sample tile and 128 / h1 vectors.
+// Warp 0 issues TMA: per stage of 32 K-elements, the three X part tiles
+// [128 samples x 32] and the three W1 part tiles [128 rows x 32] (64-byte
+// rows, 64-byte swizzle).  Warp 1 issues the MMAs, both operands from shared
+// memory.  Warps 2..5 read the accumulators (one sample row per thread),
+// add b1, apply the activation and store the row, or run the fused output
+// layer.  Every wait is bounded; a wait that gives up sets a bit in the
+// status word and the CTA drains its copies and MMAs and returns.
 #include <cuda.h>
 
 #include "fp32x3.cuh"
@@ -39,9 +37,7 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kBKf = 32;           // FP32 K elements per stage (128 bytes)
-constexpr int kSlotK = 16;         // K elements per TMEM slot of the X parts
 constexpr int kMaxStages = 6;
-constexpr int kMaxSlots = 8;
 constexpr int kParts = 3;          // BF16 parts per operand
 constexpr int kThreads = 192;      // warp 0 TMA, warp 1 MMA, warps 2..5 convert + epilogue
 constexpr uint32_t kTmemCols = 512;
@@ -50,8 +46,6 @@ constexpr uint64_t kWaitBudget = 1ull << 32;
 struct Bars {
   uint64_t full[kMaxStages];   // stage landed (TMA)
   uint64_t empty[kMaxStages];  // stage free (its MMAs completed)
-  uint64_t a_full[kMaxSlots];  // slot written (and, for a stage's first slot, the stage's W1 parts split)
-  uint64_t a_empty[kMaxSlots]; // slot free (its MMAs completed)
   uint64_t done;
   uint32_t tmem_base;
   volatile int abort_flag;
@@ -132,20 +126,14 @@ __device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
 __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
-// D (TMEM) (+)= A (TMEM) x B (shared memory), BF16 inputs.
-__device__ __forceinline__ void mma_bf16_ta(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t accum) {
+// D (TMEM) (+)= A x B, both from shared memory, BF16 inputs.
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
-      "r"(a_tmem), "l"(b), "r"(idesc), "r"(accum)
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
       : "memory");
-}
-// 32 lanes x 8 consecutive 32-bit columns.
-__device__ __forceinline__ void tmem_st8u(uint32_t taddr, const uint32_t* v) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
-               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
-               : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* b) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(b))
@@ -173,6 +161,33 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& p1, uint32_t&
   p3 = *reinterpret_cast<const uint32_t*>(&h3);
 }
 
+}  // namespace
+
+// Part p of element pair e (elements 2e, 2e + 1) of source row r -- row
+// idx[r] (or r) of src, elements from `off` -- goes to word
+// dst[r * rstride + p * pstride + e], two BF16 per word.
+__global__ void __launch_bounds__(256) k_split_bf16x3(const float* __restrict__ src, int64_t ld,
+                                                      const int32_t* __restrict__ idx, int32_t rows, int64_t off,
+                                                      int64_t pairs, uint32_t* __restrict__ dst, int64_t rstride,
+                                                      int64_t pstride) {
+  griddep_wait();
+  griddep_launch_dependents();
+  const int64_t total = (int64_t)rows * pairs;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / pairs, e = t - r * pairs;
+    const float2 v =
+        *reinterpret_cast<const float2*>(src + (int64_t)(idx ? idx[r] : r) * ld + off + 2 * e);
+    uint32_t p1, p2, p3;
+    split2(v.x, v.y, p1, p2, p3);
+    uint32_t* d = dst + r * rstride + e;
+    d[0] = p1;
+    d[pstride] = p2;
+    d[2 * pstride] = p3;
+  }
+}
+
+namespace {
+
 struct Args {
   int32_t N;        // samples
   int32_t d_in;
@@ -196,59 +211,42 @@ struct Args {
 // Each CTA takes V = 128 / H vectors, so that every MMA is M=128, N=128:
 // the tensor core's cost per instruction barely depends on N at these
 // widths, so fewer, wider products are the faster way through the six.
-// Shared memory per stage: the FP32 X tile, the FP32 tile of the V stacked
-// W1 blocks (128 rows) and its three BF16 parts (128 rows x 64 bytes each).
-// TMEM: the accumulators (main even, main odd, corrections: 3 x 128 columns)
-// and then the X slots: one K step of 16, 3 parts x 8 columns (two BF16 per
-// 32-bit column).
+// Shared memory per stage: the three X part tiles and the three part tiles
+// of the V stacked W1 blocks, 128 rows x 64 bytes each.  TMEM: the
+// accumulators (main even, main odd, corrections: 3 x 128 columns).
 constexpr int kN = 128;
 constexpr int kMaxC = 32;           // classes of a fused output layer
-constexpr int kStages = 3;
-constexpr int kSlots = 4;
-constexpr uint32_t kABytes = kBM * 128;
-constexpr uint32_t kBBytes = kN * 128;     // FP32 W1 tile of a stage
-constexpr uint32_t kBhBytes = kN * 64;     // one BF16 part of it
-constexpr uint32_t kPartCols = kSlotK / 2;
-constexpr uint32_t kSlotCols = kParts * kPartCols;
-constexpr uint32_t kSlot0 = 3 * kN;  // first TMEM column of the X slots
-static_assert(kSlot0 + kSlots * kSlotCols <= kTmemCols, "accumulators and X slots fit in TMEM");
-static_assert(kStages <= kMaxStages && kSlots <= kMaxSlots, "barrier arrays");
-static_assert(kBKf == 2 * kSlotK, "two slots per stage");
+constexpr int kStages = 4;
+constexpr uint32_t kPartBytes = 128 * 64;  // one part tile of a stage (X or W1)
+constexpr uint32_t kStageBytes = 2 * kParts * kPartBytes;
+static_assert(3 * kN <= kTmemCols, "accumulators fit in TMEM");
+static_assert(kStages <= kMaxStages, "barrier arrays");
 
 // NL: register slots for the logits of a fused output layer (C <= NL).
 template <int H, int NL>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_l1_fp32x3(const __grid_constant__ CUtensorMap tmap_x, const __grid_constant__ CUtensorMap tmap_w, Args a) {
+    k_l1_fp32x3(const __grid_constant__ CUtensorMap tmap_xs, const __grid_constant__ CUtensorMap tmap_ws, Args a) {
   griddep_wait();
   griddep_launch_dependents();
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   constexpr int V = kN / H;
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  // X tile of stage s at base + s * kABytes; part p of the W1 tiles of stage s after all X tiles
-  uint8_t* b_f32 = base + (size_t)kStages * kABytes;
-  uint8_t* b_half = b_f32 + (size_t)kStages * kBBytes;
-  auto A = [&](int s) { return base + (size_t)s * kABytes; };
-  auto Bf = [&](int s) { return b_f32 + (size_t)s * kBBytes; };
-  auto Bh = [&](int p, int s) { return b_half + ((size_t)p * kStages + s) * kBhBytes; };
-  Bars* sb = reinterpret_cast<Bars*>(b_half + (size_t)kParts * kStages * kBhBytes);
+  // part p of stage s: X at base + (s * 2 + 0) * 3 parts, W1 at (s * 2 + 1) * 3 parts
+  auto Xp = [&](int p, int s) { return base + ((size_t)s * 2 * kParts + p) * kPartBytes; };
+  auto Wp = [&](int p, int s) { return base + ((size_t)s * 2 * kParts + kParts + p) * kPartBytes; };
+  Bars* sb = reinterpret_cast<Bars*>(base + (size_t)kStages * kStageBytes);
   float* w2s = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(sb) + ((sizeof(Bars) + 15) & ~size_t(15)));
   float* b2s = w2s + (size_t)V * kMaxC * H;  // fused output layer: W2 [V][C][H], b2 [V][C] of the CTA's vectors
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int mt = blockIdx.x, r0 = blockIdx.y * V;
   // vector v of this CTA: r0 + v, or (past the last vector) the last one again, computed and not stored
-  auto row_of = [&](int v) {
-    const int r = r0 + v < a.R ? r0 + v : a.R - 1;
-    return a.idx ? a.idx[r] : r;
-  };
+  auto vec_of = [&](int v) { return r0 + v < a.R ? r0 + v : a.R - 1; };
+  auto row_of = [&](int v) { return a.idx ? a.idx[vec_of(v)] : vec_of(v); };
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&sb->full[s], 1);
       mbar_init(&sb->empty[s], 1);
-    }
-    for (int j = 0; j < kSlots; ++j) {
-      mbar_init(&sb->a_full[j], 4);
-      mbar_init(&sb->a_empty[j], 1);
     }
     mbar_init(&sb->done, 1);
     sb->abort_flag = 0;
@@ -268,19 +266,22 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      int rows[V];
+      int vz[V];
 #pragma unroll
-      for (int v = 0; v < V; ++v) rows[v] = row_of(v);
+      for (int v = 0; v < V; ++v) vz[v] = vec_of(v) * kParts;  // the vector's first part in the W1 part buffer
       int kb = 0;
       for (; kb < a.k_blocks; ++kb) {
         const int s = kb % kStages;
         const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
         if (!mbar_wait(sb, &sb->empty[s], ph ^ 1u, a.status, 1u)) break;
-        mbar_expect_tx(&sb->full[s], kABytes + kBBytes);
-        tma_2d(A(s), &tmap_x, kb * kBKf, mt * kBM, &sb->full[s]);
+        mbar_expect_tx(&sb->full[s], kStageBytes);
 #pragma unroll
-        for (int v = 0; v < V; ++v)
-          tma_3d(Bf(s) + (size_t)v * H * 128, &tmap_w, kb * kBKf, 0, rows[v], &sb->full[s]);
+        for (int p = 0; p < kParts; ++p) {
+          tma_3d(Xp(p, s), &tmap_xs, kb * kBKf, mt * kBM, p, &sb->full[s]);
+#pragma unroll
+          for (int v = 0; v < V; ++v)
+            tma_3d(Wp(p, s) + (size_t)v * H * 64, &tmap_ws, kb * kBKf, 0, vz[v] + p, &sb->full[s]);
+        }
       }
       // every issued copy lands before the CTA may exit
       for (int j = kb - kStages > 0 ? kb - kStages : 0; j < kb; ++j)
@@ -290,33 +291,27 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(kBM, kN);
       int kb = 0;
-      bool ok = true;
-      for (; kb < a.k_blocks && ok; ++kb) {
+      for (; kb < a.k_blocks; ++kb) {
         const int s = kb % kStages;
-        const uint32_t b1 = smem_u32(Bh(0, s)), b2 = smem_u32(Bh(1, s)), b3 = smem_u32(Bh(2, s));
+        const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
+        if (!mbar_wait(sb, &sb->full[s], ph, a.status, 2u)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t x1 = smem_u32(Xp(0, s)), x2 = smem_u32(Xp(1, s)), x3 = smem_u32(Xp(2, s));
+        const uint32_t w1 = smem_u32(Wp(0, s)), w2 = smem_u32(Wp(1, s)), w3 = smem_u32(Wp(2, s));
         const uint32_t d_main = tmem + (uint32_t)((kb & 1) * kN), d_corr = tmem + (uint32_t)(2 * kN);
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-          const int hk = 2 * kb + j;  // slot use number
-          const int slot = hk % kSlots;
-          if (!mbar_wait(sb, &sb->a_full[slot], (uint32_t)(hk / kSlots) & 1u, a.status, 2u)) {
-            ok = false;
-            break;
-          }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t a1 = tmem + kSlot0 + (uint32_t)slot * kSlotCols, a2 = a1 + kPartCols, a3 = a2 + kPartCols;
-          const uint32_t o = (uint32_t)j * 32u;  // byte offset of this K step (16 BF16) in a 64-byte W1 row
+          const uint32_t o = (uint32_t)j * 32u;  // byte offset of this K step (16 BF16) in a 64-byte row
           const uint32_t first = (kb < 2 && j == 0) ? 0u : 1u;     // this main accumulator's first product
           const uint32_t first_c = (kb == 0 && j == 0) ? 0u : 1u;  // the corrections' first
-          mma_bf16_ta(d_main, a1, smem_desc_sw64(b1 + o), idesc, first);
-          mma_bf16_ta(d_corr, a1, smem_desc_sw64(b2 + o), idesc, first_c);
-          mma_bf16_ta(d_corr, a2, smem_desc_sw64(b1 + o), idesc, 1u);
-          mma_bf16_ta(d_corr, a2, smem_desc_sw64(b2 + o), idesc, 1u);
-          mma_bf16_ta(d_corr, a1, smem_desc_sw64(b3 + o), idesc, 1u);
-          mma_bf16_ta(d_corr, a3, smem_desc_sw64(b1 + o), idesc, 1u);
-          mma_commit(&sb->a_empty[slot]);
+          mma_bf16(d_main, smem_desc_sw64(x1 + o), smem_desc_sw64(w1 + o), idesc, first);
+          mma_bf16(d_corr, smem_desc_sw64(x1 + o), smem_desc_sw64(w2 + o), idesc, first_c);
+          mma_bf16(d_corr, smem_desc_sw64(x2 + o), smem_desc_sw64(w1 + o), idesc, 1u);
+          mma_bf16(d_corr, smem_desc_sw64(x2 + o), smem_desc_sw64(w2 + o), idesc, 1u);
+          mma_bf16(d_corr, smem_desc_sw64(x1 + o), smem_desc_sw64(w3 + o), idesc, 1u);
+          mma_bf16(d_corr, smem_desc_sw64(x3 + o), smem_desc_sw64(w1 + o), idesc, 1u);
         }
-        if (ok) mma_commit(&sb->empty[s]);
+        mma_commit(&sb->empty[s]);
       }
       mma_commit(&sb->done);  // after every issued MMA (also on abort)
     }
@@ -337,64 +332,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         b2s[e] = a.rows[(int64_t)row_of(v) * a.ld + a.b2_off + (e - v * a.C)];
       }
     }
-    bool ok = true;
-    for (int kb = 0; kb < a.k_blocks && ok; ++kb) {
-      const int s = kb % kStages;
-      const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
-      ok = mbar_wait(sb, &sb->full[s], ph, a.status, 4u);
-      if (!ok) break;
-      // W1 row ct -> its three BF16 parts, each a 64-byte row with 16-byte chunk c at c ^ ((row / 2) & 3)
-      // (64-byte swizzle; the part buffers are free: the stage's MMAs of its last use completed)
-      {
-        const uint8_t* wrow = Bf(s) + ct * 128;
-        uint32_t w1[16], w2[16], w3[16];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const float4 v = *reinterpret_cast<const float4*>(wrow + ((c ^ (ct & 7)) << 4));
-          split2(v.x, v.y, w1[2 * c], w2[2 * c], w3[2 * c]);
-          split2(v.z, v.w, w1[2 * c + 1], w2[2 * c + 1], w3[2 * c + 1]);
-        }
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int off = ct * 64 + ((c ^ ((ct >> 1) & 3)) << 4);
-          *reinterpret_cast<uint4*>(Bh(0, s) + off) = make_uint4(w1[4 * c], w1[4 * c + 1], w1[4 * c + 2], w1[4 * c + 3]);
-          *reinterpret_cast<uint4*>(Bh(1, s) + off) = make_uint4(w2[4 * c], w2[4 * c + 1], w2[4 * c + 2], w2[4 * c + 3]);
-          *reinterpret_cast<uint4*>(Bh(2, s) + off) = make_uint4(w3[4 * c], w3[4 * c + 1], w3[4 * c + 2], w3[4 * c + 3]);
-        }
-      }
-      // generic-proxy writes become visible to the tensor core's (async proxy) reads
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      const uint8_t* xrow = A(s) + rrow * 128;
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const int hk = 2 * kb + j;
-        const int slot = hk % kSlots;
-        // 16 K-elements of this sample: 16-byte chunks 4j..4j+3 of its row, at chunk c ^ (row & 7) (128-byte swizzle)
-        uint32_t x1[8], x2[8], x3[8];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const float4 v = *reinterpret_cast<const float4*>(xrow + (((4 * j + c) ^ (rrow & 7)) << 4));
-          split2(v.x, v.y, x1[2 * c], x2[2 * c], x3[2 * c]);
-          split2(v.z, v.w, x1[2 * c + 1], x2[2 * c + 1], x3[2 * c + 1]);
-        }
-        ok = mbar_wait(sb, &sb->a_empty[slot], ((uint32_t)(hk / kSlots) & 1u) ^ 1u, a.status, 8u);
-        if (!ok) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t xa = lanes + kSlot0 + (uint32_t)slot * kSlotCols;
-        tmem_st8u(xa, x1);
-        tmem_st8u(xa + kPartCols, x2);
-        tmem_st8u(xa + 2 * kPartCols, x3);
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&sb->a_full[slot]);
-      }
-    }
     // epilogue: row = this thread's TMEM lane; columns [v H, (v + 1) H) are vector r0 + v
     mbar_drain(&sb->done, 0u, a.status);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int64_t n = (int64_t)mt * kBM + rrow;
-    const bool valid = ok && !sb->abort_flag && n < a.N;
+    const bool valid = !sb->abort_flag && n < a.N;
     const bool odd = a.k_blocks > 1;  // the odd-block accumulator holds products
     if (fused) {
       asm volatile("bar.sync 1, 128;" ::: "memory");  // W2, b2 staged by all four warps
@@ -527,18 +469,19 @@ EncodeTiled encoder() {
   return fn;
 }
 
-bool encode(CUtensorMap* map, uint32_t rank, const void* ptr, const cuuint64_t* dims, const cuuint64_t* strides,
-            const cuuint32_t* box) {
+// BF16 part tiles: 32 K-elements (64 bytes) per row, 64-byte swizzle.
+bool encode_bf16(CUtensorMap* map, const void* ptr, const cuuint64_t* dims, const cuuint64_t* strides,
+                 const cuuint32_t* box) {
   EncodeTiled enc = encoder();
   if (!enc) return false;
   cuuint32_t estr[3] = {1, 1, 1};
-  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<void*>(ptr), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(ptr), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 size_t smem_bytes() {
-  return 1024 + (size_t)kStages * (kABytes + kBBytes + (size_t)kParts * kBhBytes) + ((sizeof(Bars) + 15) & ~size_t(15)) +
+  return 1024 + (size_t)kStages * kStageBytes + ((sizeof(Bars) + 15) & ~size_t(15)) +
          sizeof(float) * ((size_t)kN * kMaxC + (size_t)kN / 32 * kMaxC) + 64;
 }
 
@@ -548,7 +491,7 @@ cudaError_t go_nl(const L1Plan& pl, const Args& a, int R, cudaStream_t s, bool p
   if (e != cudaSuccess || prep) return e;
   constexpr int V = kN / H;
   const dim3 grid((unsigned)((a.N + kBM - 1) / kBM), (unsigned)((R + V - 1) / V));
-  return launch_pdl(k_l1_fp32x3<H, NL>, grid, dim3(kThreads), smem_bytes(), s, pl.tmap_x, pl.tmap_w, a);
+  return launch_pdl(k_l1_fp32x3<H, NL>, grid, dim3(kThreads), smem_bytes(), s, pl.tmap_xs, pl.tmap_ws, a);
 }
 
 template <int H>
@@ -560,38 +503,59 @@ cudaError_t go(const L1Plan& pl, const Args& a, int R, cudaStream_t s, bool prep
   return a.loss && a.C > 16 ? go_nl<H, 32>(pl, a, R, s, false) : go_nl<H, 16>(pl, a, R, s, false);
 }
 
+int split_launch(const float* src, int64_t ld, const int32_t* idx, int32_t rows, int64_t off, int64_t pairs,
+                 uint32_t* dst, int64_t rstride, int64_t pstride, cudaStream_t s) {
+  const int64_t total = (int64_t)rows * pairs;
+  const int64_t blocks = (total + 255) / 256;
+  const unsigned grid = (unsigned)(blocks < 4096 ? (blocks < 1 ? 1 : blocks) : 4096);
+  return launch_pdl(k_split_bf16x3, dim3(grid), dim3(256), 0, s, src, ld, idx, rows, off, pairs, dst, rstride,
+                    pstride) == cudaSuccess
+             ? 1
+             : -1;
+}
+
 }  // namespace
 
 bool l1_fp32x3_supported(const Mlp& mlp) {
   const int h1 = mlp.widths[1];
-  return mlp.widths[0] % 4 == 0 && (h1 == 32 || h1 == 64 || h1 == 128);
+  return mlp.widths[0] % 8 == 0 && (h1 == 32 || h1 == 64 || h1 == 128);
 }
 
-bool l1_fp32x3_plan(L1Plan& pl, const Mlp& mlp, const float* rows, int64_t ld, int64_t max_rows) {
+int64_t l1_fp32x3_x_words(const Mlp& mlp) { return 3 * mlp.N * (mlp.widths[0] / 2); }
+int64_t l1_fp32x3_w_words(const Mlp& mlp, int64_t max_rows) {
+  return 3 * max_rows * (int64_t)mlp.widths[1] * (mlp.widths[0] / 2);
+}
+
+bool l1_fp32x3_plan(L1Plan& pl, const Mlp& mlp, const float* rows, int64_t ld, int64_t max_rows, uint32_t* xs,
+                    uint32_t* ws) {
   pl = L1Plan();
-  if (!l1_fp32x3_supported(mlp)) return false;
+  if (!l1_fp32x3_supported(mlp) || !xs || !ws) return false;
   int dev = 0;
   cudaDeviceProp prop;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess || prop.major != 10) {
     cudaGetLastError();
     return false;
   }
-  const int d_in = mlp.widths[0], h1 = mlp.widths[1];
+  const int64_t d_in = mlp.widths[0], h1 = mlp.widths[1];
   {
-    cuuint64_t dims[2] = {(cuuint64_t)d_in, (cuuint64_t)mlp.N};
-    cuuint64_t strides[1] = {(cuuint64_t)d_in * 4};
-    cuuint32_t box[2] = {kBKf, kBM};
-    if (!encode(&pl.tmap_x, 2, mlp.X, dims, strides, box)) return false;
+    // X parts [3][N][d_in] BF16, box 32 x 128 x 1
+    cuuint64_t dims[3] = {(cuuint64_t)d_in, (cuuint64_t)mlp.N, 3};
+    cuuint64_t strides[2] = {(cuuint64_t)d_in * 2, (cuuint64_t)(mlp.N * d_in * 2)};
+    cuuint32_t box[3] = {kBKf, kBM, 1};
+    if (!encode_bf16(&pl.tmap_xs, xs, dims, strides, box)) return false;
   }
   {
-    // W1 of every spark row: [max_rows][h1][d_in], box 32 x h1 x 1
-    cuuint64_t dims[3] = {(cuuint64_t)d_in, (cuuint64_t)h1, (cuuint64_t)max_rows};
-    cuuint64_t strides[2] = {(cuuint64_t)d_in * 4, (cuuint64_t)ld * 4};
+    // W1 parts of the launch's vectors [max_rows][3][h1][d_in] BF16, box 32 x h1 x 1
+    cuuint64_t dims[3] = {(cuuint64_t)d_in, (cuuint64_t)h1, (cuuint64_t)(3 * max_rows)};
+    cuuint64_t strides[2] = {(cuuint64_t)d_in * 2, (cuuint64_t)(h1 * d_in * 2)};
     cuuint32_t box[3] = {kBKf, (cuuint32_t)h1, 1};
-    if (!encode(&pl.tmap_w, 3, rows + mlp.w_off[0], dims, strides, box)) return false;
+    if (!encode_bf16(&pl.tmap_ws, ws, dims, strides, box)) return false;
   }
   pl.rows = rows;
   pl.ld = ld;
+  pl.xs = xs;
+  pl.ws = ws;
+  pl.max_rows = max_rows;
   pl.ready = true;
   Args a = {};
   const bool prep_ok = (h1 == 32 ? go<32>(pl, a, 0, nullptr, true)
@@ -604,11 +568,18 @@ bool l1_fp32x3_plan(L1Plan& pl, const Mlp& mlp, const float* rows, int64_t ld, i
   return pl.ready;
 }
 
+int launch_l1_split_x(const L1Plan& pl, const Mlp& mlp, cudaStream_t s) {
+  if (!pl.ready) return 0;
+  const int64_t pairs = mlp.widths[0] / 2;
+  return split_launch(mlp.X, mlp.widths[0], nullptr, (int32_t)mlp.N, 0, pairs, pl.xs, pairs, mlp.N * pairs, s);
+}
+
 bool l1_fp32x3_fuses_output(const Mlp& mlp) { return mlp.n_layers == 2 && mlp.widths[2] <= kMaxC; }
 
 int launch_l1_fp32x3(const L1Plan& pl, const Mlp& mlp, const int32_t* idx, int32_t R, float* out,
                      uint32_t* status, cudaStream_t s, float* loss) {
   if (!pl.ready || R <= 0) return R <= 0 ? 0 : -1;
+  if (R > pl.max_rows) return -1;
   Args a;
   a.N = (int32_t)mlp.N;
   a.d_in = mlp.widths[0];
@@ -630,6 +601,9 @@ int launch_l1_fp32x3(const L1Plan& pl, const Mlp& mlp, const int32_t* idx, int32
     a.C = mlp.widths[2];
     a.y = mlp.y;
   }
+  // the launch's W1 blocks -> their BF16 parts [R][3][h1][d_in]
+  const int64_t pairs = (int64_t)mlp.widths[1] * (mlp.widths[0] / 2);
+  if (split_launch(pl.rows, pl.ld, idx, R, mlp.w_off[0], pairs, pl.ws, 3 * pairs, pairs, s) < 0) return -1;
   cudaError_t e;
   switch (mlp.widths[1]) {
     case 32: e = go<32>(pl, a, R, s, false); break;
@@ -637,7 +611,7 @@ int launch_l1_fp32x3(const L1Plan& pl, const Mlp& mlp, const int32_t* idx, int32
     case 128: e = go<128>(pl, a, R, s, false); break;
     default: return -1;
   }
-  return e == cudaSuccess ? 1 : -1;
+  return e == cudaSuccess ? 2 : -1;
 }
 
 }  // namespace mgfwa

@@ -60,6 +60,9 @@ struct mgfwa_handle {
   float* rescore_scratch = nullptr;
   L1Plan rescore_l1;            // their first layer on the tensor cores (over the spark rows)
   L1Plan refine_l1;             // the refinement's first layer on the tensor cores (over its rows)
+  uint32_t* l1_xs = nullptr;    // X as three BF16 parts, for both (when the shape allows the layer)
+  uint32_t* rescore_ws = nullptr;  // the re-scored rows' W1 parts
+  uint32_t* refine_ws = nullptr;   // the refined rows' W1 parts
   float* best_x = nullptr;
   float* best_f = nullptr;
   double* ce64 = nullptr;
@@ -692,6 +695,11 @@ size_t carve_all(mgfwa_t* h, char* base) {
   h->elite = carve<int32_t>(cur, F * (cfg->elite_rescore > 0 ? cfg->elite_rescore : 1));
   const bool rescore = want_op && cfg->elite_rescore > 0;
   h->rescore_scratch = rescore ? carve<float>(cur, (size_t)h->rescore_plan.floats) : nullptr;
+  // the FP32-accurate tensor-core first layer's BF16 operand parts (sized by shape, whatever the device)
+  const bool l1 = (rescore || h->refine) && h->kind == MGFWA_OBJ_MLP_CE && l1_fp32x3_supported(mlp);
+  h->l1_xs = l1 ? carve<uint32_t>(cur, (size_t)l1_fp32x3_x_words(mlp)) : nullptr;
+  h->rescore_ws = l1 && rescore ? carve<uint32_t>(cur, (size_t)l1_fp32x3_w_words(mlp, h->rescore_plan.R)) : nullptr;
+  h->refine_ws = l1 && h->refine ? carve<uint32_t>(cur, (size_t)l1_fp32x3_w_words(mlp, p.B)) : nullptr;
   h->best_x = carve<float>(cur, (int64_t)p.B * p.Dp);
   h->best_f = carve<float>(cur, p.B);
   h->ce64 = carve<double>(cur, N > 0 ? N : 1);
@@ -825,8 +833,12 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
   }
   // the FP32-accurate first layer of the elite re-score and of the refinement on the tensor cores
   // (where the shape allows; otherwise they keep the CUDA-core products)
-  if (h->rescore_scratch) l1_fp32x3_plan(h->rescore_l1, h->mlp, h->sparks, p.Dp, h->PA);
-  if (h->refine) l1_fp32x3_plan(h->refine_l1, h->mlp, h->rw, p.Dp, p.B);
+  if (h->rescore_ws)
+    l1_fp32x3_plan(h->rescore_l1, h->mlp, h->sparks, p.Dp, h->rescore_plan.R, h->l1_xs, h->rescore_ws);
+  if (h->refine_ws) l1_fp32x3_plan(h->refine_l1, h->mlp, h->rw, p.Dp, p.B, h->l1_xs, h->refine_ws);
+  if (h->rescore_l1.ready || h->refine_l1.ready)
+    CREATE_LAUNCH(launch_l1_split_x(h->rescore_l1.ready ? h->rescore_l1 : h->refine_l1, h->mlp, h->stream),
+                  "X parts");
   TRACE("create: batch copied");
   // Algorithm 1, init: mu fireworks uniform in the box, evaluated.
   CREATE_LAUNCH(launch_init(p, h->fw_x, h->fw_amp, h->stream), "init");
