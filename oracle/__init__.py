@@ -49,7 +49,7 @@ class Params(ctypes.Structure):
                 ("mu", ctypes.c_int32), ("lam", ctypes.c_int32), ("m", ctypes.c_int32),
                 ("k", ctypes.c_int32), ("beta", ctypes.c_float), ("amp0", ctypes.c_float),
                 ("c_a", ctypes.c_float), ("c_r", ctypes.c_float), ("refine_every", ctypes.c_int32),
-                ("refine_steps", ctypes.c_int32), ("refine_lr", ctypes.c_float)]
+                ("refine_steps", ctypes.c_int32), ("refine_lr", ctypes.c_float), ("loser_out", ctypes.c_int32)]
 
 
 class Objective(ctypes.Structure):
@@ -86,6 +86,8 @@ def lib():
             L.orc_rank.argtypes = [pp, f32p, i32p, i32p]
             L.orc_guide.argtypes = [pp, ctypes.c_uint64, ctypes.c_uint32, f32p, f32p, f32p, i32p, i32p, f32p]
             L.orc_select.argtypes = [pp, f32p, f32p, f32p, f32p, f32p, f32p, f32p, i32p]
+            L.orc_loser_out.argtypes = [pp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32, ctypes.c_float, f32p,
+                                        f32p, f32p, f32p, i32p]
             L.orc_run.argtypes = [pp, op, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                   f32p, f64p, i64p, i32p, f32p]
             L.orc_run.restype = ctypes.c_int32
@@ -120,12 +122,13 @@ def subset_size(sigma: float, g: int) -> int:
 
 
 def make_params(dim, lb, ub, mu, lam, m, sigma=0.2, k=None, beta=1.0, amp0=None, c_a=1.2, c_r=0.9,
-                refine_every=0, refine_steps=0, refine_lr=0.0) -> Params:
+                refine_every=0, refine_steps=0, refine_lr=0.0, loser_out=0) -> Params:
     if k is None:
         k = subset_size(sigma, lam // m)
     if amp0 is None:
         amp0 = float(np.float32(ub) - np.float32(lb))
-    return Params(dim, lb, ub, mu, lam, m, k, beta, amp0, c_a, c_r, refine_every, refine_steps, refine_lr)
+    return Params(dim, lb, ub, mu, lam, m, k, beta, amp0, c_a, c_r, refine_every, refine_steps, refine_lr,
+                  loser_out)
 
 
 def params_for(w, **over) -> Params:
@@ -224,6 +227,24 @@ def select(p: Params, fit_e, fit_g, sparks, guides, fw_x, fw_amp, fw_f):
     return fw_x, fw_amp, fw_f, win
 
 
+def loser_out(p: Params, seed: int, gen: int, g_rem: int, run_best: float, f_old, fw_x, fw_amp, fw_f):
+    """The loser-out tournament after a selection: returns updated copies (fw_x, fw_amp, fw_f, loser)."""
+    f_old = np.ascontiguousarray(f_old, np.float32)
+    fw_x = np.array(fw_x, np.float32, copy=True)
+    fw_amp = np.array(fw_amp, np.float32, copy=True)
+    fw_f = np.array(fw_f, np.float32, copy=True)
+    lo = np.zeros(p.mu, np.int32)
+    lib().orc_loser_out(ctypes.byref(p), seed, gen, g_rem, float(run_best), _p(f_old, ctypes.c_float),
+                        _p(fw_x, ctypes.c_float), _p(fw_amp, ctypes.c_float), _p(fw_f, ctypes.c_float),
+                        _p(lo, ctypes.c_int32))
+    return fw_x, fw_amp, fw_f, lo
+
+
+def g_max(p: Params, budget: int) -> int:
+    """Generations the budget allows at mu (lam + m) evaluations each, after the mu initial ones."""
+    return max(0, (budget - p.mu) // (p.mu * (p.lam + p.m)))
+
+
 def run(p: Params, prob: Problem, seed: int, budget: int, max_gens: int = 1 << 30,
         n_threads: int = 1, want_trace: bool = False):
     """A whole oracle run.  Returns dict(best_x, best_f, evals, gens, trace)."""
@@ -266,8 +287,11 @@ def refine_cost(p: Params) -> int:
     return int(lib().orc_refine_cost(ctypes.byref(p)))
 
 
-def generation(p: Params, prob: Problem, seed: int, gen: int, fw_x, fw_amp, fw_f, n_threads: int = 1):
-    """One oracle generation, returning every intermediate (for step-by-step parity)."""
+def generation(p: Params, prob: Problem, seed: int, gen: int, fw_x, fw_amp, fw_f, n_threads: int = 1,
+               run_best=None, g_rem=None):
+    """One oracle generation, returning every intermediate (for step-by-step parity).  With the loser-out
+    tournament on (p.loser_out), run_best (the run's best-so-far before this generation) and g_rem (the
+    generations the budget allows after this one) are needed."""
     sparks = explode(p, seed, gen, fw_x, fw_amp)
     fit_e64 = prob.fitness_many(sparks, n_threads)
     fit_e = fit_e64.astype(np.float32)
@@ -276,8 +300,21 @@ def generation(p: Params, prob: Problem, seed: int, gen: int, fw_x, fw_amp, fw_f
     fit_g64 = prob.fitness_many(guides, n_threads)
     fit_g = fit_g64.astype(np.float32)
     nx, na, nf, win = select(p, fit_e, fit_g, sparks, guides, fw_x, fw_amp, fw_f)
-    return dict(sparks=sparks, fit_e64=fit_e64, fit_e=fit_e, top=top, bottom=bot, guides=guides,
-                fit_g64=fit_g64, fit_g=fit_g, fw_x=nx, fw_amp=na, fw_f=nf, winner=win)
+    out = dict(sparks=sparks, fit_e64=fit_e64, fit_e=fit_e, top=top, bottom=bot, guides=guides,
+               fit_g64=fit_g64, fit_g=fit_g, fw_x=nx, fw_amp=na, fw_f=nf, winner=win)
+    if p.loser_out:
+        rb = np.float32(run_best)
+        for f in nf:
+            if _key(f) < _key(rb):
+                rb = f
+        out["run_best"] = rb
+        out["fw_x"], out["fw_amp"], out["fw_f"], out["loser"] = loser_out(p, seed, gen, g_rem, rb,
+                                                                          np.asarray(fw_f, np.float32), nx, na, nf)
+    return out
+
+
+def _key(f) -> float:
+    return float("inf") if np.isnan(f) else float(f)
 
 
 # ---------------------------------------------------------------------------

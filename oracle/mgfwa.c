@@ -194,6 +194,28 @@ void orc_select(const orc_params* p, const float* fit_e, const float* fit_g, con
   }
 }
 
+void orc_loser_out(const orc_params* p, uint64_t seed, uint32_t gen, int32_t g_rem, float run_best,
+                   const float* f_old, float* fw_x, float* fw_amp, float* fw_f, int32_t* loser) {
+  int32_t e = 0;
+  for (int32_t i = 1; i < p->mu; ++i)
+    if (key(fw_f[i]) < key(fw_f[e])) e = i;
+  const float width = p->ub - p->lb;
+  for (int32_t i = 0; i < p->mu; ++i) {
+    loser[i] = 0;
+    if (i == e || !isfinite(f_old[i]) || !isfinite(fw_f[i])) continue;
+    const float improvement = f_old[i] - fw_f[i];
+    const float proj = fmaf(-improvement, (float)g_rem, fw_f[i]);
+    if (!(proj > run_best)) continue;
+    loser[i] = 1;
+    for (int64_t d = 0; d < p->dim; ++d) {
+      const float u = orc_uniform(seed, ORC_LOSER, gen, (uint32_t)i, d);
+      fw_x[(int64_t)i * p->dim + d] = fmaf(u, width, p->lb);
+    }
+    fw_amp[i] = p->amp0;
+    fw_f[i] = INFINITY;
+  }
+}
+
 static void eval_f32(const orc_objective* obj, const float* xs, int64_t count, int64_t stride,
                      float* out, int32_t n_threads) {
   double* tmp = (double*)malloc(sizeof(double) * (size_t)count);
@@ -244,6 +266,8 @@ int32_t orc_run(const orc_params* p, const orc_objective* obj, uint64_t seed, in
   int32_t* top = (int32_t*)malloc(sizeof(int32_t) * (size_t)(p->mu * p->m * p->k));
   int32_t* bottom = (int32_t*)malloc(sizeof(int32_t) * (size_t)(p->mu * p->m * p->k));
   int32_t* winner = (int32_t*)malloc(sizeof(int32_t) * (size_t)p->mu);
+  float* f_old = (float*)malloc(sizeof(float) * (size_t)p->mu);
+  int32_t* loser = (int32_t*)malloc(sizeof(int32_t) * (size_t)p->mu);
 
   orc_init(p, seed, fw_x, fw_amp);
   eval_f32(obj, fw_x, p->mu, D, fw_f, n_threads);
@@ -255,6 +279,8 @@ int32_t orc_run(const orc_params* p, const orc_objective* obj, uint64_t seed, in
   memcpy(best_x, fw_x + (int64_t)best_i * D, sizeof(float) * (size_t)D);
 
   const int64_t per_gen = (int64_t)p->mu * (p->lam + p->m);
+  /* the generations the budget allows at per_gen evaluations each (refinement not counted) */
+  const int64_t g_max = (budget - p->mu) / per_gen;
   int32_t gen = 0;
   float* refined = (float*)malloc(sizeof(float) * (size_t)D);
   while (gen < max_gens && evals + per_gen + (refine_due(p, gen + 1) ? orc_refine_cost(p) : 0) <= budget) {
@@ -264,6 +290,7 @@ int32_t orc_run(const orc_params* p, const orc_objective* obj, uint64_t seed, in
     orc_rank(p, fit_e, top, bottom);
     orc_guide(p, seed, (uint32_t)gen, fw_x, fw_amp, sparks, top, bottom, guides);
     eval_f32(obj, guides, (int64_t)p->mu * p->m, D, fit_g, n_threads);
+    memcpy(f_old, fw_f, sizeof(float) * (size_t)p->mu);
     orc_select(p, fit_e, fit_g, sparks, guides, fw_x, fw_amp, fw_f, winner);
     evals += per_gen;
     for (int32_t i = 0; i < p->mu; ++i) {
@@ -271,6 +298,10 @@ int32_t orc_run(const orc_params* p, const orc_objective* obj, uint64_t seed, in
         run_best = fw_f[i];
         memcpy(best_x, fw_x + (int64_t)i * D, sizeof(float) * (size_t)D);
       }
+    }
+    if (p->loser_out) {
+      const int64_t g_rem = g_max - gen > 0 ? g_max - gen : 0;
+      orc_loser_out(p, seed, (uint32_t)gen, (int32_t)g_rem, run_best, f_old, fw_x, fw_amp, fw_f, loser);
     }
     if (refine_due(p, gen)) {
       /* refine the run's elite firework (first minimum); keep the result
@@ -297,6 +328,6 @@ int32_t orc_run(const orc_params* p, const orc_objective* obj, uint64_t seed, in
   *gens_out = gen;
 
   free(fw_x); free(fw_amp); free(fw_f); free(sparks); free(guides);
-  free(fit_e); free(fit_g); free(top); free(bottom); free(winner); free(refined);
+  free(fit_e); free(fit_g); free(top); free(bottom); free(winner); free(refined); free(f_old); free(loser);
   return 0;
 }

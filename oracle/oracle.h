@@ -30,7 +30,7 @@ extern "C" {
 #endif
 
 /* Philox stream purposes (the fourth counter word). */
-enum { ORC_INIT = 0, ORC_EXPLODE = 1, ORC_MAP = 2, ORC_GMAP = 3 };
+enum { ORC_INIT = 0, ORC_EXPLODE = 1, ORC_MAP = 2, ORC_GMAP = 3, ORC_LOSER = 4 };
 
 /* Objective kinds and hidden activations. */
 enum { ORC_MLP_CE = 0, ORC_SPHERE = 1 };
@@ -50,6 +50,8 @@ typedef struct {
   int32_t refine_every;  /* T: after the selection of every T-th generation */
   int32_t refine_steps;  /* T_g projected gradient steps */
   float refine_lr;       /* eta */
+  /* loser-out tournament after each selection (0 = off); see orc_loser_out */
+  int32_t loser_out;
 } orc_params;
 
 typedef struct {
@@ -103,6 +105,23 @@ void orc_guide(const orc_params* p, uint64_t seed, uint32_t gen, const float* fw
                const int32_t* bottom, float* guides);
 void orc_select(const orc_params* p, const float* fit_e, const float* fit_g, const float* sparks,
                 const float* guides, float* fw_x, float* fw_amp, float* fw_f, int32_t* winner);
+
+/*
+ * Loser-out tournament (Algorithm 1, last step of the loop; reading C-R15):
+ * after the selection of generation `gen` and the run's best-so-far update
+ * (run_best), every firework i except the run's best one (the first
+ * minimum of fw_f) whose fitness before the selection, f_old[i], and after
+ * it, fw_f[i], are both finite is projected forward at its last
+ * improvement I = f_old[i] - fw_f[i] over the g_rem generations the budget
+ * still allows: proj = fmaf(-I, g_rem, fw_f[i]).  If proj > run_best it
+ * cannot reach the run's best and loses: it is re-initialised uniformly in
+ * [lb, ub]^D (purpose ORC_LOSER, generation gen, unit i), its amplitude
+ * set back to A0 and its fitness to +infinity (unknown until its sparks
+ * are evaluated: the next selection takes its best candidate).
+ * loser[i] = 1 for a loser, else 0.
+ */
+void orc_loser_out(const orc_params* p, uint64_t seed, uint32_t gen, int32_t g_rem, float run_best,
+                   const float* f_old, float* fw_x, float* fw_amp, float* fw_f, int32_t* loser);
 
 /* A whole run: init, then generations while the budget allows (and at most
  * max_gens).  Writes the best vector, its FP64 fitness, the evaluations
