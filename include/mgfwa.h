@@ -94,6 +94,19 @@ typedef struct {
   int32_t refine_every;
   int32_t refine_steps;
   float refine_lr;
+  /* Loser-out tournament (Algorithm 1, the step after the selection; 0 =
+   * off, 1 = on).  After each selection and the runs' best-so-far update,
+   * every firework except its run's best (the first minimum of the run's
+   * fireworks' fitness) whose fitness before and after the selection are
+   * both finite is projected forward at its last improvement I (fitness
+   * before minus after) over the g_rem generations the budget still allows
+   * at mu (lambda + m) evaluations each (refinement not counted):
+   * fmaf(-I, g_rem, f) in FP32.  If that is above the run's best-so-far the
+   * firework loses: it is re-drawn uniformly in [lb, ub]^D (Philox purpose
+   * 4), its amplitude set back to A0 and its fitness to +infinity (unknown
+   * until its next sparks are evaluated; the next selection takes its best
+   * candidate).  Costs no evaluations. */
+  int32_t loser_out;
 } mgfwa_config;
 
 typedef struct {

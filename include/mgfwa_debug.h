@@ -52,7 +52,8 @@ typedef enum {
   MGFWA_BUF_BEST_F = 11, /* [B] FP32 best-so-far fitness per run (the precision decisions use) */
   MGFWA_BUF_REFINE_X = 12,     /* [B][D] FP32 each run's vector after its last refinement (refining handles) */
   MGFWA_BUF_REFINE_F = 13,     /* [B] FP32 fitness of that vector */
-  MGFWA_BUF_REFINE_ELITE = 14  /* [B] int32 index within the run of the firework it refined */
+  MGFWA_BUF_REFINE_ELITE = 14, /* [B] int32 index within the run of the firework it refined */
+  MGFWA_BUF_LOSER = 15         /* [B*mu] int32: 1 where the last selection's loser-out tournament re-drew the firework */
 } mgfwa_buffer;
 
 /* Copy a buffer to / from host memory (rows packed D floats apart);

@@ -72,16 +72,24 @@ __device__ __forceinline__ void take_if_before(float& bf, int& bc, float of, int
 // amplitude update (x C_a on improvement, x C_r otherwise); winner[z] is
 // the winning candidate or -1.  Then the run's best-so-far: strict
 // improvement over its new fireworks in index order; winner[B*mu + b] is
-// that firework or -1.  k_select_copy moves the rows.
+// that firework or -1, winner[B*mu + B] this generation's number.  Then,
+// with p.lo_gmax > 0, the loser-out tournament: every firework but the
+// run's first minimum whose fitness before (f_old) and after the selection
+// are finite, and whose last improvement I extrapolated over the g_rem =
+// lo_gmax - gen generations left, fmaf(-I, g_rem, f), stays above the run's
+// best-so-far, loses: fitness +infinity, amplitude A0, loser[z] = 1 (its
+// row is re-drawn by k_select_copy).  gens_done is only read here.
 __global__ void __launch_bounds__(kSelThreads) k_select_decide(Problem p, const float* __restrict__ fit_e,
                                                                const float* __restrict__ fit_g,
                                                                float* __restrict__ fw_amp, float* __restrict__ fw_f,
                                                                int32_t* __restrict__ winner,
                                                                float* __restrict__ best_f,
-                                                               uint32_t* __restrict__ gens_done) {
+                                                               const uint32_t* __restrict__ gens_done,
+                                                               float* __restrict__ f_old, int32_t* __restrict__ loser) {
   griddep_wait();
   griddep_launch_dependents();
   const int b = blockIdx.x;
+  const uint32_t gen = *gens_done + 1u;  // this generation
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int n_cand = p.lam + p.m;
   for (int il = warp; il < p.mu; il += kSelThreads / 32) {
@@ -100,6 +108,7 @@ __global__ void __launch_bounds__(kSelThreads) k_select_decide(Problem p, const 
     }
     if (lane == 0) {
       const float amp = fw_amp[i];
+      f_old[i] = fw_f[i];
       if (rank_key(bf) < rank_key(fw_f[i])) {
         fw_f[i] = bf;
         fw_amp[i] = __fmul_rn(amp, p.c_a);
@@ -123,7 +132,27 @@ __global__ void __launch_bounds__(kSelThreads) k_select_decide(Problem p, const 
     }
     if (bi >= 0) best_f[b] = bfv;
     winner[(int64_t)p.B * p.mu + b] = bi;
-    if (gens_done && b == 0) *gens_done += 1u;  // the generation is complete
+    if (b == 0) winner[(int64_t)p.B * p.mu + p.B] = (int32_t)gen;
+    int e = 0;  // the run's best firework: never a loser
+    for (int i = 1; i < p.mu; ++i)
+      if (rank_key(f[i]) < rank_key(f[e])) e = i;
+    const int64_t left = (int64_t)p.lo_gmax - (int64_t)gen;
+    const float g_rem = (float)(left > 0 ? left : 0);
+    const float rb = best_f[b];
+    for (int il = 0; il < p.mu; ++il) {
+      const int64_t z = (int64_t)b * p.mu + il;
+      int32_t lo = 0;
+      const float fo = f_old[z], fn = f[il];
+      if (p.lo_gmax > 0 && il != e && isfinite(fo) && isfinite(fn)) {
+        const float proj = __fmaf_rn(-__fsub_rn(fo, fn), g_rem, fn);
+        if (proj > rb) {
+          lo = 1;
+          fw_f[z] = __int_as_float(0x7f800000);
+          fw_amp[z] = p.amp0;
+        }
+      }
+      loser[z] = lo;
+    }
   }
 }
 
@@ -134,20 +163,45 @@ __host__ __device__ inline int copy_blocks(int64_t Dp) {
 }
 
 // The rows of the selection, grid (row chunks, B*mu + B): row y < B*mu is
-// firework y's winning candidate copied into fw_x (when one won); row
-// B*mu + b is run b's best firework copied into best_x, read from where
+// firework y's winning candidate copied into fw_x (when one won), or, for a
+// loser of the tournament, a uniform draw in [lb, ub] (purpose kLoser,
+// generation winner[B*mu + B], unit = the firework's index in its run);
+// row B*mu + b is run b's best firework copied into best_x, read from where
 // that firework's new position comes from (its winning candidate, or its
-// own row, which no block writes then).
+// own row, which no block writes then; the best firework never loses).
+// Advances gens_done (nothing else in this launch reads it).
 __global__ void __launch_bounds__(256) k_select_copy(Problem p, const float* __restrict__ sparks,
                                                      const float* __restrict__ guides, float* __restrict__ fw_x,
                                                      const int32_t* __restrict__ winner,
-                                                     float* __restrict__ best_x) {
+                                                     float* __restrict__ best_x, const int32_t* __restrict__ loser,
+                                                     uint32_t* __restrict__ gens_done) {
   griddep_wait();
   griddep_launch_dependents();
   const int nz = p.B * p.mu;
   const int y = blockIdx.y;
+  if (blockIdx.x == 0 && y == 0 && threadIdx.x == 0) *gens_done += 1u;  // the generation is complete
+  const int64_t n4 = p.Dp / 4;
+  const int64_t chunk = (n4 + gridDim.x - 1) / gridDim.x;
+  const int64_t e0 = (int64_t)blockIdx.x * chunk;
+  const int64_t e1 = e0 + chunk < n4 ? e0 + chunk : n4;
   int z, c;
   float* dst;
+  if (y < nz && loser[y]) {
+    const int b = y / p.mu, il = y - b * p.mu;
+    const uint32_t gen = (uint32_t)winner[(int64_t)nz + p.B];
+    uint32_t k0, k1;
+    run_key(p, b, k0, k1);
+    const float width = __fsub_rn(p.ub, p.lb);
+    float4* d4 = reinterpret_cast<float4*>(fw_x + (int64_t)y * p.Dp);
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const uint4 r = philox4x32_10(make_uint4((uint32_t)e, (uint32_t)il, gen, kLoser), k0, k1);
+      float v[4];
+#pragma unroll
+      for (int l = 0; l < 4; ++l) v[l] = (4 * e + l < p.D) ? __fmaf_rn(u24(lane_of(r, l)), width, p.lb) : 0.0f;
+      d4[e] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    return;
+  }
   if (y < nz) {
     z = y;
     c = winner[z];
@@ -164,10 +218,6 @@ __global__ void __launch_bounds__(256) k_select_copy(Problem p, const float* __r
   const float* src = c < 0 ? fw_x + (int64_t)z * p.Dp
                      : c < p.lam ? sparks + ((int64_t)z * p.lam + c) * p.Dp
                                  : guides + ((int64_t)z * p.m + (c - p.lam)) * p.Dp;
-  const int64_t n4 = p.Dp / 4;
-  const int64_t chunk = (n4 + gridDim.x - 1) / gridDim.x;
-  const int64_t e0 = (int64_t)blockIdx.x * chunk;
-  const int64_t e1 = e0 + chunk < n4 ? e0 + chunk : n4;
   const float4* s4 = reinterpret_cast<const float4*>(src);
   float4* d4 = reinterpret_cast<float4*>(dst);
   for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) d4[e] = s4[e];
@@ -278,12 +328,12 @@ int launch_rank(const Problem& p, float* fit_e, int32_t* top, int32_t* bottom, c
 
 int launch_select(const Problem& p, const float* fit_e, const float* fit_g, const float* sparks,
                   const float* guides, float* fw_x, float* fw_amp, float* fw_f, int32_t* winner, float* best_x,
-                  float* best_f, uint32_t* gens_done, cudaStream_t s) {
+                  float* best_f, uint32_t* gens_done, float* f_old, int32_t* loser, cudaStream_t s) {
   if (launch_pdl(k_select_decide, dim3(p.B), dim3(kSelThreads), 0, s, p, fit_e, fit_g, fw_amp, fw_f, winner, best_f,
-                 gens_done) != cudaSuccess)
+                 (const uint32_t*)gens_done, f_old, loser) != cudaSuccess)
     return -1;
   if (launch_pdl(k_select_copy, dim3(copy_blocks(p.Dp), p.B * p.mu + p.B), dim3(256), 0, s, p, sparks, guides, fw_x,
-                 (const int32_t*)winner, best_x) != cudaSuccess)
+                 (const int32_t*)winner, best_x, (const int32_t*)loser, gens_done) != cudaSuccess)
     return -1;
   return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;
 }

@@ -55,6 +55,8 @@ struct mgfwa_handle {
   int32_t* top = nullptr;
   int32_t* bottom = nullptr;
   int32_t* winner = nullptr;
+  float* f_old = nullptr;     // [B*mu] fitness before the selection (loser-out tournament)
+  int32_t* loser = nullptr;   // [B*mu] 1 where the last tournament re-drew the firework
   int32_t* elite = nullptr;     // [B*mu*E] spark rows picked for the FP32 re-score
   GradPlan rescore_plan;        // FP32 forward of the B*mu*E re-scored rows
   float* rescore_scratch = nullptr;
@@ -347,7 +349,9 @@ mgfwa_status run_phase(mgfwa_t* h, int32_t phase) {
     case MGFWA_PHASE_SELECT: {
       Mark mk(h, G_SELECT);
       MG_LAUNCH(h, launch_select(p, h->fit, h->fit + n_e, h->sparks, h->sparks + n_e * p.Dp, h->fw_x, h->fw_amp,
-                                 h->fw_f, h->winner, h->best_x, h->best_f, h->gens_done, h->stream), "select");
+                                 h->fw_f, h->winner, h->best_x, h->best_f, h->gens_done, h->f_old, h->loser,
+                                 h->stream),
+                "select");
       if (!h->capturing) h->evals += h->P;
       return MGFWA_OK;
     }
@@ -470,6 +474,7 @@ mgfwa_status validate(const mgfwa_config* c, const mgfwa_objective* o) {
   if (c->precision != MGFWA_FP32 && c->precision != MGFWA_BF16 && c->precision != MGFWA_FP8)
     return fail(nullptr, MGFWA_EINVAL, "precision %d not supported (FP32 = 0, BF16 = 1, FP8 = 2)", c->precision);
   if (c->refine_every < 0) return fail(nullptr, MGFWA_EINVAL, "refine_every must be >= 0");
+  if (c->loser_out != 0 && c->loser_out != 1) return fail(nullptr, MGFWA_EINVAL, "loser_out must be 0 or 1");
   if (c->refine_every > 0) {
     if (o->kind != MGFWA_OBJ_MLP_CE) return fail(nullptr, MGFWA_EINVAL, "refinement needs an MLP objective");
     if (c->refine_steps < 1 || c->refine_steps > 10000)
@@ -582,6 +587,7 @@ uint64_t problem_fingerprint(const mgfwa_config* cfg, const mgfwa_objective* obj
   mix(&cfg->refine_every, sizeof(cfg->refine_every));
   mix(&cfg->refine_steps, sizeof(cfg->refine_steps));
   mix(&cfg->refine_lr, sizeof(cfg->refine_lr));
+  mix(&cfg->loser_out, sizeof(cfg->loser_out));
   mix(&obj->kind, sizeof(obj->kind));
   mix(&obj->n_layers, sizeof(obj->n_layers));
   if (obj->kind == MGFWA_OBJ_MLP_CE) {
@@ -619,6 +625,12 @@ void plan_handle(mgfwa_t* h, const mgfwa_config* cfg, const mgfwa_objective* obj
   p.B = cfg->n_runs;
   p.seed = cfg->seed;
   h->P = (int64_t)p.mu * (p.lam + p.m);
+  // loser-out tournament: the generations the budget allows at P evaluations each (0 = off)
+  p.lo_gmax = 0;
+  if (cfg->loser_out) {
+    const int64_t g = (cfg->eval_budget - p.mu) / h->P;
+    p.lo_gmax = (int32_t)(g < 1 ? 1 : (g > (1 << 30) ? (1 << 30) : g));
+  }
   h->PA = (int64_t)p.B * h->P;
 
   Mlp& mlp = h->mlp;
@@ -691,7 +703,9 @@ size_t carve_all(mgfwa_t* h, char* base) {
   h->partial = carve<float>(cur, (size_t)h->mtiles * h->PA);
   h->top = carve<int32_t>(cur, F * p.m * p.k);
   h->bottom = carve<int32_t>(cur, F * p.m * p.k);
-  h->winner = carve<int32_t>(cur, F + p.B);  // per firework, then per run (the selection's decisions)
+  h->winner = carve<int32_t>(cur, F + p.B + 1);  // per firework, per run, the generation (the selection's decisions)
+  h->f_old = carve<float>(cur, F);
+  h->loser = carve<int32_t>(cur, F);
   h->elite = carve<int32_t>(cur, F * (cfg->elite_rescore > 0 ? cfg->elite_rescore : 1));
   const bool rescore = want_op && cfg->elite_rescore > 0;
   h->rescore_scratch = rescore ? carve<float>(cur, (size_t)h->rescore_plan.floats) : nullptr;
@@ -1314,6 +1328,7 @@ bool buffer_view(mgfwa_t* h, int32_t buf, BufView* v) {
       if (!h->refine) return false;
       *v = {h->relite, 0, 0, 0, (int64_t)sizeof(int32_t) * p.B};
       return true;
+    case MGFWA_BUF_LOSER: *v = {h->loser, 0, 0, 0, (int64_t)sizeof(int32_t) * F}; return true;
   }
   return false;
 }

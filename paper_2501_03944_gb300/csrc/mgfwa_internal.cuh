@@ -10,7 +10,7 @@
 namespace mgfwa {
 
 // Philox stream purposes: the fourth counter word.
-constexpr uint32_t kInit = 0, kExplode = 1, kMap = 2, kGmap = 3;
+constexpr uint32_t kInit = 0, kExplode = 1, kMap = 2, kGmap = 3, kLoser = 4;
 
 // Scalar parameters of one run, passed by value to the kernels.
 // Fireworks of all runs are numbered globally, z = b * mu + i (run b,
@@ -23,6 +23,7 @@ struct Problem {
   int32_t B;       // independent runs
   float beta, amp0, c_a, c_r;
   uint64_t seed;   // run b draws from Philox keyed by seed + b
+  int32_t lo_gmax; // loser-out tournament: the generations the budget allows (0 = tournament off)
 };
 
 // Philox key of run b: low and high words of seed + b.
@@ -212,12 +213,15 @@ int launch_run_best_init(const Problem& p, const float* fw_x, const float* fw_f,
 
 // Selection of every firework (winner[z]: its winning candidate or -1) and
 // each run's best-so-far (winner[B*mu + b]: the run's improving firework or
-// -1; winner holds B*mu + B entries), then the copies of the winning rows
-// into fw_x and best_x; advances gens_done[0] by one (the generation is
+// -1; winner[B*mu + B]: the generation; winner holds B*mu + B + 1
+// entries), the loser-out tournament when p.lo_gmax > 0 (f_old [B*mu]:
+// scratch for the fitness before the selection; loser [B*mu]: 1 where a
+// firework lost), then the copies of the winning rows into fw_x and best_x
+// and the losers' new rows; advances gens_done[0] by one (the generation is
 // complete).
 int launch_select(const Problem& p, const float* fit_e, const float* fit_g, const float* sparks,
                   const float* guides, float* fw_x, float* fw_amp, float* fw_f, int32_t* winner,
-                  float* best_x, float* best_f, uint32_t* gens_done, cudaStream_t s);
+                  float* best_x, float* best_f, uint32_t* gens_done, float* f_old, int32_t* loser, cudaStream_t s);
 
 // FP32 CUDA-core fitness of `count` rows (stride `ld` floats; row r is
 // rows[idx[r]] when idx is given): per-(m-tile, r) partial cross-entropy

@@ -40,6 +40,8 @@ def _specs(pkg):
                      {"n_runs": 2}),
         "refine": (W.scaled(small, eval_budget=3000), 28, pkg.MGFWA_FP32,
                    {"refine_every": 2, "refine_steps": 4, "refine_lr": 0.5}),
+        "loser_out": (W.scaled(big, eval_budget=W.budget_for_generations(3, 20, 4, 6)), 29, pkg.MGFWA_BF16,
+                      {"loser_out": 1}),
     }
 
 
@@ -48,7 +50,8 @@ def _make(pkg, w, seed, prec, kw):
     return pkg.Mgfwa.for_workload(w, seed, precision=prec, X=X, y=y, **kw)
 
 
-@pytest.mark.parametrize("case", ["fp32", "bf16", "bf16_full", "fp8", "three_layer", "sphere", "two_runs", "refine"])
+@pytest.mark.parametrize("case", ["fp32", "bf16", "bf16_full", "fp8", "three_layer", "sphere", "two_runs", "refine",
+                                  "loser_out"])
 def test_graph_replay_equals_kernel_by_kernel(pkg, case):
     spec = _specs(pkg)[case]
     states = []
