@@ -330,6 +330,9 @@ def gpu_arm(args):
         # E4M3 first layer on the tensor cores (elite candidates re-scored in FP32)
         extra["fp8_one_run"] = dict(timed_generations({"precision": pkg.MGFWA_FP8}, max(5, args.steps // 2)),
                                     precision="fp8")
+        # the same run with the loser-out tournament (Algorithm 1's step after the selection) on
+        extra["loser_out_one_run"] = dict(timed_generations({"precision": prec, "loser_out": 1},
+                                                            max(5, args.steps // 2)), precision=args.precision)
         # 8 independent runs of the same workload in one handle (one fitness launch per generation)
         extra["batched_8_runs"] = dict(timed_generations({"precision": prec, "n_runs": 8}, max(5, args.steps // 2)),
                                        runs=8, precision=args.precision)
