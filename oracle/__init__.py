@@ -23,7 +23,7 @@ _lib = None
 _lock = threading.Lock()
 
 INIT, EXPLODE, MAP, GMAP = 0, 1, 2, 3
-MLP_CE, SPHERE = 0, 1
+MLP_CE, SPHERE, NET_OUTPUT = 0, 1, 2
 TANH, RELU = 0, 1
 
 
@@ -56,7 +56,7 @@ class Objective(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("dim", ctypes.c_int64), ("n_layers", ctypes.c_int32),
                 ("widths", ctypes.POINTER(ctypes.c_int32)), ("acts", ctypes.POINTER(ctypes.c_int32)),
                 ("n_samples", ctypes.c_int64), ("X", ctypes.POINTER(ctypes.c_float)),
-                ("y", ctypes.POINTER(ctypes.c_int32))]
+                ("y", ctypes.POINTER(ctypes.c_int32)), ("params", ctypes.POINTER(ctypes.c_float))]
 
 
 def _p(a: np.ndarray, ct):
@@ -142,21 +142,25 @@ def params_for(w, **over) -> Params:
 class Problem:
     """An objective plus the buffers it points into (kept alive here)."""
 
-    def __init__(self, kind: int, dim: int, widths=(), acts=(), X=None, y=None):
+    def __init__(self, kind: int, dim: int, widths=(), acts=(), X=None, y=None, params=None):
         self.kind = kind
         self.widths = np.ascontiguousarray(widths, dtype=np.int32) if len(widths) else np.zeros(1, np.int32)
         self.acts = np.ascontiguousarray(acts, dtype=np.int32) if len(acts) else np.zeros(1, np.int32)
         self.X = np.ascontiguousarray(X if X is not None else np.zeros((1, 1)), dtype=np.float32)
         self.y = np.ascontiguousarray(y if y is not None else np.zeros(1), dtype=np.int32)
         n = 0 if X is None else self.X.shape[0]
+        self.params = np.ascontiguousarray(params if params is not None else np.zeros(1), dtype=np.float32)
         self.obj = Objective(kind, dim, max(len(widths) - 1, 0), _p(self.widths, ctypes.c_int32),
                              _p(self.acts, ctypes.c_int32), n, _p(self.X, ctypes.c_float),
-                             _p(self.y, ctypes.c_int32))
+                             _p(self.y, ctypes.c_int32), _p(self.params, ctypes.c_float))
 
     @classmethod
     def for_workload(cls, w, X=None, y=None):
         if w.kind == SPHERE:
             return cls(SPHERE, w.dim)
+        if w.kind == NET_OUTPUT:
+            import workloads
+            return cls(NET_OUTPUT, w.dim, w.widths, w.acts, params=workloads.make_net(w))
         if X is None:
             import workloads
             X, y = workloads.make_data(w)

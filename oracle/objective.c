@@ -14,6 +14,12 @@
  * first.  Every multiply and add is plain double arithmetic in index order.
  *
  * The sphere objective f(x) = sum_k x_k^2 is kept for convergence checks.
+ *
+ * The paper's own testbed (Sec. 4.1, Eq. 1): the search vector x is the
+ * input of a fixed network and f(x) its scalar output,
+ *   a_0 = x;  a_l = act(W_l a_{l-1} + b_l) for hidden layers;  f = W_L a_{L-1} + b_L,
+ * activations ReLU, tanh or GELU(v) = v (1 + erf(v / sqrt 2)) / 2, the
+ * network's parameters in the same nn.Linear order.
  */
 #include <math.h>
 #include <pthread.h>
@@ -24,7 +30,35 @@
 
 static double act(int32_t kind, double v) {
   if (kind == ORC_TANH) return tanh(v);
+  if (kind == ORC_GELU) return 0.5 * v * (1.0 + erf(v / sqrt(2.0)));
   return v > 0.0 ? v : 0.0;
+}
+
+static double net_output(const orc_objective* obj, const float* x) {
+  const int32_t L = obj->n_layers;
+  int32_t wmax = 0;
+  for (int32_t l = 0; l <= L; ++l)
+    if (obj->widths[l] > wmax) wmax = obj->widths[l];
+  double* a = (double*)malloc(sizeof(double) * (size_t)wmax);
+  double* b = (double*)malloc(sizeof(double) * (size_t)wmax);
+  for (int32_t i = 0; i < obj->widths[0]; ++i) a[i] = (double)x[i];
+  const float* p = obj->params;
+  for (int32_t l = 0; l < L; ++l) {
+    const int32_t fan_in = obj->widths[l], fan_out = obj->widths[l + 1];
+    const float* W = p;
+    const float* bias = p + (int64_t)fan_in * fan_out;
+    for (int32_t j = 0; j < fan_out; ++j) {
+      double s = (double)bias[j];
+      for (int32_t i = 0; i < fan_in; ++i) s += (double)W[(int64_t)j * fan_in + i] * a[i];
+      b[j] = (l + 1 < L) ? act(obj->acts[l], s) : s;
+    }
+    p = bias + fan_out;
+    double* t = a; a = b; b = t;
+  }
+  const double f = a[0];
+  free(a);
+  free(b);
+  return f;
 }
 
 static double mlp_ce(const orc_objective* obj, const float* x) {
@@ -70,6 +104,7 @@ double orc_fitness(const orc_objective* obj, const float* x) {
     for (int64_t k = 0; k < obj->dim; ++k) s += (double)x[k] * (double)x[k];
     return s;
   }
+  if (obj->kind == ORC_NET_OUTPUT) return net_output(obj, x);
   return mlp_ce(obj, x);
 }
 

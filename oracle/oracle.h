@@ -33,8 +33,8 @@ extern "C" {
 enum { ORC_INIT = 0, ORC_EXPLODE = 1, ORC_MAP = 2, ORC_GMAP = 3, ORC_LOSER = 4 };
 
 /* Objective kinds and hidden activations. */
-enum { ORC_MLP_CE = 0, ORC_SPHERE = 1 };
-enum { ORC_TANH = 0, ORC_RELU = 1 };
+enum { ORC_MLP_CE = 0, ORC_SPHERE = 1, ORC_NET_OUTPUT = 2 };
+enum { ORC_TANH = 0, ORC_RELU = 1, ORC_GELU = 2 };
 
 typedef struct {
   int64_t dim;      /* D */
@@ -63,6 +63,10 @@ typedef struct {
   int64_t n_samples;       /* N */
   const float* X;          /* [N][d_in] row-major */
   const int32_t* y;        /* [N] labels in [0, C) */
+  /* ORC_NET_OUTPUT (the paper's testbed, Sec. 4.1, Eq. 1): the output of a
+   * fixed network at the search vector, its input; widths d, h.., 1 and
+   * its parameters in nn.Linear order (W_1[h][d] row-major, b_1, ...). */
+  const float* params;
 } orc_objective;
 
 /* Philox4x32 with 10 rounds: out = bijection(ctr) keyed by key. */

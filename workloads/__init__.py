@@ -21,9 +21,11 @@ import numpy as np
 
 ACT_TANH = 0
 ACT_RELU = 1
+ACT_GELU = 2
 
 KIND_MLP_CE = 0
 KIND_SPHERE = 1
+KIND_NET_OUTPUT = 2   # the paper's testbed: minimise a fixed network's output over its input
 
 
 @dataclasses.dataclass(frozen=True)
@@ -55,6 +57,9 @@ class Workload:
 
     def flops_per_spark(self) -> float:
         """2 N sum(fan_in * fan_out): the dense multiply-adds of one fitness evaluation."""
+        if self.kind == KIND_NET_OUTPUT:
+            w = self.widths
+            return 2.0 * sum(w[i] * w[i + 1] for i in range(len(w) - 1))
         if self.kind != KIND_MLP_CE:
             return 2.0 * self.dim
         w = self.widths
@@ -96,6 +101,38 @@ SPHERE_30 = Workload(
     name="sphere30", kind=KIND_SPHERE, widths=(), acts=(), n_samples=0, dim=30,
     lb=-5.0, ub=5.0, n_fireworks=5, sparks_per_firework=40, guiding_per_firework=4,
     sigma=0.2, eval_budget=100_000)
+
+def table2_net(net_id: int, **over) -> Workload:
+    """The paper's testbed network `net_id` of Table 2 (Sec. 4.1): minimise its scalar output over its input.
+    Widths [input] + [hidden] * (layer_num + 1) + [1] (the reading under which nets 2-9 match the printed
+    parameter counts), ReLU for odd ids and GELU for even ones, input box [-1, 1]^d (the paper states no
+    bounds), the bench's population; weights from make_net."""
+    rows = {1: (10, 16, 4), 2: (10, 32, 4), 3: (20, 16, 4), 4: (20, 32, 4), 5: (100, 64, 7), 6: (100, 128, 7),
+            7: (200, 64, 7), 8: (200, 128, 7), 9: (1000, 256, 10), 10: (1000, 512, 10), 11: (2000, 256, 10),
+            12: (2000, 512, 10)}
+    d, h, layer_num = rows[net_id]
+    widths = (d,) + (h,) * (layer_num + 1) + (1,)
+    act = ACT_RELU if net_id % 2 else ACT_GELU
+    kw = dict(name=f"net{net_id}_{d}-{h}x{layer_num + 1}-1", kind=KIND_NET_OUTPUT, widths=widths,
+              acts=(act,) * (len(widths) - 2), n_samples=0, dim=d, lb=-1.0, ub=1.0, n_fireworks=5,
+              sparks_per_firework=200, guiding_per_firework=8, sigma=0.2,
+              eval_budget=budget_for_generations(5, 200, 8, 200), data_seed=net_id)
+    kw.update(over)
+    return Workload(**kw)
+
+
+def make_net(w: Workload) -> np.ndarray:
+    """The fixed parameters of a testbed network (nn.Linear order), each layer's weights and biases drawn
+    U(-1/sqrt(fan_in), 1/sqrt(fan_in)) (torch's nn.Linear default; the paper does not state its init)."""
+    rng = np.random.default_rng(1000 + w.data_seed)
+    parts = []
+    for i in range(len(w.widths) - 1):
+        fi, fo = w.widths[i], w.widths[i + 1]
+        bound = 1.0 / np.sqrt(fi)
+        parts.append(rng.uniform(-bound, bound, size=fi * fo))
+        parts.append(rng.uniform(-bound, bound, size=fo))
+    return np.ascontiguousarray(np.concatenate(parts), dtype=np.float32)
+
 
 ALL = {w.name: w for w in (MLP_8_16_3, MLP_784_64_10, MLP_3072_128_64_10, SPHERE_30)}
 
