@@ -234,6 +234,29 @@ def reference_arm(args):
     return 0
 
 
+def testbed_net(pkg, stream, net_id, steps):
+    """sparks/s of one run on Table 2's network `net_id` (FP32 layers on the CUDA cores), after 3 warm-up
+    generations, with the FP32 FLOP rate of its layers."""
+    import torch
+    w = W.table2_net(net_id)
+    w = W.scaled(w, eval_budget=W.budget_for_generations(w.n_fireworks, w.sparks_per_firework,
+                                                         w.guiding_per_firework, steps + 5))
+    h = pkg.Mgfwa.for_workload(w, 23, stream=stream.cuda_stream)
+    h.step(3)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    h.step(steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t = a.elapsed_time(b)
+    n = h.info().sparks_per_gen * steps
+    h.close()
+    sps = n / (t / 1e3)
+    return {"workload": w.name, "value": sps, "unit": UNIT, "ms_per_step": t / steps, "precision": "fp32",
+            "layer_tflops": sps * w.flops_per_spark() / 1e12}
+
+
 def _config(args, world):
     return {"workload": WORKLOAD.name, "widths": list(WORKLOAD.widths), "dim": WORKLOAD.dim,
             "n_samples": WORKLOAD.n_samples, "fireworks": WORKLOAD.n_fireworks,
@@ -333,6 +356,8 @@ def gpu_arm(args):
         # the same run with the loser-out tournament (Algorithm 1's step after the selection) on
         extra["loser_out_one_run"] = dict(timed_generations({"precision": prec, "loser_out": 1},
                                                             max(5, args.steps // 2)), precision=args.precision)
+        # the paper's own testbed (Sec. 4.1): Table 2's network 10, its output minimised over its input
+        extra["testbed_net10"] = testbed_net(pkg, stream, 10, max(5, args.steps // 2))
         # 8 independent runs of the same workload in one handle (one fitness launch per generation)
         extra["batched_8_runs"] = dict(timed_generations({"precision": prec, "n_runs": 8}, max(5, args.steps // 2)),
                                        runs=8, precision=args.precision)

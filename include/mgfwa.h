@@ -60,8 +60,12 @@ typedef enum {
                      with d_in % 16 == 0 */
 } mgfwa_precision;
 
-enum { MGFWA_OBJ_MLP_CE = 0, MGFWA_OBJ_SPHERE = 1 };
-enum { MGFWA_ACT_TANH = 0, MGFWA_ACT_RELU = 1 };
+/* Objectives: the cross-entropy of an MLP whose flattened parameters are the
+ * search vector; the sphere; and the paper's own testbed (Sec. 4.1, Eq. 1),
+ * the scalar output of a fixed network whose input is the search vector. */
+enum { MGFWA_OBJ_MLP_CE = 0, MGFWA_OBJ_SPHERE = 1, MGFWA_OBJ_NET_OUTPUT = 2 };
+/* GELU(v) = v (1 + erf(v / sqrt 2)) / 2, the exact form (testbed networks only) */
+enum { MGFWA_ACT_TANH = 0, MGFWA_ACT_RELU = 1, MGFWA_ACT_GELU = 2 };
 
 typedef struct {
   int64_t dim;                  /* D; equals the MLP parameter count for MLP objectives */
@@ -110,14 +114,19 @@ typedef struct {
 } mgfwa_config;
 
 typedef struct {
-  int32_t kind;          /* MGFWA_OBJ_MLP_CE or MGFWA_OBJ_SPHERE */
-  int32_t n_layers;      /* linear layers, 2 or 3 (MLP) */
-  const int32_t* widths; /* n_layers + 1 widths d_in, h1, [h2,] C: d_in % 8 == 0, hidden widths <= 192,
-                            C in [2, 32]; the tensor-core shapes are listed at mgfwa_precision */
-  const int32_t* acts;   /* n_layers - 1 hidden activations (MGFWA_ACT_*) */
-  int64_t n_samples;     /* N >= 1 */
-  const float* X;        /* [N][d_in] row-major FP32 */
-  const int32_t* y;      /* [N] labels in [0, C) */
+  int32_t kind;          /* MGFWA_OBJ_MLP_CE, MGFWA_OBJ_SPHERE or MGFWA_OBJ_NET_OUTPUT */
+  int32_t n_layers;      /* linear layers: 2 or 3 (MLP); 1 to 16 (testbed network) */
+  const int32_t* widths; /* n_layers + 1 widths.  MLP: d_in, h1, [h2,] C: d_in % 8 == 0, hidden widths
+                            <= 192, C in [2, 32]; the tensor-core shapes are listed at mgfwa_precision.
+                            Testbed network: d (= dim), hidden widths, 1; every width in [1, 4096] */
+  const int32_t* acts;   /* n_layers - 1 hidden activations (MGFWA_ACT_*; GELU for testbed networks only) */
+  int64_t n_samples;     /* N >= 1 (MLP) */
+  const float* X;        /* [N][d_in] row-major FP32 (MLP) */
+  const int32_t* y;      /* [N] labels in [0, C) (MLP) */
+  /* testbed network: its fixed parameters in nn.Linear order (W_1[h][d]
+   * row-major, b_1, W_2, b_2, ...), copied at create; the precision must be
+   * MGFWA_FP32 (CUDA-core products, FP32 accumulation in index order) */
+  const float* params;
 } mgfwa_objective;
 
 typedef struct mgfwa_handle mgfwa_t;

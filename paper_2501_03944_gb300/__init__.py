@@ -21,8 +21,8 @@ LIB_PATH = os.path.join(_HERE, "libmgfwa.so")
 
 MGFWA_OK, MGFWA_EINVAL, MGFWA_ENOMEM, MGFWA_ECUDA, MGFWA_ETIMEOUT, MGFWA_EBUDGET = range(6)
 MGFWA_FP32, MGFWA_BF16, MGFWA_FP8 = 0, 1, 2
-MGFWA_OBJ_MLP_CE, MGFWA_OBJ_SPHERE = 0, 1
-MGFWA_ACT_TANH, MGFWA_ACT_RELU = 0, 1
+MGFWA_OBJ_MLP_CE, MGFWA_OBJ_SPHERE, MGFWA_OBJ_NET_OUTPUT = 0, 1, 2
+MGFWA_ACT_TANH, MGFWA_ACT_RELU, MGFWA_ACT_GELU = 0, 1, 2
 (MGFWA_PHASE_EXPLODE, MGFWA_PHASE_EVAL_E, MGFWA_PHASE_RANK, MGFWA_PHASE_GUIDE, MGFWA_PHASE_EVAL_G,
  MGFWA_PHASE_RESCORE, MGFWA_PHASE_SELECT, MGFWA_PHASE_REFINE) = range(8)
 (MGFWA_BUF_FW_X, MGFWA_BUF_FW_AMP, MGFWA_BUF_FW_F, MGFWA_BUF_SPARKS, MGFWA_BUF_GUIDES, MGFWA_BUF_FIT_E,
@@ -61,7 +61,7 @@ class mgfwa_objective(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("n_layers", ctypes.c_int32),
                 ("widths", ctypes.POINTER(ctypes.c_int32)), ("acts", ctypes.POINTER(ctypes.c_int32)),
                 ("n_samples", ctypes.c_int64), ("X", ctypes.POINTER(ctypes.c_float)),
-                ("y", ctypes.POINTER(ctypes.c_int32))]
+                ("y", ctypes.POINTER(ctypes.c_int32)), ("params", ctypes.POINTER(ctypes.c_float))]
 
 
 class mgfwa_info(ctypes.Structure):
@@ -175,7 +175,7 @@ def _check(st: int, handle=None):
 
 
 class _ObjectiveBuffers:
-    def __init__(self, kind, widths=(), acts=(), X=None, y=None):
+    def __init__(self, kind, widths=(), acts=(), X=None, y=None, params=None):
         self.widths = np.ascontiguousarray(widths if len(widths) else [0], dtype=np.int32)
         self.acts = np.ascontiguousarray(acts if len(acts) else [0], dtype=np.int32)
         self.X = np.ascontiguousarray(X if X is not None else np.zeros((1, 1)), dtype=np.float32)
@@ -185,6 +185,10 @@ class _ObjectiveBuffers:
                                    self.acts.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                    0 if X is None else self.X.shape[0], _f32p(self.X),
                                    self.y.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        # the testbed network's fixed parameters (kept alive with the struct)
+        self.params = None if params is None else np.ascontiguousarray(params, dtype=np.float32).ravel()
+        if self.params is not None:
+            self.obj.params = _f32p(self.params)
 
 
 def mgfwa_create(cfg: mgfwa_config, objective: mgfwa_objective, stream: int = 0) -> int:
@@ -279,7 +283,7 @@ class Mgfwa:
                  seed, sigma=0.2, boost=1.0, amp_init=0.0, c_amplify=1.2, c_reduce=0.9, precision=MGFWA_FP32,
                  kind=MGFWA_OBJ_MLP_CE, widths=(), acts=(), X=None, y=None, stream: int = 0, n_runs: int = 1,
                  elite_rescore: int = 2, refine_every: int = 0, refine_steps: int = 0, refine_lr: float = 0.0,
-                 loser_out: int = 0):
+                 loser_out: int = 0, params=None):
         cfg = mgfwa_config_init()
         cfg.dim, cfg.lb, cfg.ub = dim, lb, ub
         cfg.n_fireworks, cfg.sparks_per_firework, cfg.guiding_per_firework = (
@@ -291,7 +295,7 @@ class Mgfwa:
         cfg.refine_every, cfg.refine_steps, cfg.refine_lr = refine_every, refine_steps, refine_lr
         cfg.loser_out = loser_out
         self.cfg = cfg
-        self._obj = _ObjectiveBuffers(kind, widths, acts, X, y)
+        self._obj = _ObjectiveBuffers(kind, widths, acts, X, y, params)
         self.dim = dim
         self.handle = mgfwa_create(cfg, self._obj.obj, stream)
         info = mgfwa_get_info(self.handle)
@@ -308,6 +312,9 @@ class Mgfwa:
                 import workloads
                 X, y = workloads.make_data(w)
             kw.update(widths=w.widths, acts=w.acts, X=X, y=y)
+        elif w.kind == MGFWA_OBJ_NET_OUTPUT:
+            import workloads
+            kw.update(widths=w.widths, acts=w.acts, params=workloads.make_net(w))
         kw.update(over)
         return cls(**kw)
 
@@ -437,6 +444,9 @@ def workload_request(w, seed, precision=MGFWA_FP32, X=None, y=None, **over):
             import workloads
             X, y = workloads.make_data(w)
         obj = _ObjectiveBuffers(MGFWA_OBJ_MLP_CE, w.widths, w.acts, X, y)
+    elif w.kind == MGFWA_OBJ_NET_OUTPUT:
+        import workloads
+        obj = _ObjectiveBuffers(MGFWA_OBJ_NET_OUTPUT, w.widths, w.acts, params=workloads.make_net(w))
     else:
         obj = _ObjectiveBuffers(MGFWA_OBJ_SPHERE)
     return cfg, obj

@@ -30,6 +30,9 @@ struct mgfwa_handle {
   mgfwa_config cfg;
   Problem p;
   Mlp mlp;
+  NetOut net;                   // testbed network objective (params point into the arena)
+  int64_t net_count = 0;        // its parameter count
+  float* net_act = nullptr;     // [2][PA][hmax] hidden activations
   int32_t kind = MGFWA_OBJ_MLP_CE;
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -203,6 +206,12 @@ mgfwa_status eval_rows(mgfwa_t* h, int64_t first, int32_t count, int32_t precisi
   if (h->kind == MGFWA_OBJ_SPHERE) {
     Mark mk(h, group);
     MG_LAUNCH(h, launch_fitness_sphere(rows, h->p.Dp, h->p.D, count, fit, h->stream), "sphere fitness");
+    return MGFWA_OK;
+  }
+  if (h->kind == MGFWA_OBJ_NET_OUTPUT) {
+    Mark mk(h, group);
+    MG_LAUNCH(h, launch_net_output(h->net, rows, h->p.Dp, count, fit, h->net_act, h->net.hmax, h->stream),
+              "network output");
     return MGFWA_OK;
   }
   {
@@ -483,6 +492,23 @@ mgfwa_status validate(const mgfwa_config* c, const mgfwa_objective* o) {
       return fail(nullptr, MGFWA_EINVAL, "refine_lr must be positive and finite");
   }
   if (o->kind == MGFWA_OBJ_SPHERE) return MGFWA_OK;
+  if (o->kind == MGFWA_OBJ_NET_OUTPUT) {
+    const int32_t L = o->n_layers;
+    if (L < 1 || L > kNetMaxLayers || !o->widths || (L > 1 && !o->acts) || !o->params)
+      return fail(nullptr, MGFWA_EINVAL, "network objective needs 1 to %d layers, widths, acts and params",
+                  kNetMaxLayers);
+    for (int l = 0; l <= L; ++l)
+      if (o->widths[l] < 1 || o->widths[l] > 4096)
+        return fail(nullptr, MGFWA_EINVAL, "network width %d out of [1, 4096]", o->widths[l]);
+    if (o->widths[0] != c->dim || o->widths[L] != 1)
+      return fail(nullptr, MGFWA_EINVAL, "network widths must run from dim (%lld) to 1", (long long)c->dim);
+    for (int l = 0; l + 1 < L; ++l)
+      if (o->acts[l] != MGFWA_ACT_TANH && o->acts[l] != MGFWA_ACT_RELU && o->acts[l] != MGFWA_ACT_GELU)
+        return fail(nullptr, MGFWA_EINVAL, "unknown activation %d", o->acts[l]);
+    if (c->precision != MGFWA_FP32)
+      return fail(nullptr, MGFWA_EINVAL, "the network objective runs in FP32 only");
+    return MGFWA_OK;
+  }
   if (o->kind != MGFWA_OBJ_MLP_CE) return fail(nullptr, MGFWA_EINVAL, "unknown objective kind %d", o->kind);
   if (o->n_layers < 2 || o->n_layers > 3 || !o->widths || !o->acts || !o->X || !o->y)
     return fail(nullptr, MGFWA_EINVAL, "MLP objective needs 2 or 3 layers, widths, acts, X and y");
@@ -597,6 +623,12 @@ uint64_t problem_fingerprint(const mgfwa_config* cfg, const mgfwa_objective* obj
     const int64_t nx = obj->n_samples * (int64_t)obj->widths[0];
     for (int64_t e = 0; e < nx; e += 61) mix(obj->X + e, sizeof(float));
     for (int64_t e = 0; e < obj->n_samples; e += 61) mix(obj->y + e, sizeof(int32_t));
+  } else if (obj->kind == MGFWA_OBJ_NET_OUTPUT) {
+    mix(obj->widths, sizeof(int32_t) * (size_t)(obj->n_layers + 1));
+    if (obj->n_layers > 1) mix(obj->acts, sizeof(int32_t) * (size_t)(obj->n_layers - 1));
+    int64_t n = 0;
+    for (int l = 0; l < obj->n_layers; ++l) n += (int64_t)obj->widths[l] * obj->widths[l + 1] + obj->widths[l + 1];
+    for (int64_t e = 0; e < n; e += 61) mix(obj->params + e, sizeof(float));
   }
   return f;
 }
@@ -653,6 +685,27 @@ void plan_handle(mgfwa_t* h, const mgfwa_config* cfg, const mgfwa_objective* obj
     h->mtiles = (int32_t)((N + 127) / 128);
   } else {
     h->mtiles = 1;
+  }
+  NetOut& net = h->net;
+  std::memset(&net, 0, sizeof(net));
+  h->net_count = 0;
+  if (obj->kind == MGFWA_OBJ_NET_OUTPUT) {
+    net.n_layers = obj->n_layers;
+    net.hmax = 1;
+    int64_t off = 0;
+    for (int l = 0; l <= obj->n_layers; ++l) {
+      net.widths[l] = obj->widths[l];
+      if (obj->widths[l] > net.wmax) net.wmax = obj->widths[l];
+      if (l > 0 && l < obj->n_layers && obj->widths[l] > net.hmax) net.hmax = obj->widths[l];
+    }
+    for (int l = 0; l < obj->n_layers; ++l) {
+      if (l + 1 < obj->n_layers) net.acts[l] = obj->acts[l];
+      net.w_off[l] = off;
+      off += (int64_t)obj->widths[l] * obj->widths[l + 1];
+      net.b_off[l] = off;
+      off += obj->widths[l + 1];
+    }
+    h->net_count = off;
   }
   h->fingerprint = problem_fingerprint(cfg, obj);
   h->want_op = obj->kind == MGFWA_OBJ_MLP_CE && (cfg->precision == MGFWA_BF16 || cfg->precision == MGFWA_FP8);
@@ -714,6 +767,10 @@ size_t carve_all(mgfwa_t* h, char* base) {
   h->l1_xs = l1 ? carve<uint32_t>(cur, (size_t)l1_fp32x3_x_words(mlp)) : nullptr;
   h->rescore_ws = l1 && rescore ? carve<uint32_t>(cur, (size_t)l1_fp32x3_w_words(mlp, h->rescore_plan.R)) : nullptr;
   h->refine_ws = l1 && h->refine ? carve<uint32_t>(cur, (size_t)l1_fp32x3_w_words(mlp, p.B)) : nullptr;
+  if (h->kind == MGFWA_OBJ_NET_OUTPUT) {
+    h->net.params = carve<float>(cur, (size_t)h->net_count);
+    h->net_act = h->net.n_layers > 1 ? carve<float>(cur, (size_t)(2 * h->PA * h->net.hmax)) : nullptr;
+  }
   h->best_x = carve<float>(cur, (int64_t)p.B * p.Dp);
   h->best_f = carve<float>(cur, p.B);
   h->ce64 = carve<double>(cur, N > 0 ? N : 1);
@@ -837,6 +894,10 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
       return bail(cuda_fail(h, "copy batch"));
     if (want_op) CREATE_LAUNCH(launch_f32_to_op(h->X, N * d_in, h->op_kind, h->inv_x, h->Xop, h->stream), "X operand");
   }
+  if (h->kind == MGFWA_OBJ_NET_OUTPUT &&
+      cudaMemcpyAsync(const_cast<float*>(h->net.params), obj->params, sizeof(float) * h->net_count,
+                      cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return bail(cuda_fail(h, "copy network parameters"));
   if (want_op) {
     st = tc_plan(h->tc, h->mlp, op_rows(h, 0), h->sparks, p.Dp, h->PA);
     if (st != MGFWA_OK) {
@@ -913,6 +974,8 @@ mgfwa_status mgfwa_best_run(mgfwa_t* h, int32_t run, float* x_out, double* f_out
   if (f_out) {
     if (h->kind == MGFWA_OBJ_SPHERE)
       MG_LAUNCH(h, launch_sphere_f64(bx, h->p.D, h->f64, h->stream), "FP64 sphere");
+    else if (h->kind == MGFWA_OBJ_NET_OUTPUT)
+      MG_LAUNCH(h, launch_net_output_f64(h->net, bx, h->f64, h->stream), "FP64 network output");
     else
       MG_LAUNCH(h, launch_fitness_f64(h->mlp, bx, h->ce64, h->f64, h->stream), "FP64 fitness");
     if (cudaMemcpyAsync(f_out, h->f64, sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)

@@ -46,7 +46,20 @@ struct Mlp {
   int64_t w1_elems;           // h1 * d_in
 };
 
-enum { kActTanh = 0, kActRelu = 1 };
+enum { kActTanh = 0, kActRelu = 1, kActGelu = 2 };
+
+// The testbed network of Sec. 4.1 (Eq. 1) as the kernels see it: fixed
+// parameters (nn.Linear order) in device memory, the search vector is its input.
+constexpr int kNetMaxLayers = 16;
+struct NetOut {
+  int32_t n_layers;                        // linear layers, 1 to kNetMaxLayers
+  int32_t widths[kNetMaxLayers + 1];       // d, hidden widths, 1
+  int32_t acts[kNetMaxLayers];             // hidden activations
+  int64_t w_off[kNetMaxLayers], b_off[kNetMaxLayers];  // offsets of W_l and b_l in params
+  int32_t wmax;                            // largest width
+  int32_t hmax;                            // largest hidden width (1 without hidden layers)
+  const float* params;                     // device copy
+};
 
 // The first-layer GEMM operand the samplers write beside the FP32 rows:
 // row r holds the spark's first w1_elems coordinates ([h1][d_in] row-major)
@@ -252,6 +265,13 @@ int launch_fitness_sphere(const float* rows, int64_t ld, int64_t D, int32_t coun
 // fixed-order mean into *out.
 int launch_fitness_f64(const Mlp& mlp, const float* x, double* ce64, double* out, cudaStream_t s);
 int launch_sphere_f64(const float* x, int64_t D, double* out, cudaStream_t s);
+// The testbed network's output for `count` rows (row stride ld) into fit, one
+// launch per layer; scratch holds 2 * count * scratch_ld floats of hidden
+// activations.  Returns the launch count or -1.
+int launch_net_output(const NetOut& net, const float* rows, int64_t ld, int32_t count, float* fit, float* scratch,
+                      int64_t scratch_ld, cudaStream_t s);
+// Its FP64 output for one vector into *out (one launch).
+int launch_net_output_f64(const NetOut& net, const float* x, double* out, cudaStream_t s);
 
 // BF16 copy of the first-layer weights of `count` rows (stride ld) into op.
 int launch_to_operand(const float* rows, int64_t ld, int32_t count, const OpDesc& op, cudaStream_t s);

@@ -30,7 +30,7 @@ struct Request {
   // owned copy of the objective
   int32_t kind = 0, n_layers = 0;
   std::vector<int32_t> widths, acts, y;
-  std::vector<float> X;
+  std::vector<float> X, params;
   int64_t n_samples = 0;
   mgfwa_objective obj() const {
     mgfwa_objective o;
@@ -42,6 +42,7 @@ struct Request {
     o.n_samples = n_samples;
     o.X = X.empty() ? nullptr : X.data();
     o.y = y.empty() ? nullptr : y.data();
+    o.params = params.empty() ? nullptr : params.data();
     return o;
   }
   mgfwa_request_info info;
@@ -147,6 +148,14 @@ mgfwa_status mgfwa_server_submit(mgfwa_server_t* s, const mgfwa_config* cfg, con
     r->n_samples = obj->n_samples;
     r->X.assign(obj->X, obj->X + obj->n_samples * obj->widths[0]);
     r->y.assign(obj->y, obj->y + obj->n_samples);
+  } else if (obj->kind == MGFWA_OBJ_NET_OUTPUT) {
+    r->widths.assign(obj->widths, obj->widths + obj->n_layers + 1);
+    r->acts.assign(obj->acts ? obj->acts : obj->widths, (obj->acts ? obj->acts : obj->widths) +
+                                                           (obj->n_layers > 1 ? obj->n_layers - 1 : 0));
+    if (r->acts.empty()) r->acts.push_back(0);
+    int64_t n = 0;
+    for (int l = 0; l < obj->n_layers; ++l) n += (int64_t)obj->widths[l] * obj->widths[l + 1] + obj->widths[l + 1];
+    r->params.assign(obj->params, obj->params + n);
   }
   std::memset(&r->info, 0, sizeof(r->info));
   r->info.state = MGFWA_REQ_QUEUED;

@@ -86,6 +86,31 @@ def test_create_rejects_bad_configs_without_a_gpu(pkg):
         pkg.Mgfwa.for_workload(w, 0, X=X, y=ybad)
 
 
+def test_network_objective_validation_without_a_gpu(pkg):
+    """The testbed network (Sec. 4.1) is checked before any CUDA call: widths from dim to 1, each in
+    [1, 4096], at most 16 layers, known activations, parameters given, FP32 only."""
+    import workloads as W
+    w = W.table2_net(1)
+    bad = [dict(precision=pkg.MGFWA_BF16), dict(widths=(10, 16, 2)), dict(widths=(12, 16, 1)),
+           dict(widths=(10, 5000, 1), acts=(W.ACT_RELU,)), dict(acts=(W.ACT_RELU, 7, W.ACT_RELU, W.ACT_RELU,
+                                                                      W.ACT_RELU, W.ACT_RELU)),
+           dict(widths=(10,) + (4,) * 17 + (1,), acts=(W.ACT_RELU,) * 17), dict(params=None),
+           dict(refine_every=1, refine_steps=1, refine_lr=0.1)]
+    for over in bad:
+        kw = dict(dim=w.dim, lb=w.lb, ub=w.ub, n_fireworks=w.n_fireworks, sparks_per_firework=w.sparks_per_firework,
+                  guiding_per_firework=w.guiding_per_firework, eval_budget=w.eval_budget, seed=0,
+                  kind=pkg.MGFWA_OBJ_NET_OUTPUT, widths=w.widths, acts=w.acts, params=W.make_net(w))
+        kw.update(over)
+        with pytest.raises(pkg.MgfwaError) as e:
+            pkg.Mgfwa(**kw)
+        assert e.value.status == pkg.MGFWA_EINVAL, over
+    # the MLP objective keeps GELU out
+    m = W.MLP_8_16_3
+    X, y = W.make_data(m)
+    with pytest.raises(pkg.MgfwaError):
+        pkg.Mgfwa.for_workload(m, 0, X=X, y=y, acts=(W.ACT_GELU,))
+
+
 def test_binding_refuses_missing_library(pkg, tmp_path):
     with pytest.raises(ImportError):
         pkg.load_library(str(tmp_path / "nope.so"))
