@@ -125,7 +125,8 @@ typedef struct {
   const int32_t* y;      /* [N] labels in [0, C) (MLP) */
   /* testbed network: its fixed parameters in nn.Linear order (W_1[h][d]
    * row-major, b_1, W_2, b_2, ...), copied at create; the precision must be
-   * MGFWA_FP32 (CUDA-core products, FP32 accumulation in index order) */
+   * MGFWA_FP32 (CUDA-core products, FP32 accumulation in an order fixed by
+   * the layer shape alone) */
   const float* params;
 } mgfwa_objective;
 

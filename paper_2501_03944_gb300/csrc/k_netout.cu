@@ -3,17 +3,22 @@
 //   a_0 = x;  a_l = act(W_l a_{l-1} + b_l) for hidden layers;  f = W_L a_{L-1} + b_L.
 // Here the sparks are the rows of a batch and the weights are shared, so each
 // layer is one dense product [rows x fan_in] x [fan_in x fan_out] with the
-// bias and the activation in its epilogue (FP32 on the CUDA cores; every
-// output accumulates its products in index order, so a spark's fitness does
-// not depend on which sparks share the launch).  The last layer writes the
-// fitness.  An FP64 forward of one vector gives the reported best fitness.
+// bias and the activation in its epilogue (FP32 on the CUDA cores).  The
+// summation order of every output is fixed by the layer's fan-in alone (four
+// contiguous chunks of i, each a chain of fmaf in index order, the chunk sums
+// added in chunk order, then the bias), so a spark's fitness does not depend
+// on which sparks share the launch.  The last layer writes the fitness.  An
+// FP64 forward of one vector gives the reported best fitness.
 #include "mgfwa_internal.cuh"
 
 namespace mgfwa {
 
 namespace {
 
-constexpr int kBM = 64, kBN = 64, kBK = 16;
+constexpr int kBK = 16;      // k-slab depth
+constexpr int kTile = 32;    // output tile: 32 rows x 32 columns per block
+constexpr int kGroups = 4;   // fan-in chunks, one per 64-thread group
+constexpr int kPad = kTile + 4;
 
 __device__ __forceinline__ float act32(int a, float v) {
   if (a == kActTanh) return tanhf(v);
@@ -21,55 +26,116 @@ __device__ __forceinline__ float act32(int a, float v) {
   return fmaxf(v, 0.0f);
 }
 
+// The fan-in chunk of group g: [g c, min((g + 1) c, k)) with c = 16 ceil(k / 64).
+__host__ __device__ __forceinline__ int chunk_len(int k) { return kBK * ((k + kBK * kGroups - 1) / (kBK * kGroups)); }
+
 // out[r][j] = act(sum_i A[r][i] W[j][i] + b[j]) (no activation when act < 0)
-// for r < rows, j < n; A row stride lda, out row stride ldo.  256 threads,
-// 4 x 4 outputs each.
-__global__ void __launch_bounds__(256) k_net_layer(const float* __restrict__ A, int64_t lda, int32_t rows,
+// for r < rows, j < n; A row stride lda, out row stride ldo.  One 256-thread
+// block per 32 x 32 output tile.  Group g (threads 64 g ..) multiplies the
+// tile over its fan-in chunk, 4 x 4 outputs per thread: k-slabs of A and W
+// go through registers into the group's two shared buffers (k-major, so a
+// thread's 4 rows and 4 columns are contiguous), the next slab's global loads
+// in flight while the current one is multiplied, one group barrier per slab.
+// The four partial tiles then meet in shared memory and every thread adds
+// them in group order for 4 outputs, adds the bias and applies the activation.
+// A quarter of the fan-in per group cuts each block's serial slab chain to a
+// quarter, which is what bounds the small-row launches (the guiding sparks).
+__global__ void __launch_bounds__(256, 4) k_net_layer(const float* __restrict__ A, int64_t lda, int32_t rows,
                                                    const float* __restrict__ W, const float* __restrict__ bias,
                                                    int32_t k, int32_t n, int32_t act, float* __restrict__ out,
                                                    int64_t ldo) {
   griddep_wait();
   griddep_launch_dependents();
-  __shared__ float As[kBK][kBM + 4];
-  __shared__ float Ws[kBK][kBN + 4];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int r0 = blockIdx.y * kBM, j0 = blockIdx.x * kBN;
-  float acc[4][4] = {};
-  for (int k0 = 0; k0 < k; k0 += kBK) {
-    for (int e = threadIdx.x; e < kBM * kBK; e += 256) {
-      const int rr = e / kBK, kk = e - rr * kBK;
-      const int r = r0 + rr, kc = k0 + kk;
-      As[kk][rr] = (r < rows && kc < k) ? A[(int64_t)r * lda + kc] : 0.0f;
-      const int j = j0 + rr;
-      Ws[kk][rr] = (j < n && kc < k) ? W[(int64_t)j * k + kc] : 0.0f;
+  // slabs [group][buffer][A or W][kBK][kPad]; afterwards the partial tiles [group][kTile][kPad]
+  __shared__ __align__(16) float sm[kGroups * 2 * 2 * kBK * kPad];
+  const int g = threadIdx.x >> 6, t = threadIdx.x & 63;
+  const int tx = t & 7, ty = t >> 3;
+  const int r0 = blockIdx.x * kTile, j0 = blockIdx.y * kTile;  // row tiles on x: up to 2^24 rows
+  const int c = chunk_len(k);
+  const int kbeg = g * c, kend = min(kbeg + c, k);
+  const int slabs = kend > kbeg ? (kend - kbeg + kBK - 1) / kBK : 0;
+  float* const base = sm + g * (2 * 2 * kBK * kPad);
+  auto As = [&](int buf) { return base + buf * (2 * kBK * kPad); };
+  auto Ws = [&](int buf) { return base + buf * (2 * kBK * kPad) + kBK * kPad; };
+  constexpr int L = kTile * kBK / 64;  // slab elements each thread stages, per operand
+  // element q of a thread is (row rq + 4 q, column kq) of the slab: 16
+  // neighbouring threads read 16 consecutive floats of one row
+  const int kq = t % kBK, rq = t / kBK;
+  const float* pa = A + (int64_t)(r0 + rq) * lda + kq;  // dereferenced only where in range
+  const float* pw = W + (int64_t)(j0 + rq) * k + kq;
+  const int64_t sa = 4 * lda, sw = 4 * (int64_t)k;
+  unsigned va = 0, vw = 0;
+#pragma unroll
+  for (int q = 0; q < L; ++q) {
+    va |= (r0 + rq + 4 * q < rows ? 1u : 0u) << q;
+    vw |= (j0 + rq + 4 * q < n ? 1u : 0u) << q;
+  }
+  float ra[L], rw[L];
+  auto fetch = [&](int k0) {
+    const bool kin = k0 + kq < kend;
+#pragma unroll
+    for (int q = 0; q < L; ++q) {
+      ra[q] = (kin && (va >> q & 1u)) ? pa[q * sa + k0] : 0.0f;
+      rw[q] = (kin && (vw >> q & 1u)) ? pw[q * sw + k0] : 0.0f;
     }
-    __syncthreads();
+  };
+  auto stash = [&](int buf) {
+    float* a = As(buf) + kq * kPad + rq;
+    float* w = Ws(buf) + kq * kPad + rq;
+#pragma unroll
+    for (int q = 0; q < L; ++q) {
+      a[4 * q] = ra[q];
+      w[4 * q] = rw[q];
+    }
+  };
+  auto group_sync = [&]() { asm volatile("bar.sync %0, 64;" ::"r"(g + 1) : "memory"); };
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+  if (slabs > 0) {
+    fetch(kbeg);
+    stash(0);
+    group_sync();
+  }
+  for (int s = 0; s < slabs; ++s) {
+    const int cur = s & 1;
+    if (s + 1 < slabs) fetch(kbeg + (s + 1) * kBK);
+    const float* a = As(cur);
+    const float* w = Ws(cur);
 #pragma unroll
     for (int kk = 0; kk < kBK; ++kk) {
-      float a[4], w[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        a[i] = As[kk][ty * 4 + i];
-        w[i] = Ws[kk][tx * 4 + i];
-      }
+      const float4 av = *reinterpret_cast<const float4*>(a + kk * kPad + ty * 4);
+      const float4 wv = *reinterpret_cast<const float4*>(w + kk * kPad + tx * 4);
+      const float ai[4] = {av.x, av.y, av.z, av.w}, wj[4] = {wv.x, wv.y, wv.z, wv.w};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], w[j], acc[i][j]);
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ai[i], wj[j], acc[i][j]);
     }
-    __syncthreads();
+    // the other buffer was last read in slab s - 1, which every thread of the
+    // group finished before the barrier that ended it
+    if (s + 1 < slabs) stash(cur ^ 1);
+    group_sync();
   }
+  __syncthreads();  // every group done with its slabs: the space holds the partial tiles now
+  float* part = sm + g * (kTile * kPad);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int r = r0 + ty * 4 + i;
-    if (r >= rows) continue;
+  for (int i = 0; i < 4; ++i)
+    *reinterpret_cast<float4*>(part + (ty * 4 + i) * kPad + tx * 4) =
+        make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+  __syncthreads();
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = j0 + tx * 4 + j;
-      if (c >= n) continue;
-      const float z = acc[i][j] + bias[c];
-      out[(int64_t)r * ldo + c] = act >= 0 ? act32(act, z) : z;
-    }
+  for (int q = 0; q < kTile * kTile / 256; ++q) {
+    const int o = threadIdx.x + 256 * q, rr = o / kTile, cc = o % kTile;
+    const int r = r0 + rr, j = j0 + cc;
+    if (r >= rows || j >= n) continue;
+    float z = sm[rr * kPad + cc];
+#pragma unroll
+    for (int h = 1; h < kGroups; ++h) z += sm[h * (kTile * kPad) + rr * kPad + cc];
+    z += bias[j];
+    out[(int64_t)r * ldo + j] = act >= 0 ? act32(act, z) : z;
   }
 }
 
@@ -117,10 +183,12 @@ int launch_net_output(const NetOut& net, const float* rows, int64_t ld, int32_t 
     const bool last = l + 1 == net.n_layers;
     float* o = last ? fit : scratch + (int64_t)(l & 1) * scratch_ld * count;
     const int64_t ldo = last ? 1 : scratch_ld;
-    const dim3 grid((unsigned)((fo + kBN - 1) / kBN), (unsigned)((count + kBM - 1) / kBM));
-    if (launch_pdl(k_net_layer, grid, dim3(256), 0, s, a, lda, count, (const float*)(net.params + net.w_off[l]),
-                   (const float*)(net.params + net.b_off[l]), (int32_t)fi, (int32_t)fo,
-                   (int32_t)(last ? -1 : net.acts[l]), o, ldo) != cudaSuccess)
+    const float* W = net.params + net.w_off[l];
+    const float* b = net.params + net.b_off[l];
+    const int32_t ak = last ? -1 : net.acts[l];
+    const dim3 grid((unsigned)((count + kTile - 1) / kTile), (unsigned)((fo + kTile - 1) / kTile));
+    if (launch_pdl(k_net_layer, grid, dim3(256), 0, s, a, lda, count, W, b, (int32_t)fi, (int32_t)fo, ak, o, ldo) !=
+        cudaSuccess)
       return -1;
     ++n;
     a = o;

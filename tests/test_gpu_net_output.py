@@ -1,8 +1,10 @@
 """The paper's testbed objective (Sec. 4.1, Eq. 1: the scalar output of a
 fixed network, minimised over its input) on the GPU against the oracle.
 
-The GPU computes each layer in FP32 (one fmaf per product, in index order,
-then the bias and the activation); the oracle in FP64.  The tolerance comes
+The GPU computes each layer in FP32: the fan-in split into four contiguous
+chunks of 16 ceil(fan_in / 64), each a chain of fmaf in index order, the
+chunk sums added in chunk order, then the bias and the activation; the
+oracle in FP64.  The tolerance comes
 from that arithmetic: every rounding is modelled as an independent error of
 at most half an FP32 ulp of the value it rounds (variance |v|^2 2^-48 / 3),
 propagated through the network's own weights and activation slopes in
@@ -55,9 +57,18 @@ def fp32_sigma(w, params, x):
         off += fi * fo
         b = params[off:off + fo].astype(np.float64)
         off += fo
-        partial = np.cumsum(Wl * a[None, :], axis=1)  # the running sums the fmaf chain rounds
-        z = partial[:, -1] + b
-        v = (partial ** 2).sum(axis=1) * _U * _U / 3.0 + z * z * _U * _U / 3.0 + (Wl * Wl) @ var
+        c = 16 * -(-fi // 64)  # fan-in chunk
+        prod = Wl * a[None, :]
+        sq = np.zeros(fo)
+        totals = []
+        for g in range(0, fi, c):
+            partial = np.cumsum(prod[:, g:g + c], axis=1)  # the running sums one fmaf chain rounds
+            sq += (partial ** 2).sum(axis=1)
+            totals.append(partial[:, -1])
+        running = np.cumsum(np.stack(totals), axis=0)  # the chunk sums added in order
+        sq += (running[1:] ** 2).sum(axis=0)
+        z = running[-1] + b
+        v = sq * _U * _U / 3.0 + z * z * _U * _U / 3.0 + (Wl * Wl) @ var
         if l + 1 < L:
             a, slope = _act(w.acts[l], z)
             # FP32 tanh/erf: a few ulps; GELU's 1 + erf loses them relative to
