@@ -49,7 +49,8 @@ class Params(ctypes.Structure):
                 ("mu", ctypes.c_int32), ("lam", ctypes.c_int32), ("m", ctypes.c_int32),
                 ("k", ctypes.c_int32), ("beta", ctypes.c_float), ("amp0", ctypes.c_float),
                 ("c_a", ctypes.c_float), ("c_r", ctypes.c_float), ("refine_every", ctypes.c_int32),
-                ("refine_steps", ctypes.c_int32), ("refine_lr", ctypes.c_float), ("loser_out", ctypes.c_int32)]
+                ("refine_steps", ctypes.c_int32), ("refine_lr", ctypes.c_float), ("loser_out", ctypes.c_int32),
+                ("lagged_guiding", ctypes.c_int32)]
 
 
 class Objective(ctypes.Structure):
@@ -86,6 +87,8 @@ def lib():
             L.orc_rank.argtypes = [pp, f32p, i32p, i32p]
             L.orc_guide.argtypes = [pp, ctypes.c_uint64, ctypes.c_uint32, f32p, f32p, f32p, i32p, i32p, f32p]
             L.orc_select.argtypes = [pp, f32p, f32p, f32p, f32p, f32p, f32p, f32p, i32p]
+            L.orc_guiding_vectors.argtypes = [pp, f32p, i32p, i32p, f32p]
+            L.orc_guide_from.argtypes = [pp, ctypes.c_uint64, ctypes.c_uint32, f32p, f32p, f32p, f32p]
             L.orc_loser_out.argtypes = [pp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32, ctypes.c_float, f32p,
                                         f32p, f32p, f32p, i32p]
             L.orc_run.argtypes = [pp, op, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
@@ -122,13 +125,13 @@ def subset_size(sigma: float, g: int) -> int:
 
 
 def make_params(dim, lb, ub, mu, lam, m, sigma=0.2, k=None, beta=1.0, amp0=None, c_a=1.2, c_r=0.9,
-                refine_every=0, refine_steps=0, refine_lr=0.0, loser_out=0) -> Params:
+                refine_every=0, refine_steps=0, refine_lr=0.0, loser_out=0, lagged_guiding=0) -> Params:
     if k is None:
         k = subset_size(sigma, lam // m)
     if amp0 is None:
         amp0 = float(np.float32(ub) - np.float32(lb))
     return Params(dim, lb, ub, mu, lam, m, k, beta, amp0, c_a, c_r, refine_every, refine_steps, refine_lr,
-                  loser_out)
+                  loser_out, lagged_guiding)
 
 
 def params_for(w, **over) -> Params:
@@ -215,6 +218,28 @@ def guide(p: Params, seed: int, gen: int, fw_x, fw_amp, sparks, top, bottom) -> 
     return g
 
 
+def guiding_vectors(p: Params, sparks, top, bottom) -> np.ndarray:
+    """The guiding vectors GV [mu * m][D] alone (lagged multi-guiding)."""
+    sparks = np.ascontiguousarray(sparks, np.float32)
+    top = np.ascontiguousarray(top, np.int32)
+    bottom = np.ascontiguousarray(bottom, np.int32)
+    gv = np.zeros((p.mu * p.m, p.dim), np.float32)
+    lib().orc_guiding_vectors(ctypes.byref(p), _p(sparks, ctypes.c_float), _p(top, ctypes.c_int32),
+                              _p(bottom, ctypes.c_int32), _p(gv, ctypes.c_float))
+    return gv
+
+
+def guide_from(p: Params, seed: int, gen: int, fw_x, fw_amp, gv) -> np.ndarray:
+    """Guiding sparks G = x + beta GV with the mapping, from given vectors (lagged multi-guiding)."""
+    fw_x = np.ascontiguousarray(fw_x, np.float32)
+    fw_amp = np.ascontiguousarray(fw_amp, np.float32)
+    gv = np.ascontiguousarray(gv, np.float32)
+    g = np.zeros((p.mu * p.m, p.dim), np.float32)
+    lib().orc_guide_from(ctypes.byref(p), seed, gen, _p(fw_x, ctypes.c_float), _p(fw_amp, ctypes.c_float),
+                         _p(gv, ctypes.c_float), _p(g, ctypes.c_float))
+    return g
+
+
 def select(p: Params, fit_e, fit_g, sparks, guides, fw_x, fw_amp, fw_f):
     """Returns updated copies (fw_x, fw_amp, fw_f, winner)."""
     fit_e = np.ascontiguousarray(fit_e, np.float32)
@@ -292,20 +317,26 @@ def refine_cost(p: Params) -> int:
 
 
 def generation(p: Params, prob: Problem, seed: int, gen: int, fw_x, fw_amp, fw_f, n_threads: int = 1,
-               run_best=None, g_rem=None):
+               run_best=None, g_rem=None, gv_prev=None):
     """One oracle generation, returning every intermediate (for step-by-step parity).  With the loser-out
     tournament on (p.loser_out), run_best (the run's best-so-far before this generation) and g_rem (the
-    generations the budget allows after this one) are needed."""
+    generations the budget allows after this one) are needed.  With lagged multi-guiding
+    (p.lagged_guiding), gv_prev is the previous generation's "gv" (None in generation 1)."""
     sparks = explode(p, seed, gen, fw_x, fw_amp)
     fit_e64 = prob.fitness_many(sparks, n_threads)
     fit_e = fit_e64.astype(np.float32)
     top, bot = rank(p, fit_e)
-    guides = guide(p, seed, gen, fw_x, fw_amp, sparks, top, bot)
+    if p.lagged_guiding and gv_prev is not None:
+        guides = guide_from(p, seed, gen, fw_x, fw_amp, gv_prev)
+    else:
+        guides = guide(p, seed, gen, fw_x, fw_amp, sparks, top, bot)
     fit_g64 = prob.fitness_many(guides, n_threads)
     fit_g = fit_g64.astype(np.float32)
     nx, na, nf, win = select(p, fit_e, fit_g, sparks, guides, fw_x, fw_amp, fw_f)
     out = dict(sparks=sparks, fit_e64=fit_e64, fit_e=fit_e, top=top, bottom=bot, guides=guides,
                fit_g64=fit_g64, fit_g=fit_g, fw_x=nx, fw_amp=na, fw_f=nf, winner=win)
+    if p.lagged_guiding:
+        out["gv"] = guiding_vectors(p, sparks, top, bot)
     if p.loser_out:
         rb = np.float32(run_best)
         for f in nf:

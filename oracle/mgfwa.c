@@ -159,6 +159,49 @@ void orc_guide(const orc_params* p, uint64_t seed, uint32_t gen, const float* fw
   }
 }
 
+/* Lagged multi-guiding: the guiding vectors alone (Sec. 2.1's GV, sums in
+ * list order as in orc_guide), and the guiding sparks from given vectors. */
+void orc_guiding_vectors(const orc_params* p, const float* sparks, const int32_t* top, const int32_t* bottom,
+                         float* gv) {
+  const int32_t k = p->k;
+  const float fk = (float)k;
+  for (int32_t i = 0; i < p->mu; ++i) {
+    const float* fs = sparks + (int64_t)i * p->lam * p->dim;
+    for (int32_t q = 0; q < p->m; ++q) {
+      const int32_t* t = top + ((int64_t)i * p->m + q) * k;
+      const int32_t* bt = bottom + ((int64_t)i * p->m + q) * k;
+      float* out = gv + ((int64_t)i * p->m + q) * p->dim;
+      for (int64_t d = 0; d < p->dim; ++d) {
+        float sum_top = fs[(int64_t)t[0] * p->dim + d];
+        float sum_bot = fs[(int64_t)bt[0] * p->dim + d];
+        for (int32_t r = 1; r < k; ++r) {
+          sum_top = sum_top + fs[(int64_t)t[r] * p->dim + d];
+          sum_bot = sum_bot + fs[(int64_t)bt[r] * p->dim + d];
+        }
+        out[d] = (sum_top - sum_bot) / fk;
+      }
+    }
+  }
+}
+
+void orc_guide_from(const orc_params* p, uint64_t seed, uint32_t gen, const float* fw_x, const float* fw_amp,
+                    const float* gv, float* guides) {
+  for (int32_t i = 0; i < p->mu; ++i) {
+    const float* x = fw_x + (int64_t)i * p->dim;
+    const float amp = fw_amp[i];
+    for (int32_t q = 0; q < p->m; ++q) {
+      const uint32_t unit = (uint32_t)(i * p->m + q);
+      const float* g = gv + (int64_t)unit * p->dim;
+      float* G = guides + (int64_t)unit * p->dim;
+      for (int64_t d = 0; d < p->dim; ++d) {
+        float v = fmaf(p->beta, g[d], x[d]);
+        if (v < p->lb || v > p->ub) v = map_coord(p, v, x[d], amp, orc_uniform(seed, ORC_GMAP, gen, unit, d));
+        G[d] = v;
+      }
+    }
+  }
+}
+
 /*
  * Selection of the best individual of each firework's population with the
  * dynamic amplitude (reading): candidates in the order explosion 0..lam-1,
@@ -268,6 +311,7 @@ int32_t orc_run(const orc_params* p, const orc_objective* obj, uint64_t seed, in
   int32_t* winner = (int32_t*)malloc(sizeof(int32_t) * (size_t)p->mu);
   float* f_old = (float*)malloc(sizeof(float) * (size_t)p->mu);
   int32_t* loser = (int32_t*)malloc(sizeof(int32_t) * (size_t)p->mu);
+  float* gv = p->lagged_guiding ? (float*)malloc(sizeof(float) * (size_t)((int64_t)p->mu * p->m * D)) : NULL;
 
   orc_init(p, seed, fw_x, fw_amp);
   eval_f32(obj, fw_x, p->mu, D, fw_f, n_threads);
@@ -286,10 +330,21 @@ int32_t orc_run(const orc_params* p, const orc_objective* obj, uint64_t seed, in
   while (gen < max_gens && evals + per_gen + (refine_due(p, gen + 1) ? orc_refine_cost(p) : 0) <= budget) {
     ++gen;
     orc_explode(p, seed, (uint32_t)gen, fw_x, fw_amp, sparks);
-    eval_f32(obj, sparks, (int64_t)p->mu * p->lam, D, fit_e, n_threads);
-    orc_rank(p, fit_e, top, bottom);
-    orc_guide(p, seed, (uint32_t)gen, fw_x, fw_amp, sparks, top, bottom, guides);
-    eval_f32(obj, guides, (int64_t)p->mu * p->m, D, fit_g, n_threads);
+    if (p->lagged_guiding && gen > 1) {
+      /* lagged: the guiding sparks from generation gen - 1's vectors, then
+       * this generation's ranks give the vectors for the next one */
+      orc_guide_from(p, seed, (uint32_t)gen, fw_x, fw_amp, gv, guides);
+      eval_f32(obj, sparks, (int64_t)p->mu * p->lam, D, fit_e, n_threads);
+      eval_f32(obj, guides, (int64_t)p->mu * p->m, D, fit_g, n_threads);
+      orc_rank(p, fit_e, top, bottom);
+      orc_guiding_vectors(p, sparks, top, bottom, gv);
+    } else {
+      eval_f32(obj, sparks, (int64_t)p->mu * p->lam, D, fit_e, n_threads);
+      orc_rank(p, fit_e, top, bottom);
+      orc_guide(p, seed, (uint32_t)gen, fw_x, fw_amp, sparks, top, bottom, guides);
+      eval_f32(obj, guides, (int64_t)p->mu * p->m, D, fit_g, n_threads);
+      if (p->lagged_guiding) orc_guiding_vectors(p, sparks, top, bottom, gv);
+    }
     memcpy(f_old, fw_f, sizeof(float) * (size_t)p->mu);
     orc_select(p, fit_e, fit_g, sparks, guides, fw_x, fw_amp, fw_f, winner);
     evals += per_gen;
@@ -329,5 +384,6 @@ int32_t orc_run(const orc_params* p, const orc_objective* obj, uint64_t seed, in
 
   free(fw_x); free(fw_amp); free(fw_f); free(sparks); free(guides);
   free(fit_e); free(fit_g); free(top); free(bottom); free(winner); free(refined); free(f_old); free(loser);
+  free(gv);
   return 0;
 }

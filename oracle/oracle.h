@@ -52,6 +52,8 @@ typedef struct {
   float refine_lr;       /* eta */
   /* loser-out tournament after each selection (0 = off); see orc_loser_out */
   int32_t loser_out;
+  /* lagged multi-guiding (0 = off); see orc_guiding_vectors */
+  int32_t lagged_guiding;
 } orc_params;
 
 typedef struct {
@@ -107,6 +109,27 @@ void orc_rank(const orc_params* p, const float* fit_e, int32_t* top, int32_t* bo
 void orc_guide(const orc_params* p, uint64_t seed, uint32_t gen, const float* fw_x,
                const float* fw_amp, const float* sparks, const int32_t* top,
                const int32_t* bottom, float* guides);
+/*
+ * Lagged multi-guiding (a variant of the generation's order, off by
+ * default): generation t >= 2 builds its guiding sparks from the guiding
+ * vectors of generation t - 1, applied at the fireworks' positions of
+ * generation t,
+ *   G_t = x_t + beta * GV_{t-1}   (then the random mapping, stream GMAP, generation t),
+ * so that a generation's explosion and guiding sparks need no ranking in
+ * between and can be evaluated together.  Generation 1 has no earlier ranks
+ * and runs the method as written (and records its GV).
+ *
+ * orc_guiding_vectors: GV of group q of firework i (row i*m + q) from the
+ * explosion sparks and the rank lists, (sum top - sum bottom) / k with each
+ * sum in list order, as in orc_guide.
+ * orc_guide_from: the guiding sparks G = x + beta * GV with the mapping,
+ * from given vectors.
+ */
+void orc_guiding_vectors(const orc_params* p, const float* sparks, const int32_t* top, const int32_t* bottom,
+                         float* gv);
+void orc_guide_from(const orc_params* p, uint64_t seed, uint32_t gen, const float* fw_x, const float* fw_amp,
+                    const float* gv, float* guides);
+
 void orc_select(const orc_params* p, const float* fit_e, const float* fit_g, const float* sparks,
                 const float* guides, float* fw_x, float* fw_amp, float* fw_f, int32_t* winner);
 
