@@ -356,6 +356,9 @@ def gpu_arm(args):
         # the same run with the loser-out tournament (Algorithm 1's step after the selection) on
         extra["loser_out_one_run"] = dict(timed_generations({"precision": prec, "loser_out": 1},
                                                             max(5, args.steps // 2)), precision=args.precision)
+        # lagged multi-guiding: explosion and guiding sparks evaluated in one launch from generation 2 on
+        extra["lagged_guiding_one_run"] = dict(timed_generations({"precision": prec, "lagged_guiding": 1},
+                                                                 max(5, args.steps // 2)), precision=args.precision)
         # the paper's own testbed (Sec. 4.1): Table 2's network 10, its output minimised over its input
         extra["testbed_net10"] = testbed_net(pkg, stream, 10, max(5, args.steps // 2))
         # 8 independent runs of the same workload in one handle (one fitness launch per generation)

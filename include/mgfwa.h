@@ -111,6 +111,13 @@ typedef struct {
    * until its next sparks are evaluated; the next selection takes its best
    * candidate).  Costs no evaluations. */
   int32_t loser_out;
+  /* Lagged multi-guiding (a variant of the generation's order; 0 = off,
+   * 1 = on).  Generation t >= 2 builds its guiding sparks from the guiding
+   * vectors of generation t - 1 at the fireworks' current positions,
+   * G = x + beta GV_{t-1} (then the mapping), so that the explosion and
+   * guiding sparks are evaluated in one launch; generation 1 runs the method
+   * as written.  Handles with it cannot be checkpointed or grouped. */
+  int32_t lagged_guiding;
 } mgfwa_config;
 
 typedef struct {

@@ -53,7 +53,8 @@ typedef enum {
   MGFWA_BUF_REFINE_X = 12,     /* [B][D] FP32 each run's vector after its last refinement (refining handles) */
   MGFWA_BUF_REFINE_F = 13,     /* [B] FP32 fitness of that vector */
   MGFWA_BUF_REFINE_ELITE = 14, /* [B] int32 index within the run of the firework it refined */
-  MGFWA_BUF_LOSER = 15         /* [B*mu] int32: 1 where the last selection's loser-out tournament re-drew the firework */
+  MGFWA_BUF_LOSER = 15,        /* [B*mu] int32: 1 where the last selection's loser-out tournament re-drew the firework */
+  MGFWA_BUF_GV = 16            /* [B*mu*m][D] FP32 the last recorded guiding vectors (lagged_guiding handles) */
 } mgfwa_buffer;
 
 /* Copy a buffer to / from host memory (rows packed D floats apart);

@@ -27,7 +27,7 @@ MGFWA_ACT_TANH, MGFWA_ACT_RELU, MGFWA_ACT_GELU = 0, 1, 2
  MGFWA_PHASE_RESCORE, MGFWA_PHASE_SELECT, MGFWA_PHASE_REFINE) = range(8)
 (MGFWA_BUF_FW_X, MGFWA_BUF_FW_AMP, MGFWA_BUF_FW_F, MGFWA_BUF_SPARKS, MGFWA_BUF_GUIDES, MGFWA_BUF_FIT_E,
  MGFWA_BUF_FIT_G, MGFWA_BUF_TOP, MGFWA_BUF_BOTTOM, MGFWA_BUF_WINNER, MGFWA_BUF_BEST_X, MGFWA_BUF_BEST_F,
- MGFWA_BUF_REFINE_X, MGFWA_BUF_REFINE_F, MGFWA_BUF_REFINE_ELITE, MGFWA_BUF_LOSER) = range(16)
+ MGFWA_BUF_REFINE_X, MGFWA_BUF_REFINE_F, MGFWA_BUF_REFINE_ELITE, MGFWA_BUF_LOSER, MGFWA_BUF_GV) = range(17)
 
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EBUDGET"}
 
@@ -54,7 +54,8 @@ class mgfwa_config(ctypes.Structure):
                 ("amp_init", ctypes.c_float), ("c_amplify", ctypes.c_float), ("c_reduce", ctypes.c_float),
                 ("eval_budget", ctypes.c_int64), ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32),
                 ("elite_rescore", ctypes.c_int32), ("n_runs", ctypes.c_int32), ("refine_every", ctypes.c_int32),
-                ("refine_steps", ctypes.c_int32), ("refine_lr", ctypes.c_float), ("loser_out", ctypes.c_int32)]
+                ("refine_steps", ctypes.c_int32), ("refine_lr", ctypes.c_float), ("loser_out", ctypes.c_int32),
+                ("lagged_guiding", ctypes.c_int32)]
 
 
 class mgfwa_objective(ctypes.Structure):
@@ -283,7 +284,7 @@ class Mgfwa:
                  seed, sigma=0.2, boost=1.0, amp_init=0.0, c_amplify=1.2, c_reduce=0.9, precision=MGFWA_FP32,
                  kind=MGFWA_OBJ_MLP_CE, widths=(), acts=(), X=None, y=None, stream: int = 0, n_runs: int = 1,
                  elite_rescore: int = 2, refine_every: int = 0, refine_steps: int = 0, refine_lr: float = 0.0,
-                 loser_out: int = 0, params=None):
+                 loser_out: int = 0, params=None, lagged_guiding: int = 0):
         cfg = mgfwa_config_init()
         cfg.dim, cfg.lb, cfg.ub = dim, lb, ub
         cfg.n_fireworks, cfg.sparks_per_firework, cfg.guiding_per_firework = (
@@ -294,6 +295,7 @@ class Mgfwa:
         cfg.elite_rescore = elite_rescore
         cfg.refine_every, cfg.refine_steps, cfg.refine_lr = refine_every, refine_steps, refine_lr
         cfg.loser_out = loser_out
+        cfg.lagged_guiding = lagged_guiding
         self.cfg = cfg
         self._obj = _ObjectiveBuffers(kind, widths, acts, X, y, params)
         self.dim = dim
@@ -352,7 +354,8 @@ class Mgfwa:
                   MGFWA_BUF_BOTTOM: ((mu, m, k), np.int32), MGFWA_BUF_WINNER: ((mu,), np.int32),
                   MGFWA_BUF_BEST_X: ((B, D) if B > 1 else (D,), np.float32), MGFWA_BUF_BEST_F: ((B,), np.float32),
                   MGFWA_BUF_REFINE_X: ((B, D), np.float32), MGFWA_BUF_REFINE_F: ((B,), np.float32),
-                  MGFWA_BUF_REFINE_ELITE: ((B,), np.int32), MGFWA_BUF_LOSER: ((mu,), np.int32)}
+                  MGFWA_BUF_REFINE_ELITE: ((B,), np.int32), MGFWA_BUF_LOSER: ((mu,), np.int32),
+                  MGFWA_BUF_GV: ((mu * m, D), np.float32)}
         shape, dt = shapes[buf]
         return mgfwa_debug_read(self.handle, buf, np.zeros(shape, dt))
 
@@ -419,7 +422,8 @@ class Mgfwa:
 
 def make_config(*, dim, lb, ub, n_fireworks, sparks_per_firework, guiding_per_firework, eval_budget, seed,
                 sigma=0.2, boost=1.0, amp_init=0.0, c_amplify=1.2, c_reduce=0.9, precision=MGFWA_FP32, n_runs=1,
-                elite_rescore=2, refine_every=0, refine_steps=0, refine_lr=0.0, loser_out=0) -> mgfwa_config:
+                elite_rescore=2, refine_every=0, refine_steps=0, refine_lr=0.0, loser_out=0,
+                lagged_guiding=0) -> mgfwa_config:
     cfg = mgfwa_config_init()
     cfg.dim, cfg.lb, cfg.ub = dim, lb, ub
     cfg.n_fireworks, cfg.sparks_per_firework, cfg.guiding_per_firework = (
@@ -429,6 +433,7 @@ def make_config(*, dim, lb, ub, n_fireworks, sparks_per_firework, guiding_per_fi
         eval_budget, seed, precision, n_runs, elite_rescore)
     cfg.refine_every, cfg.refine_steps, cfg.refine_lr = refine_every, refine_steps, refine_lr
     cfg.loser_out = loser_out
+    cfg.lagged_guiding = lagged_guiding
     return cfg
 
 

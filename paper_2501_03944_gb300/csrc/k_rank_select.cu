@@ -308,20 +308,20 @@ __global__ void k_elite_pick(Problem p, const float* __restrict__ fit_e, float* 
 }  // namespace
 
 int launch_elite_pick(const Problem& p, const float* fit_e, float* fit_g, int32_t E, int32_t* elite,
-                      cudaStream_t s, const float* partial, int32_t mtiles, int64_t N) {
+                      cudaStream_t s, const float* partial, int32_t mtiles, int64_t N, int64_t stride) {
   if (E <= 0) return 0;
   if (launch_pdl(k_elite_pick, dim3(p.B * p.mu), dim3(32), 0, s, p, fit_e, fit_g, E, elite, partial, mtiles,
-                 p.B * p.mu * p.m, (float)N) != cudaSuccess)
+                 (int32_t)(stride > 0 ? stride : (int64_t)p.B * p.mu * p.m), (float)N) != cudaSuccess)
     return -1;
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 int launch_rank(const Problem& p, float* fit_e, int32_t* top, int32_t* bottom, cudaStream_t s, const float* partial,
-                int32_t mtiles, int64_t N) {
+                int32_t mtiles, int64_t N, int64_t stride) {
   const int threads = p.g >= 256 ? 256 : ((p.g + 31) / 32) * 32;
   const size_t smem = (size_t)p.g * (sizeof(float) + sizeof(int));
   if (launch_pdl(k_rank, dim3(p.B * p.mu * p.m), dim3(threads), smem, s, p, fit_e, top, bottom, partial, mtiles,
-                 p.B * p.mu * p.lam, (float)N) != cudaSuccess)
+                 (int32_t)(stride > 0 ? stride : (int64_t)p.B * p.mu * p.lam), (float)N) != cudaSuccess)
     return -1;
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }

@@ -162,6 +162,9 @@ __global__ void __launch_bounds__(kThreads) k_explode(Problem p, const uint32_t*
 // each sum in list order, then the random mapping with its own stream.
 // KU > 0: k == KU, all 2k row loads in flight before the ordered sums, with
 // registers for exactly those rows; KU == 0: any k, two rows at a time.
+// Lagged multi-guiding: with gv_out the vectors GV are also stored (row
+// z * m + q, [Dp]); with gv_in the sums are skipped and the given vectors
+// used instead; with a null `guides` only the vectors are produced.
 template <int KU>
 __global__ void __launch_bounds__(kThreads) k_guide(Problem p, const uint32_t* __restrict__ gens_done,
                                                     const float* __restrict__ fw_x,
@@ -169,6 +172,7 @@ __global__ void __launch_bounds__(kThreads) k_guide(Problem p, const uint32_t* _
                                                     const float* __restrict__ sparks,
                                                     const int32_t* __restrict__ top,
                                                     const int32_t* __restrict__ bottom,
+                                                    const float* __restrict__ gv_in, float* __restrict__ gv_out,
                                                     float* __restrict__ guides, const OpDesc op) {
   griddep_wait();
   griddep_launch_dependents();
@@ -183,6 +187,12 @@ __global__ void __launch_bounds__(kThreads) k_guide(Problem p, const uint32_t* _
   const int64_t d0 = c4 * 4;
   if (d0 >= p.Dp) return;
   const int k = p.k;
+  const float fk = (float)k;
+  float gvl[4];
+  if (gv_in) {
+    const float4 g4 = *reinterpret_cast<const float4*>(gv_in + (int64_t)gq * p.Dp + d0);
+    gvl[0] = g4.x; gvl[1] = g4.y; gvl[2] = g4.z; gvl[3] = g4.w;
+  } else {
   const int32_t* t = top + (int64_t)gq * k;
   const int32_t* b = bottom + (int64_t)gq * k;
   const float* fs = sparks + (int64_t)i * p.lam * p.Dp + d0;
@@ -216,15 +226,19 @@ __global__ void __launch_bounds__(kThreads) k_guide(Problem p, const uint32_t* _
       sb.z = __fadd_rn(sb.z, c.z); sb.w = __fadd_rn(sb.w, c.w);
     }
   }
+#pragma unroll
+  for (int l = 0; l < 4; ++l) gvl[l] = __fdiv_rn(__fsub_rn(lane_of(st, l), lane_of(sb, l)), fk);
+  if (gv_out)
+    *reinterpret_cast<float4*>(gv_out + (int64_t)gq * p.Dp + d0) = make_float4(gvl[0], gvl[1], gvl[2], gvl[3]);
+  }
+  if (!guides) return;
   const float amp = fw_amp[i];
   const float4 x4 = *reinterpret_cast<const float4*>(fw_x + (int64_t)i * p.Dp + d0);
-  const float fk = (float)k;
   float v[4];
   bool out_of_bounds = false;
 #pragma unroll
   for (int l = 0; l < 4; ++l) {
-    const float gv = __fdiv_rn(__fsub_rn(lane_of(st, l), lane_of(sb, l)), fk);
-    v[l] = __fmaf_rn(p.beta, gv, lane_of(x4, l));
+    v[l] = __fmaf_rn(p.beta, gvl[l], lane_of(x4, l));
     out_of_bounds |= (d0 + l < p.D) && (v[l] < p.lb || v[l] > p.ub);
   }
   if (out_of_bounds) {
@@ -281,17 +295,18 @@ int launch_explode(const Problem& p, const uint32_t* gens_done, const float* fw_
 
 int launch_guide(const Problem& p, const uint32_t* gens_done, const float* fw_x, const float* fw_amp, const float* sparks,
                  const int32_t* top, const int32_t* bottom, float* guides, const OpDesc& op_guides,
-                 cudaStream_t s) {
+                 cudaStream_t s, const float* gv_in, float* gv_out) {
   dim3 grid(blocks_for(p.Dp / 4), p.m, p.B * p.mu);
   cudaError_t e;
-  switch (p.k) {
+  const int ku = gv_in ? 0 : p.k;  // given vectors: no row loads to unroll
+  switch (ku) {
 #define MG_GUIDE_K(K) \
   case K: e = launch_pdl(k_guide<K>, grid, dim3(kThreads), 0, s, p, gens_done, fw_x, fw_amp, sparks, top, bottom, \
-                         guides, op_guides); break;
+                         gv_in, gv_out, guides, op_guides); break;
     MG_GUIDE_K(1) MG_GUIDE_K(2) MG_GUIDE_K(3) MG_GUIDE_K(4) MG_GUIDE_K(5) MG_GUIDE_K(6) MG_GUIDE_K(7) MG_GUIDE_K(8)
 #undef MG_GUIDE_K
     default: e = launch_pdl(k_guide<0>, grid, dim3(kThreads), 0, s, p, gens_done, fw_x, fw_amp, sparks, top, bottom,
-                            guides, op_guides);
+                            gv_in, gv_out, guides, op_guides);
   }
   return e == cudaSuccess ? 1 : -1;
 }

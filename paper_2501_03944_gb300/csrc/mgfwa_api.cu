@@ -60,6 +60,9 @@ struct mgfwa_handle {
   int32_t* winner = nullptr;
   float* f_old = nullptr;     // [B*mu] fitness before the selection (loser-out tournament)
   int32_t* loser = nullptr;   // [B*mu] 1 where the last tournament re-drew the firework
+  float* gv = nullptr;        // [B*mu*m][Dp] lagged multi-guiding: the last recorded guiding vectors
+  bool gv_ready = false;      // gv holds a generation's vectors
+  bool lag_now = false;       // this generation guides from the previous one's vectors
   int32_t* elite = nullptr;     // [B*mu*E] spark rows picked for the FP32 re-score
   GradPlan rescore_plan;        // FP32 forward of the B*mu*E re-scored rows
   float* rescore_scratch = nullptr;
@@ -316,35 +319,57 @@ mgfwa_status run_phase(mgfwa_t* h, int32_t phase) {
   switch (phase) {
     case MGFWA_PHASE_EXPLODE: {
       if (!h->capturing) h->gen += 1;
+      // lagged multi-guiding: once a generation's vectors are recorded, the
+      // guiding sparks come from them right after the explosion
+      h->lag_now = h->cfg.lagged_guiding && h->gv_ready;
       Mark mk(h, G_EXPLODE);
       MG_LAUNCH(h, launch_explode(p, h->gens_done, h->fw_x, h->fw_amp, h->sparks, op_rows(h, 0), h->stream),
                 "explode");
+      if (h->lag_now)
+        MG_LAUNCH(h, launch_guide(p, h->gens_done, h->fw_x, h->fw_amp, h->sparks, h->top, h->bottom,
+                                  h->sparks + n_e * p.Dp, op_rows(h, n_e), h->stream, h->gv, nullptr),
+                  "lagged guide");
       return MGFWA_OK;
     }
     case MGFWA_PHASE_EVAL_E:
+      // lagged: explosion and guiding rows are contiguous and evaluated in one launch; the means are
+      // finished by the rank and the elite pick when both fuse the finish, else here
+      if (h->lag_now) return eval_rows(h, 0, (int32_t)(n_e + (int64_t)p.B * p.mu * p.m), prec, finish_in_pick(h));
       return eval_rows(h, 0, (int32_t)n_e, prec, finish_in_rank(h));
     case MGFWA_PHASE_RANK: {
       Mark mk(h, G_RANK);
-      if (finish_in_rank(h))
-        MG_LAUNCH(h, launch_rank(p, h->fit, h->top, h->bottom, h->stream, h->partial, h->mtiles, h->mlp.N), "rank");
+      const bool fin = h->lag_now ? finish_in_pick(h) : finish_in_rank(h);
+      const int64_t stride = h->lag_now ? n_e + (int64_t)p.B * p.mu * p.m : n_e;
+      if (fin)
+        MG_LAUNCH(h, launch_rank(p, h->fit, h->top, h->bottom, h->stream, h->partial, h->mtiles, h->mlp.N, stride),
+                  "rank");
       else
         MG_LAUNCH(h, launch_rank(p, h->fit, h->top, h->bottom, h->stream), "rank");
       return MGFWA_OK;
     }
     case MGFWA_PHASE_GUIDE: {
       Mark mk(h, G_GUIDE);
+      // lagged: record this generation's vectors only (its guiding sparks exist already)
       MG_LAUNCH(h, launch_guide(p, h->gens_done, h->fw_x, h->fw_amp, h->sparks, h->top, h->bottom,
-                                h->sparks + n_e * p.Dp, op_rows(h, n_e), h->stream), "guide");
+                                h->lag_now ? nullptr : h->sparks + n_e * p.Dp, op_rows(h, n_e), h->stream, nullptr,
+                                h->cfg.lagged_guiding ? h->gv : nullptr),
+                "guide");
+      if (h->cfg.lagged_guiding) h->gv_ready = true;
       return MGFWA_OK;
     }
     case MGFWA_PHASE_EVAL_G:
+      if (h->lag_now) return MGFWA_OK;
       return eval_rows(h, n_e, p.B * p.mu * p.m, prec, finish_in_pick(h));
     case MGFWA_PHASE_RESCORE: {
       // low precision: each firework's elite candidates get their fitness in FP32
       const int32_t E = h->cfg.elite_rescore;
       if (!rescore_on(h)) return MGFWA_OK;
       Mark mk(h, G_RESCORE);
-      if (finish_in_pick(h))
+      if (finish_in_pick(h) && h->lag_now)
+        MG_LAUNCH(h, launch_elite_pick(p, h->fit, h->fit + n_e, E, h->elite, h->stream, h->partial + n_e, h->mtiles,
+                                       h->mlp.N, n_e + (int64_t)p.B * p.mu * p.m),
+                  "elite pick");
+      else if (finish_in_pick(h))
         MG_LAUNCH(h, launch_elite_pick(p, h->fit, h->fit + n_e, E, h->elite, h->stream, h->partial, h->mtiles,
                                        h->mlp.N),
                   "elite pick");
@@ -424,6 +449,15 @@ mgfwa_status one_generation(mgfwa_t* h) {
     }
     return MGFWA_OK;
   }
+  if (h->cfg.lagged_guiding && !h->gv_ready) {
+    // lagged multi-guiding's first generation has no vectors to guide from: it runs as written, kernel by
+    // kernel, and the graph is captured at the next one
+    for (int32_t ph = MGFWA_PHASE_EXPLODE; ph <= MGFWA_PHASE_REFINE; ++ph) {
+      mgfwa_status st = run_phase(h, ph);
+      if (st != MGFWA_OK) return st;
+    }
+    return MGFWA_OK;
+  }
   if (!h->gen_exec) {
     mgfwa_status st = capture_generation(h);
     if (st != MGFWA_OK) return st;
@@ -484,6 +518,8 @@ mgfwa_status validate(const mgfwa_config* c, const mgfwa_objective* o) {
     return fail(nullptr, MGFWA_EINVAL, "precision %d not supported (FP32 = 0, BF16 = 1, FP8 = 2)", c->precision);
   if (c->refine_every < 0) return fail(nullptr, MGFWA_EINVAL, "refine_every must be >= 0");
   if (c->loser_out != 0 && c->loser_out != 1) return fail(nullptr, MGFWA_EINVAL, "loser_out must be 0 or 1");
+  if (c->lagged_guiding != 0 && c->lagged_guiding != 1)
+    return fail(nullptr, MGFWA_EINVAL, "lagged_guiding must be 0 or 1");
   if (c->refine_every > 0) {
     if (o->kind != MGFWA_OBJ_MLP_CE) return fail(nullptr, MGFWA_EINVAL, "refinement needs an MLP objective");
     if (c->refine_steps < 1 || c->refine_steps > 10000)
@@ -614,6 +650,7 @@ uint64_t problem_fingerprint(const mgfwa_config* cfg, const mgfwa_objective* obj
   mix(&cfg->refine_steps, sizeof(cfg->refine_steps));
   mix(&cfg->refine_lr, sizeof(cfg->refine_lr));
   mix(&cfg->loser_out, sizeof(cfg->loser_out));
+  mix(&cfg->lagged_guiding, sizeof(cfg->lagged_guiding));
   mix(&obj->kind, sizeof(obj->kind));
   mix(&obj->n_layers, sizeof(obj->n_layers));
   if (obj->kind == MGFWA_OBJ_MLP_CE) {
@@ -759,6 +796,7 @@ size_t carve_all(mgfwa_t* h, char* base) {
   h->winner = carve<int32_t>(cur, F + p.B + 1);  // per firework, per run, the generation (the selection's decisions)
   h->f_old = carve<float>(cur, F);
   h->loser = carve<int32_t>(cur, F);
+  h->gv = cfg->lagged_guiding ? carve<float>(cur, F * p.m * p.Dp) : nullptr;
   h->elite = carve<int32_t>(cur, F * (cfg->elite_rescore > 0 ? cfg->elite_rescore : 1));
   const bool rescore = want_op && cfg->elite_rescore > 0;
   h->rescore_scratch = rescore ? carve<float>(cur, (size_t)h->rescore_plan.floats) : nullptr;
@@ -1065,6 +1103,7 @@ mgfwa_status mgfwa_checkpoint_save(mgfwa_t* h, void* host, int64_t bytes) {
   const int64_t need = (int64_t)sizeof(CkptHeader) + ckpt_payload(h);
   if (!host || bytes != need) return fail(h, MGFWA_EINVAL, "checkpoint: buffer must hold %lld bytes", (long long)need);
   if (h->next_phase != MGFWA_PHASE_EXPLODE) return fail(h, MGFWA_EINVAL, "a debug generation is in progress");
+  if (h->cfg.lagged_guiding) return fail(h, MGFWA_EINVAL, "checkpoint: not supported with lagged_guiding");
   CkptHeader hd{kCkptMagic, h->fingerprint, h->evals, h->launches, h->gen, 0u, ckpt_payload(h)};
   char* out = static_cast<char*>(host) + sizeof(CkptHeader);
   const int64_t F = (int64_t)h->p.B * h->p.mu, B = h->p.B;
@@ -1091,6 +1130,7 @@ mgfwa_status mgfwa_checkpoint_load(mgfwa_t* h, const void* host, int64_t bytes) 
   if (!host || bytes != need) return fail(h, MGFWA_EINVAL, "checkpoint: buffer must hold %lld bytes", (long long)need);
   if (h->next_phase != MGFWA_PHASE_EXPLODE || h->grouped)
     return fail(h, MGFWA_EINVAL, "checkpoint: not between generations, or the handle is in a group");
+  if (h->cfg.lagged_guiding) return fail(h, MGFWA_EINVAL, "checkpoint: not supported with lagged_guiding");
   CkptHeader hd;
   std::memcpy(&hd, host, sizeof(hd));
   if (hd.magic != kCkptMagic || hd.payload_bytes != ckpt_payload(h))
@@ -1255,8 +1295,10 @@ mgfwa_status mgfwa_group_create(mgfwa_t* const* handles, int32_t count, mgfwa_gr
         set_thread_error("group: a handle appears twice");
         return MGFWA_EINVAL;
       }
-    if (h->refine || h->profiling || h->next_phase != MGFWA_PHASE_EXPLODE || h->device != handles[0]->device) {
-      set_thread_error("group: members must not refine, profile or be inside a debug generation, one device");
+    if (h->refine || h->profiling || h->cfg.lagged_guiding || h->next_phase != MGFWA_PHASE_EXPLODE ||
+        h->device != handles[0]->device) {
+      set_thread_error("group: members must not refine, profile, guide lagged or be inside a debug generation, "
+                       "one device");
       return MGFWA_EINVAL;
     }
   }
@@ -1392,6 +1434,10 @@ bool buffer_view(mgfwa_t* h, int32_t buf, BufView* v) {
       *v = {h->relite, 0, 0, 0, (int64_t)sizeof(int32_t) * p.B};
       return true;
     case MGFWA_BUF_LOSER: *v = {h->loser, 0, 0, 0, (int64_t)sizeof(int32_t) * F}; return true;
+    case MGFWA_BUF_GV:
+      if (!h->gv) return false;
+      *v = {h->gv, F * p.m, rb, pitch, 0};
+      return true;
   }
   return false;
 }

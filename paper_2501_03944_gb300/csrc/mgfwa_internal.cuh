@@ -208,17 +208,18 @@ int launch_init(const Problem& p, float* fw_x, float* fw_amp, cudaStream_t s);
 int launch_explode(const Problem& p, const uint32_t* gens_done, const float* fw_x, const float* fw_amp,
                    float* sparks, const OpDesc& op, cudaStream_t s);
 
-// With `partial` ([mtiles][mu*lam] per-sample-tile loss sums of the
-// explosion rows, N samples), the rank kernel also finishes the explosion
-// fitness into fit_e, exactly as launch_fitness_finish would.
+// With `partial` ([mtiles][stride] per-sample-tile loss sums, the explosion
+// rows first, N samples; stride 0 means B*mu*lam), the rank kernel also
+// finishes the explosion fitness into fit_e, exactly as
+// launch_fitness_finish would.
 int launch_rank(const Problem& p, float* fit_e, int32_t* top, int32_t* bottom, cudaStream_t s,
-                const float* partial = nullptr, int32_t mtiles = 0, int64_t N = 0);
+                const float* partial = nullptr, int32_t mtiles = 0, int64_t N = 0, int64_t stride = 0);
 
 // Guiding sparks written to `guides` (mu*m rows of stride Dp) and, if non-
 // null, their operand rows `op_guides`.
 int launch_guide(const Problem& p, const uint32_t* gens_done, const float* fw_x, const float* fw_amp,
                  const float* sparks, const int32_t* top, const int32_t* bottom, float* guides,
-                 const OpDesc& op_guides, cudaStream_t s);
+                 const OpDesc& op_guides, cudaStream_t s, const float* gv_in = nullptr, float* gv_out = nullptr);
 
 // Per run: best-so-far over its fireworks (init: the first minimum).
 int launch_run_best_init(const Problem& p, const float* fw_x, const float* fw_f, float* best_x, float* best_f,
@@ -253,11 +254,13 @@ int launch_fitness_finish(const float* partial, int32_t mtiles, int32_t count, i
 // `E` best of its lam explosion and m guiding sparks by the current
 // fitness, as rows of the spark buffer (explosion z*lam + c, guiding
 // n_e + z*m + q) into elite[z*E + e].
-// With `partial` ([mtiles][mu*m] per-sample-tile loss sums of the guiding
-// rows, N samples), the pick also finishes the guiding fitness into fit_g
-// first, exactly as launch_fitness_finish would.
+// With `partial` ([mtiles][stride] per-sample-tile loss sums whose columns
+// start at the guiding rows, N samples; stride 0 means B*mu*m), the pick
+// also finishes the guiding fitness into fit_g first, exactly as
+// launch_fitness_finish would.
 int launch_elite_pick(const Problem& p, const float* fit_e, float* fit_g, int32_t E, int32_t* elite,
-                      cudaStream_t s, const float* partial = nullptr, int32_t mtiles = 0, int64_t N = 0);
+                      cudaStream_t s, const float* partial = nullptr, int32_t mtiles = 0, int64_t N = 0,
+                      int64_t stride = 0);
 
 int launch_fitness_sphere(const float* rows, int64_t ld, int64_t D, int32_t count, float* fit, cudaStream_t s);
 

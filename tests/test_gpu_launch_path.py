@@ -6,7 +6,9 @@ events, and with the fitness means finished by their own kernel instead
 of inside the rank and the elite pick.  Both paths must end bitwise in the
 same state: FP32, BF16 with the elite re-score (at full size on the
 tensor-core FP32 layer with its fused output layer), FP8, a three-layer
-net, the sphere, two runs in one handle, and the hybrid refinement."""
+net, the sphere, two runs in one handle, the hybrid refinement, the
+loser-out tournament and lagged multi-guiding (its first generation kernel
+by kernel, the graph from the second)."""
 import numpy as np
 import pytest
 
@@ -42,6 +44,10 @@ def _specs(pkg):
                    {"refine_every": 2, "refine_steps": 4, "refine_lr": 0.5}),
         "loser_out": (W.scaled(big, eval_budget=W.budget_for_generations(3, 20, 4, 6)), 29, pkg.MGFWA_BF16,
                       {"loser_out": 1}),
+        "lagged_bf16": (W.scaled(big, eval_budget=W.budget_for_generations(3, 20, 4, 6)), 30, pkg.MGFWA_BF16,
+                        {"lagged_guiding": 1}),
+        "lagged_fp32": (W.scaled(small, eval_budget=W.budget_for_generations(5, 40, 4, 8)), 31, pkg.MGFWA_FP32,
+                        {"lagged_guiding": 1}),
     }
 
 
@@ -51,7 +57,7 @@ def _make(pkg, w, seed, prec, kw):
 
 
 @pytest.mark.parametrize("case", ["fp32", "bf16", "bf16_full", "fp8", "three_layer", "sphere", "two_runs", "refine",
-                                  "loser_out"])
+                                  "loser_out", "lagged_bf16", "lagged_fp32"])
 def test_graph_replay_equals_kernel_by_kernel(pkg, case):
     spec = _specs(pkg)[case]
     states = []
