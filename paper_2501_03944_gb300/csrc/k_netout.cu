@@ -16,9 +16,19 @@ namespace mgfwa {
 namespace {
 
 constexpr int kBK = 16;      // k-slab depth
-constexpr int kTile = 32;    // output tile: 32 rows x 32 columns per block
+constexpr int kTN = 32;      // output tile columns per block
 constexpr int kGroups = 4;   // fan-in chunks, one per 64-thread group
-constexpr int kPad = kTile + 4;
+constexpr int kPadW = kTN + 4;
+
+// Tile geometry for TR output rows per thread: 8 TR rows x 32 columns per block.
+template <int TR>
+struct NetTile {
+  static constexpr int kTM = 8 * TR;
+  static constexpr int kPadA = kTM + 4;
+  static constexpr int kGroupFloats = 2 * kBK * (kPadA + kPadW);  // two slab buffers of A and W per group
+  static constexpr size_t kSmem = sizeof(float) * kGroups * kGroupFloats;
+  static_assert(kTM * kPadW <= kGroupFloats, "partial tiles must fit in the slab space");
+};
 
 __device__ __forceinline__ float act32(int a, float v) {
   if (a == kActTanh) return tanhf(v);
@@ -31,33 +41,39 @@ __host__ __device__ __forceinline__ int chunk_len(int k) { return kBK * ((k + kB
 
 // out[r][j] = act(sum_i A[r][i] W[j][i] + b[j]) (no activation when act < 0)
 // for r < rows, j < n; A row stride lda, out row stride ldo.  One 256-thread
-// block per 32 x 32 output tile.  Group g (threads 64 g ..) multiplies the
-// tile over its fan-in chunk, 4 x 4 outputs per thread: k-slabs of A and W
-// go through registers into the group's two shared buffers (k-major, so a
-// thread's 4 rows and 4 columns are contiguous), the next slab's global loads
-// in flight while the current one is multiplied, one group barrier per slab.
-// The four partial tiles then meet in shared memory and every thread adds
-// them in group order for 4 outputs, adds the bias and applies the activation.
-// A quarter of the fan-in per group cuts each block's serial slab chain to a
-// quarter, which is what bounds the small-row launches (the guiding sparks).
-__global__ void __launch_bounds__(256, 4) k_net_layer(const float* __restrict__ A, int64_t lda, int32_t rows,
+// block per (8 TR) x 32 output tile.  Group g (threads 64 g ..) multiplies
+// the tile over its fan-in chunk, TR x 4 outputs per thread:
+// k-slabs of A and W go through registers into the group's two shared
+// buffers (k-major, so a thread's rows and columns are contiguous), the next
+// slab's global loads in flight while the current one is multiplied, one
+// group barrier per slab.  The four partial tiles then meet in shared memory
+// and every thread adds them in group order for 8 outputs, adds the bias and
+// applies the activation.  A quarter of the fan-in per group cuts each
+// block's serial slab chain to a quarter, which is what bounds the small-row
+// launches (the guiding sparks).  TR = 8 takes three 16-byte shared loads per
+// 32 FMAs (for launches that fill the SMs), TR = 4 two per 16 with twice the
+// blocks.  Both compute every output with the same operations in the same
+// order, so the choice never changes a result.
+template <int TR>
+__global__ void __launch_bounds__(256, TR == 4 ? 4 : 2) k_net_layer(const float* __restrict__ A, int64_t lda, int32_t rows,
                                                    const float* __restrict__ W, const float* __restrict__ bias,
                                                    int32_t k, int32_t n, int32_t act, float* __restrict__ out,
                                                    int64_t ldo) {
+  constexpr int kTM = NetTile<TR>::kTM, kPadA = NetTile<TR>::kPadA, kGroupFloats = NetTile<TR>::kGroupFloats;
   griddep_wait();
   griddep_launch_dependents();
-  // slabs [group][buffer][A or W][kBK][kPad]; afterwards the partial tiles [group][kTile][kPad]
-  __shared__ __align__(16) float sm[kGroups * 2 * 2 * kBK * kPad];
+  // slabs [group][buffer]{A [kBK][kPadA], W [kBK][kPadW]}; afterwards the partial tiles [group][kTM][kPadW]
+  extern __shared__ __align__(16) float sm[];
   const int g = threadIdx.x >> 6, t = threadIdx.x & 63;
   const int tx = t & 7, ty = t >> 3;
-  const int r0 = blockIdx.x * kTile, j0 = blockIdx.y * kTile;  // row tiles on x: up to 2^24 rows
+  const int r0 = blockIdx.x * kTM, j0 = blockIdx.y * kTN;  // row tiles on x: up to 2^24 rows
   const int c = chunk_len(k);
   const int kbeg = g * c, kend = min(kbeg + c, k);
   const int slabs = kend > kbeg ? (kend - kbeg + kBK - 1) / kBK : 0;
-  float* const base = sm + g * (2 * 2 * kBK * kPad);
-  auto As = [&](int buf) { return base + buf * (2 * kBK * kPad); };
-  auto Ws = [&](int buf) { return base + buf * (2 * kBK * kPad) + kBK * kPad; };
-  constexpr int L = kTile * kBK / 64;  // slab elements each thread stages, per operand
+  float* const base = sm + g * kGroupFloats;
+  auto As = [&](int buf) { return base + buf * kBK * (kPadA + kPadW); };
+  auto Ws = [&](int buf) { return base + buf * kBK * (kPadA + kPadW) + kBK * kPadA; };
+  constexpr int LA = kTM * kBK / 64, LW = kTN * kBK / 64;  // slab elements each thread stages
   // element q of a thread is (row rq + 4 q, column kq) of the slab: 16
   // neighbouring threads read 16 consecutive floats of one row
   const int kq = t % kBK, rq = t / kBK;
@@ -66,32 +82,29 @@ __global__ void __launch_bounds__(256, 4) k_net_layer(const float* __restrict__ 
   const int64_t sa = 4 * lda, sw = 4 * (int64_t)k;
   unsigned va = 0, vw = 0;
 #pragma unroll
-  for (int q = 0; q < L; ++q) {
-    va |= (r0 + rq + 4 * q < rows ? 1u : 0u) << q;
-    vw |= (j0 + rq + 4 * q < n ? 1u : 0u) << q;
-  }
-  float ra[L], rw[L];
+  for (int q = 0; q < LA; ++q) va |= (r0 + rq + 4 * q < rows ? 1u : 0u) << q;
+#pragma unroll
+  for (int q = 0; q < LW; ++q) vw |= (j0 + rq + 4 * q < n ? 1u : 0u) << q;
+  float ra[LA], rw[LW];
   auto fetch = [&](int k0) {
     const bool kin = k0 + kq < kend;
 #pragma unroll
-    for (int q = 0; q < L; ++q) {
-      ra[q] = (kin && (va >> q & 1u)) ? pa[q * sa + k0] : 0.0f;
-      rw[q] = (kin && (vw >> q & 1u)) ? pw[q * sw + k0] : 0.0f;
-    }
+    for (int q = 0; q < LA; ++q) ra[q] = (kin && (va >> q & 1u)) ? pa[q * sa + k0] : 0.0f;
+#pragma unroll
+    for (int q = 0; q < LW; ++q) rw[q] = (kin && (vw >> q & 1u)) ? pw[q * sw + k0] : 0.0f;
   };
   auto stash = [&](int buf) {
-    float* a = As(buf) + kq * kPad + rq;
-    float* w = Ws(buf) + kq * kPad + rq;
+    float* a = As(buf) + kq * kPadA + rq;
+    float* w = Ws(buf) + kq * kPadW + rq;
 #pragma unroll
-    for (int q = 0; q < L; ++q) {
-      a[4 * q] = ra[q];
-      w[4 * q] = rw[q];
-    }
+    for (int q = 0; q < LA; ++q) a[4 * q] = ra[q];
+#pragma unroll
+    for (int q = 0; q < LW; ++q) w[4 * q] = rw[q];
   };
   auto group_sync = [&]() { asm volatile("bar.sync %0, 64;" ::"r"(g + 1) : "memory"); };
-  float acc[4][4];
+  float acc[TR][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TR; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
   if (slabs > 0) {
@@ -106,11 +119,16 @@ __global__ void __launch_bounds__(256, 4) k_net_layer(const float* __restrict__ 
     const float* w = Ws(cur);
 #pragma unroll
     for (int kk = 0; kk < kBK; ++kk) {
-      const float4 av = *reinterpret_cast<const float4*>(a + kk * kPad + ty * 4);
-      const float4 wv = *reinterpret_cast<const float4*>(w + kk * kPad + tx * 4);
-      const float ai[4] = {av.x, av.y, av.z, av.w}, wj[4] = {wv.x, wv.y, wv.z, wv.w};
+      float ai[TR];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int h = 0; h < TR / 4; ++h) {
+        const float4 av = *reinterpret_cast<const float4*>(a + kk * kPadA + ty * TR + 4 * h);
+        ai[4 * h] = av.x; ai[4 * h + 1] = av.y; ai[4 * h + 2] = av.z; ai[4 * h + 3] = av.w;
+      }
+      const float4 wv = *reinterpret_cast<const float4*>(w + kk * kPadW + tx * 4);
+      const float wj[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+      for (int i = 0; i < TR; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ai[i], wj[j], acc[i][j]);
     }
@@ -120,20 +138,20 @@ __global__ void __launch_bounds__(256, 4) k_net_layer(const float* __restrict__ 
     group_sync();
   }
   __syncthreads();  // every group done with its slabs: the space holds the partial tiles now
-  float* part = sm + g * (kTile * kPad);
+  float* part = sm + g * (kTM * kPadW);
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-    *reinterpret_cast<float4*>(part + (ty * 4 + i) * kPad + tx * 4) =
+  for (int i = 0; i < TR; ++i)
+    *reinterpret_cast<float4*>(part + (ty * TR + i) * kPadW + tx * 4) =
         make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
   __syncthreads();
 #pragma unroll
-  for (int q = 0; q < kTile * kTile / 256; ++q) {
-    const int o = threadIdx.x + 256 * q, rr = o / kTile, cc = o % kTile;
+  for (int q = 0; q < kTM * kTN / 256; ++q) {
+    const int o = threadIdx.x + 256 * q, rr = o / kTN, cc = o % kTN;
     const int r = r0 + rr, j = j0 + cc;
     if (r >= rows || j >= n) continue;
-    float z = sm[rr * kPad + cc];
+    float z = sm[rr * kPadW + cc];
 #pragma unroll
-    for (int h = 1; h < kGroups; ++h) z += sm[h * (kTile * kPad) + rr * kPad + cc];
+    for (int h = 1; h < kGroups; ++h) z += sm[h * (kTM * kPadW) + rr * kPadW + cc];
     z += bias[j];
     out[(int64_t)r * ldo + j] = act >= 0 ? act32(act, z) : z;
   }
@@ -175,6 +193,11 @@ __global__ void __launch_bounds__(256) k_net_f64(NetOut net, const float* __rest
 int launch_net_output(const NetOut& net, const float* rows, int64_t ld, int32_t count, float* fit, float* scratch,
                       int64_t scratch_ld, cudaStream_t s) {
   if (count <= 0) return 0;
+  if (ensure_smem_limit<k_net_layer<8>>(NetTile<8>::kSmem) != cudaSuccess) return -1;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                 cudaSuccess)
+    return -1;
   const float* a = rows;
   int64_t lda = ld;
   int n = 0;
@@ -186,10 +209,16 @@ int launch_net_output(const NetOut& net, const float* rows, int64_t ld, int32_t 
     const float* W = net.params + net.w_off[l];
     const float* b = net.params + net.b_off[l];
     const int32_t ak = last ? -1 : net.acts[l];
-    const dim3 grid((unsigned)((count + kTile - 1) / kTile), (unsigned)((fo + kTile - 1) / kTile));
-    if (launch_pdl(k_net_layer, grid, dim3(256), 0, s, a, lda, count, W, b, (int32_t)fi, (int32_t)fo, ak, o, ldo) !=
-        cudaSuccess)
-      return -1;
+    // 64-row tiles where they fill the SMs, else 32-row tiles (twice the blocks)
+    const bool wide = (int64_t)((count + 63) / 64) * ((fo + kTN - 1) / kTN) >= sms;
+    cudaError_t e;
+    if (wide)
+      e = launch_pdl(k_net_layer<8>, dim3((unsigned)((count + 63) / 64), (unsigned)((fo + kTN - 1) / kTN)),
+                     dim3(256), NetTile<8>::kSmem, s, a, lda, count, W, b, (int32_t)fi, (int32_t)fo, ak, o, ldo);
+    else
+      e = launch_pdl(k_net_layer<4>, dim3((unsigned)((count + 31) / 32), (unsigned)((fo + kTN - 1) / kTN)),
+                     dim3(256), NetTile<4>::kSmem, s, a, lda, count, W, b, (int32_t)fi, (int32_t)fo, ak, o, ldo);
+    if (e != cudaSuccess) return -1;
     ++n;
     a = o;
     lda = ldo;

@@ -74,7 +74,7 @@ def test_create_rejects_bad_configs_without_a_gpu(pkg):
     w = W.MLP_8_16_3
     X, y = W.make_data(w)
     bad = [dict(sparks_per_firework=41), dict(lb=1.0, ub=-1.0), dict(dim=100), dict(eval_budget=2),
-           dict(sigma=0.0), dict(precision=7), dict(n_runs=0)]
+           dict(sigma=0.0), dict(precision=7), dict(n_runs=0), dict(loser_out=2), dict(lagged_guiding=-1)]
     for over in bad:
         with pytest.raises(pkg.MgfwaError) as e:
             pkg.Mgfwa.for_workload(w, 0, X=X, y=y, **over)
