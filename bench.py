@@ -234,14 +234,14 @@ def reference_arm(args):
     return 0
 
 
-def testbed_net(pkg, stream, net_id, steps):
+def testbed_net(pkg, stream, net_id, steps, **handle_kw):
     """sparks/s of one run on Table 2's network `net_id` (FP32 layers on the CUDA cores), after 3 warm-up
     generations, with the FP32 FLOP rate of its layers."""
     import torch
     w = W.table2_net(net_id)
     w = W.scaled(w, eval_budget=W.budget_for_generations(w.n_fireworks, w.sparks_per_firework,
                                                          w.guiding_per_firework, steps + 5))
-    h = pkg.Mgfwa.for_workload(w, 23, stream=stream.cuda_stream)
+    h = pkg.Mgfwa.for_workload(w, 23, stream=stream.cuda_stream, **handle_kw)
     h.step(3)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -361,6 +361,9 @@ def gpu_arm(args):
                                                                  max(5, args.steps // 2)), precision=args.precision)
         # the paper's own testbed (Sec. 4.1): Table 2's network 10, its output minimised over its input
         extra["testbed_net10"] = testbed_net(pkg, stream, 10, max(5, args.steps // 2))
+        # the same with lagged multi-guiding: the 40 guiding rows ride in the explosion rows' launches
+        extra["testbed_net10_lagged"] = dict(testbed_net(pkg, stream, 10, max(5, args.steps // 2),
+                                                         lagged_guiding=1), lagged_guiding=1)
         # 8 independent runs of the same workload in one handle (one fitness launch per generation)
         extra["batched_8_runs"] = dict(timed_generations({"precision": prec, "n_runs": 8}, max(5, args.steps // 2)),
                                        runs=8, precision=args.precision)

@@ -137,6 +137,19 @@ def test_single_linear_layer_and_tanh(pkg):
         assert abs(got[i] - ref[i]) <= 10.0 * sig + 1e-30, (i, got[i], ref[i], sig)
 
 
+def test_value_does_not_depend_on_the_batch(pkg):
+    """A spark's value is the same bit for bit whichever rows share its launch: 1040 rows (64-row tiles
+    on the wide layers), 40 at a time and 7 (32-row tiles)."""
+    w = W.table2_net(10)
+    xs = _inputs(w, 1040, 5)
+    with pkg.Mgfwa.for_workload(w, 1) as run:
+        full = run.evaluate(xs)
+        parts = np.concatenate([run.evaluate(xs[i:i + 40]) for i in range(0, len(xs), 40)])
+        few = run.evaluate(xs[100:107])
+    assert np.array_equal(full, parts)
+    assert np.array_equal(full[100:107], few)
+
+
 @pytest.mark.parametrize("net_id", [5, 10])
 def test_generation_fitness_and_reported_best(pkg, net_id):
     """Whole generations through the library: every spark's fitness (read
