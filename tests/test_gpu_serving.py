@@ -21,7 +21,7 @@ def pkg():
 
 
 def _mix(pkg):
-    """Requests of three kinds and several budgets: (workload, seed, precision, data)."""
+    """Requests of four kinds and several budgets: (workload, seed, precision, data)."""
     small = W.MLP_8_16_3
     big = W.scaled(W.MLP_784_64_10, n_samples=300, n_fireworks=3, sparks_per_firework=20, guiding_per_firework=4)
     sph = W.SPHERE_30
@@ -38,6 +38,10 @@ def _mix(pkg):
             w = W.scaled(sph, eval_budget=W.budget_for_generations(sph.n_fireworks, sph.sparks_per_firework,
                                                                    sph.guiding_per_firework, 5 + k))
             out.append((w, 300 + k, pkg.MGFWA_FP32, (None, None)))
+    # the paper's testbed objective: the server copies the network's parameters at submit
+    net = W.scaled(W.table2_net(5), sparks_per_firework=40, guiding_per_firework=4,
+                   eval_budget=W.budget_for_generations(5, 40, 4, 6))
+    out.append((net, 400, pkg.MGFWA_FP32, (None, None)))
     return out
 
 

@@ -38,6 +38,24 @@ def test_footprint_grows_with_the_problem(pkg):
         pkg.mgfwa_footprint(bad, bobj)
 
 
+def test_testbed_footprint_and_submit(pkg):
+    """The testbed objective's arena holds the network's parameters and two hidden-activation buffers of
+    [rows][widest hidden layer]; the server copies the parameters at submit."""
+    w = W.table2_net(5)  # 100 -> 64 x 8 -> 1
+    cfg, obj = pkg.workload_request(w, seed=1)
+    fp = pkg.mgfwa_footprint(cfg, obj)
+    params = W.mlp_param_count(w.widths)
+    rows = w.sparks_per_generation
+    assert fp >= 4 * (params + 2 * rows * 64 + rows * 128)
+    with pkg.Server(1, 1 << 40) as s:
+        rid = s.submit(cfg, obj)
+        del obj
+        import gc
+        gc.collect()
+        info = s.poll(rid)[0]
+        assert info.state == pkg.MGFWA_REQ_QUEUED and info.footprint == fp
+
+
 def test_submit_rejects_requests_larger_than_the_limit(pkg):
     cfg, obj = pkg.workload_request(W.MLP_8_16_3, seed=1)
     fp = pkg.mgfwa_footprint(cfg, obj)
