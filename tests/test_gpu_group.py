@@ -1,6 +1,6 @@
 """Groups: many runs of different shapes (dimension, population, network,
 batch, precision) stepped together, one CUDA graph launch per generation
-(the batching trait for uneven runs).  The claim to check is that grouping
+(the batching trait for uneven runs), the paper's testbed objective among them.  The claim to check is that grouping
 changes no result: every member ends bitwise where the same handle ends
 when run alone, also when its budget ends before the others' (the graph is
 captured again without it) and when group steps and the member's own steps
@@ -33,11 +33,13 @@ def _specs(pkg):
         (W.scaled(small, eval_budget=W.budget_for_generations(5, 40, 4, 10)), 14, pkg.MGFWA_FP32, {"n_runs": 2}),
         (W.scaled(deep, eval_budget=W.budget_for_generations(2, 16, 4, 5)), 15, pkg.MGFWA_BF16, {}),
         (W.scaled(big, eval_budget=W.budget_for_generations(3, 20, 4, 4)), 16, pkg.MGFWA_FP8, {"elite_rescore": 0}),
+        (W.scaled(W.table2_net(6), sparks_per_firework=40, guiding_per_firework=4,
+                  eval_budget=W.budget_for_generations(5, 40, 4, 7)), 17, pkg.MGFWA_FP32, {}),
     ]
 
 
 def _make(pkg, w, seed, prec, kw):
-    X, y = (None, None) if w.kind == W.KIND_SPHERE else W.make_data(w)
+    X, y = W.make_data(w) if w.kind == W.KIND_MLP_CE else (None, None)
     return pkg.Mgfwa.for_workload(w, seed, precision=prec, X=X, y=y, **kw)
 
 
