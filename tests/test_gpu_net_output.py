@@ -137,6 +137,26 @@ def test_single_linear_layer_and_tanh(pkg):
         assert abs(got[i] - ref[i]) <= 10.0 * sig + 1e-30, (i, got[i], ref[i], sig)
 
 
+def test_maximum_shapes(pkg):
+    """The ABI's limits: a 4096-wide layer (GELU) and 16 layers; 70 rows (a full 64-row tile and a
+    ragged one)."""
+    wide = W.scaled(W.table2_net(2), widths=(4096, 4096, 1), acts=(W.ACT_GELU,), dim=4096, name="wide")
+    deep = W.scaled(W.table2_net(1), widths=(10,) + (24,) * 15 + (1,), acts=(W.ACT_RELU,) * 15, name="deep")
+    for w, n_model in ((wide, 6), (deep, 70)):
+        params = W.make_net(w)
+        prob = oracle.Problem.for_workload(w)
+        xs = _inputs(w, 70, 21)
+        with pkg.Mgfwa.for_workload(w, 4) as run:
+            got = run.evaluate(xs).astype(np.float64)
+            x0, f0, _ = run.best()  # the FP64 report (64 KB of shared memory at width 4096)
+        assert abs(f0 - prob.fitness(x0)) <= 1e-9 * max(1.0, abs(f0)), w.name
+        ref = prob.fitness_many(xs, n_threads=8)
+        for i in range(n_model):
+            _, sig = fp32_sigma(w, params, xs[i])
+            assert abs(got[i] - ref[i]) <= 10.0 * sig + 1e-30, (w.name, i, got[i], ref[i], sig)
+        assert np.all(np.abs(got - ref) <= 1e-3 * (np.abs(ref) + 1e-2)), w.name
+
+
 def test_value_does_not_depend_on_the_batch(pkg):
     """A spark's value is the same bit for bit whichever rows share its launch: 1040 rows (64-row tiles
     on the wide layers), 40 at a time and 7 (32-row tiles)."""
