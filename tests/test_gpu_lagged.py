@@ -70,6 +70,44 @@ def test_lagged_phase_by_phase(pkg, name):
         assert run.info().evals == w.n_fireworks + gens * w.sparks_per_generation
 
 
+def test_lagged_with_the_loser_out_tournament(pkg):
+    """Both variants on: a re-drawn firework's next guiding sparks come from the recorded vectors at its
+    new position (the mapping draws inside its reset amplitude box), bit for bit as in the oracle."""
+    w = W.scaled(W.MLP_8_16_3, n_samples=300, eval_budget=W.budget_for_generations(5, 40, 4, 5))
+    seed = 77
+    X, y = W.make_data(w)
+    prob = oracle.Problem.for_workload(w, X, y)
+    p = oracle.params_for(w, lagged_guiding=1, loser_out=1)
+    g_max = oracle.g_max(p, w.eval_budget)
+    losers = 0
+    with pkg.Mgfwa.for_workload(w, seed, X=X, y=y, lagged_guiding=1, loser_out=1) as run:
+        fw_x, fw_a = oracle.init(p, seed)
+        fw_f = prob.fitness_many(fw_x).astype(np.float32)
+        run.write(pkg.MGFWA_BUF_FW_F, fw_f)
+        rb = fw_f[int(np.argmin([np.inf if np.isnan(f) else f for f in fw_f]))]
+        run.write(pkg.MGFWA_BUF_BEST_F, np.array([rb], np.float32))
+        gv = None
+        for gen in range(1, g_max + 1):
+            ref = oracle.generation(p, prob, seed, gen, fw_x, fw_a, fw_f, run_best=rb, g_rem=max(0, g_max - gen),
+                                    gv_prev=gv)
+            for ph, buf, key in ((pkg.MGFWA_PHASE_EXPLODE, None, None), (pkg.MGFWA_PHASE_EVAL_E, pkg.MGFWA_BUF_FIT_E,
+                                                                      "fit_e"),
+                                 (pkg.MGFWA_PHASE_RANK, None, None), (pkg.MGFWA_PHASE_GUIDE, None, None),
+                                 (pkg.MGFWA_PHASE_EVAL_G, pkg.MGFWA_BUF_FIT_G, "fit_g")):
+                run.phase(ph)
+                if buf is not None:
+                    run.write(buf, ref[key])
+            assert np.array_equal(run.read(pkg.MGFWA_BUF_GUIDES), ref["guides"]), gen
+            run.phase(pkg.MGFWA_PHASE_SELECT)
+            assert np.array_equal(run.read(pkg.MGFWA_BUF_LOSER), ref["loser"]), gen
+            assert np.array_equal(run.read(pkg.MGFWA_BUF_FW_X), ref["fw_x"]), gen
+            assert np.array_equal(run.read(pkg.MGFWA_BUF_FW_AMP), ref["fw_amp"]), gen
+            assert np.array_equal(run.read(pkg.MGFWA_BUF_FW_F), ref["fw_f"]), gen
+            losers += int(ref["loser"].sum())
+            fw_x, fw_a, fw_f, rb, gv = ref["fw_x"], ref["fw_amp"], ref["fw_f"], ref["run_best"], ref["gv"]
+    assert losers > 0, "the case should make some fireworks lose"
+
+
 def test_lagged_fitness_of_both_spark_sets_in_one_launch(pkg):
     """From generation 2 on, the explosion and guiding sparks' fitness comes from one launch and still
     equals the oracle's objective on the GPU's own sparks (FP32)."""

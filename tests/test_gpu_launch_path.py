@@ -48,6 +48,8 @@ def _specs(pkg):
                         {"lagged_guiding": 1}),
         "lagged_fp32": (W.scaled(small, eval_budget=W.budget_for_generations(5, 40, 4, 8)), 31, pkg.MGFWA_FP32,
                         {"lagged_guiding": 1}),
+        "lagged_two_runs_loser_out": (W.scaled(big, eval_budget=W.budget_for_generations(3, 20, 4, 6)), 32,
+                                      pkg.MGFWA_BF16, {"lagged_guiding": 1, "n_runs": 2, "loser_out": 1}),
     }
 
 
@@ -57,7 +59,7 @@ def _make(pkg, w, seed, prec, kw):
 
 
 @pytest.mark.parametrize("case", ["fp32", "bf16", "bf16_full", "fp8", "three_layer", "sphere", "two_runs", "refine",
-                                  "loser_out", "lagged_bf16", "lagged_fp32"])
+                                  "loser_out", "lagged_bf16", "lagged_fp32", "lagged_two_runs_loser_out"])
 def test_graph_replay_equals_kernel_by_kernel(pkg, case):
     spec = _specs(pkg)[case]
     states = []
