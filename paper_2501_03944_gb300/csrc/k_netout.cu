@@ -16,6 +16,7 @@ namespace mgfwa {
 namespace {
 
 constexpr int kBK = 16;      // k-slab depth
+constexpr int kStages = 3;   // slabs in flight per group (cp.async ring)
 constexpr int kTN = 32;      // output tile columns per block
 constexpr int kGroups = 4;   // fan-in chunks, one per 64-thread group
 constexpr int kPadW = kTN + 4;
@@ -25,7 +26,7 @@ template <int TR>
 struct NetTile {
   static constexpr int kTM = 8 * TR;
   static constexpr int kPadA = kTM + 4;
-  static constexpr int kGroupFloats = 2 * kBK * (kPadA + kPadW);  // two slab buffers of A and W per group
+  static constexpr int kGroupFloats = kStages * kBK * (kPadA + kPadW);  // the ring of A and W slabs per group
   static constexpr size_t kSmem = sizeof(float) * kGroups * kGroupFloats;
   static_assert(kTM * kPadW <= kGroupFloats, "partial tiles must fit in the slab space");
 };
@@ -36,6 +37,16 @@ __device__ __forceinline__ float act32(int a, float v) {
   return fmaxf(v, 0.0f);
 }
 
+// 4-byte asynchronous global -> shared copy; src_bytes = 0 writes a zero
+// without reading (the source address must still be a valid one).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, uint32_t src_bytes) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // The fan-in chunk of group g: [g c, min((g + 1) c, k)) with c = 16 ceil(k / 64).
 __host__ __device__ __forceinline__ int chunk_len(int k) { return kBK * ((k + kBK * kGroups - 1) / (kBK * kGroups)); }
 
@@ -43,9 +54,9 @@ __host__ __device__ __forceinline__ int chunk_len(int k) { return kBK * ((k + kB
 // for r < rows, j < n; A row stride lda, out row stride ldo.  One 256-thread
 // block per (8 TR) x 32 output tile.  Group g (threads 64 g ..) multiplies
 // the tile over its fan-in chunk, TR x 4 outputs per thread:
-// k-slabs of A and W go through registers into the group's two shared
-// buffers (k-major, so a thread's rows and columns are contiguous), the next
-// slab's global loads in flight while the current one is multiplied, one
+// k-slabs of A and W are copied asynchronously (4-byte cp.async, transposed
+// to k-major so a thread's rows and columns are contiguous) into the group's
+// ring of kStages slabs, two slabs in flight while one is multiplied, one
 // group barrier per slab.  The four partial tiles then meet in shared memory
 // and every thread adds them in group order for 8 outputs, adds the bias and
 // applies the activation.  A quarter of the fan-in per group cuts each
@@ -62,7 +73,7 @@ __global__ void __launch_bounds__(256, TR == 4 ? 4 : 2) k_net_layer(const float*
   constexpr int kTM = NetTile<TR>::kTM, kPadA = NetTile<TR>::kPadA, kGroupFloats = NetTile<TR>::kGroupFloats;
   griddep_wait();
   griddep_launch_dependents();
-  // slabs [group][buffer]{A [kBK][kPadA], W [kBK][kPadW]}; afterwards the partial tiles [group][kTM][kPadW]
+  // slabs [group][stage]{A [kBK][kPadA], W [kBK][kPadW]}; afterwards the partial tiles [group][kTM][kPadW]
   extern __shared__ __align__(16) float sm[];
   const int g = threadIdx.x >> 6, t = threadIdx.x & 63;
   const int tx = t & 7, ty = t >> 3;
@@ -71,9 +82,9 @@ __global__ void __launch_bounds__(256, TR == 4 ? 4 : 2) k_net_layer(const float*
   const int kbeg = g * c, kend = min(kbeg + c, k);
   const int slabs = kend > kbeg ? (kend - kbeg + kBK - 1) / kBK : 0;
   float* const base = sm + g * kGroupFloats;
-  auto As = [&](int buf) { return base + buf * kBK * (kPadA + kPadW); };
-  auto Ws = [&](int buf) { return base + buf * kBK * (kPadA + kPadW) + kBK * kPadA; };
-  constexpr int LA = kTM * kBK / 64, LW = kTN * kBK / 64;  // slab elements each thread stages
+  auto As = [&](int stage) { return base + stage * kBK * (kPadA + kPadW); };
+  auto Ws = [&](int stage) { return base + stage * kBK * (kPadA + kPadW) + kBK * kPadA; };
+  constexpr int LA = kTM * kBK / 64, LW = kTN * kBK / 64;  // slab elements each thread copies
   // element q of a thread is (row rq + 4 q, column kq) of the slab: 16
   // neighbouring threads read 16 consecutive floats of one row
   const int kq = t % kBK, rq = t / kBK;
@@ -85,21 +96,21 @@ __global__ void __launch_bounds__(256, TR == 4 ? 4 : 2) k_net_layer(const float*
   for (int q = 0; q < LA; ++q) va |= (r0 + rq + 4 * q < rows ? 1u : 0u) << q;
 #pragma unroll
   for (int q = 0; q < LW; ++q) vw |= (j0 + rq + 4 * q < n ? 1u : 0u) << q;
-  float ra[LA], rw[LW];
-  auto fetch = [&](int k0) {
+  auto fetch = [&](int slab, int stage) {
+    const int k0 = kbeg + slab * kBK;
     const bool kin = k0 + kq < kend;
+    float* a = As(stage) + kq * kPadA + rq;
+    float* w = Ws(stage) + kq * kPadW + rq;
 #pragma unroll
-    for (int q = 0; q < LA; ++q) ra[q] = (kin && (va >> q & 1u)) ? pa[q * sa + k0] : 0.0f;
+    for (int q = 0; q < LA; ++q) {
+      const bool in = kin && (va >> q & 1u);
+      cp_async4(a + 4 * q, in ? pa + q * sa + k0 : A, in ? 4u : 0u);
+    }
 #pragma unroll
-    for (int q = 0; q < LW; ++q) rw[q] = (kin && (vw >> q & 1u)) ? pw[q * sw + k0] : 0.0f;
-  };
-  auto stash = [&](int buf) {
-    float* a = As(buf) + kq * kPadA + rq;
-    float* w = Ws(buf) + kq * kPadW + rq;
-#pragma unroll
-    for (int q = 0; q < LA; ++q) a[4 * q] = ra[q];
-#pragma unroll
-    for (int q = 0; q < LW; ++q) w[4 * q] = rw[q];
+    for (int q = 0; q < LW; ++q) {
+      const bool in = kin && (vw >> q & 1u);
+      cp_async4(w + 4 * q, in ? pw + q * sw + k0 : W, in ? 4u : 0u);
+    }
   };
   auto group_sync = [&]() { asm volatile("bar.sync %0, 64;" ::"r"(g + 1) : "memory"); };
   float acc[TR][4];
@@ -107,14 +118,15 @@ __global__ void __launch_bounds__(256, TR == 4 ? 4 : 2) k_net_layer(const float*
   for (int i = 0; i < TR; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
-  if (slabs > 0) {
-    fetch(kbeg);
-    stash(0);
-    group_sync();
+#pragma unroll
+  for (int i = 0; i < kStages - 1; ++i) {
+    if (i < slabs) fetch(i, i);
+    cp_async_commit();
   }
   for (int s = 0; s < slabs; ++s) {
-    const int cur = s & 1;
-    if (s + 1 < slabs) fetch(kbeg + (s + 1) * kBK);
+    const int cur = s % kStages;
+    cp_async_wait<kStages - 2>();  // this thread's copies of slab s have landed
+    group_sync();                  // everyone's have; everyone is done with slab s - 1
     const float* a = As(cur);
     const float* w = Ws(cur);
 #pragma unroll
@@ -132,11 +144,12 @@ __global__ void __launch_bounds__(256, TR == 4 ? 4 : 2) k_net_layer(const float*
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ai[i], wj[j], acc[i][j]);
     }
-    // the other buffer was last read in slab s - 1, which every thread of the
-    // group finished before the barrier that ended it
-    if (s + 1 < slabs) stash(cur ^ 1);
-    group_sync();
+    // the ring slot of slab s + kStages - 1 last held slab s - 1, which every
+    // thread of the group finished before the barrier above
+    if (s + kStages - 1 < slabs) fetch(s + kStages - 1, (s + kStages - 1) % kStages);
+    cp_async_commit();
   }
+  cp_async_wait<0>();
   __syncthreads();  // every group done with its slabs: the space holds the partial tiles now
   float* part = sm + g * (kTM * kPadW);
 #pragma unroll
@@ -193,7 +206,9 @@ __global__ void __launch_bounds__(256) k_net_f64(NetOut net, const float* __rest
 int launch_net_output(const NetOut& net, const float* rows, int64_t ld, int32_t count, float* fit, float* scratch,
                       int64_t scratch_ld, cudaStream_t s) {
   if (count <= 0) return 0;
-  if (ensure_smem_limit<k_net_layer<8>>(NetTile<8>::kSmem) != cudaSuccess) return -1;
+  if (ensure_smem_limit<k_net_layer<8>>(NetTile<8>::kSmem) != cudaSuccess ||
+      ensure_smem_limit<k_net_layer<4>>(NetTile<4>::kSmem) != cudaSuccess)
+    return -1;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
                                                  cudaSuccess)
