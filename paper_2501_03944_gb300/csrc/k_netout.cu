@@ -58,8 +58,8 @@ __host__ __device__ __forceinline__ int chunk_len(int k) { return kBK * ((k + kB
 // to k-major so a thread's rows and columns are contiguous) into the group's
 // ring of kStages slabs, two slabs in flight while one is multiplied, one
 // group barrier per slab.  The four partial tiles then meet in shared memory
-// and every thread adds them in group order for 8 outputs, adds the bias and
-// applies the activation.  A quarter of the fan-in per group cuts each
+// and every thread adds them in group order for TR of the tile's outputs,
+// adds the bias and applies the activation.  A quarter of the fan-in per group cuts each
 // block's serial slab chain to a quarter, which is what bounds the small-row
 // launches (the guiding sparks).  TR = 8 takes three 16-byte shared loads per
 // 32 FMAs (for launches that fill the SMs), TR = 4 two per 16 with twice the
