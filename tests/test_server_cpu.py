@@ -56,6 +56,16 @@ def test_testbed_footprint_and_submit(pkg):
         assert info.state == pkg.MGFWA_REQ_QUEUED and info.footprint == fp
 
 
+def test_lagged_guiding_footprint(pkg):
+    """Lagged multi-guiding adds exactly its recorded vectors, [mu m][Dp] FP32 (256-byte aligned)."""
+    w = W.MLP_8_16_3
+    cfg, obj = pkg.workload_request(w, seed=1)
+    lag, lobj = pkg.workload_request(w, seed=1, lagged_guiding=1)
+    dp = (w.dim + 63) // 64 * 64
+    gv = w.n_fireworks * w.guiding_per_firework * dp * 4
+    assert pkg.mgfwa_footprint(lag, lobj) - pkg.mgfwa_footprint(cfg, obj) == (gv + 255) // 256 * 256
+
+
 def test_submit_rejects_requests_larger_than_the_limit(pkg):
     cfg, obj = pkg.workload_request(W.MLP_8_16_3, seed=1)
     fp = pkg.mgfwa_footprint(cfg, obj)
