@@ -178,8 +178,11 @@ MGFWA_API mgfwa_status mgfwa_best_run(mgfwa_t* h, int32_t run, float* x_out, dou
 
 /* Evaluate `count` host vectors (each D floats, row-major) with the
  * handle's objective in the given precision; f_out gets count FP32 values.
- * Uses the handle's device workspace (count <= the sparks of one
- * generation of all runs) and synchronises.  Only between generations. */
+ * The precision selects the MLP objective's path (BF16 / FP8 need the
+ * handle's own tensor-core precision); the sphere and the testbed network
+ * are always FP32.  Uses the handle's device workspace (count <= the sparks
+ * of one generation of all runs) and synchronises.  Only between
+ * generations. */
 MGFWA_API mgfwa_status mgfwa_evaluate(mgfwa_t* h, const float* xs, int64_t count, int32_t precision,
                             float* f_out);
 
