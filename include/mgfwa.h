@@ -127,7 +127,7 @@ typedef struct {
                             <= 192, C in [2, 32]; the tensor-core shapes are listed at mgfwa_precision.
                             Testbed network: d (= dim), hidden widths, 1; every width in [1, 4096] */
   const int32_t* acts;   /* n_layers - 1 hidden activations (MGFWA_ACT_*; GELU for testbed networks only) */
-  int64_t n_samples;     /* N >= 1 (MLP) */
+  int64_t n_samples;     /* 1 <= N <= 65535 * 128 (MLP) */
   const float* X;        /* [N][d_in] row-major FP32 (MLP) */
   const int32_t* y;      /* [N] labels in [0, C) (MLP) */
   /* testbed network: its fixed parameters in nn.Linear order (W_1[h][d]
@@ -236,13 +236,20 @@ MGFWA_API const char* mgfwa_last_error(const mgfwa_t* h);
  *  - fitness_dev [count] FP32 receives the results (device pointer).
  *  - The work is enqueued on cuda_stream (a cudaStream_t, NULL = legacy
  *    default stream); the call does not synchronise.
- *  - Scratch is a fixed array inside the library's device image (1 MiB, held
- *    by every GPU that loads the library until the process exits):
- *    ceil(n_samples / 128) * count must be <= 262,144, else MGFWA_EINVAL.
- *    The first call on each device looks up that array's device address
- *    (cudaGetSymbolAddress), so make that first call before any stream
- *    capture.  Calls share the array: calls that overlap on the GPU (other
- *    streams, other threads) race and give wrong results; serialise them.
+ *  - 1 <= n_samples <= 65535 * 128.
+ *  - Scratch is a fixed array inside the library's device image (1 MiB,
+ *    held by every GPU that has loaded the library's device code, until the
+ *    process exits): ceil(n_samples / 128) * count must be <= 262,144, else
+ *    MGFWA_EINVAL.  The first call on each device looks up that array's
+ *    device address (cudaGetSymbolAddress).  Under CUDA's default lazy
+ *    module loading that first call (or any earlier use of the library on
+ *    that device) is also what loads the device code there, which takes
+ *    device memory for the code and this array; make the first call during
+ *    set-up, before any stream capture and before the caller's memory is
+ *    budgeted.  The address is cached per device ordinal for the device's
+ *    primary context (the CUDA runtime's default context).  Calls share the
+ *    array: calls that overlap on the GPU (other streams, other threads)
+ *    race and give wrong results; serialise them.
  *  - Returns EINVAL on bad arguments (reason in mgfwa_last_error(NULL)),
  *    ECUDA if a launch fails. */
 MGFWA_API mgfwa_status mgfwa_evaluate_fp32_noalloc(int32_t n_layers, const int32_t* widths, const int32_t* acts,

@@ -1,0 +1,627 @@
+// Tensor-core fitness on CTA pairs (GPU-MGFWA, Algorithm 1: "parallel
+// evaluate all the fitness of the sparks") for two-layer networks with
+// h1 in {64, 128}, written for sm_103a: tcgen05 MMAs over a pair of CTAs
+// (cta_group::2) with TMEM accumulators and TMA loads.
+//
+// A tile is 256 samples x S whole sparks, S = floor(256 / (h1 + NL)) (three
+// for the 784-64-10 network), NL = 16 or 32 logit columns per spark.  Layer
+// 1 is one dense product of the shared batch X against the sparks' stacked
+// first-layer weights: M = 256 (128 samples in each CTA of the pair), N =
+// S * h1 (all the tile's hidden units), BF16 or E4M3 operands, FP32
+// accumulation.  Each CTA loads its own 128 rows of X and its own half of
+// the tile's W1 block, so every SM stages and reads half the B operand a
+// one-CTA tile of the same shape would; the accumulator of each CTA holds
+// its 128 samples x all N columns.
+//
+// The epilogue adds b1 (after the E4M3 scale), applies the activation and
+// writes the result back into TMEM as packed BF16 pairs, in the first h1/2
+// columns of each spark's h1.  Layer 2 is then one BF16 MMA chain per
+// spark (M = 256, N = NL, K = h1) with A read from TMEM and B = the spark's
+// W2, which the samplers store as BF16 beside the first-layer operand (each
+// CTA holds half of the logit rows).  The logits land in columns of their
+// own after the tile's accumulator (S * (h1 + NL) <= 256), so layer 1 of
+// tile t+2 in the same TMEM half waits only for layer 2 of tile t to have
+// read its activations, never for the epilogue.  The epilogue reads the
+// logits, adds b2 and reduces the per-sample cross-entropy into one partial
+// sum per (128-sample tile, spark): the same partial layout as the one-CTA
+// kernel.  TMEM (512 columns) holds two halves of 256 columns, one per tile
+// in flight; the MMA thread issues layer 2 of a tile as soon as both
+// epilogues have written its activations, between K blocks of the next tile.
+//
+// Warp roles (both CTAs unless stated):
+//   warp 0  TMA producer: per tile, the biases (bulk copies, completing on
+//           this CTA's barrier) and this CTA's half of the tile's W2 rows;
+//           then per K step this CTA's X tile and W1 half into a ring of
+//           stages.  A K step is two 128-byte K atoms (one tiled load per
+//           operand through a view of K as atoms x 128 bytes): a stage takes
+//           about the same time to arrive whatever its size, so fewer, larger
+//           stages carry more bytes per unit time.  The atom that d_in ends
+//           in, when partial, is a step of its own through the plain view,
+//           whose fill past d_in is zero.  The operand loads of both CTAs complete on the even
+//           CTA's barriers (the CTA-pair form of the tiled load), whose
+//           producer expects both halves' bytes, so the MMA thread waits on
+//           one barrier per stage.
+//   warp 1  TMEM allocation for the pair (both CTAs); in the even CTA, the
+//           single-thread MMA issuer.
+//   warps 2..  epilogue, one warp per spark of the tile and TMEM lane
+//           quadrant (at least two per quadrant).
+// Every wait is bounded.  A CTA whose wait gives up raises its own and its
+// peer's abort flag and a bit in the status word; every role leaves its
+// loop, the even CTA's producer waits (bounded) for the stages it armed, the
+// MMA thread for its MMAs, and an aborting CTA lets its last copies land (a
+// bounded pause: the odd CTA cannot observe the even CTA's barriers) before
+// the pair meets at a cluster barrier and frees TMEM.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <string>
+
+#include "fitness_tc.cuh"
+#include "tc_ptx.cuh"
+
+namespace mgfwa {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kPM = 128;     // samples per CTA (a pair covers 256)
+constexpr int kRowB = 128;   // bytes of K per stage row: one 128-byte swizzle row
+constexpr int kMmaKB = 32;   // bytes of K per layer-1 MMA (16 BF16 or 32 E4M3)
+constexpr int kMaxStg = 8;
+constexpr int kTBufs = 3;    // tail buffers: the producer runs ahead of layer 2
+constexpr int kCols = 512;   // two halves of 256 columns
+
+// Tile shape: S = 256 / h1 sparks fill a TMEM half of 256 columns with
+// their layer-1 accumulators (N = S * h1 = 256).  Each spark's logits then
+// go into the second half of its own columns, freed once the activations
+// are packed as BF16 pairs into the first half; so the next layer 1 into the
+// same TMEM half waits for both epilogues to have read the logits.
+__host__ __device__ constexpr int pair_sparks(int h1) { return 256 / h1; }
+// Epilogue warps: one per spark and TMEM lane quadrant, at least two per quadrant.
+__host__ __device__ constexpr int pair_groups(int h1) { return pair_sparks(h1) < 2 ? 2 : pair_sparks(h1); }
+__host__ __device__ constexpr int pair_threads(int h1) { return 64 + 128 * pair_groups(h1); }
+
+struct PairSmem {
+  uint64_t full[kMaxStg];      // even CTA: both CTAs' loads of the stage landed
+  uint64_t empty[kMaxStg];     // the stage's MMAs completed
+  uint64_t tmem_full[2];       // layer 1 of the half's tile is complete
+  uint64_t a2_full[2];         // even CTA: both CTAs wrote the half's activations
+  uint64_t l2_full[2];         // layer 2 of the half's tile is complete (its logits)
+  uint64_t tmem_empty[2];      // even CTA: both CTAs read the half's logits (the half is free)
+  uint64_t bias_full[kTBufs];  // this CTA's biases of the buffer's tile landed
+  uint64_t w2_full[kTBufs];    // even CTA: both CTAs' W2 halves of the buffer's tile landed
+  uint64_t tail_empty[kTBufs]; // layer 2 read the W2 halves, this CTA's epilogue the biases
+  uint64_t mma_done;
+  uint32_t tmem_base;
+  volatile int abort_flag;
+};
+
+struct PairArgs {
+  int32_t count;        // sparks in this launch
+  int32_t first_spark;  // first spark row of the launch (operand tensor maps)
+  int32_t m_pairs;      // 256-sample tiles
+  int32_t m_tiles;      // 128-sample tiles (rows of `partial`)
+  int32_t n_tiles;
+  int32_t n_full;       // K atoms entirely inside d_in
+  int32_t n_steps;      // K steps per tile: ceil(n_full / 2), plus one for a partial last atom
+  int32_t k_last;       // layer-1 MMAs in the partial last atom (0 if d_in ends on an atom)
+  int32_t stages;
+  int32_t C;            // classes (<= NL)
+  int32_t act;
+  int32_t c_pad;        // C rounded up to 4 (floats of b2 copied)
+  float scale;          // layer-1 accumulator multiplier (1 for BF16; 1 / (inv_x inv_w) for E4M3)
+  int64_t N;
+  int64_t ld;           // FP32 row stride of the sparks
+  int64_t b1_off, b2_off;
+  const float* rows;    // FP32 spark rows of this launch (biases)
+  const int32_t* y;
+  float* partial;       // [m_tiles][count]
+  uint32_t* status;
+};
+
+__device__ __forceinline__ float act_f(int a, float v) { return a == kActTanh ? tanhf(v) : fmaxf(v, 0.0f); }
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// shared::cluster address of this CTA's object `p` in CTA `rank` of the pair.
+__device__ __forceinline__ uint32_t map_to(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Two FP32 values as a BF16 pair (round to nearest even), the lower K index
+// in the low half.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+template <int H1, int NL, bool F8>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
+    k_fitness_pair(const __grid_constant__ CUtensorMap tmap_x3, const __grid_constant__ CUtensorMap tmap_x,
+                   const __grid_constant__ CUtensorMap tmap_w3, const __grid_constant__ CUtensorMap tmap_w,
+                   const __grid_constant__ CUtensorMap tmap_w2, PairArgs a) {
+  griddep_wait();
+  griddep_launch_dependents();
+  constexpr int S = pair_sparks(H1);             // sparks per tile
+  constexpr int kNT = S * H1;                    // layer-1 accumulator columns per tile (256)
+  constexpr int kBK = F8 ? 128 : 64;             // K elements per atom (one 128-byte row)
+  constexpr int kGroups = pair_groups(H1);       // epilogue warps per TMEM lane quadrant
+  constexpr int kEpi = 4 * kGroups;
+  constexpr int kHalfNL = NL / 2;                // W2 rows (logits) each CTA holds
+  constexpr int kW2Atoms = H1 / 64;              // 128-byte K atoms of a BF16 W2 row
+  constexpr uint32_t kW2AtomBytes = kHalfNL * 128;
+  constexpr uint32_t kW2Bytes = kW2Atoms * kW2AtomBytes;  // one spark's W2 half
+  constexpr int kTailF = H1 + 32;                // b1 and b2 (C <= 32) of one spark
+  constexpr uint32_t kAtomA = kPM * kRowB;       // one K atom of this CTA's 128 samples
+  constexpr uint32_t kAtomB = (kNT / 2) * kRowB; // one K atom of this CTA's half of the tile's W1 rows
+  constexpr uint32_t kStageA = 2 * kAtomA;       // a stage: two atoms of each operand
+  constexpr uint32_t kStageB = 2 * kAtomB;
+  static_assert(kHalfNL % 8 == 0, "each W2 half is whole 8-row swizzle groups");
+  static_assert(S >= 1 && kNT == 256 && NL <= H1 / 2, "a spark's logits fit beside its packed activations");
+  static_assert((kNT / 2) % 8 == 0 && kNT % 16 == 0, "a W1 half is whole 8-row groups; N is a multiple of 16");
+
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* stage_a = base;
+  uint8_t* stage_b = base + (size_t)a.stages * kStageA;
+  uint8_t* w2s = stage_b + (size_t)a.stages * kStageB;                              // [kTBufs][S][kW2Bytes]
+  float* tails = reinterpret_cast<float*>(w2s + (size_t)kTBufs * S * kW2Bytes);      // [kTBufs][S][kTailF]
+  float* red = tails + (size_t)kTBufs * S * kTailF;                                  // [S][4]
+  PairSmem* sm = reinterpret_cast<PairSmem*>((reinterpret_cast<uintptr_t>(red + 4 * S) + 15) & ~uintptr_t(15));
+
+  // TMEM columns of spark s within a half: its accumulator / packed activations, its logits
+  auto col_h = [](int sp) { return (uint32_t)(sp * H1); };
+  auto col_lg = [](int sp) { return (uint32_t)(sp * H1 + H1 / 2); };
+  const uint32_t rank = cluster_rank();
+  const bool lead = rank == 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pair = (int)(blockIdx.x >> 1), npairs = (int)(gridDim.x >> 1);
+  const int tiles = a.m_pairs * a.n_tiles;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < a.stages; ++s) {
+      mbar_init(&sm->full[s], 1);
+      mbar_init(&sm->empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sm->tmem_full[b], 1);
+      mbar_init(&sm->a2_full[b], 2 * kEpi);
+      mbar_init(&sm->l2_full[b], 1);
+      mbar_init(&sm->tmem_empty[b], 2 * kEpi);
+    }
+    for (int b = 0; b < kTBufs; ++b) {
+      mbar_init(&sm->bias_full[b], 1);
+      mbar_init(&sm->w2_full[b], 1);
+      mbar_init(&sm->tail_empty[b], 1 + kEpi);
+    }
+    mbar_init(&sm->mma_done, 1);
+    sm->abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm->tmem_base)),
+                 "n"(kCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  cluster_sync();  // both CTAs' barriers initialised and TMEM allocated before any cross-CTA access
+  tc_fence_after();
+  const uint32_t tmem_base = sm->tmem_base;
+
+  // A wait that gives up also stops the peer CTA.
+  const uint32_t peer_abort = map_to((const void*)&sm->abort_flag, rank ^ 1u);
+  auto wait = [&](uint64_t* bar, uint32_t parity, uint32_t code) -> bool {
+    if (mbar_wait(&sm->abort_flag, bar, parity, a.status, code)) return true;
+    asm volatile("st.relaxed.cluster.shared::cluster.u32 [%0], %1;" ::"r"(peer_abort), "r"(1u) : "memory");
+    return false;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer (both CTAs) ----------------
+      uint32_t it = 0;
+      int local = 0;
+      bool ok = true;
+      const uint32_t bias_bytes = (uint32_t)(H1 + a.c_pad) * 4u;
+      for (int t = pair; t < tiles && ok; t += npairs, ++local) {
+        const int mt = t % a.m_pairs, nt = t / a.m_pairs;
+        const int s0 = nt * S;
+        const int s_valid = min(S, a.count - s0);
+        const int tb = local % kTBufs;
+        const uint32_t tuse = (uint32_t)(local / kTBufs);
+        if (!wait(&sm->tail_empty[tb], (tuse & 1u) ^ 1u, 1u)) break;
+        mbar_expect_tx(&sm->bias_full[tb], bias_bytes * (uint32_t)s_valid);
+        for (int s = 0; s < s_valid; ++s) {
+          const float* row = a.rows + (int64_t)(s0 + s) * a.ld;
+          float* tl = tails + ((size_t)tb * S + s) * kTailF;
+          bulk_load(tl, row + a.b1_off, (uint32_t)H1 * 4u, &sm->bias_full[tb]);
+          bulk_load(tl + H1, row + a.b2_off, (uint32_t)a.c_pad * 4u, &sm->bias_full[tb]);
+        }
+        // this CTA's W2 halves; the even CTA's barrier expects both CTAs' bytes
+        if (lead) mbar_expect_tx(&sm->w2_full[tb], 2u * kW2Bytes * (uint32_t)s_valid);
+        const uint32_t w2_bar = map_to(&sm->w2_full[tb], 0u);
+        for (int s = 0; s < s_valid; ++s) {
+          uint8_t* w2 = w2s + ((size_t)tb * S + s) * kW2Bytes;
+#pragma unroll
+          for (int at = 0; at < kW2Atoms; ++at)
+            tma_load_3d_pair(w2 + at * kW2AtomBytes, &tmap_w2, at * 64, (int)rank * kHalfNL, a.first_spark + s0 + s,
+                             w2_bar);
+        }
+        const int row_x = mt * (2 * kPM) + (int)rank * kPM;
+        const int row_w = (a.first_spark + s0) * H1 + (int)rank * (kNT / 2);
+        const int n_pairs = (a.n_full + 1) / 2;
+        for (int kb = 0; kb < a.n_steps; ++kb, ++it) {
+          const int st = (int)(it % (uint32_t)a.stages);
+          const uint32_t ph = (it / (uint32_t)a.stages) & 1u;
+          if (!wait(&sm->empty[st], ph ^ 1u, 1u)) {
+            ok = false;
+            break;
+          }
+          const uint32_t bar = map_to(&sm->full[st], 0u);
+          if (kb < n_pairs) {
+            // atoms 2 kb and 2 kb + 1 (the second one past n_full is zero fill)
+            if (lead) mbar_expect_tx(&sm->full[st], 2u * (kStageA + kStageB));
+            tma_load_3d_pair(stage_a + (size_t)st * kStageA, &tmap_x3, 0, row_x, 2 * kb, bar);
+            tma_load_3d_pair(stage_b + (size_t)st * kStageB, &tmap_w3, 0, row_w, 2 * kb, bar);
+          } else {
+            // the partial last atom, zero past d_in
+            if (lead) mbar_expect_tx(&sm->full[st], 2u * (kAtomA + kAtomB));
+            tma_load_2d_pair(stage_a + (size_t)st * kStageA, &tmap_x, a.n_full * kBK, row_x, bar);
+            tma_load_2d_pair(stage_b + (size_t)st * kStageB, &tmap_w, a.n_full * kBK, row_w, bar);
+          }
+        }
+      }
+      // copies land before the CTA may leave: this CTA's biases, and (even CTA) the stages and W2 it
+      // armed, which also carry the odd CTA's bytes.  Short budgets: only an aborting run waits here.
+      constexpr uint64_t kDrain = 1ull << 24;
+      for (int l = local - kTBufs > 0 ? local - kTBufs : 0; l < local; ++l) {
+        mbar_drain(&sm->bias_full[l % kTBufs], (uint32_t)((l / kTBufs) & 1), a.status, kDrain);
+        if (lead) mbar_drain(&sm->w2_full[l % kTBufs], (uint32_t)((l / kTBufs) & 1), a.status, kDrain);
+      }
+      if (lead && it > 0) {
+        const uint32_t last = it - 1;
+        for (uint32_t j = (last + 1 > (uint32_t)a.stages ? last + 1 - a.stages : 0); j <= last; ++j)
+          mbar_drain(&sm->full[j % (uint32_t)a.stages], (j / (uint32_t)a.stages) & 1u, a.status, kDrain);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && lead) {
+      // ---------------- MMA issuer (even CTA) ----------------
+      const uint32_t idesc1 = instr_desc(2 * kPM, kNT, F8 ? 0u : 1u);
+      const uint32_t idesc2 = instr_desc(2 * kPM, NL, 1u);
+      auto commit_both = [&](uint64_t* bar) {
+        mma2_commit(map_to(bar, 0u));
+        mma2_commit(map_to(bar, 1u));
+      };
+      // layer 2 of the tile with local index j (global index tj) is ready when both
+      // CTAs wrote its activations and both W2 halves landed
+      auto l2_ready = [&](int j) -> bool {
+        const int tbj = j % kTBufs;
+        const uint32_t tu = (uint32_t)(j / kTBufs) & 1u;
+        return mbar_test_wait(&sm->a2_full[j & 1], (uint32_t)(j >> 1) & 1u) && mbar_test_wait(&sm->w2_full[tbj], tu);
+      };
+      auto layer2 = [&](int j, int tj) -> bool {
+        const int bj = j & 1;
+        const int tbj = j % kTBufs;
+        const uint32_t tu = (uint32_t)(j / kTBufs) & 1u;
+        if (!wait(&sm->a2_full[bj], (uint32_t)(j >> 1) & 1u, 2u)) return false;
+        if (!wait(&sm->w2_full[tbj], tu, 2u)) return false;
+        tc_fence_after();
+        const int s_valid = min(S, a.count - (tj / a.m_pairs) * S);
+        const uint32_t half = tmem_base + (uint32_t)(bj * 256);
+        for (int s = 0; s < s_valid; ++s) {
+          const uint32_t w2 = smem_u32(w2s + ((size_t)tbj * S + s) * kW2Bytes);
+#pragma unroll
+          for (int kk = 0; kk < H1 / 16; ++kk) {
+            const uint32_t b_addr = w2 + (uint32_t)((kk * 16) / 64) * kW2AtomBytes + (uint32_t)((kk * 16) % 64) * 2u;
+            mma2_bf16_ta(half + col_lg(s), half + col_h(s) + (uint32_t)(kk * 8), smem_desc(b_addr), idesc2,
+                         kk > 0 ? 1u : 0u);
+          }
+        }
+        commit_both(&sm->l2_full[bj]);
+        commit_both(&sm->tail_empty[tbj]);
+        return true;
+      };
+      uint32_t it = 0;
+      int local = 0;
+      bool ok = true;
+      int pend = -1, pend_t = -1;  // the tile whose layer 2 is not issued yet
+      for (int t = pair; t < tiles && ok; t += npairs, ++local) {
+        const int b = local & 1;
+        const uint32_t use = (uint32_t)(local >> 1);
+        if (!wait(&sm->tmem_empty[b], (use & 1u) ^ 1u, 2u)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(b * 256);
+        const int n_pairs = (a.n_full + 1) / 2;
+        for (int kb = 0; kb < a.n_steps; ++kb, ++it) {
+          if (pend >= 0 && l2_ready(pend)) {
+            if (!layer2(pend, pend_t)) {
+              ok = false;
+              break;
+            }
+            pend = -1;
+          }
+          const int st = (int)(it % (uint32_t)a.stages);
+          const uint32_t ph = (it / (uint32_t)a.stages) & 1u;
+          if (!wait(&sm->full[st], ph, 2u)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_addr = smem_u32(stage_a + (size_t)st * kStageA);
+          const uint32_t b_addr = smem_u32(stage_b + (size_t)st * kStageB);
+          // MMAs of this step: four per full atom (two atoms, or one if n_full is odd and this is its
+          // last pair), k_last for the partial atom
+          const int atoms = kb < n_pairs ? (2 * kb + 1 < a.n_full ? 2 : 1) : 1;
+#pragma unroll
+          for (int at = 0; at < 2; ++at) {
+            if (at >= atoms) break;
+            const int nk = kb < n_pairs ? kRowB / kMmaKB : a.k_last;
+            const uint32_t aa = a_addr + (uint32_t)at * kAtomA, bb = b_addr + (uint32_t)at * kAtomB;
+#pragma unroll
+            for (int k = 0; k < kRowB / kMmaKB; ++k) {
+              if (k >= nk) break;
+              const uint32_t acc = (kb > 0 || at > 0 || k > 0) ? 1u : 0u;
+              if (F8)
+                mma2_e4m3(d_tmem, smem_desc(aa + k * kMmaKB), smem_desc(bb + k * kMmaKB), idesc1, acc);
+              else
+                mma2_bf16(d_tmem, smem_desc(aa + k * kMmaKB), smem_desc(bb + k * kMmaKB), idesc1, acc);
+            }
+          }
+          commit_both(&sm->empty[st]);
+        }
+        if (!ok) break;
+        commit_both(&sm->tmem_full[b]);
+        if (pend >= 0 && !layer2(pend, pend_t)) {
+          ok = false;
+          break;
+        }
+        pend = local;
+        pend_t = t;
+      }
+      if (ok && pend >= 0) layer2(pend, pend_t);
+      // every issued MMA completes before TMEM is released: one more commit, bounded wait
+      mma2_commit(map_to(&sm->mma_done, 0u));
+      mbar_drain(&sm->mma_done, 0u, a.status);
+    }
+  } else {
+    // ---------------- epilogue (both CTAs) ----------------
+    const int ew = warp - 2;            // 0 .. kEpi-1
+    const int quad = warp & 3;          // TMEM lane quadrant this warp may access
+    const int grp = ew >> 2;            // the tile's spark this warp takes (none when grp >= S)
+    const int et = threadIdx.x - 64;    // 0 .. 32 kEpi - 1
+    const int row_in_tile = quad * 32 + lane;
+    const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16);
+    const float sc = a.scale;
+    int local = 0;
+    for (int t = pair; t < tiles; t += npairs, ++local) {
+      const int mt = t % a.m_pairs, nt = t / a.m_pairs;
+      const int b = local & 1;
+      const uint32_t use = (uint32_t)(local >> 1);
+      const int s0 = nt * S;
+      const int s_valid = min(S, a.count - s0);
+      const int64_t n = (int64_t)mt * (2 * kPM) + (int64_t)rank * kPM + row_in_tile;
+      const bool valid_row = n < a.N;
+      const int label = valid_row ? a.y[n] : 0;  // issued before the waits
+      const int tb = local % kTBufs;
+      bool ok = wait(&sm->tmem_full[b], use & 1u, 4u);
+      ok = ok && wait(&sm->bias_full[tb], (uint32_t)(local / kTBufs) & 1u, 4u);
+      if (epi_bar_any<kEpi>(!ok || sm->abort_flag)) break;
+      tc_fence_after();
+      const float* tail = tails + (size_t)tb * S * kTailF;
+      const uint32_t hbase = lane_base + (uint32_t)(b * 256);
+      // act(h * scale + b1) as packed BF16 into the spark's first h1/2 columns: layer 2's A operand.
+      // Chunk j0 writes columns [j0/2, j0/2 + 8), whose accumulators were read by this or an earlier chunk.
+      if (grp < s_valid) {
+        const int s = grp;
+        const float* b1 = tail + (size_t)s * kTailF;
+#pragma unroll 1
+        for (int j0 = 0; j0 < H1; j0 += 16) {
+          float h[16];
+          tmem_ld16(hbase + col_h(s) + (uint32_t)j0, h);
+          tmem_wait_ld();
+          uint32_t pk[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float2 bb = *reinterpret_cast<const float2*>(b1 + j0 + 2 * q);
+            pk[q] = pack_bf16x2(act_f(a.act, fmaf(h[2 * q], sc, bb.x)), act_f(a.act, fmaf(h[2 * q + 1], sc, bb.y)));
+          }
+          tmem_st8u(hbase + col_h(s) + (uint32_t)(j0 / 2), pk);
+        }
+      }
+      tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(map_to(&sm->a2_full[b], 0u));
+      ok = wait(&sm->l2_full[b], use & 1u, 4u);
+      if (epi_bar_any<kEpi>(!ok || sm->abort_flag)) break;
+      tc_fence_after();
+      // read this warp's logits, then give their columns back before the loss math
+      float z[NL];
+      if (grp < s_valid) {
+#pragma unroll
+        for (int q = 0; q < NL; q += 16) tmem_ld16(hbase + col_lg(grp) + (uint32_t)q, z + q);
+      }
+      tmem_wait_ld();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(map_to(&sm->tmem_empty[b], 0u));
+      if (grp < s_valid) {
+        const int s = grp;
+        const float* b2 = tail + (size_t)s * kTailF + H1;
+        float ce = 0.0f;
+        if (valid_row) {
+          const int C = a.C;
+          float zmax = -INFINITY;
+          float zy = 0.0f;
+#pragma unroll
+          for (int c = 0; c < NL; ++c) {
+            if (c < C) {
+              z[c] += b2[c];
+              zmax = fmaxf(zmax, z[c]);
+              if (c == label) zy = z[c];
+            }
+          }
+          float se = 0.0f;
+#pragma unroll
+          for (int c = 0; c < NL; ++c)
+            if (c < C) se += expf(z[c] - zmax);
+          ce = (zmax + logf(se)) - zy;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) ce += __shfl_xor_sync(0xffffffffu, ce, off);
+        if (lane == 0) red[s * 4 + quad] = ce;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm->tail_empty[tb]);
+      epi_bar<kEpi>();
+      const int m128 = mt * 2 + (int)rank;
+      if (et < s_valid && m128 < a.m_tiles) {
+        const int s = et;
+        const float v = ((red[s * 4 + 0] + red[s * 4 + 1]) + red[s * 4 + 2]) + red[s * 4 + 3];
+        a.partial[(int64_t)m128 * a.count + s0 + s] = v;
+      }
+    }
+  }
+
+  if (sm->abort_flag) {
+    // aborting: the odd CTA's last copies complete on the even CTA's barriers, which it cannot watch,
+    // so let any copy in flight land (a bounded pause, far above a copy's latency) before leaving
+    const long long t0 = clock64();
+    while ((uint64_t)(clock64() - t0) < (1ull << 24)) {
+    }
+  }
+  tc_fence_before();
+  cluster_sync();  // the pair's MMAs are done and no cross-CTA access is pending
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "n"(kCols) : "memory");
+  }
+}
+
+template <int H1, int NL, bool F8>
+cudaError_t launch_pair(const TcPlan& plan, const PairArgs& args, cudaStream_t s, bool prepare_only, int* pairs_out) {
+  cudaError_t e = ensure_smem_limit<k_fitness_pair<H1, NL, F8>>(plan.smem_bytes);
+  if (e != cudaSuccess) return e;
+  if (prepare_only) {
+    // pairs that fit at once (one CTA per SM): the persistent grid
+    if (pairs_out) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(2 * (plan.num_sms / 2));
+      cfg.blockDim = dim3(pair_threads(H1));
+      cfg.dynamicSmemBytes = plan.smem_bytes;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, k_fitness_pair<H1, NL, F8>, &cfg) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        n = plan.num_sms / 2;
+      }
+      *pairs_out = n;
+    }
+    return cudaSuccess;
+  }
+  const int tiles = args.m_pairs * args.n_tiles;
+  const int pairs = tiles < plan.pairs ? tiles : plan.pairs;
+  return launch_pdl(k_fitness_pair<H1, NL, F8>, dim3(2 * pairs), dim3(pair_threads(H1)), plan.smem_bytes, s,
+                    plan.tmap_x3, plan.tmap_x, plan.tmap_wk, plan.tmap_w, plan.tmap_w2b, args);
+}
+
+cudaError_t dispatch_pair(const TcPlan& plan, int h1, int nl, const PairArgs& a, cudaStream_t s, bool prep,
+                          int* pairs_out) {
+  const int key = h1 * 4 + (nl == 32 ? 2 : 0) + (plan.f8 ? 1 : 0);
+  switch (key) {
+    case 64 * 4 + 0: return launch_pair<64, 16, false>(plan, a, s, prep, pairs_out);
+    case 64 * 4 + 2: return launch_pair<64, 32, false>(plan, a, s, prep, pairs_out);
+    case 64 * 4 + 1: return launch_pair<64, 16, true>(plan, a, s, prep, pairs_out);
+    case 64 * 4 + 3: return launch_pair<64, 32, true>(plan, a, s, prep, pairs_out);
+    case 128 * 4 + 0: return launch_pair<128, 16, false>(plan, a, s, prep, pairs_out);
+    case 128 * 4 + 2: return launch_pair<128, 32, false>(plan, a, s, prep, pairs_out);
+    case 128 * 4 + 1: return launch_pair<128, 16, true>(plan, a, s, prep, pairs_out);
+    case 128 * 4 + 3: return launch_pair<128, 32, true>(plan, a, s, prep, pairs_out);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+bool tc_pair_supported(const int32_t* widths, int n_layers) {
+  if (n_layers != 2 || widths[0] % 8 != 0) return false;
+  return (widths[1] == 64 || widths[1] == 128) && widths[2] >= 2 && widths[2] <= 32;
+}
+
+int tc_pair_logit_rows(int C) { return C <= 16 ? 16 : 32; }
+
+int tc_pair_sparks(int h1, int C) {
+  (void)C;
+  return pair_sparks(h1);
+}
+
+size_t tc_pair_fixed_smem(int h1, int C) {
+  const int nl = tc_pair_logit_rows(C), S = pair_sparks(h1);
+  const size_t w2 = (size_t)kTBufs * S * (h1 / 64) * (nl / 2) * 128;
+  const size_t tails = sizeof(float) * ((size_t)kTBufs * S * (h1 + 32) + 4 * (size_t)S);
+  return 1024 + w2 + tails + 16 + sizeof(PairSmem) + 64;
+}
+
+size_t tc_pair_stage_bytes(int h1, int C) {
+  (void)h1;
+  (void)C;
+  return 2 * ((size_t)kPM * kRowB + (size_t)(256 / 2) * kRowB);
+}
+
+int tc_pair_max_stages() { return kMaxStg; }
+
+int launch_fitness_pair(const TcPlan& plan, const Mlp& mlp, int64_t first, const float* rows, int64_t ld,
+                        int32_t count, float scale, float* partial, uint32_t* status, cudaStream_t s) {
+  PairArgs a = {};
+  const int h1 = mlp.widths[1];
+  const int S = tc_pair_sparks(h1, mlp.widths[2]);
+  a.count = count;
+  a.first_spark = (int32_t)first;
+  a.m_pairs = (int32_t)((mlp.N + 2 * kPM - 1) / (2 * kPM));
+  a.m_tiles = (int32_t)((mlp.N + kPM - 1) / kPM);
+  a.n_tiles = (count + S - 1) / S;
+  const int bk = plan.f8 ? 128 : 64;
+  {
+    const int ke = plan.f8 ? 32 : 16;                 // K elements per MMA
+    a.n_full = mlp.widths[0] / bk;
+    const int rem = mlp.widths[0] - a.n_full * bk;   // K elements of the partial last atom
+    a.k_last = (rem + ke - 1) / ke;
+    a.n_steps = (a.n_full + 1) / 2 + (rem > 0 ? 1 : 0);
+  }
+  a.stages = plan.stages;
+  a.C = mlp.widths[2];
+  a.act = mlp.acts[0];
+  a.c_pad = (a.C + 3) / 4 * 4;
+  a.scale = scale;
+  a.N = mlp.N;
+  a.ld = ld;
+  a.b1_off = mlp.b_off[0];
+  a.b2_off = mlp.b_off[1];
+  a.rows = rows;
+  a.y = mlp.y;
+  a.partial = partial;
+  a.status = status;
+  return dispatch_pair(plan, h1, tc_pair_logit_rows(a.C), a, s, false, nullptr) == cudaSuccess ? 1 : -1;
+}
+
+cudaError_t tc_pair_prepare(TcPlan& plan, const Mlp& mlp) {
+  PairArgs a = {};
+  int pairs = 0;
+  cudaError_t e = dispatch_pair(plan, mlp.widths[1], tc_pair_logit_rows(mlp.widths[2]), a, nullptr, true, &pairs);
+  if (e == cudaSuccess) plan.pairs = pairs;
+  return e;
+}
+
+}  // namespace mgfwa

@@ -43,10 +43,13 @@
 #include <string>
 
 #include "fitness_tc.cuh"
+#include "tc_ptx.cuh"
 
 namespace mgfwa {
 
 namespace {
+
+using namespace tc;
 
 constexpr int kBM = 128;         // samples per tile
 constexpr int kRowBytes = 128;   // bytes of K per stage row: one 128-byte swizzle row
@@ -61,7 +64,6 @@ __host__ __device__ constexpr int threads_for(bool f8) { return 64 + 32 * epi_wa
 constexpr int kMaxStages = 6;
 constexpr int kTmemCols = 512;   // two halves of 256 columns
 constexpr int kTailBufs = 3;     // tail buffers (biases, W2[, W3]): the producer runs a tile ahead of layer 2
-constexpr uint64_t kWaitBudget = 1ull << 32;  // clock64 ticks before a wait gives up (~2 s)
 
 struct Smem {
   uint64_t full[kMaxStages];
@@ -80,194 +82,6 @@ struct Smem {
   volatile int abort_flag;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait; false if this CTA is aborting (timeout here or elsewhere).
-__device__ __forceinline__ bool mbar_wait(Smem* sm, uint64_t* bar, uint32_t parity, uint32_t* status,
-                                          uint32_t code) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (sm->abort_flag) return false;
-    if ((uint64_t)(clock64() - t0) > kWaitBudget) {
-      sm->abort_flag = 1;
-      atomicOr(status, code);
-      return false;
-    }
-  }
-  return true;
-}
-
-// Bounded wait used while draining (ignores the abort flag).
-__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity, uint32_t* status) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if ((uint64_t)(clock64() - t0) > kWaitBudget) {
-      atomicOr(status, 16u);
-      return;
-    }
-  }
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
-          "r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// Untiled bulk copy global -> shared (16-byte aligned, size a multiple of 16).
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Shared-memory matrix descriptor: K-major operand in 128-byte swizzled
-// rows, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr & 0x3FFFF) >> 4);        // start address
-  d |= (uint64_t)1 << 16;                         // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset: 8 rows x 128 B
-  d |= (uint64_t)1 << 46;                         // descriptor version for tcgen05
-  d |= (uint64_t)2 << 61;                         // 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptors: D FP32; A and B K-major; kind::f16 with BF16
-// inputs (format 1), kind::tf32 with TF32 inputs (format 2), kind::f8f6f4
-// with E4M3 inputs (format 0).
-__host__ __device__ constexpr uint32_t instr_desc(int m, int n, uint32_t ab_format) {
-  return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((uint32_t)(n >> 3) << 17) |
-         ((uint32_t)(m >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accum)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accum)
-      : "memory");
-}
-
-// D (TMEM) (+)= A (TMEM) x B (shared memory), TF32 inputs.
-__device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
-                                            uint32_t accum) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "r"(a_tmem), "l"(b), "r"(idesc), "r"(accum)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-// 32 lanes x 8 / 16 consecutive 32-bit columns.
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
-  uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float* v) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
-               "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
-               "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
-               "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-template <int kEpi>
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpi) : "memory"); }
-
-// Named barrier over the epilogue warps that also ORs a flag across them, so
-// that every epilogue thread takes the same branch afterwards.
-template <int kEpi>
-__device__ __forceinline__ bool epi_bar_any(bool flag) {
-  uint32_t out;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\t"
-      "setp.ne.u32 p, %1, 0;\n\t"
-      "bar.red.or.pred q, 1, %2, p;\n\t"
-      "selp.u32 %0, 1, 0, q;\n\t}"
-      : "=r"(out)
-      : "r"((uint32_t)flag), "n"(32 * kEpi)
-      : "memory");
-  return out != 0;
-}
-
 __device__ __forceinline__ float act_f(int a, float v) { return a == kActTanh ? tanhf(v) : fmaxf(v, 0.0f); }
 
 struct TcArgs {
@@ -275,6 +89,7 @@ struct TcArgs {
   int32_t first_spark;  // first spark row of the launch (operand and W2 tensor maps)
   int32_t m_tiles, n_tiles;
   int32_t k_blocks;
+  int32_t k_last;       // layer-1 MMAs in the last K block (the rest of it is past d_in: zero fill)
   int32_t stages;
   int32_t S;            // sparks per tile
   int32_t C;            // classes (<= N2)
@@ -383,7 +198,7 @@ __global__ void __launch_bounds__(threads_for(F8), 1)
           // biases, W2 [and W3] of the tile's sparks, for the epilogue and layers 2 [and 3]
           const int tb = local % kTB;
           const uint32_t tuse = (uint32_t)(local / kTB);
-          if (!mbar_wait(sm, &sm->tail_empty[tb], (tuse & 1u) ^ 1u, a.status, 1u)) break;
+          if (!mbar_wait(&sm->abort_flag, &sm->tail_empty[tb], (tuse & 1u) ^ 1u, a.status, 1u)) break;
           const int s0 = nt * S;
           const int s_valid = min(S, a.count - s0);
           mbar_expect_tx(&sm->tail_full[tb], tail_bytes * (uint32_t)s_valid);
@@ -406,7 +221,7 @@ __global__ void __launch_bounds__(threads_for(F8), 1)
         for (int kb = 0; kb < a.k_blocks; ++kb, ++it) {
           const int s = (int)(it % (uint32_t)a.stages);
           const uint32_t ph = (it / (uint32_t)a.stages) & 1u;
-          if (!mbar_wait(sm, &sm->empty[s], ph ^ 1u, a.status, 1u)) {
+          if (!mbar_wait(&sm->abort_flag, &sm->empty[s], ph ^ 1u, a.status, 1u)) {
             ok = false;
             break;
           }
@@ -439,9 +254,9 @@ __global__ void __launch_bounds__(threads_for(F8), 1)
         const int bj = j & 1;
         const uint32_t uj = (uint32_t)(j >> 1);
         const int tj_buf = j % kTB;
-        if (!mbar_wait(sm, &sm->a2_full[bj], uj & 1u, a.status, 2u)) return false;
-        if (!mbar_wait(sm, &sm->tail_full[tj_buf], (uint32_t)(j / kTB) & 1u, a.status, 2u)) return false;
-        if (!mbar_wait(sm, &sm->l2_empty[bj], (uj & 1u) ^ 1u, a.status, 2u)) return false;
+        if (!mbar_wait(&sm->abort_flag, &sm->a2_full[bj], uj & 1u, a.status, 2u)) return false;
+        if (!mbar_wait(&sm->abort_flag, &sm->tail_full[tj_buf], (uint32_t)(j / kTB) & 1u, a.status, 2u)) return false;
+        if (!mbar_wait(&sm->abort_flag, &sm->l2_empty[bj], (uj & 1u) ^ 1u, a.status, 2u)) return false;
         tc_fence_after();
         const int ntj = tj / a.m_tiles;
         const int s_valid = min(S, a.count - ntj * S);
@@ -458,7 +273,7 @@ __global__ void __launch_bounds__(threads_for(F8), 1)
         }
         mma_commit(&sm->l2_full[bj]);
         if (kL3) {
-          if (!mbar_wait(sm, &sm->a3_full[bj], uj & 1u, a.status, 2u)) return false;
+          if (!mbar_wait(&sm->abort_flag, &sm->a3_full[bj], uj & 1u, a.status, 2u)) return false;
           tc_fence_after();
           for (int s = 0; s < s_valid; ++s) {
             const uint32_t w3 = smem_u32(w2s + ((size_t)tj_buf * S + s) * kW2Bytes) + (uint32_t)(kAtoms * kAtomBytes);
@@ -479,21 +294,23 @@ __global__ void __launch_bounds__(threads_for(F8), 1)
       for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++local) {
         const int b = local & 1;
         const uint32_t use = (uint32_t)(local >> 1);
-        if (!mbar_wait(sm, &sm->tmem_empty[b], (use & 1u) ^ 1u, a.status, 2u)) break;
+        if (!mbar_wait(&sm->abort_flag, &sm->tmem_empty[b], (use & 1u) ^ 1u, a.status, 2u)) break;
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(b * 256);
         for (int kb = 0; kb < a.k_blocks; ++kb, ++it) {
           const int s = (int)(it % (uint32_t)a.stages);
           const uint32_t ph = (it / (uint32_t)a.stages) & 1u;
-          if (!mbar_wait(sm, &sm->full[s], ph, a.status, 2u)) {
+          if (!mbar_wait(&sm->abort_flag, &sm->full[s], ph, a.status, 2u)) {
             ok = false;
             break;
           }
           tc_fence_after();
           const uint32_t a_addr = smem_u32(stage_a + (size_t)s * a_bytes);
           const uint32_t b_addr = smem_u32(stage_b + (size_t)s * b_bytes);
+          const int nk = kb + 1 == a.k_blocks ? a.k_last : kRowBytes / kUmmaKBytes;
 #pragma unroll
           for (int k = 0; k < kRowBytes / kUmmaKBytes; ++k) {
+            if (k >= nk) break;
             if (F8)
               mma_e4m3(d_tmem, smem_desc(a_addr + k * kUmmaKBytes), smem_desc(b_addr + k * kUmmaKBytes), idesc1,
                        (kb > 0 || k > 0) ? 1u : 0u);
@@ -535,8 +352,8 @@ __global__ void __launch_bounds__(threads_for(F8), 1)
       const bool valid_row = n < a.N;
       const int label = valid_row ? a.y[n] : 0;   // issued before the waits
       const int tb = local % kTB;
-      bool ok = mbar_wait(sm, &sm->tmem_full[b], use & 1u, a.status, 4u);
-      ok = ok && mbar_wait(sm, &sm->tail_full[tb], (uint32_t)(local / kTB) & 1u, a.status, 4u);
+      bool ok = mbar_wait(&sm->abort_flag, &sm->tmem_full[b], use & 1u, a.status, 4u);
+      ok = ok && mbar_wait(&sm->abort_flag, &sm->tail_full[tb], (uint32_t)(local / kTB) & 1u, a.status, 4u);
       if (epi_bar_any<kEpiWarps>(!ok || sm->abort_flag)) break;
       tc_fence_after();
       const float* tail = tails + (size_t)tb * S * kTailFloats;
@@ -565,7 +382,7 @@ __global__ void __launch_bounds__(threads_for(F8), 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&sm->a2_full[b]);
-      ok = mbar_wait(sm, &sm->l2_full[b], use & 1u, a.status, 4u);
+      ok = mbar_wait(&sm->abort_flag, &sm->l2_full[b], use & 1u, a.status, 4u);
       if (epi_bar_any<kEpiWarps>(!ok || sm->abort_flag)) break;
       tc_fence_after();
       if (kL3) {
@@ -587,7 +404,7 @@ __global__ void __launch_bounds__(threads_for(F8), 1)
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm->a3_full[b]);
-        ok = mbar_wait(sm, &sm->l3_full[b], use & 1u, a.status, 4u);
+        ok = mbar_wait(&sm->abort_flag, &sm->l3_full[b], use & 1u, a.status, 4u);
         if (epi_bar_any<kEpiWarps>(!ok || sm->abort_flag)) break;
         tc_fence_after();
       }
@@ -774,6 +591,67 @@ mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const OpDesc& op, const float
   const int C = mlp.widths[mlp.n_layers];
   const int n2 = n2_of(C);
   plan.num_sms = prop.multiProcessorCount;
+  const CUtensorMapDataType dt = f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  if (op.w2 && tc_pair_supported(mlp.widths, mlp.n_layers)) {
+    // the CTA-pair kernel: 256 samples x S sparks per tile, each CTA loading half of either operand
+    plan.pair = true;
+    plan.sparks_per_tile = tc_pair_sparks(h1, C);
+    plan.n_tile = plan.sparks_per_tile * h1;
+    const size_t fixed = tc_pair_fixed_smem(h1, C), stage = tc_pair_stage_bytes(h1, C);
+    const size_t limit = (size_t)prop.sharedMemPerBlockOptin;
+    int stages = tc_pair_max_stages();
+    while (stages > 2 && fixed + stages * stage > limit) --stages;
+    if (fixed + stages * stage > limit) {
+      g_err = "shared memory too small for the tensor-core pair tiles";
+      return MGFWA_EINVAL;
+    }
+    plan.stages = stages;
+    plan.smem_bytes = fixed + stages * stage;
+    plan.pairs = plan.num_sms / 2;
+    const int nl = tc_pair_logit_rows(C);
+    if (op.w2_rows != nl || op.w2_h1 != h1) {
+      g_err = "pair kernel: the BF16 W2 copy has the wrong shape";
+      return MGFWA_EINVAL;
+    }
+    {
+      // X [N][d_in], box (one 128-byte row of K) x 128 samples
+      cuuint64_t dims[2] = {(cuuint64_t)d_in, (cuuint64_t)mlp.N};
+      cuuint64_t strides[1] = {(cuuint64_t)d_in * esize};
+      cuuint32_t box[2] = {(cuuint32_t)bk, kBM};
+      if (!encode(&plan.tmap_x, dt, 2, mlp.Xop, dims, strides, box)) return MGFWA_ECUDA;
+    }
+    {
+      // first-layer operand [max_rows*h1][d_in], box (one 128-byte row of K) x half a tile's rows
+      cuuint64_t dims[2] = {(cuuint64_t)d_in, (cuuint64_t)(max_rows * h1)};
+      cuuint64_t strides[1] = {(cuuint64_t)d_in * esize};
+      cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)(plan.n_tile / 2)};
+      if (!encode(&plan.tmap_w, dt, 2, op.base, dims, strides, box)) return MGFWA_ECUDA;
+    }
+    {
+      // the same two operands viewed as [K atoms entirely inside d_in][rows][one 128-byte atom] (the atom
+      // stride is 128 bytes), so that one load brings two atoms; the partial last atom goes through the
+      // plain views above, whose fill past d_in is zero
+      const int n_full = d_in / bk > 0 ? d_in / bk : 1;
+      cuuint64_t dx[3] = {(cuuint64_t)bk, (cuuint64_t)mlp.N, (cuuint64_t)n_full};
+      cuuint64_t sx[2] = {(cuuint64_t)d_in * esize, (cuuint64_t)kRowBytes};
+      cuuint32_t bx[3] = {(cuuint32_t)bk, kBM, 2};
+      if (!encode(&plan.tmap_x3, dt, 3, mlp.Xop, dx, sx, bx)) return MGFWA_ECUDA;
+      cuuint64_t dw[3] = {(cuuint64_t)bk, (cuuint64_t)(max_rows * h1), (cuuint64_t)n_full};
+      cuuint32_t bw[3] = {(cuuint32_t)bk, (cuuint32_t)(plan.n_tile / 2), 2};
+      if (!encode(&plan.tmap_wk, dt, 3, op.base, dw, sx, bw)) return MGFWA_ECUDA;
+    }
+    {
+      // BF16 W2 [max_rows][nl][h1], box 64 x nl/2 x 1 (one CTA's half of the logit rows, one K atom)
+      cuuint64_t dims[3] = {(cuuint64_t)h1, (cuuint64_t)nl, (cuuint64_t)max_rows};
+      cuuint64_t strides[2] = {(cuuint64_t)h1 * 2, (cuuint64_t)nl * h1 * 2};
+      cuuint32_t box[3] = {64, (cuuint32_t)(nl / 2), 1};
+      if (!encode(&plan.tmap_w2b, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, op.w2, dims, strides, box)) return MGFWA_ECUDA;
+    }
+    plan.tmap_w2 = plan.tmap_w2b;  // unused by the pair kernel
+    plan.tmap_w3 = plan.tmap_w2b;
+    plan.ready = true;
+    return MGFWA_OK;
+  }
   plan.sparks_per_tile = sparks_per_tile(h1, h2, C);
   plan.n_tile = plan.sparks_per_tile * h1;
   const size_t a_bytes = (size_t)kBM * kRowBytes, b_bytes = (size_t)plan.n_tile * kRowBytes;
@@ -792,7 +670,6 @@ mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const OpDesc& op, const float
   }
   plan.stages = stages;
   plan.smem_bytes = fixed + stages * (a_bytes + b_bytes);
-  const CUtensorMapDataType dt = f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   {
     // X [N][d_in], box (one 128-byte row of K) x 128
     cuuint64_t dims[2] = {(cuuint64_t)d_in, (cuuint64_t)mlp.N};
@@ -837,6 +714,7 @@ void tc_release(TcPlan& plan) { plan.ready = false; }
 int launch_fitness_tc(const TcPlan& plan, const Mlp& mlp, int64_t first, const float* rows, int64_t ld,
                       int32_t count, float scale, float* partial, uint32_t* status, cudaStream_t s) {
   if (!plan.ready || count <= 0) return count <= 0 ? 0 : -1;
+  if (plan.pair) return launch_fitness_pair(plan, mlp, first, rows, ld, count, scale, partial, status, s);
   TcArgs a;
   a.count = count;
   a.first_spark = (int32_t)first;
@@ -845,6 +723,11 @@ int launch_fitness_tc(const TcPlan& plan, const Mlp& mlp, int64_t first, const f
   a.n_tiles = (count + a.S - 1) / a.S;
   const int bk = plan.f8 ? 128 : 64;
   a.k_blocks = (mlp.widths[0] + bk - 1) / bk;
+  {
+    const int ke = plan.f8 ? 32 : 16;                       // K elements per MMA
+    const int rem = mlp.widths[0] - (a.k_blocks - 1) * bk;  // K elements of the last block
+    a.k_last = (rem + ke - 1) / ke;
+  }
   a.scale = scale;
   a.stages = plan.stages;
   const bool l3 = mlp.n_layers == 3;
@@ -864,8 +747,9 @@ int launch_fitness_tc(const TcPlan& plan, const Mlp& mlp, int64_t first, const f
   return dispatch(plan, mlp, a, s, false) == cudaSuccess ? 1 : -1;
 }
 
-cudaError_t tc_prepare(const TcPlan& plan, const Mlp& mlp) {
+cudaError_t tc_prepare(TcPlan& plan, const Mlp& mlp) {
   if (!plan.ready) return cudaErrorInvalidValue;
+  if (plan.pair) return tc_pair_prepare(plan, mlp);
   TcArgs a = {};
   a.C = mlp.widths[mlp.n_layers];
   return dispatch(plan, mlp, a, nullptr, true);

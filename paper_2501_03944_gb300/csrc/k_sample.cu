@@ -62,6 +62,18 @@ __device__ __forceinline__ void store_op4(const OpDesc& op, int64_t row, int64_t
     store_bf16x4(reinterpret_cast<__nv_bfloat16*>(base) + row * op.w1_elems + d0, a, b, c, d);
 }
 
+// Coordinates [d0, d0 + 4) of row `row` into the BF16 copy of W2 when they
+// lie in W2 (h1 is a multiple of 4 and W2 starts on a multiple of 4, so the
+// four never straddle two rows of W2).
+__device__ __forceinline__ void store_w2_4(const OpDesc& op, int64_t row, int64_t d0, float a, float b, float c,
+                                           float d) {
+  const int64_t e = d0 - op.w2_off;
+  if (e < 0 || e >= (int64_t)op.w2_classes * op.w2_h1) return;
+  const int64_t cls = e / op.w2_h1;
+  const int64_t j = e - cls * op.w2_h1;
+  store_bf16x4(static_cast<__nv_bfloat16*>(op.w2) + row * op.w2_row_elems() + cls * op.w2_h1 + j, a, b, c, d);
+}
+
 // grid (coordinate blocks, B * mu): global firework z = b * mu + i.
 __global__ void __launch_bounds__(kThreads) k_init(Problem p, float* __restrict__ fw_x,
                                                    float* __restrict__ fw_amp) {
@@ -121,6 +133,7 @@ __device__ __forceinline__ void explode4(const Problem& p, uint32_t gen, uint32_
   }
   *reinterpret_cast<float4*>(srow + d0) = make_float4(v[0], v[1], v[2], v[3]);
   if (op.kind != kOpNone && d0 < (uint32_t)op.w1_elems) store_op4(op, row, d0, v[0], v[1], v[2], v[3]);
+  if (op.w2) store_w2_4(op, row, d0, v[0], v[1], v[2], v[3]);
 }
 
 // grid (coordinate blocks, lambda, B * mu): one block covers 2 * kThreads
@@ -252,16 +265,28 @@ __global__ void __launch_bounds__(kThreads) k_guide(Problem p, const uint32_t* _
     if (d0 + l >= p.D) v[l] = 0.0f;
   *reinterpret_cast<float4*>(guides + (int64_t)gq * p.Dp + d0) = make_float4(v[0], v[1], v[2], v[3]);
   if (op.kind != kOpNone && d0 < op.w1_elems) store_op4(op, gq, d0, v[0], v[1], v[2], v[3]);
+  if (op.w2) store_w2_4(op, gq, d0, v[0], v[1], v[2], v[3]);
 }
 
+// The operand copies of `count` FP32 rows: the first-layer block and, with
+// op.w2, the BF16 W2.  grid (coordinate blocks up to op_span(op), rows).
 __global__ void k_to_operand(const float* __restrict__ rows, int64_t ld, const OpDesc op) {
   griddep_wait();
   griddep_launch_dependents();
   const int row = blockIdx.y;
   const int64_t d0 = ((int64_t)blockIdx.x * kThreads + threadIdx.x) * 4;
-  if (d0 >= op.w1_elems) return;
+  const bool in_w1 = d0 < op.w1_elems;
+  const bool in_w2 = op.w2 && d0 >= op.w2_off && d0 < op.w2_off + (int64_t)op.w2_classes * op.w2_h1;
+  if (!in_w1 && !in_w2) return;
   const float4 v = *reinterpret_cast<const float4*>(rows + (int64_t)row * ld + d0);
-  store_op4(op, row, d0, v.x, v.y, v.z, v.w);
+  if (in_w1) store_op4(op, row, d0, v.x, v.y, v.z, v.w);
+  if (in_w2) store_w2_4(op, row, d0, v.x, v.y, v.z, v.w);
+}
+
+// Coordinates k_to_operand covers: the first-layer block, and W2 when copied.
+inline int64_t op_span(const OpDesc& op) {
+  const int64_t w2_end = op.w2 ? op.w2_off + (int64_t)op.w2_classes * op.w2_h1 : 0;
+  return op.w1_elems > w2_end ? op.w1_elems : w2_end;
 }
 
 __global__ void k_f32_to_op(const float* __restrict__ src, int64_t n, int32_t kind, float inv, void* dst) {
@@ -313,7 +338,7 @@ int launch_guide(const Problem& p, const uint32_t* gens_done, const float* fw_x,
 
 int launch_to_operand(const float* rows, int64_t ld, int32_t count, const OpDesc& op, cudaStream_t s) {
   if (count <= 0 || op.kind == kOpNone) return 0;
-  dim3 grid(blocks_for(op.w1_elems / 4), count);
+  dim3 grid(blocks_for(op_span(op) / 4), count);
   k_to_operand<<<grid, kThreads, 0, s>>>(rows, ld, op);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }

@@ -50,6 +50,8 @@ struct mgfwa_handle {
   float* fw_f = nullptr;
   float* sparks = nullptr;  // [P][Dp]: explosion rows, then guiding rows
   void* op = nullptr;            // [P][w1_elems] first-layer operand (BF16 or E4M3)
+  void* w2op = nullptr;          // [P][w2_rows][h1] BF16 W2 for the CTA-pair fitness kernel, or null
+  int32_t w2_rows = 0;           // 16 or 32 (rows C.. are zero)
   int32_t op_kind = kOpNone;
   float inv_x = 1.0f, inv_w = 1.0f;  // E4M3: stored = E4M3(value * inv)
   float op_scale = 1.0f;             // layer-1 accumulator multiplier: 1 / (inv_x inv_w)
@@ -260,6 +262,13 @@ OpDesc op_rows(const mgfwa_t* h, int64_t first) {
   d.kind = h->op ? h->op_kind : kOpNone;
   d.inv_scale = h->inv_w;
   d.w1_elems = h->mlp.w1_elems;
+  if (h->op && h->w2op) {
+    d.w2 = h->w2op;
+    d.w2_off = h->mlp.w_off[1];
+    d.w2_h1 = h->mlp.widths[1];
+    d.w2_classes = h->mlp.widths[2];
+    d.w2_rows = h->w2_rows;
+  }
   return d.from(first);
 }
 
@@ -548,7 +557,8 @@ mgfwa_status validate(const mgfwa_config* c, const mgfwa_objective* o) {
   if (o->kind != MGFWA_OBJ_MLP_CE) return fail(nullptr, MGFWA_EINVAL, "unknown objective kind %d", o->kind);
   if (o->n_layers < 2 || o->n_layers > 3 || !o->widths || !o->acts || !o->X || !o->y)
     return fail(nullptr, MGFWA_EINVAL, "MLP objective needs 2 or 3 layers, widths, acts, X and y");
-  if (o->n_samples < 1 || o->n_samples > (1 << 24)) return fail(nullptr, MGFWA_EINVAL, "n_samples out of range");
+  if (o->n_samples < 1 || o->n_samples > mgfwa::kMaxSamples)
+    return fail(nullptr, MGFWA_EINVAL, "n_samples must be in [1, %lld]", (long long)mgfwa::kMaxSamples);
   int64_t params = 0;
   for (int l = 0; l < o->n_layers; ++l) {
     if (o->widths[l] < 1 || o->widths[l + 1] < 1) return fail(nullptr, MGFWA_EINVAL, "layer widths must be >= 1");
@@ -789,6 +799,9 @@ size_t carve_all(mgfwa_t* h, char* base) {
   h->fw_f = carve<float>(cur, F);
   h->sparks = carve<float>(cur, h->PA * p.Dp);
   h->op = want_op ? carve<uint8_t>(cur, h->PA * mlp.w1_elems * esize) : nullptr;
+  // the CTA-pair fitness kernel reads W2 as BF16 from its own copy
+  h->w2_rows = want_op && tc_pair_supported(mlp.widths, mlp.n_layers) ? tc_pair_logit_rows(mlp.widths[2]) : 0;
+  h->w2op = h->w2_rows ? carve<uint16_t>(cur, h->PA * h->w2_rows * mlp.widths[1]) : nullptr;
   h->fit = carve<float>(cur, h->PA);
   h->partial = carve<float>(cur, (size_t)h->mtiles * h->PA);
   h->top = carve<int32_t>(cur, F * p.m * p.k);
@@ -936,6 +949,9 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
       cudaMemcpyAsync(const_cast<float*>(h->net.params), obj->params, sizeof(float) * h->net_count,
                       cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
     return bail(cuda_fail(h, "copy network parameters"));
+  if (h->w2op &&
+      cudaMemsetAsync(h->w2op, 0, sizeof(uint16_t) * h->PA * h->w2_rows * h->mlp.widths[1], h->stream) != cudaSuccess)
+    return bail(cuda_fail(h, "clear the W2 copy"));
   if (want_op) {
     st = tc_plan(h->tc, h->mlp, op_rows(h, 0), h->sparks, p.Dp, h->PA);
     if (st != MGFWA_OK) {

@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 namespace mgfwa {
 
 // Philox stream purposes: the fourth counter word.
@@ -64,17 +66,27 @@ struct NetOut {
 // The first-layer GEMM operand the samplers write beside the FP32 rows:
 // row r holds the spark's first w1_elems coordinates ([h1][d_in] row-major)
 // as BF16, or as E4M3 of (coordinate * inv_scale) with saturation.
+// With w2 set (the CTA-pair kernel's two-layer networks) the samplers also
+// store each spark's second-layer weights W2 [C][h1] as BF16, row r at
+// w2 + r * w2_rows * h1 ([w2_rows][h1], rows C..w2_rows-1 kept zero).
 enum { kOpNone = 0, kOpBf16 = 1, kOpFp8 = 2 };
 struct OpDesc {
   void* base = nullptr;  // row 0
   int32_t kind = kOpNone;
   float inv_scale = 1.0f;
   int64_t w1_elems = 0;
+  void* w2 = nullptr;     // BF16 W2 of row 0, or null
+  int64_t w2_off = 0;     // coordinate of W2[0][0] in a spark row
+  int32_t w2_h1 = 0;      // h1 (elements per W2 row)
+  int32_t w2_classes = 0; // C (W2 rows the samplers write)
+  int32_t w2_rows = 0;    // W2 rows per spark in the buffer (16 or 32)
   __host__ __device__ int64_t row_bytes() const { return w1_elems * (kind == kOpFp8 ? 1 : 2); }
+  __host__ __device__ int64_t w2_row_elems() const { return (int64_t)w2_rows * w2_h1; }
   // the descriptor of rows [first, ...)
   OpDesc from(int64_t first) const {
     OpDesc d = *this;
     if (base) d.base = static_cast<uint8_t*>(base) + first * row_bytes();
+    if (w2) d.w2 = static_cast<uint16_t*>(w2) + first * w2_row_elems();
     return d;
   }
 };
@@ -112,19 +124,26 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 // Raise kernel K's dynamic shared-memory limit on the current device once.
 // The attribute belongs to one kernel on one device, so the cache is per
 // kernel (one template instance per kernel, not per kernel type) and per
-// device.
+// device.  Host threads may launch concurrently, so the cached limit is
+// updated under a lock.
 template <auto K>
 inline cudaError_t ensure_smem_limit(size_t bytes) {
   constexpr int kMaxDevices = 64;
   static size_t configured[kMaxDevices] = {};
+  static std::mutex mu;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
   if (dev >= 0 && dev < kMaxDevices && bytes <= configured[dev]) return cudaSuccess;
   e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess && dev >= 0 && dev < kMaxDevices) configured[dev] = bytes;
   return e;
 }
+
+// Largest batch the FP32 fitness kernels accept: their grid carries the
+// 128-sample tiles in its y dimension, which is limited to 65535 blocks.
+constexpr int64_t kMaxSamples = 65535LL * 128;
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products

@@ -9,11 +9,15 @@
 // per-sample-tile partial sums of the cross-entropy) in a fixed array that
 // lives in the library's own device image, so a call allocates nothing.
 //
-// That array is a file-scope __device__ object: every GPU that loads the
-// library holds it (kScratchFloats floats = 1 MiB) until the process exits.
-// Host code cannot use the array's name as a device address (in host code the
-// name is a host-side stand-in); its device address is taken once per device
-// with cudaGetSymbolAddress and cached.
+// That array is a file-scope __device__ object: every GPU on which the
+// library's device code is loaded holds it (kScratchFloats floats = 1 MiB)
+// until the process exits.  With CUDA's default lazy module loading the code
+// is loaded on a device at its first use there (the first launch or symbol
+// lookup), so the first call on a device may take device memory for it; it
+// belongs in the caller's set-up.  Host code cannot use the array's name as a
+// device address (in host code the name is a host-side stand-in); its device
+// address is taken once per device with cudaGetSymbolAddress and cached per
+// device ordinal, for the device's primary context.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -69,7 +73,8 @@ extern "C" MGFWA_API mgfwa_status mgfwa_evaluate_fp32_noalloc(int32_t n_layers, 
   if (n_layers < 2 || n_layers > 3 || !widths || !acts)
     return reject(MGFWA_EINVAL, "noalloc: need 2 or 3 layers with widths and activations");
   if (!X_dev || !y_dev || !rows_dev || !fitness_dev) return reject(MGFWA_EINVAL, "noalloc: null device pointer");
-  if (n_samples < 1 || n_samples > (1 << 24)) return reject(MGFWA_EINVAL, "noalloc: n_samples out of range");
+  if (n_samples < 1 || n_samples > mgfwa::kMaxSamples)
+    return reject(MGFWA_EINVAL, "noalloc: n_samples must be in [1, 65535 * 128]");
   if (count < 1 || count > 65535) return reject(MGFWA_EINVAL, "noalloc: count must be in [1, 65535]");
   int64_t params = 0;
   for (int l = 0; l < n_layers; ++l) {
