@@ -103,44 +103,17 @@ __device__ __forceinline__ float signed_u24(uint32_t r) {
   return __fmaf_rn(__uint2float_rn(r >> 8), 0x1p-23f, -1.0f);
 }
 
-// Coordinates [d0, d0 + 4) of explosion spark `row` (one Philox block);
-// `full` when all four coordinates are < D.
-__device__ __forceinline__ void explode4(const Problem& p, uint32_t gen, uint32_t unit, const PhiloxKeys& rk,
-                                         uint32_t c4, const float4 x4, float amp, float* __restrict__ srow,
-                                         const OpDesc& op, uint32_t row, bool full) {
-  const uint32_t d0 = c4 * 4u;
-  const uint4 r = philox4x32_10(make_uint4(c4, unit, gen, kExplode), rk);
-  float v[4];
-#pragma unroll
-  for (int l = 0; l < 4; ++l) v[l] = __fmaf_rn(amp, signed_u24(lane_of(r, l)), lane_of(x4, l));
-  bool oob[4];
-  bool any = false;
-#pragma unroll
-  for (int l = 0; l < 4; ++l) {
-    oob[l] = (v[l] < p.lb || v[l] > p.ub) && (full || d0 + l < (uint32_t)p.D);
-    any |= oob[l];
-  }
-  if (any) {
-    const uint4 r2 = philox4x32_10(make_uint4(c4, unit, gen, kMap), rk);
-#pragma unroll
-    for (int l = 0; l < 4; ++l)
-      if (oob[l]) v[l] = map_coord(lane_of(x4, l), amp, p.lb, p.ub, u24(lane_of(r2, l)));
-  }
-  if (!full) {
-#pragma unroll
-    for (int l = 0; l < 4; ++l)
-      if (d0 + l >= (uint32_t)p.D) v[l] = 0.0f;
-  }
-  *reinterpret_cast<float4*>(srow + d0) = make_float4(v[0], v[1], v[2], v[3]);
-  if (op.kind != kOpNone && d0 < (uint32_t)op.w1_elems) store_op4(op, row, d0, v[0], v[1], v[2], v[3]);
-  if (op.w2) store_w2_4(op, row, d0, v[0], v[1], v[2], v[3]);
-}
+// grid (coordinate blocks, lambda, B * mu): one block covers kExplodeBlocks *
+// kThreads Philox blocks (4 coordinates each) of one spark row; each thread
+// takes kExplodeBlocks of them, kThreads apart, so a warp's stores stay
+// contiguous.  Global firework z = b * mu + i, spark row z * lam + j, Philox
+// unit i * lam + j of run b's stream.  The thread's firework coordinates are
+// loaded first; per Philox block the explosion draw, then -- when any lane
+// of the warp has a coordinate outside [lb, ub] -- the mapping stream's block
+// for the whole warp (a warp-uniform branch), taken only where a lane is out
+// of bounds.
+constexpr int kExplodeBlocks = 4;
 
-// grid (coordinate blocks, lambda, B * mu): one block covers 2 * kThreads
-// Philox blocks (8 * kThreads coordinates) of one spark row; each thread does
-// two, kThreads blocks apart, so a warp's stores stay contiguous.  Global
-// firework z = b * mu + i, spark row z * lam + j, Philox unit i * lam + j of
-// run b's stream.
 __global__ void __launch_bounds__(kThreads) k_explode(Problem p, const uint32_t* __restrict__ gens_done,
                                                       const float* __restrict__ fw_x,
                                                       const float* __restrict__ fw_amp,
@@ -154,18 +127,53 @@ __global__ void __launch_bounds__(kThreads) k_explode(Problem p, const uint32_t*
   const uint32_t unit = i * (uint32_t)p.lam + blockIdx.y;
   uint32_t k0, k1;
   run_key(p, (int)b, k0, k1);
-  const PhiloxKeys rk = philox_keys(k0, k1);  // shared by the thread's (up to four) Philox blocks
+  const PhiloxKeys rk = philox_keys(k0, k1);  // shared by the thread's Philox blocks
   const float amp = fw_amp[z];
-  const float* xrow = fw_x + (int64_t)z * p.Dp;
-  float* srow = sparks + (int64_t)row * p.Dp;
+  const float lb = p.lb, ub = p.ub;
+  const float* xrow = fw_x + (size_t)z * (size_t)p.Dp;
+  float* srow = sparks + (size_t)row * (size_t)p.Dp;
   const uint32_t n4 = (uint32_t)(p.Dp / 4);
   const uint32_t full4 = (uint32_t)(p.D / 4);  // blocks whose 4 coordinates are all < D
+  const uint32_t D = (uint32_t)p.D;
+  const uint32_t c0 = blockIdx.x * (uint32_t)(kExplodeBlocks * kThreads) + threadIdx.x;
+  float4 x4[kExplodeBlocks];
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const uint32_t c4 = blockIdx.x * (2 * kThreads) + (uint32_t)h * kThreads + threadIdx.x;
-    if (c4 >= n4) continue;
-    const float4 x4 = *reinterpret_cast<const float4*>(xrow + (size_t)c4 * 4);
-    explode4(p, gen, unit, rk, c4, x4, amp, srow, op, row, c4 < full4);
+  for (int h = 0; h < kExplodeBlocks; ++h) {
+    const uint32_t c4 = c0 + (uint32_t)h * kThreads;
+    x4[h] = c4 < n4 ? *reinterpret_cast<const float4*>(xrow + (size_t)c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int h = 0; h < kExplodeBlocks; ++h) {
+    const uint32_t c4 = c0 + (uint32_t)h * kThreads;
+    const bool live = c4 < n4;
+    const uint32_t d0 = c4 * 4u;
+    const uint4 r = philox4x32_10(make_uint4(c4, unit, gen, kExplode), rk);
+    float v[4];
+    bool oob[4];
+    bool any = false;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      v[l] = __fmaf_rn(amp, signed_u24(lane_of(r, l)), lane_of(x4[h], l));
+      oob[l] = live && (v[l] < lb || v[l] > ub) && (c4 < full4 || d0 + (uint32_t)l < D);
+      any |= oob[l];
+    }
+    if (__any_sync(0xffffffffu, any)) {
+      const uint4 r2 = philox4x32_10(make_uint4(c4, unit, gen, kMap), rk);
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const float m = map_coord(lane_of(x4[h], l), amp, lb, ub, u24(lane_of(r2, l)));
+        v[l] = oob[l] ? m : v[l];
+      }
+    }
+    if (!live) continue;
+    if (c4 >= full4) {
+#pragma unroll
+      for (int l = 0; l < 4; ++l)
+        if (d0 + (uint32_t)l >= D) v[l] = 0.0f;
+    }
+    *reinterpret_cast<float4*>(srow + d0) = make_float4(v[0], v[1], v[2], v[3]);
+    if (op.kind != kOpNone && d0 < (uint32_t)op.w1_elems) store_op4(op, row, d0, v[0], v[1], v[2], v[3]);
+    if (op.w2) store_w2_4(op, row, d0, v[0], v[1], v[2], v[3]);
   }
 }
 
@@ -312,7 +320,7 @@ int launch_init(const Problem& p, float* fw_x, float* fw_amp, cudaStream_t s) {
 
 int launch_explode(const Problem& p, const uint32_t* gens_done, const float* fw_x, const float* fw_amp, float* sparks,
                    const OpDesc& op, cudaStream_t s) {
-  dim3 grid((unsigned)((p.Dp / 4 + 2 * kThreads - 1) / (2 * kThreads)), p.lam, p.B * p.mu);
+  dim3 grid((unsigned)((p.Dp / 4 + kExplodeBlocks * kThreads - 1) / (kExplodeBlocks * kThreads)), p.lam, p.B * p.mu);
   return launch_pdl(k_explode, grid, dim3(kThreads), 0, s, p, gens_done, fw_x, fw_amp, sparks, op) == cudaSuccess
              ? 1
              : -1;
