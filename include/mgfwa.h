@@ -118,6 +118,21 @@ typedef struct {
    * guiding sparks are evaluated in one launch; generation 1 runs the method
    * as written.  Handles with it cannot be checkpointed or grouped. */
   int32_t lagged_guiding;
+  /* Sharding one run's fireworks over several handles (for example one per
+   * GPU): the mu fireworks are split into n_shards contiguous ranges, and
+   * this handle holds range shard_id, fireworks [shard_id mu / n_shards,
+   * (shard_id + 1) mu / n_shards) of the run (integer division).  Every
+   * firework draws from the Philox units of its index in the whole run, so
+   * each shard's fireworks evolve bit for bit as in the unsharded run: the
+   * selection is per firework, and nothing else crosses fireworks once the
+   * loser-out tournament and the refinement (which read the run's best) are
+   * off, as they must be with n_shards > 1.  eval_budget stays the whole
+   * run's budget: a shard runs a generation exactly when the whole run
+   * would.  The run's best is the minimum over the shards' best keys
+   * (mgfwa_shard_key, mgfwa_reduce_best_keys).  n_shards 0 or 1 = one
+   * handle holds the run. */
+  int32_t shard_id;
+  int32_t n_shards;
 } mgfwa_config;
 
 typedef struct {
@@ -256,6 +271,46 @@ MGFWA_API mgfwa_status mgfwa_evaluate_fp32_noalloc(int32_t n_layers, const int32
                                                    int64_t n_samples, const float* X_dev, const int32_t* y_dev,
                                                    const float* rows_dev, int64_t ld, int32_t count,
                                                    float* fitness_dev, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * The run's best over shards (the sharding seam; see mgfwa_config).
+ *
+ * A shard's key is its run's best-so-far FP32 fitness and its shard index.
+ * The run's best is the key with the smallest fitness (NaN ranks last), the
+ * smallest shard on ties: the same first minimum the unsharded run takes
+ * over its fireworks in index order.  Callers that combine keys across
+ * processes (an all-gather, an all-reduce) register that step as a hook;
+ * mgfwa_reduce_best_keys is the host reduction such a hook (or a caller
+ * holding every shard's key) applies.  Algorithm 1's "find the best
+ * individual" over the whole population.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  float f;          /* best-so-far FP32 fitness of the shard's run (NaN ranks last) */
+  int32_t shard;    /* the shard's shard_id */
+  int32_t run;      /* run index within the handle (0 .. n_runs - 1) */
+  int32_t pad;      /* zero */
+} mgfwa_best_key;
+
+/* This handle's key for run `run` (synchronises the handle's stream).
+ * Errors: EINVAL (bad handle or run), ECUDA. */
+MGFWA_API mgfwa_status mgfwa_shard_key(mgfwa_t* h, int32_t run, mgfwa_best_key* key_out);
+
+/* The reduction of `n` >= 1 keys (host memory) into *out: smallest f (NaN
+ * last), then smallest shard, then smallest run.  Pure host code. */
+MGFWA_API mgfwa_status mgfwa_reduce_best_keys(const mgfwa_best_key* keys, int32_t n, mgfwa_best_key* out);
+
+/* Hook that combines this shard's key with the other shards' keys in place
+ * (on every shard the same result); returns 0 on success.  `ctx` is the
+ * caller's. */
+typedef int32_t (*mgfwa_reduce_best_fn)(void* ctx, mgfwa_best_key* key);
+
+/* Register (or, with fn NULL, remove) the handle's hook. */
+MGFWA_API mgfwa_status mgfwa_set_reduce_best(mgfwa_t* h, mgfwa_reduce_best_fn fn, void* ctx);
+
+/* The run's best key over all shards: this shard's key passed through the
+ * hook, or this shard's key when no hook is registered (a handle that holds
+ * the whole run).  Errors: as mgfwa_shard_key, ECUDA if the hook fails. */
+MGFWA_API mgfwa_status mgfwa_global_best_key(mgfwa_t* h, int32_t run, mgfwa_best_key* key_out);
 
 /* ------------------------------------------------------------------------
  * Serving: many optimisation requests on one GPU with continuous batching.

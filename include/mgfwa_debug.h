@@ -86,6 +86,16 @@ MGFWA_API mgfwa_status mgfwa_debug_gradient(mgfwa_t* h, const float* xs, int32_t
 MGFWA_API mgfwa_status mgfwa_debug_fp32_tc(const mgfwa_t* h, int32_t* rescore, int32_t* refine);
 MGFWA_API mgfwa_status mgfwa_debug_profile(mgfwa_t* h, int32_t enable);
 MGFWA_API mgfwa_status mgfwa_debug_kernel_times(mgfwa_t* h, double* ms_out, int64_t* launches_out);
+/* Budget, in SM clock ticks (clock64), of every bounded mbarrier wait in the
+ * handle's tensor-core fitness kernels, for launches made after the call
+ * (0 restores the default of about 2 s; a generation graph captured earlier
+ * keeps the budget it was captured with).  With a budget of a few ticks an
+ * ordinary wait runs out: the kernel raises its abort flag, every role leaves
+ * its loop, drains its own copies and MMAs (fixed budgets), frees TMEM and
+ * returns, and the call that launched it reports MGFWA_ETIMEOUT.  Failure
+ * detection tests use it; nothing faults and no arrival is withheld.
+ * Errors: EINVAL (null handle). */
+MGFWA_API mgfwa_status mgfwa_debug_wait_budget(mgfwa_t* h, uint64_t ticks);
 
 #ifdef __cplusplus
 }

@@ -40,7 +40,8 @@ EXPORTS = ("mgfwa_config_init", "mgfwa_create", "mgfwa_step", "mgfwa_run", "mgfw
            "mgfwa_footprint", "mgfwa_server_create", "mgfwa_server_submit", "mgfwa_server_tick", "mgfwa_server_poll",
            "mgfwa_server_stats_get", "mgfwa_server_now", "mgfwa_server_destroy", "mgfwa_group_create",
            "mgfwa_group_step", "mgfwa_group_destroy", "mgfwa_checkpoint_size", "mgfwa_checkpoint_save",
-           "mgfwa_checkpoint_load")
+           "mgfwa_checkpoint_load", "mgfwa_shard_key", "mgfwa_reduce_best_keys", "mgfwa_set_reduce_best",
+           "mgfwa_global_best_key", "mgfwa_debug_wait_budget")
 MGFWA_REQ_QUEUED, MGFWA_REQ_RUNNING, MGFWA_REQ_DONE, MGFWA_REQ_FAILED = range(4)
 N_KERNEL_GROUPS = 9
 KERNEL_GROUPS = ("explode", "fitness_explosion", "fitness_finish", "rank", "guide", "fitness_guiding", "select",
@@ -55,7 +56,15 @@ class mgfwa_config(ctypes.Structure):
                 ("eval_budget", ctypes.c_int64), ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32),
                 ("elite_rescore", ctypes.c_int32), ("n_runs", ctypes.c_int32), ("refine_every", ctypes.c_int32),
                 ("refine_steps", ctypes.c_int32), ("refine_lr", ctypes.c_float), ("loser_out", ctypes.c_int32),
-                ("lagged_guiding", ctypes.c_int32)]
+                ("lagged_guiding", ctypes.c_int32), ("shard_id", ctypes.c_int32), ("n_shards", ctypes.c_int32)]
+
+
+class mgfwa_best_key(ctypes.Structure):
+    _fields_ = [("f", ctypes.c_float), ("shard", ctypes.c_int32), ("run", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+# int32_t (*)(void* ctx, mgfwa_best_key* key)
+REDUCE_BEST_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(mgfwa_best_key))
 
 
 class mgfwa_objective(ctypes.Structure):
@@ -125,6 +134,11 @@ def load_library(path: Optional[str] = None):
     L.mgfwa_debug_fp32_tc.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
     i32p = ctypes.POINTER(ctypes.c_int32)
     L.mgfwa_evaluate_fp32_noalloc.argtypes = [i32, i32p, i32p, i64, vp, vp, vp, i64, i32, vp, vp]
+    L.mgfwa_shard_key.argtypes = [vp, i32, ctypes.POINTER(mgfwa_best_key)]
+    L.mgfwa_debug_wait_budget.argtypes = [vp, ctypes.c_uint64]
+    L.mgfwa_reduce_best_keys.argtypes = [ctypes.POINTER(mgfwa_best_key), i32, ctypes.POINTER(mgfwa_best_key)]
+    L.mgfwa_set_reduce_best.argtypes = [vp, REDUCE_BEST_FN, vp]
+    L.mgfwa_global_best_key.argtypes = [vp, i32, ctypes.POINTER(mgfwa_best_key)]
     L.mgfwa_footprint.argtypes = [ctypes.POINTER(mgfwa_config), ctypes.POINTER(mgfwa_objective),
                                   ctypes.POINTER(ctypes.c_int64)]
     L.mgfwa_server_create.argtypes = [i32, i64, ctypes.POINTER(vp)]
@@ -253,6 +267,20 @@ def mgfwa_evaluate_fp32_noalloc(widths, acts, n_samples: int, X_dev: int, y_dev:
     _check(st)
 
 
+def mgfwa_reduce_best_keys(keys) -> mgfwa_best_key:
+    """The run's best of the shards' keys (host reduction in the library): smallest f, NaN last, then shard."""
+    arr = (mgfwa_best_key * len(keys))(*keys)
+    out = mgfwa_best_key()
+    _check(load_library().mgfwa_reduce_best_keys(arr, len(keys), ctypes.byref(out)))
+    return out
+
+
+def shard_range(n_fireworks: int, shard_id: int, n_shards: int):
+    """Fireworks [lo, hi) of the run that shard `shard_id` of `n_shards` holds."""
+    n = max(n_shards, 1)
+    return shard_id * n_fireworks // n, (shard_id + 1) * n_fireworks // n
+
+
 def mgfwa_debug_phase(handle: int, phase: int) -> int:
     return load_library().mgfwa_debug_phase(handle, phase)
 
@@ -284,7 +312,7 @@ class Mgfwa:
                  seed, sigma=0.2, boost=1.0, amp_init=0.0, c_amplify=1.2, c_reduce=0.9, precision=MGFWA_FP32,
                  kind=MGFWA_OBJ_MLP_CE, widths=(), acts=(), X=None, y=None, stream: int = 0, n_runs: int = 1,
                  elite_rescore: int = 2, refine_every: int = 0, refine_steps: int = 0, refine_lr: float = 0.0,
-                 loser_out: int = 0, params=None, lagged_guiding: int = 0):
+                 loser_out: int = 0, params=None, lagged_guiding: int = 0, shard_id: int = 0, n_shards: int = 1):
         cfg = mgfwa_config_init()
         cfg.dim, cfg.lb, cfg.ub = dim, lb, ub
         cfg.n_fireworks, cfg.sparks_per_firework, cfg.guiding_per_firework = (
@@ -296,7 +324,11 @@ class Mgfwa:
         cfg.refine_every, cfg.refine_steps, cfg.refine_lr = refine_every, refine_steps, refine_lr
         cfg.loser_out = loser_out
         cfg.lagged_guiding = lagged_guiding
+        cfg.shard_id, cfg.n_shards = shard_id, n_shards
         self.cfg = cfg
+        lo, hi = shard_range(n_fireworks, shard_id, n_shards)
+        self.mu_local = hi - lo          # fireworks this handle holds
+        self._hook = None
         self._obj = _ObjectiveBuffers(kind, widths, acts, X, y, params)
         self.dim = dim
         self.handle = mgfwa_create(cfg, self._obj.obj, stream)
@@ -343,9 +375,41 @@ class Mgfwa:
     def phase(self, ph: int) -> None:
         _check(mgfwa_debug_phase(self.handle, ph), self.handle)
 
+    def wait_budget(self, ticks: int) -> None:
+        """Budget (SM clock ticks) of the tensor-core kernels' bounded waits; 0 restores the default."""
+        _check(load_library().mgfwa_debug_wait_budget(self.handle, ticks), self.handle)
+
+    def shard_key(self, run: int = 0) -> mgfwa_best_key:
+        key = mgfwa_best_key()
+        _check(load_library().mgfwa_shard_key(self.handle, run, ctypes.byref(key)), self.handle)
+        return key
+
+    def set_reduce_best(self, fn) -> None:
+        """Register fn(key) -> key (the combination of this shard's key with the other shards', e.g. over
+        torch.distributed) as the handle's reduce_best hook; None removes it."""
+        if fn is None:
+            self._hook = None
+            _check(load_library().mgfwa_set_reduce_best(self.handle, REDUCE_BEST_FN(), None), self.handle)
+            return
+
+        def hook(ctx, key_p):
+            try:
+                out = fn(mgfwa_best_key(key_p[0].f, key_p[0].shard, key_p[0].run, 0))
+                key_p[0] = out
+                return 0
+            except Exception:  # noqa: BLE001 - a failing hook is reported through the status
+                return 1
+        self._hook = REDUCE_BEST_FN(hook)  # kept alive with the handle
+        _check(load_library().mgfwa_set_reduce_best(self.handle, self._hook, None), self.handle)
+
+    def global_best_key(self, run: int = 0) -> mgfwa_best_key:
+        key = mgfwa_best_key()
+        _check(load_library().mgfwa_global_best_key(self.handle, run, ctypes.byref(key)), self.handle)
+        return key
+
     def read(self, buf: int) -> np.ndarray:
         B = self.cfg.n_runs
-        mu, lam, m, D, k = (B * self.cfg.n_fireworks, self.cfg.sparks_per_firework, self.cfg.guiding_per_firework,
+        mu, lam, m, D, k = (B * self.mu_local, self.cfg.sparks_per_firework, self.cfg.guiding_per_firework,
                             self.dim, self.k)
         shapes = {MGFWA_BUF_FW_X: ((mu, D), np.float32), MGFWA_BUF_FW_AMP: ((mu,), np.float32),
                   MGFWA_BUF_FW_F: ((mu,), np.float32), MGFWA_BUF_SPARKS: ((mu * lam, D), np.float32),
@@ -554,3 +618,12 @@ class Group:
             self.close()
         except Exception:
             pass
+
+
+def allgather_reduce_best(key: mgfwa_best_key, group=None) -> mgfwa_best_key:
+    """A reduce_best hook body over torch.distributed: gather every rank's key, reduce them with the library's
+    host reduction.  Each rank holds one shard of the run."""
+    import torch.distributed as dist
+    keys = [None] * dist.get_world_size(group)
+    dist.all_gather_object(keys, (float(key.f), int(key.shard), int(key.run)), group=group)
+    return mgfwa_reduce_best_keys([mgfwa_best_key(f, s, r, 0) for f, s, r in keys])

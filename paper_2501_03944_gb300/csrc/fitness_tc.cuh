@@ -13,6 +13,7 @@ struct TcPlan {
   bool f8 = false;      // E4M3 operands (else BF16)
   bool pair = false;    // the CTA-pair kernel (two layers, h1 in {64, 128}); else the one-CTA kernel
   int pairs = 0;        // CTA pairs resident at once (the pair kernel's persistent grid)
+  uint64_t wait_budget = 0;  // clock64 ticks before a bounded wait gives up (0 = the kernels' default, ~2 s)
   CUtensorMap tmap_w2b; // pair kernel: BF16 W2 [P][16 or 32][h1], box 64 x half the rows x 1, 128B swizzle
   CUtensorMap tmap_x3;  // pair kernel: X viewed as [K atoms][N][one 128-byte atom], box one atom x 128 x 2 atoms
   CUtensorMap tmap_wk;  // pair kernel: the first-layer operand viewed the same way, box one atom x half a tile x 2

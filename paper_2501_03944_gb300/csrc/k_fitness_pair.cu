@@ -118,6 +118,7 @@ struct PairArgs {
   const int32_t* y;
   float* partial;       // [m_tiles][count]
   uint32_t* status;
+  uint64_t wait_budget; // clock64 ticks before a wait gives up (0 = the default)
 };
 
 __device__ __forceinline__ float act_f(int a, float v) { return a == kActTanh ? tanhf(v) : fmaxf(v, 0.0f); }
@@ -223,7 +224,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
   // A wait that gives up also stops the peer CTA.
   const uint32_t peer_abort = map_to((const void*)&sm->abort_flag, rank ^ 1u);
   auto wait = [&](uint64_t* bar, uint32_t parity, uint32_t code) -> bool {
-    if (mbar_wait(&sm->abort_flag, bar, parity, a.status, code)) return true;
+    if (mbar_wait(&sm->abort_flag, bar, parity, a.status, code, a.wait_budget)) return true;
     asm volatile("st.relaxed.cluster.shared::cluster.u32 [%0], %1;" ::"r"(peer_abort), "r"(1u) : "memory");
     return false;
   };
@@ -613,6 +614,7 @@ int launch_fitness_pair(const TcPlan& plan, const Mlp& mlp, int64_t first, const
   a.y = mlp.y;
   a.partial = partial;
   a.status = status;
+  a.wait_budget = plan.wait_budget;
   return dispatch_pair(plan, h1, tc_pair_logit_rows(a.C), a, s, false, nullptr) == cudaSuccess ? 1 : -1;
 }
 

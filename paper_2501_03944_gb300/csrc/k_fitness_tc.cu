@@ -104,6 +104,7 @@ struct TcArgs {
   const int32_t* y;
   float* partial;       // [m_tiles][count]
   uint32_t* status;
+  uint64_t wait_budget; // clock64 ticks before a wait gives up (0 = the default)
 };
 
 // H2 = 0: two layers, logits (NL columns per spark) = act(h + b1) W2^T.
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(threads_for(F8), 1)
           // biases, W2 [and W3] of the tile's sparks, for the epilogue and layers 2 [and 3]
           const int tb = local % kTB;
           const uint32_t tuse = (uint32_t)(local / kTB);
-          if (!mbar_wait(&sm->abort_flag, &sm->tail_empty[tb], (tuse & 1u) ^ 1u, a.status, 1u)) break;
+          if (!mbar_wait(&sm->abort_flag, &sm->tail_empty[tb], (tuse & 1u) ^ 1u, a.status, 1u, a.wait_budget)) break;
           const int s0 = nt * S;
           const int s_valid = min(S, a.count - s0);
           mbar_expect_tx(&sm->tail_full[tb], tail_bytes * (uint32_t)s_valid);
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(threads_for(F8), 1)
         for (int kb = 0; kb < a.k_blocks; ++kb, ++it) {
           const int s = (int)(it % (uint32_t)a.stages);
           const uint32_t ph = (it / (uint32_t)a.stages) & 1u;
-          if (!mbar_wait(&sm->abort_flag, &sm->empty[s], ph ^ 1u, a.status, 1u)) {
+          if (!mbar_wait(&sm->abort_flag, &sm->empty[s], ph ^ 1u, a.status, 1u, a.wait_budget)) {
             ok = false;
             break;
           }
@@ -254,9 +255,9 @@ __global__ void __launch_bounds__(threads_for(F8), 1)
         const int bj = j & 1;
         const uint32_t uj = (uint32_t)(j >> 1);
         const int tj_buf = j % kTB;
-        if (!mbar_wait(&sm->abort_flag, &sm->a2_full[bj], uj & 1u, a.status, 2u)) return false;
-        if (!mbar_wait(&sm->abort_flag, &sm->tail_full[tj_buf], (uint32_t)(j / kTB) & 1u, a.status, 2u)) return false;
-        if (!mbar_wait(&sm->abort_flag, &sm->l2_empty[bj], (uj & 1u) ^ 1u, a.status, 2u)) return false;
+        if (!mbar_wait(&sm->abort_flag, &sm->a2_full[bj], uj & 1u, a.status, 2u, a.wait_budget)) return false;
+        if (!mbar_wait(&sm->abort_flag, &sm->tail_full[tj_buf], (uint32_t)(j / kTB) & 1u, a.status, 2u, a.wait_budget)) return false;
+        if (!mbar_wait(&sm->abort_flag, &sm->l2_empty[bj], (uj & 1u) ^ 1u, a.status, 2u, a.wait_budget)) return false;
         tc_fence_after();
         const int ntj = tj / a.m_tiles;
         const int s_valid = min(S, a.count - ntj * S);
@@ -273,7 +274,7 @@ __global__ void __launch_bounds__(threads_for(F8), 1)
         }
         mma_commit(&sm->l2_full[bj]);
         if (kL3) {
-          if (!mbar_wait(&sm->abort_flag, &sm->a3_full[bj], uj & 1u, a.status, 2u)) return false;
+          if (!mbar_wait(&sm->abort_flag, &sm->a3_full[bj], uj & 1u, a.status, 2u, a.wait_budget)) return false;
           tc_fence_after();
           for (int s = 0; s < s_valid; ++s) {
             const uint32_t w3 = smem_u32(w2s + ((size_t)tj_buf * S + s) * kW2Bytes) + (uint32_t)(kAtoms * kAtomBytes);
@@ -294,13 +295,13 @@ __global__ void __launch_bounds__(threads_for(F8), 1)
       for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++local) {
         const int b = local & 1;
         const uint32_t use = (uint32_t)(local >> 1);
-        if (!mbar_wait(&sm->abort_flag, &sm->tmem_empty[b], (use & 1u) ^ 1u, a.status, 2u)) break;
+        if (!mbar_wait(&sm->abort_flag, &sm->tmem_empty[b], (use & 1u) ^ 1u, a.status, 2u, a.wait_budget)) break;
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(b * 256);
         for (int kb = 0; kb < a.k_blocks; ++kb, ++it) {
           const int s = (int)(it % (uint32_t)a.stages);
           const uint32_t ph = (it / (uint32_t)a.stages) & 1u;
-          if (!mbar_wait(&sm->abort_flag, &sm->full[s], ph, a.status, 2u)) {
+          if (!mbar_wait(&sm->abort_flag, &sm->full[s], ph, a.status, 2u, a.wait_budget)) {
             ok = false;
             break;
           }
@@ -352,8 +353,8 @@ __global__ void __launch_bounds__(threads_for(F8), 1)
       const bool valid_row = n < a.N;
       const int label = valid_row ? a.y[n] : 0;   // issued before the waits
       const int tb = local % kTB;
-      bool ok = mbar_wait(&sm->abort_flag, &sm->tmem_full[b], use & 1u, a.status, 4u);
-      ok = ok && mbar_wait(&sm->abort_flag, &sm->tail_full[tb], (uint32_t)(local / kTB) & 1u, a.status, 4u);
+      bool ok = mbar_wait(&sm->abort_flag, &sm->tmem_full[b], use & 1u, a.status, 4u, a.wait_budget);
+      ok = ok && mbar_wait(&sm->abort_flag, &sm->tail_full[tb], (uint32_t)(local / kTB) & 1u, a.status, 4u, a.wait_budget);
       if (epi_bar_any<kEpiWarps>(!ok || sm->abort_flag)) break;
       tc_fence_after();
       const float* tail = tails + (size_t)tb * S * kTailFloats;
@@ -382,7 +383,7 @@ __global__ void __launch_bounds__(threads_for(F8), 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&sm->a2_full[b]);
-      ok = mbar_wait(&sm->abort_flag, &sm->l2_full[b], use & 1u, a.status, 4u);
+      ok = mbar_wait(&sm->abort_flag, &sm->l2_full[b], use & 1u, a.status, 4u, a.wait_budget);
       if (epi_bar_any<kEpiWarps>(!ok || sm->abort_flag)) break;
       tc_fence_after();
       if (kL3) {
@@ -404,7 +405,7 @@ __global__ void __launch_bounds__(threads_for(F8), 1)
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm->a3_full[b]);
-        ok = mbar_wait(&sm->abort_flag, &sm->l3_full[b], use & 1u, a.status, 4u);
+        ok = mbar_wait(&sm->abort_flag, &sm->l3_full[b], use & 1u, a.status, 4u, a.wait_budget);
         if (epi_bar_any<kEpiWarps>(!ok || sm->abort_flag)) break;
         tc_fence_after();
       }
@@ -744,6 +745,7 @@ int launch_fitness_tc(const TcPlan& plan, const Mlp& mlp, int64_t first, const f
   a.y = mlp.y;
   a.partial = partial;
   a.status = status;
+  a.wait_budget = plan.wait_budget;
   return dispatch(plan, mlp, a, s, false) == cudaSuccess ? 1 : -1;
 }
 

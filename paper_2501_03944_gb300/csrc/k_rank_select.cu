@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(256) k_select_copy(Problem p, const float* __r
     const float width = __fsub_rn(p.ub, p.lb);
     float4* d4 = reinterpret_cast<float4*>(fw_x + (int64_t)y * p.Dp);
     for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const uint4 r = philox4x32_10(make_uint4((uint32_t)e, (uint32_t)il, gen, kLoser), k0, k1);
+      const uint4 r = philox4x32_10(make_uint4((uint32_t)e, (uint32_t)(il + p.fw_off), gen, kLoser), k0, k1);
       float v[4];
 #pragma unroll
       for (int l = 0; l < 4; ++l) v[l] = (4 * e + l < p.D) ? __fmaf_rn(u24(lane_of(r, l)), width, p.lb) : 0.0f;

@@ -74,7 +74,8 @@ __device__ __forceinline__ void store_w2_4(const OpDesc& op, int64_t row, int64_
   store_bf16x4(static_cast<__nv_bfloat16*>(op.w2) + row * op.w2_row_elems() + cls * op.w2_h1 + j, a, b, c, d);
 }
 
-// grid (coordinate blocks, B * mu): global firework z = b * mu + i.
+// grid (coordinate blocks, B * mu): global firework z = b * mu + i (Philox
+// unit: the firework's index in its run, i + fw_off).
 __global__ void __launch_bounds__(kThreads) k_init(Problem p, float* __restrict__ fw_x,
                                                    float* __restrict__ fw_amp) {
   griddep_wait();
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(kThreads) k_init(Problem p, float* __restrict_
   if (d0 >= p.Dp) return;
   uint32_t k0, k1;
   run_key(p, b, k0, k1);
-  const uint4 r = philox4x32_10(make_uint4((uint32_t)c4, (uint32_t)i, 0u, kInit), k0, k1);
+  const uint4 r = philox4x32_10(make_uint4((uint32_t)c4, (uint32_t)(i + p.fw_off), 0u, kInit), k0, k1);
   const float width = __fsub_rn(p.ub, p.lb);
   float v[4];
 #pragma unroll
@@ -107,7 +108,7 @@ __device__ __forceinline__ float signed_u24(uint32_t r) {
 // kThreads Philox blocks (4 coordinates each) of one spark row; each thread
 // takes kExplodeBlocks of them, kThreads apart, so a warp's stores stay
 // contiguous.  Global firework z = b * mu + i, spark row z * lam + j, Philox
-// unit i * lam + j of run b's stream.  The thread's firework coordinates are
+// unit (i + fw_off) * lam + j of run b's stream.  The thread's firework coordinates are
 // loaded first; per Philox block the explosion draw, then -- when any lane
 // of the warp has a coordinate outside [lb, ub] -- the mapping stream's block
 // for the whole warp (a warp-uniform branch), taken only where a lane is out
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(kThreads) k_explode(Problem p, const uint32_t*
   const uint32_t z = blockIdx.z;
   const uint32_t b = z / (uint32_t)p.mu, i = z - b * (uint32_t)p.mu;
   const uint32_t row = z * (uint32_t)p.lam + blockIdx.y;
-  const uint32_t unit = i * (uint32_t)p.lam + blockIdx.y;
+  const uint32_t unit = (i + (uint32_t)p.fw_off) * (uint32_t)p.lam + blockIdx.y;
   uint32_t k0, k1;
   run_key(p, (int)b, k0, k1);
   const PhiloxKeys rk = philox_keys(k0, k1);  // shared by the thread's Philox blocks
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(kThreads) k_guide(Problem p, const uint32_t* _
   const int i = blockIdx.z;               // global firework z = b * mu + i_local
   const int gq = i * p.m + blockIdx.y;    // global guiding row z * m + q
   const int run = i / p.mu;
-  const uint32_t gunit = (uint32_t)((i - run * p.mu) * p.m + (int)blockIdx.y);  // i_local * m + q
+  const uint32_t gunit = (uint32_t)((i - run * p.mu + p.fw_off) * p.m + (int)blockIdx.y);  // (index in run) * m + q
   uint32_t k0, k1;
   run_key(p, run, k0, k1);
   const int64_t c4 = (int64_t)blockIdx.x * kThreads + threadIdx.x;

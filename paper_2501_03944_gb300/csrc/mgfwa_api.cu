@@ -100,6 +100,9 @@ struct mgfwa_handle {
   int32_t mtiles = 0;  // sample tiles of 128
   int64_t evals = 0;
   int32_t gen = 0;
+  int32_t mu_run = 0;                       // fireworks of the whole run (this handle holds a shard of them)
+  mgfwa_reduce_best_fn reduce_best = nullptr;  // combines the shards' best keys (null: the handle is the run)
+  void* reduce_ctx = nullptr;
   int32_t next_phase = MGFWA_PHASE_EXPLODE;
   int64_t launches = 0;
   bool broken = false;
@@ -480,6 +483,11 @@ mgfwa_status one_generation(mgfwa_t* h) {
 
 // The next generation fits: its sparks and, if due, its refinement.
 bool budget_allows(const mgfwa_t* h) {
+  if (h->cfg.n_shards > 1) {
+    // a shard runs a generation when the whole run would (no refinement with shards)
+    const int64_t P_run = (int64_t)h->mu_run * (h->p.lam + h->p.m);
+    return (int64_t)h->mu_run + (int64_t)(h->gen + 1) * P_run <= h->cfg.eval_budget;
+  }
   return h->evals + h->P + (refine_due(h, h->gen + 1) ? refine_cost(h) : 0) <= h->cfg.eval_budget;
 }
 
@@ -529,6 +537,16 @@ mgfwa_status validate(const mgfwa_config* c, const mgfwa_objective* o) {
   if (c->loser_out != 0 && c->loser_out != 1) return fail(nullptr, MGFWA_EINVAL, "loser_out must be 0 or 1");
   if (c->lagged_guiding != 0 && c->lagged_guiding != 1)
     return fail(nullptr, MGFWA_EINVAL, "lagged_guiding must be 0 or 1");
+  if (c->n_shards < 0 || c->n_shards > c->n_fireworks)
+    return fail(nullptr, MGFWA_EINVAL, "n_shards must be in [0, n_fireworks]");
+  if (c->n_shards > 1) {
+    if (c->shard_id < 0 || c->shard_id >= c->n_shards)
+      return fail(nullptr, MGFWA_EINVAL, "shard_id must be in [0, n_shards)");
+    if (c->loser_out || c->refine_every > 0)
+      return fail(nullptr, MGFWA_EINVAL, "a shard of a run cannot use the loser-out tournament or refinement");
+  } else if (c->shard_id != 0) {
+    return fail(nullptr, MGFWA_EINVAL, "shard_id must be 0 without sharding");
+  }
   if (c->refine_every > 0) {
     if (o->kind != MGFWA_OBJ_MLP_CE) return fail(nullptr, MGFWA_EINVAL, "refinement needs an MLP objective");
     if (c->refine_steps < 1 || c->refine_steps > 10000)
@@ -661,6 +679,8 @@ uint64_t problem_fingerprint(const mgfwa_config* cfg, const mgfwa_objective* obj
   mix(&cfg->refine_lr, sizeof(cfg->refine_lr));
   mix(&cfg->loser_out, sizeof(cfg->loser_out));
   mix(&cfg->lagged_guiding, sizeof(cfg->lagged_guiding));
+  mix(&cfg->shard_id, sizeof(cfg->shard_id));
+  mix(&cfg->n_shards, sizeof(cfg->n_shards));
   mix(&obj->kind, sizeof(obj->kind));
   mix(&obj->n_layers, sizeof(obj->n_layers));
   if (obj->kind == MGFWA_OBJ_MLP_CE) {
@@ -693,6 +713,15 @@ void plan_handle(mgfwa_t* h, const mgfwa_config* cfg, const mgfwa_objective* obj
   p.lb = cfg->lb;
   p.ub = cfg->ub;
   p.mu = cfg->n_fireworks;
+  p.fw_off = 0;
+  h->mu_run = cfg->n_fireworks;
+  if (cfg->n_shards > 1) {
+    // this shard's fireworks: [shard_id mu / n_shards, (shard_id + 1) mu / n_shards) of the run
+    const int64_t lo = (int64_t)cfg->shard_id * cfg->n_fireworks / cfg->n_shards;
+    const int64_t hi = (int64_t)(cfg->shard_id + 1) * cfg->n_fireworks / cfg->n_shards;
+    p.mu = (int32_t)(hi - lo);
+    p.fw_off = (int32_t)lo;
+  }
   p.lam = cfg->sparks_per_firework;
   p.m = cfg->guiding_per_firework;
   p.g = p.lam / p.m;
@@ -1040,6 +1069,54 @@ mgfwa_status mgfwa_best_run(mgfwa_t* h, int32_t run, float* x_out, double* f_out
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h, "best synchronise");
   if (evals_out) *evals_out = h->evals;
   return check_status_word(h);
+}
+
+// ---------------------------------------------------------------------------
+// The run's best over shards.
+
+mgfwa_status mgfwa_reduce_best_keys(const mgfwa_best_key* keys, int32_t n, mgfwa_best_key* out) {
+  if (!keys || !out || n < 1) return MGFWA_EINVAL;
+  auto before = [](const mgfwa_best_key& a, const mgfwa_best_key& b) {
+    const float fa = std::isnan(a.f) ? INFINITY : a.f, fb = std::isnan(b.f) ? INFINITY : b.f;
+    if (fa != fb) return fa < fb;
+    if (std::isnan(a.f) != std::isnan(b.f)) return !std::isnan(a.f);  // +inf before NaN
+    if (a.shard != b.shard) return a.shard < b.shard;
+    return a.run < b.run;
+  };
+  mgfwa_best_key best = keys[0];
+  for (int32_t i = 1; i < n; ++i)
+    if (before(keys[i], best)) best = keys[i];
+  *out = best;
+  return MGFWA_OK;
+}
+
+mgfwa_status mgfwa_shard_key(mgfwa_t* h, int32_t run, mgfwa_best_key* key_out) {
+  mgfwa_status st = check_usable(h);
+  if (st != MGFWA_OK) return st;
+  if (!key_out || run < 0 || run >= h->p.B) return fail(h, MGFWA_EINVAL, "shard key: bad run or null output");
+  float f = 0.0f;
+  if (cudaMemcpyAsync(&f, h->best_f + run, sizeof(float), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return cuda_fail(h, "read the run's best");
+  key_out->f = f;
+  key_out->shard = h->cfg.n_shards > 1 ? h->cfg.shard_id : 0;
+  key_out->run = run;
+  key_out->pad = 0;
+  return check_status_word(h);
+}
+
+mgfwa_status mgfwa_set_reduce_best(mgfwa_t* h, mgfwa_reduce_best_fn fn, void* ctx) {
+  if (!h) return MGFWA_EINVAL;
+  h->reduce_best = fn;
+  h->reduce_ctx = fn ? ctx : nullptr;
+  return MGFWA_OK;
+}
+
+mgfwa_status mgfwa_global_best_key(mgfwa_t* h, int32_t run, mgfwa_best_key* key_out) {
+  mgfwa_status st = mgfwa_shard_key(h, run, key_out);
+  if (st != MGFWA_OK || !h->reduce_best) return st;
+  if (h->reduce_best(h->reduce_ctx, key_out) != 0) return fail(h, MGFWA_ECUDA, "the reduce_best hook failed");
+  return MGFWA_OK;
 }
 
 mgfwa_status mgfwa_best(mgfwa_t* h, float* x_out, double* f_out, int64_t* evals_out) {
@@ -1512,6 +1589,12 @@ mgfwa_status mgfwa_debug_fp32_tc(const mgfwa_t* h, int32_t* rescore, int32_t* re
   if (!h) return MGFWA_EINVAL;
   if (rescore) *rescore = h->rescore_scratch ? (l1_on_tensor_cores(h->rescore_plan, h->mlp, &h->rescore_l1) ? 1 : 0) : -1;
   if (refine) *refine = h->refine ? (l1_on_tensor_cores(h->gp, h->mlp, &h->refine_l1) ? 1 : 0) : -1;
+  return MGFWA_OK;
+}
+
+mgfwa_status mgfwa_debug_wait_budget(mgfwa_t* h, uint64_t ticks) {
+  if (!h) return MGFWA_EINVAL;
+  h->tc.wait_budget = ticks;
   return MGFWA_OK;
 }
 

@@ -26,6 +26,8 @@ struct Problem {
   float beta, amp0, c_a, c_r;
   uint64_t seed;   // run b draws from Philox keyed by seed + b
   int32_t lo_gmax; // loser-out tournament: the generations the budget allows (0 = tournament off)
+  int32_t fw_off;  // index in the run of this handle's first firework (a shard of the run), 0 otherwise;
+                   // Philox units number fireworks by their index in the run
 };
 
 // Philox key of run b: low and high words of seed + b.

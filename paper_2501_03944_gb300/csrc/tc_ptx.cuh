@@ -61,13 +61,15 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
 
 // Bounded wait; false if the CTA is aborting (a timeout here or elsewhere).
 // On a timeout it raises *abort and ORs `code` into the status word.
+// `budget` is in clock64 ticks; 0 means kWaitBudget.
 __device__ __forceinline__ bool mbar_wait(volatile int* abort, uint64_t* bar, uint32_t parity, uint32_t* status,
-                                          uint32_t code) {
+                                          uint32_t code, uint64_t budget = 0) {
   if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t limit = budget ? budget : kWaitBudget;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort) return false;
-    if ((uint64_t)(clock64() - t0) > kWaitBudget) {
+    if ((uint64_t)(clock64() - t0) > limit) {
       *abort = 1;
       atomicOr(status, code);
       return false;

@@ -42,7 +42,7 @@ def test_structure_layout_matches_header(pkg, tmp_path):
     """Compile a C program against the header and compare every field offset with the ctypes mirror."""
     import ctypes
     classes = (pkg.mgfwa_config, pkg.mgfwa_objective, pkg.mgfwa_info, pkg.mgfwa_request_info,
-               pkg.mgfwa_server_stats)
+               pkg.mgfwa_server_stats, pkg.mgfwa_best_key)
     body = []
     for cls in classes:
         body.append(f'  printf("{cls.__name__} %zu\\n", sizeof({cls.__name__}));')
