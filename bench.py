@@ -391,7 +391,10 @@ def gpu_arm(args):
 
     extra = {}
     if not args.no_extras and world == 1:
-        extra["serving"] = serving_trace(pkg, X, y)
+        # the serving mix at its arrival rate (an overload: the queue grows) and at a sub-saturating rate,
+        # each a bounded window of the trace (--serving-full runs the 2,000-request window)
+        extra["serving"] = {"overload": serving_trace(pkg, X, y, n_requests=200, rate_hz=200.0),
+                            "sub_saturating": serving_trace(pkg, X, y, n_requests=60, rate_hz=10.0, seed=6)}
         extra["grouped_64_mixed"] = grouped_mixed(pkg)
         extra["fitness_rel_err_vs_fp32"] = fitness_error_vs_fp32(pkg, X, y, stream)
     if not args.no_extras:
@@ -677,6 +680,20 @@ def serving_trace(pkg, X, y, n_requests: int = 40, rate_hz: float = 200.0, max_l
                    "evaluations; Poisson arrivals"}
 
 
+def serving_full(args):
+    """The serving workload's full window: 2,000 Poisson requests at 200/s, and 500 at a sub-saturating
+    10/s; one JSON line with both (rank 0, one GPU)."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2501_03944_gb300 as pkg
+    pkg.load_library()
+    X, y = W.make_data(WORKLOAD)
+    out = {"serving_full": {"overload": serving_trace(pkg, X, y, n_requests=2000, rate_hz=200.0),
+                            "sub_saturating": serving_trace(pkg, X, y, n_requests=500, rate_hz=10.0, seed=6)}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -687,11 +704,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end request (profiling runs)")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP32 and batched comparison runs")
+    ap.add_argument("--serving-full", action="store_true",
+                    help="only the serving workload's full 2,000-request window (a few minutes)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return reference_arm(args)
+    if args.serving_full:
+        return serving_full(args)
     return gpu_arm(args)
 
 

@@ -124,3 +124,50 @@ def test_requests_arriving_while_others_run(pkg):
             info, x = s.poll(rid, want_x=True)
             ax, af, _ = _alone(pkg, w, seed, prec, d)
             assert np.array_equal(x, ax) and info.best_f == af
+
+
+def test_admission_never_exceeds_the_limit_over_a_long_trace(pkg):
+    """120 requests of six footprints (sphere runs of several dimensions and populations, 8-16-3 nets)
+    arriving a few per tick while others run: after every tick the live runs' device bytes stay within the
+    limit and the live count within the slots, admission stays first-in first-out, and every request
+    finishes with the evaluations its budget allows."""
+    rng = np.random.default_rng(11)
+    small = W.MLP_8_16_3
+    data_small = W.make_data(small)
+    kinds = []
+    for dim, mu in ((30, 5), (200, 3), (1000, 4), (4000, 2)):
+        kinds.append((W.scaled(W.SPHERE_30, dim=dim, n_fireworks=mu), (None, None)))
+    kinds.append((W.scaled(small, n_fireworks=3), data_small))
+    kinds.append((small, data_small))
+    reqs = []
+    for k in range(120):
+        w, d = kinds[int(rng.integers(len(kinds)))]
+        gens = int(rng.integers(2, 9))
+        w = W.scaled(w, eval_budget=W.budget_for_generations(w.n_fireworks, w.sparks_per_firework,
+                                                             w.guiding_per_firework, gens))
+        reqs.append((w, 900 + k, d, gens))
+    fps = [pkg.mgfwa_footprint(*pkg.workload_request(w, s, pkg.MGFWA_FP32, X=d[0], y=d[1])) for w, s, d, _ in reqs]
+    limit = int(1.6 * max(fps))             # the largest fits, and the limit binds most ticks
+    assert sum(sorted(fps)[-3:]) > limit
+    max_live = 5
+    with pkg.Server(max_live=max_live, device_bytes_limit=limit) as s:
+        ids, nxt = [], 0
+        for _ in range(20_000):
+            for _ in range(int(rng.integers(0, 4))):
+                if nxt < len(reqs):
+                    w, seed, d, _ = reqs[nxt]
+                    ids.append(s.submit(*pkg.workload_request(w, seed, pkg.MGFWA_FP32, X=d[0], y=d[1])))
+                    nxt += 1
+            st = s.stats()
+            assert st.device_bytes_in_use <= limit and st.live <= max_live
+            if nxt == len(reqs) and st.live == 0 and st.queued == 0:
+                break
+            s.tick(1)
+            st = s.stats()
+            assert st.device_bytes_in_use <= limit and st.live <= max_live
+        infos = [s.poll(rid)[0] for rid in ids]
+    assert len(infos) == len(reqs) and all(i.state == pkg.MGFWA_REQ_DONE for i in infos)
+    admits = [i.t_admit for i in infos]
+    assert admits == sorted(admits)
+    for i, (w, _, _, gens) in zip(infos, reqs):
+        assert i.evals == w.n_fireworks + gens * w.sparks_per_generation
