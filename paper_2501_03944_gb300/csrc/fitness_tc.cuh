@@ -58,6 +58,53 @@ void tc_release(TcPlan& plan);
 int launch_fitness_tc(const TcPlan& plan, const Mlp& mlp, int64_t first, const float* rows, int64_t ld,
                       int32_t count, float scale, float* partial, uint32_t* status, cudaStream_t s);
 
+// Arguments of one launch of the CTA-pair kernel (one handle's rows).
+struct PairArgs {
+  int32_t count;        // sparks in this launch
+  int32_t first_spark;  // first spark row of the launch (operand tensor maps)
+  int32_t m_pairs;      // 256-sample tiles
+  int32_t m_tiles;      // 128-sample tiles (rows of `partial`)
+  int32_t n_tiles;
+  int32_t n_full;       // K atoms entirely inside d_in
+  int32_t n_steps;      // K steps per tile: ceil(n_full / 2), plus one for a partial last atom
+  int32_t k_last;       // layer-1 MMAs in the partial last atom (0 if d_in ends on an atom)
+  int32_t stages;
+  int32_t C;            // classes (<= NL)
+  int32_t act;
+  int32_t c_pad;        // C rounded up to 4 (floats of b2 copied)
+  float scale;          // layer-1 accumulator multiplier (1 for BF16; 1 / (inv_x inv_w) for E4M3)
+  int64_t N;
+  int64_t ld;           // FP32 row stride of the sparks
+  int64_t b1_off, b2_off;
+  const float* rows;    // FP32 spark rows of this launch (biases)
+  const int32_t* y;
+  float* partial;       // [m_tiles][count]
+  uint32_t* status;
+  uint64_t wait_budget; // clock64 ticks before a wait gives up (0 = the default)
+};
+
+// One member of a grouped launch: its tensor maps and arguments, in device
+// memory, and where its tiles start among the launch's.
+struct alignas(64) PairMember {
+  CUtensorMap x3, x, w3, w, w2;
+  PairArgs a;
+  int32_t tile_start, tiles;
+};
+
+// The member entry of one launch's worth of rows (as launch_fitness_tc would
+// make them) of a handle on the pair kernel.
+void tc_pair_member(const TcPlan& plan, const Mlp& mlp, int64_t first, const float* rows, int64_t ld, int32_t count,
+                    float scale, float* partial, uint32_t* status, PairMember* out);
+// True if two pair plans run the same kernel instance (h1, logit rows,
+// operand type), so their launches can be grouped.
+bool tc_pair_same_instance(const TcPlan& a, const Mlp& ma, const TcPlan& b, const Mlp& mb);
+// One launch of the pair kernel over `n` members (table_dev: n entries in
+// device memory, tile_start filled, laid end to end, total_tiles in all);
+// `plan` gives the instance, shared-memory size and grid.  Returns 1, or -1
+// after a launch error.
+int launch_fitness_pair_group(const TcPlan& plan, const Mlp& mlp, const PairMember* table_dev, int32_t n,
+                              uint32_t* status, cudaStream_t s, int32_t total_tiles);
+
 // The CTA-pair kernel's pieces (k_fitness_pair.cu), used by tc_plan and
 // launch_fitness_tc.
 int tc_pair_sparks(int h1, int C);  // sparks per tile: floor(256 / (h1 + logit rows))

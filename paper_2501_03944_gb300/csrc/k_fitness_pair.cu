@@ -97,29 +97,6 @@ struct PairSmem {
   volatile int abort_flag;
 };
 
-struct PairArgs {
-  int32_t count;        // sparks in this launch
-  int32_t first_spark;  // first spark row of the launch (operand tensor maps)
-  int32_t m_pairs;      // 256-sample tiles
-  int32_t m_tiles;      // 128-sample tiles (rows of `partial`)
-  int32_t n_tiles;
-  int32_t n_full;       // K atoms entirely inside d_in
-  int32_t n_steps;      // K steps per tile: ceil(n_full / 2), plus one for a partial last atom
-  int32_t k_last;       // layer-1 MMAs in the partial last atom (0 if d_in ends on an atom)
-  int32_t stages;
-  int32_t C;            // classes (<= NL)
-  int32_t act;
-  int32_t c_pad;        // C rounded up to 4 (floats of b2 copied)
-  float scale;          // layer-1 accumulator multiplier (1 for BF16; 1 / (inv_x inv_w) for E4M3)
-  int64_t N;
-  int64_t ld;           // FP32 row stride of the sparks
-  int64_t b1_off, b2_off;
-  const float* rows;    // FP32 spark rows of this launch (biases)
-  const int32_t* y;
-  float* partial;       // [m_tiles][count]
-  uint32_t* status;
-  uint64_t wait_budget; // clock64 ticks before a wait gives up (0 = the default)
-};
 
 __device__ __forceinline__ float act_f(int a, float v) { return a == kActTanh ? tanhf(v) : fmaxf(v, 0.0f); }
 
@@ -147,11 +124,18 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-template <int H1, int NL, bool F8>
+// kGroup: one launch over several handles' sparks.  Their tiles are laid end
+// to end (member i's tiles from members[i].tile_start on), and each role
+// walks ascending tiles with a cursor into the member table (device memory:
+// the members' tensor maps and arguments).  Otherwise the kernel parameters
+// hold the one launch's maps and `a` its arguments.  `a` also carries what
+// every member shares: stages, the status word and the wait budget.
+template <int H1, int NL, bool F8, bool kGroup>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
     k_fitness_pair(const __grid_constant__ CUtensorMap tmap_x3, const __grid_constant__ CUtensorMap tmap_x,
                    const __grid_constant__ CUtensorMap tmap_w3, const __grid_constant__ CUtensorMap tmap_w,
-                   const __grid_constant__ CUtensorMap tmap_w2, PairArgs a) {
+                   const __grid_constant__ CUtensorMap tmap_w2, PairArgs a, const PairMember* __restrict__ members,
+                   int32_t n_members) {
   griddep_wait();
   griddep_launch_dependents();
   constexpr int S = pair_sparks(H1);             // sparks per tile
@@ -188,7 +172,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
   const bool lead = rank == 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int pair = (int)(blockIdx.x >> 1), npairs = (int)(gridDim.x >> 1);
-  const int tiles = a.m_pairs * a.n_tiles;
+  const int tiles = kGroup ? members[n_members - 1].tile_start + members[n_members - 1].tiles : a.m_pairs * a.n_tiles;
+  // the member of tile t (advancing `cur`) and t's index among that member's tiles
+  auto member_at = [&](int t, int& cur) -> int {
+    if (!kGroup) return t;
+    while (cur + 1 < n_members && t >= members[cur + 1].tile_start) ++cur;
+    return t - members[cur].tile_start;
+  };
+  auto args_of = [&](int cur) -> const PairArgs& { return kGroup ? members[cur].a : a; };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < a.stages; ++s) {
@@ -235,20 +226,34 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
       uint32_t it = 0;
       int local = 0;
       bool ok = true;
-      const uint32_t bias_bytes = (uint32_t)(H1 + a.c_pad) * 4u;
+      int cur = 0, fenced = -1;
       for (int t = pair; t < tiles && ok; t += npairs, ++local) {
-        const int mt = t % a.m_pairs, nt = t / a.m_pairs;
+        const int lt = member_at(t, cur);
+        const PairArgs& m = args_of(cur);
+        const CUtensorMap* mx3 = kGroup ? &members[cur].x3 : &tmap_x3;
+        const CUtensorMap* mx = kGroup ? &members[cur].x : &tmap_x;
+        const CUtensorMap* mw3 = kGroup ? &members[cur].w3 : &tmap_w3;
+        const CUtensorMap* mw = kGroup ? &members[cur].w : &tmap_w;
+        const CUtensorMap* mw2 = kGroup ? &members[cur].w2 : &tmap_w2;
+        if (kGroup && fenced != cur) {
+          // the member's maps were written to global memory by the host: order the tensor-map proxy's reads
+          for (const CUtensorMap* mp : {mx3, mx, mw3, mw, mw2})
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mp) : "memory");
+          fenced = cur;
+        }
+        const uint32_t bias_bytes = (uint32_t)(H1 + m.c_pad) * 4u;
+        const int mt = lt % m.m_pairs, nt = lt / m.m_pairs;
         const int s0 = nt * S;
-        const int s_valid = min(S, a.count - s0);
+        const int s_valid = min(S, m.count - s0);
         const int tb = local % kTBufs;
         const uint32_t tuse = (uint32_t)(local / kTBufs);
         if (!wait(&sm->tail_empty[tb], (tuse & 1u) ^ 1u, 1u)) break;
         mbar_expect_tx(&sm->bias_full[tb], bias_bytes * (uint32_t)s_valid);
         for (int s = 0; s < s_valid; ++s) {
-          const float* row = a.rows + (int64_t)(s0 + s) * a.ld;
+          const float* row = m.rows + (int64_t)(s0 + s) * m.ld;
           float* tl = tails + ((size_t)tb * S + s) * kTailF;
-          bulk_load(tl, row + a.b1_off, (uint32_t)H1 * 4u, &sm->bias_full[tb]);
-          bulk_load(tl + H1, row + a.b2_off, (uint32_t)a.c_pad * 4u, &sm->bias_full[tb]);
+          bulk_load(tl, row + m.b1_off, (uint32_t)H1 * 4u, &sm->bias_full[tb]);
+          bulk_load(tl + H1, row + m.b2_off, (uint32_t)m.c_pad * 4u, &sm->bias_full[tb]);
         }
         // this CTA's W2 halves; the even CTA's barrier expects both CTAs' bytes
         if (lead) mbar_expect_tx(&sm->w2_full[tb], 2u * kW2Bytes * (uint32_t)s_valid);
@@ -257,13 +262,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
           uint8_t* w2 = w2s + ((size_t)tb * S + s) * kW2Bytes;
 #pragma unroll
           for (int at = 0; at < kW2Atoms; ++at)
-            tma_load_3d_pair(w2 + at * kW2AtomBytes, &tmap_w2, at * 64, (int)rank * kHalfNL, a.first_spark + s0 + s,
+            tma_load_3d_pair(w2 + at * kW2AtomBytes, mw2, at * 64, (int)rank * kHalfNL, m.first_spark + s0 + s,
                              w2_bar);
         }
         const int row_x = mt * (2 * kPM) + (int)rank * kPM;
-        const int row_w = (a.first_spark + s0) * H1 + (int)rank * (kNT / 2);
-        const int n_pairs = (a.n_full + 1) / 2;
-        for (int kb = 0; kb < a.n_steps; ++kb, ++it) {
+        const int row_w = (m.first_spark + s0) * H1 + (int)rank * (kNT / 2);
+        const int n_pairs = (m.n_full + 1) / 2;
+        for (int kb = 0; kb < m.n_steps; ++kb, ++it) {
           const int st = (int)(it % (uint32_t)a.stages);
           const uint32_t ph = (it / (uint32_t)a.stages) & 1u;
           if (!wait(&sm->empty[st], ph ^ 1u, 1u)) {
@@ -274,13 +279,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
           if (kb < n_pairs) {
             // atoms 2 kb and 2 kb + 1 (the second one past n_full is zero fill)
             if (lead) mbar_expect_tx(&sm->full[st], 2u * (kStageA + kStageB));
-            tma_load_3d_pair(stage_a + (size_t)st * kStageA, &tmap_x3, 0, row_x, 2 * kb, bar);
-            tma_load_3d_pair(stage_b + (size_t)st * kStageB, &tmap_w3, 0, row_w, 2 * kb, bar);
+            tma_load_3d_pair(stage_a + (size_t)st * kStageA, mx3, 0, row_x, 2 * kb, bar);
+            tma_load_3d_pair(stage_b + (size_t)st * kStageB, mw3, 0, row_w, 2 * kb, bar);
           } else {
             // the partial last atom, zero past d_in
             if (lead) mbar_expect_tx(&sm->full[st], 2u * (kAtomA + kAtomB));
-            tma_load_2d_pair(stage_a + (size_t)st * kStageA, &tmap_x, a.n_full * kBK, row_x, bar);
-            tma_load_2d_pair(stage_b + (size_t)st * kStageB, &tmap_w, a.n_full * kBK, row_w, bar);
+            tma_load_2d_pair(stage_a + (size_t)st * kStageA, mx, m.n_full * kBK, row_x, bar);
+            tma_load_2d_pair(stage_b + (size_t)st * kStageB, mw, m.n_full * kBK, row_w, bar);
           }
         }
       }
@@ -313,14 +318,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
         const uint32_t tu = (uint32_t)(j / kTBufs) & 1u;
         return mbar_test_wait(&sm->a2_full[j & 1], (uint32_t)(j >> 1) & 1u) && mbar_test_wait(&sm->w2_full[tbj], tu);
       };
-      auto layer2 = [&](int j, int tj) -> bool {
+      auto layer2 = [&](int j, int s_valid) -> bool {
         const int bj = j & 1;
         const int tbj = j % kTBufs;
         const uint32_t tu = (uint32_t)(j / kTBufs) & 1u;
         if (!wait(&sm->a2_full[bj], (uint32_t)(j >> 1) & 1u, 2u)) return false;
         if (!wait(&sm->w2_full[tbj], tu, 2u)) return false;
         tc_fence_after();
-        const int s_valid = min(S, a.count - (tj / a.m_pairs) * S);
         const uint32_t half = tmem_base + (uint32_t)(bj * 256);
         for (int s = 0; s < s_valid; ++s) {
           const uint32_t w2 = smem_u32(w2s + ((size_t)tbj * S + s) * kW2Bytes);
@@ -338,17 +342,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
       uint32_t it = 0;
       int local = 0;
       bool ok = true;
-      int pend = -1, pend_t = -1;  // the tile whose layer 2 is not issued yet
+      int pend = -1, pend_sv = 0;  // the tile whose layer 2 is not issued yet, and its spark count
+      int cur = 0;
       for (int t = pair; t < tiles && ok; t += npairs, ++local) {
+        const int lt = member_at(t, cur);
+        const PairArgs& m = args_of(cur);
         const int b = local & 1;
         const uint32_t use = (uint32_t)(local >> 1);
         if (!wait(&sm->tmem_empty[b], (use & 1u) ^ 1u, 2u)) break;
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(b * 256);
-        const int n_pairs = (a.n_full + 1) / 2;
-        for (int kb = 0; kb < a.n_steps; ++kb, ++it) {
+        const int n_pairs = (m.n_full + 1) / 2;
+        for (int kb = 0; kb < m.n_steps; ++kb, ++it) {
           if (pend >= 0 && l2_ready(pend)) {
-            if (!layer2(pend, pend_t)) {
+            if (!layer2(pend, pend_sv)) {
               ok = false;
               break;
             }
@@ -365,11 +372,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
           const uint32_t b_addr = smem_u32(stage_b + (size_t)st * kStageB);
           // MMAs of this step: four per full atom (two atoms, or one if n_full is odd and this is its
           // last pair), k_last for the partial atom
-          const int atoms = kb < n_pairs ? (2 * kb + 1 < a.n_full ? 2 : 1) : 1;
+          const int atoms = kb < n_pairs ? (2 * kb + 1 < m.n_full ? 2 : 1) : 1;
 #pragma unroll
           for (int at = 0; at < 2; ++at) {
             if (at >= atoms) break;
-            const int nk = kb < n_pairs ? kRowB / kMmaKB : a.k_last;
+            const int nk = kb < n_pairs ? kRowB / kMmaKB : m.k_last;
             const uint32_t aa = a_addr + (uint32_t)at * kAtomA, bb = b_addr + (uint32_t)at * kAtomB;
 #pragma unroll
             for (int k = 0; k < kRowB / kMmaKB; ++k) {
@@ -385,14 +392,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
         }
         if (!ok) break;
         commit_both(&sm->tmem_full[b]);
-        if (pend >= 0 && !layer2(pend, pend_t)) {
+        if (pend >= 0 && !layer2(pend, pend_sv)) {
           ok = false;
           break;
         }
         pend = local;
-        pend_t = t;
+        pend_sv = min(S, m.count - (lt / m.m_pairs) * S);
       }
-      if (ok && pend >= 0) layer2(pend, pend_t);
+      if (ok && pend >= 0) layer2(pend, pend_sv);
       // every issued MMA completes before TMEM is released: one more commit, bounded wait
       mma2_commit(map_to(&sm->mma_done, 0u));
       mbar_drain(&sm->mma_done, 0u, a.status);
@@ -405,17 +412,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
     const int et = threadIdx.x - 64;    // 0 .. 32 kEpi - 1
     const int row_in_tile = quad * 32 + lane;
     const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16);
-    const float sc = a.scale;
     int local = 0;
+    int cur = 0;
     for (int t = pair; t < tiles; t += npairs, ++local) {
-      const int mt = t % a.m_pairs, nt = t / a.m_pairs;
+      const int lt = member_at(t, cur);
+      const PairArgs& m = args_of(cur);
+      const float sc = m.scale;
+      const int mt = lt % m.m_pairs, nt = lt / m.m_pairs;
       const int b = local & 1;
       const uint32_t use = (uint32_t)(local >> 1);
       const int s0 = nt * S;
-      const int s_valid = min(S, a.count - s0);
+      const int s_valid = min(S, m.count - s0);
       const int64_t n = (int64_t)mt * (2 * kPM) + (int64_t)rank * kPM + row_in_tile;
-      const bool valid_row = n < a.N;
-      const int label = valid_row ? a.y[n] : 0;  // issued before the waits
+      const bool valid_row = n < m.N;
+      const int label = valid_row ? m.y[n] : 0;  // issued before the waits
       const int tb = local % kTBufs;
       bool ok = wait(&sm->tmem_full[b], use & 1u, 4u);
       ok = ok && wait(&sm->bias_full[tb], (uint32_t)(local / kTBufs) & 1u, 4u);
@@ -437,7 +447,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             const float2 bb = *reinterpret_cast<const float2*>(b1 + j0 + 2 * q);
-            pk[q] = pack_bf16x2(act_f(a.act, fmaf(h[2 * q], sc, bb.x)), act_f(a.act, fmaf(h[2 * q + 1], sc, bb.y)));
+            pk[q] = pack_bf16x2(act_f(m.act, fmaf(h[2 * q], sc, bb.x)), act_f(m.act, fmaf(h[2 * q + 1], sc, bb.y)));
           }
           tmem_st8u(hbase + col_h(s) + (uint32_t)(j0 / 2), pk);
         }
@@ -464,7 +474,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
         const float* b2 = tail + (size_t)s * kTailF + H1;
         float ce = 0.0f;
         if (valid_row) {
-          const int C = a.C;
+          const int C = m.C;
           float zmax = -INFINITY;
           float zy = 0.0f;
 #pragma unroll
@@ -489,10 +499,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
       if (lane == 0) mbar_arrive(&sm->tail_empty[tb]);
       epi_bar<kEpi>();
       const int m128 = mt * 2 + (int)rank;
-      if (et < s_valid && m128 < a.m_tiles) {
+      if (et < s_valid && m128 < m.m_tiles) {
         const int s = et;
         const float v = ((red[s * 4 + 0] + red[s * 4 + 1]) + red[s * 4 + 2]) + red[s * 4 + 3];
-        a.partial[(int64_t)m128 * a.count + s0 + s] = v;
+        m.partial[(int64_t)m128 * m.count + s0 + s] = v;
       }
     }
   }
@@ -513,8 +523,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
 }
 
 template <int H1, int NL, bool F8>
-cudaError_t launch_pair(const TcPlan& plan, const PairArgs& args, cudaStream_t s, bool prepare_only, int* pairs_out) {
-  cudaError_t e = ensure_smem_limit<k_fitness_pair<H1, NL, F8>>(plan.smem_bytes);
+cudaError_t launch_pair(const TcPlan& plan, const PairArgs& args, cudaStream_t s, bool prepare_only, int* pairs_out,
+                        const PairMember* members, int32_t n_members, int32_t group_tiles) {
+  cudaError_t e = ensure_smem_limit<k_fitness_pair<H1, NL, F8, false>>(plan.smem_bytes);
+  if (e != cudaSuccess) return e;
+  e = ensure_smem_limit<k_fitness_pair<H1, NL, F8, true>>(plan.smem_bytes);
   if (e != cudaSuccess) return e;
   if (prepare_only) {
     // pairs that fit at once (one CTA per SM): the persistent grid
@@ -524,7 +537,7 @@ cudaError_t launch_pair(const TcPlan& plan, const PairArgs& args, cudaStream_t s
       cfg.blockDim = dim3(pair_threads(H1));
       cfg.dynamicSmemBytes = plan.smem_bytes;
       int n = 0;
-      if (cudaOccupancyMaxActiveClusters(&n, k_fitness_pair<H1, NL, F8>, &cfg) != cudaSuccess || n < 1) {
+      if (cudaOccupancyMaxActiveClusters(&n, k_fitness_pair<H1, NL, F8, false>, &cfg) != cudaSuccess || n < 1) {
         cudaGetLastError();
         n = plan.num_sms / 2;
       }
@@ -532,26 +545,71 @@ cudaError_t launch_pair(const TcPlan& plan, const PairArgs& args, cudaStream_t s
     }
     return cudaSuccess;
   }
+  if (members) {
+    const int pairs = group_tiles < plan.pairs ? group_tiles : plan.pairs;
+    return launch_pdl(k_fitness_pair<H1, NL, F8, true>, dim3(2 * pairs), dim3(pair_threads(H1)), plan.smem_bytes, s,
+                      plan.tmap_x3, plan.tmap_x, plan.tmap_wk, plan.tmap_w, plan.tmap_w2b, args, members, n_members);
+  }
   const int tiles = args.m_pairs * args.n_tiles;
   const int pairs = tiles < plan.pairs ? tiles : plan.pairs;
-  return launch_pdl(k_fitness_pair<H1, NL, F8>, dim3(2 * pairs), dim3(pair_threads(H1)), plan.smem_bytes, s,
-                    plan.tmap_x3, plan.tmap_x, plan.tmap_wk, plan.tmap_w, plan.tmap_w2b, args);
+  return launch_pdl(k_fitness_pair<H1, NL, F8, false>, dim3(2 * pairs), dim3(pair_threads(H1)), plan.smem_bytes, s,
+                    plan.tmap_x3, plan.tmap_x, plan.tmap_wk, plan.tmap_w, plan.tmap_w2b, args,
+                    static_cast<const PairMember*>(nullptr), 0);
 }
 
 cudaError_t dispatch_pair(const TcPlan& plan, int h1, int nl, const PairArgs& a, cudaStream_t s, bool prep,
-                          int* pairs_out) {
+                          int* pairs_out, const PairMember* members = nullptr, int32_t n_members = 0,
+                          int32_t group_tiles = 0) {
   const int key = h1 * 4 + (nl == 32 ? 2 : 0) + (plan.f8 ? 1 : 0);
+#define MG_PAIR(H, L, F) launch_pair<H, L, F>(plan, a, s, prep, pairs_out, members, n_members, group_tiles)
   switch (key) {
-    case 64 * 4 + 0: return launch_pair<64, 16, false>(plan, a, s, prep, pairs_out);
-    case 64 * 4 + 2: return launch_pair<64, 32, false>(plan, a, s, prep, pairs_out);
-    case 64 * 4 + 1: return launch_pair<64, 16, true>(plan, a, s, prep, pairs_out);
-    case 64 * 4 + 3: return launch_pair<64, 32, true>(plan, a, s, prep, pairs_out);
-    case 128 * 4 + 0: return launch_pair<128, 16, false>(plan, a, s, prep, pairs_out);
-    case 128 * 4 + 2: return launch_pair<128, 32, false>(plan, a, s, prep, pairs_out);
-    case 128 * 4 + 1: return launch_pair<128, 16, true>(plan, a, s, prep, pairs_out);
-    case 128 * 4 + 3: return launch_pair<128, 32, true>(plan, a, s, prep, pairs_out);
+    case 64 * 4 + 0: return MG_PAIR(64, 16, false);
+    case 64 * 4 + 2: return MG_PAIR(64, 32, false);
+    case 64 * 4 + 1: return MG_PAIR(64, 16, true);
+    case 64 * 4 + 3: return MG_PAIR(64, 32, true);
+    case 128 * 4 + 0: return MG_PAIR(128, 16, false);
+    case 128 * 4 + 2: return MG_PAIR(128, 32, false);
+    case 128 * 4 + 1: return MG_PAIR(128, 16, true);
+    case 128 * 4 + 3: return MG_PAIR(128, 32, true);
     default: return cudaErrorInvalidValue;
   }
+#undef MG_PAIR
+}
+
+// The arguments of one launch of `count` rows from `first` (as launch_fitness_tc makes them).
+PairArgs make_args(const TcPlan& plan, const Mlp& mlp, int64_t first, const float* rows, int64_t ld, int32_t count,
+                   float scale, float* partial, uint32_t* status) {
+  PairArgs a = {};
+  const int h1 = mlp.widths[1];
+  const int S = pair_sparks(h1);
+  a.count = count;
+  a.first_spark = (int32_t)first;
+  a.m_pairs = (int32_t)((mlp.N + 2 * kPM - 1) / (2 * kPM));
+  a.m_tiles = (int32_t)((mlp.N + kPM - 1) / kPM);
+  a.n_tiles = (count + S - 1) / S;
+  const int bk = plan.f8 ? 128 : 64;
+  {
+    const int ke = plan.f8 ? 32 : 16;                 // K elements per MMA
+    a.n_full = mlp.widths[0] / bk;
+    const int rem = mlp.widths[0] - a.n_full * bk;   // K elements of the partial last atom
+    a.k_last = (rem + ke - 1) / ke;
+    a.n_steps = (a.n_full + 1) / 2 + (rem > 0 ? 1 : 0);
+  }
+  a.stages = plan.stages;
+  a.C = mlp.widths[2];
+  a.act = mlp.acts[0];
+  a.c_pad = (a.C + 3) / 4 * 4;
+  a.scale = scale;
+  a.N = mlp.N;
+  a.ld = ld;
+  a.b1_off = mlp.b_off[0];
+  a.b2_off = mlp.b_off[1];
+  a.rows = rows;
+  a.y = mlp.y;
+  a.partial = partial;
+  a.status = status;
+  a.wait_budget = plan.wait_budget;
+  return a;
 }
 
 }  // namespace
@@ -585,37 +643,39 @@ int tc_pair_max_stages() { return kMaxStg; }
 
 int launch_fitness_pair(const TcPlan& plan, const Mlp& mlp, int64_t first, const float* rows, int64_t ld,
                         int32_t count, float scale, float* partial, uint32_t* status, cudaStream_t s) {
+  const PairArgs a = make_args(plan, mlp, first, rows, ld, count, scale, partial, status);
+  return dispatch_pair(plan, mlp.widths[1], tc_pair_logit_rows(a.C), a, s, false, nullptr) == cudaSuccess ? 1 : -1;
+}
+
+void tc_pair_member(const TcPlan& plan, const Mlp& mlp, int64_t first, const float* rows, int64_t ld, int32_t count,
+                    float scale, float* partial, uint32_t* status, PairMember* out) {
+  out->x3 = plan.tmap_x3;
+  out->x = plan.tmap_x;
+  out->w3 = plan.tmap_wk;
+  out->w = plan.tmap_w;
+  out->w2 = plan.tmap_w2b;
+  out->a = make_args(plan, mlp, first, rows, ld, count, scale, partial, status);
+  out->tiles = out->a.m_pairs * out->a.n_tiles;
+  out->tile_start = 0;
+}
+
+bool tc_pair_same_instance(const TcPlan& a, const Mlp& ma, const TcPlan& b, const Mlp& mb) {
+  return a.ready && b.ready && a.pair && b.pair && a.f8 == b.f8 && ma.widths[1] == mb.widths[1] &&
+         tc_pair_logit_rows(ma.widths[2]) == tc_pair_logit_rows(mb.widths[2]) && a.smem_bytes == b.smem_bytes &&
+         a.stages == b.stages;
+}
+
+int launch_fitness_pair_group(const TcPlan& plan, const Mlp& mlp, const PairMember* table_dev, int32_t n,
+                              uint32_t* status, cudaStream_t s, int32_t total_tiles) {
+  if (n < 1 || total_tiles < 1) return 0;
   PairArgs a = {};
-  const int h1 = mlp.widths[1];
-  const int S = tc_pair_sparks(h1, mlp.widths[2]);
-  a.count = count;
-  a.first_spark = (int32_t)first;
-  a.m_pairs = (int32_t)((mlp.N + 2 * kPM - 1) / (2 * kPM));
-  a.m_tiles = (int32_t)((mlp.N + kPM - 1) / kPM);
-  a.n_tiles = (count + S - 1) / S;
-  const int bk = plan.f8 ? 128 : 64;
-  {
-    const int ke = plan.f8 ? 32 : 16;                 // K elements per MMA
-    a.n_full = mlp.widths[0] / bk;
-    const int rem = mlp.widths[0] - a.n_full * bk;   // K elements of the partial last atom
-    a.k_last = (rem + ke - 1) / ke;
-    a.n_steps = (a.n_full + 1) / 2 + (rem > 0 ? 1 : 0);
-  }
   a.stages = plan.stages;
-  a.C = mlp.widths[2];
-  a.act = mlp.acts[0];
-  a.c_pad = (a.C + 3) / 4 * 4;
-  a.scale = scale;
-  a.N = mlp.N;
-  a.ld = ld;
-  a.b1_off = mlp.b_off[0];
-  a.b2_off = mlp.b_off[1];
-  a.rows = rows;
-  a.y = mlp.y;
-  a.partial = partial;
   a.status = status;
   a.wait_budget = plan.wait_budget;
-  return dispatch_pair(plan, h1, tc_pair_logit_rows(a.C), a, s, false, nullptr) == cudaSuccess ? 1 : -1;
+  return dispatch_pair(plan, mlp.widths[1], tc_pair_logit_rows(mlp.widths[2]), a, s, false, nullptr, table_dev, n,
+                       total_tiles) == cudaSuccess
+             ? 1
+             : -1;
 }
 
 cudaError_t tc_pair_prepare(TcPlan& plan, const Mlp& mlp) {

@@ -1294,11 +1294,14 @@ struct mgfwa_group {
   std::vector<mgfwa_t*> members;
   cudaStream_t stream = nullptr;          // where the graph runs
   std::vector<cudaStream_t> branch;       // capture branches, one per member
-  std::vector<cudaEvent_t> join;
-  cudaEvent_t fork = nullptr, done = nullptr;
+  std::vector<cudaEvent_t> join, mid_a, mid_b;  // per member: end, after its explosion, after its guide
+  cudaEvent_t fork = nullptr, done = nullptr, fit_e = nullptr, fit_g = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<int> live;                  // members captured in exec
   std::vector<int64_t> kernels;           // kernels per generation of each member
+  int64_t group_kernels = 0;              // grouped fitness launches per generation
+  PairMember* table = nullptr;            // device: the grouped launches' members (explosion, then guiding)
+  int32_t table_cap = 0;
   std::string err;
 };
 
@@ -1308,9 +1311,11 @@ void group_release(mgfwa_group* g) {
   if (g->exec) cudaGraphExecDestroy(g->exec);
   g->exec = nullptr;
   for (cudaStream_t b : g->branch) if (b) cudaStreamDestroy(b);
-  for (cudaEvent_t e : g->join) if (e) cudaEventDestroy(e);
-  if (g->fork) cudaEventDestroy(g->fork);
-  if (g->done) cudaEventDestroy(g->done);
+  for (auto* v : {&g->join, &g->mid_a, &g->mid_b})
+    for (cudaEvent_t e : *v) if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : {g->fork, g->done, g->fit_e, g->fit_g}) if (e) cudaEventDestroy(e);
+  if (g->table) cudaFree(g->table);
+  g->table = nullptr;
   if (g->stream) cudaStreamDestroy(g->stream);
   cudaGetLastError();
 }
@@ -1323,37 +1328,130 @@ mgfwa_status group_fail(mgfwa_group* g, mgfwa_status st, const char* what) {
   return st;
 }
 
-// Capture one generation of every live member as parallel branches of one
-// graph: fork from the group stream, each member's kernels on its branch
-// (the member's stream swapped for the branch while capturing), join.
+// Members whose sparks one grouped launch of the CTA-pair fitness kernel
+// can evaluate with the others': an MLP on the pair kernel, the same kernel
+// instance as the first such member.
+std::vector<int> group_fusable(mgfwa_group* g, const std::vector<int>& live) {
+  std::vector<int> out;
+  const mgfwa_t* first = nullptr;
+  for (int i : live) {
+    const mgfwa_t* h = g->members[(size_t)i];
+    if (h->kind != MGFWA_OBJ_MLP_CE || !use_tc(h, h->cfg.precision) || !h->tc.pair) continue;
+    if (first && !tc_pair_same_instance(first->tc, first->mlp, h->tc, h->mlp)) continue;
+    if (!first) first = h;
+    out.push_back(i);
+  }
+  if (out.size() < 2) out.clear();  // a lone member gains nothing from a grouped launch
+  return out;
+}
+
+// Capture one generation of every live member into one graph.  Each member's
+// kernels run on a branch of their own (the member's stream swapped for the
+// branch while capturing).  Members on the same CTA-pair kernel instance
+// share two grouped fitness launches: every such member's explosion, then one
+// launch for all their explosion sparks, then every member's rank and guide,
+// then one launch for all their guiding sparks, then every member's re-score
+// and selection.  A grouped launch gives each spark bitwise the fitness of
+// the member's own launch (a tile owns whole sparks and writes the member's
+// partial sums in its own layout).  Other members run their whole generation
+// on their branch.
 mgfwa_status group_capture(mgfwa_group* g, const std::vector<int>& live) {
   if (g->exec) cudaGraphExecDestroy(g->exec);
   g->exec = nullptr;
   g->live.clear();
+  const std::vector<int> fused = group_fusable(g, live);
+  std::vector<char> is_fused(g->members.size(), 0);
+  for (int i : fused) is_fused[(size_t)i] = 1;
+  // the grouped launches' member tables (fixed for the graph's life), written before the capture
+  const int32_t nf = (int32_t)fused.size();
+  int32_t tiles_e = 0, tiles_g = 0;
+  if (nf > 0) {
+    std::vector<PairMember> tab((size_t)(2 * nf));
+    for (int32_t k = 0; k < nf; ++k) {
+      mgfwa_t* h = g->members[(size_t)fused[(size_t)k]];
+      const Problem& p = h->p;
+      const int64_t n_e = (int64_t)p.B * p.mu * p.lam, n_g = (int64_t)p.B * p.mu * p.m;
+      tc_pair_member(h->tc, h->mlp, 0, h->sparks, p.Dp, (int32_t)n_e, h->op_scale, h->partial, h->status,
+                     &tab[(size_t)k]);
+      tc_pair_member(h->tc, h->mlp, n_e, h->sparks + n_e * p.Dp, p.Dp, (int32_t)n_g, h->op_scale, h->partial,
+                     h->status, &tab[(size_t)(nf + k)]);
+      tab[(size_t)k].tile_start = tiles_e;
+      tiles_e += tab[(size_t)k].tiles;
+      tab[(size_t)(nf + k)].tile_start = tiles_g;
+      tiles_g += tab[(size_t)(nf + k)].tiles;
+    }
+    if (g->table_cap < 2 * nf) {
+      if (g->table) cudaFree(g->table);
+      g->table = nullptr;
+      g->table_cap = 0;
+      if (cudaMalloc(&g->table, sizeof(PairMember) * (size_t)(2 * nf)) != cudaSuccess)
+        return group_fail(g, MGFWA_ENOMEM, "group: grouped launch table");
+      g->table_cap = 2 * nf;
+    }
+    if (cudaMemcpy(g->table, tab.data(), sizeof(PairMember) * tab.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return group_fail(g, MGFWA_ECUDA, "group: grouped launch table copy");
+  }
   if (cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
     return group_fail(g, MGFWA_ECUDA, "group: begin capture");
   mgfwa_status st = MGFWA_OK;
   bool ok = cudaEventRecord(g->fork, g->stream) == cudaSuccess;
-  for (int i : live) {
-    if (!ok) break;
+  // phases [p0, p1] of member i on its branch after event `wait`, skipping its own fitness launches when it is
+  // fused; the branch then records `end`, which the group stream waits on
+  auto member_phases = [&](int i, int32_t p0, int32_t p1, cudaEvent_t wait, cudaEvent_t end) -> bool {
     mgfwa_t* h = g->members[(size_t)i];
-    ok = cudaStreamWaitEvent(g->branch[(size_t)i], g->fork, 0) == cudaSuccess;
-    if (!ok) break;
+    cudaStream_t br = g->branch[(size_t)i];
+    if (cudaStreamWaitEvent(br, wait, 0) != cudaSuccess) return false;
     cudaStream_t own = h->stream;
-    h->stream = g->branch[(size_t)i];
+    h->stream = br;
     h->capturing = true;
     const int64_t before = h->launches;
-    for (int32_t ph = MGFWA_PHASE_EXPLODE; ph <= MGFWA_PHASE_SELECT && st == MGFWA_OK; ++ph) st = run_phase(h, ph);
-    g->kernels[(size_t)i] = h->launches - before;
+    for (int32_t ph = p0; ph <= p1 && st == MGFWA_OK; ++ph) {
+      if (is_fused[(size_t)i] && (ph == MGFWA_PHASE_EVAL_E || ph == MGFWA_PHASE_EVAL_G)) continue;
+      st = run_phase(h, ph);
+      if (st == MGFWA_OK && is_fused[(size_t)i] && ph == MGFWA_PHASE_RESCORE && !finish_in_pick(h)) {
+        // the grouped guiding launch left the partial sums, and this member's pick does not finish them
+        const Problem& p = h->p;
+        const int64_t n_e = (int64_t)p.B * p.mu * p.lam;
+        if (launch_fitness_finish(h->partial, h->mtiles, p.B * p.mu * p.m, h->mlp.N, h->fit + n_e, br) < 0)
+          st = cuda_fail(h, "group: guiding fitness means");
+        else
+          h->launches += 1;
+      }
+    }
+    g->kernels[(size_t)i] += h->launches - before;
     h->launches = before;
     h->capturing = false;
     h->stream = own;
-    if (st != MGFWA_OK) {
-      ok = false;
-      break;
+    if (st != MGFWA_OK) return false;
+    return cudaEventRecord(end, br) == cudaSuccess && cudaStreamWaitEvent(g->stream, end, 0) == cudaSuccess;
+  };
+  for (int i : live) g->kernels[(size_t)i] = 0;
+  g->group_kernels = 0;
+  // stage 1: every member's explosion (and the whole generation of a member that is not fused)
+  for (int i : live) {
+    if (!ok) break;
+    ok = is_fused[(size_t)i] ? member_phases(i, MGFWA_PHASE_EXPLODE, MGFWA_PHASE_EXPLODE, g->fork, g->mid_a[(size_t)i])
+                             : member_phases(i, MGFWA_PHASE_EXPLODE, MGFWA_PHASE_SELECT, g->fork, g->join[(size_t)i]);
+  }
+  if (ok && nf > 0) {
+    const mgfwa_t* h0 = g->members[(size_t)fused[0]];
+    // stage 2: one launch for all fused members' explosion sparks, then each member's rank and guide
+    ok = launch_fitness_pair_group(h0->tc, h0->mlp, g->table, nf, h0->status, g->stream, tiles_e) == 1 &&
+         cudaEventRecord(g->fit_e, g->stream) == cudaSuccess;
+    g->group_kernels += 1;
+    for (int i : fused) {
+      if (!ok) break;
+      ok = member_phases(i, MGFWA_PHASE_EVAL_E, MGFWA_PHASE_EVAL_G, g->fit_e, g->mid_b[(size_t)i]);
     }
-    ok = cudaEventRecord(g->join[(size_t)i], g->branch[(size_t)i]) == cudaSuccess &&
-         cudaStreamWaitEvent(g->stream, g->join[(size_t)i], 0) == cudaSuccess;
+    // stage 3: one launch for all fused members' guiding sparks, then each member's re-score and selection
+    if (ok)
+      ok = launch_fitness_pair_group(h0->tc, h0->mlp, g->table + nf, nf, h0->status, g->stream, tiles_g) == 1 &&
+           cudaEventRecord(g->fit_g, g->stream) == cudaSuccess;
+    g->group_kernels += 1;
+    for (int i : fused) {
+      if (!ok) break;
+      ok = member_phases(i, MGFWA_PHASE_RESCORE, MGFWA_PHASE_SELECT, g->fit_g, g->join[(size_t)i]);
+    }
   }
   cudaGraph_t graph = nullptr;
   const bool ended = cudaStreamEndCapture(g->stream, &graph) == cudaSuccess;
@@ -1400,13 +1498,19 @@ mgfwa_status mgfwa_group_create(mgfwa_t* const* handles, int32_t count, mgfwa_gr
   g->members.assign(handles, handles + count);
   g->branch.assign((size_t)count, nullptr);
   g->join.assign((size_t)count, nullptr);
+  g->mid_a.assign((size_t)count, nullptr);
+  g->mid_b.assign((size_t)count, nullptr);
   g->kernels.assign((size_t)count, 0);
   bool ok = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) == cudaSuccess &&
             cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming) == cudaSuccess &&
-            cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming) == cudaSuccess;
+            cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&g->fit_e, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&g->fit_g, cudaEventDisableTiming) == cudaSuccess;
   for (int32_t i = 0; i < count && ok; ++i)
     ok = cudaStreamCreateWithFlags(&g->branch[(size_t)i], cudaStreamNonBlocking) == cudaSuccess &&
-         cudaEventCreateWithFlags(&g->join[(size_t)i], cudaEventDisableTiming) == cudaSuccess;
+         cudaEventCreateWithFlags(&g->join[(size_t)i], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&g->mid_a[(size_t)i], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&g->mid_b[(size_t)i], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     group_fail(g, MGFWA_ECUDA, "group: streams and events");
     group_release(g);

@@ -35,6 +35,13 @@ def _specs(pkg):
         (W.scaled(big, eval_budget=W.budget_for_generations(3, 20, 4, 4)), 16, pkg.MGFWA_FP8, {"elite_rescore": 0}),
         (W.scaled(W.table2_net(6), sparks_per_firework=40, guiding_per_firework=4,
                   eval_budget=W.budget_for_generations(5, 40, 4, 7)), 17, pkg.MGFWA_FP32, {}),
+        # more members on the CTA-pair kernel, so that the group's grouped fitness launches cover several
+        # handles: two runs without the re-score (the group finishes their guiding means), and d_in = 96
+        # (a partial last K atom) with another batch size
+        (W.scaled(big, n_samples=200, eval_budget=W.budget_for_generations(3, 20, 4, 5)), 18, pkg.MGFWA_BF16,
+         {"n_runs": 2, "elite_rescore": 0}),
+        (W.scaled(big, widths=(96, 64, 10), n_samples=700, eval_budget=W.budget_for_generations(3, 20, 4, 7)), 19,
+         pkg.MGFWA_BF16, {}),
     ]
 
 
