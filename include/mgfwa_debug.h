@@ -96,6 +96,25 @@ MGFWA_API mgfwa_status mgfwa_debug_kernel_times(mgfwa_t* h, double* ms_out, int6
  * detection tests use it; nothing faults and no arrival is withheld.
  * Errors: EINVAL (null handle). */
 MGFWA_API mgfwa_status mgfwa_debug_wait_budget(mgfwa_t* h, uint64_t ticks);
+/* The CTA-pair fitness kernel's tile of a BF16 or FP8 handle (Sec. 3.3's
+ * fitness of many sparks at once as one contraction): *sparks_per_tile
+ * sparks per 256-sample tile -- 256/h1 when each spark's logits go into its
+ * own accumulator columns once its activations are packed, 256/(h1 + 16 or
+ * 32 logit rows) when the logits have columns of their own -- and *stages
+ * shared-memory pipeline stages; *tuned is 1 where mgfwa_create chose the
+ * two by timing every shape and depth that fits (once per device and
+ * problem shape in the process), 0 where they were set.  All three are -1
+ * for a handle not on the pair kernel.  Any pointer may be NULL.
+ * Errors: EINVAL (null handle). */
+MGFWA_API mgfwa_status mgfwa_debug_pair_tile(const mgfwa_t* h, int32_t* sparks_per_tile, int32_t* stages,
+                                             int32_t* tuned);
+/* Set the pair kernel's tile for the generations that follow (the
+ * handle's generation graph is captured again).  Every shape and depth
+ * gives every spark bitwise the same fitness.  Synchronises the handle's
+ * stream.  Errors: EINVAL (null handle, not on the pair kernel, a tile the
+ * kernel has not got for this network, a depth outside 2 .. the deepest
+ * that fits), ECUDA. */
+MGFWA_API mgfwa_status mgfwa_debug_set_pair_tile(mgfwa_t* h, int32_t sparks_per_tile, int32_t stages);
 
 #ifdef __cplusplus
 }

@@ -41,7 +41,8 @@ EXPORTS = ("mgfwa_config_init", "mgfwa_create", "mgfwa_step", "mgfwa_run", "mgfw
            "mgfwa_server_stats_get", "mgfwa_server_now", "mgfwa_server_destroy", "mgfwa_group_create",
            "mgfwa_group_step", "mgfwa_group_destroy", "mgfwa_checkpoint_size", "mgfwa_checkpoint_save",
            "mgfwa_checkpoint_load", "mgfwa_shard_key", "mgfwa_reduce_best_keys", "mgfwa_set_reduce_best",
-           "mgfwa_global_best_key", "mgfwa_debug_wait_budget")
+           "mgfwa_global_best_key", "mgfwa_debug_wait_budget", "mgfwa_debug_pair_tile",
+           "mgfwa_debug_set_pair_tile")
 MGFWA_REQ_QUEUED, MGFWA_REQ_RUNNING, MGFWA_REQ_DONE, MGFWA_REQ_FAILED = range(4)
 N_KERNEL_GROUPS = 9
 KERNEL_GROUPS = ("explode", "fitness_explosion", "fitness_finish", "rank", "guide", "fitness_guiding", "select",
@@ -136,6 +137,8 @@ def load_library(path: Optional[str] = None):
     L.mgfwa_evaluate_fp32_noalloc.argtypes = [i32, i32p, i32p, i64, vp, vp, vp, i64, i32, vp, vp]
     L.mgfwa_shard_key.argtypes = [vp, i32, ctypes.POINTER(mgfwa_best_key)]
     L.mgfwa_debug_wait_budget.argtypes = [vp, ctypes.c_uint64]
+    L.mgfwa_debug_pair_tile.argtypes = [vp, i32p, i32p, i32p]
+    L.mgfwa_debug_set_pair_tile.argtypes = [vp, i32, i32]
     L.mgfwa_reduce_best_keys.argtypes = [ctypes.POINTER(mgfwa_best_key), i32, ctypes.POINTER(mgfwa_best_key)]
     L.mgfwa_set_reduce_best.argtypes = [vp, REDUCE_BEST_FN, vp]
     L.mgfwa_global_best_key.argtypes = [vp, i32, ctypes.POINTER(mgfwa_best_key)]
@@ -378,6 +381,16 @@ class Mgfwa:
     def wait_budget(self, ticks: int) -> None:
         """Budget (SM clock ticks) of the tensor-core kernels' bounded waits; 0 restores the default."""
         _check(load_library().mgfwa_debug_wait_budget(self.handle, ticks), self.handle)
+
+    def pair_tile(self) -> tuple:
+        """(sparks per tile, stages, tuned) of the CTA-pair fitness kernel; all -1 off that kernel."""
+        v = [ctypes.c_int32() for _ in range(3)]
+        _check(load_library().mgfwa_debug_pair_tile(self.handle, *[ctypes.byref(x) for x in v]), self.handle)
+        return tuple(x.value for x in v)
+
+    def set_pair_tile(self, sparks_per_tile: int, stages: int) -> None:
+        """Run the following generations with this tile of the CTA-pair fitness kernel."""
+        _check(load_library().mgfwa_debug_set_pair_tile(self.handle, sparks_per_tile, stages), self.handle)
 
     def shard_key(self, run: int = 0) -> mgfwa_best_key:
         key = mgfwa_best_key()

@@ -26,6 +26,9 @@ struct TcPlan {
   int n_tile = 0;           // accumulator columns per tile (sparks_per_tile * h1)
   int stages = 0;           // shared-memory pipeline depth
   size_t smem_bytes = 0;
+  int tuned = 0;            // pair kernel: 1 if the tile shape and depth were chosen by timing
+  const void* w_base = nullptr;  // pair kernel: the first-layer operand and its rows (for re-encoding W1's maps)
+  int64_t w_rows = 0;
 };
 
 // True if the tensor-core path handles this network: d_in % 8 == 0 and
@@ -84,8 +87,9 @@ struct PairArgs {
 };
 
 // One member of a grouped launch: its tensor maps and arguments, in device
-// memory, and where its tiles start among the launch's.
-struct alignas(64) PairMember {
+// memory, and where its tiles start among the launch's (aligned as the
+// tensor maps require, which the array's allocation honours).
+struct PairMember {
   CUtensorMap x3, x, w3, w, w2;
   PairArgs a;
   int32_t tile_start, tiles;
@@ -106,11 +110,28 @@ int launch_fitness_pair_group(const TcPlan& plan, const Mlp& mlp, const PairMemb
                               uint32_t* status, cudaStream_t s, int32_t total_tiles);
 
 // The CTA-pair kernel's pieces (k_fitness_pair.cu), used by tc_plan and
-// launch_fitness_tc.
-int tc_pair_sparks(int h1, int C);  // sparks per tile: floor(256 / (h1 + logit rows))
-size_t tc_pair_fixed_smem(int h1, int C);
-size_t tc_pair_stage_bytes(int h1, int C);
+// launch_fitness_tc.  Sparks per tile: 256 / h1 when the logits share the
+// sparks' columns, else 256 / (h1 + logit rows).
+int tc_pair_sparks(int h1, int C, bool shared);
+size_t tc_pair_fixed_smem(int h1, int C, int sparks_per_tile);
+size_t tc_pair_stage_bytes(int h1, int sparks_per_tile);
 int tc_pair_max_stages();
+// Deepest pipeline of the tile shape that fits the device's shared memory
+// (`limit` bytes per block), or 0 if not even two stages fit.
+int tc_pair_stages_fit(int h1, int C, int sparks_per_tile, size_t limit);
+
+// Set a pair plan's tile shape and pipeline depth (re-encoding the W1 maps,
+// whose box is half a tile's rows) and its kernel's attributes; MGFWA_EINVAL
+// for a shape the kernel does not have or a depth that does not fit.  Every
+// shape and depth gives every spark bitwise the same fitness.
+mgfwa_status tc_pair_configure(TcPlan& plan, const Mlp& mlp, int sparks_per_tile, int stages);
+// Time every tile shape and depth on `count` rows of the planned buffers
+// (as launch_fitness_tc would run them, on stream s; `partial` is
+// overwritten) and keep the fastest.  Choices are cached per device and
+// problem shape for the process, so a second handle of the same shape
+// times nothing.  Skipped (the plan's default stays) while s is capturing.
+mgfwa_status tc_pair_tune(TcPlan& plan, const Mlp& mlp, const float* rows, int64_t ld, int32_t count, float scale,
+                          float* partial, uint32_t* status, cudaStream_t s);
 cudaError_t tc_pair_prepare(TcPlan& plan, const Mlp& mlp);
 int launch_fitness_pair(const TcPlan& plan, const Mlp& mlp, int64_t first, const float* rows, int64_t ld,
                         int32_t count, float scale, float* partial, uint32_t* status, cudaStream_t s);

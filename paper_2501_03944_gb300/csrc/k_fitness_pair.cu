@@ -72,15 +72,24 @@ constexpr int kMaxStg = 8;
 constexpr int kTBufs = 3;    // tail buffers: the producer runs ahead of layer 2
 constexpr int kCols = 512;   // two halves of 256 columns
 
-// Tile shape: S = 256 / h1 sparks fill a TMEM half of 256 columns with
-// their layer-1 accumulators (N = S * h1 = 256).  Each spark's logits then
-// go into the second half of its own columns, freed once the activations
-// are packed as BF16 pairs into the first half; so the next layer 1 into the
-// same TMEM half waits for both epilogues to have read the logits.
-__host__ __device__ constexpr int pair_sparks(int h1) { return 256 / h1; }
+// Tile shapes (S sparks of h1 hidden units, N = S * h1 accumulator columns
+// of a TMEM half of 256):
+//  * "shared" S = 256 / h1 (N = 256): each spark's logits go into the second
+//    half of its own columns, freed once its activations are packed as BF16
+//    pairs into the first half, so the next layer 1 into the same TMEM half
+//    waits for both epilogues to have read the logits;
+//  * "separate" S = 256 / (h1 + nl): the logits have columns of their own
+//    after the accumulators, so the next layer 1 waits only for layer 2 to
+//    have read the activations, and layer 2 for the epilogues to have read
+//    the logits of the tile before.
+// Both give every spark bitwise the same fitness (its columns are its own
+// sums in the same order); which is faster depends on the shape, and the
+// plan's tuner times both.
+__host__ __device__ constexpr int pair_sparks_shared(int h1) { return 256 / h1; }
+__host__ __device__ constexpr int pair_sparks_separate(int h1, int nl) { return 256 / (h1 + nl); }
 // Epilogue warps: one per spark and TMEM lane quadrant, at least two per quadrant.
-__host__ __device__ constexpr int pair_groups(int h1) { return pair_sparks(h1) < 2 ? 2 : pair_sparks(h1); }
-__host__ __device__ constexpr int pair_threads(int h1) { return 64 + 128 * pair_groups(h1); }
+__host__ __device__ constexpr int pair_groups(int S) { return S < 2 ? 2 : S; }
+__host__ __device__ constexpr int pair_threads(int S) { return 64 + 128 * pair_groups(S); }
 
 struct PairSmem {
   uint64_t full[kMaxStg];      // even CTA: both CTAs' loads of the stage landed
@@ -88,7 +97,9 @@ struct PairSmem {
   uint64_t tmem_full[2];       // layer 1 of the half's tile is complete
   uint64_t a2_full[2];         // even CTA: both CTAs wrote the half's activations
   uint64_t l2_full[2];         // layer 2 of the half's tile is complete (its logits)
-  uint64_t tmem_empty[2];      // even CTA: both CTAs read the half's logits (the half is free)
+  uint64_t tmem_empty[2];      // even CTA: the half is free for the next layer 1 (shared: both CTAs read its
+                               // logits; separate: layer 2 read its activations)
+  uint64_t l2_empty[2];        // even CTA, separate logits: both CTAs read the half's logits
   uint64_t bias_full[kTBufs];  // this CTA's biases of the buffer's tile landed
   uint64_t w2_full[kTBufs];    // even CTA: both CTAs' W2 halves of the buffer's tile landed
   uint64_t tail_empty[kTBufs]; // layer 2 read the W2 halves, this CTA's epilogue the biases
@@ -130,18 +141,18 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 // the members' tensor maps and arguments).  Otherwise the kernel parameters
 // hold the one launch's maps and `a` its arguments.  `a` also carries what
 // every member shares: stages, the status word and the wait budget.
-template <int H1, int NL, bool F8, bool kGroup>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
+template <int H1, int NL, int S, bool F8, bool kGroup>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
     k_fitness_pair(const __grid_constant__ CUtensorMap tmap_x3, const __grid_constant__ CUtensorMap tmap_x,
                    const __grid_constant__ CUtensorMap tmap_w3, const __grid_constant__ CUtensorMap tmap_w,
                    const __grid_constant__ CUtensorMap tmap_w2, PairArgs a, const PairMember* __restrict__ members,
                    int32_t n_members) {
   griddep_wait();
   griddep_launch_dependents();
-  constexpr int S = pair_sparks(H1);             // sparks per tile
-  constexpr int kNT = S * H1;                    // layer-1 accumulator columns per tile (256)
+  constexpr int kNT = S * H1;                    // layer-1 accumulator columns per tile
+  constexpr bool kShared = S * (H1 + NL) > 256;  // the logits share the spark's accumulator columns
   constexpr int kBK = F8 ? 128 : 64;             // K elements per atom (one 128-byte row)
-  constexpr int kGroups = pair_groups(H1);       // epilogue warps per TMEM lane quadrant
+  constexpr int kGroups = pair_groups(S);        // epilogue warps per TMEM lane quadrant
   constexpr int kEpi = 4 * kGroups;
   constexpr int kHalfNL = NL / 2;                // W2 rows (logits) each CTA holds
   constexpr int kW2Atoms = H1 / 64;              // 128-byte K atoms of a BF16 W2 row
@@ -153,7 +164,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
   constexpr uint32_t kStageA = 2 * kAtomA;       // a stage: two atoms of each operand
   constexpr uint32_t kStageB = 2 * kAtomB;
   static_assert(kHalfNL % 8 == 0, "each W2 half is whole 8-row swizzle groups");
-  static_assert(S >= 1 && kNT == 256 && NL <= H1 / 2, "a spark's logits fit beside its packed activations");
+  static_assert(S >= 1 && kNT <= 256 && (!kShared || NL <= H1 / 2), "a tile's columns fit in a TMEM half");
   static_assert((kNT / 2) % 8 == 0 && kNT % 16 == 0, "a W1 half is whole 8-row groups; N is a multiple of 16");
 
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -167,7 +178,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
 
   // TMEM columns of spark s within a half: its accumulator / packed activations, its logits
   auto col_h = [](int sp) { return (uint32_t)(sp * H1); };
-  auto col_lg = [](int sp) { return (uint32_t)(sp * H1 + H1 / 2); };
+  auto col_lg = [](int sp) { return kShared ? (uint32_t)(sp * H1 + H1 / 2) : (uint32_t)(S * H1 + sp * NL); };
   const uint32_t rank = cluster_rank();
   const bool lead = rank == 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -175,9 +186,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
   const int tiles = kGroup ? members[n_members - 1].tile_start + members[n_members - 1].tiles : a.m_pairs * a.n_tiles;
   // the member of tile t (advancing `cur`) and t's index among that member's tiles
   auto member_at = [&](int t, int& cur) -> int {
-    if (!kGroup) return t;
-    while (cur + 1 < n_members && t >= members[cur + 1].tile_start) ++cur;
-    return t - members[cur].tile_start;
+    if constexpr (kGroup) {
+      while (cur + 1 < n_members && t >= members[cur + 1].tile_start) ++cur;
+      return t - members[cur].tile_start;
+    } else {
+      (void)cur;
+      return t;
+    }
   };
   auto args_of = [&](int cur) -> const PairArgs& { return kGroup ? members[cur].a : a; };
 
@@ -190,7 +205,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
       mbar_init(&sm->tmem_full[b], 1);
       mbar_init(&sm->a2_full[b], 2 * kEpi);
       mbar_init(&sm->l2_full[b], 1);
-      mbar_init(&sm->tmem_empty[b], 2 * kEpi);
+      mbar_init(&sm->tmem_empty[b], kShared ? 2 * kEpi : 1);
+      mbar_init(&sm->l2_empty[b], 2 * kEpi);
     }
     for (int b = 0; b < kTBufs; ++b) {
       mbar_init(&sm->bias_full[b], 1);
@@ -316,7 +332,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
       auto l2_ready = [&](int j) -> bool {
         const int tbj = j % kTBufs;
         const uint32_t tu = (uint32_t)(j / kTBufs) & 1u;
-        return mbar_test_wait(&sm->a2_full[j & 1], (uint32_t)(j >> 1) & 1u) && mbar_test_wait(&sm->w2_full[tbj], tu);
+        return mbar_test_wait(&sm->a2_full[j & 1], (uint32_t)(j >> 1) & 1u) && mbar_test_wait(&sm->w2_full[tbj], tu) &&
+               (kShared || mbar_test_wait(&sm->l2_empty[j & 1], ((uint32_t)(j >> 1) & 1u) ^ 1u));
       };
       auto layer2 = [&](int j, int s_valid) -> bool {
         const int bj = j & 1;
@@ -324,6 +341,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
         const uint32_t tu = (uint32_t)(j / kTBufs) & 1u;
         if (!wait(&sm->a2_full[bj], (uint32_t)(j >> 1) & 1u, 2u)) return false;
         if (!wait(&sm->w2_full[tbj], tu, 2u)) return false;
+        if (!kShared && !wait(&sm->l2_empty[bj], ((uint32_t)(j >> 1) & 1u) ^ 1u, 2u)) return false;
         tc_fence_after();
         const uint32_t half = tmem_base + (uint32_t)(bj * 256);
         for (int s = 0; s < s_valid; ++s) {
@@ -336,6 +354,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
           }
         }
         commit_both(&sm->l2_full[bj]);
+        if (!kShared) mma2_commit(map_to(&sm->tmem_empty[bj], 0u));
         commit_both(&sm->tail_empty[tbj]);
         return true;
       };
@@ -468,7 +487,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
       tmem_wait_ld();
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive_cluster(map_to(&sm->tmem_empty[b], 0u));
+      if (lane == 0) mbar_arrive_cluster(map_to(kShared ? &sm->tmem_empty[b] : &sm->l2_empty[b], 0u));
       if (grp < s_valid) {
         const int s = grp;
         const float* b2 = tail + (size_t)s * kTailF + H1;
@@ -522,22 +541,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(H1), 1)
   }
 }
 
-template <int H1, int NL, bool F8>
+template <int H1, int NL, int S, bool F8>
 cudaError_t launch_pair(const TcPlan& plan, const PairArgs& args, cudaStream_t s, bool prepare_only, int* pairs_out,
                         const PairMember* members, int32_t n_members, int32_t group_tiles) {
-  cudaError_t e = ensure_smem_limit<k_fitness_pair<H1, NL, F8, false>>(plan.smem_bytes);
+  cudaError_t e = ensure_smem_limit<k_fitness_pair<H1, NL, S, F8, false>>(plan.smem_bytes);
   if (e != cudaSuccess) return e;
-  e = ensure_smem_limit<k_fitness_pair<H1, NL, F8, true>>(plan.smem_bytes);
+  e = ensure_smem_limit<k_fitness_pair<H1, NL, S, F8, true>>(plan.smem_bytes);
   if (e != cudaSuccess) return e;
   if (prepare_only) {
     // pairs that fit at once (one CTA per SM): the persistent grid
     if (pairs_out) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(2 * (plan.num_sms / 2));
-      cfg.blockDim = dim3(pair_threads(H1));
+      cfg.blockDim = dim3(pair_threads(S));
       cfg.dynamicSmemBytes = plan.smem_bytes;
       int n = 0;
-      if (cudaOccupancyMaxActiveClusters(&n, k_fitness_pair<H1, NL, F8, false>, &cfg) != cudaSuccess || n < 1) {
+      if (cudaOccupancyMaxActiveClusters(&n, k_fitness_pair<H1, NL, S, F8, false>, &cfg) != cudaSuccess || n < 1) {
         cudaGetLastError();
         n = plan.num_sms / 2;
       }
@@ -547,32 +566,41 @@ cudaError_t launch_pair(const TcPlan& plan, const PairArgs& args, cudaStream_t s
   }
   if (members) {
     const int pairs = group_tiles < plan.pairs ? group_tiles : plan.pairs;
-    return launch_pdl(k_fitness_pair<H1, NL, F8, true>, dim3(2 * pairs), dim3(pair_threads(H1)), plan.smem_bytes, s,
-                      plan.tmap_x3, plan.tmap_x, plan.tmap_wk, plan.tmap_w, plan.tmap_w2b, args, members, n_members);
+    return launch_pdl(k_fitness_pair<H1, NL, S, F8, true>, dim3(2 * pairs), dim3(pair_threads(S)), plan.smem_bytes,
+                      s, plan.tmap_x3, plan.tmap_x, plan.tmap_wk, plan.tmap_w, plan.tmap_w2b, args, members,
+                      n_members);
   }
   const int tiles = args.m_pairs * args.n_tiles;
   const int pairs = tiles < plan.pairs ? tiles : plan.pairs;
-  return launch_pdl(k_fitness_pair<H1, NL, F8, false>, dim3(2 * pairs), dim3(pair_threads(H1)), plan.smem_bytes, s,
+  return launch_pdl(k_fitness_pair<H1, NL, S, F8, false>, dim3(2 * pairs), dim3(pair_threads(S)), plan.smem_bytes, s,
                     plan.tmap_x3, plan.tmap_x, plan.tmap_wk, plan.tmap_w, plan.tmap_w2b, args,
                     static_cast<const PairMember*>(nullptr), 0);
 }
 
+// The kernel instance of the plan: h1, the logit rows, the tile shape (shared or separate logits) and the
+// operand type.
 cudaError_t dispatch_pair(const TcPlan& plan, int h1, int nl, const PairArgs& a, cudaStream_t s, bool prep,
                           int* pairs_out, const PairMember* members = nullptr, int32_t n_members = 0,
                           int32_t group_tiles = 0) {
-  const int key = h1 * 4 + (nl == 32 ? 2 : 0) + (plan.f8 ? 1 : 0);
-#define MG_PAIR(H, L, F) launch_pair<H, L, F>(plan, a, s, prep, pairs_out, members, n_members, group_tiles)
+  const bool shared = plan.sparks_per_tile == pair_sparks_shared(h1);
+  if (!shared && plan.sparks_per_tile != pair_sparks_separate(h1, nl)) return cudaErrorInvalidValue;
+  const int key = h1 * 8 + (nl == 32 ? 4 : 0) + (shared ? 2 : 0) + (plan.f8 ? 1 : 0);
+#define MG_PAIR(H, L, SH, F)                                                                                      \
+  launch_pair<H, L, SH ? pair_sparks_shared(H) : pair_sparks_separate(H, L), F>(plan, a, s, prep, pairs_out, members, \
+                                                                                 n_members, group_tiles)
+#define MG_PAIR_CASES(H, L, NLK)                                   \
+  case H * 8 + NLK + 0: return MG_PAIR(H, L, false, false);        \
+  case H * 8 + NLK + 1: return MG_PAIR(H, L, false, true);         \
+  case H * 8 + NLK + 2: return MG_PAIR(H, L, true, false);         \
+  case H * 8 + NLK + 3: return MG_PAIR(H, L, true, true);
   switch (key) {
-    case 64 * 4 + 0: return MG_PAIR(64, 16, false);
-    case 64 * 4 + 2: return MG_PAIR(64, 32, false);
-    case 64 * 4 + 1: return MG_PAIR(64, 16, true);
-    case 64 * 4 + 3: return MG_PAIR(64, 32, true);
-    case 128 * 4 + 0: return MG_PAIR(128, 16, false);
-    case 128 * 4 + 2: return MG_PAIR(128, 32, false);
-    case 128 * 4 + 1: return MG_PAIR(128, 16, true);
-    case 128 * 4 + 3: return MG_PAIR(128, 32, true);
+    MG_PAIR_CASES(64, 16, 0)
+    MG_PAIR_CASES(64, 32, 4)
+    MG_PAIR_CASES(128, 16, 0)
+    MG_PAIR_CASES(128, 32, 4)
     default: return cudaErrorInvalidValue;
   }
+#undef MG_PAIR_CASES
 #undef MG_PAIR
 }
 
@@ -580,8 +608,7 @@ cudaError_t dispatch_pair(const TcPlan& plan, int h1, int nl, const PairArgs& a,
 PairArgs make_args(const TcPlan& plan, const Mlp& mlp, int64_t first, const float* rows, int64_t ld, int32_t count,
                    float scale, float* partial, uint32_t* status) {
   PairArgs a = {};
-  const int h1 = mlp.widths[1];
-  const int S = pair_sparks(h1);
+  const int S = plan.sparks_per_tile;
   a.count = count;
   a.first_spark = (int32_t)first;
   a.m_pairs = (int32_t)((mlp.N + 2 * kPM - 1) / (2 * kPM));
@@ -621,25 +648,27 @@ bool tc_pair_supported(const int32_t* widths, int n_layers) {
 
 int tc_pair_logit_rows(int C) { return C <= 16 ? 16 : 32; }
 
-int tc_pair_sparks(int h1, int C) {
-  (void)C;
-  return pair_sparks(h1);
+int tc_pair_sparks(int h1, int C, bool shared) {
+  return shared ? pair_sparks_shared(h1) : pair_sparks_separate(h1, tc_pair_logit_rows(C));
 }
 
-size_t tc_pair_fixed_smem(int h1, int C) {
-  const int nl = tc_pair_logit_rows(C), S = pair_sparks(h1);
+size_t tc_pair_fixed_smem(int h1, int C, int S) {
+  const int nl = tc_pair_logit_rows(C);
   const size_t w2 = (size_t)kTBufs * S * (h1 / 64) * (nl / 2) * 128;
   const size_t tails = sizeof(float) * ((size_t)kTBufs * S * (h1 + 32) + 4 * (size_t)S);
   return 1024 + w2 + tails + 16 + sizeof(PairSmem) + 64;
 }
 
-size_t tc_pair_stage_bytes(int h1, int C) {
-  (void)h1;
-  (void)C;
-  return 2 * ((size_t)kPM * kRowB + (size_t)(256 / 2) * kRowB);
-}
+size_t tc_pair_stage_bytes(int h1, int S) { return 2 * ((size_t)kPM * kRowB + (size_t)(S * h1 / 2) * kRowB); }
 
 int tc_pair_max_stages() { return kMaxStg; }
+
+int tc_pair_stages_fit(int h1, int C, int S, size_t limit) {
+  const size_t fixed = tc_pair_fixed_smem(h1, C, S), stage = tc_pair_stage_bytes(h1, S);
+  int st = kMaxStg;
+  while (st >= 2 && fixed + (size_t)st * stage > limit) --st;
+  return st >= 2 ? st : 0;
+}
 
 int launch_fitness_pair(const TcPlan& plan, const Mlp& mlp, int64_t first, const float* rows, int64_t ld,
                         int32_t count, float scale, float* partial, uint32_t* status, cudaStream_t s) {
@@ -661,8 +690,8 @@ void tc_pair_member(const TcPlan& plan, const Mlp& mlp, int64_t first, const flo
 
 bool tc_pair_same_instance(const TcPlan& a, const Mlp& ma, const TcPlan& b, const Mlp& mb) {
   return a.ready && b.ready && a.pair && b.pair && a.f8 == b.f8 && ma.widths[1] == mb.widths[1] &&
-         tc_pair_logit_rows(ma.widths[2]) == tc_pair_logit_rows(mb.widths[2]) && a.smem_bytes == b.smem_bytes &&
-         a.stages == b.stages;
+         tc_pair_logit_rows(ma.widths[2]) == tc_pair_logit_rows(mb.widths[2]) &&
+         a.sparks_per_tile == b.sparks_per_tile;
 }
 
 int launch_fitness_pair_group(const TcPlan& plan, const Mlp& mlp, const PairMember* table_dev, int32_t n,

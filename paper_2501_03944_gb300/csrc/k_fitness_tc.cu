@@ -39,8 +39,13 @@
 #include <cuda.h>
 
 #include <cstdio>
+#include <array>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "fitness_tc.cuh"
 #include "tc_ptx.cuh"
@@ -562,6 +567,38 @@ bool tc_supported(const int32_t* widths, int n_layers) {
   return false;
 }
 
+namespace {
+
+// The pair plan's tile shape: S sparks per tile, `stages` pipeline stages, and the first-layer operand's
+// maps, whose box is half a tile's rows.
+mgfwa_status pair_shape(TcPlan& plan, const Mlp& mlp, int S, int stages) {
+  const int h1 = mlp.widths[1], d_in = mlp.widths[0], C = mlp.widths[2];
+  const int esize = plan.f8 ? 1 : 2, bk = kRowBytes / esize;
+  const CUtensorMapDataType dt = plan.f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  plan.sparks_per_tile = S;
+  plan.n_tile = S * h1;
+  plan.stages = stages;
+  plan.smem_bytes = tc_pair_fixed_smem(h1, C, S) + (size_t)stages * tc_pair_stage_bytes(h1, S);
+  {
+    // first-layer operand [max_rows*h1][d_in], box (one 128-byte row of K) x half a tile's rows
+    cuuint64_t dims[2] = {(cuuint64_t)d_in, (cuuint64_t)plan.w_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)d_in * esize};
+    cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)(plan.n_tile / 2)};
+    if (!encode(&plan.tmap_w, dt, 2, plan.w_base, dims, strides, box)) return MGFWA_ECUDA;
+  }
+  {
+    // the same operand viewed as [K atoms entirely inside d_in][rows][one 128-byte atom], two atoms a load
+    const int n_full = d_in / bk > 0 ? d_in / bk : 1;
+    cuuint64_t dw[3] = {(cuuint64_t)bk, (cuuint64_t)plan.w_rows, (cuuint64_t)n_full};
+    cuuint64_t sw[2] = {(cuuint64_t)d_in * esize, (cuuint64_t)kRowBytes};
+    cuuint32_t bw[3] = {(cuuint32_t)bk, (cuuint32_t)(plan.n_tile / 2), 2};
+    if (!encode(&plan.tmap_wk, dt, 3, plan.w_base, dw, sw, bw)) return MGFWA_ECUDA;
+  }
+  return MGFWA_OK;
+}
+
+}  // namespace
+
 mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const OpDesc& op, const float* rows, int64_t ld,
                      int64_t max_rows) {
   plan = TcPlan();
@@ -596,19 +633,9 @@ mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const OpDesc& op, const float
   if (op.w2 && tc_pair_supported(mlp.widths, mlp.n_layers)) {
     // the CTA-pair kernel: 256 samples x S sparks per tile, each CTA loading half of either operand
     plan.pair = true;
-    plan.sparks_per_tile = tc_pair_sparks(h1, C);
-    plan.n_tile = plan.sparks_per_tile * h1;
-    const size_t fixed = tc_pair_fixed_smem(h1, C), stage = tc_pair_stage_bytes(h1, C);
-    const size_t limit = (size_t)prop.sharedMemPerBlockOptin;
-    int stages = tc_pair_max_stages();
-    while (stages > 2 && fixed + stages * stage > limit) --stages;
-    if (fixed + stages * stage > limit) {
-      g_err = "shared memory too small for the tensor-core pair tiles";
-      return MGFWA_EINVAL;
-    }
-    plan.stages = stages;
-    plan.smem_bytes = fixed + stages * stage;
     plan.pairs = plan.num_sms / 2;
+    plan.w_base = op.base;
+    plan.w_rows = max_rows * h1;
     const int nl = tc_pair_logit_rows(C);
     if (op.w2_rows != nl || op.w2_h1 != h1) {
       g_err = "pair kernel: the BF16 W2 copy has the wrong shape";
@@ -622,24 +649,14 @@ mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const OpDesc& op, const float
       if (!encode(&plan.tmap_x, dt, 2, mlp.Xop, dims, strides, box)) return MGFWA_ECUDA;
     }
     {
-      // first-layer operand [max_rows*h1][d_in], box (one 128-byte row of K) x half a tile's rows
-      cuuint64_t dims[2] = {(cuuint64_t)d_in, (cuuint64_t)(max_rows * h1)};
-      cuuint64_t strides[1] = {(cuuint64_t)d_in * esize};
-      cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)(plan.n_tile / 2)};
-      if (!encode(&plan.tmap_w, dt, 2, op.base, dims, strides, box)) return MGFWA_ECUDA;
-    }
-    {
-      // the same two operands viewed as [K atoms entirely inside d_in][rows][one 128-byte atom] (the atom
-      // stride is 128 bytes), so that one load brings two atoms; the partial last atom goes through the
-      // plain views above, whose fill past d_in is zero
+      // X viewed as [K atoms entirely inside d_in][N][one 128-byte atom] (the atom stride is 128 bytes),
+      // so that one load brings two atoms; the partial last atom goes through the plain view above, whose
+      // fill past d_in is zero
       const int n_full = d_in / bk > 0 ? d_in / bk : 1;
       cuuint64_t dx[3] = {(cuuint64_t)bk, (cuuint64_t)mlp.N, (cuuint64_t)n_full};
       cuuint64_t sx[2] = {(cuuint64_t)d_in * esize, (cuuint64_t)kRowBytes};
       cuuint32_t bx[3] = {(cuuint32_t)bk, kBM, 2};
       if (!encode(&plan.tmap_x3, dt, 3, mlp.Xop, dx, sx, bx)) return MGFWA_ECUDA;
-      cuuint64_t dw[3] = {(cuuint64_t)bk, (cuuint64_t)(max_rows * h1), (cuuint64_t)n_full};
-      cuuint32_t bw[3] = {(cuuint32_t)bk, (cuuint32_t)(plan.n_tile / 2), 2};
-      if (!encode(&plan.tmap_wk, dt, 3, op.base, dw, sx, bw)) return MGFWA_ECUDA;
     }
     {
       // BF16 W2 [max_rows][nl][h1], box 64 x nl/2 x 1 (one CTA's half of the logit rows, one K atom)
@@ -650,8 +667,17 @@ mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const OpDesc& op, const float
     }
     plan.tmap_w2 = plan.tmap_w2b;  // unused by the pair kernel
     plan.tmap_w3 = plan.tmap_w2b;
+    // the default shape: the logits in the sparks' own columns, the deepest pipeline that fits
+    const int S = tc_pair_sparks(h1, C, true);
+    const int stages = tc_pair_stages_fit(h1, C, S, (size_t)prop.sharedMemPerBlockOptin);
+    if (stages < 2) {
+      g_err = "shared memory too small for the tensor-core pair tiles";
+      return MGFWA_EINVAL;
+    }
     plan.ready = true;
-    return MGFWA_OK;
+    const mgfwa_status st = pair_shape(plan, mlp, S, stages);
+    if (st != MGFWA_OK) plan.ready = false;
+    return st;
   }
   plan.sparks_per_tile = sparks_per_tile(h1, h2, C);
   plan.n_tile = plan.sparks_per_tile * h1;
@@ -755,6 +781,127 @@ cudaError_t tc_prepare(TcPlan& plan, const Mlp& mlp) {
   TcArgs a = {};
   a.C = mlp.widths[mlp.n_layers];
   return dispatch(plan, mlp, a, nullptr, true);
+}
+
+mgfwa_status tc_pair_configure(TcPlan& plan, const Mlp& mlp, int sparks_per_tile, int stages) {
+  if (!plan.ready || !plan.pair) return MGFWA_EINVAL;
+  const int h1 = mlp.widths[1], C = mlp.widths[2];
+  if (sparks_per_tile != tc_pair_sparks(h1, C, true) && sparks_per_tile != tc_pair_sparks(h1, C, false)) {
+    g_err = "pair kernel: no tile of that many sparks for this network";
+    return MGFWA_EINVAL;
+  }
+  int dev = 0, limit = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    g_err = "device query failed";
+    return MGFWA_ECUDA;
+  }
+  if (stages < 2 || stages > tc_pair_stages_fit(h1, C, sparks_per_tile, (size_t)limit)) {
+    g_err = "pair kernel: that pipeline depth does not fit in shared memory";
+    return MGFWA_EINVAL;
+  }
+  const mgfwa_status st = pair_shape(plan, mlp, sparks_per_tile, stages);
+  if (st != MGFWA_OK) return st;
+  if (tc_pair_prepare(plan, mlp) != cudaSuccess) {
+    g_err = "pair kernel attributes";
+    return MGFWA_ECUDA;
+  }
+  return MGFWA_OK;
+}
+
+namespace {
+
+// Tuned choices per (device, operand type, d_in, h1, classes, 256-sample tiles rounded up to a power of
+// two, launch rows rounded up to a power of two): sparks per tile and stages.
+std::mutex g_tune_mu;
+std::map<std::array<int64_t, 7>, std::pair<int, int>> g_tuned;
+
+int64_t pow2_at_least(int64_t v) {
+  int64_t r = 1;
+  while (r < v) r <<= 1;
+  return r;
+}
+
+}  // namespace
+
+mgfwa_status tc_pair_tune(TcPlan& plan, const Mlp& mlp, const float* rows, int64_t ld, int32_t count, float scale,
+                          float* partial, uint32_t* status, cudaStream_t s) {
+  if (!plan.ready || !plan.pair || count <= 0) return MGFWA_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return MGFWA_OK;
+  }
+  const int h1 = mlp.widths[1], C = mlp.widths[2];
+  int dev = 0, limit = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    g_err = "device query failed";
+    return MGFWA_ECUDA;
+  }
+  const std::array<int64_t, 7> key = {dev, plan.f8 ? 1 : 0, mlp.widths[0], h1, C, pow2_at_least((mlp.N + 255) / 256),
+                                      pow2_at_least(count)};
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto hit = g_tuned.find(key);
+  if (hit != g_tuned.end()) {
+    const mgfwa_status st = tc_pair_configure(plan, mlp, hit->second.first, hit->second.second);
+    if (st == MGFWA_OK) plan.tuned = 1;
+    return st;
+  }
+  // the candidates: both tile shapes, every depth from two to the deepest that fits
+  std::vector<std::pair<int, int>> cand;
+  for (bool shared : {true, false}) {
+    const int S = tc_pair_sparks(h1, C, shared);
+    if (!shared && S == tc_pair_sparks(h1, C, true)) continue;
+    const int fit = tc_pair_stages_fit(h1, C, S, (size_t)limit);
+    for (int st = 2; st <= fit; ++st) cand.emplace_back(S, st);
+  }
+  if (cand.empty()) return MGFWA_OK;
+  std::vector<float> best(cand.size(), 1e30f);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    g_err = "event creation failed";
+    return MGFWA_ECUDA;
+  }
+  mgfwa_status st = MGFWA_OK;
+  // the candidates interleaved over rounds (the first one untimed: module loads, clocks ramping), each
+  // timed over two launches, the minimum kept
+  constexpr int kRounds = 4, kLaunches = 2;
+  for (int r = 0; r < kRounds && st == MGFWA_OK; ++r) {
+    for (size_t c = 0; c < cand.size() && st == MGFWA_OK; ++c) {
+      st = tc_pair_configure(plan, mlp, cand[c].first, cand[c].second);
+      if (st != MGFWA_OK) break;
+      if (launch_fitness_tc(plan, mlp, 0, rows, ld, count, scale, partial, status, s) < 0 ||
+          cudaEventRecord(e0, s) != cudaSuccess) {
+        st = MGFWA_ECUDA;
+        break;
+      }
+      for (int l = 0; l < kLaunches; ++l)
+        if (launch_fitness_tc(plan, mlp, 0, rows, ld, count, scale, partial, status, s) < 0) st = MGFWA_ECUDA;
+      float ms = 0.0f;
+      if (st != MGFWA_OK || cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        st = MGFWA_ECUDA;
+        break;
+      }
+      if (r > 0 && ms < best[c]) best[c] = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != MGFWA_OK) {
+    if (st == MGFWA_ECUDA) g_err = "pair kernel tuning launch failed";
+    return st;
+  }
+  size_t pick = 0;
+  for (size_t c = 1; c < cand.size(); ++c)
+    if (best[c] < best[pick]) pick = c;
+  st = tc_pair_configure(plan, mlp, cand[pick].first, cand[pick].second);
+  if (st != MGFWA_OK) return st;
+  plan.tuned = 1;
+  g_tuned[key] = cand[pick];
+  return MGFWA_OK;
 }
 
 }  // namespace mgfwa

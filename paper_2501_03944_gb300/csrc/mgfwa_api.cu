@@ -988,6 +988,16 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
       return bail(st);
     }
     if (tc_prepare(h->tc, h->mlp) != cudaSuccess) return bail(cuda_fail(h, "tensor-core kernel attributes"));
+    if (h->tc.pair) {
+      // the pair kernel's tile shape and depth, timed on one explosion's worth of rows (all give the same
+      // fitness; the rows are not yet the run's)
+      st = tc_pair_tune(h->tc, h->mlp, h->sparks, p.Dp, (int32_t)((int64_t)p.B * p.mu * p.lam), h->op_scale,
+                        h->partial, h->status, h->stream);
+      if (st != MGFWA_OK) {
+        h->err = tc_last_error();
+        return bail(st);
+      }
+    }
   }
   // the FP32-accurate first layer of the elite re-score and of the refinement on the tensor cores
   // (where the shape allows; otherwise they keep the CUDA-core products)
@@ -1699,6 +1709,29 @@ mgfwa_status mgfwa_debug_fp32_tc(const mgfwa_t* h, int32_t* rescore, int32_t* re
 mgfwa_status mgfwa_debug_wait_budget(mgfwa_t* h, uint64_t ticks) {
   if (!h) return MGFWA_EINVAL;
   h->tc.wait_budget = ticks;
+  return MGFWA_OK;
+}
+
+mgfwa_status mgfwa_debug_pair_tile(const mgfwa_t* h, int32_t* sparks_per_tile, int32_t* stages, int32_t* tuned) {
+  if (!h) return MGFWA_EINVAL;
+  const bool on = h->tc.ready && h->tc.pair;
+  if (sparks_per_tile) *sparks_per_tile = on ? h->tc.sparks_per_tile : -1;
+  if (stages) *stages = on ? h->tc.stages : -1;
+  if (tuned) *tuned = on ? h->tc.tuned : -1;
+  return MGFWA_OK;
+}
+
+mgfwa_status mgfwa_debug_set_pair_tile(mgfwa_t* h, int32_t sparks_per_tile, int32_t stages) {
+  mgfwa_status st = check_usable(h);
+  if (st != MGFWA_OK) return st;
+  if (!h->tc.ready || !h->tc.pair) return fail(h, MGFWA_EINVAL, "the handle is not on the CTA-pair fitness kernel");
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h, "set pair tile synchronise");
+  st = tc_pair_configure(h->tc, h->mlp, sparks_per_tile, stages);
+  if (st != MGFWA_OK) return fail(h, st, "%s", tc_last_error());
+  h->tc.tuned = 0;
+  // the next generation is captured again, with the new shape
+  if (h->gen_exec) cudaGraphExecDestroy(h->gen_exec);
+  h->gen_exec = nullptr;
   return MGFWA_OK;
 }
 
