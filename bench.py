@@ -402,6 +402,9 @@ def gpu_arm(args):
         extra["fp32_one_run"] = dict(timed_generations({"precision": pkg.MGFWA_FP32}, 5), precision="fp32")
         # the 3072-128(ReLU)-64(ReLU)-10 network (N = 4096, 8 fireworks x (256 + 8) sparks) in each precision
         extra["mlp3072_128_64_10"] = precision_sweep_3072(pkg, stream)
+        X3, y3 = W.make_data(W.MLP_3072_128_64_10)
+        extra["mlp3072_128_64_10"]["fitness_rel_err_vs_fp32"] = fitness_error_vs_fp32(
+            pkg, X3, y3, stream, n_sparks=64, workload=W.MLP_3072_128_64_10)
         # E4M3 first layer on the tensor cores (elite candidates re-scored in FP32)
         extra["fp8_one_run"] = dict(timed_generations({"precision": pkg.MGFWA_FP8}, max(5, args.steps // 2)),
                                     precision="fp8")
@@ -447,6 +450,14 @@ def gpu_arm(args):
         avg_s = fit_ms / max(fit_n, 1) / 1e3
         kernels = {g: {"ms_total": round(t, 4), "launches": n, "share": round(t / max(ms_profiled, 1e-9), 4)}
                    for g, (t, n) in ktimes.items()}
+        if "mlp3072_128_64_10" in extra:
+            # the 3072-128-64-10 explosion fitness launch against the burst peak of its operand type
+            sw = extra["mlp3072_128_64_10"]
+            f8 = lib_peaks.get("fp8_tflops") or 2.0 * bf16_peak
+            for name, pk in (("bf16", bf16_peak), ("fp8", f8)):
+                if name in sw:
+                    sw[name]["fitness_frac_of_burst"] = sw[name]["fitness_tflops"] / pk
+                    sw[name]["peak_tflops"] = pk
         # the kernel is timed launch by launch (a few tenths of a millisecond each), so the burst peak is the
         # denominator; the ratio to the sustained (power-capped) peak is reported beside it
         if prec == pkg.MGFWA_BF16:
@@ -530,7 +541,7 @@ def precision_sweep_3072(pkg, stream, gens: int = 3):
     out = {}
     for name, prec, g in (("bf16", pkg.MGFWA_BF16, gens), ("fp8", pkg.MGFWA_FP8, gens), ("fp32", pkg.MGFWA_FP32, 2)):
         w = W.scaled(w0, eval_budget=W.budget_for_generations(w0.n_fireworks, w0.sparks_per_firework,
-                                                              w0.guiding_per_firework, g + 1))
+                                                              w0.guiding_per_firework, g + 2))
         h = pkg.Mgfwa.for_workload(w, 77, precision=prec, X=X3, y=y3, stream=stream.cuda_stream)
         h.step(1)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -540,18 +551,26 @@ def precision_sweep_3072(pkg, stream, gens: int = 3):
         b.record(stream)
         torch.cuda.synchronize()
         t = a.elapsed_time(b)
+        # one more generation kernel by kernel: the explosion-spark fitness launch's duration
+        h.profile(True)
+        h.step(1)
+        fit_ms, fit_n = h.kernel_times()["fitness_explosion"]
+        h.profile(False)
         _, best_f, _ = h.best()
         h.close()
+        n_e = w0.n_fireworks * w0.sparks_per_firework
         out[name] = {"sparks_per_s": h.sparks_per_gen * g / (t / 1e3), "ms_per_generation": t / g,
-                     "best_f_fp64": best_f}
+                     "best_f_fp64": best_f, "fitness_launch_ms": fit_ms / max(fit_n, 1),
+                     "fitness_tflops": w0.flops_per_spark() * n_e / (fit_ms / max(fit_n, 1) / 1e3) / 1e12}
     return out
 
 
-def fitness_error_vs_fp32(pkg, X, y, stream, n_sparks: int = 128):
-    """Relative error of the BF16 and FP8 fitness against the FP32 path on the bench workload's own
-    explosion sparks (generation 4 of a run), the qualifier of the throughput metric (<= 1e-2)."""
+def fitness_error_vs_fp32(pkg, X, y, stream, n_sparks: int = 128, workload=None):
+    """Relative error of the BF16 and FP8 fitness against the FP32 path on a workload's own explosion
+    sparks (generation 4 of a run; the bench workload by default), the qualifier of the throughput metric
+    (<= 1e-2)."""
     out = {}
-    w = W.scaled(WORKLOAD, eval_budget=10 ** 9)
+    w = W.scaled(workload or WORKLOAD, eval_budget=10 ** 9)
     for name, prec in (("bf16", pkg.MGFWA_BF16), ("fp8", pkg.MGFWA_FP8)):
         h = pkg.Mgfwa.for_workload(w, 4242, precision=prec, X=X, y=y, stream=stream.cuda_stream)
         h.step(3)

@@ -14,7 +14,9 @@ struct TcPlan {
   bool pair = false;    // the CTA-pair kernel (two layers, h1 in {64, 128}); else the one-CTA kernel
   int pairs = 0;        // CTA pairs resident at once (the pair kernel's persistent grid)
   uint64_t wait_budget = 0;  // clock64 ticks before a bounded wait gives up (0 = the kernels' default, ~2 s)
-  CUtensorMap tmap_w2b; // pair kernel: BF16 W2 [P][16 or 32][h1], box 64 x half the rows x 1, 128B swizzle
+  CUtensorMap tmap_w2b; // pair kernel: BF16 W2 [P][16 or 32 (two layers) or h2][h1], box 64 x half the rows x 1,
+                        // 128B swizzle
+  CUtensorMap tmap_w3b; // pair kernel, three layers: BF16 W3 [P][16][h2], box 64 x 8 x 1
   CUtensorMap tmap_x3;  // pair kernel: X viewed as [K atoms][N][one 128-byte atom], box one atom x 128 x 2 atoms
   CUtensorMap tmap_wk;  // pair kernel: the first-layer operand viewed the same way, box one atom x half a tile x 2
   CUtensorMap tmap_x;   // X  [N][d_in], box 128 rows x 128 bytes of K, 128B swizzle
@@ -36,11 +38,14 @@ struct TcPlan {
 // three with (h1, h2) in {(128, 64), (64, 32)} and 2..16 classes.
 bool tc_supported(const int32_t* widths, int n_layers);
 
-// True if the CTA-pair kernel handles this network: two linear layers,
-// h1 in {64, 128}, 2..32 classes, d_in % 8 == 0.  It needs the BF16 copy of
-// W2 (OpDesc::w2) with tc_pair_logit_rows(C) rows per spark.
+// True if the CTA-pair kernel handles this network (d_in % 8 == 0): two
+// linear layers with h1 in {64, 128} and 2..32 classes, or three with
+// (h1, h2) = (128, 64) and 2..16 classes.  It needs the BF16 copy of W2
+// (OpDesc::w2) with tc_pair_w2_rows rows per spark, and with three layers
+// that of W3 (OpDesc::w3) with tc_pair_logit_rows(C) rows.
 bool tc_pair_supported(const int32_t* widths, int n_layers);
 int tc_pair_logit_rows(int C);
+int tc_pair_w2_rows(const int32_t* widths, int n_layers);
 
 // Encode the tensor maps over the handle's X copy (mlp.Xop), first-layer
 // operand (BF16 or E4M3, op.kind) and FP32 spark rows (`sparks`, row stride
@@ -74,11 +79,14 @@ struct PairArgs {
   int32_t stages;
   int32_t C;            // classes (<= NL)
   int32_t act;
-  int32_t c_pad;        // C rounded up to 4 (floats of b2 copied)
+  int32_t act2;         // three layers: the second hidden layer's activation
+  int32_t c_pad;        // C rounded up to 4 (floats of the logits' bias copied)
   float scale;          // layer-1 accumulator multiplier (1 for BF16; 1 / (inv_x inv_w) for E4M3)
   int64_t N;
   int64_t ld;           // FP32 row stride of the sparks
-  int64_t b1_off, b2_off;
+  int64_t b1_off;
+  int64_t b2_off;       // three layers: the second hidden layer's bias
+  int64_t bl_off;       // the logits' bias
   const float* rows;    // FP32 spark rows of this launch (biases)
   const int32_t* y;
   float* partial;       // [m_tiles][count]
@@ -90,7 +98,7 @@ struct PairArgs {
 // memory, and where its tiles start among the launch's (aligned as the
 // tensor maps require, which the array's allocation honours).
 struct PairMember {
-  CUtensorMap x3, x, w3, w, w2;
+  CUtensorMap x3, x, w3, w, w2, wl3;  // wl3: the BF16 W3 copy (three layers)
   PairArgs a;
   int32_t tile_start, tiles;
 };
@@ -111,14 +119,15 @@ int launch_fitness_pair_group(const TcPlan& plan, const Mlp& mlp, const PairMemb
 
 // The CTA-pair kernel's pieces (k_fitness_pair.cu), used by tc_plan and
 // launch_fitness_tc.  Sparks per tile: 256 / h1 when the logits share the
-// sparks' columns, else 256 / (h1 + logit rows).
-int tc_pair_sparks(int h1, int C, bool shared);
-size_t tc_pair_fixed_smem(int h1, int C, int sparks_per_tile);
+// sparks' columns, else 256 / (h1 + logit rows) (two layers only; 0 for
+// three).
+int tc_pair_sparks(const Mlp& mlp, bool shared);
+size_t tc_pair_fixed_smem(const Mlp& mlp, int sparks_per_tile);
 size_t tc_pair_stage_bytes(int h1, int sparks_per_tile);
 int tc_pair_max_stages();
 // Deepest pipeline of the tile shape that fits the device's shared memory
 // (`limit` bytes per block), or 0 if not even two stages fit.
-int tc_pair_stages_fit(int h1, int C, int sparks_per_tile, size_t limit);
+int tc_pair_stages_fit(const Mlp& mlp, int sparks_per_tile, size_t limit);
 
 // Set a pair plan's tile shape and pipeline depth (re-encoding the W1 maps,
 // whose box is half a tile's rows) and its kernel's attributes; MGFWA_EINVAL

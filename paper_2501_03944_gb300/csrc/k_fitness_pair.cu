@@ -95,14 +95,17 @@ struct PairSmem {
   uint64_t full[kMaxStg];      // even CTA: both CTAs' loads of the stage landed
   uint64_t empty[kMaxStg];     // the stage's MMAs completed
   uint64_t tmem_full[2];       // layer 1 of the half's tile is complete
-  uint64_t a2_full[2];         // even CTA: both CTAs wrote the half's activations
-  uint64_t l2_full[2];         // layer 2 of the half's tile is complete (its logits)
+  uint64_t a2_full[2];         // even CTA: both CTAs wrote the half's first-layer activations
+  uint64_t l2_full[2];         // layer 2 of the half's tile is complete
+  uint64_t a3_full[2];         // three layers, even CTA: both CTAs wrote the half's second-layer activations
+  uint64_t l3_full[2];         // three layers: layer 3 (the logits) of the half's tile is complete
   uint64_t tmem_empty[2];      // even CTA: the half is free for the next layer 1 (shared: both CTAs read its
                                // logits; separate: layer 2 read its activations)
   uint64_t l2_empty[2];        // even CTA, separate logits: both CTAs read the half's logits
   uint64_t bias_full[kTBufs];  // this CTA's biases of the buffer's tile landed
-  uint64_t w2_full[kTBufs];    // even CTA: both CTAs' W2 halves of the buffer's tile landed
-  uint64_t tail_empty[kTBufs]; // layer 2 read the W2 halves, this CTA's epilogue the biases
+  uint64_t w2_full[kTBufs];    // even CTA: both CTAs' W2 (and W3) halves of the buffer's tile landed
+  uint64_t w2_empty;           // three layers: layer 3 read the single W2/W3 buffer
+  uint64_t tail_empty[kTBufs]; // the MMAs and this CTA's epilogue are done with the buffer's tile
   uint64_t mma_done;
   uint32_t tmem_base;
   volatile int abort_flag;
@@ -135,50 +138,93 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
+// act(acc * sc + bias) of `n` accumulator columns of this warp's lanes, from
+// column `src`, as packed BF16 pairs into the columns from `dst` (dst <= src:
+// chunk j0 writes [dst + j0/2, dst + j0/2 + 8), which this or an earlier
+// chunk has read).
+template <int n>
+__device__ __forceinline__ void pack_layer(uint32_t src, uint32_t dst, const float* bias, float sc, int act) {
+#pragma unroll 1
+  for (int j0 = 0; j0 < n; j0 += 16) {
+    float h[16];
+    tmem_ld16(src + (uint32_t)j0, h);
+    tmem_wait_ld();
+    uint32_t pk[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float2 bb = *reinterpret_cast<const float2*>(bias + j0 + 2 * q);
+      pk[q] = pack_bf16x2(act_f(act, fmaf(h[2 * q], sc, bb.x)), act_f(act, fmaf(h[2 * q + 1], sc, bb.y)));
+    }
+    tmem_st8u(dst + (uint32_t)(j0 / 2), pk);
+  }
+}
+
+// H2 > 0: three layers (h1 -> h2 -> logits, both hidden layers activated).
+// Then the tile is always the shared shape (S = 256 / h1): per spark, the
+// packed first-layer activations in its first h1/2 columns, layer 2's h2
+// outputs in the next h2 columns, packed in place by the epilogue into h2/2
+// columns, and the logits after them.  W2 and W3 (BF16 copies beside the
+// first-layer operand, each CTA holding half of either's rows) share one
+// buffer, loaded by the producer between K steps of the tile once layer 3 of
+// the tile before has read it.
+//
 // kGroup: one launch over several handles' sparks.  Their tiles are laid end
 // to end (member i's tiles from members[i].tile_start on), and each role
 // walks ascending tiles with a cursor into the member table (device memory:
 // the members' tensor maps and arguments).  Otherwise the kernel parameters
 // hold the one launch's maps and `a` its arguments.  `a` also carries what
 // every member shares: stages, the status word and the wait budget.
-template <int H1, int NL, int S, bool F8, bool kGroup>
+template <int H1, int H2, int NL, int S, bool F8, bool kGroup>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
     k_fitness_pair(const __grid_constant__ CUtensorMap tmap_x3, const __grid_constant__ CUtensorMap tmap_x,
                    const __grid_constant__ CUtensorMap tmap_w3, const __grid_constant__ CUtensorMap tmap_w,
-                   const __grid_constant__ CUtensorMap tmap_w2, PairArgs a, const PairMember* __restrict__ members,
-                   int32_t n_members) {
+                   const __grid_constant__ CUtensorMap tmap_w2, const __grid_constant__ CUtensorMap tmap_wl3,
+                   PairArgs a, const PairMember* __restrict__ members, int32_t n_members) {
   griddep_wait();
   griddep_launch_dependents();
-  constexpr int kNT = S * H1;                    // layer-1 accumulator columns per tile
-  constexpr bool kShared = S * (H1 + NL) > 256;  // the logits share the spark's accumulator columns
-  constexpr int kBK = F8 ? 128 : 64;             // K elements per atom (one 128-byte row)
-  constexpr int kGroups = pair_groups(S);        // epilogue warps per TMEM lane quadrant
+  constexpr bool kL3 = H2 > 0;
+  constexpr int kNT = S * H1;                              // layer-1 accumulator columns per tile
+  constexpr bool kShared = kL3 || S * (H1 + NL) > 256;     // the logits share the spark's accumulator columns
+  constexpr int kBK = F8 ? 128 : 64;                       // K elements per atom (one 128-byte row)
+  constexpr int kGroups = pair_groups(S);                  // epilogue warps per TMEM lane quadrant
   constexpr int kEpi = 4 * kGroups;
-  constexpr int kHalfNL = NL / 2;                // W2 rows (logits) each CTA holds
-  constexpr int kW2Atoms = H1 / 64;              // 128-byte K atoms of a BF16 W2 row
-  constexpr uint32_t kW2AtomBytes = kHalfNL * 128;
-  constexpr uint32_t kW2Bytes = kW2Atoms * kW2AtomBytes;  // one spark's W2 half
-  constexpr int kTailF = H1 + 32;                // b1 and b2 (C <= 32) of one spark
-  constexpr uint32_t kAtomA = kPM * kRowB;       // one K atom of this CTA's 128 samples
-  constexpr uint32_t kAtomB = (kNT / 2) * kRowB; // one K atom of this CTA's half of the tile's W1 rows
-  constexpr uint32_t kStageA = 2 * kAtomA;       // a stage: two atoms of each operand
+  constexpr int kWB = kL3 ? 1 : kTBufs;                    // W2 (and W3) buffers
+  constexpr int kN2 = kL3 ? H2 : NL;                       // layer-2 outputs per spark
+  constexpr int kW2Atoms = H1 / 64;                        // 128-byte K atoms of a BF16 W2 row
+  constexpr uint32_t kW2AtomBytes = (kN2 / 2) * 128;       // each CTA holds half of W2's rows
+  constexpr uint32_t kW2Bytes = kW2Atoms * kW2AtomBytes;   // one spark's W2 half
+  constexpr int kW3Atoms = kL3 ? H2 / 64 : 0;
+  constexpr uint32_t kW3AtomBytes = (NL / 2) * 128;
+  constexpr uint32_t kW3Bytes = kW3Atoms * kW3AtomBytes;   // one spark's W3 half
+  constexpr uint32_t kWSpark = kW2Bytes + kW3Bytes;
+  constexpr int kTailF = H1 + H2 + 32;                     // b1, b2 (three layers) and the logits' bias
+  constexpr uint32_t kAtomA = kPM * kRowB;                 // one K atom of this CTA's 128 samples
+  constexpr uint32_t kAtomB = (kNT / 2) * kRowB;           // one K atom of this CTA's half of the tile's W1 rows
+  constexpr uint32_t kStageA = 2 * kAtomA;                 // a stage: two atoms of each operand
   constexpr uint32_t kStageB = 2 * kAtomB;
-  static_assert(kHalfNL % 8 == 0, "each W2 half is whole 8-row swizzle groups");
+  static_assert((kN2 / 2) % 8 == 0 && (NL / 2) % 8 == 0, "each W2 / W3 half is whole 8-row swizzle groups");
   static_assert(S >= 1 && kNT <= 256 && (!kShared || NL <= H1 / 2), "a tile's columns fit in a TMEM half");
+  static_assert(!kL3 || (H2 % 64 == 0 && H2 <= H1 / 2 && H2 / 2 + NL <= H1 / 2 && NL == 16),
+                "three layers: layer 2's outputs and the logits fit in the spark's second h1/2 columns");
   static_assert((kNT / 2) % 8 == 0 && kNT % 16 == 0, "a W1 half is whole 8-row groups; N is a multiple of 16");
 
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* stage_a = base;
   uint8_t* stage_b = base + (size_t)a.stages * kStageA;
-  uint8_t* w2s = stage_b + (size_t)a.stages * kStageB;                              // [kTBufs][S][kW2Bytes]
-  float* tails = reinterpret_cast<float*>(w2s + (size_t)kTBufs * S * kW2Bytes);      // [kTBufs][S][kTailF]
+  uint8_t* w2s = stage_b + (size_t)a.stages * kStageB;                               // [kWB][S][kWSpark]
+  float* tails = reinterpret_cast<float*>(w2s + (size_t)kWB * S * kWSpark);          // [kTBufs][S][kTailF]
   float* red = tails + (size_t)kTBufs * S * kTailF;                                  // [S][4]
   PairSmem* sm = reinterpret_cast<PairSmem*>((reinterpret_cast<uintptr_t>(red + 4 * S) + 15) & ~uintptr_t(15));
 
-  // TMEM columns of spark s within a half: its accumulator / packed activations, its logits
+  // TMEM columns of spark s within a half: its accumulator / packed activations, layer 2's outputs / their
+  // packed activations (three layers), its logits
   auto col_h = [](int sp) { return (uint32_t)(sp * H1); };
-  auto col_lg = [](int sp) { return kShared ? (uint32_t)(sp * H1 + H1 / 2) : (uint32_t)(S * H1 + sp * NL); };
+  auto col_l2 = [](int sp) {
+    return kL3 ? (uint32_t)(sp * H1 + H1 / 2)
+               : (kShared ? (uint32_t)(sp * H1 + H1 / 2) : (uint32_t)(S * H1 + sp * NL));
+  };
+  auto col_lg = [&](int sp) { return kL3 ? (uint32_t)(sp * H1 + H1 / 2 + H2 / 2) : col_l2(sp); };
   const uint32_t rank = cluster_rank();
   const bool lead = rank == 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -195,6 +241,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
     }
   };
   auto args_of = [&](int cur) -> const PairArgs& { return kGroup ? members[cur].a : a; };
+  // the W2 buffer of the tile with local index j, and the phase of its barriers for that tile
+  auto w_buf = [](int j) { return kL3 ? 0 : j % kTBufs; };
+  auto w_phase = [](int j) { return kL3 ? (uint32_t)(j & 1) : (uint32_t)(j / kTBufs) & 1u; };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < a.stages; ++s) {
@@ -205,6 +254,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
       mbar_init(&sm->tmem_full[b], 1);
       mbar_init(&sm->a2_full[b], 2 * kEpi);
       mbar_init(&sm->l2_full[b], 1);
+      mbar_init(&sm->a3_full[b], 2 * kEpi);
+      mbar_init(&sm->l3_full[b], 1);
       mbar_init(&sm->tmem_empty[b], kShared ? 2 * kEpi : 1);
       mbar_init(&sm->l2_empty[b], 2 * kEpi);
     }
@@ -213,6 +264,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
       mbar_init(&sm->w2_full[b], 1);
       mbar_init(&sm->tail_empty[b], 1 + kEpi);
     }
+    mbar_init(&sm->w2_empty, 1);
     mbar_init(&sm->mma_done, 1);
     sm->abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -243,6 +295,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
       int local = 0;
       bool ok = true;
       int cur = 0, fenced = -1;
+      int w_last = -1;  // three layers: the last tile whose W2/W3 loads were issued
       for (int t = pair; t < tiles && ok; t += npairs, ++local) {
         const int lt = member_at(t, cur);
         const PairArgs& m = args_of(cur);
@@ -251,13 +304,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
         const CUtensorMap* mw3 = kGroup ? &members[cur].w3 : &tmap_w3;
         const CUtensorMap* mw = kGroup ? &members[cur].w : &tmap_w;
         const CUtensorMap* mw2 = kGroup ? &members[cur].w2 : &tmap_w2;
+        const CUtensorMap* mwl3 = kGroup ? &members[cur].wl3 : &tmap_wl3;
         if (kGroup && fenced != cur) {
           // the member's maps were written to global memory by the host: order the tensor-map proxy's reads
-          for (const CUtensorMap* mp : {mx3, mx, mw3, mw, mw2})
+          for (const CUtensorMap* mp : {mx3, mx, mw3, mw, mw2, mwl3})
             asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mp) : "memory");
           fenced = cur;
         }
-        const uint32_t bias_bytes = (uint32_t)(H1 + m.c_pad) * 4u;
+        const uint32_t bias_bytes = (uint32_t)(H1 + H2 + m.c_pad) * 4u;
         const int mt = lt % m.m_pairs, nt = lt / m.m_pairs;
         const int s0 = nt * S;
         const int s_valid = min(S, m.count - s0);
@@ -269,22 +323,35 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
           const float* row = m.rows + (int64_t)(s0 + s) * m.ld;
           float* tl = tails + ((size_t)tb * S + s) * kTailF;
           bulk_load(tl, row + m.b1_off, (uint32_t)H1 * 4u, &sm->bias_full[tb]);
-          bulk_load(tl + H1, row + m.b2_off, (uint32_t)m.c_pad * 4u, &sm->bias_full[tb]);
+          if (kL3) bulk_load(tl + H1, row + m.b2_off, (uint32_t)H2 * 4u, &sm->bias_full[tb]);
+          bulk_load(tl + H1 + H2, row + m.bl_off, (uint32_t)m.c_pad * 4u, &sm->bias_full[tb]);
         }
-        // this CTA's W2 halves; the even CTA's barrier expects both CTAs' bytes
-        if (lead) mbar_expect_tx(&sm->w2_full[tb], 2u * kW2Bytes * (uint32_t)s_valid);
-        const uint32_t w2_bar = map_to(&sm->w2_full[tb], 0u);
-        for (int s = 0; s < s_valid; ++s) {
-          uint8_t* w2 = w2s + ((size_t)tb * S + s) * kW2Bytes;
+        // this CTA's W2 (and W3) halves; the even CTA's barrier expects both CTAs' bytes
+        const int wb = w_buf(local);
+        auto issue_w = [&]() {
+          if (lead) mbar_expect_tx(&sm->w2_full[wb], 2u * kWSpark * (uint32_t)s_valid);
+          const uint32_t w2_bar = map_to(&sm->w2_full[wb], 0u);
+          for (int s = 0; s < s_valid; ++s) {
+            uint8_t* w2 = w2s + ((size_t)wb * S + s) * kWSpark;
 #pragma unroll
-          for (int at = 0; at < kW2Atoms; ++at)
-            tma_load_3d_pair(w2 + at * kW2AtomBytes, mw2, at * 64, (int)rank * kHalfNL, m.first_spark + s0 + s,
-                             w2_bar);
-        }
+            for (int at = 0; at < kW2Atoms; ++at)
+              tma_load_3d_pair(w2 + at * kW2AtomBytes, mw2, at * 64, (int)rank * (kN2 / 2), m.first_spark + s0 + s,
+                               w2_bar);
+#pragma unroll
+            for (int at = 0; at < kW3Atoms; ++at)
+              tma_load_3d_pair(w2 + kW2Bytes + at * kW3AtomBytes, mwl3, at * 64, (int)rank * (NL / 2),
+                               m.first_spark + s0 + s, w2_bar);
+          }
+          w_last = local;
+        };
+        // two layers: W2 rides in the tail buffer just freed; three: once layer 3 of the tile before read
+        // the single buffer, between this tile's K steps
+        if (!kL3) issue_w();
         const int row_x = mt * (2 * kPM) + (int)rank * kPM;
         const int row_w = (m.first_spark + s0) * H1 + (int)rank * (kNT / 2);
         const int n_pairs = (m.n_full + 1) / 2;
         for (int kb = 0; kb < m.n_steps; ++kb, ++it) {
+          if (kL3 && w_last != local && mbar_test_wait(&sm->w2_empty, ((uint32_t)local & 1u) ^ 1u)) issue_w();
           const int st = (int)(it % (uint32_t)a.stages);
           const uint32_t ph = (it / (uint32_t)a.stages) & 1u;
           if (!wait(&sm->empty[st], ph ^ 1u, 1u)) {
@@ -304,14 +371,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
             tma_load_2d_pair(stage_b + (size_t)st * kStageB, mw, m.n_full * kBK, row_w, bar);
           }
         }
+        if (kL3 && ok && w_last != local) {
+          if (!wait(&sm->w2_empty, ((uint32_t)local & 1u) ^ 1u, 1u)) {
+            ok = false;
+          } else {
+            issue_w();
+          }
+        }
       }
       // copies land before the CTA may leave: this CTA's biases, and (even CTA) the stages and W2 it
       // armed, which also carry the odd CTA's bytes.  Short budgets: only an aborting run waits here.
       constexpr uint64_t kDrain = 1ull << 24;
       for (int l = local - kTBufs > 0 ? local - kTBufs : 0; l < local; ++l) {
         mbar_drain(&sm->bias_full[l % kTBufs], (uint32_t)((l / kTBufs) & 1), a.status, kDrain);
-        if (lead) mbar_drain(&sm->w2_full[l % kTBufs], (uint32_t)((l / kTBufs) & 1), a.status, kDrain);
+        if (lead && !kL3) mbar_drain(&sm->w2_full[l % kTBufs], (uint32_t)((l / kTBufs) & 1), a.status, kDrain);
       }
+      if (lead && kL3 && w_last >= 0) mbar_drain(&sm->w2_full[0], (uint32_t)(w_last & 1), a.status, kDrain);
       if (lead && it > 0) {
         const uint32_t last = it - 1;
         for (uint32_t j = (last + 1 > (uint32_t)a.stages ? last + 1 - a.stages : 0); j <= last; ++j)
@@ -322,46 +397,85 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
     if (lane == 0 && lead) {
       // ---------------- MMA issuer (even CTA) ----------------
       const uint32_t idesc1 = instr_desc(2 * kPM, kNT, F8 ? 0u : 1u);
-      const uint32_t idesc2 = instr_desc(2 * kPM, NL, 1u);
+      const uint32_t idesc2 = instr_desc(2 * kPM, kN2, 1u);
+      const uint32_t idesc3 = instr_desc(2 * kPM, NL, 1u);
       auto commit_both = [&](uint64_t* bar) {
         mma2_commit(map_to(bar, 0u));
         mma2_commit(map_to(bar, 1u));
       };
-      // layer 2 of the tile with local index j (global index tj) is ready when both
-      // CTAs wrote its activations and both W2 halves landed
+      // layer 2 of the tile with local index j is ready when both CTAs wrote its activations and both W2
+      // halves landed (and, separate logits, both epilogues read the logits of the tile before in the half)
       auto l2_ready = [&](int j) -> bool {
-        const int tbj = j % kTBufs;
-        const uint32_t tu = (uint32_t)(j / kTBufs) & 1u;
-        return mbar_test_wait(&sm->a2_full[j & 1], (uint32_t)(j >> 1) & 1u) && mbar_test_wait(&sm->w2_full[tbj], tu) &&
+        return mbar_test_wait(&sm->a2_full[j & 1], (uint32_t)(j >> 1) & 1u) &&
+               mbar_test_wait(&sm->w2_full[w_buf(j)], w_phase(j)) &&
                (kShared || mbar_test_wait(&sm->l2_empty[j & 1], ((uint32_t)(j >> 1) & 1u) ^ 1u));
       };
       auto layer2 = [&](int j, int s_valid) -> bool {
         const int bj = j & 1;
-        const int tbj = j % kTBufs;
-        const uint32_t tu = (uint32_t)(j / kTBufs) & 1u;
+        const int wbj = w_buf(j);
         if (!wait(&sm->a2_full[bj], (uint32_t)(j >> 1) & 1u, 2u)) return false;
-        if (!wait(&sm->w2_full[tbj], tu, 2u)) return false;
+        if (!wait(&sm->w2_full[wbj], w_phase(j), 2u)) return false;
         if (!kShared && !wait(&sm->l2_empty[bj], ((uint32_t)(j >> 1) & 1u) ^ 1u, 2u)) return false;
         tc_fence_after();
         const uint32_t half = tmem_base + (uint32_t)(bj * 256);
         for (int s = 0; s < s_valid; ++s) {
-          const uint32_t w2 = smem_u32(w2s + ((size_t)tbj * S + s) * kW2Bytes);
+          const uint32_t w2 = smem_u32(w2s + ((size_t)wbj * S + s) * kWSpark);
 #pragma unroll
           for (int kk = 0; kk < H1 / 16; ++kk) {
             const uint32_t b_addr = w2 + (uint32_t)((kk * 16) / 64) * kW2AtomBytes + (uint32_t)((kk * 16) % 64) * 2u;
-            mma2_bf16_ta(half + col_lg(s), half + col_h(s) + (uint32_t)(kk * 8), smem_desc(b_addr), idesc2,
+            mma2_bf16_ta(half + col_l2(s), half + col_h(s) + (uint32_t)(kk * 8), smem_desc(b_addr), idesc2,
                          kk > 0 ? 1u : 0u);
           }
         }
         commit_both(&sm->l2_full[bj]);
         if (!kShared) mma2_commit(map_to(&sm->tmem_empty[bj], 0u));
-        commit_both(&sm->tail_empty[tbj]);
+        if (!kL3) commit_both(&sm->tail_empty[j % kTBufs]);
+        return true;
+      };
+      // three layers: layer 3 (the logits) once both CTAs packed the second-layer activations
+      auto layer3 = [&](int j, int s_valid) -> bool {
+        const int bj = j & 1;
+        if (!wait(&sm->a3_full[bj], (uint32_t)(j >> 1) & 1u, 2u)) return false;
+        tc_fence_after();
+        const uint32_t half = tmem_base + (uint32_t)(bj * 256);
+        for (int s = 0; s < s_valid; ++s) {
+          const uint32_t w3 = smem_u32(w2s + (size_t)s * kWSpark + kW2Bytes);
+#pragma unroll
+          for (int kk = 0; kk < H2 / 16; ++kk) {
+            const uint32_t b_addr = w3 + (uint32_t)((kk * 16) / 64) * kW3AtomBytes + (uint32_t)((kk * 16) % 64) * 2u;
+            mma2_bf16_ta(half + col_lg(s), half + col_l2(s) + (uint32_t)(kk * 8), smem_desc(b_addr), idesc3,
+                         kk > 0 ? 1u : 0u);
+          }
+        }
+        commit_both(&sm->l3_full[bj]);
+        commit_both(&sm->w2_empty);
+        commit_both(&sm->tail_empty[j % kTBufs]);
         return true;
       };
       uint32_t it = 0;
       int local = 0;
       bool ok = true;
-      int pend = -1, pend_sv = 0;  // the tile whose layer 2 is not issued yet, and its spark count
+      // the tile whose later layers are not all issued yet, its spark count, and its next layer (2 or 3)
+      int pend = -1, pend_sv = 0, pend_layer = 2;
+      // issue the pending tile's next layers: those that are ready, or (block) all of them
+      auto advance = [&](bool block) -> bool {
+        if (pend < 0) return true;
+        if (pend_layer == 2) {
+          if (!block && !l2_ready(pend)) return true;
+          if (!layer2(pend, pend_sv)) return false;
+          if (!kL3) {
+            pend = -1;
+            return true;
+          }
+          pend_layer = 3;
+        }
+        if constexpr (kL3) {
+          if (!block && !mbar_test_wait(&sm->a3_full[pend & 1], (uint32_t)(pend >> 1) & 1u)) return true;
+          if (!layer3(pend, pend_sv)) return false;
+        }
+        pend = -1;
+        return true;
+      };
       int cur = 0;
       for (int t = pair; t < tiles && ok; t += npairs, ++local) {
         const int lt = member_at(t, cur);
@@ -373,12 +487,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
         const uint32_t d_tmem = tmem_base + (uint32_t)(b * 256);
         const int n_pairs = (m.n_full + 1) / 2;
         for (int kb = 0; kb < m.n_steps; ++kb, ++it) {
-          if (pend >= 0 && l2_ready(pend)) {
-            if (!layer2(pend, pend_sv)) {
-              ok = false;
-              break;
-            }
-            pend = -1;
+          if (!advance(false)) {
+            ok = false;
+            break;
           }
           const int st = (int)(it % (uint32_t)a.stages);
           const uint32_t ph = (it / (uint32_t)a.stages) & 1u;
@@ -411,14 +522,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
         }
         if (!ok) break;
         commit_both(&sm->tmem_full[b]);
-        if (pend >= 0 && !layer2(pend, pend_sv)) {
+        if (!advance(true)) {
           ok = false;
           break;
         }
         pend = local;
+        pend_layer = 2;
         pend_sv = min(S, m.count - (lt / m.m_pairs) * S);
       }
-      if (ok && pend >= 0) layer2(pend, pend_sv);
+      if (ok) advance(true);
       // every issued MMA completes before TMEM is released: one more commit, bounded wait
       mma2_commit(map_to(&sm->mma_done, 0u));
       mbar_drain(&sm->mma_done, 0u, a.status);
@@ -436,7 +548,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
     for (int t = pair; t < tiles; t += npairs, ++local) {
       const int lt = member_at(t, cur);
       const PairArgs& m = args_of(cur);
-      const float sc = m.scale;
       const int mt = lt % m.m_pairs, nt = lt / m.m_pairs;
       const int b = local & 1;
       const uint32_t use = (uint32_t)(local >> 1);
@@ -452,30 +563,26 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
       tc_fence_after();
       const float* tail = tails + (size_t)tb * S * kTailF;
       const uint32_t hbase = lane_base + (uint32_t)(b * 256);
-      // act(h * scale + b1) as packed BF16 into the spark's first h1/2 columns: layer 2's A operand.
-      // Chunk j0 writes columns [j0/2, j0/2 + 8), whose accumulators were read by this or an earlier chunk.
-      if (grp < s_valid) {
-        const int s = grp;
-        const float* b1 = tail + (size_t)s * kTailF;
-#pragma unroll 1
-        for (int j0 = 0; j0 < H1; j0 += 16) {
-          float h[16];
-          tmem_ld16(hbase + col_h(s) + (uint32_t)j0, h);
-          tmem_wait_ld();
-          uint32_t pk[8];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const float2 bb = *reinterpret_cast<const float2*>(b1 + j0 + 2 * q);
-            pk[q] = pack_bf16x2(act_f(m.act, fmaf(h[2 * q], sc, bb.x)), act_f(m.act, fmaf(h[2 * q + 1], sc, bb.y)));
-          }
-          tmem_st8u(hbase + col_h(s) + (uint32_t)(j0 / 2), pk);
-        }
-      }
+      // act(h * scale + b1) as packed BF16 into the spark's first h1/2 columns: layer 2's A operand
+      if (grp < s_valid)
+        pack_layer<H1>(hbase + col_h(grp), hbase + col_h(grp), tail + (size_t)grp * kTailF, m.scale, m.act);
       tmem_wait_st();
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(map_to(&sm->a2_full[b], 0u));
       ok = wait(&sm->l2_full[b], use & 1u, 4u);
+      if constexpr (kL3) {
+        // act(layer 2 + b2) packed in place: layer 3's A operand
+        if (epi_bar_any<kEpi>(!ok || sm->abort_flag)) break;
+        tc_fence_after();
+        if (grp < s_valid)
+          pack_layer<H2>(hbase + col_l2(grp), hbase + col_l2(grp), tail + (size_t)grp * kTailF + H1, 1.0f, m.act2);
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(map_to(&sm->a3_full[b], 0u));
+        ok = wait(&sm->l3_full[b], use & 1u, 4u);
+      }
       if (epi_bar_any<kEpi>(!ok || sm->abort_flag)) break;
       tc_fence_after();
       // read this warp's logits, then give their columns back before the loss math
@@ -490,7 +597,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
       if (lane == 0) mbar_arrive_cluster(map_to(kShared ? &sm->tmem_empty[b] : &sm->l2_empty[b], 0u));
       if (grp < s_valid) {
         const int s = grp;
-        const float* b2 = tail + (size_t)s * kTailF + H1;
+        const float* bl = tail + (size_t)s * kTailF + H1 + H2;
         float ce = 0.0f;
         if (valid_row) {
           const int C = m.C;
@@ -499,7 +606,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
 #pragma unroll
           for (int c = 0; c < NL; ++c) {
             if (c < C) {
-              z[c] += b2[c];
+              z[c] += bl[c];
               zmax = fmaxf(zmax, z[c]);
               if (c == label) zy = z[c];
             }
@@ -541,12 +648,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
   }
 }
 
-template <int H1, int NL, int S, bool F8>
+template <int H1, int H2, int NL, int S, bool F8>
 cudaError_t launch_pair(const TcPlan& plan, const PairArgs& args, cudaStream_t s, bool prepare_only, int* pairs_out,
                         const PairMember* members, int32_t n_members, int32_t group_tiles) {
-  cudaError_t e = ensure_smem_limit<k_fitness_pair<H1, NL, S, F8, false>>(plan.smem_bytes);
+  cudaError_t e = ensure_smem_limit<k_fitness_pair<H1, H2, NL, S, F8, false>>(plan.smem_bytes);
   if (e != cudaSuccess) return e;
-  e = ensure_smem_limit<k_fitness_pair<H1, NL, S, F8, true>>(plan.smem_bytes);
+  e = ensure_smem_limit<k_fitness_pair<H1, H2, NL, S, F8, true>>(plan.smem_bytes);
   if (e != cudaSuccess) return e;
   if (prepare_only) {
     // pairs that fit at once (one CTA per SM): the persistent grid
@@ -556,7 +663,8 @@ cudaError_t launch_pair(const TcPlan& plan, const PairArgs& args, cudaStream_t s
       cfg.blockDim = dim3(pair_threads(S));
       cfg.dynamicSmemBytes = plan.smem_bytes;
       int n = 0;
-      if (cudaOccupancyMaxActiveClusters(&n, k_fitness_pair<H1, NL, S, F8, false>, &cfg) != cudaSuccess || n < 1) {
+      if (cudaOccupancyMaxActiveClusters(&n, k_fitness_pair<H1, H2, NL, S, F8, false>, &cfg) != cudaSuccess ||
+          n < 1) {
         cudaGetLastError();
         n = plan.num_sms / 2;
       }
@@ -566,28 +674,36 @@ cudaError_t launch_pair(const TcPlan& plan, const PairArgs& args, cudaStream_t s
   }
   if (members) {
     const int pairs = group_tiles < plan.pairs ? group_tiles : plan.pairs;
-    return launch_pdl(k_fitness_pair<H1, NL, S, F8, true>, dim3(2 * pairs), dim3(pair_threads(S)), plan.smem_bytes,
-                      s, plan.tmap_x3, plan.tmap_x, plan.tmap_wk, plan.tmap_w, plan.tmap_w2b, args, members,
-                      n_members);
+    return launch_pdl(k_fitness_pair<H1, H2, NL, S, F8, true>, dim3(2 * pairs), dim3(pair_threads(S)),
+                      plan.smem_bytes, s, plan.tmap_x3, plan.tmap_x, plan.tmap_wk, plan.tmap_w, plan.tmap_w2b,
+                      plan.tmap_w3b, args, members, n_members);
   }
   const int tiles = args.m_pairs * args.n_tiles;
   const int pairs = tiles < plan.pairs ? tiles : plan.pairs;
-  return launch_pdl(k_fitness_pair<H1, NL, S, F8, false>, dim3(2 * pairs), dim3(pair_threads(S)), plan.smem_bytes, s,
-                    plan.tmap_x3, plan.tmap_x, plan.tmap_wk, plan.tmap_w, plan.tmap_w2b, args,
-                    static_cast<const PairMember*>(nullptr), 0);
+  return launch_pdl(k_fitness_pair<H1, H2, NL, S, F8, false>, dim3(2 * pairs), dim3(pair_threads(S)),
+                    plan.smem_bytes, s, plan.tmap_x3, plan.tmap_x, plan.tmap_wk, plan.tmap_w, plan.tmap_w2b,
+                    plan.tmap_w3b, args, static_cast<const PairMember*>(nullptr), 0);
 }
 
-// The kernel instance of the plan: h1, the logit rows, the tile shape (shared or separate logits) and the
-// operand type.
-cudaError_t dispatch_pair(const TcPlan& plan, int h1, int nl, const PairArgs& a, cudaStream_t s, bool prep,
+// The kernel instance of the plan: h1 (and h2), the logit rows, the tile shape (shared or separate logits)
+// and the operand type.
+cudaError_t dispatch_pair(const TcPlan& plan, const Mlp& mlp, const PairArgs& a, cudaStream_t s, bool prep,
                           int* pairs_out, const PairMember* members = nullptr, int32_t n_members = 0,
                           int32_t group_tiles = 0) {
+  const int h1 = mlp.widths[1], h2 = mlp.n_layers == 3 ? mlp.widths[2] : 0;
+  const int nl = tc_pair_logit_rows(mlp.widths[mlp.n_layers]);
+  if (h2 > 0) {
+    if (h1 != 128 || h2 != 64 || nl != 16 || plan.sparks_per_tile != pair_sparks_shared(128))
+      return cudaErrorInvalidValue;
+    return plan.f8 ? launch_pair<128, 64, 16, 2, true>(plan, a, s, prep, pairs_out, members, n_members, group_tiles)
+                   : launch_pair<128, 64, 16, 2, false>(plan, a, s, prep, pairs_out, members, n_members, group_tiles);
+  }
   const bool shared = plan.sparks_per_tile == pair_sparks_shared(h1);
   if (!shared && plan.sparks_per_tile != pair_sparks_separate(h1, nl)) return cudaErrorInvalidValue;
   const int key = h1 * 8 + (nl == 32 ? 4 : 0) + (shared ? 2 : 0) + (plan.f8 ? 1 : 0);
-#define MG_PAIR(H, L, SH, F)                                                                                      \
-  launch_pair<H, L, SH ? pair_sparks_shared(H) : pair_sparks_separate(H, L), F>(plan, a, s, prep, pairs_out, members, \
-                                                                                 n_members, group_tiles)
+#define MG_PAIR(H, L, SH, F)                                                                                    \
+  launch_pair<H, 0, L, SH ? pair_sparks_shared(H) : pair_sparks_separate(H, L), F>(plan, a, s, prep, pairs_out, \
+                                                                                    members, n_members, group_tiles)
 #define MG_PAIR_CASES(H, L, NLK)                                   \
   case H * 8 + NLK + 0: return MG_PAIR(H, L, false, false);        \
   case H * 8 + NLK + 1: return MG_PAIR(H, L, false, true);         \
@@ -609,6 +725,7 @@ PairArgs make_args(const TcPlan& plan, const Mlp& mlp, int64_t first, const floa
                    float scale, float* partial, uint32_t* status) {
   PairArgs a = {};
   const int S = plan.sparks_per_tile;
+  const bool l3 = mlp.n_layers == 3;
   a.count = count;
   a.first_spark = (int32_t)first;
   a.m_pairs = (int32_t)((mlp.N + 2 * kPM - 1) / (2 * kPM));
@@ -623,14 +740,16 @@ PairArgs make_args(const TcPlan& plan, const Mlp& mlp, int64_t first, const floa
     a.n_steps = (a.n_full + 1) / 2 + (rem > 0 ? 1 : 0);
   }
   a.stages = plan.stages;
-  a.C = mlp.widths[2];
+  a.C = mlp.widths[mlp.n_layers];
   a.act = mlp.acts[0];
+  a.act2 = l3 ? mlp.acts[1] : 0;
   a.c_pad = (a.C + 3) / 4 * 4;
   a.scale = scale;
   a.N = mlp.N;
   a.ld = ld;
   a.b1_off = mlp.b_off[0];
-  a.b2_off = mlp.b_off[1];
+  a.b2_off = l3 ? mlp.b_off[1] : 0;
+  a.bl_off = mlp.b_off[mlp.n_layers - 1];
   a.rows = rows;
   a.y = mlp.y;
   a.partial = partial;
@@ -642,20 +761,31 @@ PairArgs make_args(const TcPlan& plan, const Mlp& mlp, int64_t first, const floa
 }  // namespace
 
 bool tc_pair_supported(const int32_t* widths, int n_layers) {
-  if (n_layers != 2 || widths[0] % 8 != 0) return false;
-  return (widths[1] == 64 || widths[1] == 128) && widths[2] >= 2 && widths[2] <= 32;
+  if (widths[0] % 8 != 0) return false;
+  if (n_layers == 2) return (widths[1] == 64 || widths[1] == 128) && widths[2] >= 2 && widths[2] <= 32;
+  return n_layers == 3 && widths[1] == 128 && widths[2] == 64 && widths[3] >= 2 && widths[3] <= 16;
 }
 
 int tc_pair_logit_rows(int C) { return C <= 16 ? 16 : 32; }
 
-int tc_pair_sparks(int h1, int C, bool shared) {
-  return shared ? pair_sparks_shared(h1) : pair_sparks_separate(h1, tc_pair_logit_rows(C));
+int tc_pair_w2_rows(const int32_t* widths, int n_layers) {
+  return n_layers == 3 ? widths[2] : tc_pair_logit_rows(widths[2]);
 }
 
-size_t tc_pair_fixed_smem(int h1, int C, int S) {
-  const int nl = tc_pair_logit_rows(C);
-  const size_t w2 = (size_t)kTBufs * S * (h1 / 64) * (nl / 2) * 128;
-  const size_t tails = sizeof(float) * ((size_t)kTBufs * S * (h1 + 32) + 4 * (size_t)S);
+int tc_pair_sparks(const Mlp& mlp, bool shared) {
+  const int h1 = mlp.widths[1];
+  if (mlp.n_layers == 3) return shared ? pair_sparks_shared(h1) : 0;
+  return shared ? pair_sparks_shared(h1) : pair_sparks_separate(h1, tc_pair_logit_rows(mlp.widths[2]));
+}
+
+size_t tc_pair_fixed_smem(const Mlp& mlp, int S) {
+  const int h1 = mlp.widths[1], h2 = mlp.n_layers == 3 ? mlp.widths[2] : 0;
+  const int nl = tc_pair_logit_rows(mlp.widths[mlp.n_layers]);
+  // W2 (and W3) halves of every spark of a tile, per buffer (three buffers for two layers, one for three)
+  const size_t w_spark = h2 > 0 ? (size_t)(h1 / 64) * (h2 / 2) * 128 + (size_t)(h2 / 64) * (nl / 2) * 128
+                                : (size_t)(h1 / 64) * (nl / 2) * 128;
+  const size_t w2 = (size_t)(h2 > 0 ? 1 : kTBufs) * S * w_spark;
+  const size_t tails = sizeof(float) * ((size_t)kTBufs * S * (h1 + h2 + 32) + 4 * (size_t)S);
   return 1024 + w2 + tails + 16 + sizeof(PairSmem) + 64;
 }
 
@@ -663,8 +793,8 @@ size_t tc_pair_stage_bytes(int h1, int S) { return 2 * ((size_t)kPM * kRowB + (s
 
 int tc_pair_max_stages() { return kMaxStg; }
 
-int tc_pair_stages_fit(int h1, int C, int S, size_t limit) {
-  const size_t fixed = tc_pair_fixed_smem(h1, C, S), stage = tc_pair_stage_bytes(h1, S);
+int tc_pair_stages_fit(const Mlp& mlp, int S, size_t limit) {
+  const size_t fixed = tc_pair_fixed_smem(mlp, S), stage = tc_pair_stage_bytes(mlp.widths[1], S);
   int st = kMaxStg;
   while (st >= 2 && fixed + (size_t)st * stage > limit) --st;
   return st >= 2 ? st : 0;
@@ -673,7 +803,7 @@ int tc_pair_stages_fit(int h1, int C, int S, size_t limit) {
 int launch_fitness_pair(const TcPlan& plan, const Mlp& mlp, int64_t first, const float* rows, int64_t ld,
                         int32_t count, float scale, float* partial, uint32_t* status, cudaStream_t s) {
   const PairArgs a = make_args(plan, mlp, first, rows, ld, count, scale, partial, status);
-  return dispatch_pair(plan, mlp.widths[1], tc_pair_logit_rows(a.C), a, s, false, nullptr) == cudaSuccess ? 1 : -1;
+  return dispatch_pair(plan, mlp, a, s, false, nullptr) == cudaSuccess ? 1 : -1;
 }
 
 void tc_pair_member(const TcPlan& plan, const Mlp& mlp, int64_t first, const float* rows, int64_t ld, int32_t count,
@@ -683,14 +813,16 @@ void tc_pair_member(const TcPlan& plan, const Mlp& mlp, int64_t first, const flo
   out->w3 = plan.tmap_wk;
   out->w = plan.tmap_w;
   out->w2 = plan.tmap_w2b;
+  out->wl3 = plan.tmap_w3b;
   out->a = make_args(plan, mlp, first, rows, ld, count, scale, partial, status);
   out->tiles = out->a.m_pairs * out->a.n_tiles;
   out->tile_start = 0;
 }
 
 bool tc_pair_same_instance(const TcPlan& a, const Mlp& ma, const TcPlan& b, const Mlp& mb) {
+  if (ma.n_layers != mb.n_layers || (ma.n_layers == 3 && ma.widths[2] != mb.widths[2])) return false;
   return a.ready && b.ready && a.pair && b.pair && a.f8 == b.f8 && ma.widths[1] == mb.widths[1] &&
-         tc_pair_logit_rows(ma.widths[2]) == tc_pair_logit_rows(mb.widths[2]) &&
+         tc_pair_logit_rows(ma.widths[ma.n_layers]) == tc_pair_logit_rows(mb.widths[mb.n_layers]) &&
          a.sparks_per_tile == b.sparks_per_tile;
 }
 
@@ -701,8 +833,7 @@ int launch_fitness_pair_group(const TcPlan& plan, const Mlp& mlp, const PairMemb
   a.stages = plan.stages;
   a.status = status;
   a.wait_budget = plan.wait_budget;
-  return dispatch_pair(plan, mlp.widths[1], tc_pair_logit_rows(mlp.widths[2]), a, s, false, nullptr, table_dev, n,
-                       total_tiles) == cudaSuccess
+  return dispatch_pair(plan, mlp, a, s, false, nullptr, table_dev, n, total_tiles) == cudaSuccess
              ? 1
              : -1;
 }
@@ -710,7 +841,7 @@ int launch_fitness_pair_group(const TcPlan& plan, const Mlp& mlp, const PairMemb
 cudaError_t tc_pair_prepare(TcPlan& plan, const Mlp& mlp) {
   PairArgs a = {};
   int pairs = 0;
-  cudaError_t e = dispatch_pair(plan, mlp.widths[1], tc_pair_logit_rows(mlp.widths[2]), a, nullptr, true, &pairs);
+  cudaError_t e = dispatch_pair(plan, mlp, a, nullptr, true, &pairs);
   if (e == cudaSuccess) plan.pairs = pairs;
   return e;
 }

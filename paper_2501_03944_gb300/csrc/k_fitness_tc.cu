@@ -572,13 +572,13 @@ namespace {
 // The pair plan's tile shape: S sparks per tile, `stages` pipeline stages, and the first-layer operand's
 // maps, whose box is half a tile's rows.
 mgfwa_status pair_shape(TcPlan& plan, const Mlp& mlp, int S, int stages) {
-  const int h1 = mlp.widths[1], d_in = mlp.widths[0], C = mlp.widths[2];
+  const int h1 = mlp.widths[1], d_in = mlp.widths[0];
   const int esize = plan.f8 ? 1 : 2, bk = kRowBytes / esize;
   const CUtensorMapDataType dt = plan.f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   plan.sparks_per_tile = S;
   plan.n_tile = S * h1;
   plan.stages = stages;
-  plan.smem_bytes = tc_pair_fixed_smem(h1, C, S) + (size_t)stages * tc_pair_stage_bytes(h1, S);
+  plan.smem_bytes = tc_pair_fixed_smem(mlp, S) + (size_t)stages * tc_pair_stage_bytes(h1, S);
   {
     // first-layer operand [max_rows*h1][d_in], box (one 128-byte row of K) x half a tile's rows
     cuuint64_t dims[2] = {(cuuint64_t)d_in, (cuuint64_t)plan.w_rows};
@@ -637,8 +637,9 @@ mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const OpDesc& op, const float
     plan.w_base = op.base;
     plan.w_rows = max_rows * h1;
     const int nl = tc_pair_logit_rows(C);
-    if (op.w2_rows != nl || op.w2_h1 != h1) {
-      g_err = "pair kernel: the BF16 W2 copy has the wrong shape";
+    const int w2r = tc_pair_w2_rows(mlp.widths, mlp.n_layers);
+    if (op.w2_rows != w2r || op.w2_h1 != h1 || (l3 && (!op.w3 || op.w3_rows != nl || op.w3_k != h2))) {
+      g_err = "pair kernel: the BF16 W2 / W3 copies have the wrong shape";
       return MGFWA_EINVAL;
     }
     {
@@ -659,17 +660,26 @@ mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const OpDesc& op, const float
       if (!encode(&plan.tmap_x3, dt, 3, mlp.Xop, dx, sx, bx)) return MGFWA_ECUDA;
     }
     {
-      // BF16 W2 [max_rows][nl][h1], box 64 x nl/2 x 1 (one CTA's half of the logit rows, one K atom)
-      cuuint64_t dims[3] = {(cuuint64_t)h1, (cuuint64_t)nl, (cuuint64_t)max_rows};
-      cuuint64_t strides[2] = {(cuuint64_t)h1 * 2, (cuuint64_t)nl * h1 * 2};
-      cuuint32_t box[3] = {64, (cuuint32_t)(nl / 2), 1};
+      // BF16 W2 [max_rows][w2r][h1], box 64 x w2r/2 x 1 (one CTA's half of the rows, one K atom)
+      cuuint64_t dims[3] = {(cuuint64_t)h1, (cuuint64_t)w2r, (cuuint64_t)max_rows};
+      cuuint64_t strides[2] = {(cuuint64_t)h1 * 2, (cuuint64_t)w2r * h1 * 2};
+      cuuint32_t box[3] = {64, (cuuint32_t)(w2r / 2), 1};
       if (!encode(&plan.tmap_w2b, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, op.w2, dims, strides, box)) return MGFWA_ECUDA;
+    }
+    if (l3) {
+      // BF16 W3 [max_rows][nl][h2], box 64 x nl/2 x 1
+      cuuint64_t dims[3] = {(cuuint64_t)h2, (cuuint64_t)nl, (cuuint64_t)max_rows};
+      cuuint64_t strides[2] = {(cuuint64_t)h2 * 2, (cuuint64_t)nl * h2 * 2};
+      cuuint32_t box[3] = {64, (cuuint32_t)(nl / 2), 1};
+      if (!encode(&plan.tmap_w3b, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, op.w3, dims, strides, box)) return MGFWA_ECUDA;
+    } else {
+      plan.tmap_w3b = plan.tmap_w2b;  // unused by the two-layer kernels
     }
     plan.tmap_w2 = plan.tmap_w2b;  // unused by the pair kernel
     plan.tmap_w3 = plan.tmap_w2b;
     // the default shape: the logits in the sparks' own columns, the deepest pipeline that fits
-    const int S = tc_pair_sparks(h1, C, true);
-    const int stages = tc_pair_stages_fit(h1, C, S, (size_t)prop.sharedMemPerBlockOptin);
+    const int S = tc_pair_sparks(mlp, true);
+    const int stages = tc_pair_stages_fit(mlp, S, (size_t)prop.sharedMemPerBlockOptin);
     if (stages < 2) {
       g_err = "shared memory too small for the tensor-core pair tiles";
       return MGFWA_EINVAL;
@@ -785,8 +795,8 @@ cudaError_t tc_prepare(TcPlan& plan, const Mlp& mlp) {
 
 mgfwa_status tc_pair_configure(TcPlan& plan, const Mlp& mlp, int sparks_per_tile, int stages) {
   if (!plan.ready || !plan.pair) return MGFWA_EINVAL;
-  const int h1 = mlp.widths[1], C = mlp.widths[2];
-  if (sparks_per_tile != tc_pair_sparks(h1, C, true) && sparks_per_tile != tc_pair_sparks(h1, C, false)) {
+  if (sparks_per_tile <= 0 ||
+      (sparks_per_tile != tc_pair_sparks(mlp, true) && sparks_per_tile != tc_pair_sparks(mlp, false))) {
     g_err = "pair kernel: no tile of that many sparks for this network";
     return MGFWA_EINVAL;
   }
@@ -796,7 +806,7 @@ mgfwa_status tc_pair_configure(TcPlan& plan, const Mlp& mlp, int sparks_per_tile
     g_err = "device query failed";
     return MGFWA_ECUDA;
   }
-  if (stages < 2 || stages > tc_pair_stages_fit(h1, C, sparks_per_tile, (size_t)limit)) {
+  if (stages < 2 || stages > tc_pair_stages_fit(mlp, sparks_per_tile, (size_t)limit)) {
     g_err = "pair kernel: that pipeline depth does not fit in shared memory";
     return MGFWA_EINVAL;
   }
@@ -832,15 +842,17 @@ mgfwa_status tc_pair_tune(TcPlan& plan, const Mlp& mlp, const float* rows, int64
     cudaGetLastError();
     return MGFWA_OK;
   }
-  const int h1 = mlp.widths[1], C = mlp.widths[2];
   int dev = 0, limit = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
     g_err = "device query failed";
     return MGFWA_ECUDA;
   }
-  const std::array<int64_t, 7> key = {dev, plan.f8 ? 1 : 0, mlp.widths[0], h1, C, pow2_at_least((mlp.N + 255) / 256),
-                                      pow2_at_least(count)};
+  // the network: d_in, then the hidden widths and classes packed (each below 2^16)
+  int64_t net = 0;
+  for (int l = 1; l <= mlp.n_layers; ++l) net = (net << 16) | mlp.widths[l];
+  const std::array<int64_t, 7> key = {dev, plan.f8 ? 1 : 0, mlp.widths[0], net, mlp.n_layers,
+                                      pow2_at_least((mlp.N + 255) / 256), pow2_at_least(count)};
   std::lock_guard<std::mutex> lock(g_tune_mu);
   auto hit = g_tuned.find(key);
   if (hit != g_tuned.end()) {
@@ -851,9 +863,9 @@ mgfwa_status tc_pair_tune(TcPlan& plan, const Mlp& mlp, const float* rows, int64
   // the candidates: both tile shapes, every depth from two to the deepest that fits
   std::vector<std::pair<int, int>> cand;
   for (bool shared : {true, false}) {
-    const int S = tc_pair_sparks(h1, C, shared);
-    if (!shared && S == tc_pair_sparks(h1, C, true)) continue;
-    const int fit = tc_pair_stages_fit(h1, C, S, (size_t)limit);
+    const int S = tc_pair_sparks(mlp, shared);
+    if (S <= 0 || (!shared && S == tc_pair_sparks(mlp, true))) continue;
+    const int fit = tc_pair_stages_fit(mlp, S, (size_t)limit);
     for (int st = 2; st <= fit; ++st) cand.emplace_back(S, st);
   }
   if (cand.empty()) return MGFWA_OK;

@@ -62,16 +62,25 @@ __device__ __forceinline__ void store_op4(const OpDesc& op, int64_t row, int64_t
     store_bf16x4(reinterpret_cast<__nv_bfloat16*>(base) + row * op.w1_elems + d0, a, b, c, d);
 }
 
-// Coordinates [d0, d0 + 4) of row `row` into the BF16 copy of W2 when they
-// lie in W2 (h1 is a multiple of 4 and W2 starts on a multiple of 4, so the
-// four never straddle two rows of W2).
+// Coordinates [d0, d0 + 4) of row `row` into a BF16 copy of one weight
+// matrix [classes][k] (at coordinate `off` of a spark row; `row_elems` per
+// spark in the copy) when they lie in it (k is a multiple of 4 and the
+// matrix starts on a multiple of 4, so the four never straddle two of its
+// rows).
+__device__ __forceinline__ void store_copy4(void* copy, int64_t off, int32_t k, int32_t classes, int64_t row_elems,
+                                            int64_t row, int64_t d0, float a, float b, float c, float d) {
+  const int64_t e = d0 - off;
+  if (e < 0 || e >= (int64_t)classes * k) return;
+  const int64_t cls = e / k;
+  const int64_t j = e - cls * k;
+  store_bf16x4(static_cast<__nv_bfloat16*>(copy) + row * row_elems + cls * k + j, a, b, c, d);
+}
+
+// The BF16 copies of W2 and W3 (where the descriptor has them).
 __device__ __forceinline__ void store_w2_4(const OpDesc& op, int64_t row, int64_t d0, float a, float b, float c,
                                            float d) {
-  const int64_t e = d0 - op.w2_off;
-  if (e < 0 || e >= (int64_t)op.w2_classes * op.w2_h1) return;
-  const int64_t cls = e / op.w2_h1;
-  const int64_t j = e - cls * op.w2_h1;
-  store_bf16x4(static_cast<__nv_bfloat16*>(op.w2) + row * op.w2_row_elems() + cls * op.w2_h1 + j, a, b, c, d);
+  store_copy4(op.w2, op.w2_off, op.w2_h1, op.w2_classes, op.w2_row_elems(), row, d0, a, b, c, d);
+  if (op.w3) store_copy4(op.w3, op.w3_off, op.w3_k, op.w3_classes, op.w3_row_elems(), row, d0, a, b, c, d);
 }
 
 // grid (coordinate blocks, B * mu): global firework z = b * mu + i (Philox
@@ -285,17 +294,20 @@ __global__ void k_to_operand(const float* __restrict__ rows, int64_t ld, const O
   const int row = blockIdx.y;
   const int64_t d0 = ((int64_t)blockIdx.x * kThreads + threadIdx.x) * 4;
   const bool in_w1 = d0 < op.w1_elems;
-  const bool in_w2 = op.w2 && d0 >= op.w2_off && d0 < op.w2_off + (int64_t)op.w2_classes * op.w2_h1;
+  const bool in_w2 = (op.w2 && d0 >= op.w2_off && d0 < op.w2_off + (int64_t)op.w2_classes * op.w2_h1) ||
+                     (op.w3 && d0 >= op.w3_off && d0 < op.w3_off + (int64_t)op.w3_classes * op.w3_k);
   if (!in_w1 && !in_w2) return;
   const float4 v = *reinterpret_cast<const float4*>(rows + (int64_t)row * ld + d0);
   if (in_w1) store_op4(op, row, d0, v.x, v.y, v.z, v.w);
   if (in_w2) store_w2_4(op, row, d0, v.x, v.y, v.z, v.w);
 }
 
-// Coordinates k_to_operand covers: the first-layer block, and W2 when copied.
+// Coordinates k_to_operand covers: the first-layer block, and W2 (and W3) when copied.
 inline int64_t op_span(const OpDesc& op) {
-  const int64_t w2_end = op.w2 ? op.w2_off + (int64_t)op.w2_classes * op.w2_h1 : 0;
-  return op.w1_elems > w2_end ? op.w1_elems : w2_end;
+  int64_t end = op.w1_elems;
+  if (op.w2 && op.w2_off + (int64_t)op.w2_classes * op.w2_h1 > end) end = op.w2_off + (int64_t)op.w2_classes * op.w2_h1;
+  if (op.w3 && op.w3_off + (int64_t)op.w3_classes * op.w3_k > end) end = op.w3_off + (int64_t)op.w3_classes * op.w3_k;
+  return end;
 }
 
 __global__ void k_f32_to_op(const float* __restrict__ src, int64_t n, int32_t kind, float inv, void* dst) {

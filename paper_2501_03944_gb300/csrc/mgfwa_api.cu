@@ -51,7 +51,9 @@ struct mgfwa_handle {
   float* sparks = nullptr;  // [P][Dp]: explosion rows, then guiding rows
   void* op = nullptr;            // [P][w1_elems] first-layer operand (BF16 or E4M3)
   void* w2op = nullptr;          // [P][w2_rows][h1] BF16 W2 for the CTA-pair fitness kernel, or null
-  int32_t w2_rows = 0;           // 16 or 32 (rows C.. are zero)
+  int32_t w2_rows = 0;           // 16 or 32 (rows C.. are zero), or h2 with three layers
+  void* w3op = nullptr;          // [P][w3_rows][h2] BF16 W3 for the three-layer CTA-pair kernel, or null
+  int32_t w3_rows = 0;           // 16 (rows C.. are zero)
   int32_t op_kind = kOpNone;
   float inv_x = 1.0f, inv_w = 1.0f;  // E4M3: stored = E4M3(value * inv)
   float op_scale = 1.0f;             // layer-1 accumulator multiplier: 1 / (inv_x inv_w)
@@ -271,6 +273,13 @@ OpDesc op_rows(const mgfwa_t* h, int64_t first) {
     d.w2_h1 = h->mlp.widths[1];
     d.w2_classes = h->mlp.widths[2];
     d.w2_rows = h->w2_rows;
+  }
+  if (h->op && h->w3op) {
+    d.w3 = h->w3op;
+    d.w3_off = h->mlp.w_off[2];
+    d.w3_k = h->mlp.widths[2];
+    d.w3_classes = h->mlp.widths[3];
+    d.w3_rows = h->w3_rows;
   }
   return d.from(first);
 }
@@ -829,8 +838,11 @@ size_t carve_all(mgfwa_t* h, char* base) {
   h->sparks = carve<float>(cur, h->PA * p.Dp);
   h->op = want_op ? carve<uint8_t>(cur, h->PA * mlp.w1_elems * esize) : nullptr;
   // the CTA-pair fitness kernel reads W2 as BF16 from its own copy
-  h->w2_rows = want_op && tc_pair_supported(mlp.widths, mlp.n_layers) ? tc_pair_logit_rows(mlp.widths[2]) : 0;
+  const bool pair = want_op && tc_pair_supported(mlp.widths, mlp.n_layers);
+  h->w2_rows = pair ? tc_pair_w2_rows(mlp.widths, mlp.n_layers) : 0;
   h->w2op = h->w2_rows ? carve<uint16_t>(cur, h->PA * h->w2_rows * mlp.widths[1]) : nullptr;
+  h->w3_rows = pair && mlp.n_layers == 3 ? tc_pair_logit_rows(mlp.widths[3]) : 0;
+  h->w3op = h->w3_rows ? carve<uint16_t>(cur, h->PA * h->w3_rows * mlp.widths[2]) : nullptr;
   h->fit = carve<float>(cur, h->PA);
   h->partial = carve<float>(cur, (size_t)h->mtiles * h->PA);
   h->top = carve<int32_t>(cur, F * p.m * p.k);
@@ -981,6 +993,9 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
   if (h->w2op &&
       cudaMemsetAsync(h->w2op, 0, sizeof(uint16_t) * h->PA * h->w2_rows * h->mlp.widths[1], h->stream) != cudaSuccess)
     return bail(cuda_fail(h, "clear the W2 copy"));
+  if (h->w3op &&
+      cudaMemsetAsync(h->w3op, 0, sizeof(uint16_t) * h->PA * h->w3_rows * h->mlp.widths[2], h->stream) != cudaSuccess)
+    return bail(cuda_fail(h, "clear the W3 copy"));
   if (want_op) {
     st = tc_plan(h->tc, h->mlp, op_rows(h, 0), h->sparks, p.Dp, h->PA);
     if (st != MGFWA_OK) {

@@ -68,9 +68,11 @@ struct NetOut {
 // The first-layer GEMM operand the samplers write beside the FP32 rows:
 // row r holds the spark's first w1_elems coordinates ([h1][d_in] row-major)
 // as BF16, or as E4M3 of (coordinate * inv_scale) with saturation.
-// With w2 set (the CTA-pair kernel's two-layer networks) the samplers also
-// store each spark's second-layer weights W2 [C][h1] as BF16, row r at
-// w2 + r * w2_rows * h1 ([w2_rows][h1], rows C..w2_rows-1 kept zero).
+// With w2 set (the CTA-pair kernel's networks) the samplers also store each
+// spark's second-layer weights W2 [classes][h1] as BF16, row r at
+// w2 + r * w2_rows * h1 ([w2_rows][h1], rows classes..w2_rows-1 kept zero;
+// classes = C for two layers, h2 for three), and with w3 set (three layers)
+// W3 [C][h2] the same way at w3 + r * w3_rows * h2.
 enum { kOpNone = 0, kOpBf16 = 1, kOpFp8 = 2 };
 struct OpDesc {
   void* base = nullptr;  // row 0
@@ -80,15 +82,22 @@ struct OpDesc {
   void* w2 = nullptr;     // BF16 W2 of row 0, or null
   int64_t w2_off = 0;     // coordinate of W2[0][0] in a spark row
   int32_t w2_h1 = 0;      // h1 (elements per W2 row)
-  int32_t w2_classes = 0; // C (W2 rows the samplers write)
-  int32_t w2_rows = 0;    // W2 rows per spark in the buffer (16 or 32)
+  int32_t w2_classes = 0; // W2 rows the samplers write (C, or h2 with three layers)
+  int32_t w2_rows = 0;    // W2 rows per spark in the buffer
+  void* w3 = nullptr;     // BF16 W3 of row 0, or null
+  int64_t w3_off = 0;     // coordinate of W3[0][0] in a spark row
+  int32_t w3_k = 0;       // h2 (elements per W3 row)
+  int32_t w3_classes = 0; // C
+  int32_t w3_rows = 0;    // W3 rows per spark in the buffer (16)
   __host__ __device__ int64_t row_bytes() const { return w1_elems * (kind == kOpFp8 ? 1 : 2); }
   __host__ __device__ int64_t w2_row_elems() const { return (int64_t)w2_rows * w2_h1; }
+  __host__ __device__ int64_t w3_row_elems() const { return (int64_t)w3_rows * w3_k; }
   // the descriptor of rows [first, ...)
   OpDesc from(int64_t first) const {
     OpDesc d = *this;
     if (base) d.base = static_cast<uint8_t*>(base) + first * row_bytes();
     if (w2) d.w2 = static_cast<uint16_t*>(w2) + first * w2_row_elems();
+    if (w3) d.w3 = static_cast<uint16_t*>(w3) + first * w3_row_elems();
     return d;
   }
 };

@@ -122,3 +122,27 @@ def test_mixed_batch_group(pkg):
         with _make(pkg, w, 100 + k, p, {}) as alone:
             alone.run()
             _same(got, _state(pkg, alone))
+
+
+def test_group_three_layer_pair_members(pkg):
+    """Three members on the three-layer CTA-pair kernel (3072-128-64-10): one grouped fitness launch serves
+    all of them (batches of 300, 512 and 700 samples; an odd spark count per launch in one, and E4M3 in
+    another, which runs on its own branch), and each ends bitwise where it ends alone."""
+    base = W.scaled(W.MLP_3072_128_64_10, n_fireworks=2, sparks_per_firework=12, guiding_per_firework=4,
+                    eval_budget=W.budget_for_generations(2, 12, 4, 4))
+    specs = [
+        (W.scaled(base, n_samples=300), 41, pkg.MGFWA_BF16, {}),
+        (W.scaled(base, n_samples=512, n_fireworks=3, sparks_per_firework=8,
+                  eval_budget=W.budget_for_generations(3, 8, 4, 3)), 42, pkg.MGFWA_BF16, {"elite_rescore": 0}),
+        (W.scaled(base, n_samples=700), 43, pkg.MGFWA_BF16, {"n_runs": 2}),
+        (W.scaled(base, n_samples=512), 44, pkg.MGFWA_FP8, {"elite_rescore": 0}),
+    ]
+    members = [_make(pkg, *sp) for sp in specs]
+    with pkg.Group(members) as g:
+        g.run()
+    for h, sp in zip(members, specs):
+        got = _state(pkg, h)
+        h.close()
+        with _make(pkg, *sp) as alone:
+            alone.run()
+            _same(got, _state(pkg, alone))

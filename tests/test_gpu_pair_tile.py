@@ -9,7 +9,9 @@ every shape, so every shape and depth must give bitwise the same fitness:
 the creation-time tuner that picks the fastest changes no result.  Checked
 on whole runs (fireworks, best, the last generation's explosion and
 guiding fitness) over the networks the kernel has: h1 = 64 and 128, 16 and
-32 logit rows, d_in ending on a K atom or not, BF16 and E4M3 operands."""
+32 logit rows, d_in ending on a K atom or not, BF16 and E4M3 operands, and
+the three-layer 3072-128-64-10 network (whose tile is always the shared
+shape: only the depth varies)."""
 import numpy as np
 import pytest
 
@@ -35,6 +37,10 @@ def _cases(pkg):
         ("200-64-20 bf16", W.scaled(base, widths=(200, 64, 20)), pkg.MGFWA_BF16, {}),
         ("256-128-10 bf16", W.scaled(base, widths=(256, 128, 10), acts=(0,)), pkg.MGFWA_BF16, {}),
         ("784-64-10 fp8", base, pkg.MGFWA_FP8, {"elite_rescore": 0}),
+        ("3072-128-64-10 bf16", W.scaled(base, widths=(3072, 128, 64, 10), acts=(1, 1), n_samples=300,
+                                         sparks_per_firework=12), pkg.MGFWA_BF16, {}),
+        ("3072-128-64-10 fp8", W.scaled(base, widths=(3072, 128, 64, 10), acts=(1, 0), n_samples=520,
+                                        sparks_per_firework=12), pkg.MGFWA_FP8, {"elite_rescore": 0}),
     ]
 
 
@@ -49,13 +55,15 @@ def _state(pkg, h):
 
 
 def _tiles(w):
-    h1, C = w.widths[1], w.widths[2]
+    """The tile shapes the kernel has for the network: (shared, separate or None)."""
+    h1, C = w.widths[1], w.widths[-1]
+    if len(w.widths) == 4:
+        return 256 // h1, None
     nl = 16 if C <= 16 else 32
-    shared, separate = 256 // h1, 256 // (h1 + nl)
-    return shared, separate
+    return 256 // h1, 256 // (h1 + nl)
 
 
-@pytest.mark.parametrize("i", range(5))
+@pytest.mark.parametrize("i", range(7))
 def test_every_tile_gives_the_same_run(pkg, i):
     name, w, prec, kw = _cases(pkg)[i]
     shared, separate = _tiles(w)
@@ -66,7 +74,7 @@ def test_every_tile_gives_the_same_run(pkg, i):
         ref = _state(pkg, h)
     assert ref[-1] >= 2
     tried = []
-    for S in (shared, separate):
+    for S in (shared, separate) if separate else (shared,):
         for st in range(2, 9):
             with _make(pkg, w, 31 + i, prec, kw) as h:
                 try:
@@ -81,14 +89,14 @@ def test_every_tile_gives_the_same_run(pkg, i):
                 assert np.array_equal(a, b), (name, S, st)
             assert got[-1] == ref[-1]
             tried.append((S, st))
-    assert len(tried) >= 3, tried
+    assert len(tried) >= (3 if separate else 2), tried
 
 
 def test_tile_settings_out_of_range(pkg):
     name, w, prec, kw = _cases(pkg)[0]
     shared, separate = _tiles(w)
     with _make(pkg, w, 5, prec, kw) as h:
-        for S, st in ((shared + 1, 2), (separate, 1), (shared, 9)):
+        for S, st in ((shared + 1, 2), (separate, 1), (shared, 9), (0, 2)):
             with pytest.raises(pkg.MgfwaError) as e:
                 h.set_pair_tile(S, st)
             assert e.value.status == pkg.MGFWA_EINVAL
