@@ -117,12 +117,83 @@ __device__ __forceinline__ float signed_u24(uint32_t r) {
 // kThreads Philox blocks (4 coordinates each) of one spark row; each thread
 // takes kExplodeBlocks of them, kThreads apart, so a warp's stores stay
 // contiguous.  Global firework z = b * mu + i, spark row z * lam + j, Philox
-// unit (i + fw_off) * lam + j of run b's stream.  The thread's firework coordinates are
-// loaded first; per Philox block the explosion draw, then -- when any lane
-// of the warp has a coordinate outside [lb, ub] -- the mapping stream's block
-// for the whole warp (a warp-uniform branch), taken only where a lane is out
-// of bounds.
+// unit (i + fw_off) * lam + j of run b's stream.  The thread's firework
+// coordinates are loaded first; per Philox block the explosion draw, then
+// the mapping stream's block for the coordinates outside [lb, ub].  While the
+// firework's amplitude is at least a quarter of the box, nearly every block
+// has such a coordinate and the mapping block is drawn unconditionally (no
+// vote, so the compiler interleaves it with the next block's draw); below
+// that it is drawn only when a lane of the warp needs it (a warp-uniform
+// branch).  The values are the same either way: a mapped value replaces only
+// an out-of-bound coordinate.  Threads whose four blocks all lie inside the
+// row's first D coordinates (all but the row's last few) skip the per-
+// coordinate range checks.  Two more exact shortcuts, each chosen per
+// firework: with symmetric bounds (lb = -ub) a coordinate is out of bounds
+// iff |v| > ub; with an amplitude of at least ub - lb (rounded up), the
+// mapping box of every firework coordinate (fireworks lie inside the bounds)
+// is the whole of [lb, ub], so the mapped value is lb + u (ub - lb).
 constexpr int kExplodeBlocks = 4;
+
+template <bool kAlwaysMap, bool kFull, bool kSym, bool kBox>
+__device__ __forceinline__ void explode_blocks(const Problem& p, const PhiloxKeys& rk, uint32_t unit, uint32_t gen,
+                                               float amp, uint32_t c0, const float* __restrict__ xrow,
+                                               float* __restrict__ srow, const OpDesc& op, uint32_t row,
+                                               uint8_t* op_row, __nv_bfloat16* op_row16) {
+  const float lb = p.lb, ub = p.ub;
+  const uint32_t n4 = (uint32_t)(p.Dp / 4);
+  const uint32_t full4 = (uint32_t)(p.D / 4);  // blocks whose 4 coordinates are all < D
+  const uint32_t D = (uint32_t)p.D;
+  const uint32_t w1e = (uint32_t)op.w1_elems;
+  const uint32_t w2lo = (uint32_t)op.w2_off, w2len = (uint32_t)(op.w2_classes * op.w2_h1);
+  const uint32_t w3lo = (uint32_t)op.w3_off, w3len = (uint32_t)(op.w3_classes * op.w3_k);
+  float4 x4[kExplodeBlocks];
+#pragma unroll
+  for (int h = 0; h < kExplodeBlocks; ++h) {
+    const uint32_t c4 = c0 + (uint32_t)h * kThreads;
+    x4[h] = (kFull || c4 < n4) ? *reinterpret_cast<const float4*>(xrow + (size_t)c4 * 4)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int h = 0; h < kExplodeBlocks; ++h) {
+    const uint32_t c4 = c0 + (uint32_t)h * kThreads;
+    const bool live = kFull || c4 < n4;
+    const uint32_t d0 = c4 * 4u;
+    const uint4 r = philox4x32_10(make_uint4(c4, unit, gen, kExplode), rk);
+    float v[4];
+    bool oob[4];
+    bool any = false;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      v[l] = __fmaf_rn(amp, signed_u24(lane_of(r, l)), lane_of(x4[h], l));
+      oob[l] = kSym ? fabsf(v[l]) > ub : (v[l] < lb || v[l] > ub);
+      if (!kFull) oob[l] = oob[l] && live && (c4 < full4 || d0 + (uint32_t)l < D);
+      any |= oob[l];
+    }
+    if (kAlwaysMap || __any_sync(0xffffffffu, any)) {
+      const uint4 r2 = philox4x32_10(make_uint4(c4, unit, gen, kMap), rk);
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const float m = kBox ? __fmaf_rn(u24(lane_of(r2, l)), __fsub_rn(ub, lb), lb)
+                             : map_coord(lane_of(x4[h], l), amp, lb, ub, u24(lane_of(r2, l)));
+        v[l] = oob[l] ? m : v[l];
+      }
+    }
+    if (!live) continue;
+    if (!kFull && c4 >= full4) {
+#pragma unroll
+      for (int l = 0; l < 4; ++l)
+        if (d0 + (uint32_t)l >= D) v[l] = 0.0f;
+    }
+    *reinterpret_cast<float4*>(srow + d0) = make_float4(v[0], v[1], v[2], v[3]);
+    if (d0 < w1e) {
+      if (op.kind == kOpBf16)
+        store_bf16x4(op_row16 + d0, v[0], v[1], v[2], v[3]);
+      else if (op.kind == kOpFp8)
+        store_fp8x4(op_row + d0, op.inv_scale, v[0], v[1], v[2], v[3]);
+    }
+    if (d0 - w2lo < w2len || d0 - w3lo < w3len) store_w2_4(op, row, d0, v[0], v[1], v[2], v[3]);
+  }
+}
 
 __global__ void __launch_bounds__(kThreads) k_explode(Problem p, const uint32_t* __restrict__ gens_done,
                                                       const float* __restrict__ fw_x,
@@ -139,52 +210,26 @@ __global__ void __launch_bounds__(kThreads) k_explode(Problem p, const uint32_t*
   run_key(p, (int)b, k0, k1);
   const PhiloxKeys rk = philox_keys(k0, k1);  // shared by the thread's Philox blocks
   const float amp = fw_amp[z];
-  const float lb = p.lb, ub = p.ub;
   const float* xrow = fw_x + (size_t)z * (size_t)p.Dp;
   float* srow = sparks + (size_t)row * (size_t)p.Dp;
-  const uint32_t n4 = (uint32_t)(p.Dp / 4);
-  const uint32_t full4 = (uint32_t)(p.D / 4);  // blocks whose 4 coordinates are all < D
-  const uint32_t D = (uint32_t)p.D;
+  uint8_t* op_row = op.kind == kOpNone ? nullptr : static_cast<uint8_t*>(op.base) + (size_t)row * op.row_bytes();
+  __nv_bfloat16* op_row16 = reinterpret_cast<__nv_bfloat16*>(op_row);
   const uint32_t c0 = blockIdx.x * (uint32_t)(kExplodeBlocks * kThreads) + threadIdx.x;
-  float4 x4[kExplodeBlocks];
-#pragma unroll
-  for (int h = 0; h < kExplodeBlocks; ++h) {
-    const uint32_t c4 = c0 + (uint32_t)h * kThreads;
-    x4[h] = c4 < n4 ? *reinterpret_cast<const float4*>(xrow + (size_t)c4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-#pragma unroll
-  for (int h = 0; h < kExplodeBlocks; ++h) {
-    const uint32_t c4 = c0 + (uint32_t)h * kThreads;
-    const bool live = c4 < n4;
-    const uint32_t d0 = c4 * 4u;
-    const uint4 r = philox4x32_10(make_uint4(c4, unit, gen, kExplode), rk);
-    float v[4];
-    bool oob[4];
-    bool any = false;
-#pragma unroll
-    for (int l = 0; l < 4; ++l) {
-      v[l] = __fmaf_rn(amp, signed_u24(lane_of(r, l)), lane_of(x4[h], l));
-      oob[l] = live && (v[l] < lb || v[l] > ub) && (c4 < full4 || d0 + (uint32_t)l < D);
-      any |= oob[l];
-    }
-    if (__any_sync(0xffffffffu, any)) {
-      const uint4 r2 = philox4x32_10(make_uint4(c4, unit, gen, kMap), rk);
-#pragma unroll
-      for (int l = 0; l < 4; ++l) {
-        const float m = map_coord(lane_of(x4[h], l), amp, lb, ub, u24(lane_of(r2, l)));
-        v[l] = oob[l] ? m : v[l];
-      }
-    }
-    if (!live) continue;
-    if (c4 >= full4) {
-#pragma unroll
-      for (int l = 0; l < 4; ++l)
-        if (d0 + (uint32_t)l >= D) v[l] = 0.0f;
-    }
-    *reinterpret_cast<float4*>(srow + d0) = make_float4(v[0], v[1], v[2], v[3]);
-    if (op.kind != kOpNone && d0 < (uint32_t)op.w1_elems) store_op4(op, row, d0, v[0], v[1], v[2], v[3]);
-    if (op.w2) store_w2_4(op, row, d0, v[0], v[1], v[2], v[3]);
-  }
+  const bool full = c0 + (uint32_t)((kExplodeBlocks - 1) * kThreads) < (uint32_t)(p.D / 4);
+  const bool always_map = __fmul_rn(4.0f, amp) >= __fsub_rn(p.ub, p.lb);
+  const bool box = amp >= __fsub_ru(p.ub, p.lb);
+  const bool sym = p.lb == -p.ub;
+#define MG_EXPLODE(A, F, SY, BX) explode_blocks<A, F, SY, BX>(p, rk, unit, gen, amp, c0, xrow, srow, op, row, op_row, \
+                                                               op_row16)
+  if (!full)
+    MG_EXPLODE(false, false, false, false);
+  else if (box)
+    sym ? MG_EXPLODE(true, true, true, true) : MG_EXPLODE(true, true, false, true);
+  else if (always_map)
+    sym ? MG_EXPLODE(true, true, true, false) : MG_EXPLODE(true, true, false, false);
+  else
+    sym ? MG_EXPLODE(false, true, true, false) : MG_EXPLODE(false, true, false, false);
+#undef MG_EXPLODE
 }
 
 // Multi-guiding sparks, reading: group q of firework i has ranked index

@@ -101,6 +101,33 @@ def test_generation_phase_by_phase(pkg, name):
         assert run.info().evals == w.n_fireworks + 3 * w.sparks_per_generation
 
 
+@pytest.mark.parametrize("w", [
+    W.scaled(W.MLP_8_16_3, lb=-2.0, ub=3.0, n_fireworks=5),
+    W.scaled(W.MLP_784_64_10, n_samples=64, n_fireworks=5, sparks_per_firework=8, guiding_per_firework=2),
+    W.scaled(W.MLP_784_64_10, n_samples=64, n_fireworks=5, sparks_per_firework=8, guiding_per_firework=2,
+             lb=-0.5, ub=1.5),
+], ids=["8-16-3_bounds_-2_3", "784-64-10", "784-64-10_bounds_-0.5_1.5"])
+def test_explosion_across_amplitude_regimes(pkg, w):
+    """Explosion sparks bit-exact for amplitudes from 1% of the box to beyond it (the sampler's mapping is
+    drawn only where a warp needs it, always, or as the whole-box draw), symmetric and asymmetric bounds, rows
+    shorter than one thread's coordinates and rows much longer."""
+    seed = 77
+    X, y, prob, p = _setup(w, seed)
+    with pkg.Mgfwa.for_workload(w, seed, X=X, y=y) as run:
+        fw_x, _ = oracle.init(p, seed)
+        width = np.float32(w.ub) - np.float32(w.lb)
+        fw_a = (np.array([0.01, 0.3, 0.9, 1.0, 1.7], np.float32) * width).astype(np.float32)
+        fw_f = prob.fitness_many(fw_x).astype(np.float32)
+        run.write(pkg.MGFWA_BUF_FW_AMP, fw_a)
+        run.write(pkg.MGFWA_BUF_FW_F, fw_f)
+        ref = oracle.generation(p, prob, seed, 1, fw_x, fw_a, fw_f)
+        run.phase(pkg.MGFWA_PHASE_EXPLODE)
+        got = run.read(pkg.MGFWA_BUF_SPARKS)
+    assert np.array_equal(got, ref["sparks"])
+    inside = got[:, :w.dim]
+    assert np.all(inside >= np.float32(w.lb)) and np.all(inside <= np.float32(w.ub))
+
+
 def test_rank_and_select_with_ties_and_nan(pkg):
     w = W.scaled(W.MLP_8_16_3, n_samples=64, n_fireworks=3, sparks_per_firework=24, guiding_per_firework=3)
     seed = 77
