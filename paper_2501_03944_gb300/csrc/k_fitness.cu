@@ -147,6 +147,91 @@ __global__ void __launch_bounds__(kThreads) k_fitness_simt(Mlp mlp, const float*
   }
 }
 
+// Small two-layer networks (d_in = DI, h1 = H1, C classes, all compile-time):
+// one block = 128 samples (one per thread, its inputs in registers) x up to
+// kSmallSparks sparks, whose rows are staged in shared memory and read as
+// broadcasts.  Each hidden unit is accumulated over the inputs in ascending
+// order from zero, then the bias is added and the activation applied, and
+// each logit starts from its bias and accumulates the hidden units in
+// ascending order: the same operations in the same order as k_fitness_simt,
+// so both kernels give bitwise the same fitness.  The block's cross-entropy
+// sum per spark goes to partial[mt][row] (warp sums added in warp order, as
+// there).
+constexpr int kSmallSparks = 8;
+
+template <int DI, int H1, int C>
+__global__ void __launch_bounds__(kMT) k_fitness_small(Mlp mlp, const float* __restrict__ rows, int64_t ld,
+                                                       int32_t count, const int32_t* __restrict__ idx,
+                                                       float* __restrict__ partial) {
+  constexpr int D = DI * H1 + H1 + C * H1 + C;   // parameters per spark (nn.Linear order)
+  constexpr int kB1 = DI * H1, kW2 = kB1 + H1, kB2 = kW2 + C * H1;
+  __shared__ float ws[kSmallSparks][D];
+  __shared__ float red[kSmallSparks][kMT / 32];
+  griddep_wait();
+  griddep_launch_dependents();
+  const int s0 = blockIdx.x * kSmallSparks, mt = blockIdx.y;
+  const int gs = min(kSmallSparks, count - s0);
+  for (int e = threadIdx.x; e < gs * D; e += kMT) {
+    const int g = e / D, k = e - g * D;
+    const int r = s0 + g;
+    ws[g][k] = rows[(int64_t)(idx != nullptr ? idx[r] : r) * ld + k];
+  }
+  const int64_t n = (int64_t)mt * kMT + threadIdx.x;
+  const bool valid = n < mlp.N;
+  float x[DI];
+#pragma unroll
+  for (int i = 0; i < DI; ++i) x[i] = valid ? mlp.X[n * DI + i] : 0.0f;
+  const int label = valid ? mlp.y[n] : 0;
+  const int act = mlp.acts[0];
+  __syncthreads();
+  for (int g = 0; g < gs; ++g) {
+    const float* W = ws[g];
+    float z[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) z[c] = W[kB2 + c];
+#pragma unroll
+    for (int j = 0; j < H1; ++j) {
+      float a = 0.0f;
+#pragma unroll
+      for (int i = 0; i < DI; ++i) a = fmaf(x[i], W[j * DI + i], a);
+      a = act_f(act, a + W[kB1 + j]);
+#pragma unroll
+      for (int c = 0; c < C; ++c) z[c] = fmaf(W[kW2 + c * H1 + j], a, z[c]);
+    }
+    float ce = 0.0f;
+    if (valid) {
+      float zmax = z[0];
+#pragma unroll
+      for (int c = 1; c < C; ++c) zmax = fmaxf(zmax, z[c]);
+      float se = 0.0f;
+#pragma unroll
+      for (int c = 0; c < C; ++c) se += expf(z[c] - zmax);
+      float zy = z[0];
+#pragma unroll
+      for (int c = 1; c < C; ++c) zy = label == c ? z[c] : zy;
+      ce = (zmax + logf(se)) - zy;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) ce += __shfl_xor_sync(0xffffffffu, ce, off);
+    if ((threadIdx.x & 31) == 0) red[g][threadIdx.x >> 5] = ce;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < gs) {
+    float v = red[threadIdx.x][0];
+#pragma unroll
+    for (int wi = 1; wi < kMT / 32; ++wi) v += red[threadIdx.x][wi];
+    partial[(int64_t)mt * count + s0 + threadIdx.x] = v;
+  }
+}
+
+// True if the network is one that k_fitness_small is instantiated for, with
+// the parameter layout it assumes.
+bool small_net(const Mlp& mlp, int di, int h1, int c) {
+  return mlp.n_layers == 2 && mlp.widths[0] == di && mlp.widths[1] == h1 && mlp.widths[2] == c &&
+         mlp.w_off[0] == 0 && mlp.b_off[0] == (int64_t)di * h1 && mlp.w_off[1] == mlp.b_off[0] + h1 &&
+         mlp.b_off[1] == mlp.w_off[1] + (int64_t)c * h1;
+}
+
 __global__ void k_fitness_finish(const float* __restrict__ partial, int32_t mtiles, int32_t count, float n_f,
                                  const int32_t* __restrict__ idx, float* __restrict__ fit) {
   griddep_wait();
@@ -287,9 +372,16 @@ int launch_fitness_finish(const float* partial, int32_t mtiles, int32_t count, i
 int launch_fitness_simt_main(const Mlp& mlp, const float* rows, int64_t ld, int32_t count, float* partial,
                              cudaStream_t s, const int32_t* idx) {
   if (count <= 0) return 0;
+  const int mtiles = (int)((mlp.N + kMT - 1) / kMT);
+  if (small_net(mlp, 8, 16, 3)) {
+    dim3 grid((count + kSmallSparks - 1) / kSmallSparks, mtiles);
+    return launch_pdl(k_fitness_small<8, 16, 3>, grid, dim3(kMT), 0, s, mlp, rows, ld, count, idx, partial) ==
+                   cudaSuccess
+               ? 1
+               : -1;
+  }
   const size_t smem = smem_for(mlp);
   if (ensure_smem_limit<k_fitness_simt>(smem) != cudaSuccess) return -1;
-  const int mtiles = (int)((mlp.N + kMT - 1) / kMT);
   dim3 grid(count, mtiles);
   return launch_pdl(k_fitness_simt, grid, dim3(kThreads), smem, s, mlp, rows, ld, count, idx, partial) == cudaSuccess
              ? 1
