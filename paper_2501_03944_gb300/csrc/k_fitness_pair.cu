@@ -139,23 +139,29 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 }
 
 // act(acc * sc + bias) of `n` accumulator columns of this warp's lanes, from
-// column `src`, as packed BF16 pairs into the columns from `dst` (dst <= src:
-// chunk j0 writes [dst + j0/2, dst + j0/2 + 8), which this or an earlier
-// chunk has read).
+// column `src`, as packed BF16 pairs into the columns from `dst` (dst <= src).
+// Sixteen columns are loaded with one wait, then packed and stored: a group
+// writes [dst + g/2, dst + g/2 + 8) for the group at src + g, columns that
+// this or an earlier group has read.
 template <int n>
 __device__ __forceinline__ void pack_layer(uint32_t src, uint32_t dst, const float* bias, float sc, int act) {
+  constexpr int kG = n < 16 ? n : 16;
 #pragma unroll 1
-  for (int j0 = 0; j0 < n; j0 += 16) {
-    float h[16];
-    tmem_ld16(src + (uint32_t)j0, h);
-    tmem_wait_ld();
-    uint32_t pk[8];
+  for (int g = 0; g < n; g += kG) {
+    float h[kG];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const float2 bb = *reinterpret_cast<const float2*>(bias + j0 + 2 * q);
-      pk[q] = pack_bf16x2(act_f(act, fmaf(h[2 * q], sc, bb.x)), act_f(act, fmaf(h[2 * q + 1], sc, bb.y)));
+    for (int j0 = 0; j0 < kG; j0 += 16) tmem_ld16(src + (uint32_t)(g + j0), h + j0);
+    tmem_wait_ld();
+#pragma unroll
+    for (int j0 = 0; j0 < kG; j0 += 16) {
+      uint32_t pk[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float2 bb = *reinterpret_cast<const float2*>(bias + g + j0 + 2 * q);
+        pk[q] = pack_bf16x2(act_f(act, fmaf(h[j0 + 2 * q], sc, bb.x)), act_f(act, fmaf(h[j0 + 2 * q + 1], sc, bb.y)));
+      }
+      tmem_st8u(dst + (uint32_t)((g + j0) / 2), pk);
     }
-    tmem_st8u(dst + (uint32_t)(j0 / 2), pk);
   }
 }
 
@@ -543,8 +549,62 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
     const int et = threadIdx.x - 64;    // 0 .. 32 kEpi - 1
     const int row_in_tile = quad * 32 + lane;
     const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16);
+    // Tiles are pipelined by one: a tile's logits are read into registers and its TMEM half handed back
+    // at once, and its loss is taken during the next tile, between packing that tile's activations and
+    // waiting for its logits, so the loss math overlaps the MMAs of the next tile's later layers.
+    float zp[NL];
+    struct Prev {
+      bool on;
+      bool valid_row;
+      int label, cur, mt, s0, s_valid, tb;
+    } prev = {false, false, 0, 0, 0, 0, 0, 0};
+    // the loss of the tile in `prev` (its logits in zp): per-sample CE, the warp's sum per spark, the
+    // tile's partial sums
+    auto finish = [&]() {
+      const PairArgs& m = args_of(prev.cur);
+      const float* tail = tails + (size_t)prev.tb * S * kTailF;
+      if (grp < prev.s_valid) {
+        const int s = grp;
+        const float* bl = tail + (size_t)s * kTailF + H1 + H2;
+        float ce = 0.0f;
+        if (prev.valid_row) {
+          const int C = m.C;
+          float zmax = -INFINITY;
+          float zy = 0.0f;
+#pragma unroll
+          for (int c = 0; c < NL; ++c) {
+            if (c < C) {
+              zp[c] += bl[c];
+              zmax = fmaxf(zmax, zp[c]);
+              if (c == prev.label) zy = zp[c];
+            }
+          }
+          // the fast exponential and logarithm (a few units in the last place: far inside the BF16 / E4M3
+          // operands' error)
+          float se = 0.0f;
+#pragma unroll
+          for (int c = 0; c < NL; ++c)
+            if (c < C) se += __expf(zp[c] - zmax);
+          ce = (zmax + __logf(se)) - zy;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) ce += __shfl_xor_sync(0xffffffffu, ce, off);
+        if (lane == 0) red[s * 4 + quad] = ce;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm->tail_empty[prev.tb]);
+      epi_bar<kEpi>();
+      const int m128 = prev.mt * 2 + (int)rank;
+      if (et < prev.s_valid && m128 < m.m_tiles) {
+        const int s = et;
+        const float v = ((red[s * 4 + 0] + red[s * 4 + 1]) + red[s * 4 + 2]) + red[s * 4 + 3];
+        m.partial[(int64_t)m128 * m.count + prev.s0 + s] = v;
+      }
+      prev.on = false;
+    };
     int local = 0;
     int cur = 0;
+    bool aborted = false;
     for (int t = pair; t < tiles; t += npairs, ++local) {
       const int lt = member_at(t, cur);
       const PairArgs& m = args_of(cur);
@@ -559,7 +619,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
       const int tb = local % kTBufs;
       bool ok = wait(&sm->tmem_full[b], use & 1u, 4u);
       ok = ok && wait(&sm->bias_full[tb], (uint32_t)(local / kTBufs) & 1u, 4u);
-      if (epi_bar_any<kEpi>(!ok || sm->abort_flag)) break;
+      if (epi_bar_any<kEpi>(!ok || sm->abort_flag)) {
+        aborted = true;
+        break;
+      }
       tc_fence_after();
       const float* tail = tails + (size_t)tb * S * kTailF;
       const uint32_t hbase = lane_base + (uint32_t)(b * 256);
@@ -570,10 +633,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(map_to(&sm->a2_full[b], 0u));
+      if (prev.on) finish();
       ok = wait(&sm->l2_full[b], use & 1u, 4u);
       if constexpr (kL3) {
         // act(layer 2 + b2) packed in place: layer 3's A operand
-        if (epi_bar_any<kEpi>(!ok || sm->abort_flag)) break;
+        if (epi_bar_any<kEpi>(!ok || sm->abort_flag)) {
+          aborted = true;
+          break;
+        }
         tc_fence_after();
         if (grp < s_valid)
           pack_layer<H2>(hbase + col_l2(grp), hbase + col_l2(grp), tail + (size_t)grp * kTailF + H1, 1.0f, m.act2);
@@ -583,54 +650,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
         if (lane == 0) mbar_arrive_cluster(map_to(&sm->a3_full[b], 0u));
         ok = wait(&sm->l3_full[b], use & 1u, 4u);
       }
-      if (epi_bar_any<kEpi>(!ok || sm->abort_flag)) break;
+      if (epi_bar_any<kEpi>(!ok || sm->abort_flag)) {
+        aborted = true;
+        break;
+      }
       tc_fence_after();
-      // read this warp's logits, then give their columns back before the loss math
-      float z[NL];
+      // read this warp's logits, then give their columns back; the loss follows during the next tile
       if (grp < s_valid) {
 #pragma unroll
-        for (int q = 0; q < NL; q += 16) tmem_ld16(hbase + col_lg(grp) + (uint32_t)q, z + q);
+        for (int q = 0; q < NL; q += 16) tmem_ld16(hbase + col_lg(grp) + (uint32_t)q, zp + q);
       }
       tmem_wait_ld();
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(map_to(kShared ? &sm->tmem_empty[b] : &sm->l2_empty[b], 0u));
-      if (grp < s_valid) {
-        const int s = grp;
-        const float* bl = tail + (size_t)s * kTailF + H1 + H2;
-        float ce = 0.0f;
-        if (valid_row) {
-          const int C = m.C;
-          float zmax = -INFINITY;
-          float zy = 0.0f;
-#pragma unroll
-          for (int c = 0; c < NL; ++c) {
-            if (c < C) {
-              z[c] += bl[c];
-              zmax = fmaxf(zmax, z[c]);
-              if (c == label) zy = z[c];
-            }
-          }
-          float se = 0.0f;
-#pragma unroll
-          for (int c = 0; c < NL; ++c)
-            if (c < C) se += expf(z[c] - zmax);
-          ce = (zmax + logf(se)) - zy;
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) ce += __shfl_xor_sync(0xffffffffu, ce, off);
-        if (lane == 0) red[s * 4 + quad] = ce;
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sm->tail_empty[tb]);
-      epi_bar<kEpi>();
-      const int m128 = mt * 2 + (int)rank;
-      if (et < s_valid && m128 < m.m_tiles) {
-        const int s = et;
-        const float v = ((red[s * 4 + 0] + red[s * 4 + 1]) + red[s * 4 + 2]) + red[s * 4 + 3];
-        m.partial[(int64_t)m128 * m.count + s0 + s] = v;
-      }
+      prev = {true, valid_row, label, cur, mt, s0, s_valid, tb};
     }
+    if (!aborted && prev.on) finish();
   }
 
   if (sm->abort_flag) {

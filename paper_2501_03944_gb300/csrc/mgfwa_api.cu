@@ -1355,16 +1355,49 @@ mgfwa_status group_fail(mgfwa_group* g, mgfwa_status st, const char* what) {
 
 // Members whose sparks one grouped launch of the CTA-pair fitness kernel
 // can evaluate with the others': an MLP on the pair kernel, the same kernel
-// instance as the first such member.
+// instance as the first such member.  Members of the same network family
+// and operand type whose tuned tile differs are first set to the tile most
+// of them have (every tile gives bitwise the same fitness, and a generation
+// graph a member captured before keeps the kernel and maps it was captured
+// with), so that one launch serves them all.
 std::vector<int> group_fusable(mgfwa_group* g, const std::vector<int>& live) {
-  std::vector<int> out;
-  const mgfwa_t* first = nullptr;
+  std::vector<int> cand;
   for (int i : live) {
     const mgfwa_t* h = g->members[(size_t)i];
-    if (h->kind != MGFWA_OBJ_MLP_CE || !use_tc(h, h->cfg.precision) || !h->tc.pair) continue;
-    if (first && !tc_pair_same_instance(first->tc, first->mlp, h->tc, h->mlp)) continue;
-    if (!first) first = h;
-    out.push_back(i);
+    if (h->kind == MGFWA_OBJ_MLP_CE && use_tc(h, h->cfg.precision) && h->tc.pair) cand.push_back(i);
+  }
+  std::vector<int> out;
+  if (cand.empty()) return out;
+  // the family of the first candidate: the same network layers (h1, h2, logit rows) and operand type
+  const mgfwa_t* h0 = g->members[(size_t)cand[0]];
+  auto same_family = [&](const mgfwa_t* h) {
+    TcPlan a = h0->tc, b = h->tc;
+    b.sparks_per_tile = a.sparks_per_tile;
+    return tc_pair_same_instance(a, h0->mlp, b, h->mlp);
+  };
+  std::vector<int> fam;
+  for (int i : cand)
+    if (same_family(g->members[(size_t)i])) fam.push_back(i);
+  // the tile most of the family has (the first member's on a tie), and a member that has it
+  int best_s = h0->tc.sparks_per_tile, best_n = 0;
+  const mgfwa_t* lead = h0;
+  for (int i : fam) {
+    const mgfwa_t* h = g->members[(size_t)i];
+    int n = 0;
+    for (int k : fam) n += g->members[(size_t)k]->tc.sparks_per_tile == h->tc.sparks_per_tile ? 1 : 0;
+    if (n > best_n) {
+      best_n = n;
+      best_s = h->tc.sparks_per_tile;
+      lead = h;
+    }
+  }
+  for (int i : fam) {
+    mgfwa_t* h = g->members[(size_t)i];
+    if (h->tc.sparks_per_tile != best_s) {
+      if (tc_pair_configure(h->tc, h->mlp, best_s, lead->tc.stages) != MGFWA_OK) continue;  // keeps its own tile
+      h->tc.tuned = 0;
+    }
+    if (tc_pair_same_instance(lead->tc, lead->mlp, h->tc, h->mlp)) out.push_back(i);
   }
   if (out.size() < 2) out.clear();  // a lone member gains nothing from a grouped launch
   return out;
