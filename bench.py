@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -264,7 +265,8 @@ def cpu_baseline(steps: int = 1, warmup: int = 0):
         sparks += n
     dt = time.perf_counter() - t0
     return {"value": sparks / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{steps} oracle generation(s) of 1 of the 5 fireworks ({p1.lam}+{p1.m} sparks each) of "
+            "sample": f"{steps} oracle generation(s) of 1 of the {WORKLOAD.n_fireworks} fireworks ({p1.lam}+{p1.m} "
+                      "sparks each) of "
                       f"{WORKLOAD.name}, FP64 fitness, {threads} threads", "seconds": dt}
 
 
@@ -313,7 +315,9 @@ def _config(args, world):
             "guiding_per_firework": WORKLOAD.guiding_per_firework,
             "sparks_per_generation": WORKLOAD.sparks_per_generation, "runs": world,
             "parallelism": f"independent runs x{world}",
-            "l2": "working set > L2: 203.6 MB FP32 sparks + 101.8 MB BF16 operand rewritten every generation"}
+            "l2": (f"working set > L2: {WORKLOAD.sparks_per_generation * WORKLOAD.dim * 4 / 1e6:.1f} MB FP32 sparks + "
+                   f"{WORKLOAD.sparks_per_generation * WORKLOAD.widths[0] * WORKLOAD.widths[1] * 2 / 1e6:.1f} MB BF16 "
+                   "first-layer operand rewritten every generation")}
 
 
 # ---------------------------------------------------------------------------
@@ -477,18 +481,24 @@ def gpu_arm(args):
                     "peak_source": ("measured fp32 without tensor cores (torch.matmul 4096^3, TF32 off)" if f32 else
                                     "derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x 2070 MHz")}
         roof["frac"] = roof["achieved"] / roof["peak"]
-        roof["traffic"] = (_traffic("k_fitness_pair", "paper_2501_03944_gb300/csrc/k_fitness_pair.cu")
+        tkey = "k_fitness_pair" + ("" if WORKLOAD is W.MLP_784_64_10 else ":" + WORKLOAD.name)
+        roof["traffic"] = (_traffic(tkey, "paper_2501_03944_gb300/csrc/k_fitness_pair.cu")
                            if prec == pkg.MGFWA_BF16 else None)
         roof["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
-        roof["kernel"] = "fitness of the explosion sparks (1000 sparks x 2048 samples per launch)"
+        roof["kernel"] = (f"fitness of the explosion sparks ({n_e} sparks x {WORKLOAD.n_samples} samples per "
+                          "launch)")
         # HBM-bound kernels: algorithmic bytes / time
         D = WORKLOAD.dim
-        w1 = WORKLOAD.widths[0] * WORKLOAD.widths[1]
-        w2 = WORKLOAD.widths[1] * WORKLOAD.widths[2]
-        # operand bytes per spark: the first-layer block (BF16 or E4M3) and the BF16 copy of W2
-        op_b = {pkg.MGFWA_BF16: 2 * w1 + 2 * w2, pkg.MGFWA_FP8: w1 + 2 * w2}.get(prec, 0)
+        wd = WORKLOAD.widths
+        w1 = wd[0] * wd[1]
+        w_later = sum(wd[l] * wd[l + 1] for l in range(1, len(wd) - 1))
+        # operand bytes per spark: the first-layer block (BF16 or E4M3) and the BF16 copies of the later
+        # layers' weights
+        op_b = {pkg.MGFWA_BF16: 2 * w1 + 2 * w_later, pkg.MGFWA_FP8: w1 + 2 * w_later}.get(prec, 0)
         exp_bytes = n_e * (4 * D + op_b)
-        k = 5
+        # rows each guiding spark reads: its top and bottom subsets, k = round(sigma * lambda / m) each
+        g_size = WORKLOAD.sparks_per_firework // WORKLOAD.guiding_per_firework
+        k = max(1, min(int(math.floor(WORKLOAD.sigma * g_size + 0.5)), g_size // 2))
         n_g = WORKLOAD.n_fireworks * WORKLOAD.guiding_per_firework
         guide_bytes = n_g * (2 * k * 4 * D + 4 * D + op_b)
         hbm = {}
@@ -725,7 +735,16 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the FP32 and batched comparison runs")
     ap.add_argument("--serving-full", action="store_true",
                     help="only the serving workload's full 2,000-request window (a few minutes)")
+    ap.add_argument("--workload", default=W.MLP_784_64_10.name,
+                    choices=[w.name for w in (W.MLP_784_64_10, W.MLP_3072_128_64_10)],
+                    help="the timed step's workload (the metric is quoted on the 784-64-10 one)")
+    ap.add_argument("--fireworks", type=int, default=0,
+                    help="override the workload's firework count (smaller profiling captures)")
     args = ap.parse_args()
+    global WORKLOAD
+    WORKLOAD = W.ALL[args.workload]
+    if args.fireworks > 0:
+        WORKLOAD = W.scaled(WORKLOAD, n_fireworks=args.fireworks)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -165,8 +165,13 @@ MGFWA_API mgfwa_status mgfwa_config_init(mgfwa_config* cfg);
  * is a cudaStream_t or NULL (the handle then creates its own).  The device
  * state is one allocation from the library's stream-ordered pool (one per
  * device); memory freed by mgfwa_destroy stays in that pool for later
- * handles.  On success *out is a new handle; on failure *out is NULL and
- * nothing is leaked.  Errors: EINVAL (configuration), ENOMEM, ECUDA. */
+ * handles.  A BF16 or E4M3 handle on the CTA-pair fitness kernel times
+ * that kernel's tile shapes and pipeline depths once per device and
+ * problem shape in the process (a few launches on the handle's stream) and
+ * keeps the fastest; every choice gives bitwise the same fitness, and the
+ * environment variable MGFWA_TUNE=0 keeps the default tile instead.  On
+ * success *out is a new handle; on failure *out is NULL and nothing is
+ * leaked.  Errors: EINVAL (configuration), ENOMEM, ECUDA. */
 MGFWA_API mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, void* cuda_stream,
                           mgfwa_t** out);
 

@@ -40,6 +40,7 @@
 
 #include <cstdio>
 #include <array>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -837,6 +838,9 @@ int64_t pow2_at_least(int64_t v) {
 mgfwa_status tc_pair_tune(TcPlan& plan, const Mlp& mlp, const float* rows, int64_t ld, int32_t count, float scale,
                           float* partial, uint32_t* status, cudaStream_t s) {
   if (!plan.ready || !plan.pair || count <= 0) return MGFWA_OK;
+  // MGFWA_TUNE=0 keeps the default tile (deterministic creation time, reproducible profiles)
+  if (const char* env = std::getenv("MGFWA_TUNE"))
+    if (env[0] == '0' && env[1] == '\0') return MGFWA_OK;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
     cudaGetLastError();
