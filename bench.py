@@ -304,7 +304,8 @@ def testbed_net(pkg, stream, net_id, steps, **handle_kw):
     n = h.info().sparks_per_gen * steps
     h.close()
     sps = n / (t / 1e3)
-    return {"workload": w.name, "value": sps, "unit": UNIT, "ms_per_step": t / steps, "precision": "fp32",
+    prec = {0: "fp32", 3: "fp32x3"}.get(handle_kw.get("precision", 0), str(handle_kw.get("precision")))
+    return {"workload": w.name, "value": sps, "unit": UNIT, "ms_per_step": t / steps, "precision": prec,
             "layer_tflops": sps * w.flops_per_spark() / 1e12}
 
 
@@ -420,6 +421,9 @@ def gpu_arm(args):
                                                                  max(5, args.steps // 2)), precision=args.precision)
         # the paper's own testbed (Sec. 4.1): Table 2's network 10, its output minimised over its input
         extra["testbed_net10"] = testbed_net(pkg, stream, 10, max(5, args.steps // 2))
+        # the same network's layers on the tensor cores at FP32 accuracy (three BF16 parts per operand)
+        extra["testbed_net10_fp32x3"] = testbed_net(pkg, stream, 10, max(5, args.steps // 2),
+                                                    precision=pkg.MGFWA_FP32X3)
         # the same with lagged multi-guiding: the 40 guiding rows ride in the explosion rows' launches
         extra["testbed_net10_lagged"] = dict(testbed_net(pkg, stream, 10, max(5, args.steps // 2),
                                                          lagged_guiding=1), lagged_guiding=1)

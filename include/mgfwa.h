@@ -58,6 +58,10 @@ typedef enum {
   MGFWA_FP8 = 2,  /* tensor cores: E4M3 first layer (X scaled by 448 / max|X|, weights by 448 / max(|lb|, |ub|),
                      the product rescaled before the bias), TF32 later layers, FP32 accumulate; the BF16 shapes
                      with d_in % 16 == 0 */
+  MGFWA_FP32X3 = 3, /* the testbed network objective at FP32 accuracy on the tensor cores: every FP32 operand
+                       split into three BF16 parts, six products per K step into three FP32 accumulators; the
+                       layers with fan_in % 8 == 0 and an even fan_out >= 16 (the others, and the final
+                       1-output layer, on the CUDA cores) */
 } mgfwa_precision;
 
 /* Objectives: the cross-entropy of an MLP whose flattened parameters are the
@@ -146,9 +150,10 @@ typedef struct {
   const float* X;        /* [N][d_in] row-major FP32 (MLP) */
   const int32_t* y;      /* [N] labels in [0, C) (MLP) */
   /* testbed network: its fixed parameters in nn.Linear order (W_1[h][d]
-   * row-major, b_1, W_2, b_2, ...), copied at create; the precision must be
+   * row-major, b_1, W_2, b_2, ...), copied at create; the precision is
    * MGFWA_FP32 (CUDA-core products, FP32 accumulation in an order fixed by
-   * the layer shape alone) */
+   * the layer shape alone) or MGFWA_FP32X3 (tensor-core layers at FP32
+   * accuracy, also in an order fixed by the shape) */
   const float* params;
 } mgfwa_objective;
 
@@ -199,8 +204,9 @@ MGFWA_API mgfwa_status mgfwa_best_run(mgfwa_t* h, int32_t run, float* x_out, dou
 /* Evaluate `count` host vectors (each D floats, row-major) with the
  * handle's objective in the given precision; f_out gets count FP32 values.
  * The precision selects the MLP objective's path (BF16 / FP8 need the
- * handle's own tensor-core precision); the sphere and the testbed network
- * are always FP32.  Uses the handle's device workspace (count <= the sparks
+ * handle's own tensor-core precision) and the testbed network's (FP32 on
+ * the CUDA cores, or FP32X3 on a handle created in FP32X3); the sphere is
+ * always FP32.  Uses the handle's device workspace (count <= the sparks
  * of one generation of all runs) and synchronises.  Only between
  * generations. */
 MGFWA_API mgfwa_status mgfwa_evaluate(mgfwa_t* h, const float* xs, int64_t count, int32_t precision,

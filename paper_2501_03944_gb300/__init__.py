@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmgfwa.so")
 
 MGFWA_OK, MGFWA_EINVAL, MGFWA_ENOMEM, MGFWA_ECUDA, MGFWA_ETIMEOUT, MGFWA_EBUDGET = range(6)
-MGFWA_FP32, MGFWA_BF16, MGFWA_FP8 = 0, 1, 2
+MGFWA_FP32, MGFWA_BF16, MGFWA_FP8, MGFWA_FP32X3 = 0, 1, 2, 3
 MGFWA_OBJ_MLP_CE, MGFWA_OBJ_SPHERE, MGFWA_OBJ_NET_OUTPUT = 0, 1, 2
 MGFWA_ACT_TANH, MGFWA_ACT_RELU, MGFWA_ACT_GELU = 0, 1, 2
 (MGFWA_PHASE_EXPLODE, MGFWA_PHASE_EVAL_E, MGFWA_PHASE_RANK, MGFWA_PHASE_GUIDE, MGFWA_PHASE_EVAL_G,

@@ -52,4 +52,31 @@ bool l1_fp32x3_fuses_output(const Mlp& mlp);
 int launch_l1_fp32x3(const L1Plan& pl, const Mlp& mlp, const int32_t* idx, int32_t R, float* out, uint32_t* status,
                      cudaStream_t s, float* loss = nullptr);
 
+// The testbed network on the tensor cores at FP32 accuracy (three BF16
+// parts per operand, six products, three accumulators).  A layer runs there
+// when fan_in % 8 == 0, fan_out >= 16 and fan_out is even (net_x3_layer);
+// the others, among them the final 1-output layer, on the CUDA cores.
+struct NetX3Plan {
+  bool ready = false;
+  bool tc[kNetMaxLayers] = {};
+  CUtensorMap tmap_a[kNetMaxLayers];  // layer l's input parts [3][max_rows][fan_in] in act_parts[l & 1]
+  CUtensorMap tmap_w[kNetMaxLayers];  // layer l's weight parts [3][fan_out][fan_in]
+  uint32_t* act_parts[2] = {nullptr, nullptr};
+  uint32_t* w_parts[kNetMaxLayers] = {};
+  float* partial = nullptr;  // the split layers' partial sums [splits][max_rows][fan_out]
+  int64_t max_rows = 0;
+};
+bool net_x3_layer(int fan_in, int fan_out);
+// 32-bit words of the plan's buffers (two BF16 per word).
+int64_t net_x3_words(const NetOut& net, int64_t max_rows);
+// False (plan not ready) off a Blackwell GPU or when no layer qualifies.
+bool net_x3_plan(NetX3Plan& pl, const NetOut& net, int64_t max_rows, uint32_t* buf);
+// The weights -> their parts (once, after the parameters are on the device).
+int launch_net_x3_split_w(const NetX3Plan& pl, const NetOut& net, cudaStream_t s);
+// fit[r] = the network's output for spark row r < count (as
+// launch_net_output, `scratch` [2][count][scratch_ld] FP32 for the CUDA-core
+// layers).  A device wait that gives up sets *status.  Kernels or -1.
+int launch_net_output_x3(const NetX3Plan& pl, const NetOut& net, const float* rows, int64_t ld, int32_t count,
+                         float* fit, float* scratch, int64_t scratch_ld, uint32_t* status, cudaStream_t s);
+
 }  // namespace mgfwa

@@ -614,4 +614,378 @@ int launch_l1_fp32x3(const L1Plan& pl, const Mlp& mlp, const int32_t* idx, int32
   return e == cudaSuccess ? 2 : -1;
 }
 
+// ---------------------------------------------------------------------------
+// The testbed network's layers (the paper's Eq. 1 objective) at FP32 accuracy
+// on the tensor cores: out[r][j] = act(sum_i A[r][i] W[j][i] + b[j]) for a
+// layer whose input A (the sparks, or the previous layer's output) and
+// weights W are both given as three BF16 parts, the same six products and
+// three accumulators as above.  One CTA per 128 rows x 128 outputs x one
+// K split of kNetKPer 32-element blocks (splits = ceil(fan_in / 128): a
+// number fixed by the layer's fan-in alone).  With one split the epilogue
+// adds the bias, applies the activation and writes the FP32 output and/or
+// its three BF16 parts (the next tensor-core layer's A); with several, each
+// split's CTA writes its partial sum ((even + odd) + corrections) and a
+// second kernel adds the partials in split order, then the bias.  A row's
+// outputs are sums over its own inputs in an order fixed by the layer's
+// fan-in, so a spark's value does not depend on which rows share the
+// launch.
+
+namespace {
+
+constexpr int kNetKPer = 4;  // 32-element K blocks per split
+
+struct NetX3Args {
+  int32_t rows;        // rows of this launch (A rows [0, rows))
+  int32_t k_blocks;    // 32-element K blocks of the fan-in
+  int32_t splits;      // K splits (gridDim.z); > 1: partial sums into `partial`
+  float* partial;      // [splits][rows][n]
+  int32_t n;           // fan-out
+  int32_t act;         // activation, or < 0 for none
+  const float* bias;   // [n]
+  float* out;          // FP32 output [rows][ldo], or null
+  int64_t ldo;
+  uint32_t* parts;     // the output's BF16 parts, plane p at parts + p * plane_words, row r at + r * n / 2; or null
+  int64_t plane_words;
+  uint32_t* status;
+};
+
+__device__ __forceinline__ float net_act(int a, float v) {
+  if (a == kActTanh) return tanhf(v);
+  if (a == kActGelu) return 0.5f * v * (1.0f + erff(v * 0.70710678118654752f));
+  return fmaxf(v, 0.0f);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_net_x3(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_w, NetX3Args a) {
+  griddep_wait();
+  griddep_launch_dependents();
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  auto Ap = [&](int p, int s) { return base + ((size_t)s * 2 * kParts + p) * kPartBytes; };
+  auto Wp = [&](int p, int s) { return base + ((size_t)s * 2 * kParts + kParts + p) * kPartBytes; };
+  Bars* sb = reinterpret_cast<Bars*>(base + (size_t)kStages * kStageBytes);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mt = blockIdx.x, nt = blockIdx.y;
+  // this CTA's K blocks [kb0, kb0 + nkb)
+  const int kb0 = (int)blockIdx.z * kNetKPer;
+  const int nkb = min(kNetKPer, a.k_blocks - kb0);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&sb->full[s], 1);
+      mbar_init(&sb->empty[s], 1);
+    }
+    mbar_init(&sb->done, 1);
+    sb->abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sb->tmem_base)),
+                 "n"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = sb->tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int kb = 0;
+      for (; kb < nkb; ++kb) {
+        const int s = kb % kStages;
+        const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
+        if (!mbar_wait(sb, &sb->empty[s], ph ^ 1u, a.status, 1u)) break;
+        mbar_expect_tx(&sb->full[s], kStageBytes);
+#pragma unroll
+        for (int p = 0; p < kParts; ++p) {
+          tma_3d(Ap(p, s), &tmap_a, (kb0 + kb) * kBKf, mt * kBM, p, &sb->full[s]);
+          tma_3d(Wp(p, s), &tmap_w, (kb0 + kb) * kBKf, nt * kN, p, &sb->full[s]);
+        }
+      }
+      for (int j = kb - kStages > 0 ? kb - kStages : 0; j < kb; ++j)
+        mbar_drain(&sb->full[j % kStages], (uint32_t)(j / kStages) & 1u, a.status);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(kBM, kN);
+      int kb = 0;
+      for (; kb < nkb; ++kb) {
+        const int s = kb % kStages;
+        const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
+        if (!mbar_wait(sb, &sb->full[s], ph, a.status, 2u)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t x1 = smem_u32(Ap(0, s)), x2 = smem_u32(Ap(1, s)), x3 = smem_u32(Ap(2, s));
+        const uint32_t w1 = smem_u32(Wp(0, s)), w2 = smem_u32(Wp(1, s)), w3 = smem_u32(Wp(2, s));
+        const uint32_t d_main = tmem + (uint32_t)((kb & 1) * kN), d_corr = tmem + (uint32_t)(2 * kN);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const uint32_t o = (uint32_t)j * 32u;
+          const uint32_t first = (kb < 2 && j == 0) ? 0u : 1u;
+          const uint32_t first_c = (kb == 0 && j == 0) ? 0u : 1u;
+          mma_bf16(d_main, smem_desc_sw64(x1 + o), smem_desc_sw64(w1 + o), idesc, first);
+          mma_bf16(d_corr, smem_desc_sw64(x1 + o), smem_desc_sw64(w2 + o), idesc, first_c);
+          mma_bf16(d_corr, smem_desc_sw64(x2 + o), smem_desc_sw64(w1 + o), idesc, 1u);
+          mma_bf16(d_corr, smem_desc_sw64(x2 + o), smem_desc_sw64(w2 + o), idesc, 1u);
+          mma_bf16(d_corr, smem_desc_sw64(x1 + o), smem_desc_sw64(w3 + o), idesc, 1u);
+          mma_bf16(d_corr, smem_desc_sw64(x3 + o), smem_desc_sw64(w1 + o), idesc, 1u);
+        }
+        mma_commit(&sb->empty[s]);
+      }
+      mma_commit(&sb->done);
+    }
+  } else {
+    const int q = warp & 3;
+    const int rrow = q * 32 + lane;
+    const uint32_t lanes = tmem + ((uint32_t)(q * 32) << 16);
+    mbar_drain(&sb->done, 0u, a.status);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int64_t r = (int64_t)mt * kBM + rrow;
+    const bool valid = !sb->abort_flag && r < a.rows;
+    const bool odd = nkb > 1;
+    const int half_n = a.n / 2;
+    const bool split = a.splits > 1;
+#pragma unroll 1
+    for (int j0 = 0; j0 < kN; j0 += 8) {
+      const int col = nt * kN + j0;
+      float x[8], x1[8], xc[8];
+      tmem_ld8(lanes + (uint32_t)j0, x);
+      tmem_ld8(lanes + (uint32_t)(kN + j0), x1);
+      tmem_ld8(lanes + (uint32_t)(2 * kN + j0), xc);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (!valid || col >= a.n) continue;
+      if (split) {
+        // this split's partial sums; the bias and the activation follow the split-ordered sum
+        float* prow = a.partial + ((int64_t)blockIdx.z * a.rows + r) * a.n;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (col + i < a.n) prow[col + i] = (odd ? x[i] + x1[i] : x[i]) + xc[i];
+        continue;
+      }
+      float o[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float z = ((odd ? x[i] + x1[i] : x[i]) + xc[i]) + (col + i < a.n ? a.bias[col + i] : 0.0f);
+        o[i] = a.act >= 0 ? net_act(a.act, z) : z;
+      }
+      if (a.out) {
+        float* orow = a.out + r * a.ldo;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (col + i < a.n) orow[col + i] = o[i];
+      }
+      if (a.parts) {
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) {
+          if (col + i >= a.n) break;
+          uint32_t p1, p2, p3;
+          split2(o[i], o[i + 1], p1, p2, p3);
+          uint32_t* d = a.parts + r * half_n + (col + i) / 2;
+          d[0] = p1;
+          d[a.plane_words] = p2;
+          d[2 * a.plane_words] = p3;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kTmemCols) : "memory");
+  }
+}
+
+// The split layer's outputs: z = ((p_0 + p_1) + ...) + b, activated, into the FP32 output and/or the BF16
+// parts (one thread per pair of outputs of a row).
+__global__ void __launch_bounds__(256) k_net_x3_reduce(NetX3Args a) {
+  griddep_wait();
+  griddep_launch_dependents();
+  const int64_t half_n = a.n / 2;
+  const int64_t total = (int64_t)a.rows * half_n;
+  const int64_t plane = (int64_t)a.rows * a.n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / half_n, j = 2 * (t - r * half_n);
+    const float* p = a.partial + r * a.n + j;
+    float z0 = p[0], z1 = p[1];
+    for (int s = 1; s < a.splits; ++s) {
+      z0 += p[s * plane];
+      z1 += p[s * plane + 1];
+    }
+    z0 += a.bias[j];
+    z1 += a.bias[j + 1];
+    if (a.act >= 0) {
+      z0 = net_act(a.act, z0);
+      z1 = net_act(a.act, z1);
+    }
+    if (a.out) {
+      a.out[r * a.ldo + j] = z0;
+      a.out[r * a.ldo + j + 1] = z1;
+    }
+    if (a.parts) {
+      uint32_t p1, p2, p3;
+      split2(z0, z1, p1, p2, p3);
+      uint32_t* d = a.parts + r * half_n + j / 2;
+      d[0] = p1;
+      d[a.plane_words] = p2;
+      d[2 * a.plane_words] = p3;
+    }
+  }
+}
+
+size_t net_x3_smem() { return 1024 + (size_t)kStages * kStageBytes + ((sizeof(Bars) + 15) & ~size_t(15)) + 64; }
+
+}  // namespace
+
+bool net_x3_layer(int fi, int fo) { return fi % 8 == 0 && fo >= 16 && fo % 2 == 0; }
+
+int net_x3_splits(int fan_in) { return (fan_in + kNetKPer * kBKf - 1) / (kNetKPer * kBKf); }
+
+int64_t net_x3_words(const NetOut& net, int64_t max_rows) {
+  int64_t w = 2 * 3 * max_rows * (int64_t)((net.wmax + 1) / 2);
+  int ks = 1;
+  for (int l = 0; l < net.n_layers; ++l)
+    if (net_x3_layer(net.widths[l], net.widths[l + 1]) && net_x3_splits(net.widths[l]) > ks)
+      ks = net_x3_splits(net.widths[l]);
+  if (ks > 1) w += (int64_t)ks * max_rows * net.wmax;  // the split layers' FP32 partial sums
+  for (int l = 0; l < net.n_layers; ++l)
+    if (net_x3_layer(net.widths[l], net.widths[l + 1])) w += 3 * (int64_t)net.widths[l + 1] * (net.widths[l] / 2);
+  return w;
+}
+
+bool net_x3_plan(NetX3Plan& pl, const NetOut& net, int64_t max_rows, uint32_t* buf) {
+  pl = NetX3Plan();
+  if (!buf) return false;
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess || prop.major != 10) {
+    cudaGetLastError();
+    return false;
+  }
+  pl.max_rows = max_rows;
+  const int64_t act_words = 3 * max_rows * (int64_t)((net.wmax + 1) / 2);
+  pl.act_parts[0] = buf;
+  pl.act_parts[1] = buf + act_words;
+  uint32_t* wcur = buf + 2 * act_words;
+  int ks = 1;
+  for (int l = 0; l < net.n_layers; ++l)
+    if (net_x3_layer(net.widths[l], net.widths[l + 1]) && net_x3_splits(net.widths[l]) > ks)
+      ks = net_x3_splits(net.widths[l]);
+  if (ks > 1) {
+    pl.partial = reinterpret_cast<float*>(wcur);
+    wcur += (int64_t)ks * max_rows * net.wmax;
+  }
+  bool any = false;
+  for (int l = 0; l < net.n_layers; ++l) {
+    const int fi = net.widths[l], fo = net.widths[l + 1];
+    pl.tc[l] = net_x3_layer(fi, fo);
+    if (!pl.tc[l]) continue;
+    any = true;
+    pl.w_parts[l] = wcur;
+    wcur += 3 * (int64_t)fo * (fi / 2);
+    {
+      // the layer's input parts [3][max_rows][fi] in buffer l & 1, box 32 x 128 x 1
+      cuuint64_t dims[3] = {(cuuint64_t)fi, (cuuint64_t)max_rows, 3};
+      cuuint64_t strides[2] = {(cuuint64_t)fi * 2, (cuuint64_t)(max_rows * fi * 2)};
+      cuuint32_t box[3] = {kBKf, kBM, 1};
+      if (!encode_bf16(&pl.tmap_a[l], pl.act_parts[l & 1], dims, strides, box)) return false;
+    }
+    {
+      // the weights' parts [3][fo][fi], box 32 x 128 x 1 (rows past fo are zero fill)
+      cuuint64_t dims[3] = {(cuuint64_t)fi, (cuuint64_t)fo, 3};
+      cuuint64_t strides[2] = {(cuuint64_t)fi * 2, (cuuint64_t)((int64_t)fo * fi * 2)};
+      cuuint32_t box[3] = {kBKf, (cuuint32_t)kN, 1};
+      if (!encode_bf16(&pl.tmap_w[l], pl.w_parts[l], dims, strides, box)) return false;
+    }
+  }
+  if (!any || ensure_smem_limit<k_net_x3>(net_x3_smem()) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  pl.ready = true;
+  return true;
+}
+
+int launch_net_x3_split_w(const NetX3Plan& pl, const NetOut& net, cudaStream_t s) {
+  if (!pl.ready) return 0;
+  int n = 0;
+  for (int l = 0; l < net.n_layers; ++l) {
+    if (!pl.tc[l]) continue;
+    const int fi = net.widths[l], fo = net.widths[l + 1];
+    const int64_t pairs = fi / 2;
+    if (split_launch(net.params + net.w_off[l], fi, nullptr, fo, 0, pairs, pl.w_parts[l], pairs, (int64_t)fo * pairs,
+                     s) < 0)
+      return -1;
+    ++n;
+  }
+  return n;
+}
+
+int launch_net_output_x3(const NetX3Plan& pl, const NetOut& net, const float* rows, int64_t ld, int32_t count,
+                         float* fit, float* scratch, int64_t scratch_ld, uint32_t* status, cudaStream_t s) {
+  if (count <= 0) return 0;
+  if (!pl.ready || count > pl.max_rows) return -1;
+  int n = 0;
+  const float* a = rows;  // the FP32 input of the next CUDA-core layer
+  int64_t lda = ld;
+  for (int l = 0; l < net.n_layers; ++l) {
+    const int fi = net.widths[l], fo = net.widths[l + 1];
+    const bool last = l + 1 == net.n_layers;
+    const bool next_tc = !last && pl.tc[l + 1];
+    float* o = last ? fit : scratch + (int64_t)(l & 1) * scratch_ld * count;
+    const int64_t ldo = last ? 1 : scratch_ld;
+    const float* b = net.params + net.b_off[l];
+    const int32_t ak = last ? -1 : net.acts[l];
+    if (pl.tc[l]) {
+      if (l == 0) {
+        // the sparks -> their BF16 parts in buffer 0
+        const int64_t pairs = fi / 2;
+        if (split_launch(rows, ld, nullptr, count, 0, pairs, pl.act_parts[0], pairs, pl.max_rows * pairs, s) < 0)
+          return -1;
+        ++n;
+      }
+      NetX3Args x;
+      x.rows = count;
+      x.k_blocks = (fi + kBKf - 1) / kBKf;
+      x.splits = net_x3_splits(fi);
+      x.partial = pl.partial;
+      x.n = fo;
+      x.act = ak;
+      x.bias = b;
+      x.out = next_tc ? nullptr : o;
+      x.ldo = ldo;
+      x.parts = next_tc ? pl.act_parts[(l + 1) & 1] : nullptr;
+      x.plane_words = pl.max_rows * (fo / 2);
+      x.status = status;
+      const dim3 grid((unsigned)((count + kBM - 1) / kBM), (unsigned)((fo + kN - 1) / kN), (unsigned)x.splits);
+      if (launch_pdl(k_net_x3, grid, dim3(kThreads), net_x3_smem(), s, pl.tmap_a[l], pl.tmap_w[l], x) !=
+          cudaSuccess)
+        return -1;
+      ++n;
+      if (x.splits > 1) {
+        const int64_t pairs = (int64_t)count * (fo / 2);
+        const unsigned blocks = (unsigned)((pairs + 255) / 256 < 4096 ? (pairs + 255) / 256 : 4096);
+        if (launch_pdl(k_net_x3_reduce, dim3(blocks), dim3(256), 0, s, x) != cudaSuccess) return -1;
+        ++n;
+      }
+    } else {
+      if (launch_net_layer(a, lda, count, net.params + net.w_off[l], b, fi, fo, ak, o, ldo, s) < 0) return -1;
+      ++n;
+      if (next_tc) {
+        // this layer's FP32 output -> the next layer's parts
+        const int64_t pairs = fo / 2;
+        if (split_launch(o, ldo, nullptr, count, 0, pairs, pl.act_parts[(l + 1) & 1], pairs, pl.max_rows * pairs,
+                         s) < 0)
+          return -1;
+        ++n;
+      }
+    }
+    a = o;
+    lda = ldo;
+  }
+  return n;
+}
+
 }  // namespace mgfwa

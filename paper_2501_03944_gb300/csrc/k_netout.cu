@@ -203,9 +203,8 @@ __global__ void __launch_bounds__(256) k_net_f64(NetOut net, const float* __rest
 
 }  // namespace
 
-int launch_net_output(const NetOut& net, const float* rows, int64_t ld, int32_t count, float* fit, float* scratch,
-                      int64_t scratch_ld, cudaStream_t s) {
-  if (count <= 0) return 0;
+int launch_net_layer(const float* a, int64_t lda, int32_t count, const float* W, const float* b, int32_t fi,
+                     int32_t fo, int32_t ak, float* o, int64_t ldo, cudaStream_t s) {
   if (ensure_smem_limit<k_net_layer<8>>(NetTile<8>::kSmem) != cudaSuccess ||
       ensure_smem_limit<k_net_layer<4>>(NetTile<4>::kSmem) != cudaSuccess)
     return -1;
@@ -213,6 +212,21 @@ int launch_net_output(const NetOut& net, const float* rows, int64_t ld, int32_t 
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
                                                  cudaSuccess)
     return -1;
+  // 64-row tiles where they fill the SMs, else 32-row tiles (twice the blocks)
+  const bool wide = (int64_t)((count + 63) / 64) * ((fo + kTN - 1) / kTN) >= sms;
+  cudaError_t e;
+  if (wide)
+    e = launch_pdl(k_net_layer<8>, dim3((unsigned)((count + 63) / 64), (unsigned)((fo + kTN - 1) / kTN)), dim3(256),
+                   NetTile<8>::kSmem, s, a, lda, count, W, b, fi, fo, ak, o, ldo);
+  else
+    e = launch_pdl(k_net_layer<4>, dim3((unsigned)((count + 31) / 32), (unsigned)((fo + kTN - 1) / kTN)), dim3(256),
+                   NetTile<4>::kSmem, s, a, lda, count, W, b, fi, fo, ak, o, ldo);
+  return e == cudaSuccess ? 1 : -1;
+}
+
+int launch_net_output(const NetOut& net, const float* rows, int64_t ld, int32_t count, float* fit, float* scratch,
+                      int64_t scratch_ld, cudaStream_t s) {
+  if (count <= 0) return 0;
   const float* a = rows;
   int64_t lda = ld;
   int n = 0;
@@ -221,19 +235,9 @@ int launch_net_output(const NetOut& net, const float* rows, int64_t ld, int32_t 
     const bool last = l + 1 == net.n_layers;
     float* o = last ? fit : scratch + (int64_t)(l & 1) * scratch_ld * count;
     const int64_t ldo = last ? 1 : scratch_ld;
-    const float* W = net.params + net.w_off[l];
-    const float* b = net.params + net.b_off[l];
-    const int32_t ak = last ? -1 : net.acts[l];
-    // 64-row tiles where they fill the SMs, else 32-row tiles (twice the blocks)
-    const bool wide = (int64_t)((count + 63) / 64) * ((fo + kTN - 1) / kTN) >= sms;
-    cudaError_t e;
-    if (wide)
-      e = launch_pdl(k_net_layer<8>, dim3((unsigned)((count + 63) / 64), (unsigned)((fo + kTN - 1) / kTN)),
-                     dim3(256), NetTile<8>::kSmem, s, a, lda, count, W, b, (int32_t)fi, (int32_t)fo, ak, o, ldo);
-    else
-      e = launch_pdl(k_net_layer<4>, dim3((unsigned)((count + 31) / 32), (unsigned)((fo + kTN - 1) / kTN)),
-                     dim3(256), NetTile<4>::kSmem, s, a, lda, count, W, b, (int32_t)fi, (int32_t)fo, ak, o, ldo);
-    if (e != cudaSuccess) return -1;
+    if (launch_net_layer(a, lda, count, net.params + net.w_off[l], net.params + net.b_off[l], fi, fo,
+                         last ? -1 : net.acts[l], o, ldo, s) < 0)
+      return -1;
     ++n;
     a = o;
     lda = ldo;

@@ -33,6 +33,8 @@ struct mgfwa_handle {
   NetOut net;                   // testbed network objective (params point into the arena)
   int64_t net_count = 0;        // its parameter count
   float* net_act = nullptr;     // [2][PA][hmax] hidden activations
+  uint32_t* net_x3_buf = nullptr;  // FP32X3: the layers' BF16 parts (activations ping-pong, weights)
+  NetX3Plan net_x3;             // FP32X3: the testbed network's tensor-core layers
   int32_t kind = MGFWA_OBJ_MLP_CE;
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -220,8 +222,13 @@ mgfwa_status eval_rows(mgfwa_t* h, int64_t first, int32_t count, int32_t precisi
   }
   if (h->kind == MGFWA_OBJ_NET_OUTPUT) {
     Mark mk(h, group);
-    MG_LAUNCH(h, launch_net_output(h->net, rows, h->p.Dp, count, fit, h->net_act, h->net.hmax, h->stream),
-              "network output");
+    if (precision == MGFWA_FP32X3)
+      MG_LAUNCH(h, launch_net_output_x3(h->net_x3, h->net, rows, h->p.Dp, count, fit, h->net_act, h->net.hmax,
+                                        h->status, h->stream),
+                "network output (tensor cores)");
+    else
+      MG_LAUNCH(h, launch_net_output(h->net, rows, h->p.Dp, count, fit, h->net_act, h->net.hmax, h->stream),
+                "network output");
     return MGFWA_OK;
   }
   {
@@ -540,8 +547,12 @@ mgfwa_status validate(const mgfwa_config* c, const mgfwa_objective* o) {
   if (PA > (1 << 24)) return fail(nullptr, MGFWA_EINVAL, "n_runs mu (lambda + m) = %lld exceeds 2^24", (long long)PA);
   if (!(c->sigma > 0.0f) || !(c->sigma <= 0.5f)) return fail(nullptr, MGFWA_EINVAL, "sigma must be in (0, 0.5]");
   if (c->eval_budget < c->n_fireworks) return fail(nullptr, MGFWA_EINVAL, "eval_budget below the mu initial evaluations");
-  if (c->precision != MGFWA_FP32 && c->precision != MGFWA_BF16 && c->precision != MGFWA_FP8)
-    return fail(nullptr, MGFWA_EINVAL, "precision %d not supported (FP32 = 0, BF16 = 1, FP8 = 2)", c->precision);
+  if (c->precision != MGFWA_FP32 && c->precision != MGFWA_BF16 && c->precision != MGFWA_FP8 &&
+      c->precision != MGFWA_FP32X3)
+    return fail(nullptr, MGFWA_EINVAL, "precision %d not supported (FP32 = 0, BF16 = 1, FP8 = 2, FP32X3 = 3)",
+                c->precision);
+  if (c->precision == MGFWA_FP32X3 && o->kind != MGFWA_OBJ_NET_OUTPUT)
+    return fail(nullptr, MGFWA_EINVAL, "FP32X3 is the testbed network objective's precision");
   if (c->refine_every < 0) return fail(nullptr, MGFWA_EINVAL, "refine_every must be >= 0");
   if (c->loser_out != 0 && c->loser_out != 1) return fail(nullptr, MGFWA_EINVAL, "loser_out must be 0 or 1");
   if (c->lagged_guiding != 0 && c->lagged_guiding != 1)
@@ -577,8 +588,15 @@ mgfwa_status validate(const mgfwa_config* c, const mgfwa_objective* o) {
     for (int l = 0; l + 1 < L; ++l)
       if (o->acts[l] != MGFWA_ACT_TANH && o->acts[l] != MGFWA_ACT_RELU && o->acts[l] != MGFWA_ACT_GELU)
         return fail(nullptr, MGFWA_EINVAL, "unknown activation %d", o->acts[l]);
-    if (c->precision != MGFWA_FP32)
-      return fail(nullptr, MGFWA_EINVAL, "the network objective runs in FP32 only");
+    if (c->precision != MGFWA_FP32 && c->precision != MGFWA_FP32X3)
+      return fail(nullptr, MGFWA_EINVAL, "the network objective runs in FP32 or FP32X3");
+    if (c->precision == MGFWA_FP32X3) {
+      bool any = false;
+      for (int l = 0; l < L; ++l) any = any || net_x3_layer(o->widths[l], o->widths[l + 1]);
+      if (!any)
+        return fail(nullptr, MGFWA_EINVAL,
+                    "FP32X3: no layer of this network has fan_in % 8 == 0 and an even fan_out >= 16");
+    }
     return MGFWA_OK;
   }
   if (o->kind != MGFWA_OBJ_MLP_CE) return fail(nullptr, MGFWA_EINVAL, "unknown objective kind %d", o->kind);
@@ -862,6 +880,8 @@ size_t carve_all(mgfwa_t* h, char* base) {
   if (h->kind == MGFWA_OBJ_NET_OUTPUT) {
     h->net.params = carve<float>(cur, (size_t)h->net_count);
     h->net_act = h->net.n_layers > 1 ? carve<float>(cur, (size_t)(2 * h->PA * h->net.hmax)) : nullptr;
+    h->net_x3_buf =
+        h->cfg.precision == MGFWA_FP32X3 ? carve<uint32_t>(cur, (size_t)net_x3_words(h->net, h->PA)) : nullptr;
   }
   h->best_x = carve<float>(cur, (int64_t)p.B * p.Dp);
   h->best_f = carve<float>(cur, p.B);
@@ -990,6 +1010,12 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
       cudaMemcpyAsync(const_cast<float*>(h->net.params), obj->params, sizeof(float) * h->net_count,
                       cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
     return bail(cuda_fail(h, "copy network parameters"));
+  if (h->net_x3_buf) {
+    // FP32X3: the tensor-core layers' maps, and the weights' BF16 parts once
+    if (!net_x3_plan(h->net_x3, h->net, h->PA, h->net_x3_buf))
+      return bail(fail(h, MGFWA_EINVAL, "FP32X3 needs a Blackwell (sm_10x) GPU"));
+    CREATE_LAUNCH(launch_net_x3_split_w(h->net_x3, h->net, h->stream), "FP32X3 weight parts");
+  }
   if (h->w2op &&
       cudaMemsetAsync(h->w2op, 0, sizeof(uint16_t) * h->PA * h->w2_rows * h->mlp.widths[1], h->stream) != cudaSuccess)
     return bail(cuda_fail(h, "clear the W2 copy"));
@@ -1033,7 +1059,7 @@ mgfwa_status mgfwa_create(const mgfwa_config* cfg, const mgfwa_objective* obj, v
   if (want_op) CREATE_LAUNCH(launch_to_operand(h->sparks, p.Dp, F, op_rows(h, 0), h->stream), "init operand");
   TRACE("create: staged");
   // with an FP32 elite re-score the initial fireworks are scored in FP32 too
-  st = eval_rows(h, 0, F, cfg->elite_rescore > 0 ? MGFWA_FP32 : cfg->precision);
+  st = eval_rows(h, 0, F, cfg->elite_rescore > 0 && h->kind == MGFWA_OBJ_MLP_CE ? MGFWA_FP32 : cfg->precision);
   if (st != MGFWA_OK) return bail(st);
   TRACE("create: evaluated");
   if (cudaMemcpyAsync(h->fw_f, h->fit, sizeof(float) * F, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
@@ -1168,8 +1194,10 @@ mgfwa_status mgfwa_evaluate(mgfwa_t* h, const float* xs, int64_t count, int32_t 
   if (st != MGFWA_OK) return st;
   if (!xs || !f_out || count < 0 || count > h->PA)
     return fail(h, MGFWA_EINVAL, "evaluate: bad arguments (count <= %lld)", (long long)h->PA);
-  if (precision != MGFWA_FP32 && precision != MGFWA_BF16 && precision != MGFWA_FP8)
+  if (precision != MGFWA_FP32 && precision != MGFWA_BF16 && precision != MGFWA_FP8 && precision != MGFWA_FP32X3)
     return fail(h, MGFWA_EINVAL, "evaluate: bad precision");
+  if (precision == MGFWA_FP32X3 && !h->net_x3.ready)
+    return fail(h, MGFWA_EINVAL, "evaluate: FP32X3 needs a testbed-network handle created in FP32X3");
   if (use_tc(h, precision) && (!h->op || precision != h->cfg.precision))
     return fail(h, MGFWA_EINVAL, "evaluate: the handle's tensor-core operand is not of precision %d", precision);
   if (h->next_phase != MGFWA_PHASE_EXPLODE) return fail(h, MGFWA_EINVAL, "a debug generation is in progress");

@@ -305,6 +305,9 @@ int launch_net_output(const NetOut& net, const float* rows, int64_t ld, int32_t 
                       int64_t scratch_ld, cudaStream_t s);
 // Its FP64 output for one vector into *out (one launch).
 int launch_net_output_f64(const NetOut& net, const float* x, double* out, cudaStream_t s);
+// One CUDA-core layer of the testbed network: out[r][j] = act(A[r] . W[j] + b[j]) (no activation for act < 0).
+int launch_net_layer(const float* A, int64_t lda, int32_t rows, const float* W, const float* b, int32_t k, int32_t n,
+                     int32_t act, float* out, int64_t ldo, cudaStream_t s);
 
 // BF16 copy of the first-layer weights of `count` rows (stride ld) into op.
 int launch_to_operand(const float* rows, int64_t ld, int32_t count, const OpDesc& op, cudaStream_t s);
