@@ -740,7 +740,7 @@ def main():
     ap.add_argument("--serving-full", action="store_true",
                     help="only the serving workload's full 2,000-request window (a few minutes)")
     ap.add_argument("--workload", default=W.MLP_784_64_10.name,
-                    choices=[w.name for w in (W.MLP_784_64_10, W.MLP_3072_128_64_10)],
+                    choices=[w.name for w in (W.MLP_784_64_10, W.MLP_3072_128_64_10, W.MLP_8_16_3)],
                     help="the timed step's workload (the metric is quoted on the 784-64-10 one)")
     ap.add_argument("--fireworks", type=int, default=0,
                     help="override the workload's firework count (smaller profiling captures)")
