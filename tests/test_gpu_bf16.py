@@ -161,7 +161,8 @@ def test_bf16_full_size_784_64_10(pkg):
         run.phase(pkg.MGFWA_PHASE_EVAL_E)
         sparks = run.read(pkg.MGFWA_BUF_SPARKS)
         fe = run.read(pkg.MGFWA_BUF_FIT_E)
-        pick = np.concatenate([np.arange(4), np.random.default_rng(2).choice(1000, 12, replace=False), [996, 997, 998, 999]])
+        pick = np.concatenate([np.arange(4), np.random.default_rng(2).choice(np.arange(4, 996), 92, replace=False),
+                               [996, 997, 998, 999]])
         assert np.all(_rel(fe[pick], prob.fitness_many(sparks[pick], 8)) <= BF16_RTOL)
         for ph in (pkg.MGFWA_PHASE_RANK, pkg.MGFWA_PHASE_GUIDE, pkg.MGFWA_PHASE_EVAL_G, pkg.MGFWA_PHASE_SELECT):
             run.phase(ph)
@@ -170,6 +171,27 @@ def test_bf16_full_size_784_64_10(pkg):
         assert np.all(_rel(fg, prob.fitness_many(guides, 8)) <= BF16_RTOL)
         # BF16 and FP32 agree on every spark of the launch within the BF16 bar
         f32 = run.evaluate(sparks[:1000], pkg.MGFWA_FP32)
+        assert np.all(_rel(fe, f32.astype(np.float64)) <= BF16_RTOL)
+
+
+def test_bf16_full_size_3072_128_64_10(pkg):
+    """The 3072-128-64-10 network at its full batch (N = 4096; 2 of its 8 fireworks, 512 explosion sparks per
+    launch on the three-layer pair kernel): sampled sparks against the oracle, every spark against FP32."""
+    w = W.scaled(W.MLP_3072_128_64_10, n_fireworks=2)
+    X, y = W.make_data(w)
+    prob = oracle.Problem.for_workload(w, X, y)
+    with pkg.Mgfwa.for_workload(w, 6, precision=pkg.MGFWA_BF16, X=X, y=y) as run:
+        run.phase(pkg.MGFWA_PHASE_EXPLODE)
+        run.phase(pkg.MGFWA_PHASE_EVAL_E)
+        sparks = run.read(pkg.MGFWA_BUF_SPARKS)
+        fe = run.read(pkg.MGFWA_BUF_FIT_E)
+        n_e = len(fe)
+        pick = np.concatenate([[0, 1], np.random.default_rng(3).choice(np.arange(2, n_e - 2), 6, replace=False),
+                               [n_e - 2, n_e - 1]])
+        assert np.all(_rel(fe[pick], prob.fitness_many(sparks[pick], 16)) <= BF16_RTOL)
+        for ph in (pkg.MGFWA_PHASE_RANK, pkg.MGFWA_PHASE_GUIDE, pkg.MGFWA_PHASE_EVAL_G, pkg.MGFWA_PHASE_SELECT):
+            run.phase(ph)
+        f32 = run.evaluate(sparks[:n_e], pkg.MGFWA_FP32)
         assert np.all(_rel(fe, f32.astype(np.float64)) <= BF16_RTOL)
 
 

@@ -63,6 +63,23 @@ def test_fp8_fitness_equals_quantized_oracle(pkg, widths, acts, N, count):
     assert np.all(np.abs(got - exact) <= 0.3 * np.abs(exact) + 0.05)
 
 
+def test_fp8_full_size_3072_128_64_10(pkg):
+    """The 3072-128-64-10 network at its full batch (N = 4096, 2 of 8 fireworks): sampled explosion sparks
+    against the oracle's quantized network."""
+    w = W.scaled(W.MLP_3072_128_64_10, n_fireworks=2)
+    X, y = W.make_data(w)
+    prob = oracle.Problem.for_workload(w, X, y)
+    with pkg.Mgfwa.for_workload(w, 7, precision=pkg.MGFWA_FP8, X=X, y=y, elite_rescore=0) as run:
+        info = run.info()
+        run.phase(pkg.MGFWA_PHASE_EXPLODE)
+        run.phase(pkg.MGFWA_PHASE_EVAL_E)
+        sparks = run.read(pkg.MGFWA_BUF_SPARKS)
+        fe = run.read(pkg.MGFWA_BUF_FIT_E)
+    pick = np.random.default_rng(4).choice(len(fe), 4, replace=False)
+    want = np.array([oracle.fitness_fp8(prob, sparks[i], info.fp8_inv_scale_x, info.fp8_inv_scale_w) for i in pick])
+    assert np.all(_rel(fe[pick], want) <= RTOL), np.max(_rel(fe[pick], want))
+
+
 def test_fp8_rejects_unaligned_inputs_and_other_precisions(pkg):
     w = W.scaled(W.MLP_784_64_10, widths=(8, 32, 3), acts=(0,), n_samples=64)
     X, y = W.make_data(w)
