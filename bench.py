@@ -62,9 +62,9 @@ def whole_job_rate(world: int, units_per_rank: float, seconds: float) -> float:
     return world * units_per_rank / seconds
 
 
-def _traffic(kernel: str, source: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None
-    when the kernel's source changed since that capture."""
+def _capture(kernel: str, source: str):
+    """The committed ncu record of `kernel` (profiles/traffic.json), or None when
+    the kernel's source changed since that capture."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
@@ -74,6 +74,15 @@ def _traffic(kernel: str, source: str):
         return None
     sha = hashlib.sha256(open(os.path.join(ROOT, source), "rb").read()).hexdigest()
     if sha != rec.get("sha256"):
+        return None
+    return rec
+
+
+def _traffic(kernel: str, source: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None
+    when the kernel's source changed since that capture."""
+    rec = _capture(kernel, source)
+    if not rec or "dram_bytes_read" not in rec:
         return None
     return rec["dram_bytes_read"] + rec["dram_bytes_write"]
 
@@ -511,6 +520,22 @@ def gpu_arm(args):
             if n:
                 gbs = b / (t / n / 1e3) / 1e9
                 hbm[g] = {"GB/s": round(gbs, 1), "frac": round(gbs / hbm_peak, 4), "bytes_per_launch": b}
+        # the sampler's own bound is instruction issue (one warp instruction per cycle per scheduler): its
+        # warp instructions per launch from the committed ncu capture of this source, against the issue rate
+        # of every scheduler at the SM clock sampled during the timed region
+        ex = _capture("k_explode", "paper_2501_03944_gb300/csrc/k_sample.cu")
+        if ex and "explode" in hbm and prec == pkg.MGFWA_BF16 and WORKLOAD is W.MLP_784_64_10:
+            import torch
+            t, n = ktimes["explode"]
+            sms = torch.cuda.get_device_properties(0).multi_processor_count
+            mhz = clk.summary().get("sm_mhz") or 2070.0
+            peak = sms * 4 * mhz * 1e6 / 1e9
+            ach = ex["warp_instructions"] / (t / n / 1e3) / 1e9
+            hbm["explode"]["issue_roofline"] = {
+                "bound": "alu", "achieved": round(ach, 1), "peak": round(peak, 1),
+                "unit": "G warp instructions/s", "frac": round(ach / peak, 4),
+                "warp_instructions": ex["warp_instructions"],
+                "peak_source": f"derived: {sms} SMs x 4 schedulers x 1 warp instruction per cycle x {mhz:.0f} MHz"}
         # the whole generation against its ideal: every spark's fitness at the tensor peak above plus the
         # sampling and guiding bytes at the HBM peak (rank and selection take a few microseconds; the FP32
         # re-score of the elite candidates is accuracy work on top of the metric's and is left out)
