@@ -354,6 +354,7 @@ def gpu_arm(args):
     w = W.scaled(WORKLOAD, eval_budget=W.budget_for_generations(WORKLOAD.n_fireworks, WORKLOAD.sparks_per_firework,
                                                                  WORKLOAD.guiding_per_firework, budget_gens))
     run = pkg.Mgfwa.for_workload(w, seed, precision=prec, X=X, y=y, stream=stream.cuda_stream)
+    tile = run.pair_tile()  # the fitness kernel's tile, as the creation-time tuner chose it
     run.step(args.warmup)
     torch.cuda.synchronize()
     launches0 = run.info().kernel_launches
@@ -559,6 +560,8 @@ def gpu_arm(args):
                     "d2h_bytes_per_step": (4 * D + 8) / args.steps,
                     "note": "create (X, y from pinned host) + K generations + best (x, FP64 loss) + destroy"},
                 "roofline": roof, "generation_roofline": gen_roof, "hbm_kernels": hbm, "kernels": kernels,
+                "fitness_tile": None if tile[0] < 0 else {
+                    "sparks_per_tile": tile[0], "stages": tile[1], "k_tail_mmas": tile[3], "tuned": bool(tile[2])},
                 "library_peaks": lib_peaks,
                 "kernel_timing": {"how": "the next `steps` generations after the timed region, launched kernel by "
                                          "kernel with CUDA events on the handle's stream around each kernel group "

@@ -100,21 +100,30 @@ MGFWA_API mgfwa_status mgfwa_debug_wait_budget(mgfwa_t* h, uint64_t ticks);
  * fitness of many sparks at once as one contraction): *sparks_per_tile
  * sparks per 256-sample tile -- 256/h1 when each spark's logits go into its
  * own accumulator columns once its activations are packed, 256/(h1 + 16 or
- * 32 logit rows) when the logits have columns of their own -- and *stages
- * shared-memory pipeline stages; *tuned is 1 where mgfwa_create chose the
- * two by timing every shape and depth that fits (once per device and
- * problem shape in the process), 0 where they were set.  All three are -1
- * for a handle not on the pair kernel.  Any pointer may be NULL.
+ * 32 logit rows) when the logits have columns of their own -- *stages
+ * shared-memory pipeline stages, and *k_tail the layer-1 MMAs of the
+ * partial last K atom (d_in not a multiple of 64 BF16 or 128 E4M3 values)
+ * that go through the two K-tail buffers instead of taking a pipeline stage
+ * of their own (0: none, or the atom is a stage); *tuned is 1 where
+ * mgfwa_create chose the three by timing every shape, depth and K-tail
+ * choice that fits (once per device and problem shape in the process), 0
+ * where they were set.  All four are -1 for a handle not on the pair
+ * kernel.  Any pointer may be NULL.
  * Errors: EINVAL (null handle). */
 MGFWA_API mgfwa_status mgfwa_debug_pair_tile(const mgfwa_t* h, int32_t* sparks_per_tile, int32_t* stages,
-                                             int32_t* tuned);
+                                             int32_t* tuned, int32_t* k_tail);
 /* Set the pair kernel's tile for the generations that follow (the
- * handle's generation graph is captured again).  Every shape and depth
- * gives every spark bitwise the same fitness.  Synchronises the handle's
- * stream.  Errors: EINVAL (null handle, not on the pair kernel, a tile the
- * kernel has not got for this network, a depth outside 2 .. the deepest
- * that fits), ECUDA. */
-MGFWA_API mgfwa_status mgfwa_debug_set_pair_tile(mgfwa_t* h, int32_t sparks_per_tile, int32_t stages);
+ * handle's generation graph is captured again).  k_tail: 1 = the partial
+ * last K atom through the K-tail buffers, 0 = as a pipeline stage, -1 = the
+ * buffers where the network has such an atom and they fit beside the
+ * pipeline.  Every shape, depth and K-tail choice gives every spark bitwise
+ * the same fitness.  Synchronises the handle's stream.  Errors: EINVAL
+ * (null handle, not on the pair kernel, a tile the kernel has not got for
+ * this network, a depth outside 2 .. the deepest that fits, k_tail = 1
+ * without a partial atom or with buffers that do not fit beside the
+ * pipeline, k_tail outside -1 .. 1), ECUDA. */
+MGFWA_API mgfwa_status mgfwa_debug_set_pair_tile(mgfwa_t* h, int32_t sparks_per_tile, int32_t stages,
+                                                 int32_t k_tail);
 
 #ifdef __cplusplus
 }

@@ -137,8 +137,8 @@ def load_library(path: Optional[str] = None):
     L.mgfwa_evaluate_fp32_noalloc.argtypes = [i32, i32p, i32p, i64, vp, vp, vp, i64, i32, vp, vp]
     L.mgfwa_shard_key.argtypes = [vp, i32, ctypes.POINTER(mgfwa_best_key)]
     L.mgfwa_debug_wait_budget.argtypes = [vp, ctypes.c_uint64]
-    L.mgfwa_debug_pair_tile.argtypes = [vp, i32p, i32p, i32p]
-    L.mgfwa_debug_set_pair_tile.argtypes = [vp, i32, i32]
+    L.mgfwa_debug_pair_tile.argtypes = [vp, i32p, i32p, i32p, i32p]
+    L.mgfwa_debug_set_pair_tile.argtypes = [vp, i32, i32, i32]
     L.mgfwa_reduce_best_keys.argtypes = [ctypes.POINTER(mgfwa_best_key), i32, ctypes.POINTER(mgfwa_best_key)]
     L.mgfwa_set_reduce_best.argtypes = [vp, REDUCE_BEST_FN, vp]
     L.mgfwa_global_best_key.argtypes = [vp, i32, ctypes.POINTER(mgfwa_best_key)]
@@ -383,14 +383,15 @@ class Mgfwa:
         _check(load_library().mgfwa_debug_wait_budget(self.handle, ticks), self.handle)
 
     def pair_tile(self) -> tuple:
-        """(sparks per tile, stages, tuned) of the CTA-pair fitness kernel; all -1 off that kernel."""
-        v = [ctypes.c_int32() for _ in range(3)]
+        """(sparks per tile, stages, tuned, K-tail MMAs) of the CTA-pair fitness kernel; all -1 off that kernel."""
+        v = [ctypes.c_int32() for _ in range(4)]
         _check(load_library().mgfwa_debug_pair_tile(self.handle, *[ctypes.byref(x) for x in v]), self.handle)
         return tuple(x.value for x in v)
 
-    def set_pair_tile(self, sparks_per_tile: int, stages: int) -> None:
-        """Run the following generations with this tile of the CTA-pair fitness kernel."""
-        _check(load_library().mgfwa_debug_set_pair_tile(self.handle, sparks_per_tile, stages), self.handle)
+    def set_pair_tile(self, sparks_per_tile: int, stages: int, k_tail: int = -1) -> None:
+        """Run the following generations with this tile of the CTA-pair fitness kernel (k_tail: 1 the partial
+        last K atom through the K-tail buffers, 0 as a pipeline stage, -1 the buffers where they fit)."""
+        _check(load_library().mgfwa_debug_set_pair_tile(self.handle, sparks_per_tile, stages, k_tail), self.handle)
 
     def shard_key(self, run: int = 0) -> mgfwa_best_key:
         key = mgfwa_best_key()

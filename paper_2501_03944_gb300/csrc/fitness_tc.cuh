@@ -19,6 +19,8 @@ struct TcPlan {
   CUtensorMap tmap_w3b; // pair kernel, three layers: BF16 W3 [P][16][h2], box 64 x 8 x 1
   CUtensorMap tmap_x3;  // pair kernel: X viewed as [K atoms][N][one 128-byte atom], box one atom x 128 x 2 atoms
   CUtensorMap tmap_wk;  // pair kernel: the first-layer operand viewed the same way, box one atom x half a tile x 2
+  CUtensorMap tmap_xt;  // pair kernel: X, box one MMA's K (32 bytes) x 128, 32B swizzle (the partial last atom)
+  CUtensorMap tmap_wt;  // pair kernel: the first-layer operand, box 32 bytes x half a tile's rows, 32B swizzle
   CUtensorMap tmap_x;   // X  [N][d_in], box 128 rows x 128 bytes of K, 128B swizzle
   CUtensorMap tmap_w;   // op [P*h1][d_in], box n_tile rows x 128 bytes of K, 128B swizzle
   CUtensorMap tmap_w2;  // W2 inside the FP32 spark rows [P][C or h2][h1], box 32 x rows x 1, 128B swizzle
@@ -29,6 +31,8 @@ struct TcPlan {
   int stages = 0;           // shared-memory pipeline depth
   size_t smem_bytes = 0;
   int tuned = 0;            // pair kernel: 1 if the tile shape and depth were chosen by timing
+  int ktail = 0;            // pair kernel: MMAs of the partial last K atom taken through the K-tail buffers
+                            // (their shared memory is reserved), 0 = the atom is a pipeline stage of its own
   const void* w_base = nullptr;  // pair kernel: the first-layer operand and its rows (for re-encoding W1's maps)
   int64_t w_rows = 0;
 };
@@ -76,6 +80,9 @@ struct PairArgs {
   int32_t n_full;       // K atoms entirely inside d_in
   int32_t n_steps;      // K steps per tile: ceil(n_full / 2), plus one for a partial last atom
   int32_t k_last;       // layer-1 MMAs in the partial last atom (0 if d_in ends on an atom)
+  int32_t kt;           // k_last when the partial atom may go through the K-tail buffers (some full atom
+                        // before it), else 0; it does when kt <= kt_region of the launch
+  int32_t kt_region;    // the launch's K-tail buffers (MMAs per buffer; 0 = none): the shared-memory layout
   int32_t stages;
   int32_t C;            // classes (<= NL)
   int32_t act;
@@ -99,6 +106,7 @@ struct PairArgs {
 // tensor maps require, which the array's allocation honours).
 struct PairMember {
   CUtensorMap x3, x, w3, w, w2, wl3;  // wl3: the BF16 W3 copy (three layers)
+  CUtensorMap xt, wt;                  // the partial last atom's loads through the K-tail buffers
   PairArgs a;
   int32_t tile_start, tiles;
 };
@@ -124,17 +132,28 @@ int launch_fitness_pair_group(const TcPlan& plan, const Mlp& mlp, const PairMemb
 int tc_pair_sparks(const Mlp& mlp, bool shared);
 size_t tc_pair_fixed_smem(const Mlp& mlp, int sparks_per_tile);
 size_t tc_pair_stage_bytes(int h1, int sparks_per_tile);
+// MMAs of the network's partial last K atom that the K-tail buffers can take
+// (1 .. 3, with at least one full atom before it), else 0; and the shared
+// memory of both K-tail buffers for `mmas` of them.
+int tc_pair_ktail_mmas(const Mlp& mlp, bool f8);
+size_t tc_pair_ktail_bytes(int h1, int sparks_per_tile, int mmas);
 int tc_pair_max_stages();
 // Deepest pipeline of the tile shape that fits the device's shared memory
-// (`limit` bytes per block), or 0 if not even two stages fit.
-int tc_pair_stages_fit(const Mlp& mlp, int sparks_per_tile, size_t limit);
+// (`limit` bytes per block) beside K-tail buffers for `kt_mmas` MMAs, or 0
+// if not even two stages fit.
+int tc_pair_stages_fit(const Mlp& mlp, int sparks_per_tile, size_t limit, int kt_mmas = 0);
 
-// Set a pair plan's tile shape and pipeline depth (re-encoding the W1 maps,
-// whose box is half a tile's rows) and its kernel's attributes; MGFWA_EINVAL
-// for a shape the kernel does not have or a depth that does not fit.  Every
-// shape and depth gives every spark bitwise the same fitness.
-mgfwa_status tc_pair_configure(TcPlan& plan, const Mlp& mlp, int sparks_per_tile, int stages);
-// Time every tile shape and depth on `count` rows of the planned buffers
+// Set a pair plan's tile shape, pipeline depth and K-tail buffers
+// (re-encoding the W1 maps, whose box is half a tile's rows) and its
+// kernel's attributes.  ktail: 1 = the partial last K atom through the
+// K-tail buffers, 0 = as a stage of its own, -1 = the buffers where the
+// network has such an atom and they fit beside the pipeline.  MGFWA_EINVAL
+// for a shape the kernel does not have, a depth that does not fit, or
+// ktail = 1 where the network has no such atom or the buffers do not fit.
+// Every shape, depth and K-tail choice gives every spark bitwise the same
+// fitness.
+mgfwa_status tc_pair_configure(TcPlan& plan, const Mlp& mlp, int sparks_per_tile, int stages, int ktail = -1);
+// Time every tile shape, depth and K-tail choice on `count` rows of the planned buffers
 // (as launch_fitness_tc would run them, on stream s; `partial` is
 // overwritten) and keep the fastest.  Choices are cached per device and
 // problem shape for the process, so a second handle of the same shape

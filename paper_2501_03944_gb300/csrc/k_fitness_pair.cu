@@ -36,11 +36,16 @@
 //           operand through a view of K as atoms x 128 bytes): a stage takes
 //           about the same time to arrive whatever its size, so fewer, larger
 //           stages carry more bytes per unit time.  The atom that d_in ends
-//           in, when partial, is a step of its own through the plain view,
-//           whose fill past d_in is zero.  The operand loads of both CTAs complete on the even
-//           CTA's barriers (the CTA-pair form of the tiled load), whose
-//           producer expects both halves' bytes, so the MMA thread waits on
-//           one barrier per stage.
+//           in, when partial, is either a step of its own through the plain
+//           view, whose fill past d_in is zero, or (the K-tail buffers) one
+//           small load per MMA of it and per operand (32 bytes of K, 32-byte
+//           swizzle, zero past d_in) into one of two K-tail buffers, issued
+//           after the tile's first step: a stage costs about one ring cycle
+//           whatever it carries, so a ring of whole two-atom stages saves
+//           one cycle per tile.  The operand loads of both CTAs complete on
+//           the even CTA's barriers (the CTA-pair form of the tiled load),
+//           whose producer expects both halves' bytes, so the MMA thread
+//           waits on one barrier per stage.
 //   warp 1  TMEM allocation for the pair (both CTAs); in the even CTA, the
 //           single-thread MMA issuer.
 //   warps 2..  epilogue, one warp per spark of the tile and TMEM lane
@@ -71,6 +76,8 @@ constexpr int kMmaKB = 32;   // bytes of K per layer-1 MMA (16 BF16 or 32 E4M3)
 constexpr int kMaxStg = 8;
 constexpr int kTBufs = 3;    // tail buffers: the producer runs ahead of layer 2
 constexpr int kCols = 512;   // two halves of 256 columns
+constexpr int kKtBox = 32;   // bytes of K per K-tail load row: one MMA's K, one 32-byte swizzle row
+constexpr int kMaxKt = 3;    // K-tail MMAs a buffer may hold
 
 // Tile shapes (S sparks of h1 hidden units, N = S * h1 accumulator columns
 // of a TMEM half of 256):
@@ -105,6 +112,8 @@ struct PairSmem {
   uint64_t bias_full[kTBufs];  // this CTA's biases of the buffer's tile landed
   uint64_t w2_full[kTBufs];    // even CTA: both CTAs' W2 (and W3) halves of the buffer's tile landed
   uint64_t w2_empty;           // three layers: layer 3 read the single W2/W3 buffer
+  uint64_t kt_full[2];         // even CTA: both CTAs' K-tail loads of the buffer's tile landed
+  uint64_t kt_empty[2];        // the K-tail MMAs of the buffer's tile completed
   uint64_t tail_empty[kTBufs]; // the MMAs and this CTA's epilogue are done with the buffer's tile
   uint64_t mma_done;
   uint32_t tmem_base;
@@ -185,6 +194,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
     k_fitness_pair(const __grid_constant__ CUtensorMap tmap_x3, const __grid_constant__ CUtensorMap tmap_x,
                    const __grid_constant__ CUtensorMap tmap_w3, const __grid_constant__ CUtensorMap tmap_w,
                    const __grid_constant__ CUtensorMap tmap_w2, const __grid_constant__ CUtensorMap tmap_wl3,
+                   const __grid_constant__ CUtensorMap tmap_xt, const __grid_constant__ CUtensorMap tmap_wt,
                    PairArgs a, const PairMember* __restrict__ members, int32_t n_members) {
   griddep_wait();
   griddep_launch_dependents();
@@ -208,6 +218,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
   constexpr uint32_t kAtomB = (kNT / 2) * kRowB;           // one K atom of this CTA's half of the tile's W1 rows
   constexpr uint32_t kStageA = 2 * kAtomA;                 // a stage: two atoms of each operand
   constexpr uint32_t kStageB = 2 * kAtomB;
+  constexpr uint32_t kKtA = kPM * kKtBox;                  // one K-tail MMA's K of this CTA's samples
+  constexpr uint32_t kKtB = (kNT / 2) * kKtBox;            // and of its half of the tile's W1 rows
+  constexpr int kKtElems = F8 ? 32 : 16;                   // K elements per K-tail load
   static_assert((kN2 / 2) % 8 == 0 && (NL / 2) % 8 == 0, "each W2 / W3 half is whole 8-row swizzle groups");
   static_assert(S >= 1 && kNT <= 256 && (!kShared || NL <= H1 / 2), "a tile's columns fit in a TMEM half");
   static_assert(!kL3 || (H2 % 64 == 0 && H2 <= H1 / 2 && H2 / 2 + NL <= H1 / 2 && NL == 16),
@@ -216,8 +229,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
 
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* stage_a = base;
-  uint8_t* stage_b = base + (size_t)a.stages * kStageA;
+  // [2 buffers][kt_region A loads, kt_region B loads], each a multiple of 1024 bytes, before the stages
+  uint8_t* ktail = base;
+  const uint32_t kt_buf = (uint32_t)a.kt_region * (kKtA + kKtB);
+  auto kt_a = [&](int buf, int k) { return ktail + (uint32_t)buf * kt_buf + (uint32_t)k * kKtA; };
+  auto kt_b = [&](int buf, int k) {
+    return ktail + (uint32_t)buf * kt_buf + (uint32_t)a.kt_region * kKtA + (uint32_t)k * kKtB;
+  };
+  // the partial last atom of a member goes through the K-tail buffers when they can hold it
+  auto kt_on = [&](const PairArgs& m) { return m.kt > 0 && m.kt <= a.kt_region; };
+  uint8_t* stage_a = base + 2 * kt_buf;
+  uint8_t* stage_b = stage_a + (size_t)a.stages * kStageA;
   uint8_t* w2s = stage_b + (size_t)a.stages * kStageB;                               // [kWB][S][kWSpark]
   float* tails = reinterpret_cast<float*>(w2s + (size_t)kWB * S * kWSpark);          // [kTBufs][S][kTailF]
   float* red = tails + (size_t)kTBufs * S * kTailF;                                  // [S][4]
@@ -271,6 +293,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
       mbar_init(&sm->tail_empty[b], 1 + kEpi);
     }
     mbar_init(&sm->w2_empty, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sm->kt_full[b], 1);
+      mbar_init(&sm->kt_empty[b], 1);
+    }
     mbar_init(&sm->mma_done, 1);
     sm->abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -302,6 +328,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
       bool ok = true;
       int cur = 0, fenced = -1;
       int w_last = -1;  // three layers: the last tile whose W2/W3 loads were issued
+      int kt_n = 0;     // tiles whose K-tail loads were issued
       for (int t = pair; t < tiles && ok; t += npairs, ++local) {
         const int lt = member_at(t, cur);
         const PairArgs& m = args_of(cur);
@@ -311,9 +338,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
         const CUtensorMap* mw = kGroup ? &members[cur].w : &tmap_w;
         const CUtensorMap* mw2 = kGroup ? &members[cur].w2 : &tmap_w2;
         const CUtensorMap* mwl3 = kGroup ? &members[cur].wl3 : &tmap_wl3;
+        const CUtensorMap* mxt = kGroup ? &members[cur].xt : &tmap_xt;
+        const CUtensorMap* mwt = kGroup ? &members[cur].wt : &tmap_wt;
         if (kGroup && fenced != cur) {
           // the member's maps were written to global memory by the host: order the tensor-map proxy's reads
-          for (const CUtensorMap* mp : {mx3, mx, mw3, mw, mw2, mwl3})
+          for (const CUtensorMap* mp : {mx3, mx, mw3, mw, mw2, mwl3, mxt, mwt})
             asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mp) : "memory");
           fenced = cur;
         }
@@ -356,7 +385,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
         const int row_x = mt * (2 * kPM) + (int)rank * kPM;
         const int row_w = (m.first_spark + s0) * H1 + (int)rank * (kNT / 2);
         const int n_pairs = (m.n_full + 1) / 2;
-        for (int kb = 0; kb < m.n_steps; ++kb, ++it) {
+        const bool kt = kt_on(m);
+        const int steps = kt ? n_pairs : m.n_steps;
+        for (int kb = 0; kb < steps; ++kb, ++it) {
           if (kL3 && w_last != local && mbar_test_wait(&sm->w2_empty, ((uint32_t)local & 1u) ^ 1u)) issue_w();
           const int st = (int)(it % (uint32_t)a.stages);
           const uint32_t ph = (it / (uint32_t)a.stages) & 1u;
@@ -376,6 +407,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
             tma_load_2d_pair(stage_a + (size_t)st * kStageA, mx, m.n_full * kBK, row_x, bar);
             tma_load_2d_pair(stage_b + (size_t)st * kStageB, mw, m.n_full * kBK, row_w, bar);
           }
+          if (kt && kb == 0) {
+            // the partial last atom into a K-tail buffer (needed only after the tile's last stage), zero
+            // past d_in
+            const int kbuf = kt_n & 1;
+            if (!wait(&sm->kt_empty[kbuf], ((uint32_t)(kt_n >> 1) & 1u) ^ 1u, 1u)) {
+              ++it;  // this step's stage is armed: the drain below counts it
+              ok = false;
+              break;
+            }
+            if (lead) mbar_expect_tx(&sm->kt_full[kbuf], 2u * (uint32_t)m.kt * (kKtA + kKtB));
+            const uint32_t kbar = map_to(&sm->kt_full[kbuf], 0u);
+            for (int k = 0; k < m.kt; ++k) {
+              tma_load_2d_pair(kt_a(kbuf, k), mxt, m.n_full * kBK + k * kKtElems, row_x, kbar);
+              tma_load_2d_pair(kt_b(kbuf, k), mwt, m.n_full * kBK + k * kKtElems, row_w, kbar);
+            }
+            ++kt_n;
+          }
         }
         if (kL3 && ok && w_last != local) {
           if (!wait(&sm->w2_empty, ((uint32_t)local & 1u) ^ 1u, 1u)) {
@@ -393,6 +441,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
         if (lead && !kL3) mbar_drain(&sm->w2_full[l % kTBufs], (uint32_t)((l / kTBufs) & 1), a.status, kDrain);
       }
       if (lead && kL3 && w_last >= 0) mbar_drain(&sm->w2_full[0], (uint32_t)(w_last & 1), a.status, kDrain);
+      if (lead)
+        for (int j = kt_n > 2 ? kt_n - 2 : 0; j < kt_n; ++j)
+          mbar_drain(&sm->kt_full[j & 1], (uint32_t)(j >> 1) & 1u, a.status, kDrain);
       if (lead && it > 0) {
         const uint32_t last = it - 1;
         for (uint32_t j = (last + 1 > (uint32_t)a.stages ? last + 1 - a.stages : 0); j <= last; ++j)
@@ -483,6 +534,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
         return true;
       };
       int cur = 0;
+      int kt_n = 0;  // tiles whose K-tail MMAs were issued
       for (int t = pair; t < tiles && ok; t += npairs, ++local) {
         const int lt = member_at(t, cur);
         const PairArgs& m = args_of(cur);
@@ -492,7 +544,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(b * 256);
         const int n_pairs = (m.n_full + 1) / 2;
-        for (int kb = 0; kb < m.n_steps; ++kb, ++it) {
+        const bool kt = kt_on(m);
+        const int steps = kt ? n_pairs : m.n_steps;
+        for (int kb = 0; kb < steps; ++kb, ++it) {
           if (!advance(false)) {
             ok = false;
             break;
@@ -527,6 +581,26 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
           commit_both(&sm->empty[st]);
         }
         if (!ok) break;
+        if (kt) {
+          // the partial last atom from its K-tail buffer, after every full atom (the same K order as a stage
+          // of its own)
+          const int kbuf = kt_n & 1;
+          if (!wait(&sm->kt_full[kbuf], (uint32_t)(kt_n >> 1) & 1u, 2u)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          for (int k = 0; k < m.kt; ++k) {
+            const uint64_t da = smem_desc_sw32(smem_u32(kt_a(kbuf, k)));
+            const uint64_t db = smem_desc_sw32(smem_u32(kt_b(kbuf, k)));
+            if (F8)
+              mma2_e4m3(d_tmem, da, db, idesc1, 1u);
+            else
+              mma2_bf16(d_tmem, da, db, idesc1, 1u);
+          }
+          commit_both(&sm->kt_empty[kbuf]);
+          ++kt_n;
+        }
         commit_both(&sm->tmem_full[b]);
         if (!advance(true)) {
           ok = false;
@@ -712,13 +786,13 @@ cudaError_t launch_pair(const TcPlan& plan, const PairArgs& args, cudaStream_t s
     const int pairs = group_tiles < plan.pairs ? group_tiles : plan.pairs;
     return launch_pdl(k_fitness_pair<H1, H2, NL, S, F8, true>, dim3(2 * pairs), dim3(pair_threads(S)),
                       plan.smem_bytes, s, plan.tmap_x3, plan.tmap_x, plan.tmap_wk, plan.tmap_w, plan.tmap_w2b,
-                      plan.tmap_w3b, args, members, n_members);
+                      plan.tmap_w3b, plan.tmap_xt, plan.tmap_wt, args, members, n_members);
   }
   const int tiles = args.m_pairs * args.n_tiles;
   const int pairs = tiles < plan.pairs ? tiles : plan.pairs;
   return launch_pdl(k_fitness_pair<H1, H2, NL, S, F8, false>, dim3(2 * pairs), dim3(pair_threads(S)),
                     plan.smem_bytes, s, plan.tmap_x3, plan.tmap_x, plan.tmap_wk, plan.tmap_w, plan.tmap_w2b,
-                    plan.tmap_w3b, args, static_cast<const PairMember*>(nullptr), 0);
+                    plan.tmap_w3b, plan.tmap_xt, plan.tmap_wt, args, static_cast<const PairMember*>(nullptr), 0);
 }
 
 // The kernel instance of the plan: h1 (and h2), the logit rows, the tile shape (shared or separate logits)
@@ -774,6 +848,8 @@ PairArgs make_args(const TcPlan& plan, const Mlp& mlp, int64_t first, const floa
     const int rem = mlp.widths[0] - a.n_full * bk;   // K elements of the partial last atom
     a.k_last = (rem + ke - 1) / ke;
     a.n_steps = (a.n_full + 1) / 2 + (rem > 0 ? 1 : 0);
+    a.kt = tc_pair_ktail_mmas(mlp, plan.f8);
+    a.kt_region = plan.ktail;
   }
   a.stages = plan.stages;
   a.C = mlp.widths[mlp.n_layers];
@@ -827,10 +903,22 @@ size_t tc_pair_fixed_smem(const Mlp& mlp, int S) {
 
 size_t tc_pair_stage_bytes(int h1, int S) { return 2 * ((size_t)kPM * kRowB + (size_t)(S * h1 / 2) * kRowB); }
 
+int tc_pair_ktail_mmas(const Mlp& mlp, bool f8) {
+  const int bk = f8 ? 128 : 64, ke = f8 ? 32 : 16;  // K elements per atom and per MMA
+  const int d_in = mlp.widths[0], rem = d_in % bk;
+  const int k = (rem + ke - 1) / ke;
+  return d_in >= bk && k >= 1 && k <= kMaxKt ? k : 0;
+}
+
+size_t tc_pair_ktail_bytes(int h1, int S, int mmas) {
+  return 2 * (size_t)mmas * kKtBox * ((size_t)kPM + (size_t)(S * h1 / 2));
+}
+
 int tc_pair_max_stages() { return kMaxStg; }
 
-int tc_pair_stages_fit(const Mlp& mlp, int S, size_t limit) {
-  const size_t fixed = tc_pair_fixed_smem(mlp, S), stage = tc_pair_stage_bytes(mlp.widths[1], S);
+int tc_pair_stages_fit(const Mlp& mlp, int S, size_t limit, int kt_mmas) {
+  const size_t fixed = tc_pair_fixed_smem(mlp, S) + tc_pair_ktail_bytes(mlp.widths[1], S, kt_mmas),
+               stage = tc_pair_stage_bytes(mlp.widths[1], S);
   int st = kMaxStg;
   while (st >= 2 && fixed + (size_t)st * stage > limit) --st;
   return st >= 2 ? st : 0;
@@ -850,6 +938,8 @@ void tc_pair_member(const TcPlan& plan, const Mlp& mlp, int64_t first, const flo
   out->w = plan.tmap_w;
   out->w2 = plan.tmap_w2b;
   out->wl3 = plan.tmap_w3b;
+  out->xt = plan.tmap_xt;
+  out->wt = plan.tmap_wt;
   out->a = make_args(plan, mlp, first, rows, ld, count, scale, partial, status);
   out->tiles = out->a.m_pairs * out->a.n_tiles;
   out->tile_start = 0;
@@ -867,6 +957,8 @@ int launch_fitness_pair_group(const TcPlan& plan, const Mlp& mlp, const PairMemb
   if (n < 1 || total_tiles < 1) return 0;
   PairArgs a = {};
   a.stages = plan.stages;
+  a.kt_region = plan.ktail;  // the shared-memory layout of the launch; a member with more K-tail MMAs takes
+                             // its partial atom as a stage
   a.status = status;
   a.wait_budget = plan.wait_budget;
   return dispatch_pair(plan, mlp, a, s, false, nullptr, table_dev, n, total_tiles) == cudaSuccess

@@ -490,7 +490,8 @@ EncodeTiled get_encoder() {
 }
 
 bool encode(CUtensorMap* map, CUtensorMapDataType type, uint32_t rank, const void* ptr, const cuuint64_t* dims,
-            const cuuint64_t* strides, const cuuint32_t* box) {
+            const cuuint64_t* strides, const cuuint32_t* box,
+            CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_128B) {
   EncodeTiled enc = get_encoder();
   if (!enc) {
     g_err = "cuTensorMapEncodeTiled unavailable";
@@ -498,7 +499,7 @@ bool encode(CUtensorMap* map, CUtensorMapDataType type, uint32_t rank, const voi
   }
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(map, type, rank, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                   swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     g_err = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
     return false;
@@ -570,16 +571,18 @@ bool tc_supported(const int32_t* widths, int n_layers) {
 
 namespace {
 
-// The pair plan's tile shape: S sparks per tile, `stages` pipeline stages, and the first-layer operand's
-// maps, whose box is half a tile's rows.
-mgfwa_status pair_shape(TcPlan& plan, const Mlp& mlp, int S, int stages) {
+// The pair plan's tile shape: S sparks per tile, `stages` pipeline stages, K-tail buffers for `kt` MMAs
+// (0 = none), and the first-layer operand's maps, whose box is half a tile's rows.
+mgfwa_status pair_shape(TcPlan& plan, const Mlp& mlp, int S, int stages, int kt) {
   const int h1 = mlp.widths[1], d_in = mlp.widths[0];
   const int esize = plan.f8 ? 1 : 2, bk = kRowBytes / esize;
   const CUtensorMapDataType dt = plan.f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   plan.sparks_per_tile = S;
   plan.n_tile = S * h1;
   plan.stages = stages;
-  plan.smem_bytes = tc_pair_fixed_smem(mlp, S) + (size_t)stages * tc_pair_stage_bytes(h1, S);
+  plan.ktail = kt;
+  plan.smem_bytes = tc_pair_fixed_smem(mlp, S) + (size_t)stages * tc_pair_stage_bytes(h1, S) +
+                    tc_pair_ktail_bytes(h1, S, kt);
   {
     // first-layer operand [max_rows*h1][d_in], box (one 128-byte row of K) x half a tile's rows
     cuuint64_t dims[2] = {(cuuint64_t)d_in, (cuuint64_t)plan.w_rows};
@@ -594,6 +597,16 @@ mgfwa_status pair_shape(TcPlan& plan, const Mlp& mlp, int S, int stages) {
     cuuint64_t sw[2] = {(cuuint64_t)d_in * esize, (cuuint64_t)kRowBytes};
     cuuint32_t bw[3] = {(cuuint32_t)bk, (cuuint32_t)(plan.n_tile / 2), 2};
     if (!encode(&plan.tmap_wk, dt, 3, plan.w_base, dw, sw, bw)) return MGFWA_ECUDA;
+  }
+  if (tc_pair_ktail_mmas(mlp, plan.f8) > 0) {
+    // the same operand, box one MMA's K (32 bytes) x half a tile's rows, 32-byte swizzle: the K-tail loads
+    cuuint64_t dims[2] = {(cuuint64_t)d_in, (cuuint64_t)plan.w_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)d_in * esize};
+    cuuint32_t box[2] = {(cuuint32_t)(32 / esize), (cuuint32_t)(plan.n_tile / 2)};
+    if (!encode(&plan.tmap_wt, dt, 2, plan.w_base, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_32B))
+      return MGFWA_ECUDA;
+  } else {
+    plan.tmap_wt = plan.tmap_w;  // unused: no partial atom for the K-tail buffers
   }
   return MGFWA_OK;
 }
@@ -676,17 +689,30 @@ mgfwa_status tc_plan(TcPlan& plan, const Mlp& mlp, const OpDesc& op, const float
     } else {
       plan.tmap_w3b = plan.tmap_w2b;  // unused by the two-layer kernels
     }
+    if (tc_pair_ktail_mmas(mlp, f8) > 0) {
+      // X, box one MMA's K (32 bytes) x 128 samples, 32-byte swizzle: the K-tail loads of the partial atom
+      cuuint64_t dims[2] = {(cuuint64_t)d_in, (cuuint64_t)mlp.N};
+      cuuint64_t strides[1] = {(cuuint64_t)d_in * esize};
+      cuuint32_t box[2] = {(cuuint32_t)(32 / esize), kBM};
+      if (!encode(&plan.tmap_xt, dt, 2, mlp.Xop, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_32B)) return MGFWA_ECUDA;
+    } else {
+      plan.tmap_xt = plan.tmap_x;  // unused
+    }
     plan.tmap_w2 = plan.tmap_w2b;  // unused by the pair kernel
     plan.tmap_w3 = plan.tmap_w2b;
-    // the default shape: the logits in the sparks' own columns, the deepest pipeline that fits
+    // the default shape: the logits in the sparks' own columns, the deepest pipeline that fits, and the
+    // K-tail buffers if they fit beside it
     const int S = tc_pair_sparks(mlp, true);
-    const int stages = tc_pair_stages_fit(mlp, S, (size_t)prop.sharedMemPerBlockOptin);
+    const size_t limit = (size_t)prop.sharedMemPerBlockOptin;
+    const int stages = tc_pair_stages_fit(mlp, S, limit);
     if (stages < 2) {
       g_err = "shared memory too small for the tensor-core pair tiles";
       return MGFWA_EINVAL;
     }
+    const int kt_want = tc_pair_ktail_mmas(mlp, f8);
+    const int kt = kt_want > 0 && tc_pair_stages_fit(mlp, S, limit, kt_want) >= stages ? kt_want : 0;
     plan.ready = true;
-    const mgfwa_status st = pair_shape(plan, mlp, S, stages);
+    const mgfwa_status st = pair_shape(plan, mlp, S, stages, kt);
     if (st != MGFWA_OK) plan.ready = false;
     return st;
   }
@@ -794,7 +820,7 @@ cudaError_t tc_prepare(TcPlan& plan, const Mlp& mlp) {
   return dispatch(plan, mlp, a, nullptr, true);
 }
 
-mgfwa_status tc_pair_configure(TcPlan& plan, const Mlp& mlp, int sparks_per_tile, int stages) {
+mgfwa_status tc_pair_configure(TcPlan& plan, const Mlp& mlp, int sparks_per_tile, int stages, int ktail) {
   if (!plan.ready || !plan.pair) return MGFWA_EINVAL;
   if (sparks_per_tile <= 0 ||
       (sparks_per_tile != tc_pair_sparks(mlp, true) && sparks_per_tile != tc_pair_sparks(mlp, false))) {
@@ -811,7 +837,19 @@ mgfwa_status tc_pair_configure(TcPlan& plan, const Mlp& mlp, int sparks_per_tile
     g_err = "pair kernel: that pipeline depth does not fit in shared memory";
     return MGFWA_EINVAL;
   }
-  const mgfwa_status st = pair_shape(plan, mlp, sparks_per_tile, stages);
+  if (ktail < -1 || ktail > 1) {
+    g_err = "pair kernel: the K-tail choice is -1, 0 or 1";
+    return MGFWA_EINVAL;
+  }
+  const int kt_want = tc_pair_ktail_mmas(mlp, plan.f8);
+  const bool kt_fits = kt_want > 0 && stages <= tc_pair_stages_fit(mlp, sparks_per_tile, (size_t)limit, kt_want);
+  if (ktail == 1 && !kt_fits) {
+    g_err = kt_want > 0 ? "pair kernel: the K-tail buffers do not fit beside that pipeline"
+                        : "pair kernel: the network has no partial K atom for the K-tail buffers";
+    return MGFWA_EINVAL;
+  }
+  const int kt = ktail != 0 && kt_fits ? kt_want : 0;
+  const mgfwa_status st = pair_shape(plan, mlp, sparks_per_tile, stages, kt);
   if (st != MGFWA_OK) return st;
   if (tc_pair_prepare(plan, mlp) != cudaSuccess) {
     g_err = "pair kernel attributes";
@@ -823,9 +861,9 @@ mgfwa_status tc_pair_configure(TcPlan& plan, const Mlp& mlp, int sparks_per_tile
 namespace {
 
 // Tuned choices per (device, operand type, d_in, h1, classes, 256-sample tiles rounded up to a power of
-// two, launch rows rounded up to a power of two): sparks per tile and stages.
+// two, launch rows rounded up to a power of two): sparks per tile, stages and the K-tail choice.
 std::mutex g_tune_mu;
-std::map<std::array<int64_t, 7>, std::pair<int, int>> g_tuned;
+std::map<std::array<int64_t, 7>, std::array<int, 3>> g_tuned;
 
 int64_t pow2_at_least(int64_t v) {
   int64_t r = 1;
@@ -860,17 +898,23 @@ mgfwa_status tc_pair_tune(TcPlan& plan, const Mlp& mlp, const float* rows, int64
   std::lock_guard<std::mutex> lock(g_tune_mu);
   auto hit = g_tuned.find(key);
   if (hit != g_tuned.end()) {
-    const mgfwa_status st = tc_pair_configure(plan, mlp, hit->second.first, hit->second.second);
+    const mgfwa_status st = tc_pair_configure(plan, mlp, hit->second[0], hit->second[1], hit->second[2]);
     if (st == MGFWA_OK) plan.tuned = 1;
     return st;
   }
-  // the candidates: both tile shapes, every depth from two to the deepest that fits
-  std::vector<std::pair<int, int>> cand;
+  // the candidates: both tile shapes, every depth from two to the deepest that fits, the partial K atom as a
+  // stage and (where the buffers fit beside that depth) through the K-tail buffers
+  std::vector<std::array<int, 3>> cand;
+  const int kt_want = tc_pair_ktail_mmas(mlp, plan.f8);
   for (bool shared : {true, false}) {
     const int S = tc_pair_sparks(mlp, shared);
     if (S <= 0 || (!shared && S == tc_pair_sparks(mlp, true))) continue;
     const int fit = tc_pair_stages_fit(mlp, S, (size_t)limit);
-    for (int st = 2; st <= fit; ++st) cand.emplace_back(S, st);
+    const int fit_kt = kt_want > 0 ? tc_pair_stages_fit(mlp, S, (size_t)limit, kt_want) : 0;
+    for (int st = 2; st <= fit; ++st) {
+      cand.push_back({S, st, 0});
+      if (st <= fit_kt) cand.push_back({S, st, 1});
+    }
   }
   if (cand.empty()) return MGFWA_OK;
   std::vector<float> best(cand.size(), 1e30f);
@@ -886,7 +930,7 @@ mgfwa_status tc_pair_tune(TcPlan& plan, const Mlp& mlp, const float* rows, int64
   constexpr int kRounds = 4, kLaunches = 2;
   for (int r = 0; r < kRounds && st == MGFWA_OK; ++r) {
     for (size_t c = 0; c < cand.size() && st == MGFWA_OK; ++c) {
-      st = tc_pair_configure(plan, mlp, cand[c].first, cand[c].second);
+      st = tc_pair_configure(plan, mlp, cand[c][0], cand[c][1], cand[c][2]);
       if (st != MGFWA_OK) break;
       if (launch_fitness_tc(plan, mlp, 0, rows, ld, count, scale, partial, status, s) < 0 ||
           cudaEventRecord(e0, s) != cudaSuccess) {
@@ -913,7 +957,7 @@ mgfwa_status tc_pair_tune(TcPlan& plan, const Mlp& mlp, const float* rows, int64
   size_t pick = 0;
   for (size_t c = 1; c < cand.size(); ++c)
     if (best[c] < best[pick]) pick = c;
-  st = tc_pair_configure(plan, mlp, cand[pick].first, cand[pick].second);
+  st = tc_pair_configure(plan, mlp, cand[pick][0], cand[pick][1], cand[pick][2]);
   if (st != MGFWA_OK) return st;
   plan.tuned = 1;
   g_tuned[key] = cand[pick];

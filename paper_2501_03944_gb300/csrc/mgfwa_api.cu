@@ -1788,21 +1788,23 @@ mgfwa_status mgfwa_debug_wait_budget(mgfwa_t* h, uint64_t ticks) {
   return MGFWA_OK;
 }
 
-mgfwa_status mgfwa_debug_pair_tile(const mgfwa_t* h, int32_t* sparks_per_tile, int32_t* stages, int32_t* tuned) {
+mgfwa_status mgfwa_debug_pair_tile(const mgfwa_t* h, int32_t* sparks_per_tile, int32_t* stages, int32_t* tuned,
+                                   int32_t* k_tail) {
   if (!h) return MGFWA_EINVAL;
   const bool on = h->tc.ready && h->tc.pair;
   if (sparks_per_tile) *sparks_per_tile = on ? h->tc.sparks_per_tile : -1;
   if (stages) *stages = on ? h->tc.stages : -1;
   if (tuned) *tuned = on ? h->tc.tuned : -1;
+  if (k_tail) *k_tail = on ? h->tc.ktail : -1;
   return MGFWA_OK;
 }
 
-mgfwa_status mgfwa_debug_set_pair_tile(mgfwa_t* h, int32_t sparks_per_tile, int32_t stages) {
+mgfwa_status mgfwa_debug_set_pair_tile(mgfwa_t* h, int32_t sparks_per_tile, int32_t stages, int32_t k_tail) {
   mgfwa_status st = check_usable(h);
   if (st != MGFWA_OK) return st;
   if (!h->tc.ready || !h->tc.pair) return fail(h, MGFWA_EINVAL, "the handle is not on the CTA-pair fitness kernel");
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h, "set pair tile synchronise");
-  st = tc_pair_configure(h->tc, h->mlp, sparks_per_tile, stages);
+  st = tc_pair_configure(h->tc, h->mlp, sparks_per_tile, stages, k_tail);
   if (st != MGFWA_OK) return fail(h, st, "%s", tc_last_error());
   h->tc.tuned = 0;
   // the next generation is captured again, with the new shape

@@ -149,6 +149,19 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return d;
 }
 
+// The same for a K-major operand in 32-byte swizzled rows (one MMA's K of
+// 16 BF16 or 32 E4M3 per row, as a 32-byte-swizzled tiled load writes
+// them): 8-row groups 256 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);        // start address
+  d |= (uint64_t)1 << 16;                         // leading byte offset (unused: K fits in one swizzle row)
+  d |= (uint64_t)(256 >> 4) << 32;                // stride byte offset: 8 rows x 32 B
+  d |= (uint64_t)1 << 46;                         // descriptor version for tcgen05
+  d |= (uint64_t)6 << 61;                         // 32-byte swizzle
+  return d;
+}
+
 // Instruction descriptors: D FP32; A and B K-major; kind::f16 with BF16
 // inputs (format 1), kind::tf32 with TF32 inputs (format 2), kind::f8f6f4
 // with E4M3 inputs (format 0).  m is the MMA's M: 128 for one CTA, 256 for

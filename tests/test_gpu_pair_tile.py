@@ -3,15 +3,18 @@ cross-entropy of the network its position encodes, over the batch) is one
 column block of a contraction; the kernel has two tile shapes -- the logits
 written into the spark's own accumulator columns once its activations are
 packed (256 / h1 sparks a tile), or into columns of their own
-(256 / (h1 + logit rows)) -- and a pipeline of 2 .. the deepest that fits.
-Each spark's columns hold its own sums, accumulated in the same order in
-every shape, so every shape and depth must give bitwise the same fitness:
-the creation-time tuner that picks the fastest changes no result.  Checked
-on whole runs (fireworks, best, the last generation's explosion and
-guiding fitness) over the networks the kernel has: h1 = 64 and 128, 16 and
-32 logit rows, d_in ending on a K atom or not, BF16 and E4M3 operands, and
-the three-layer 3072-128-64-10 network (whose tile is always the shared
-shape: only the depth varies)."""
+(256 / (h1 + logit rows)) -- a pipeline of 2 .. the deepest that fits, and
+the partial last K atom (d_in not a multiple of the atom) either as a stage
+of its own or through the K-tail buffers (32-byte swizzled, one load per
+MMA of it).  Each spark's columns hold its own sums, accumulated in the
+same order in every shape, so every shape, depth and K-tail choice must
+give bitwise the same fitness: the creation-time tuner that picks the
+fastest changes no result.  Checked on whole runs (fireworks, best, the
+last generation's explosion and guiding fitness) over the networks the
+kernel has: h1 = 64 and 128, 16 and 32 logit rows, d_in ending on a K atom
+or not (one and two K-tail MMAs, a last MMA half zero fill), BF16 and E4M3
+operands, and the three-layer 3072-128-64-10 network (whose tile is always
+the shared shape: only the depth varies)."""
 import numpy as np
 import pytest
 
@@ -54,6 +57,14 @@ def _state(pkg, h):
             h.read(pkg.MGFWA_BUF_FIT_G), h.read(pkg.MGFWA_BUF_BEST_F), h.info().generations)
 
 
+def _kt(w, prec, pkg):
+    """The K-tail MMAs of the network's partial last atom (0: none, or no full atom before it)."""
+    bk, ke = (128, 32) if prec == pkg.MGFWA_FP8 else (64, 16)
+    rem = w.widths[0] % bk
+    k = -(-rem // ke)
+    return k if w.widths[0] >= bk and 1 <= k <= 3 else 0
+
+
 def _tiles(w):
     """The tile shapes the kernel has for the network: (shared, separate or None)."""
     h1, C = w.widths[1], w.widths[-1]
@@ -67,47 +78,63 @@ def _tiles(w):
 def test_every_tile_gives_the_same_run(pkg, i):
     name, w, prec, kw = _cases(pkg)[i]
     shared, separate = _tiles(w)
+    kt = _kt(w, prec, pkg)
     with _make(pkg, w, 31 + i, prec, kw) as h:
-        S0, st0, tuned = h.pair_tile()
-        assert tuned == 1 and S0 in (shared, separate) and st0 >= 2, (name, S0, st0, tuned)
+        S0, st0, tuned, kt0 = h.pair_tile()
+        assert tuned == 1 and S0 in (shared, separate) and st0 >= 2 and kt0 in (0, kt), (name, S0, st0, tuned, kt0)
         h.run()
         ref = _state(pkg, h)
     assert ref[-1] >= 2
     tried = []
     for S in (shared, separate) if separate else (shared,):
         for st in range(2, 9):
-            with _make(pkg, w, 31 + i, prec, kw) as h:
-                try:
-                    h.set_pair_tile(S, st)
-                except pkg.MgfwaError as e:
-                    assert e.status == pkg.MGFWA_EINVAL and st > 2, (name, S, st, str(e))
-                    break
-                assert h.pair_tile() == (S, st, 0)
-                h.run()
-                got = _state(pkg, h)
-            for a, b in zip(ref[:-1], got[:-1]):
-                assert np.array_equal(a, b), (name, S, st)
-            assert got[-1] == ref[-1]
-            tried.append((S, st))
+            fits = False
+            for k_tail in (0, 1) if kt else (0,):
+                with _make(pkg, w, 31 + i, prec, kw) as h:
+                    try:
+                        h.set_pair_tile(S, st, k_tail)
+                    except pkg.MgfwaError as e:
+                        assert e.status == pkg.MGFWA_EINVAL and (st > 2 or k_tail == 1), (name, S, st, k_tail, str(e))
+                        continue
+                    assert h.pair_tile() == (S, st, 0, kt if k_tail else 0)
+                    h.run()
+                    got = _state(pkg, h)
+                for a, b in zip(ref[:-1], got[:-1]):
+                    assert np.array_equal(a, b), (name, S, st, k_tail)
+                assert got[-1] == ref[-1]
+                tried.append((S, st, k_tail))
+                fits = True
+            if not fits:
+                break
     assert len(tried) >= (3 if separate else 2), tried
+    if kt:
+        assert any(t[2] == 1 for t in tried), (name, tried)
 
 
 def test_tile_settings_out_of_range(pkg):
     name, w, prec, kw = _cases(pkg)[0]
     shared, separate = _tiles(w)
     with _make(pkg, w, 5, prec, kw) as h:
-        for S, st in ((shared + 1, 2), (separate, 1), (shared, 9), (0, 2)):
+        for S, st, k_tail in ((shared + 1, 2, -1), (separate, 1, -1), (shared, 9, -1), (0, 2, -1), (shared, 2, 2),
+                              (shared, 2, -2)):
             with pytest.raises(pkg.MgfwaError) as e:
-                h.set_pair_tile(S, st)
+                h.set_pair_tile(S, st, k_tail)
             assert e.value.status == pkg.MGFWA_EINVAL
         # the handle is still usable and on its tuned tile
         assert h.pair_tile()[2] == 1
         h.step(1)
+    # K-tail buffers for a network whose d_in ends on a whole atom
+    w256 = _cases(pkg)[3][1]
+    with _make(pkg, w256, 5, pkg.MGFWA_BF16, {}) as h:
+        assert h.pair_tile()[3] == 0
+        with pytest.raises(pkg.MgfwaError) as e:
+            h.set_pair_tile(_tiles(w256)[0], 2, 1)
+        assert e.value.status == pkg.MGFWA_EINVAL
 
 
 def test_off_the_pair_kernel(pkg):
     w = W.scaled(W.MLP_784_64_10, n_samples=256, n_fireworks=2, sparks_per_firework=8, guiding_per_firework=2)
     with _make(pkg, w, 3, pkg.MGFWA_FP32, {}) as h:
-        assert h.pair_tile() == (-1, -1, -1)
+        assert h.pair_tile() == (-1, -1, -1, -1)
         with pytest.raises(pkg.MgfwaError):
             h.set_pair_tile(4, 2)
