@@ -196,8 +196,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
                    const __grid_constant__ CUtensorMap tmap_w2, const __grid_constant__ CUtensorMap tmap_wl3,
                    const __grid_constant__ CUtensorMap tmap_xt, const __grid_constant__ CUtensorMap tmap_wt,
                    PairArgs a, const PairMember* __restrict__ members, int32_t n_members) {
-  griddep_wait();
-  griddep_launch_dependents();
   constexpr bool kL3 = H2 > 0;
   constexpr int kNT = S * H1;                              // layer-1 accumulator columns per tile
   constexpr bool kShared = kL3 || S * (H1 + NL) > 256;     // the logits share the spark's accumulator columns
@@ -311,6 +309,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair_threads(S), 1)
   cluster_sync();  // both CTAs' barriers initialised and TMEM allocated before any cross-CTA access
   tc_fence_after();
   const uint32_t tmem_base = sm->tmem_base;
+  // the set-up above touches nothing the previous kernel writes, so it overlaps that kernel's tail
+  griddep_wait();
+  griddep_launch_dependents();
 
   // A wait that gives up also stops the peer CTA.
   const uint32_t peer_abort = map_to((const void*)&sm->abort_flag, rank ^ 1u);

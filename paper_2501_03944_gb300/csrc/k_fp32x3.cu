@@ -226,8 +226,6 @@ static_assert(kStages <= kMaxStages, "barrier arrays");
 template <int H, int NL>
 __global__ void __launch_bounds__(kThreads, 1)
     k_l1_fp32x3(const __grid_constant__ CUtensorMap tmap_xs, const __grid_constant__ CUtensorMap tmap_ws, Args a) {
-  griddep_wait();
-  griddep_launch_dependents();
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   constexpr int V = kN / H;
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -263,6 +261,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = sb->tmem_base;
+  // the set-up above touches nothing the previous kernel writes, so it overlaps that kernel's tail
+  griddep_wait();
+  griddep_launch_dependents();
 
   if (warp == 0) {
     if (lane == 0) {

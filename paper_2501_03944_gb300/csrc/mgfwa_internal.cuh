@@ -104,13 +104,15 @@ struct OpDesc {
 
 // Programmatic dependent launch.  A kernel started by launch_pdl may be
 // scheduled while its predecessor on the stream is still running, so every
-// kernel of the library begins with griddep_wait(), which returns once the
+// kernel of the library calls griddep_wait(), which returns once the
 // predecessor grid has completed and its memory writes are visible (at once
-// when the launch was an ordinary one), and then calls
+// when the launch was an ordinary one), before it touches any memory
+// another kernel writes -- most at their first line, the tensor-core
+// kernels after setting up their barriers and TMEM -- and then calls
 // griddep_launch_dependents(), which lets the next such launch be scheduled
 // as soon as every CTA of this grid has started.  What overlaps is the next
-// kernel's launch and CTA dispatch with this kernel's last wave, never its
-// memory accesses.
+// kernel's launch, CTA dispatch and that set-up with this kernel's last
+// wave, never a memory access that depends on it.
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void griddep_launch_dependents() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
