@@ -12,8 +12,8 @@ give bitwise the same fitness: the creation-time tuner that picks the
 fastest changes no result.  Checked on whole runs (fireworks, best, the
 last generation's explosion and guiding fitness) over the networks the
 kernel has: h1 = 64 and 128, 16 and 32 logit rows, d_in ending on a K atom
-or not (one and two K-tail MMAs, a last MMA half zero fill), BF16 and E4M3
-operands, and the three-layer 3072-128-64-10 network (whose tile is always
+or not (one, two and three K-tail MMAs, a last MMA half zero fill), BF16 and
+E4M3 operands, and the three-layer 3072-128-64-10 network (whose tile is always
 the shared shape: only the depth varies)."""
 import numpy as np
 import pytest
@@ -44,6 +44,9 @@ def _cases(pkg):
                                          sparks_per_firework=12), pkg.MGFWA_BF16, {}),
         ("3072-128-64-10 fp8", W.scaled(base, widths=(3072, 128, 64, 10), acts=(1, 0), n_samples=520,
                                         sparks_per_firework=12), pkg.MGFWA_FP8, {"elite_rescore": 0}),
+        # three K-tail MMAs (48 of 64 BF16 / 80 of 128 E4M3 elements in the partial atom)
+        ("176-64-20 bf16", W.scaled(base, widths=(176, 64, 20)), pkg.MGFWA_BF16, {}),
+        ("208-64-10 fp8", W.scaled(base, widths=(208, 64, 10)), pkg.MGFWA_FP8, {"elite_rescore": 0}),
     ]
 
 
@@ -74,7 +77,7 @@ def _tiles(w):
     return 256 // h1, 256 // (h1 + nl)
 
 
-@pytest.mark.parametrize("i", range(7))
+@pytest.mark.parametrize("i", range(9))
 def test_every_tile_gives_the_same_run(pkg, i):
     name, w, prec, kw = _cases(pkg)[i]
     shared, separate = _tiles(w)
