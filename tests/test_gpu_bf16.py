@@ -151,7 +151,8 @@ def test_bf16_generation_phase_by_phase(pkg):
 
 
 def test_bf16_full_size_784_64_10(pkg):
-    """Full 784-64-10 workload (1000 explosion sparks x 2048 samples per launch): sampled sparks vs the oracle."""
+    """Full 784-64-10 workload (1000 explosion sparks x 2048 samples per launch): every explosion and guiding
+    spark of the launch vs the oracle (about 6 s of FP64 on 16 host cores), and vs the FP32 path."""
     w = W.MLP_784_64_10
     seed = 4
     X, y = W.make_data(w)
@@ -161,9 +162,8 @@ def test_bf16_full_size_784_64_10(pkg):
         run.phase(pkg.MGFWA_PHASE_EVAL_E)
         sparks = run.read(pkg.MGFWA_BUF_SPARKS)
         fe = run.read(pkg.MGFWA_BUF_FIT_E)
-        pick = np.concatenate([np.arange(4), np.random.default_rng(2).choice(np.arange(4, 996), 92, replace=False),
-                               [996, 997, 998, 999]])
-        assert np.all(_rel(fe[pick], prob.fitness_many(sparks[pick], 8)) <= BF16_RTOL)
+        err = _rel(fe, prob.fitness_many(sparks[:len(fe)], 16))
+        assert np.all(err <= BF16_RTOL), (int(np.argmax(err)), float(err.max()))
         for ph in (pkg.MGFWA_PHASE_RANK, pkg.MGFWA_PHASE_GUIDE, pkg.MGFWA_PHASE_EVAL_G, pkg.MGFWA_PHASE_SELECT):
             run.phase(ph)
         guides = run.read(pkg.MGFWA_BUF_GUIDES)
