@@ -80,6 +80,36 @@ def test_fp8_full_size_3072_128_64_10(pkg):
     assert np.all(_rel(fe[pick], want) <= RTOL), np.max(_rel(fe[pick], want))
 
 
+def test_fp8_full_size_784_64_10(pkg):
+    """The bench's E4M3 launch: 784-64-10 at its full size (1000 explosion sparks x 2048 samples, 40 guiding
+    sparks): the first and last sparks of the launch, 56 others and every guiding spark against the oracle's
+    quantized network (the FP64 evaluations on host threads)."""
+    from concurrent.futures import ThreadPoolExecutor
+    w = W.MLP_784_64_10
+    X, y = W.make_data(w)
+    prob = oracle.Problem.for_workload(w, X, y)
+    with pkg.Mgfwa.for_workload(w, 9, precision=pkg.MGFWA_FP8, X=X, y=y, elite_rescore=0) as run:
+        info = run.info()
+        run.phase(pkg.MGFWA_PHASE_EXPLODE)
+        run.phase(pkg.MGFWA_PHASE_EVAL_E)
+        sparks = run.read(pkg.MGFWA_BUF_SPARKS)
+        fe = run.read(pkg.MGFWA_BUF_FIT_E)
+        for ph in (pkg.MGFWA_PHASE_RANK, pkg.MGFWA_PHASE_GUIDE, pkg.MGFWA_PHASE_EVAL_G):
+            run.phase(ph)
+        guides = run.read(pkg.MGFWA_BUF_GUIDES)
+        fg = run.read(pkg.MGFWA_BUF_FIT_G)
+    n = len(fe)
+    pick = np.concatenate([np.arange(4), np.random.default_rng(8).choice(np.arange(4, n - 4), 56, replace=False),
+                           np.arange(n - 4, n)])
+    rows = [sparks[i] for i in pick] + list(guides[:len(fg)])
+    with ThreadPoolExecutor(8) as ex:
+        want = np.array(list(ex.map(
+            lambda x: oracle.fitness_fp8(prob, x, info.fp8_inv_scale_x, info.fp8_inv_scale_w), rows)))
+    got = np.concatenate([fe[pick], fg])
+    err = _rel(got, want)
+    assert np.all(err <= RTOL), (int(np.argmax(err)), float(err.max()))
+
+
 def test_fp8_rejects_unaligned_inputs_and_other_precisions(pkg):
     w = W.scaled(W.MLP_784_64_10, widths=(8, 32, 3), acts=(0,), n_samples=64)
     X, y = W.make_data(w)
