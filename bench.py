@@ -279,6 +279,39 @@ def cpu_baseline(steps: int = 1, warmup: int = 0):
                       f"{WORKLOAD.name}, FP64 fitness, {threads} threads", "seconds": dt}
 
 
+def oracle_rates():
+    """The oracle's rates on the three MLP workloads, single-thread and on every host core, on bounded
+    samples (about 10 s in all): the 8-16-3 workload's whole run; the 784-64-10 and 3072-128-64-10
+    workloads' fitness of sampled explosion sparks (the generation's dominant cost)."""
+    import oracle as orc
+    threads = os.cpu_count() or 1
+    out = {"cores": threads}
+    w0 = W.MLP_8_16_3
+    X0, y0 = W.make_data(w0)
+    prob0 = orc.Problem.for_workload(w0, X0, y0)
+    p0 = orc.params_for(w0)
+    r0 = {}
+    for key, n in (("single_thread", 1), ("all_cores", threads)):
+        t0 = time.perf_counter()
+        res = orc.run(p0, prob0, 0, w0.eval_budget, n_threads=n)
+        r0[key] = res["evals"] / (time.perf_counter() - t0)
+    out[w0.name] = dict(r0, unit=UNIT, sample=f"one whole run ({w0.eval_budget} evaluations)")
+    for w, n1, nall in ((W.MLP_784_64_10, 8, 4 * threads), (W.MLP_3072_128_64_10, 1, threads)):
+        X, y = W.make_data(w)
+        prob = orc.Problem.for_workload(w, X, y)
+        p1 = orc.params_for(w, mu=1)
+        fw_x, fw_a = orc.init(p1, 0)
+        sparks = orc.explode(p1, 0, 1, fw_x, fw_a)
+        r = {}
+        for key, n, cnt in (("single_thread", 1, n1), ("all_cores", threads, nall)):
+            t0 = time.perf_counter()
+            prob.fitness_many(sparks[:cnt], n)
+            r[key] = cnt / (time.perf_counter() - t0)
+        out[w.name] = dict(r, unit=UNIT, sample=f"FP64 fitness of {n1} (one thread) and {nall} (all cores) explosion "
+                                                 "sparks of the first generation")
+    return out
+
+
 def reference_arm(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -549,6 +582,7 @@ def gpu_arm(args):
         if world == 1 and not args.no_cpu_baseline:
             c = cpu_baseline(steps=3)
             cb = {k2: c[k2] for k2 in ("value", "unit", "cores", "kind", "sample")}
+            cb["by_workload"] = oracle_rates()
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": {"bf16": "bf16", "fp32": "f32", "fp8": "e4m3"}[args.precision],
