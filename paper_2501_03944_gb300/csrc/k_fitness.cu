@@ -238,9 +238,7 @@ __global__ void k_fitness_finish(const float* __restrict__ partial, int32_t mtil
   griddep_launch_dependents();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= count) return;
-  float s = partial[r];
-  for (int mt = 1; mt < mtiles; ++mt) s += partial[(int64_t)mt * count + r];
-  fit[idx != nullptr ? idx[r] : r] = __fdiv_rn(s, n_f);
+  fit[idx != nullptr ? idx[r] : r] = __fdiv_rn(tile_sum(partial, r, count, mtiles), n_f);
 }
 
 __global__ void __launch_bounds__(256) k_sphere(const float* __restrict__ rows, int64_t ld, int64_t D,

@@ -34,10 +34,9 @@ __global__ void k_rank(Problem p, float* __restrict__ fit_e, int32_t* __restrict
   for (int a = threadIdx.x; a < g; a += blockDim.x) {
     if (partial) {
       const int64_t r = (int64_t)i * p.lam + base + a;
-      float s = partial[r];
-      for (int mt = 1; mt < mtiles; ++mt) s += partial[(int64_t)mt * count + r];
-      fe[a] = __fdiv_rn(s, n_f);
-      f[a] = fe[a];
+      const float v = __fdiv_rn(tile_sum(partial, r, count, mtiles), n_f);
+      fe[a] = v;
+      f[a] = v;
     } else {
       f[a] = fe[a];
     }
@@ -57,6 +56,9 @@ __global__ void k_rank(Problem p, float* __restrict__ fit_e, int32_t* __restrict
 }
 
 constexpr int kSelThreads = 256;
+constexpr int kSelStage = 1024;  // fireworks per run whose fitness the selection's serial part reads from shared memory
+constexpr int kSelChunk = 8;     // candidates per lane loaded before they are compared
+constexpr int kPickStage = 2048; // candidates per firework the elite pick stages in shared memory
 
 __device__ __forceinline__ void take_if_before(float& bf, int& bc, float of, int oc) {
   if (oc >= 0 && (bc < 0 || before(of, oc, bf, bc))) {
@@ -92,13 +94,26 @@ __global__ void __launch_bounds__(kSelThreads) k_select_decide(Problem p, const 
   const uint32_t gen = *gens_done + 1u;  // this generation
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int n_cand = p.lam + p.m;
+  // the run's fireworks' fitness before and after this selection, for the serial part below
+  __shared__ float sh_f[kSelStage], sh_old[kSelStage];
+  const bool staged = p.mu <= kSelStage;
   for (int il = warp; il < p.mu; il += kSelThreads / 32) {
     const int i = b * p.mu + il;  // global firework
     float bf = 0.0f;
     int bc = -1;
-    for (int c = lane; c < n_cand; c += 32) {
-      const float f = c < p.lam ? fit_e[(int64_t)i * p.lam + c] : fit_g[(int64_t)i * p.m + (c - p.lam)];
-      take_if_before(bf, bc, f, c);
+    // the candidates in chunks of kSelChunk per lane, every load of a chunk issued before its compares
+    for (int c = lane; c < n_cand; c += 32 * kSelChunk) {
+      float v[kSelChunk];
+#pragma unroll
+      for (int u = 0; u < kSelChunk; ++u) {
+        const int cu = c + 32 * u;
+        v[u] = cu >= n_cand ? 0.0f
+               : cu < p.lam ? fit_e[(int64_t)i * p.lam + cu]
+                            : fit_g[(int64_t)i * p.m + (cu - p.lam)];
+      }
+#pragma unroll
+      for (int u = 0; u < kSelChunk; ++u)
+        if (c + 32 * u < n_cand) take_if_before(bf, bc, v[u], c + 32 * u);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -108,8 +123,11 @@ __global__ void __launch_bounds__(kSelThreads) k_select_decide(Problem p, const 
     }
     if (lane == 0) {
       const float amp = fw_amp[i];
-      f_old[i] = fw_f[i];
-      if (rank_key(bf) < rank_key(fw_f[i])) {
+      const float fo = fw_f[i];
+      f_old[i] = fo;
+      float fn = fo;
+      if (rank_key(bf) < rank_key(fo)) {
+        fn = bf;
         fw_f[i] = bf;
         fw_amp[i] = __fmul_rn(amp, p.c_a);
         winner[i] = bc;
@@ -117,11 +135,16 @@ __global__ void __launch_bounds__(kSelThreads) k_select_decide(Problem p, const 
         fw_amp[i] = __fmul_rn(amp, p.c_r);
         winner[i] = -1;
       }
+      if (staged) {
+        sh_f[il] = fn;
+        sh_old[il] = fo;
+      }
     }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    const float* f = fw_f + (int64_t)b * p.mu;
+    const float* f = staged ? sh_f : fw_f + (int64_t)b * p.mu;
+    const float* fold = staged ? sh_old : f_old + (int64_t)b * p.mu;
     int bi = -1;
     float bfv = best_f[b];
     for (int i = 0; i < p.mu; ++i) {
@@ -142,7 +165,7 @@ __global__ void __launch_bounds__(kSelThreads) k_select_decide(Problem p, const 
     for (int il = 0; il < p.mu; ++il) {
       const int64_t z = (int64_t)b * p.mu + il;
       int32_t lo = 0;
-      const float fo = f_old[z], fn = f[il];
+      const float fo = fold[il], fn = f[il];
       if (p.lo_gmax > 0 && il != e && isfinite(fo) && isfinite(fn)) {
         const float proj = __fmaf_rn(-__fsub_rn(fo, fn), g_rem, fn);
         if (proj > rb) {
@@ -268,16 +291,32 @@ __global__ void k_elite_pick(Problem p, const float* __restrict__ fit_e, float* 
   griddep_launch_dependents();
   const int z = blockIdx.x;
   const int lane = threadIdx.x;
+  const int n_cand = p.lam + p.m;
+  // the firework's candidates' fitness (explosion 0..lam-1, then guiding), staged once for the E passes
+  __shared__ float cand[kPickStage];
+  const bool staged = n_cand <= kPickStage;
   if (partial) {
     for (int q = lane; q < p.m; q += 32) {
       const int64_t r = (int64_t)z * p.m + q;
-      float s = partial[r];
-      for (int mt = 1; mt < mtiles; ++mt) s += partial[(int64_t)mt * count + r];
-      fit_g[r] = __fdiv_rn(s, n_f);
+      const float v = __fdiv_rn(tile_sum(partial, r, count, mtiles), n_f);
+      fit_g[r] = v;
+      if (staged) cand[p.lam + q] = v;
     }
-    __syncwarp();
+  } else if (staged) {
+    for (int q = lane; q < p.m; q += 32) cand[p.lam + q] = fit_g[(int64_t)z * p.m + q];
   }
-  const int n_cand = p.lam + p.m;
+  if (staged) {
+    for (int c = lane; c < p.lam; c += 32 * kSelChunk) {
+      float v[kSelChunk];
+#pragma unroll
+      for (int u = 0; u < kSelChunk; ++u)
+        v[u] = c + 32 * u < p.lam ? fit_e[(int64_t)z * p.lam + c + 32 * u] : 0.0f;
+#pragma unroll
+      for (int u = 0; u < kSelChunk; ++u)
+        if (c + 32 * u < p.lam) cand[c + 32 * u] = v[u];
+    }
+  }
+  __syncwarp();
   const int64_t n_e = (int64_t)p.B * p.mu * p.lam;
   float prev_f = 0.0f;
   int prev_c = -1;
@@ -285,7 +324,9 @@ __global__ void k_elite_pick(Problem p, const float* __restrict__ fit_e, float* 
     float bf = 0.0f;
     int bc = -1;
     for (int c = lane; c < n_cand; c += 32) {
-      const float f = c < p.lam ? fit_e[(int64_t)z * p.lam + c] : fit_g[(int64_t)z * p.m + (c - p.lam)];
+      const float f = staged ? cand[c]
+                      : c < p.lam ? fit_e[(int64_t)z * p.lam + c]
+                                  : fit_g[(int64_t)z * p.m + (c - p.lam)];
       if (prev_c >= 0 && !before(prev_f, prev_c, f, c)) continue;  // already picked
       take_if_before(bf, bc, f, c);
     }

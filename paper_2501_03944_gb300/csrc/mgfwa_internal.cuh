@@ -223,6 +223,25 @@ __device__ __forceinline__ bool before(float fa, int ia, float fb, int ib) {
   return a < b || (a == b && ia < ib);
 }
 
+// The fitness sum of spark r from the per-sample-tile loss sums partial[mt *
+// count + r]: the tiles added in tile order (the fitness-finish arithmetic
+// every kernel that finishes a mean shares), loads issued eight at a time so
+// that a tile's latency is paid once per eight tiles.
+__device__ __forceinline__ float tile_sum(const float* __restrict__ partial, int64_t r, int32_t count,
+                                          int32_t mtiles) {
+  float s = partial[r];
+  int mt = 1;
+  for (; mt + 8 <= mtiles; mt += 8) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = partial[(int64_t)(mt + u) * count + r];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += v[u];
+  }
+  for (; mt < mtiles; ++mt) s += partial[(int64_t)mt * count + r];
+  return s;
+}
+
 // Sets the calling thread's error text (what mgfwa_last_error(NULL) returns).
 void set_thread_error(const char* msg);
 
