@@ -208,14 +208,15 @@ def test_bf16_whole_run_learns(pkg):
     assert abs(bf - prob.fitness(bx)) <= 1e-12 * bf
 
 
-@pytest.mark.parametrize("N,mu,E", [(300, 3, 3), (2048, 5, 2)])
-def test_elite_candidates_are_rescored_in_fp32(pkg, N, mu, E):
+@pytest.mark.parametrize("N,mu,E,lam", [(300, 3, 3, 20), (2048, 5, 2, 20), (64, 2, 2, 2048)])
+def test_elite_candidates_are_rescored_in_fp32(pkg, N, mu, E, lam):
     """With BF16 fitness, each firework's E best candidates (by BF16 fitness, (fitness, index) order) get their
     fitness recomputed by the FP32 path before selection; the others keep their BF16 values.  At 2048 samples
     the 10 re-scored rows x 16 sample tiles engage the FP32-accurate tensor-core first layer; at 300 samples
-    the CUDA-core products run."""
+    the CUDA-core products run; with 2048 + 4 candidates a firework has more than the pick stages in shared
+    memory."""
     import torch
-    w = W.scaled(W.MLP_784_64_10, n_samples=N, n_fireworks=mu, sparks_per_firework=20, guiding_per_firework=4)
+    w = W.scaled(W.MLP_784_64_10, n_samples=N, n_fireworks=mu, sparks_per_firework=lam, guiding_per_firework=4)
     X, y = W.make_data(w)
     mu, lam, m = w.n_fireworks, w.sparks_per_firework, w.guiding_per_firework
     with pkg.Mgfwa.for_workload(w, 8, precision=pkg.MGFWA_BF16, X=X, y=y, elite_rescore=E) as run:

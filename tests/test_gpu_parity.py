@@ -61,6 +61,10 @@ SMALL_CASES = {
                              guiding_per_firework=4),
     "odd_dim_8-3-2": W.scaled(W.MLP_8_16_3, widths=(8, 3, 2), n_samples=64),
     "sphere30": W.SPHERE_30,
+    # more fireworks per run than the selection stages in shared memory (its serial part reads them from
+    # global memory then)
+    "sphere30_mu1030": W.scaled(W.SPHERE_30, n_fireworks=1030, sparks_per_firework=4, guiding_per_firework=2,
+                                eval_budget=W.budget_for_generations(1030, 4, 2, 5)),
 }
 
 
